@@ -1,0 +1,557 @@
+"""Pins of the FP64 oracle against closed forms, library routines, physics and
+brute force -- never against itself.  CPU only.
+
+Each test names the property it pins and the passage it follows:
+calibration (Sec. 4.1, Table 1 read noise), the Alard-Lupton kernel fit and
+direct subtraction (Sec. 4.2, Table 2), noise maps (Sec. 3.2), detection of
+transient candidates (Sec. 4.2), clipped coaddition (Sec. 4.1.3).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.signal
+import torch
+
+from paper_2207_14304_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- calibrate
+def test_calibrate_hand_values(ora):
+    g = json.load(open(os.path.join(GOLD, "calibrate_hand.json")))
+    raw = np.array([g["raw"]], np.uint16)
+    I, V, fl, n = ora.calibrate(raw, bias=g["bias"], dark=np.array([g["dark"]], np.float32),
+                                flat=np.array([g["flat"]], np.float32),
+                                bpm=np.array([g["bpm"]], np.uint8), gain=g["gain"],
+                                read_noise=g["read_noise"], sat=g["sat"])
+    assert n[0].tolist() == g["n"]
+    assert fl[0].tolist() == g["flags"]
+    np.testing.assert_allclose(I[0], g["I"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(V[0], g["V"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("gain", [1.0, 2.0])
+def test_calibrate_variance_matches_poisson_plus_read_noise(ora, gain):
+    """A flat 300 e- sky: empirical var(I) = 300 + rn^2 + gain^2/12 (ADU rounding),
+    and the propagated V averages 300 + rn^2 (Table 1: rn = 1.7 e-)."""
+    w = h = 1024
+    cal = synth.make_calib(w, h, seed=11, gain=gain, read_noise=1.7, dark_level=0.0,
+                           hot_frac=0.0, bad_frac=0.0, flat_rms=0.0)
+    cal.flat = torch.ones(h, w)
+    raw = synth.expose(torch.full((h, w), 300.0), cal, seed=12).numpy()
+    I, V, fl, _ = ora.calibrate(raw, bias=cal.bias, dark=cal.dark.numpy(),
+                                flat=cal.flat.numpy(), bpm=cal.bpm.numpy(), gain=gain,
+                                read_noise=1.7)
+    want = 300.0 + 1.7 ** 2 + gain ** 2 / 12.0
+    assert abs(I.var() / want - 1) < 0.005
+    assert abs(V.mean() / (300.0 + 1.7 ** 2) - 1) < 0.005
+    assert abs(I.mean() - 300.0) < 0.1
+    assert not fl.any()
+
+
+def test_calibrate_flat_and_dark_act_linearly(ora):
+    rng = np.random.default_rng(3)
+    raw = rng.integers(150, 5000, size=(8, 16)).astype(np.uint16)
+    dark = rng.uniform(0, 20, size=raw.shape).astype(np.float32)
+    I1, V1, _, _ = ora.calibrate(raw, dark=np.zeros_like(dark), flat=np.ones_like(dark))
+    I2, V2, _, _ = ora.calibrate(raw, dark=np.zeros_like(dark), flat=np.full_like(dark, 2.0))
+    I3, _, _, _ = ora.calibrate(raw, dark=dark, flat=np.ones_like(dark))
+    np.testing.assert_allclose(I2, I1 / 2, rtol=1e-15)
+    np.testing.assert_allclose(V2, V1 / 4, rtol=1e-15)
+    np.testing.assert_allclose(I3, I1 - dark, rtol=1e-13, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- basis
+def test_basis_count_and_normalisation(ora):
+    b = ora.Basis(ksize=11)
+    B, pq = ora.basis(b)
+    assert B.shape == (49, 11, 11)          # 28 + 15 + 6
+    assert abs(B[0].sum() - 1) < 1e-14     # B_0 carries the photometric scale
+    for n in range(1, 49):
+        assert abs(B[n].sum()) < 1e-12      # Alard 2000: zero-sum companions
+        assert abs((B[n] ** 2).sum() - 1) < 1e-12
+    b2 = ora.Basis(ksize=21, spatial_degree=2, bg_degree=2)
+    assert b2.ncoeffs == 1 + 48 * 6 + 6 == 295
+    assert ora.Basis(ksize=11).ncoeffs == 50
+
+
+def test_basis_shapes_follow_gaussian_times_monomial(ora):
+    """For every function with an odd exponent (untouched by the sum
+    correction) B / (u^p v^q) must be radial with log-slope -1/(2 sigma_g^2)."""
+    b = ora.Basis(ksize=21, sigmas=(0.7, 1.5, 3.0), degrees=(6, 4, 2))
+    B, pq = ora.basis(b)
+    r = 10
+    u = np.arange(-r, r + 1)[None, :].repeat(21, 0)
+    v = u.T
+    for n in range(49):
+        g, p, q = pq[n]
+        if p % 2 == 0 and q % 2 == 0:
+            continue
+        sel = (u != 0) & (v != 0) & (u * u + v * v <= 16)
+        ratio = B[n][sel] / (u[sel].astype(float) ** p * v[sel].astype(float) ** q)
+        rho2 = (u[sel] ** 2 + v[sel] ** 2).astype(float)
+        slope, icpt = np.polyfit(rho2, np.log(np.abs(ratio)), 1)
+        sig = b.sigmas[g]
+        assert abs(slope * (-2 * sig * sig) - 1) < 1e-9, (n, g, p, q)
+        assert np.all(np.sign(ratio) == np.sign(ratio[0]))
+
+
+def test_spatial_terms_order_and_range(ora):
+    t = ora.spatial_terms(0, 99, 100, 100, 2)      # xt = -1, yt = +1
+    np.testing.assert_array_equal(t, [1, 1, 1, -1, -1, 1])
+    t = ora.spatial_terms(49.5, 49.5, 100, 100, 2)
+    np.testing.assert_allclose(t, [1, 0, 0, 0, 0, 0], atol=1e-15)
+
+
+def test_cholesky_against_numpy_and_singular(ora):
+    rng = np.random.default_rng(0)
+    A = rng.normal(size=(40, 40))
+    M = A @ A.T + 40 * np.eye(40)
+    st, Lm = ora.cholesky(M)
+    assert st == 0
+    np.testing.assert_allclose(Lm, np.linalg.cholesky(M), rtol=1e-12, atol=1e-12)
+    b = rng.normal(size=40)
+    np.testing.assert_allclose(ora.cholesky_solve(Lm, b), np.linalg.solve(M, b), rtol=1e-10)
+    S = A[:, :10] @ A[:, :10].T          # rank 10
+    assert ora.cholesky(S)[0] == -5
+
+
+# --------------------------------------------------------------------------- fit
+def _smooth_field(w, h, seed, n=60, sigma=1.2, sky=300.0):
+    cat = synth.star_catalog(n, w, h, seed=seed, flux_min=2e3, flux_max=2e5)
+    return synth.render(cat, w, h, sigma, sky=sky).numpy()
+
+
+def _grid_centers(w, h, g, m):
+    xs = np.linspace(m, w - 1 - m, g).round().astype(int)
+    ys = np.linspace(m, h - 1 - m, g).round().astype(int)
+    return np.array([(x, y) for y in ys for x in xs], np.int32)
+
+
+def _conv(R, K):
+    """True convolution (R (x) K)(x,y) = sum K(u,v) R(x-u, y-v) via scipy."""
+    return scipy.signal.convolve2d(R, K, mode="same", boundary="fill")
+
+
+def test_fit_recovers_in_span_kernel(ora):
+    w = h = 128
+    b = ora.Basis(ksize=11)
+    B, _ = ora.basis(b)
+    R = _smooth_field(w, h, 5)
+    rng = np.random.default_rng(9)
+    a = np.zeros(b.ncoeffs)
+    a[0] = 1.0
+    a[1:49] = rng.normal(0, 0.05, 48)
+    a[49] = 4.0
+    K = np.tensordot(a[:49], B, 1)
+    I = _conv(R, K) + a[49]
+    cen = _grid_centers(w, h, 4, 20)
+    var = np.ones_like(I)
+    res = ora.fit(I, var, R, np.zeros((h, w), np.uint8), cen, 21, b)
+    assert res.status == 0
+    # inputs are float32 at the boundary: compare against the fit of the f32-rounded images
+    np.testing.assert_allclose(res.coeffs, a, rtol=0, atol=2e-4 * np.abs(a).max())
+    Kfit, bg = ora.expand(b, res.coeffs)
+    assert np.abs(Kfit[0] - K).max() < 1e-4 * np.abs(K).max()
+
+
+def test_fit_exact_in_float64_inputs(ora):
+    """With images that are exact in float32 (integers), the in-span fit is exact to
+    FP64 round-off: the design, the normal equations and the solve are consistent."""
+    w = h = 96
+    b = ora.Basis(ksize=7, sigmas=(0.8, 1.6), degrees=(2, 1))
+    B, _ = ora.basis(b)
+    rng = np.random.default_rng(1)
+    R = rng.integers(0, 1000, size=(h, w)).astype(np.float64)
+    a = np.zeros(b.ncoeffs)
+    a[: b.nb] = rng.normal(0, 1, b.nb)
+    K = np.tensordot(a[: b.nb], B, 1)
+    I = _conv(R, K)
+    cen = _grid_centers(w, h, 3, 15)
+    # I is not exact in float32; fit against float32(I) and compare with the
+    # numpy least-squares solution of the same float32 data (library route).
+    I32 = I.astype(np.float32)
+    res = ora.fit(I32, np.ones_like(I32), R.astype(np.float32), np.zeros((h, w), np.uint8), cen, 9, b)
+    rows, tgt = [], []
+    for (xs, ys) in cen:
+        for y in range(ys - 4, ys + 5):
+            for x in range(xs - 4, xs + 5):
+                rows.append([_conv(R, B[n])[y, x] for n in range(b.nb)] + [1.0])
+                tgt.append(float(I32[y, x]))
+    sol = np.linalg.lstsq(np.array(rows), np.array(tgt), rcond=None)[0]
+    np.testing.assert_allclose(res.coeffs, sol, rtol=1e-7, atol=1e-9)
+
+
+def test_fit_normal_equations_brute_force_toy(ora):
+    """One 5x5 stamp, 3 basis functions: M and b equal C^T W C and C^T W I with C
+    built from scipy convolutions (independent of the oracle's loops)."""
+    w = h = 32
+    b = ora.Basis(ksize=5, sigmas=(1.0,), degrees=(1,))
+    B, _ = ora.basis(b)
+    rng = np.random.default_rng(4)
+    R = rng.uniform(100, 200, size=(h, w)).astype(np.float32)
+    I = rng.uniform(100, 200, size=(h, w)).astype(np.float32)
+    V = rng.uniform(1, 4, size=(h, w)).astype(np.float32)
+    res = ora.fit(I, V, R, np.zeros((h, w), np.uint8), np.array([[16, 15]], np.int32), 5, b)
+    Xs = [_conv(R.astype(np.float64), B[n]) for n in range(3)]
+    C, W, T = [], [], []
+    for y in range(13, 18):
+        for x in range(14, 19):
+            C.append([Xs[0][y, x], Xs[1][y, x], Xs[2][y, x], 1.0])
+            W.append(1.0 / float(V[y, x])); T.append(float(I[y, x]))
+    C, W, T = np.array(C), np.array(W), np.array(T, np.float64)
+    np.testing.assert_allclose(res.M, C.T @ (W[:, None] * C), rtol=1e-12)
+    np.testing.assert_allclose(res.b, C.T @ (W * T), rtol=1e-12)
+    assert res.dof == 25 - 4
+
+
+def test_fit_spatially_varying_kernel_and_background(ora):
+    w, h = 160, 128
+    b = ora.Basis(ksize=9, sigmas=(0.8, 1.8), degrees=(2, 1), spatial_degree=2, bg_degree=1)
+    B, _ = ora.basis(b)
+    R = _smooth_field(w, h, 8, n=120).astype(np.float64)
+    rng = np.random.default_rng(2)
+    a = rng.normal(0, 0.05, b.ncoeffs)
+    a[0] = 0.9
+    K, bg = ora.expand(b, a)
+    x = np.arange(w)[None, :]
+    y = np.arange(h)[:, None]
+    xt = (2 * x - (w - 1)) / (w - 1) + 0 * y
+    yt = (2 * y - (h - 1)) / (h - 1) + 0 * x
+    pk = [xt ** i * yt ** j for i in range(3) for j in range(3 - i)]
+    I = sum(pk[k] * _conv(R, K[k]) for k in range(6)) + bg[0] + bg[1] * yt + bg[2] * xt
+    res = ora.fit(I.astype(np.float32), np.ones((h, w), np.float32), R.astype(np.float32),
+                  np.zeros((h, w), np.uint8), _grid_centers(w, h, 5, 14), 15, b)
+    assert res.status == 0
+    np.testing.assert_allclose(res.coeffs, a, atol=1e-4)
+
+
+def test_fit_pure_scale_and_pure_background(ora):
+    """I = 2R: the kernel's sum (only B_0 has a nonzero sum) is the photometric
+    ratio 2 and the model reproduces I; I = R + 7: ratio 1 and background 7.
+    (A delta kernel is not in the Gaussian span, so the other coefficients are
+    the basis' best delta approximation, not zero.)"""
+    w = h = 96
+    b = ora.Basis(ksize=11)
+    R = _smooth_field(w, h, 3).astype(np.float32)
+    cen = _grid_centers(w, h, 3, 20)
+    one = np.ones((h, w), np.float32)
+    z = np.zeros((h, w), np.uint8)
+    for I, ratio, bgv in ((2 * R, 2.0, 0.0), (R + 7, 1.0, 7.0)):
+        r = ora.fit(I, one, R, z, cen, 15, b)
+        K, bg = ora.expand(b, r.coeffs)
+        assert abs(r.coeffs[0] - ratio) < 1e-4 and abs(K[0].sum() - ratio) < 1e-4
+        assert abs(bg[0] - bgv) < 0.05
+        Dd, _ = ora.subtract(I, one, R, np.zeros_like(R), z, K, bg, sdeg=0, bgdeg=0)
+        assert np.abs(Dd[5:-5, 5:-5]).max() < 1e-3 * np.abs(I).max()
+
+
+def test_fit_gaussian_kernel_moments(ora):
+    """Science at sigma 1.8 shifted by (0.3,-0.2) against a sigma 1.2 reference: the
+    fitted kernel has unit sum, first moment (0.3,-0.2), variance 1.8^2 - 1.2^2."""
+    w = h = 160
+    cat = synth.star_catalog(150, w, h, seed=21, flux_min=5e3, flux_max=5e5)
+    R = synth.render(cat, w, h, 1.2, sky=300.0).numpy().astype(np.float32)
+    I = synth.render(cat, w, h, 1.8, sky=300.0, shift=(0.3, -0.2)).numpy().astype(np.float32)
+    b = ora.Basis(ksize=11)
+    res = ora.fit(I, np.ones_like(I), R, np.zeros((h, w), np.uint8), _grid_centers(w, h, 6, 16), 21, b)
+    K, bg = ora.expand(b, res.coeffs)
+    K = K[0]
+    u = np.arange(-5, 6)[None, :]
+    v = u.T
+    s = K.sum()
+    mx, my = (K * u).sum() / s, (K * v).sum() / s
+    var = ((K * (u - mx) ** 2).sum() + (K * (v - my) ** 2).sum()) / (2 * s)
+    assert abs(s - 1) < 2e-3
+    assert abs(mx - 0.3) < 0.02 and abs(my + 0.2) < 0.02
+    assert abs(var / (1.8 ** 2 - 1.2 ** 2) - 1) < 0.05
+    assert abs(bg[0]) < 0.5
+
+
+# --------------------------------------------------------------------------- subtract / variance
+def test_subtract_exact_model_gives_zero(ora):
+    w = h = 80
+    b = ora.Basis(ksize=11)
+    B, _ = ora.basis(b)
+    R = _smooth_field(w, h, 6).astype(np.float64)
+    a = np.zeros(b.ncoeffs); a[0] = 1.1; a[5] = 0.03; a[49] = 2.5
+    K, bg = ora.expand(b, a)
+    I = _conv(R, K[0]) + 2.5
+    z = np.zeros((h, w), np.uint8)
+    Dd, Vd = ora.subtract(I.astype(np.float32), np.ones((h, w), np.float32), R.astype(np.float32),
+                          np.zeros((h, w), np.float32), z, K, bg, sdeg=0, bgdeg=0)
+    inner = Dd[5:-5, 5:-5]
+    assert np.abs(inner).max() < 1e-4 * np.abs(I).max()     # float32 inputs
+    assert (Dd[:5] == 0).all() and (Vd[:, :5] == 0).all() and (Vd[:, -5:] == 0).all()
+    np.testing.assert_array_equal(Vd[5:-5, 5:-5], 1.0)        # V_ref = 0 -> V_D = V_I
+
+
+def test_subtract_orientation_shifted_delta(ora):
+    """K = unit pixel at (u,v) = (1,0): (R (x) K)(x,y) = R(x-1, y)."""
+    w, h = 40, 30
+    rng = np.random.default_rng(5)
+    R = rng.uniform(0, 100, size=(h, w)).astype(np.float32)
+    I = rng.uniform(0, 100, size=(h, w)).astype(np.float32)
+    K = np.zeros((1, 3, 3)); K[0, 1, 2] = 1.0
+    Dd, _ = ora.subtract(I, np.ones_like(I), R, np.zeros_like(R), np.zeros((h, w), np.uint8), K,
+                         [0.0], sdeg=0, bgdeg=0)
+    want = I[1:-1, 1:-1].astype(np.float64) - R[1:-1, 0:-2]
+    np.testing.assert_array_equal(Dd[1:-1, 1:-1], want)
+
+
+def test_subtract_linear_in_science(ora):
+    w = h = 48
+    rng = np.random.default_rng(6)
+    R = rng.uniform(0, 100, size=(h, w)).astype(np.float32)
+    I = rng.integers(0, 100, size=(h, w)).astype(np.float32)   # I + 3J exact in float32
+    J = rng.integers(-50, 50, size=(h, w)).astype(np.float32)
+    K = rng.normal(size=(1, 5, 5))
+    z = np.zeros((h, w), np.uint8)
+    args = (np.ones_like(I), R, np.zeros_like(R), z, K, [0.0])
+    D1, _ = ora.subtract(I, *args, sdeg=0, bgdeg=0)
+    D2, _ = ora.subtract(I + 3 * J, *args, sdeg=0, bgdeg=0)
+    np.testing.assert_allclose((D2 - D1)[2:-2, 2:-2], 3 * J[2:-2, 2:-2], atol=1e-9)
+
+
+def test_subtract_spatially_varying_matches_library_convolution(ora):
+    w, h = 70, 50
+    rng = np.random.default_rng(7)
+    R = rng.uniform(0, 100, size=(h, w)).astype(np.float32)
+    I = rng.uniform(0, 100, size=(h, w)).astype(np.float32)
+    K = rng.normal(size=(6, 7, 7))
+    bg = rng.normal(size=3)
+    x = np.arange(w)[None, :] + 0 * np.arange(h)[:, None]
+    y = np.arange(h)[:, None] + 0 * np.arange(w)[None, :]
+    xt, yt = (2 * x - (w - 1)) / (w - 1), (2 * y - (h - 1)) / (h - 1)
+    pk = [xt ** i * yt ** j for i in range(3) for j in range(3 - i)]
+    want = I - sum(pk[k] * _conv(R.astype(np.float64), K[k]) for k in range(6)) - (
+        bg[0] + bg[1] * yt + bg[2] * xt)
+    Dd, _ = ora.subtract(I, np.ones_like(I), R, np.zeros_like(R), np.zeros((h, w), np.uint8), K, bg,
+                         sdeg=2, bgdeg=1)
+    np.testing.assert_allclose(Dd[3:-3, 3:-3], want[3:-3, 3:-3], rtol=1e-11, atol=1e-9)
+    xy = np.array([[3, 3], [10, 20], [66, 46], [0, 0]], np.int32)
+    Ds, _ = ora.subtract_at(xy, I, np.ones_like(I), R, np.zeros_like(R), np.zeros((h, w), np.uint8),
+                            K, bg, sdeg=2, bgdeg=1)
+    np.testing.assert_array_equal(Ds, [Dd[3, 3], Dd[20, 10], Dd[46, 66], 0.0])
+
+
+def test_difference_variance_constant_reference_variance(ora):
+    w = h = 40
+    rng = np.random.default_rng(8)
+    K = rng.normal(size=(1, 9, 9))
+    Vi = rng.uniform(1, 5, size=(h, w)).astype(np.float32)
+    _, Vd = ora.subtract(np.zeros((h, w), np.float32), Vi, np.zeros((h, w), np.float32),
+                         np.full((h, w), 2.5, np.float32), np.zeros((h, w), np.uint8), K, [0.0],
+                         sdeg=0, bgdeg=0)
+    np.testing.assert_allclose(Vd[4:-4, 4:-4], Vi[4:-4, 4:-4] + 2.5 * (K ** 2).sum(), rtol=1e-12)
+
+
+def test_difference_variance_matches_empirical_noise(ora):
+    """Independent white noise in I and R: var(D) = V_I + V_ref * sum K^2 (1e6 px)."""
+    w = h = 1040
+    g = torch.Generator().manual_seed(77)
+    Vi, Vr = 300.0, 10.0
+    I = (torch.randn(h, w, generator=g, dtype=torch.float64) * math.sqrt(Vi)).numpy().astype(np.float32)
+    R = (torch.randn(h, w, generator=g, dtype=torch.float64) * math.sqrt(Vr)).numpy().astype(np.float32)
+    u = np.arange(-5, 6)
+    G = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * 1.3 ** 2))
+    K = (G / G.sum())[None]
+    Dd, Vd = ora.subtract(I, np.full_like(I, Vi), R, np.full_like(R, Vr), np.zeros((h, w), np.uint8),
+                          K, [0.0], sdeg=0, bgdeg=0)
+    inner = Dd[5:-5, 5:-5]
+    assert abs(inner.var() / Vd[5:-5, 5:-5].mean() - 1) < 0.01
+
+
+# --------------------------------------------------------------------------- detect
+def test_detect_spike_connectivity_and_order(ora):
+    w, h = 40, 30
+    D = np.zeros((h, w), np.float32)
+    V = np.ones((h, w), np.float32)
+    D[5, 30] = 10          # single spike
+    D[10, 10] = 8; D[11, 11] = 9   # diagonal pair -> one component
+    D[20, 5] = 7; D[20, 7] = 7     # gap -> two components
+    D[25, 20] = 6; D[25, 21] = -6  # opposite signs -> two components
+    D[2, 2] = 5.0                  # exactly at threshold: kept (>=)
+    mask, src, n = ora.detect(D, V, np.zeros((h, w), np.uint8), 5.0, 1.5)
+    assert n == 7
+    assert [(s["py"], s["px"]) for s in src] == [(2, 2), (5, 30), (11, 11), (20, 5), (20, 7),
+                                                 (25, 20), (25, 21)]
+    assert [int(s["npix"]) for s in src] == [1, 1, 2, 1, 1, 1, 1]
+    assert [int(s["sign"]) for s in src] == [1, 1, 1, 1, 1, 1, -1]
+    assert mask[25, 21] == 2 and mask[25, 20] == 1 and mask[0, 0] == 0
+
+
+def test_detect_invalid_pixels_never_detected(ora):
+    w = h = 16
+    D = np.full((h, w), 100.0, np.float32)
+    V = np.ones((h, w), np.float32)
+    fl = np.zeros((h, w), np.uint8)
+    fl[:, :8] = 1
+    V[:, 8:12] = 0
+    D[:, 12:] = np.nan
+    mask, src, n = ora.detect(D, V, fl, 5.0, 1.5)
+    assert (mask == 4).all() and n == 0
+
+
+@pytest.mark.parametrize("nsig", [3.0, 4.0])
+def test_detect_false_positive_rate_is_gaussian_tail(ora, nsig):
+    w, h = 4096, 1024
+    g = torch.Generator().manual_seed(int(nsig * 10))
+    V = np.full((h, w), 2.0, np.float32)
+    D = (torch.randn(h, w, generator=g, dtype=torch.float64) * math.sqrt(2.0)).numpy().astype(np.float32)
+    mask, _, _ = ora.detect(D, V, np.zeros((h, w), np.uint8), nsig, 1.5, cap=1 << 16)
+    npos = int((mask & 1).astype(bool).sum())
+    nneg = int((mask & 2).astype(bool).sum())
+    p = 0.5 * math.erfc(nsig / math.sqrt(2))
+    exp = p * w * h
+    assert abs(npos - exp) < 5 * math.sqrt(exp)
+    assert abs(nneg - exp) < 5 * math.sqrt(exp)
+
+
+def test_detect_recovers_injected_gaussians(ora):
+    """Isolated injected sources (pixel-integrated Gaussian, sigma = psf_sigma):
+    at optimal S/N > 150 (centroid noise ~ sqrt(2) sigma / SNR < 0.017 px) the
+    centroid is within 0.05 px and the flux within max(3 sigma_F, 0.5 %); the
+    mean centroid offset (bias) is below 0.01 px."""
+    w = h = 512
+    sig = 1.8
+    rng = np.random.default_rng(12)
+    n_inj = 50
+    xs = rng.uniform(20, w - 20, n_inj)
+    ys = (np.arange(n_inj) + 0.5) * (h / n_inj) + rng.uniform(-1, 1, n_inj)
+    F = 10 ** rng.uniform(3, 5, n_inj)
+    cat = synth.Catalog(torch.tensor(xs), torch.tensor(ys), torch.tensor(F))
+    model = synth.render(cat, w, h, sig).numpy()
+    g = torch.Generator().manual_seed(5)
+    Vd = np.full((h, w), 300.0)
+    D = (model + torch.randn(h, w, generator=g, dtype=torch.float64).numpy() * np.sqrt(Vd)).astype(np.float32)
+    mask, src, n = ora.detect(D, Vd.astype(np.float32), np.zeros((h, w), np.uint8), 5.0, sig)
+    found = 0
+    offs = []
+    for i in range(n_inj):
+        d = (src["x"] - xs[i]) ** 2 + (src["y"] - ys[i]) ** 2
+        j = int(np.argmin(d))
+        if d[j] > 4:
+            continue
+        s = src[j]
+        if F[i] / (np.sqrt(4 * np.pi) * sig * np.sqrt(300.0)) < 150:
+            continue
+        found += 1
+        offs.append((s["x"] - xs[i], s["y"] - ys[i]))
+        assert abs(s["x"] - xs[i]) < 0.05 and abs(s["y"] - ys[i]) < 0.05, (i, s, xs[i], ys[i])
+        assert abs(s["flux"] - F[i]) <= max(3 * s["flux_err"], 0.005 * F[i]), (i, s, F[i])
+    assert found >= 12
+    assert np.abs(np.mean(offs, 0)).max() < 0.01
+
+
+# --------------------------------------------------------------------------- coadd
+def _cal_args(h, w):
+    return dict(bias=100, dark=np.zeros((h, w), np.float32), flat=np.ones((h, w), np.float32),
+                bpm=np.zeros((h, w), np.uint8), gain=1.0, read_noise=1.7)
+
+
+def test_coadd_constant_frames_bit_exact(ora):
+    nf, h, w = 7, 24, 40
+    raw = np.full((nf, h, w), 400, np.uint16)
+    sh = synth.uniform_shifts(nf, seed=3).numpy()
+    co, va, nu, _ = ora.coadd(raw, sh, **_cal_args(h, w))
+    inner = (slice(2, -2), slice(2, -2))
+    assert (co[inner] == 300.0).all()
+    assert (nu[inner] == nf).all()
+
+
+def test_coadd_rejects_outlier_and_means_the_rest(ora):
+    nf, h, w = 9, 8, 8
+    rng = np.random.default_rng(1)
+    raw = rng.integers(380, 420, size=(nf, h, w)).astype(np.uint16)
+    raw[4, 3, 3] += 10000
+    co, va, nu, _ = ora.coadd(raw, np.zeros((nf, 2), np.float32), **_cal_args(h, w))
+    assert nu[3, 3] == nf - 1
+    rest = np.delete(raw[:, 3, 3].astype(np.float64) - 100, 4)
+    assert abs(co[3, 3] - rest.mean()) < 1e-12
+
+
+def test_coadd_no_clip_zero_shift_is_arithmetic_mean(ora):
+    nf, h, w = 6, 10, 12
+    rng = np.random.default_rng(2)
+    raw = rng.integers(200, 60000, size=(nf, h, w)).astype(np.uint16)
+    co, va, nu, _ = ora.coadd(raw, np.zeros((nf, 2), np.float32), kappa=1e9, **_cal_args(h, w))
+    np.testing.assert_allclose(co, (raw.astype(np.float64) - 100).mean(0), rtol=1e-13)
+    np.testing.assert_allclose(va, (np.maximum(raw - 100.0, 0) + 1.7 ** 2).sum(0) / nf ** 2, rtol=1e-13)
+
+
+def test_coadd_integer_shift_is_translation(ora):
+    nf, h, w = 4, 10, 12
+    rng = np.random.default_rng(3)
+    raw = rng.integers(200, 600, size=(nf, h, w)).astype(np.uint16)
+    sh = np.tile(np.array([[1.0, 0.0]], np.float32), (nf, 1))
+    co, va, nu, _ = ora.coadd(raw, sh, kappa=1e9, **_cal_args(h, w))
+    want = (raw.astype(np.float64) - 100).mean(0)
+    np.testing.assert_allclose(co[:, :-1], want[:, 1:], rtol=1e-13)
+    assert (nu[:, -1] == 0).all() and (co[:, -1] == 0).all()
+
+
+def test_coadd_variance_matches_empirical_scatter(ora):
+    """30 shifted 300 e- sky frames, no clipping: var(coadd) over pixels equals the
+    propagated V (bilinear weights included)."""
+    nf, h, w = 30, 256, 256
+    cal = synth.make_calib(w, h, seed=1, dark_level=0.0, hot_frac=0, bad_frac=0, flat_rms=0)
+    cal.flat = torch.ones(h, w)
+    sky = torch.full((h, w), 300.0)
+    raw = np.stack([synth.expose(sky, cal, seed=100 + f).numpy() for f in range(nf)])
+    sh = synth.uniform_shifts(nf, seed=8).numpy()
+    co, va, nu, _ = ora.coadd(raw, sh, kappa=1e9, **_cal_args(h, w))
+    inner = (slice(2, -2), slice(2, -2))
+    emp = co[inner].var()
+    quant = (1 / 12.0) * va[inner].mean() / (300 + 1.7 ** 2)   # ADU rounding, not in V
+    assert abs(emp / (va[inner].mean() + quant) - 1) < 0.02
+
+
+def test_coadd_rejects_all_cosmic_rays(ora):
+    nf, h, w = 30, 64, 64
+    cal = synth.make_calib(w, h, seed=2, dark_level=0.0, hot_frac=0, bad_frac=0, flat_rms=0)
+    cal.flat = torch.ones(h, w)
+    sky = torch.full((h, w), 300.0)
+    raw = np.stack([synth.expose(sky, cal, seed=200 + f, cosmic_frac=0.01).numpy() for f in range(nf)])
+    hits = (raw.astype(np.int64) - 100 > 300 + 600)      # >= 1e3 e- added on a 300 e- sky
+    co, va, nu, _ = ora.coadd(raw, np.zeros((nf, 2), np.float32), **_cal_args(h, w))
+    assert hits.sum() > 0.008 * nf * h * w
+    # every hit is rejected; a 3-sigma clip also drops a few Gaussian-tail values
+    # (two-sided tail 0.27 % per value, ~0.08 per 30-value pixel)
+    extra = (nf - hits.sum(0)) - nu.astype(np.int64)
+    assert extra.min() >= 0
+    assert extra.mean() < 0.15
+    hit_px = hits.any(0)
+    assert np.abs(co[hit_px] - 300.0).max() < 6 * np.sqrt(303.0 / 25)
+
+
+# --------------------------------------------------------------------------- stamps
+def test_stamp_selection_hand_placed_stars(ora):
+    """2x2 cells of 40x40 on a flat 10 e- field.  Cell (0,0): a bright star and a
+    fainter isolated one -> the bright one.  Cell (1,0): the brightest star is
+    above max_peak and the other three each have a neighbour brighter than 10 %
+    of their peak within 10 px -> none.  Cell (0,1): the only star's window holds
+    a flagged pixel -> none.  Cell (1,1): two equal peaks -> the lower (y, x)."""
+    w = h = 80
+    R = np.full((h, w), 10.0, np.float32)
+    fl = np.zeros((h, w), np.uint8)
+
+    def star(x, y, a):
+        R[y - 1:y + 2, x - 1:x + 2] += a / 4
+        R[y, x] += a
+
+    star(15, 15, 1000); star(28, 28, 500)            # cell (0,0)
+    star(55, 15, 5000)                               # too bright
+    star(60, 28, 900); star(66, 30, 200)             # 6 px apart, both > 10 % of each other
+    star(52, 30, 300)                                # (60,28) is 8 px away
+    star(20, 60, 800); fl[62, 25] = 1                # flagged in window
+    star(50, 55, 700); star(66, 55, 700)             # tie -> (50,55) (lower x, same y)
+    cen = ora.select_stamps(R, fl, 2, 2, stamp=9, khalf=3, max_peak=3000.0)
+    assert cen.tolist() == [[15, 15], [50, 55]]
+    # without the crowding rule (iso = 0) cell (1,0) takes the brightest allowed star
+    cen = ora.select_stamps(R, fl, 2, 2, stamp=9, khalf=3, max_peak=3000.0, iso=0)
+    assert cen.tolist() == [[15, 15], [60, 28], [50, 55]]
