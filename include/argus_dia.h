@@ -1,0 +1,221 @@
+/*
+ * argus_dia.h -- C ABI of the GB300 (sm_103a) difference-image-analysis path of
+ * the Argus Array Hierarchical Data Processing System (Corbett et al. 2022,
+ * "The sky at one terabit per second", arXiv:2207.14304).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Image pointers are DEVICE pointers owned by the caller, row-major with a
+ *    row pitch given in ELEMENTS (argus_shape.pitch).  pitch >= w and
+ *    pitch % 16 == 0, so rows of 1-, 2- and 4-byte images all start on a
+ *    16-byte boundary; every image base pointer must be 16-byte aligned.
+ *    Violations return ARGUS_ERR_ALIGN.  One pitch serves all images of a call.
+ *  - Small parameter structs (argus_calib, argus_basis) are HOST structs; the
+ *    arrays they point to are device arrays.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and never allocates: scratch comes from the context made
+ *    by argus_create.  A context must not be used from two streams at once.
+ *  - Argument errors are returned synchronously.  Errors found on the device
+ *    (singular normal matrix, detection capacity, spin-wait timeout) are
+ *    latched in the context and returned by argus_sync_status.
+ *  - Flag bits: ARGUS_FLAG_BAD (bad-pixel mask, or flat not a positive finite
+ *    number), ARGUS_FLAG_SAT (raw >= saturation level).  A pixel with any flag
+ *    is excluded from fits, clipping and detection.
+ */
+#ifndef ARGUS_DIA_H
+#define ARGUS_DIA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct argus_ctx argus_ctx;
+typedef struct CUstream_st *argus_stream; /* identical to cudaStream_t */
+
+enum {
+    ARGUS_OK = 0,
+    ARGUS_ERR_ARG = -1,        /* invalid argument (host check) */
+    ARGUS_ERR_ALIGN = -2,      /* pointer or pitch alignment */
+    ARGUS_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    ARGUS_ERR_NOMEM = -4,      /* argus_create could not allocate */
+    ARGUS_ERR_SINGULAR = -5,   /* Cholesky met a pivot <= 0 (device) */
+    ARGUS_ERR_CAPACITY = -6,   /* an output or scratch list overflowed (device) */
+    ARGUS_ERR_TIMEOUT = -7,    /* a bounded device wait expired (device) */
+    ARGUS_ERR_UNSUPPORTED = -8 /* size outside the compiled kernel set */
+};
+
+enum { ARGUS_PREC_FP32 = 0, ARGUS_PREC_TF32 = 1, ARGUS_PREC_BF16 = 2 };
+enum { ARGUS_FLAG_BAD = 1, ARGUS_FLAG_SAT = 2 };
+enum { ARGUS_MASK_POS = 1, ARGUS_MASK_NEG = 2, ARGUS_MASK_INVALID = 4 };
+
+typedef struct {
+    int w, h;   /* image size in pixels */
+    long pitch; /* row pitch in elements; pitch >= w, pitch % 16 == 0 */
+} argus_shape;
+
+/* Calibration frames of one camera (paper Sec. 3.2: darks, flats, bad-pixel
+ * masks held on the GPU per pointing).  Device arrays use the image pitch. */
+typedef struct {
+    const uint16_t *bias_frame; /* nullable: per-pixel bias in ADU; else bias_scalar */
+    int bias_scalar;            /* ADU */
+    const float *dark;          /* nullable (= 0): electrons in the exposure */
+    const float *flat;          /* nullable (= 1): relative response */
+    const uint8_t *bpm;         /* nullable: nonzero = bad pixel */
+    float gain;                 /* electrons per ADU */
+    float read_noise;           /* electrons rms (Table 1: 1.7 e-) */
+    int sat;                    /* raw level at and above which a pixel is SAT */
+} argus_calib;
+
+/* Alard-Lupton Gaussian basis:  B_{g,p,q}(u,v) = u^p v^q exp(-(u^2+v^2)/(2 sigma_g^2))
+ * for g < ngauss, p + q <= degree[g], u,v in [-(ksize-1)/2, (ksize-1)/2], ordered
+ * g, p, q.  B_0 is scaled to unit sum; every other function with p and q both
+ * even has (sum B) B_0 removed, then each n >= 1 is scaled to unit L2 norm.
+ * Spatial terms p_k(x,y) = xt^i yt^j (i + j <= degree, ordered i then j), with
+ * xt = (2x - (W-1))/(W-1) over the frame width W (likewise yt).  Unknowns:
+ * a_0 (B_0, constant term only), a_{n,k} (n >= 1, k < Ks), bg_k (k < Kb):
+ * Nc = 1 + (nb-1) Ks + Kb.  Limits: ksize odd <= 31, ngauss <= 4, nb <= 64,
+ * spatial_degree and bg_degree <= 2. */
+typedef struct {
+    int ksize;
+    int ngauss;
+    float sigma[4];
+    int degree[4];
+    int spatial_degree;
+    int bg_degree;
+} argus_basis;
+
+/* One detected component (see argus_detect). */
+typedef struct {
+    float x, y;      /* Gaussian-windowed centroid (pixels) */
+    float flux;      /* PSF-weighted optimal flux estimate (electrons) */
+    float flux_err;  /* its 1-sigma error */
+    float peak_snr;  /* signed S = D / sqrt(V_D) at the peak pixel */
+    int npix;        /* pixels in the 8-connected component */
+    int sign;        /* +1 positive, -1 negative */
+    int px, py;      /* peak pixel */
+} argus_source;
+
+/* Device-side result record of argus_fit_kernel. */
+typedef struct {
+    double chi2;            /* sum w (I - C a)^2 over used stamp pixels */
+    double chi2_a0;         /* the same before the refinement step */
+    double max_step;        /* max |delta| / max |a| of the refinement */
+    long long n_pix;        /* stamp pixels with nonzero weight */
+    long long dof;          /* n_pix - Nc */
+    int n_coeffs;           /* Nc */
+    int status;             /* ARGUS_OK or ARGUS_ERR_SINGULAR */
+    int n_stamps_used;      /* stamps whose window lay inside the frame */
+    int precision;          /* ARGUS_PREC_* used for the Gram matrix */
+} argus_fit_stats;
+
+/* Human-readable name of a status code. */
+const char *argus_status_string(int status);
+
+/* Create a context on `device` with scratch for frames of up to max_pixels
+ * (h * pitch), up to max_stamps stamps of side <= 31, up to max_coeffs
+ * unknowns and detection lists of up to det_cap pixels above threshold.
+ * All scratch is allocated here, once (paper Sec. 4: calibration and
+ * reference frames are pre-allocated on the GPU at the start of a pointing).
+ * Returns ARGUS_OK and *out, or ARGUS_ERR_NOMEM / ARGUS_ERR_CUDA. */
+int argus_create(argus_ctx **out, int device, size_t max_pixels, int max_stamps,
+                 int max_coeffs, int det_cap);
+int argus_destroy(argus_ctx *ctx);
+
+/* Wait for `stream`, then return and clear the latched device status. */
+int argus_sync_status(argus_ctx *ctx, argus_stream stream);
+
+/* Calibration (paper Sec. 4.1: dark subtraction, flat fielding, bad-pixel
+ * masking; Table 2 "Calibration").  Per pixel, n = raw - bias (integer),
+ *   img = (n gain - dark) / flat,  var = (max(n gain, 0) + rn^2) / flat^2,
+ *   flags = BAD | SAT as above; pixels with an unusable flat get img = var = 0.
+ * raw: uint16 [h][pitch]; img, var: float [h][pitch]; flags: uint8 [h][pitch].
+ * Only x < w is written. */
+int argus_calibrate(argus_ctx *ctx, const uint16_t *raw, argus_shape shape,
+                    const argus_calib *calib, float *img, float *var, uint8_t *flags,
+                    argus_stream stream);
+
+/* Sigma-clipped mean coadd of n raw frames (paper Sec. 4.1.3, deep coaddition;
+ * a clipped mean stands in for the matched filter there).  raw_stack: uint16
+ * [n][h][pitch]; shifts_xy: float [n][2] (device), frame f is sampled at
+ * (x + dx_f, y + dy_f) by bilinear interpolation of its calibrated pixels;
+ * clip: up to max_iter rounds of rejecting |v - median| > kappa * sigma
+ * (population sigma about the mean); output coadd = c + sum(v - c)/n_used
+ * about the final median c, var = sum V_f / n_used^2, n_used (uint8).
+ * n <= 64.  Pixels with no valid sample get 0, 0, 0. */
+int argus_coadd(argus_ctx *ctx, const uint16_t *raw_stack, int n, argus_shape shape,
+                const float *shifts_xy, const argus_calib *calib, float kappa, int max_iter,
+                float *coadd, float *var, uint8_t *n_used, argus_stream stream);
+
+/* Stamp selection (deterministic grid rule; the paper gives none).  The frame
+ * is cut into grid_x x grid_y cells; in each cell the brightest strict 3x3
+ * local maximum of ref whose window [x-m, x+m]^2 (m = stamp/2 + khalf) is in
+ * the frame and unflagged, whose value is < max_peak and which has no other
+ * strict local maximum brighter than iso_frac times it within iso pixels
+ * (Chebyshev).  Ties go to the lowest (y, x).  centers: int [grid_x*grid_y][2]
+ * (x, y), cells in row-major order, compacted; *n_stamps (device int). */
+int argus_select_stamps(argus_ctx *ctx, const float *ref, const uint8_t *flags, argus_shape shape,
+                        int grid_x, int grid_y, int stamp, int khalf, float max_peak, int iso,
+                        float iso_frac, int *centers, int *n_stamps, argus_stream stream);
+
+/* PSF-matching kernel fit (Alard-Lupton least squares; the subtraction of
+ * paper Sec. 4.2).  For every pixel of every stamp (side `stamp`, centres
+ * centers[s], s < *n_stamps, at most max_stamps):
+ *   row c = [X_0, p_k X_n (n>=1), p_k (background)], X_n = (ref (x) B_n)(x,y),
+ *   weight w = 1/sci_var if flags == 0 and sci_var > 0, else 0;
+ * M = C^T W C (operands rounded to `precision`, FP32 accumulation on the tensor
+ * cores for TF32/BF16), FP64 Cholesky on the GPU, a0 = M^-1 b, then one
+ * refinement a = a0 + M^-1 C^T W (I - C a0) with C in FP32 and FP64 sums.
+ * Stamps whose window leaves the frame are skipped.  coeffs: double [Nc]
+ * (device); stats: argus_fit_stats (device).  A singular M latches
+ * ARGUS_ERR_SINGULAR and leaves coeffs untouched. */
+int argus_fit_kernel(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
+                     const uint8_t *flags, argus_shape shape, const int *centers,
+                     const int *n_stamps, int max_stamps, int stamp, const argus_basis *basis,
+                     int precision, double *coeffs, argus_fit_stats *stats, argus_stream stream);
+
+/* Kernel expansion: K_k(u,v) = sum_n a_{n,k} B_n(u,v) (K_0 also a_0 B_0) and the
+ * background coefficients.  K: float [Ks][ksize][ksize] (device, index
+ * (v+r)*ksize + (u+r)); bg: double [Kb] (device). */
+int argus_expand_kernel(argus_ctx *ctx, const argus_basis *basis, const double *coeffs, float *K,
+                        double *bg, argus_stream stream);
+
+/* Convolution of the reference and subtraction (paper Sec. 4.2 / Table 2,
+ * direct image subtraction) with the difference variance (noise maps,
+ * Sec. 3.2):
+ *   D   = sci - sum_k p_k(x,y) sum_{u,v} K_k(u,v) ref(x-u, y-v) - sum_k bg_k p_k(x,y)
+ *   V_D = sci_var + sum_{u,v} Kc(u,v)^2 ref_var(x-u, y-v),
+ * Kc = sum_k p_k(xc,yc) K_k at the centre of the 32x32 tile (frame
+ * coordinates) holding (x,y).  Spatial terms use frame size (frame_w,
+ * frame_h) and frame coordinates (x + ox, y + oy); with spatial_degree > 0,
+ * ox and oy must be multiples of 32.  Pixels within r = ksize/2 of an image
+ * edge, or with flags != 0, get D = V_D = 0.  K: float [Ks][ksize^2], bg:
+ * double [Kb] (device).  diff_var may be NULL.  ksize in {7, 9, 11, 15, 21}. */
+int argus_subtract(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
+                   const float *ref_var, const uint8_t *flags, argus_shape shape, int frame_w,
+                   int frame_h, int ox, int oy, int ksize, int spatial_degree, const float *K,
+                   int bg_degree, const double *bg, float *diff, float *diff_var,
+                   argus_stream stream);
+
+/* Detection on the difference image (paper Sec. 4.2 transient candidates,
+ * Table 2 "Source detection"; a variance-weighted threshold):
+ *   valid = flags == 0 && V_D > 0 && D, V_D finite;  S = D / sqrt(V_D) (float);
+ *   mask = POS if S >= nsigma, NEG if S <= -nsigma, INVALID if not valid;
+ * 8-connected components of equal sign; per component the peak (max |S|,
+ * ties to the lowest (y,x)), npix, the Gaussian-windowed centroid (4 steps of
+ * c += 2 sum t (p - c) / sum t, t = sign D exp(-|p-c|^2/(2 psf_sigma^2)), over
+ * the valid pixels within ceil(3 psf_sigma) of the peak, clamped to peak +- 2)
+ * and the optimal flux sum P D/V / sum P^2/V with P the unit-sum pixel-
+ * integrated Gaussian at the centroid.  Sources are written sorted by (py, px),
+ * at most cap; *n_found (device int) receives the total count; more than cap
+ * latches ARGUS_ERR_CAPACITY.  mask: uint8 [h][pitch]. */
+int argus_detect(argus_ctx *ctx, const float *diff, const float *diff_var, const uint8_t *flags,
+                 argus_shape shape, float nsigma, float psf_sigma, uint8_t *mask,
+                 argus_source *out, int cap, int *n_found, argus_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ARGUS_DIA_H */

@@ -621,7 +621,8 @@ int ora_detect(int w, int h, const float *D, const float *VD, const uint8_t *fla
 /*     fx = dx_f - floor(dx_f) (same for y); neighbours (ix,iy), (ix+1,iy)    */
 /*     if fx > 0, (ix,iy+1) if fy > 0, (ix+1,iy+1) if both; each neighbour is */
 /*     calibrated as above; the sample is invalid if a used neighbour is     */
-/*     outside the frame or flagged.  Value by nested lerps                  */
+/*     outside the frame or flagged, or if its value is not finite.  Value   */
+/*     by nested lerps                                                        */
 /*       top = v00 + fx (v10 - v00), bot = v01 + fx (v11 - v01),             */
 /*       v = top + fy (bot - top);   V_f = sum w_i^2 V_i (bilinear w_i).     */
 /*  2. S = valid samples.  Repeat at most max_iter times: c = median(S)      */
@@ -682,7 +683,9 @@ void ora_coadd(int nf, int w, int h, const uint16_t *raw, const float *shifts, i
                     if (!need[3]) val[3] = need[1] ? val[1] : val[2];
                     double top = val[0] + fx * (val[1] - val[0]);
                     double bot = val[2] + fx * (val[3] - val[2]);
-                    v[n] = top + fy * (bot - top);
+                    double sv = top + fy * (bot - top);
+                    if (!isfinite(sv)) continue;
+                    v[n] = sv;
                     double w0 = (1 - fx) * (1 - fy), w1 = fx * (1 - fy), w2 = (1 - fx) * fy, w3 = fx * fy;
                     vv[n] = w0 * w0 * vr[0] + (need[1] ? w1 * w1 * vr[1] : 0) +
                             (need[2] ? w2 * w2 * vr[2] : 0) + (need[3] ? w3 * w3 * vr[3] : 0);

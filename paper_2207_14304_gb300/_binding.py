@@ -1,0 +1,262 @@
+"""ctypes binding of libargusdia (argument marshalling only).
+
+Every function here has the name of a C entry point declared in
+include/argus_dia.h and forwards to it: tensors become device pointers,
+shapes and parameter structs become the C structs, and the stream defaults
+to PyTorch's current stream.  All computation happens in the CUDA library;
+if it cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+ARGUS_OK = 0
+ARGUS_ERR_ARG = -1
+ARGUS_ERR_ALIGN = -2
+ARGUS_ERR_CUDA = -3
+ARGUS_ERR_NOMEM = -4
+ARGUS_ERR_SINGULAR = -5
+ARGUS_ERR_CAPACITY = -6
+ARGUS_ERR_TIMEOUT = -7
+ARGUS_ERR_UNSUPPORTED = -8
+
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
+FLAG_BAD, FLAG_SAT = 1, 2
+MASK_POS, MASK_NEG, MASK_INVALID = 1, 2, 4
+
+
+class ArgusError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: argus status {code} ({status_string(code)})")
+
+
+class argus_shape(C.Structure):
+    _fields_ = [("w", C.c_int), ("h", C.c_int), ("pitch", C.c_long)]
+
+
+class argus_calib(C.Structure):
+    _fields_ = [("bias_frame", C.c_void_p), ("bias_scalar", C.c_int), ("dark", C.c_void_p),
+                ("flat", C.c_void_p), ("bpm", C.c_void_p), ("gain", C.c_float),
+                ("read_noise", C.c_float), ("sat", C.c_int)]
+
+
+class argus_basis(C.Structure):
+    _fields_ = [("ksize", C.c_int), ("ngauss", C.c_int), ("sigma", C.c_float * 4),
+                ("degree", C.c_int * 4), ("spatial_degree", C.c_int), ("bg_degree", C.c_int)]
+
+
+class argus_source(C.Structure):
+    _fields_ = [("x", C.c_float), ("y", C.c_float), ("flux", C.c_float), ("flux_err", C.c_float),
+                ("peak_snr", C.c_float), ("npix", C.c_int), ("sign", C.c_int), ("px", C.c_int),
+                ("py", C.c_int)]
+
+
+class argus_fit_stats(C.Structure):
+    _fields_ = [("chi2", C.c_double), ("chi2_a0", C.c_double), ("max_step", C.c_double),
+                ("n_pix", C.c_longlong), ("dof", C.c_longlong), ("n_coeffs", C.c_int),
+                ("status", C.c_int), ("n_stamps_used", C.c_int), ("precision", C.c_int)]
+
+
+SOURCE_BYTES = C.sizeof(argus_source)
+FIT_STATS_BYTES = C.sizeof(argus_fit_stats)
+
+_lib = None
+
+P = C.c_void_p
+I = C.c_int
+F = C.c_float
+SH = argus_shape
+
+# entry point -> argument types
+SIGNATURES = {
+    "argus_status_string": ([I], C.c_char_p),
+    "argus_create": ([C.POINTER(P), I, C.c_size_t, I, I, I], I),
+    "argus_destroy": ([P], I),
+    "argus_sync_status": ([P, P], I),
+    "argus_calibrate": ([P, P, SH, C.POINTER(argus_calib), P, P, P, P], I),
+    "argus_coadd": ([P, P, I, SH, P, C.POINTER(argus_calib), F, I, P, P, P, P], I),
+    "argus_select_stamps": ([P, P, P, SH, I, I, I, I, F, I, F, P, P, P], I),
+    "argus_fit_kernel": ([P, P, P, P, P, SH, P, P, I, I, C.POINTER(argus_basis), I, P, P, P], I),
+    "argus_expand_kernel": ([P, C.POINTER(argus_basis), P, P, P, P], I),
+    "argus_subtract": ([P, P, P, P, P, P, SH, I, I, I, I, I, I, P, I, P, P, P, P], I),
+    "argus_detect": ([P, P, P, P, SH, F, F, P, P, I, P, P], I),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libargusdia.so (building it in-tree when missing); raise on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libargusdia.so not built at {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load(False).argus_status_string(int(code)).decode()
+    except Exception:
+        return "unknown"
+
+
+def _check(rc, what):
+    if rc != ARGUS_OK:
+        raise ArgusError(rc, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor (device memory)")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def shape_of(t: torch.Tensor, w: int | None = None) -> argus_shape:
+    """argus_shape of a [h, pitch] tensor holding w valid columns."""
+    h, pitch = t.shape[-2], t.shape[-1]
+    return argus_shape(int(w if w is not None else pitch), int(h), int(pitch))
+
+
+def make_calib(bias=100, dark=None, flat=None, bpm=None, gain=1.0, read_noise=1.7, sat=65535,
+               bias_frame=None) -> argus_calib:
+    c = argus_calib()
+    c.bias_frame = _ptr(bias_frame)
+    c.bias_scalar = int(bias)
+    c.dark = _ptr(dark)
+    c.flat = _ptr(flat)
+    c.bpm = _ptr(bpm)
+    c.gain = float(gain)
+    c.read_noise = float(read_noise)
+    c.sat = int(sat)
+    return c
+
+
+def make_basis(ksize=11, sigmas=(0.7, 1.5, 3.0), degrees=(6, 4, 2), spatial_degree=0,
+               bg_degree=0) -> argus_basis:
+    b = argus_basis()
+    b.ksize = int(ksize)
+    b.ngauss = len(sigmas)
+    for i, s in enumerate(sigmas):
+        b.sigma[i] = float(s)
+        b.degree[i] = int(degrees[i])
+    b.spatial_degree = int(spatial_degree)
+    b.bg_degree = int(bg_degree)
+    return b
+
+
+def basis_counts(b: argus_basis):
+    nb = sum((b.degree[g] + 1) * (b.degree[g] + 2) // 2 for g in range(b.ngauss))
+    ks = (b.spatial_degree + 1) * (b.spatial_degree + 2) // 2
+    kb = (b.bg_degree + 1) * (b.bg_degree + 2) // 2
+    return nb, ks, kb, 1 + (nb - 1) * ks + kb
+
+
+# ---------------------------------------------------------------------------
+def argus_create(device=0, max_pixels=1 << 22, max_stamps=400, max_coeffs=320, det_cap=1 << 22):
+    h = C.c_void_p()
+    rc = load().argus_create(C.byref(h), int(device), int(max_pixels), int(max_stamps),
+                             int(max_coeffs), int(det_cap))
+    _check(rc, "argus_create")
+    return h
+
+
+def argus_destroy(ctx):
+    _check(load().argus_destroy(ctx), "argus_destroy")
+
+
+def argus_sync_status(ctx, stream=None) -> int:
+    return load().argus_sync_status(ctx, _stream(stream))
+
+
+def argus_calibrate(ctx, raw, shape, calib, img, var, flags, stream=None):
+    _check(load().argus_calibrate(ctx, _ptr(raw), shape, C.byref(calib), _ptr(img), _ptr(var),
+                                  _ptr(flags), _stream(stream)), "argus_calibrate")
+
+
+def argus_coadd(ctx, raw_stack, n, shape, shifts_xy, calib, kappa, max_iter, coadd, var, n_used,
+                stream=None):
+    _check(load().argus_coadd(ctx, _ptr(raw_stack), int(n), shape, _ptr(shifts_xy), C.byref(calib),
+                              float(kappa), int(max_iter), _ptr(coadd), _ptr(var), _ptr(n_used),
+                              _stream(stream)), "argus_coadd")
+
+
+def argus_select_stamps(ctx, ref, flags, shape, grid_x, grid_y, stamp, khalf, max_peak, iso,
+                        iso_frac, centers, n_stamps, stream=None):
+    _check(load().argus_select_stamps(ctx, _ptr(ref), _ptr(flags), shape, int(grid_x), int(grid_y),
+                                      int(stamp), int(khalf), float(max_peak), int(iso),
+                                      float(iso_frac), _ptr(centers), _ptr(n_stamps),
+                                      _stream(stream)), "argus_select_stamps")
+
+
+def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,
+                     basis, precision, coeffs, stats, stream=None):
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(load().argus_fit_kernel(ctx, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(flags), shape,
+                                   _ptr(centers), _ptr(n_stamps), int(max_stamps), int(stamp),
+                                   C.byref(basis), prec, _ptr(coeffs), _ptr(stats), _stream(stream)),
+           "argus_fit_kernel")
+
+
+def argus_expand_kernel(ctx, basis, coeffs, K, bg, stream=None):
+    _check(load().argus_expand_kernel(ctx, C.byref(basis), _ptr(coeffs), _ptr(K), _ptr(bg),
+                                      _stream(stream)), "argus_expand_kernel")
+
+
+def argus_subtract(ctx, sci, sci_var, ref, ref_var, flags, shape, frame_w, frame_h, ox, oy, ksize,
+                   spatial_degree, K, bg_degree, bg, diff, diff_var, stream=None):
+    _check(load().argus_subtract(ctx, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(ref_var), _ptr(flags),
+                                 shape, int(frame_w), int(frame_h), int(ox), int(oy), int(ksize),
+                                 int(spatial_degree), _ptr(K), int(bg_degree), _ptr(bg), _ptr(diff),
+                                 _ptr(diff_var), _stream(stream)), "argus_subtract")
+
+
+def argus_detect(ctx, diff, diff_var, flags, shape, nsigma, psf_sigma, mask, out, cap, n_found,
+                 stream=None):
+    _check(load().argus_detect(ctx, _ptr(diff), _ptr(diff_var), _ptr(flags), shape, float(nsigma),
+                               float(psf_sigma), _ptr(mask), _ptr(out), int(cap), _ptr(n_found),
+                               _stream(stream)), "argus_detect")
+
+
+def sources_from_bytes(buf: torch.Tensor, n: int):
+    """Decode n argus_source records from a uint8 tensor (host copy) into a numpy record array."""
+    import numpy as np
+    dt = np.dtype([("x", "<f4"), ("y", "<f4"), ("flux", "<f4"), ("flux_err", "<f4"),
+                   ("peak_snr", "<f4"), ("npix", "<i4"), ("sign", "<i4"), ("px", "<i4"),
+                   ("py", "<i4")])
+    a = buf.detach().cpu().numpy().view(np.uint8)[: n * SOURCE_BYTES]
+    return a.view(dt).copy()
+
+
+def fit_stats_from_bytes(buf: torch.Tensor) -> dict:
+    raw = bytes(buf.detach().cpu().numpy().view("uint8")[:FIT_STATS_BYTES])
+    s = argus_fit_stats.from_buffer_copy(raw)
+    return {k: getattr(s, k) for k, _ in argus_fit_stats._fields_}

@@ -1,0 +1,76 @@
+// Internal declarations shared by the sm_103a translation units of libargusdia.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "argus_dia.h"
+
+// Limits of the compiled kernel set.
+#define ARGUS_MAX_KS 31          // kernel side
+#define ARGUS_MAX_NB 64          // basis functions
+#define ARGUS_MAX_NG 4           // Gaussians
+#define ARGUS_MAX_TERMS 6        // spatial terms (degree 2)
+#define ARGUS_MAX_STAMP 31       // stamp side
+#define ARGUS_MAX_FRAMES 64      // coadd stack depth
+#define ARGUS_GRAM_KCHUNK 32     // design rows per Gram pipeline stage
+
+struct argus_ctx {
+    int device;
+    int num_sms;
+    size_t max_pixels;
+    int max_stamps;
+    int max_coeffs;   // Nc limit
+    int np_cols;      // padded Gram width: round_up(max_coeffs + 1, 16)
+    int det_cap;
+    int* d_status;    // latched device status word
+
+    // basis tables (rebuilt per call from the host basis spec)
+    double* basis_img;   // [nb][ks*ks] FP64 normalised basis
+    float* basis_imgf;   // [nb][ks*ks] FP32 copy
+    float* basis_h;      // [ngauss*9][ks] 1-D factors u^p exp(-u^2/2s^2)
+    float* basis_ab;     // [nb][2] alpha, beta: B_n = alpha (h_p x h_q) - beta B_0
+
+    // fit scratch
+    float* X;            // [max_stamps * 31*31][64] basis-convolved stamp pixels
+    int gram_parts;      // number of partial Gram slots
+    float* gram_part;    // [gram_parts][np_cols][np_cols]
+    double* M;           // [np_cols][np_cols] reduced normal matrix (+ target column)
+    double* L;           // [np_cols][np_cols] Cholesky factor
+    double* vec;         // [8][np_cols] b, a0, r, delta, a, work
+    int resid_parts;
+    double* resid_part;  // [resid_parts][np_cols + 2]
+
+    // stamp selection scratch
+    unsigned long long* cell_key;   // [max cells] best candidate key per cell
+    int max_cells;
+
+    // memo of the last basis tables built (host copy of the spec)
+    argus_basis basis_memo;
+    int basis_memo_valid;
+
+    // detection scratch
+    int* label;          // [max_pixels]
+    int* det_list;       // [det_cap]
+    int* det_count;      // [8] counters
+    unsigned long long* comp_key;  // [det_cap]
+    int* comp_npix;      // [det_cap]
+    int* comp_order;     // [det_cap]
+    int* row_count;      // [max_rows + 1]
+    int max_rows;
+};
+
+// Device-side error latch: the first error wins.
+__device__ __forceinline__ void argus_latch(int* st, int code) { atomicCAS(st, 0, code); }
+
+// Host helpers (api.cu)
+int argus_check_shape(const argus_shape& s, size_t max_pixels);
+int argus_check_ptr16(const void* p);
+int argus_launch_status();   // ARGUS_OK or ARGUS_ERR_CUDA after a launch
+
+// Inter-unit launchers
+int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st);
+int argus_basis_count(const argus_basis* b);
+int argus_nterms(int deg);
+
+static inline int argus_round_up(int a, int m) { return (a + m - 1) / m * m; }

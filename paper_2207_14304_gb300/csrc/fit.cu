@@ -1,0 +1,1013 @@
+// K3-K5 and a3/a7: stamp selection, basis convolution on stamps, the
+// normal-equation Gram matrix (SIMT FP32, or tcgen05 tensor cores in TF32 /
+// BF16 with FP32 accumulation in TMEM), FP64 Cholesky with one refinement
+// step, and kernel expansion.  The fit is the Alard & Lupton (1998) / Alard
+// (2000) Gaussian-basis least-squares kernel adopted for the direct image
+// subtraction of paper Sec. 4.2 (Table 2).
+//
+// Design rows are stamp pixels; the columns are [X_0, p_k X_n (n >= 1),
+// p_k (background)] scaled by sqrt(w), plus the target sqrt(w) I as one extra
+// column, so the Gram of the augmented design holds M = C^T W C, b = C^T W I
+// and I^T W I at once.  X_n = R (x) B_n is computed separably: every basis
+// function is alpha_n (h_{g,p} (x) h_{g,q}) - beta_n B_0 with 1-D factors
+// h_{g,p}(u) = u^p exp(-u^2 / 2 sigma_g^2).
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "argus_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+struct BasisDev {
+    int ks, r, ng, nb, NH;
+    int sdeg, bgdeg, Ks, Kb, Nc;
+    float sigma[ARGUS_MAX_NG];
+    int hoff[ARGUS_MAX_NG];
+    int g[ARGUS_MAX_NB], p[ARGUS_MAX_NB], q[ARGUS_MAX_NB];
+};
+
+int nterms(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
+
+int make_basis_dev(const argus_basis* b, BasisDev* d) {
+    if (!b || b->ksize < 3 || b->ksize > ARGUS_MAX_KS || !(b->ksize & 1)) return ARGUS_ERR_ARG;
+    if (b->ngauss < 1 || b->ngauss > ARGUS_MAX_NG) return ARGUS_ERR_ARG;
+    if (b->spatial_degree < 0 || b->spatial_degree > 2 || b->bg_degree < 0 || b->bg_degree > 2)
+        return ARGUS_ERR_ARG;
+    memset(d, 0, sizeof(*d));
+    d->ks = b->ksize;
+    d->r = (b->ksize - 1) / 2;
+    d->ng = b->ngauss;
+    int n = 0, nh = 0;
+    for (int g = 0; g < b->ngauss; g++) {
+        const int deg = b->degree[g];
+        if (deg < 0 || deg > 8 || !(b->sigma[g] > 0.0f)) return ARGUS_ERR_ARG;
+        d->sigma[g] = b->sigma[g];
+        d->hoff[g] = nh;
+        nh += deg + 1;
+        for (int p = 0; p <= deg; p++)
+            for (int q = 0; q <= deg - p; q++) {
+                if (n >= ARGUS_MAX_NB) return ARGUS_ERR_UNSUPPORTED;
+                d->g[n] = g; d->p[n] = p; d->q[n] = q;
+                n++;
+            }
+    }
+    d->nb = n;
+    d->NH = nh;
+    d->sdeg = b->spatial_degree;
+    d->bgdeg = b->bg_degree;
+    d->Ks = nterms(b->spatial_degree);
+    d->Kb = nterms(b->bg_degree);
+    d->Nc = 1 + (n - 1) * d->Ks + d->Kb;
+    return ARGUS_OK;
+}
+
+__device__ __forceinline__ double ipow(double x, int p) {
+    double r = 1.0;
+    for (int i = 0; i < p; i++) r *= x;
+    return r;
+}
+
+__device__ double block_sum_d(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    return t;
+}
+
+// One block per basis function: normalised image (FP64 and FP32), its
+// separable coefficients alpha/beta, and the 1-D factor rows.
+__global__ void __launch_bounds__(256) basis_prepare_kernel(BasisDev b, double* img, float* imgf, float* hrow,
+                                                            float* ab) {
+    __shared__ double red[8];
+    __shared__ double vals[ARGUS_MAX_KS * ARGUS_MAX_KS];
+    const int n = blockIdx.x, g = b.g[n], p = b.p[n], q = b.q[n];
+    const int ks = b.ks, r = b.r, kk = ks * ks;
+    const double s0d = 2.0 * (double)b.sigma[0] * (double)b.sigma[0];
+    const double sgd = 2.0 * (double)b.sigma[g] * (double)b.sigma[g];
+    double part = 0.0;
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        const int u = e % ks - r, v = e / ks - r;
+        part += exp(-(double)(u * u + v * v) / s0d);
+        vals[e] = ipow(u, p) * ipow(v, q) * exp(-(double)(u * u + v * v) / sgd);
+    }
+    const double S0 = block_sum_d(part, red);
+    double alpha, beta = 0.0, s = 0.0;
+    if (n == 0) {
+        alpha = 1.0 / S0;
+    } else {
+        if (p % 2 == 0 && q % 2 == 0) {
+            double ps = 0.0;
+            for (int e = threadIdx.x; e < kk; e += blockDim.x) ps += vals[e];
+            s = block_sum_d(ps, red);
+        }
+        double pn = 0.0;
+        for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+            const int u = e % ks - r, v = e / ks - r;
+            const double bp = vals[e] - s * exp(-(double)(u * u + v * v) / s0d) / S0;
+            pn += bp * bp;
+        }
+        const double nrm = sqrt(block_sum_d(pn, red));
+        alpha = 1.0 / nrm;
+        beta = s / nrm;
+    }
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        double Bv;
+        if (n == 0) {
+            Bv = vals[e] * alpha;
+        } else {
+            const int u = e % ks - r, v = e / ks - r;
+            Bv = (vals[e] - s * exp(-(double)(u * u + v * v) / s0d) / S0) * alpha;
+        }
+        img[(long)n * kk + e] = Bv;
+        imgf[(long)n * kk + e] = (float)Bv;
+    }
+    if (threadIdx.x == 0) {
+        ab[2 * n] = (float)alpha;
+        ab[2 * n + 1] = (float)beta;
+    }
+    if (q == 0)
+        for (int iu = threadIdx.x; iu < ks; iu += blockDim.x) {
+            const int u = iu - r;
+            hrow[(b.hoff[g] + p) * ks + iu] = (float)(ipow(u, p) * exp(-(double)(u * u) / sgd));
+        }
+}
+
+// ---------------------------------------------------------------------------
+// K3: X_n on every stamp pixel, separably, one CTA per stamp.
+// X layout: X[(s * nb + n) * ss + pix], pix = j * stamp + i.
+__global__ void __launch_bounds__(256) stamp_conv_kernel(BasisDev b, const float* ref, long pitch, int w, int h,
+                                                         const int* centers, const int* n_stamps, int stamp,
+                                                         const float* hrow, const float* ab, float* X) {
+    extern __shared__ __align__(16) float sm[];
+    const int s = blockIdx.x;
+    if (s >= *n_stamps) return;
+    const int ks = b.ks, r = b.r, hs = stamp / 2, WW = stamp + 2 * r, ss = stamp * stamp, nb = b.nb;
+    const int xs = centers[2 * s], ys = centers[2 * s + 1];
+    float* Xs = X + (long)s * nb * ss;
+    const bool valid = xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1;
+    if (!valid) {
+        for (int e = threadIdx.x; e < nb * ss; e += blockDim.x) Xs[e] = 0.0f;
+        return;
+    }
+    float* Rw = sm;                        // [WW][WW]
+    float* H = Rw + WW * WW;               // [NH][WW][stamp]
+    float* ht = H + b.NH * WW * stamp;     // [NH][ks]
+    float* X0 = ht + b.NH * ks;            // [ss]
+    const int wx0 = xs - hs - r, wy0 = ys - hs - r;
+    for (int e = threadIdx.x; e < WW * WW; e += blockDim.x) {
+        const int wj = e / WW, wi = e - wj * WW;
+        Rw[e] = __ldg(ref + (long)(wy0 + wj) * pitch + wx0 + wi);
+    }
+    for (int e = threadIdx.x; e < b.NH * ks; e += blockDim.x) ht[e] = hrow[e];
+    __syncthreads();
+    const int nh = b.NH * WW * stamp;
+    for (int e = threadIdx.x; e < nh; e += blockDim.x) {
+        const int t = e / (WW * stamp), rem = e - t * WW * stamp;
+        const int wj = rem / stamp, i = rem - wj * stamp;
+        const float* rr = Rw + wj * WW + i + 2 * r;
+        const float* hh = ht + t * ks;
+        float acc = 0.0f;
+        for (int iu = 0; iu < ks; iu++) acc = fmaf(hh[iu], rr[-iu], acc);
+        H[e] = acc;
+    }
+    __syncthreads();
+    {
+        const int tp = b.hoff[0], tq = b.hoff[0];
+        const float a0 = ab[0];
+        for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+            const int j = e / stamp, i = e - j * stamp;
+            const float* hq = ht + tq * ks;
+            const float* hp = H + (long)tp * WW * stamp + (j + 2 * r) * stamp + i;
+            float acc = 0.0f;
+            for (int iv = 0; iv < ks; iv++) acc = fmaf(hq[iv], hp[-iv * stamp], acc);
+            X0[e] = a0 * acc;
+            Xs[e] = a0 * acc;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (nb - 1) * ss; e += blockDim.x) {
+        const int n = 1 + e / ss, pix = e - (n - 1) * ss;
+        const int j = pix / stamp, i = pix - j * stamp;
+        const int g = b.g[n];
+        const float* hq = ht + (b.hoff[g] + b.q[n]) * ks;
+        const float* hp = H + (long)(b.hoff[g] + b.p[n]) * WW * stamp + (j + 2 * r) * stamp + i;
+        float acc = 0.0f;
+        for (int iv = 0; iv < ks; iv++) acc = fmaf(hq[iv], hp[-iv * stamp], acc);
+        Xs[(long)n * ss + pix] = ab[2 * n] * acc - ab[2 * n + 1] * X0[pix];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Design rows
+struct GramArgs {
+    const float* X;
+    const float* sci;
+    const float* var;
+    const uint8_t* flags;
+    const int* centers;
+    const int* n_stamps;
+    long pitch;
+    int w, h, W, H;
+    int stamp, ss, r, max_stamps;
+    int nb, Ks, Kb, Nc, NP, sdeg, bgdeg;
+    float* part;
+    int nslots;
+    int* status;
+};
+
+constexpr int META = 16;   // per-row metadata: sqw, sqw*I, w, valid, s, pix, p_k[6] at 6.., pb[6] at 12..? (see row_meta)
+
+__device__ __forceinline__ void terms_f(float xt, float yt, int deg, float* out) {
+    int k = 0;
+    float xi = 1.0f;
+    for (int i = 0; i <= deg; i++) {
+        float yj = 1.0f;
+        for (int j = 0; j <= deg - i; j++) {
+            out[k++] = xi * yj;
+            yj *= yt;
+        }
+        xi *= xt;
+    }
+}
+
+// meta layout: [0] sqrt(w) (0 if unused), [1] sqrt(w) * I, [2] w, [3] I, [4..10) p_k, [10..16) pb_k.
+// Row index and stamp are recomputed by callers from rho.
+__device__ void row_meta(const GramArgs& g, long rho, long nrows, float* m) {
+    for (int i = 0; i < META; i++) m[i] = 0.0f;
+    if (rho >= nrows) return;
+    const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
+    const int hs = g.stamp / 2;
+    const int xs = g.centers[2 * s], ys = g.centers[2 * s + 1];
+    if (!(xs - hs - g.r >= 0 && xs + hs + g.r <= g.w - 1 && ys - hs - g.r >= 0 && ys + hs + g.r <= g.h - 1))
+        return;
+    const int x = xs - hs + pix % g.stamp, y = ys - hs + pix / g.stamp;
+    const long p = (long)y * g.pitch + x;
+    const float v = g.var[p], I = g.sci[p];
+    const float xt = g.W > 1 ? (float)(2 * x - (g.W - 1)) / (float)(g.W - 1) : 0.0f;
+    const float yt = g.H > 1 ? (float)(2 * y - (g.H - 1)) / (float)(g.H - 1) : 0.0f;
+    terms_f(xt, yt, g.sdeg, m + 4);
+    terms_f(xt, yt, g.bgdeg, m + 10);
+    if (g.flags[p] == 0 && v > 0.0f && isfinite(v) && isfinite(I)) {
+        const float wt = 1.0f / v;
+        m[0] = sqrtf(wt);
+        m[1] = m[0] * I;
+        m[2] = wt;
+        m[3] = I;
+    }
+}
+
+// column descriptor: code = n (>= 0) with spatial term k, or -1 - kb for a
+// background term, or -100 for the target, or -200 for padding.
+__device__ __forceinline__ void col_code(const GramArgs& g, int j, int& n, int& k) {
+    if (j == 0) { n = 0; k = 0; return; }
+    const int nx = 1 + (g.nb - 1) * g.Ks;
+    if (j < nx) { n = 1 + (j - 1) / g.Ks; k = (j - 1) % g.Ks; return; }
+    if (j < g.Nc) { n = -1 - (j - nx); k = 0; return; }
+    if (j == g.Nc) { n = -100; k = 0; return; }
+    n = -200; k = 0;
+}
+
+__device__ __forceinline__ float design_value(const GramArgs& g, int n, int k, const float* m, float xv) {
+    // xv = sqrt(w) * X_n at this row (only used for n >= 0)
+    if (n >= 0) return n == 0 ? xv : xv * m[4 + k];
+    if (n == -100) return m[1];
+    if (n == -200) return 0.0f;
+    return m[0] * m[10 + (-1 - n)];
+}
+
+// ---------------------------------------------------------------------------
+// K4 (FP32): SIMT Gram on 64x64 tiles of the upper triangle.
+constexpr int GT = 64;
+constexpr int GK = 32;
+
+__global__ void __launch_bounds__(256) gram_simt_kernel(GramArgs g, int ntile) {
+    __shared__ __align__(16) float As[GK][GT + 4];
+    __shared__ __align__(16) float Bs[GK][GT + 4];
+    __shared__ float meta[GK][META];
+    __shared__ int cn[2][GT], ck[2][GT];
+    // upper-triangle tile pair
+    int pr = blockIdx.y, ti = 0;
+    while (pr >= ntile - ti) { pr -= ntile - ti; ti++; }
+    const int tj = ti + pr;
+    const int tid = threadIdx.x;
+    for (int c = tid; c < 2 * GT; c += blockDim.x) {
+        const int which = c / GT, jj = c % GT;
+        int n, k;
+        col_code(g, (which ? tj : ti) * GT + jj, n, k);
+        cn[which][jj] = n;
+        ck[which][jj] = k;
+    }
+    const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
+    const long nchunks = (nrows + GK - 1) / GK;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+    const int ty = tid / 16, tx = tid % 16;
+    for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long rho0 = ch * GK;
+        __syncthreads();
+        if (tid < GK) row_meta(g, rho0 + tid, nrows, meta[tid]);
+        __syncthreads();
+        {
+            const int k = tid % GK, cg = tid / GK;   // 8 column groups of 8
+            const long rho = rho0 + k;
+            const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
+            const float sqw = meta[k][0];
+#pragma unroll
+            for (int which = 0; which < 2; which++) {
+                float(*dst)[GT + 4] = which ? Bs : As;
+#pragma unroll
+                for (int cc = 0; cc < 8; cc++) {
+                    const int jj = cg * 8 + cc;
+                    const int n = cn[which][jj];
+                    float xv = 0.0f;
+                    if (n >= 0 && sqw != 0.0f) xv = sqw * __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix);
+                    dst[k][jj] = design_value(g, n, ck[which][jj], meta[k], xv);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < GK; k++) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+    }
+    float* out = g.part + (long)blockIdx.x * g.NP * g.NP;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int row = ti * GT + ty * 4 + i;
+        if (row >= g.NP) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int col = tj * GT + tx * 4 + j;
+            if (col < g.NP) out[(long)row * g.NP + col] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4 (TF32 / BF16): tcgen05 Gram.  CTA (slot, rb) accumulates rows
+// [128 rb, 128 rb + 128) x all NP columns of the augmented Gram in TMEM over
+// its K-chunks of 32 design rows.  The design tile of a stage is written once
+// in the K-major no-swizzle canonical layout and serves as B (all columns)
+// and, offset by 16 core-matrix groups per row block, as A.
+constexpr int TC_KC = 32;
+constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // ~2 s of SM clock
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float a) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+    return r;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
+    constexpr int ESZ = FMT == 1 ? 2 : 4;          // bytes per element
+    constexpr int E = 16 / ESZ;                    // elements per 16-byte core-matrix row
+    constexpr int KQ = TC_KC / E;                  // core matrices along K per stage
+    constexpr uint32_t LBO = 128;
+    constexpr uint32_t SBO = KQ * 128;
+    constexpr int KMMA = FMT == 1 ? 16 : 8;        // K per instruction
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint32_t stage_bytes = (uint32_t)NR * TC_KC * ESZ;
+    uint8_t* stage0 = smem_raw;
+    float* meta = reinterpret_cast<float*>(smem_raw + 2 * stage_bytes);            // [32][16]
+    float* Xsm = meta + TC_KC * META;                                               // [nb][32]
+    int* cn = reinterpret_cast<int*>(Xsm + ARGUS_MAX_NB * TC_KC);                   // [NR]
+    int* ck = cn + NR;                                                              // [NR]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(ck + NR + ((NR & 1) ? 1 : 0));     // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rb = blockIdx.y, slot = blockIdx.x;
+    const int NPt = g.NP;                                  // multiple of 16
+    uint32_t ncols = 32;
+    while ((int)ncols < NPt) ncols <<= 1;
+
+    for (int j = tid; j < NR; j += blockDim.x) {
+        int n, k;
+        col_code(g, j, n, k);
+        cn[j] = n;
+        ck[j] = k;
+    }
+    if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
+    const long nchunks = (nrows + TC_KC - 1) / TC_KC;
+    const uint32_t idesc0 = tc::instr_desc(FMT, 128, NPt > 256 ? 256 : NPt);
+    const uint32_t idesc1 = NPt > 256 ? tc::instr_desc(FMT, 128, NPt - 256) : 0u;
+    int it = 0;
+    for (long ch = slot; ch < nchunks; ch += gridDim.x, it++) {
+        const int st = it & 1;
+        uint8_t* sb = stage0 + st * stage_bytes;
+        const long rho0 = ch * TC_KC;
+        __syncthreads();
+        if (tid < TC_KC) row_meta(g, rho0 + tid, nrows, meta + tid * META);
+        __syncthreads();
+        for (int e = tid; e < g.nb * TC_KC; e += blockDim.x) {
+            const int n = e / TC_KC, k = e - n * TC_KC;
+            const long rho = rho0 + k;
+            const float sqw = meta[k * META];
+            float xv = 0.0f;
+            if (sqw != 0.0f) {
+                const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
+                xv = sqw * __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix);
+            }
+            Xsm[n * TC_KC + k] = xv;
+        }
+        // the MMAs that last read this stage must be complete before it is rewritten
+        if (it >= 2) {
+            if (!tc::mbar_wait_bounded(&mbar[st], ((it >> 1) - 1) & 1, TC_WAIT_LIMIT)) *abort_flag = 1;
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        for (int e = tid; e < NR * KQ; e += blockDim.x) {
+            const int kq = e / NR, i = e - kq * NR;
+            const int n = cn[i], kk = ck[i];
+            float v[E];
+#pragma unroll
+            for (int t = 0; t < E; t++) {
+                const int k = kq * E + t;
+                v[t] = design_value(g, n, kk, meta + k * META, n >= 0 ? Xsm[n * TC_KC + k] : 0.0f);
+            }
+            uint4 pk;
+            if constexpr (FMT == 1) {
+                pk.x = pack_bf16x2(v[0], v[1]);
+                pk.y = pack_bf16x2(v[2], v[3]);
+                pk.z = pack_bf16x2(v[4], v[5]);
+                pk.w = pack_bf16x2(v[6], v[7]);
+            } else {
+                pk.x = to_tf32(v[0]);
+                pk.y = to_tf32(v[1]);
+                pk.z = to_tf32(v[2]);
+                pk.w = to_tf32(v[3]);
+            }
+            *reinterpret_cast<uint4*>(sb + (i >> 3) * SBO + kq * 128 + (i & 7) * 16) = pk;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t base = tc::smem_u32(sb);
+#pragma unroll
+            for (int s = 0; s < TC_KC / KMMA; s++) {
+                const uint32_t koff = s * 2 * LBO;
+                const uint64_t ad = tc::smem_desc(base + rb * 16 * SBO + koff, LBO, SBO);
+                const uint64_t bd0 = tc::smem_desc(base + koff, LBO, SBO);
+                const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
+                if constexpr (FMT == 1) tc::mma_bf16(tmem, ad, bd0, idesc0, acc);
+                else tc::mma_tf32(tmem, ad, bd0, idesc0, acc);
+                if (NPt > 256) {
+                    const uint64_t bd1 = tc::smem_desc(base + 32 * SBO + koff, LBO, SBO);
+                    if constexpr (FMT == 1) tc::mma_bf16(tmem + 256, ad, bd1, idesc1, acc);
+                    else tc::mma_tf32(tmem + 256, ad, bd1, idesc1, acc);
+                }
+            }
+            tc::commit(&mbar[st]);
+        }
+    }
+    // drain: wait for the last commit of each stage that was used
+    const int nit = it;
+    if (tid == 0) {
+        for (int st = 0; st < 2; st++) {
+            const int uses = (nit + 1 - st) / 2;
+            if (uses > 0 && !tc::mbar_wait_bounded(&mbar[st], (uses - 1) & 1, TC_WAIT_LIMIT)) *abort_flag = 2;
+        }
+    }
+    __syncthreads();
+    tc::fence_after();
+    if (*abort_flag) {
+        if (tid == 0) argus_latch(g.status, ARGUS_ERR_TIMEOUT);
+    } else {
+        float* out = g.part + (long)slot * g.NP * g.NP;
+        const int qd = warp & 3, half = warp >> 2;
+        const int row = rb * 128 + qd * 32 + lane;
+        for (int c0 = half * 16; c0 < NPt; c0 += 32) {
+            float v[16];
+            if (nit > 0) {
+                tc::tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 16; t++) v[t] = 0.0f;
+            }
+            if (row < g.NP) {
+                float* o = out + (long)row * g.NP + c0;
+#pragma unroll
+                for (int t = 0; t < 16; t += 4) *reinterpret_cast<float4*>(o + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+// M[i][j] = M[j][i] = sum over slots of part[slot][i][j] (i <= j), FP64, fixed order.
+__global__ void gram_reduce_kernel(const float* part, int nslots, int NP, double* M) {
+    const long tot = (long)NP * NP;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / NP), j = (int)(e - (long)i * NP);
+        if (i > j) continue;
+        double s = 0.0;
+        for (int sl = 0; sl < nslots; sl++) s += (double)part[(long)sl * tot + e];
+        M[(long)i * NP + j] = s;
+        M[(long)j * NP + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: FP64 Cholesky of M[0:n, 0:n] (leading dimension ld), one CTA.
+// flag[0] != 0 marks a failed factorisation for the kernels that follow.
+__global__ void __launch_bounds__(1024) cholesky_kernel(const double* M, int ld, int n, double* L, double* flag,
+                                                        int* status) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (long e = tid; e < (long)n * ld; e += blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e - (long)i * ld);
+        L[e] = (j <= i && j < n) ? M[(long)i * ld + j] : 0.0;
+    }
+    if (tid == 0) flag[0] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const double d = L[(long)j * ld + j];
+        if (!(d > 0.0)) {
+            if (tid == 0) {
+                flag[0] = 1.0;
+                argus_latch(status, ARGUS_ERR_SINGULAR);
+            }
+            return;
+        }
+        const double ljj = sqrt(d);
+        __syncthreads();
+        if (tid == 0) L[(long)j * ld + j] = ljj;
+        const double inv = 1.0 / ljj;
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[(long)i * ld + j] *= inv;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < n; i += nw) {
+            const double lij = L[(long)i * ld + j];
+            double* Li = L + (long)i * ld;
+            for (int k = j + 1 + lane; k <= i; k += 32) Li[k] -= lij * L[(long)k * ld + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Solve L L^T x = rhs (rhs read with stride rs), one CTA.  Skips if flag set.
+__global__ void __launch_bounds__(1024) chol_solve_kernel(const double* L, int ld, int n, const double* rhs,
+                                                          int rs, double* x, const double* flag) {
+    extern __shared__ double y[];
+    if (flag[0] != 0.0) return;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) y[i] = rhs[(long)i * rs];
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const double yj = y[j] / L[(long)j * ld + j];
+        __syncthreads();
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) y[i] -= L[(long)i * ld + j] * yj;
+        if (tid == 0) y[j] = yj;
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; j--) {
+        const double xj = y[j] / L[(long)j * ld + j];
+        __syncthreads();
+        for (int i = tid; i < j; i += blockDim.x) y[i] -= L[(long)j * ld + i] * xj;
+        if (tid == 0) y[j] = xj;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += blockDim.x) x[i] = y[i];
+}
+
+// Residual pass over all design rows with coefficients a (FP64 in, FP32 model):
+// e = I - c.a; per CTA partial sums of r_j = sum w e c_j (if want_r), chi2 = sum w e^2
+// and the count of weighted rows, in FP64 with a fixed reduction order.
+__global__ void __launch_bounds__(256) resid_kernel(GramArgs g, const double* a, const double* flag, int want_r,
+                                                    double* part) {
+    extern __shared__ __align__(16) double rsm[];   // [8 warps][NP] accumulators
+    __shared__ float af[1024];
+    __shared__ double wchi[8], wn[8];
+    if (flag[0] != 0.0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = tid; j < g.Nc; j += blockDim.x) af[j] = (float)a[j];
+    for (int j = tid; j < 8 * g.NP; j += blockDim.x) rsm[j] = 0.0;
+    __syncthreads();
+    const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
+    double chi = 0.0, cnt = 0.0;
+    const int nx = 1 + (g.nb - 1) * g.Ks;
+    for (long base = (long)(blockIdx.x * 8 + warp) * 32; base < nrows; base += (long)gridDim.x * 8 * 32) {
+        const long rho = base + lane;
+        float m[META];
+        row_meta(g, rho, nrows, m);
+        const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
+        const bool use = m[0] != 0.0f;
+        // model = X_0 a_0 + sum_n X_n sum_k p_k a_{n,k} + sum_k pb_k bg_k
+        float model = 0.0f;
+        if (use) {
+            const float* Xr = g.X + (long)s * g.nb * g.ss + pix;
+            model = __ldg(Xr) * af[0];
+            for (int n = 1; n < g.nb; n++) {
+                float qn = 0.0f;
+                for (int k = 0; k < g.Ks; k++) qn = fmaf(m[4 + k], af[1 + (n - 1) * g.Ks + k], qn);
+                model = fmaf(__ldg(Xr + (long)n * g.ss), qn, model);
+            }
+            for (int k = 0; k < g.Kb; k++) model = fmaf(m[10 + k], af[nx + k], model);
+        }
+        const float e = use ? m[3] - model : 0.0f;
+        const float we = m[2] * e;
+        chi += (double)we * (double)e;
+        cnt += use ? 1.0 : 0.0;
+        if (want_r) {
+            const float* Xr = g.X + (long)s * g.nb * g.ss + pix;
+            for (int j = 0; j < g.Nc; j++) {
+                float c = 0.0f;
+                if (use) {
+                    if (j < nx) {
+                        const int n = j == 0 ? 0 : 1 + (j - 1) / g.Ks;
+                        const float xv = __ldg(Xr + (long)n * g.ss);
+                        c = j == 0 ? xv : xv * m[4 + (j - 1) % g.Ks];
+                    } else {
+                        c = m[10 + (j - nx)];
+                    }
+                }
+                float v = c * we;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) rsm[warp * g.NP + j] += (double)v;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        chi += __shfl_xor_sync(0xffffffffu, chi, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) { wchi[warp] = chi; wn[warp] = cnt; }
+    __syncthreads();
+    double* out = part + (long)blockIdx.x * (g.NP + 4);
+    for (int j = tid; j < g.Nc; j += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < 8; w++) s += rsm[w * g.NP + j];
+        out[j] = s;
+    }
+    if (tid == 0) {
+        double c = 0.0, n = 0.0;
+        for (int w = 0; w < 8; w++) { c += wchi[w]; n += wn[w]; }
+        out[g.NP] = c;
+        out[g.NP + 1] = n;
+    }
+}
+
+__global__ void resid_reduce_kernel(const double* part, int nparts, int NP, int Nc, double* r, double* chi_n,
+                                    const double* flag) {
+    if (flag[0] != 0.0) return;
+    for (int j = threadIdx.x; j < Nc + 2; j += blockDim.x) {
+        const int col = j < Nc ? j : NP + (j - Nc);
+        double s = 0.0;
+        for (int p = 0; p < nparts; p++) s += part[(long)p * (NP + 4) + col];
+        if (j < Nc) r[j] = s;
+        else chi_n[j - Nc] = s;
+    }
+}
+
+__global__ void update_kernel(const double* a0, const double* delta, double* a, int Nc, double* work,
+                              const double* flag) {
+    __shared__ double mx[2];
+    if (flag[0] != 0.0) return;
+    if (threadIdx.x == 0) { mx[0] = 0.0; mx[1] = 0.0; }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) a[j] = a0[j] + delta[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ms = 0.0, ma = 0.0;
+        for (int j = 0; j < Nc; j++) {
+            ms = fmax(ms, fabs(delta[j]));
+            ma = fmax(ma, fabs(a[j]));
+        }
+        work[0] = ma > 0.0 ? ms / ma : 0.0;
+    }
+}
+
+__global__ void finalize_kernel(const double* a, int Nc, const double* chi_a0, const double* chi_a,
+                                const double* work, const double* flag, int n_stamps_max, const int* n_stamps,
+                                const int* centers, int stamp, int r, int w, int h, int prec, double* coeffs,
+                                argus_fit_stats* st) {
+    if (threadIdx.x == 0) {
+        argus_fit_stats s;
+        const bool bad = flag[0] != 0.0;
+        s.chi2 = bad ? 0.0 : chi_a[0];
+        s.chi2_a0 = bad ? 0.0 : chi_a0[0];
+        s.max_step = bad ? 0.0 : work[0];
+        s.n_pix = bad ? 0 : (long long)chi_a[1];
+        s.dof = s.n_pix - Nc;
+        s.n_coeffs = Nc;
+        s.status = bad ? ARGUS_ERR_SINGULAR : ARGUS_OK;
+        int used = 0;
+        const int hs = stamp / 2, ns = min(*n_stamps, n_stamps_max);
+        for (int i = 0; i < ns; i++) {
+            const int xs = centers[2 * i], ys = centers[2 * i + 1];
+            used += (xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1);
+        }
+        s.n_stamps_used = used;
+        s.precision = prec;
+        *st = s;
+    }
+    if (flag[0] != 0.0) return;
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) coeffs[j] = a[j];
+}
+
+// a7: K_k(u,v) = sum_n a_{n,k} B_n(u,v) (K_0 also a_0 B_0); bg_k.
+__global__ void expand_kernel(BasisDev b, const double* img, const double* a, float* K, double* bg) {
+    const int k = blockIdx.x, kk = b.ks * b.ks;
+    for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+        double s = (k == 0) ? a[0] * img[e] : 0.0;
+        for (int n = 1; n < b.nb; n++) s += a[1 + (n - 1) * b.Ks + k] * img[(long)n * kk + e];
+        K[(long)k * kk + e] = (float)s;
+    }
+    if (k == 0)
+        for (int t = threadIdx.x; t < b.Kb; t += blockDim.x) bg[t] = a[1 + (b.nb - 1) * b.Ks + t];
+}
+
+// ---------------------------------------------------------------------------
+// a3: stamp selection.  One thread per pixel: cheap tests first, isolation and
+// window-flag scans with early exit, then a 64-bit atomicMax per cell of
+// (order-preserving bits of R, inverted row-major rank).
+__device__ __forceinline__ bool is_lmax(const float* R, long pitch, int w, int h, int x, int y) {
+    if (x < 1 || y < 1 || x > w - 2 || y > h - 2) return false;
+    const float c = R[(long)y * pitch + x];
+    if (!isfinite(c)) return false;
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+            if (!dx && !dy) continue;
+            if (!(c > R[(long)(y + dy) * pitch + x + dx])) return false;
+        }
+    return true;
+}
+
+__global__ void select_kernel(const float* R, const uint8_t* flags, long pitch, int w, int h, int gx, int gy,
+                              int m, float max_peak, int iso, float iso_frac, unsigned long long* cell_key) {
+    const long np = (long)w * h;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < np; e += (long)gridDim.x * blockDim.x) {
+        const int y = (int)(e / w), x = (int)(e - (long)y * w);
+        if (x - m < 0 || x + m > w - 1 || y - m < 0 || y + m > h - 1) continue;
+        if (!is_lmax(R, pitch, w, h, x, y)) continue;
+        const float c = R[(long)y * pitch + x];
+        if (!(c < max_peak)) continue;
+        const float thr = iso_frac * c;
+        bool bad = false;
+        for (int yy = y - iso; yy <= y + iso && !bad; yy++)
+            for (int xx = x - iso; xx <= x + iso; xx++) {
+                if ((xx == x && yy == y) || xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                if (R[(long)yy * pitch + xx] > thr && is_lmax(R, pitch, w, h, xx, yy)) { bad = true; break; }
+            }
+        if (bad) continue;
+        for (int yy = y - m; yy <= y + m && !bad; yy++)
+            for (int xx = x - m; xx <= x + m; xx++)
+                if (flags[(long)yy * pitch + xx]) { bad = true; break; }
+        if (bad) continue;
+        const int cx = (int)(((long)(x + 1) * gx - 1) / w), cy = (int)(((long)(y + 1) * gy - 1) / h);
+        const unsigned bits = __float_as_uint(c);
+        const unsigned ord = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+        const unsigned rank = (unsigned)y * (unsigned)w + (unsigned)x;
+        const unsigned long long key = ((unsigned long long)ord << 32) | (unsigned long long)(0xffffffffu - rank);
+        atomicMax(cell_key + cy * gx + cx, key);
+    }
+}
+
+__global__ void __launch_bounds__(1024) select_compact_kernel(const unsigned long long* cell_key, int ncell, int w,
+                                                              int* centers, int* n_out) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < ncell; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const unsigned long long k = i < ncell ? cell_key[i] : 0ull;
+        const int v = k != 0ull;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int ws = wsum[lane];
+            int wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            wsum[lane] = wi - ws;
+        }
+        __syncthreads();
+        const int pos = carry + wsum[wid] + incl - v;
+        if (v) {
+            const unsigned rank = 0xffffffffu - (unsigned)(k & 0xffffffffu);
+            centers[2 * pos] = (int)(rank % (unsigned)w);
+            centers[2 * pos + 1] = (int)(rank / (unsigned)w);
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = pos + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_out = carry;
+}
+
+}  // namespace
+
+int argus_nterms(int deg) { return nterms(deg); }
+
+int argus_basis_count(const argus_basis* b) {
+    BasisDev d;
+    if (make_basis_dev(b, &d)) return -1;
+    return d.nb;
+}
+
+static bool same_basis(const argus_basis& a, const argus_basis& b) {
+    return memcmp(&a, &b, sizeof(argus_basis)) == 0;
+}
+
+int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st) {
+    BasisDev d;
+    int rc = make_basis_dev(b, &d);
+    if (rc) return rc;
+    argus_basis key;
+    memset(&key, 0, sizeof(key));
+    key.ksize = b->ksize; key.ngauss = b->ngauss;
+    for (int g = 0; g < b->ngauss; g++) { key.sigma[g] = b->sigma[g]; key.degree[g] = b->degree[g]; }
+    key.spatial_degree = b->spatial_degree; key.bg_degree = b->bg_degree;
+    if (ctx->basis_memo_valid && same_basis(ctx->basis_memo, key)) return ARGUS_OK;
+    basis_prepare_kernel<<<d.nb, 256, 0, st>>>(d, ctx->basis_img, ctx->basis_imgf, ctx->basis_h, ctx->basis_ab);
+    rc = argus_launch_status();
+    if (rc == ARGUS_OK) {
+        ctx->basis_memo = key;
+        ctx->basis_memo_valid = 1;
+    }
+    return rc;
+}
+
+extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
+                                const uint8_t* flags, argus_shape shape, const int* centers,
+                                const int* n_stamps, int max_stamps, int stamp, const argus_basis* basis,
+                                int precision, double* coeffs, argus_fit_stats* stats, argus_stream stream) {
+    if (!ctx || !sci || !sci_var || !ref || !flags || !centers || !n_stamps || !coeffs || !stats || !basis)
+        return ARGUS_ERR_ARG;
+    if (max_stamps < 1 || max_stamps > ctx->max_stamps || stamp < 1 || stamp > ARGUS_MAX_STAMP || !(stamp & 1))
+        return ARGUS_ERR_ARG;
+    if (precision < ARGUS_PREC_FP32 || precision > ARGUS_PREC_BF16) return ARGUS_ERR_ARG;
+    int rc = argus_check_shape(shape, ctx->max_pixels);
+    if (rc) return rc;
+    BasisDev d;
+    rc = make_basis_dev(basis, &d);
+    if (rc) return rc;
+    if (d.Nc > ctx->max_coeffs) return ARGUS_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = argus_basis_prepare(ctx, basis, st);
+    if (rc) return rc;
+
+    const int ss = stamp * stamp, WW = stamp + 2 * d.r;
+    const size_t conv_smem = sizeof(float) * ((size_t)WW * WW + (size_t)d.NH * WW * stamp + (size_t)d.NH * d.ks + ss);
+    if (conv_smem > 200 * 1024) return ARGUS_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(stamp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+    stamp_conv_kernel<<<max_stamps, 256, conv_smem, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers, n_stamps,
+                                                          stamp, ctx->basis_h, ctx->basis_ab, ctx->X);
+    if ((rc = argus_launch_status())) return rc;
+
+    GramArgs g;
+    g.X = ctx->X; g.sci = sci; g.var = sci_var; g.flags = flags; g.centers = centers; g.n_stamps = n_stamps;
+    g.pitch = shape.pitch; g.w = shape.w; g.h = shape.h; g.W = shape.w; g.H = shape.h;
+    g.stamp = stamp; g.ss = ss; g.r = d.r; g.max_stamps = max_stamps; g.nb = d.nb; g.Ks = d.Ks; g.Kb = d.Kb; g.Nc = d.Nc;
+    g.NP = argus_round_up(d.Nc + 1, 16);
+    g.sdeg = d.sdeg; g.bgdeg = d.bgdeg; g.part = ctx->gram_part; g.status = ctx->d_status;
+
+    const long max_rows = (long)max_stamps * ss;
+    if (precision == ARGUS_PREC_FP32) {
+        const int ntile = (g.NP + GT - 1) / GT;
+        const int npair = ntile * (ntile + 1) / 2;
+        int nslots = ctx->num_sms * 2 / npair;
+        if (nslots < 1) nslots = 1;
+        if (nslots > ctx->gram_parts) nslots = ctx->gram_parts;
+        const long nch = (max_rows + GK - 1) / GK;
+        if (nslots > nch) nslots = (int)nch;
+        g.nslots = nslots;
+        gram_simt_kernel<<<dim3(nslots, npair), 256, 0, st>>>(g, ntile);
+    } else {
+        const int RB = (g.NP + 127) / 128;
+        const int NR = RB * 128;
+        int nslots = ctx->num_sms / RB;
+        if (nslots < 1) nslots = 1;
+        if (nslots > ctx->gram_parts) nslots = ctx->gram_parts;
+        const long nch = (max_rows + TC_KC - 1) / TC_KC;
+        if (nslots > nch) nslots = (int)nch;
+        g.nslots = nslots;
+        const int esz = precision == ARGUS_PREC_BF16 ? 2 : 4;
+        size_t smem = 2 * (size_t)NR * TC_KC * esz + sizeof(float) * (TC_KC * META + ARGUS_MAX_NB * TC_KC) +
+                      sizeof(int) * (2 * NR + 2) + 64;
+        if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: each holds up to 512 TMEM columns
+        if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
+        if (precision == ARGUS_PREC_BF16) {
+            cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, NR);
+        } else {
+            cudaFuncSetAttribute(gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, NR);
+        }
+    }
+    if ((rc = argus_launch_status())) return rc;
+    const int NP = g.NP;
+    gram_reduce_kernel<<<ctx->num_sms, 256, 0, st>>>(ctx->gram_part, g.nslots, NP, ctx->M);
+
+    double* flag = ctx->vec + 7 * (size_t)ctx->np_cols;
+    double* a0 = ctx->vec + 1 * (size_t)ctx->np_cols;
+    double* rv = ctx->vec + 2 * (size_t)ctx->np_cols;
+    double* dl = ctx->vec + 3 * (size_t)ctx->np_cols;
+    double* a = ctx->vec + 4 * (size_t)ctx->np_cols;
+    double* work = ctx->vec + 5 * (size_t)ctx->np_cols;   // [0] max step, [2..3] chi/n (a0), [4..5] chi/n (a)
+    cholesky_kernel<<<1, 1024, 0, st>>>(ctx->M, NP, d.Nc, ctx->L, flag, ctx->d_status);
+    const size_t solve_smem = sizeof(double) * NP;
+    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, ctx->M + d.Nc, NP, a0, flag);
+    int nparts = ctx->num_sms * 2;
+    if (nparts > ctx->resid_parts) nparts = ctx->resid_parts;
+    const size_t rsmem = sizeof(double) * 8 * NP;
+    cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+    resid_kernel<<<nparts, 256, rsmem, st>>>(g, a0, flag, 1, ctx->resid_part);
+    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, d.Nc, rv, work + 2, flag);
+    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, rv, 1, dl, flag);
+    update_kernel<<<1, 256, 0, st>>>(a0, dl, a, d.Nc, work, flag);
+    resid_kernel<<<nparts, 256, rsmem, st>>>(g, a, flag, 0, ctx->resid_part);
+    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, work + 4, flag);
+    finalize_kernel<<<1, 256, 0, st>>>(a, d.Nc, work + 2, work + 4, work, flag, max_stamps, n_stamps, centers,
+                                       stamp, d.r, shape.w, shape.h, precision, coeffs, stats);
+    return argus_launch_status();
+}
+
+extern "C" int argus_expand_kernel(argus_ctx* ctx, const argus_basis* basis, const double* coeffs, float* K,
+                                   double* bg, argus_stream stream) {
+    if (!ctx || !basis || !coeffs || !K || !bg) return ARGUS_ERR_ARG;
+    BasisDev d;
+    int rc = make_basis_dev(basis, &d);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = argus_basis_prepare(ctx, basis, st))) return rc;
+    expand_kernel<<<d.Ks, 256, 0, st>>>(d, ctx->basis_img, coeffs, K, bg);
+    return argus_launch_status();
+}
+
+extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8_t* flags, argus_shape shape,
+                                   int grid_x, int grid_y, int stamp, int khalf, float max_peak, int iso,
+                                   float iso_frac, int* centers, int* n_stamps, argus_stream stream) {
+    if (!ctx || !ref || !flags || !centers || !n_stamps) return ARGUS_ERR_ARG;
+    if (grid_x < 1 || grid_y < 1 || grid_x * grid_y > ctx->max_cells || stamp < 1 || khalf < 0 || iso < 0 ||
+        iso > 64)
+        return ARGUS_ERR_ARG;
+    int rc = argus_check_shape(shape, ctx->max_pixels);
+    if (rc) return rc;
+    if (argus_check_ptr16(ref) || argus_check_ptr16(flags)) return ARGUS_ERR_ALIGN;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ncell = grid_x * grid_y;
+    if (cudaMemsetAsync(ctx->cell_key, 0, sizeof(unsigned long long) * ncell, st) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    const long np = (long)shape.w * shape.h;
+    long blocks = (np + 255) / 256;
+    if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
+    select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x, grid_y,
+                                                    stamp / 2 + khalf, max_peak, iso, iso_frac, ctx->cell_key);
+    select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps);
+    return argus_launch_status();
+}

@@ -1,0 +1,255 @@
+// K6: convolution of the reference with the spatially varying PSF-matching
+// kernel, subtraction, and the difference variance (paper Sec. 4.2 direct
+// image subtraction, Table 2; noise maps, Sec. 3.2).
+//
+//   D   = I - sum_k p_k(x,y) (R (x) K_k)(x,y) - sum_k bg_k p_k(x,y)
+//   V_D = V_I + (Kc^2 (x) V_ref)(x,y),  Kc the kernel at the 32x32 tile centre
+//
+// One CTA owns one 32x32 output tile, which is also the variance tile, so the
+// squared tile-centre kernel is built once per CTA.  The reference and its
+// variance are staged with their halo in shared memory; each of the 128
+// threads computes a column strip of 8 outputs for all NK spatial terms,
+// keeping 8 x NK FP32 accumulators in registers and streaming the 8 + KS - 1
+// reference values of one kernel column per step.  Kernel taps are stored
+// [iu][iv][k] (k padded to 4 or 8) so one 128-bit shared load feeds 4 terms.
+//
+// The per-pixel work is NK * KS^2 + KS^2 FMAs (3087 at KS = 21, NK = 6), far
+// above the 24 B/px of traffic: the kernel is bound by FP32 issue, not HBM.
+#include "argus_internal.cuh"
+
+namespace {
+
+constexpr int TILE = 32;
+constexpr int ROWS_PER_THREAD = 8;
+constexpr int THREADS = 128;
+
+struct SubArgs {
+    const float* sci;
+    const float* sci_var;
+    const float* ref;
+    const float* ref_var;
+    const uint8_t* flags;
+    const float* K;     // [NK][KS*KS]
+    const double* bg;   // [Kb]
+    float* diff;
+    float* diff_var;
+    long pitch;
+    int w, h, W, H, ox, oy, nbg, bg_deg, sdeg;
+};
+
+__device__ __forceinline__ void spatial_terms(float xt, float yt, int deg, float* out) {
+    // p_k = xt^i yt^j, i + j <= deg, ordered i then j
+    int k = 0;
+    float xi = 1.0f;
+    for (int i = 0; i <= deg; i++) {
+        float yj = 1.0f;
+        for (int j = 0; j <= deg - i; j++) {
+            out[k++] = xi * yj;
+            yj *= yt;
+        }
+        xi *= xt;
+    }
+}
+
+template <int KS, int NK>
+__global__ void __launch_bounds__(THREADS) subtract_kernel(SubArgs a) {
+    constexpr int R = (KS - 1) / 2;
+    constexpr int SW = TILE + 2 * R;             // staged tile side
+    constexpr int NKP = NK == 1 ? 1 : (NK <= 4 ? 4 : 8);
+    constexpr int NCOL = ROWS_PER_THREAD + KS - 1;
+    constexpr int KSP = (KS + 3) / 4 * 4;
+    constexpr int KTSZ = (KS * KS * NKP + 3) / 4 * 4;   // keeps Kc2 16-byte aligned
+
+    extern __shared__ __align__(16) float smem[];
+    float* Rs = smem;                             // [SW][SW], SW even
+    float* Vs = Rs + SW * SW;                     // [SW][SW]
+    float* Kt = Vs + SW * SW;                     // [KS][KS][NKP]
+    float* Kc2 = Kt + KTSZ;                       // [KS][KSP]
+
+    const int tx0 = blockIdx.x * TILE, ty0 = blockIdx.y * TILE;
+    const int tid = threadIdx.x;
+
+    // stage reference and reference variance with halo (zero outside the image)
+    for (int e = tid; e < SW * SW; e += THREADS) {
+        const int iy = e / SW, ix = e - iy * SW;
+        const int gy = ty0 - R + iy, gx = tx0 - R + ix;
+        float rv = 0.0f, vv = 0.0f;
+        if (gy >= 0 && gy < a.h && gx >= 0 && gx < a.w) {
+            const long p = (long)gy * a.pitch + gx;
+            rv = __ldg(a.ref + p);
+            vv = __ldg(a.ref_var + p);
+        }
+        Rs[e] = rv;
+        Vs[e] = vv;
+    }
+    // kernel taps, transposed to [iu][iv][k]
+    for (int e = tid; e < KS * KS * NKP; e += THREADS) {
+        const int k = e % NKP, t = e / NKP;
+        const int iu = t / KS, iv = t - iu * KS;
+        Kt[e] = k < NK ? __ldg(a.K + k * KS * KS + iv * KS + iu) : 0.0f;
+    }
+    // squared kernel at the tile centre (frame coordinates)
+    {
+        float pc[ARGUS_MAX_TERMS];
+        const float xc = (float)(((tx0 + a.ox) / TILE) * TILE) + 0.5f * (TILE - 1);
+        const float yc = (float)(((ty0 + a.oy) / TILE) * TILE) + 0.5f * (TILE - 1);
+        const float xt = a.W > 1 ? (2.0f * xc - (float)(a.W - 1)) / (float)(a.W - 1) : 0.0f;
+        const float yt = a.H > 1 ? (2.0f * yc - (float)(a.H - 1)) / (float)(a.H - 1) : 0.0f;
+        spatial_terms(xt, yt, a.sdeg, pc);
+        for (int e = tid; e < KS * KSP; e += THREADS) {
+            const int iu = e / KSP, iv = e - iu * KSP;
+            float kc = 0.0f;
+            if (iv < KS) {
+#pragma unroll
+                for (int k = 0; k < NK; k++) kc = fmaf(pc[k], __ldg(a.K + k * KS * KS + iv * KS + iu), kc);
+            }
+            Kc2[e] = kc * kc;
+        }
+    }
+    __syncthreads();
+
+    const int lx = tid & 31;
+    const int ly0 = (tid >> 5) * ROWS_PER_THREAD;
+
+    float acc[NK][ROWS_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < NK; k++)
+#pragma unroll
+        for (int j = 0; j < ROWS_PER_THREAD; j++) acc[k][j] = 0.0f;
+
+    // output (lx, ly0 + j), tap (du, dv) = (iu - R, iv - R):
+    //   R(x - du, y - dv) = Rs[ly0 + j + 2R - iv][lx + 2R - iu]
+#pragma unroll 1
+    for (int iu = 0; iu < KS; iu++) {
+        float col[NCOL];
+#pragma unroll
+        for (int m = 0; m < NCOL; m++) col[m] = Rs[(ly0 + m) * SW + lx + 2 * R - iu];
+        const float* kt = Kt + iu * KS * NKP;
+#pragma unroll
+        for (int iv = 0; iv < KS; iv++) {
+            float kk[NKP];
+            if constexpr (NKP == 1) {
+                kk[0] = kt[iv];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NKP; q += 4)
+                    *reinterpret_cast<float4*>(kk + q) = *reinterpret_cast<const float4*>(kt + iv * NKP + q);
+            }
+#pragma unroll
+            for (int j = 0; j < ROWS_PER_THREAD; j++) {
+                const float rv = col[j + 2 * R - iv];
+#pragma unroll
+                for (int k = 0; k < NK; k++) acc[k][j] = fmaf(kk[k], rv, acc[k][j]);
+            }
+        }
+    }
+
+    float accv[ROWS_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = 0.0f;
+#pragma unroll 1
+    for (int iu = 0; iu < KS; iu++) {
+        float col[NCOL];
+#pragma unroll
+        for (int m = 0; m < NCOL; m++) col[m] = Vs[(ly0 + m) * SW + lx + 2 * R - iu];
+        float kc[KSP];
+#pragma unroll
+        for (int q = 0; q < KSP; q += 4)
+            *reinterpret_cast<float4*>(kc + q) = *reinterpret_cast<const float4*>(Kc2 + iu * KSP + q);
+#pragma unroll
+        for (int iv = 0; iv < KS; iv++)
+#pragma unroll
+            for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = fmaf(kc[iv], col[j + 2 * R - iv], accv[j]);
+    }
+
+    // epilogue: spatial combination, background, edge and flag handling
+    const int x = tx0 + lx;
+    if (x >= a.w) return;
+    const float xt = a.W > 1 ? (float)(2 * (x + a.ox) - (a.W - 1)) / (float)(a.W - 1) : 0.0f;
+    float bgc[ARGUS_MAX_TERMS];
+    for (int k = 0; k < a.nbg; k++) bgc[k] = (float)a.bg[k];
+#pragma unroll
+    for (int j = 0; j < ROWS_PER_THREAD; j++) {
+        const int y = ty0 + ly0 + j;
+        if (y >= a.h) break;
+        const long p = (long)y * a.pitch + x;
+        float D = 0.0f, VD = 0.0f;
+        const bool inner = x >= R && y >= R && x <= a.w - 1 - R && y <= a.h - 1 - R;
+        if (inner && a.flags[p] == 0) {
+            const float yt = a.H > 1 ? (float)(2 * (y + a.oy) - (a.H - 1)) / (float)(a.H - 1) : 0.0f;
+            float pk[ARGUS_MAX_TERMS];
+            spatial_terms(xt, yt, a.sdeg, pk);
+            float conv = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NK; k++) conv = fmaf(pk[k], acc[k][j], conv);
+            float pb[ARGUS_MAX_TERMS];
+            spatial_terms(xt, yt, a.bg_deg, pb);
+            float b = 0.0f;
+            for (int k = 0; k < a.nbg; k++) b = fmaf(bgc[k], pb[k], b);
+            D = a.sci[p] - conv - b;
+            VD = a.sci_var[p] + accv[j];
+        }
+        a.diff[p] = D;
+        if (a.diff_var) a.diff_var[p] = VD;
+    }
+}
+
+template <int KS, int NK>
+int launch(const SubArgs& a, cudaStream_t st) {
+    constexpr int R = (KS - 1) / 2;
+    constexpr int SW = TILE + 2 * R;
+    constexpr int NKP = NK == 1 ? 1 : (NK <= 4 ? 4 : 8);
+    constexpr int KSP = (KS + 3) / 4 * 4;
+    constexpr int KTSZ = (KS * KS * NKP + 3) / 4 * 4;
+    const size_t smem = sizeof(float) * (2 * SW * SW + KTSZ + KS * KSP);
+    cudaFuncSetAttribute(subtract_kernel<KS, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((a.w + TILE - 1) / TILE, (a.h + TILE - 1) / TILE);
+    subtract_kernel<KS, NK><<<grid, THREADS, smem, st>>>(a);
+    return argus_launch_status();
+}
+
+template <int KS>
+int launch_nk(const SubArgs& a, int nk, cudaStream_t st) {
+    switch (nk) {
+        case 1: return launch<KS, 1>(a, st);
+        case 3: return launch<KS, 3>(a, st);
+        case 6: return launch<KS, 6>(a, st);
+    }
+    return ARGUS_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+extern "C" int argus_subtract(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
+                              const float* ref_var, const uint8_t* flags, argus_shape shape, int frame_w,
+                              int frame_h, int ox, int oy, int ksize, int spatial_degree, const float* K,
+                              int bg_degree, const double* bg, float* diff, float* diff_var,
+                              argus_stream stream) {
+    if (!ctx || !sci || !sci_var || !ref || !ref_var || !flags || !K || !diff) return ARGUS_ERR_ARG;
+    if (bg_degree >= 0 && !bg) return ARGUS_ERR_ARG;
+    int st = argus_check_shape(shape, ctx->max_pixels);
+    if (st) return st;
+    const void* ps[] = {sci, sci_var, ref, ref_var, flags, diff, diff_var};
+    for (const void* p : ps)
+        if (p && argus_check_ptr16(p)) return ARGUS_ERR_ALIGN;
+    if (spatial_degree < 0 || spatial_degree > 2 || bg_degree < -1 || bg_degree > 2) return ARGUS_ERR_ARG;
+    if (frame_w < shape.w + ox || frame_h < shape.h + oy || ox < 0 || oy < 0) return ARGUS_ERR_ARG;
+    if (spatial_degree > 0 && ((ox % TILE) || (oy % TILE))) return ARGUS_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    SubArgs a;
+    a.sci = sci; a.sci_var = sci_var; a.ref = ref; a.ref_var = ref_var; a.flags = flags; a.K = K;
+    a.bg = bg; a.diff = diff; a.diff_var = diff_var; a.pitch = shape.pitch; a.w = shape.w; a.h = shape.h;
+    a.W = frame_w; a.H = frame_h; a.ox = ox; a.oy = oy; a.sdeg = spatial_degree;
+    a.bg_deg = bg_degree < 0 ? 0 : bg_degree;
+    a.nbg = bg_degree < 0 ? 0 : argus_nterms(bg_degree);
+    const int nk = argus_nterms(spatial_degree);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ksize) {
+        case 7: return launch_nk<7>(a, nk, s);
+        case 9: return launch_nk<9>(a, nk, s);
+        case 11: return launch_nk<11>(a, nk, s);
+        case 15: return launch_nk<15>(a, nk, s);
+        case 21: return launch_nk<21>(a, nk, s);
+    }
+    return ARGUS_ERR_UNSUPPORTED;
+}

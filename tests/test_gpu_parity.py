@@ -1,0 +1,319 @@
+"""GPU (sm_103a, through the C ABI) against the FP64 oracle, element by element,
+on seeded inputs that span several tiles and a ragged tail.
+
+Tolerances (written per test): integer and flag outputs bit-exact; calibrated
+pixels within 4 float32 ulps of the operand magnitude; difference pixels within
+1e-4 of max(|I|, |R (x) K|, 1) per pixel; difference variance within 1e-5
+relative; detection masks bit-exact (the S/N decision is taken in float on both
+sides); kernel pixels within 1e-3 of max |K| (FP32 normal equations).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2207_14304_gb300 import _binding as B
+from paper_2207_14304_gb300 import synth
+from paper_2207_14304_gb300.synth import pitch_for
+from tests.gpu_helpers import F32_EPS, assert_rel, ctx_for, dev_pitched, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+
+
+# --------------------------------------------------------------------------- calibrate
+@pytest.mark.parametrize("w,h,use_bias_frame", [(1000, 37, False), (64, 64, True), (9, 3, False), (1, 1, False)])
+def test_calibrate_parity(ora, w, h, use_bias_frame):
+    rng = np.random.default_rng(w * 131 + h)
+    raw = rng.integers(0, 65536, (h, w), dtype=np.uint16)
+    raw.flat[0] = 65535
+    dark = rng.uniform(0, 50, (h, w)).astype(np.float32)
+    flat = rng.uniform(0.5, 1.5, (h, w)).astype(np.float32)
+    flat.flat[3::17] = 0
+    flat.flat[5::19] = -1
+    flat.flat[7::23] = np.inf
+    flat.flat[2::29] = np.nan
+    bpm = (rng.random((h, w)) < 0.05).astype(np.uint8)
+    biasf = rng.integers(90, 110, (h, w), dtype=np.uint16) if use_bias_frame else None
+    gain, rn, sat = float(np.float32(1.37)), float(np.float32(1.7)), 60000
+    I, V, fl, n = ora.calibrate(raw, bias=100, bias_frame=biasf, dark=dark, flat=flat, bpm=bpm,
+                                gain=gain, read_noise=rn, sat=sat)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        d_raw, d_dark, d_flat, d_bpm = (dev_pitched(a) for a in (raw, dark, flat, bpm))
+        d_bias = dev_pitched(biasf) if use_bias_frame else None
+        img = torch.full((h, pitch), -7.0, device="cuda")
+        var = torch.full((h, pitch), -7.0, device="cuda")
+        flg = torch.full((h, pitch), 0xEE, dtype=torch.uint8, device="cuda")
+        cal = B.make_calib(100, d_dark, d_flat, d_bpm, gain, rn, sat, bias_frame=d_bias)
+        B.argus_calibrate(ctx, d_raw, B.argus_shape(w, h, pitch), cal, img, var, flg)
+        torch.cuda.synchronize()
+        assert B.argus_sync_status(ctx) == 0
+        np.testing.assert_array_equal(host(flg, w), fl)
+        ng = np.abs(n.astype(np.float64) * gain)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sI = np.where(np.isfinite(flat) & (flat > 0), (ng + np.abs(dark)) / np.abs(flat), 1.0)
+            sV = np.where(np.isfinite(flat) & (flat > 0), (ng + rn * rn) / flat.astype(np.float64) ** 2, 1.0)
+        assert_rel(host(img, w), I, sI, 4 * F32_EPS, "I")
+        assert_rel(host(var, w), V, sV, 4 * F32_EPS, "V")
+        if pitch > w:   # padding untouched
+            assert (img[:, w:] == -7.0).all() and (flg[:, w:] == 0xEE).all()
+    finally:
+        B.argus_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- subtract
+def _subtract_case(ora, ks, sdeg, bgdeg, w, h, seed):
+    rng = np.random.default_rng(seed)
+    cat = synth.star_catalog(max(10, w * h // 400), w, h, seed=seed, flux_min=1e3, flux_max=1e6)
+    R = (synth.render(cat, w, h, 1.3, sky=300.0).numpy() + rng.normal(0, 3, (h, w))).astype(np.float32)
+    I = (synth.render(cat, w, h, 1.8, sky=305.0).numpy() + rng.normal(0, 17, (h, w))).astype(np.float32)
+    Vi = rng.uniform(250, 400, (h, w)).astype(np.float32)
+    Vr = rng.uniform(5, 20, (h, w)).astype(np.float32)
+    fl = (rng.random((h, w)) < 0.01).astype(np.uint8)
+    nk = (sdeg + 1) * (sdeg + 2) // 2
+    K = (rng.normal(0, 1, (nk, ks, ks)) / ks ** 2).astype(np.float32)
+    K[0] += (1.0 / ks ** 2)
+    nbg = (bgdeg + 1) * (bgdeg + 2) // 2
+    bg = rng.normal(0, 5, nbg)
+    return R, I, Vi, Vr, fl, K, bg
+
+
+@pytest.mark.parametrize("ks,sdeg,bgdeg,w,h", [(11, 0, 0, 200, 150), (21, 2, 2, 230, 170), (7, 1, 1, 97, 65),
+                                               (15, 0, 0, 128, 64), (9, 2, 0, 70, 45)])
+def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
+    R, I, Vi, Vr, fl, K, bg = _subtract_case(ora, ks, sdeg, bgdeg, w, h, seed=ks * 7 + w)
+    Do, Vo = ora.subtract(I, Vi, R, Vr, fl, K.astype(np.float64), bg, sdeg=sdeg, bgdeg=bgdeg)
+    Kabs = np.abs(K).sum(0, keepdims=True).astype(np.float64)
+    Cabs, _ = ora.subtract(np.zeros_like(I), Vi, np.abs(R), Vr, fl, Kabs, [0.0], sdeg=0, bgdeg=0,
+                           with_var=False)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        dI, dVi, dR, dVr, dfl = (dev_pitched(a) for a in (I, Vi, R, Vr, fl))
+        dK = torch.from_numpy(K.reshape(-1)).cuda()
+        dbg = torch.from_numpy(np.asarray(bg, np.float64)).cuda()
+        D = torch.full((h, pitch), -9.0, device="cuda")
+        VD = torch.full((h, pitch), -9.0, device="cuda")
+        B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, B.argus_shape(w, h, pitch), w, h, 0, 0, ks, sdeg, dK,
+                         bgdeg, dbg, D, VD)
+        torch.cuda.synchronize()
+        Dg, Vg = host(D, w), host(VD, w)
+        zero = (Do == 0) & (Vo == 0)
+        np.testing.assert_array_equal(Dg[zero], 0.0)
+        np.testing.assert_array_equal(Vg[zero], 0.0)
+        scale = np.maximum(np.maximum(np.abs(I), -Cabs), 1.0)
+        e = assert_rel(Dg, Do, scale, 1e-4, "D")
+        assert e < 1e-5, e       # FP32 accumulation is far inside the 1e-4 bound
+        assert_rel(Vg, Vo, np.maximum(Vo, 1e-6), 1e-5, "V_D")
+        if pitch > w:
+            assert (D[:, w:] == -9.0).all()
+    finally:
+        B.argus_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- detect
+def _detect_case(w, h, seed, sig=1.6):
+    rng = np.random.default_rng(seed)
+    n = 40
+    xs = rng.uniform(3, w - 3, n)
+    ys = rng.uniform(3, h - 3, n)
+    F = 10 ** rng.uniform(2.5, 4.5, n) * rng.choice([-1.0, 1.0], n)
+    cat = synth.Catalog(torch.tensor(xs), torch.tensor(ys), torch.tensor(F))
+    model = synth.render(cat, w, h, sig).numpy()
+    V = rng.uniform(50, 150, (h, w)).astype(np.float32)
+    D = (model + rng.normal(0, 1, (h, w)) * np.sqrt(V)).astype(np.float32)
+    V.flat[::997] = 0.0
+    D.flat[11::1013] = np.nan
+    fl = (rng.random((h, w)) < 0.002).astype(np.uint8)
+    return D, V, fl
+
+
+@pytest.mark.parametrize("w,h,cap", [(500, 300, 1 << 12), (131, 77, 1 << 10), (256, 256, 5)])
+def test_detect_parity(ora, w, h, cap):
+    D, V, fl = _detect_case(w, h, seed=w + h)
+    sig = 1.6
+    mo, so, no = ora.detect(D, V, fl, 5.0, sig)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        dD, dV, dfl = dev_pitched(D), dev_pitched(V), dev_pitched(fl)
+        mask = torch.full((h, pitch), 0xEE, dtype=torch.uint8, device="cuda")
+        out = torch.zeros(cap * B.SOURCE_BYTES, dtype=torch.uint8, device="cuda")
+        nf = torch.zeros(4, dtype=torch.int32, device="cuda")
+        B.argus_detect(ctx, dD, dV, dfl, B.argus_shape(w, h, pitch), 5.0, sig, mask, out, cap, nf)
+        torch.cuda.synchronize()
+        st = B.argus_sync_status(ctx)
+        ng = int(nf[0].item())
+        np.testing.assert_array_equal(host(mask, w), mo)
+        assert ng == no
+        assert st == (B.ARGUS_ERR_CAPACITY if no > cap else 0)
+        sg = B.sources_from_bytes(out, min(ng, cap))
+        so = so[: min(no, cap)]
+        for k in ("px", "py", "npix", "sign"):
+            np.testing.assert_array_equal(sg[k], so[k], err_msg=k)
+        np.testing.assert_array_equal(sg["peak_snr"], so["peak_snr"])
+        assert np.abs(sg["x"] - so["x"]).max(initial=0) < 2e-3
+        assert np.abs(sg["y"] - so["y"]).max(initial=0) < 2e-3
+        assert_rel(sg["flux"], so["flux"], np.maximum(np.abs(so["flux"]), so["flux_err"]), 1e-3, "flux")
+        assert_rel(sg["flux_err"], so["flux_err"], np.maximum(so["flux_err"], 1e-30), 1e-4, "flux_err")
+    finally:
+        B.argus_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- stamps
+def _ref_field(w, h, seed, n=300):
+    cat = synth.star_catalog(n, w, h, seed=seed, flux_min=1e3, flux_max=1e6)
+    R, Vr = synth.reference_image(synth.render(cat, w, h, 1.2, sky=300.0), 30, 1.7, seed + 1)
+    return R.numpy(), Vr.numpy()
+
+
+@pytest.mark.parametrize("w,h,gx,gy", [(300, 260, 4, 3), (257, 129, 5, 2)])
+def test_select_stamps_parity(ora, w, h, gx, gy):
+    R, _ = _ref_field(w, h, seed=w)
+    rng = np.random.default_rng(1)
+    fl = (rng.random((h, w)) < 0.0005).astype(np.uint8)
+    co = ora.select_stamps(R, fl, gx, gy, 21, 5, 3.0e4)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        cen = torch.full((gx * gy, 2), -1, dtype=torch.int32, device="cuda")
+        ns = torch.zeros(4, dtype=torch.int32, device="cuda")
+        B.argus_select_stamps(ctx, dev_pitched(R), dev_pitched(fl), B.argus_shape(w, h, pitch), gx, gy, 21, 5,
+                              3.0e4, 10, 0.1, cen, ns)
+        torch.cuda.synchronize()
+        n = int(ns[0].item())
+        assert n == len(co) and n > 0
+        np.testing.assert_array_equal(cen[:n].cpu().numpy(), co)
+    finally:
+        B.argus_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- fit + expand
+def _fit_field(w, h, seed, sdeg):
+    cat = synth.star_catalog(w * h // 80, w, h, seed=seed, flux_min=1e2, flux_max=1e6)
+    Rexp = synth.render(cat, w, h, 1.2, sky=300.0)
+    R, Vr = synth.reference_image(Rexp, 30, 1.7, seed + 1)
+    sig = synth.field_sigma(w, h, 1.5, 2.1) if sdeg else 1.8
+    Iexp = synth.render(cat, w, h, sig, sky=305.0, shift=(0.3, -0.2))
+    cal = synth.make_calib(w, h, seed + 2)
+    raw = synth.expose(Iexp, cal, seed + 3)
+    I, V, fl, _ = ora_cal(raw, cal)
+    return R.numpy(), Vr.numpy(), I.astype(np.float32), V.astype(np.float32), fl, raw.numpy(), cal
+
+
+def ora_cal(raw, cal):
+    import oracle
+    return oracle.calibrate(raw.numpy(), bias=cal.bias, dark=cal.dark.numpy(), flat=cal.flat.numpy(),
+                            bpm=cal.bpm.numpy(), gain=cal.gain, read_noise=cal.read_noise, sat=cal.sat)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("w,h,ks,sdeg,grid", [(256, 256, 11, 0, (4, 4)), (320, 288, 11, 2, (6, 5))])
+def test_fit_parity(ora, prec, w, h, ks, sdeg, grid):
+    R, Vr, I, V, fl, raw, cal = _fit_field(w, h, seed=w + ks, sdeg=sdeg)
+    b = ora.Basis(ksize=ks, spatial_degree=sdeg, bg_degree=sdeg)
+    cen = ora.select_stamps(R, fl, grid[0], grid[1], 21, ks // 2, 3.0e4)
+    assert len(cen) >= grid[0] * grid[1] // 2
+    res = ora.fit(I, V, R, fl, cen, 21, b)
+    assert res.status == 0
+    Ko, bgo = ora.expand(b, res.coeffs)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h, max_stamps=64)
+    try:
+        gb = B.make_basis(ks, (0.7, 1.5, 3.0), (6, 4, 2), sdeg, sdeg)
+        nb, Ks, Kb, Nc = B.basis_counts(gb)
+        assert Nc == b.ncoeffs
+        dcen = torch.zeros((64, 2), dtype=torch.int32, device="cuda")
+        dcen[: len(cen)] = torch.from_numpy(cen).cuda()
+        ns = torch.tensor([len(cen), 0, 0, 0], dtype=torch.int32, device="cuda")
+        coeffs = torch.zeros(Nc, dtype=torch.float64, device="cuda")
+        stats = torch.zeros(128, dtype=torch.uint8, device="cuda")
+        dI, dV, dR, dfl = dev_pitched(I), dev_pitched(V), dev_pitched(R), dev_pitched(fl)
+        B.argus_fit_kernel(ctx, dI, dV, dR, dfl, B.argus_shape(w, h, pitch), dcen, ns, 64, 21, gb, prec, coeffs,
+                           stats)
+        K = torch.zeros(Ks * ks * ks, dtype=torch.float32, device="cuda")
+        bg = torch.zeros(Kb, dtype=torch.float64, device="cuda")
+        B.argus_expand_kernel(ctx, gb, coeffs, K, bg)
+        torch.cuda.synchronize()
+        assert B.argus_sync_status(ctx) == 0
+        st = B.fit_stats_from_bytes(stats)
+        a = coeffs.cpu().numpy()
+        Kg = K.cpu().numpy().reshape(Ks, ks, ks)
+        kerr = np.abs(Kg - Ko).max() / np.abs(Ko).max()
+        aerr = np.linalg.norm(a - res.coeffs) / np.linalg.norm(res.coeffs)
+        print(f"\n[fit {prec} {w}x{h} ks{ks} sdeg{sdeg}] kernel-pixel err {kerr:.2e}  coeff err {aerr:.2e}  "
+              f"chi2 {st['chi2']:.6g} vs {res.chi2:.6g}  chi2(a0) {st['chi2_a0']:.6g}  step {st['max_step']:.2e}")
+        assert st["status"] == 0 and st["n_coeffs"] == Nc and st["n_stamps_used"] == len(cen)
+        assert st["dof"] == res.dof
+        assert abs(st["chi2"] / res.chi2 - 1) < {"fp32": 1e-4, "tf32": 1e-3, "bf16": 2e-2}[prec]
+        np.testing.assert_allclose(bg.cpu().numpy(), bgo, rtol=0,
+                                   atol={"fp32": 1e-3, "tf32": 1e-2, "bf16": 1e-1}[prec] * max(1, np.abs(bgo).max()))
+        if prec == "fp32":
+            assert kerr < 1e-3
+        else:
+            assert kerr < {"tf32": 2e-2, "bf16": 5e-2}[prec]
+    finally:
+        B.argus_destroy(ctx)
+
+
+def test_expand_parity(ora):
+    b = ora.Basis(ksize=21, spatial_degree=2, bg_degree=2)
+    rng = np.random.default_rng(3)
+    a = rng.normal(0, 0.1, b.ncoeffs)
+    Ko, bgo = ora.expand(b, a)
+    ctx = ctx_for(64, 64)
+    try:
+        gb = B.make_basis(21, (0.7, 1.5, 3.0), (6, 4, 2), 2, 2)
+        K = torch.zeros(6 * 441, dtype=torch.float32, device="cuda")
+        bg = torch.zeros(6, dtype=torch.float64, device="cuda")
+        B.argus_expand_kernel(ctx, gb, torch.from_numpy(a).cuda(), K, bg)
+        torch.cuda.synchronize()
+        assert_rel(K.cpu().numpy().reshape(6, 21, 21), Ko, np.abs(Ko).max(), 2e-7, "K")
+        np.testing.assert_array_equal(bg.cpu().numpy(), bgo)
+    finally:
+        B.argus_destroy(ctx)
+
+
+# --------------------------------------------------------------------------- coadd
+@pytest.mark.parametrize("nf,w,h", [(7, 100, 70), (30, 133, 41), (2, 40, 40), (1, 17, 9)])
+def test_coadd_parity(ora, nf, w, h):
+    cal = synth.make_calib(w, h, seed=nf, bad_frac=0.003)
+    cat = synth.star_catalog(w * h // 200, w, h, seed=nf + 1)
+    sh = synth.uniform_shifts(nf, seed=nf).numpy()
+    frames = []
+    for f in range(nf):
+        e = synth.render(cat, w, h, 1.5, sky=300.0, shift=(-float(sh[f, 0]), -float(sh[f, 1])))
+        frames.append(synth.expose(e, cal, seed=100 + f, cosmic_frac=0.01).numpy())
+    raw = np.stack(frames)
+    raw[0, 5, 5] = 65535
+    co, va, nu, mg = ora.coadd(raw, sh, bias=cal.bias, dark=cal.dark.numpy(), flat=cal.flat.numpy(),
+                               bpm=cal.bpm.numpy(), gain=cal.gain, read_noise=cal.read_noise, sat=60000)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        stack = torch.zeros((nf, h, pitch), dtype=torch.uint16)
+        stack[:, :, :w] = torch.from_numpy(raw)
+        stack = stack.cuda()
+        dsh = torch.from_numpy(sh).cuda()
+        calg = B.make_calib(cal.bias, dev_pitched(cal.dark.numpy()), dev_pitched(cal.flat.numpy()),
+                            dev_pitched(cal.bpm.numpy()), cal.gain, cal.read_noise, 60000)
+        dco = torch.zeros((h, pitch), device="cuda")
+        dva = torch.zeros((h, pitch), device="cuda")
+        dnu = torch.zeros((h, pitch), dtype=torch.uint8, device="cuda")
+        B.argus_coadd(ctx, stack, nf, B.argus_shape(w, h, pitch), dsh, calg, 3.0, 5, dco, dva, dnu)
+        torch.cuda.synchronize()
+        cg, vg, ng = host(dco, w), host(dva, w), host(dnu, w)
+        safe = mg > 1e-4
+        assert safe.mean() > 0.99
+        np.testing.assert_array_equal(ng[safe], nu[safe])
+        assert_rel(cg[safe], co[safe], np.maximum(np.abs(co[safe]), 1.0), 2e-6, "coadd")
+        assert_rel(vg[safe], va[safe], np.maximum(va[safe], 1e-6), 2e-6, "var")
+    finally:
+        B.argus_destroy(ctx)
