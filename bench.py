@@ -1,0 +1,436 @@
+"""Benchmark of the full-frame difference-imaging step on GB300.
+
+One step = one 9576 x 6388 IMX455 frame through the whole per-frame path:
+calibration, stamp selection (20 x 20 grid), kernel fit (21 x 21 Alard-Lupton
+basis, degree-2 spatial variation, 295 unknowns, FP32 normal equations, FP64
+Cholesky + one refinement), kernel expansion, subtraction with the difference
+variance, and 5-sigma detection.  Inputs are seeded synthetic star fields with
+the recipe of the paper's IMX455 frames (150,000 stars, PSF 1.3-2.2 px across
+the field, 300 e- sky, 1.7 e- read noise).  Every input is resident in HBM;
+per step the raw frame (122 MB), reference and variances (~490 MB) are read, so
+the working set is larger than the 129 MB L2 and no flush is needed.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(a bounded sample of the same workload on the host cores).  Under torchrun
+with N > 1 every rank runs its own frame stream on its own GPU (replicas: the
+path shards by frame with no collective); rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpix/s differenced per GB300 (plain vs learned/BF16), % HBM roofline"
+W, H = 9576, 6388
+N_STARS = 150_000
+KSIZE, SDEG, BGDEG = 21, 2, 2
+GRID = (20, 20)
+STAMP = 21
+# algorithmic traffic of the fused frame path, bytes per pixel: raw 2, dark 4, flat 4,
+# bpm 1, ref 4, ref var 4 in; D 4, V_D 4, mask 1 out; calibrated image, variance and
+# flags (9 B) are written and read back once between the calibration and subtraction
+# kernels and are not counted (a fused kernel would not move them).
+BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
+
+
+def workload_config(precision="fp32"):
+    return {"workload": "full-frame plain DIA, 9576x6388 uint16 IMX455 frame + float32 reference",
+            "frame": [W, H], "stars": N_STARS, "psf_sigma": "1.3-2.2 px (science), 1.2 px (reference)",
+            "kernel": KSIZE, "spatial_degree": SDEG, "bg_degree": BGDEG, "basis": "3 Gaussians x degrees (6,4,2)",
+            "stamps": GRID[0] * GRID[1], "stamp": STAMP, "normal_equations": precision, "nsigma": 5.0,
+            "l2": "working set > 129 MB L2 per step (raw 122 MB + reference/variances 490 MB); no flush"}
+
+
+# --------------------------------------------------------------------------- distributed helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """MAX of a float over all ranks (identity on one rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, elapsed_s: float, dist, device=None):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    ws = dist.get_world_size() if dist is not None else 1
+    tmax = max_over_ranks(dist, elapsed_s, device)
+    return units_per_rank * ws / tmax, tmax
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def make_inputs(device, seed=2):
+    import torch
+    from paper_2207_14304_gb300 import synth
+    cat = synth.star_catalog(N_STARS, W, H, seed=seed)
+    Rexp = synth.render(cat, W, H, 1.2, sky=300.0, device=device, dtype=torch.float32)
+    R, Vr = synth.reference_image(Rexp, 30, 1.7, seed + 1)
+    del Rexp
+    sig = synth.field_sigma(W, H, 1.3, 2.2)
+    Iexp = synth.render(cat, W, H, sig, sky=305.0, device=device, dtype=torch.float32)
+    cal = synth.make_calib(W, H, seed=seed + 2, device=device)
+    raw = synth.expose(Iexp, cal, seed=seed + 3)
+    del Iexp
+    return raw, R, Vr, cal
+
+
+def run_gpu(args):
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    from paper_2207_14304_gb300.pipeline import FramePipeline
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init(ws, "nccl")
+
+    raw, R, Vr, cal = make_inputs(device, seed=2 + rank)
+    basis = B.make_basis(KSIZE, (0.7, 1.5, 3.0), (6, 4, 2), SDEG, BGDEG)
+    pipe = FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, precision=args.precision,
+                         psf_sigma=1.8, device=local)
+    pitch = pipe.pitch
+
+    def pad(a):
+        t = torch.zeros((H, pitch), dtype=a.dtype, device=device)
+        t[:, :W] = a
+        return t
+
+    d_raw, d_R, d_Vr = pad(raw), pad(R), pad(Vr)
+    d_dark, d_flat, d_bpm = pad(cal.dark), pad(cal.flat), pad(cal.bpm)
+    calib = B.make_calib(cal.bias, d_dark, d_flat, d_bpm, cal.gain, cal.read_noise, cal.sat)
+    del raw, R, Vr
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        pipe.run(d_raw, calib, d_R, d_Vr, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(device)
+    st = pipe.status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status {st} ({B.status_string(st)}) after warm-up")
+
+    # per-stage times (untimed pass, for the report)
+    stage = {}
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    evs[0].record(stream); pipe.calibrate(d_raw, calib, stream)
+    evs[1].record(stream); pipe.select_stamps(d_R, stream)
+    evs[2].record(stream); pipe.fit(d_R, stream)
+    evs[3].record(stream); pipe.subtract(d_R, d_Vr, stream)
+    evs[4].record(stream); pipe.detect(stream)
+    evs[5].record(stream)
+    torch.cuda.synchronize(device)
+    for i, k in enumerate(["calibrate", "select_stamps", "fit", "subtract", "detect"]):
+        stage[k] = round(evs[i].elapsed_time(evs[i + 1]), 4)
+
+    # timed region: K steps, subtract kernel bracketed by events on its stream
+    sub_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sub_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), f"argus_clocks_rank{rank}_{os.getpid()}.csv")) \
+        if args.clocks else None
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    n0 = B.argus_launch_count()
+    t0.record(stream)
+    for i in range(args.steps):
+        pipe.calibrate(d_raw, calib, stream)
+        pipe.select_stamps(d_R, stream)
+        pipe.fit(d_R, stream)
+        sub_s[i].record(stream)
+        pipe.subtract(d_R, d_Vr, stream)
+        sub_e[i].record(stream)
+        pipe.detect(stream)
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    launches = B.argus_launch_count() - n0
+    barrier(dist, device)
+    clk = clocks.stop() if clocks else None
+    elapsed = t0.elapsed_time(t1) / 1e3
+    st = pipe.status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status {st} ({B.status_string(st)}) in the timed region")
+    mpix = W * H / 1e6
+    value, tmax = aggregate(mpix * args.steps, elapsed, dist, device)
+    sub_ms = statistics.mean(sub_s[i].elapsed_time(sub_e[i]) for i in range(args.steps))
+
+    # end to end through the public API: pinned host raw frame in, detection list out
+    raw_host = d_raw.cpu().pin_memory()
+    out_host = torch.empty(pipe.sources.numel(), dtype=torch.uint8).pin_memory()
+    nf_host = torch.empty(4, dtype=torch.int32).pin_memory()
+    ke = max(3, args.steps // 4)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ke):
+        d_raw.copy_(raw_host, non_blocking=True)
+        pipe.run(d_raw, calib, d_R, d_Vr, stream)
+        nf_host.copy_(pipe.n_found, non_blocking=True)
+        out_host.copy_(pipe.sources, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_value, _ = aggregate(mpix * ke, e2e_s, dist, device)
+    n_found = int(nf_host[0].item())
+
+    peaks = load_peaks()
+    # dominant kernel: subtract (FP32 FMA issue bound, see the design notes)
+    flop_px = 2 * ((SDEG + 1) * (SDEG + 2) // 2 * KSIZE * KSIZE + KSIZE * KSIZE)
+    sub_flops = flop_px * W * H
+    achieved = sub_flops / (sub_ms / 1e3) / 1e12
+    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1462.0)
+    alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x clock
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    step_s = tmax / args.steps
+    hbm_frac = BYTES_PER_PX * W * H / step_s / 1e9 / hbm
+
+    var = {}
+    if args.variants and ws == 1:
+        for prec in ("tf32", "bf16"):
+            pv = FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, precision=prec, psf_sigma=1.8,
+                               device=local, ctx=pipe.ctx)
+            for _ in range(2):
+                pv.run(d_raw, calib, d_R, d_Vr, stream)
+            torch.cuda.synchronize(device)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            kv = max(3, args.steps // 4)
+            a0.record(stream)
+            for _ in range(kv):
+                pv.run(d_raw, calib, d_R, d_Vr, stream)
+            a1.record(stream)
+            torch.cuda.synchronize(device)
+            var[prec] = round(mpix * kv / (a0.elapsed_time(a1) / 1e3), 2)
+            if pv.status(stream) != 0:
+                var[prec] = None
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.precision),
+        "roofline": {"bound": "alu", "kernel": "subtract", "achieved": round(achieved, 3),
+                     "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
+                     "traffic": None,
+                     "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz (median SM clock under load)"},
+        "hbm_roofline_frac": round(hbm_frac, 4),
+        "hbm_bytes_per_px": BYTES_PER_PX,
+        "stage_ms": stage, "subtract_ms": round(sub_ms, 4),
+        "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(raw_host.numel() * 2),
+                "d2h_bytes_per_step": int(out_host.numel() + nf_host.numel() * 4)},
+        "gpu_launches": int(launches), "sources_last_frame": n_found,
+        "variants": var, "clocks": clk,
+    }
+    if rank == 0 and args.cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args)
+    pipe.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+# --------------------------------------------------------------------------- CPU oracle arm
+def oracle_sample(band_rows=48, seed=2, threads=None):
+    """Time the FP64 oracle on a bounded sample of the full-frame workload.
+
+    The kernel fit runs in full (400 stamps, 295 unknowns); calibration,
+    subtraction and detection run on a band of `band_rows` full-width rows in
+    the middle of the frame (the fit's kernel, frame geometry and spatial terms
+    of the full frame).  Frame throughput is extrapolated linearly:
+    T_frame = T_fit + T_band * H / band_rows.
+    """
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2207_14304_gb300 import synth
+    if threads:
+        oracle.set_threads(threads)
+    cores = oracle.num_threads()
+    cat = synth.star_catalog(N_STARS, W, H, seed=seed)
+    # only the rows the sample touches are rendered: the fit stamps' rows and the band
+    y0 = H // 2 - band_rows // 2
+    ob = oracle.Basis(ksize=KSIZE, spatial_degree=SDEG, bg_degree=BGDEG)
+    Rexp = synth.render(cat, W, H, 1.2, sky=300.0, dtype=torch.float32)
+    R, Vr = synth.reference_image(Rexp, 30, 1.7, seed + 1)
+    sig = synth.field_sigma(W, H, 1.3, 2.2)
+    Iexp = synth.render(cat, W, H, sig, sky=305.0, dtype=torch.float32)
+    cal = synth.make_calib(W, H, seed=seed + 2)
+    raw = synth.expose(Iexp, cal, seed=seed + 3).numpy()
+    R, Vr = R.numpy(), Vr.numpy()
+    dark, flat, bpm = cal.dark.numpy(), cal.flat.numpy(), cal.bpm.numpy()
+    # fit: calibrate and select on the full frame is part of the per-pixel cost; the
+    # oracle's stamp selection runs on the full frame once (timed)
+    t0 = time.perf_counter()
+    I, V, fl, _ = oracle.calibrate(raw, bias=cal.bias, dark=dark, flat=flat, bpm=bpm, gain=cal.gain,
+                                   read_noise=cal.read_noise, sat=cal.sat)
+    t_cal_full = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cen = oracle.select_stamps(R, fl, GRID[0], GRID[1], STAMP, KSIZE // 2, 3.0e4)
+    t_sel = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = oracle.fit(I.astype(np.float32), V.astype(np.float32), R, fl, cen, STAMP, ob)
+    K, bg = oracle.expand(ob, res.coeffs)
+    t_fit = time.perf_counter() - t0
+    # band: subtract + detect with the full-frame geometry
+    r = KSIZE // 2
+    ys = slice(y0 - r, y0 + band_rows + r)
+    t0 = time.perf_counter()
+    Db, Vb = oracle.subtract(I[ys].astype(np.float32), V[ys].astype(np.float32), R[ys], Vr[ys], fl[ys], K, bg,
+                             sdeg=SDEG, bgdeg=BGDEG, frame=(W, H), origin=(0, y0 - r))
+    mask, src, n = oracle.detect(Db[r:-r].astype(np.float32), Vb[r:-r].astype(np.float32), fl[ys][r:-r], 5.0, 1.8)
+    t_band = time.perf_counter() - t0
+    t_frame = t_cal_full + t_sel + t_fit + t_band * H / band_rows
+    return {"value": round(W * H / 1e6 / t_frame, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": (f"full calibration ({t_cal_full:.2f} s), stamp selection ({t_sel:.2f} s) and 400-stamp "
+                       f"kernel fit ({t_fit:.2f} s) of one 9576x6388 frame, subtraction+detection on a "
+                       f"{band_rows}-row band ({t_band:.2f} s) scaled x{H / band_rows:.1f} to the frame"),
+            "seconds": round(t_cal_full + t_sel + t_fit + t_band, 2)}
+
+
+def cpu_baseline(args):
+    try:
+        return oracle_sample(band_rows=args.band_rows)
+    except Exception as e:   # the GPU line stays valid without the baseline
+        return {"value": None, "unit": "Mpix/s", "cores": None, "kind": "oracle", "sample": f"failed: {e!r}"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    import oracle
+    oracle.build()
+    vals, secs = [], []
+    last = None
+    for _ in range(max(1, args.steps)):
+        last = oracle_sample(band_rows=args.band_rows)
+        vals.append(last["value"])
+        secs.append(last["seconds"])
+    v = statistics.median(vals)
+    out = {"metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(W * H / 1e6 / v * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config("fp64"), "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--band-rows", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-clocks", dest="clocks", action="store_false")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        args.steps = min(args.steps, 3)
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,10 +109,17 @@ typedef struct {
     int status;             /* ARGUS_OK or ARGUS_ERR_SINGULAR */
     int n_stamps_used;      /* stamps whose window lay inside the frame */
     int precision;          /* ARGUS_PREC_* used for the Gram matrix */
+    int refine_iters;       /* refinement steps applied */
+    int pad_;
 } argus_fit_stats;
 
 /* Human-readable name of a status code. */
 const char *argus_status_string(int status);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side tally, all contexts).  The difference of two readings counts
+ * the kernels of the calls in between. */
+unsigned long long argus_launch_count(void);
 
 /* Create a context on `device` with scratch for frames of up to max_pixels
  * (h * pitch), up to max_stamps stamps of side <= 31, up to max_coeffs

@@ -60,7 +60,8 @@ class argus_source(C.Structure):
 class argus_fit_stats(C.Structure):
     _fields_ = [("chi2", C.c_double), ("chi2_a0", C.c_double), ("max_step", C.c_double),
                 ("n_pix", C.c_longlong), ("dof", C.c_longlong), ("n_coeffs", C.c_int),
-                ("status", C.c_int), ("n_stamps_used", C.c_int), ("precision", C.c_int)]
+                ("status", C.c_int), ("n_stamps_used", C.c_int), ("precision", C.c_int),
+                ("refine_iters", C.c_int), ("pad_", C.c_int)]
 
 
 SOURCE_BYTES = C.sizeof(argus_source)
@@ -76,6 +77,7 @@ SH = argus_shape
 # entry point -> argument types
 SIGNATURES = {
     "argus_status_string": ([I], C.c_char_p),
+    "argus_launch_count": ([], C.c_ulonglong),
     "argus_create": ([C.POINTER(P), I, C.c_size_t, I, I, I], I),
     "argus_destroy": ([P], I),
     "argus_sync_status": ([P, P], I),
@@ -157,6 +159,7 @@ def make_calib(bias=100, dark=None, flat=None, bpm=None, gain=1.0, read_noise=1.
     c.gain = float(gain)
     c.read_noise = float(read_noise)
     c.sat = int(sat)
+    c._keep = (bias_frame, dark, flat, bpm)   # the struct holds raw pointers into these tensors
     return c
 
 
@@ -187,6 +190,10 @@ def argus_create(device=0, max_pixels=1 << 22, max_stamps=400, max_coeffs=320, d
                              int(max_coeffs), int(det_cap))
     _check(rc, "argus_create")
     return h
+
+
+def argus_launch_count() -> int:
+    return int(load().argus_launch_count())
 
 
 def argus_destroy(ctx):

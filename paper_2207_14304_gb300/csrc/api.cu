@@ -7,6 +7,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "argus_internal.cuh"
 
 extern "C" const char* argus_status_string(int s) {
@@ -35,6 +37,12 @@ int argus_check_ptr16(const void* p) {
     return ((uintptr_t)p & 15u) ? ARGUS_ERR_ALIGN : ARGUS_OK;
 }
 
+static std::atomic<unsigned long long> g_launches{0};
+
+void argus_count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+extern "C" unsigned long long argus_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 int argus_launch_status() {
     return cudaGetLastError() == cudaSuccess ? ARGUS_OK : ARGUS_ERR_CUDA;
 }
@@ -50,7 +58,7 @@ extern "C" int argus_destroy(argus_ctx* c) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    void* ps[] = {c->d_status, c->basis_img, c->basis_imgf, c->basis_h, c->basis_ab, c->X,
+    void* ps[] = {c->d_status, c->basis_img, c->basis_imgf, c->basis_h, c->basis_ab, c->basis_S, c->X,
                   c->gram_part, c->M, c->L, c->vec, c->resid_part, c->cell_key, c->label,
                   c->det_list, c->det_count, c->comp_key, c->comp_npix, c->comp_order,
                   c->row_count};
@@ -87,6 +95,7 @@ extern "C" int argus_create(argus_ctx** out, int device, size_t max_pixels, int 
               dalloc(&c->basis_imgf, (size_t)ARGUS_MAX_NB * ARGUS_MAX_KS * ARGUS_MAX_KS) &&
               dalloc(&c->basis_h, (size_t)ARGUS_MAX_NG * 16 * ARGUS_MAX_KS) &&
               dalloc(&c->basis_ab, (size_t)ARGUS_MAX_NB * 2) &&
+              dalloc(&c->basis_S, (size_t)ARGUS_MAX_NB * ARGUS_MAX_NB) &&
               dalloc(&c->X, (size_t)max_stamps * ARGUS_MAX_STAMP * ARGUS_MAX_STAMP * ARGUS_MAX_NB) &&
               dalloc(&c->gram_part, (size_t)c->gram_parts * np * np) &&
               dalloc(&c->M, np * np) && dalloc(&c->L, np * np) && dalloc(&c->vec, 8 * np) &&

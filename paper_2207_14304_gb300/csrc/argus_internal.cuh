@@ -27,7 +27,8 @@ struct argus_ctx {
 
     // basis tables (rebuilt per call from the host basis spec)
     double* basis_img;   // [nb][ks*ks] FP64 normalised basis
-    float* basis_imgf;   // [nb][ks*ks] FP32 copy
+    float* basis_imgf;   // [nb][ks*ks] FP32 orthonormalised images (B'_0 = B_0)
+    double* basis_S;     // [nb][nb] B'_m = sum_n S[n][m] B_n (n, m >= 1), upper triangular
     float* basis_h;      // [ngauss*9][ks] 1-D factors u^p exp(-u^2/2s^2)
     float* basis_ab;     // [nb][2] alpha, beta: B_n = alpha (h_p x h_q) - beta B_0
 
@@ -67,6 +68,7 @@ __device__ __forceinline__ void argus_latch(int* st, int code) { atomicCAS(st, 0
 int argus_check_shape(const argus_shape& s, size_t max_pixels);
 int argus_check_ptr16(const void* p);
 int argus_launch_status();   // ARGUS_OK or ARGUS_ERR_CUDA after a launch
+void argus_count_launch(int n);   // host-side tally of kernel launches
 
 // Inter-unit launchers
 int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st);

@@ -118,6 +118,6 @@ extern "C" int argus_calibrate(argus_ctx* ctx, const uint16_t* raw, argus_shape 
     long blocks = (nv + 255) / 256;
     const long cap = (long)ctx->num_sms * 8;
     if (blocks > cap) blocks = cap;
-    calibrate_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a);
+    calibrate_kernel<<<(unsigned)blocks, 256, 0, stream>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }

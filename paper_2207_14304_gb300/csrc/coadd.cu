@@ -182,7 +182,7 @@ int launch(const CoaddArgs& a, int sms, cudaStream_t st) {
     const long np = (long)a.w * a.h;
     long blocks = (np + 127) / 128;
     if (blocks > (long)sms * 16) blocks = (long)sms * 16;
-    coadd_kernel<NMAX><<<(unsigned)blocks, 128, 0, st>>>(a);
+    coadd_kernel<NMAX><<<(unsigned)blocks, 128, 0, st>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }
 

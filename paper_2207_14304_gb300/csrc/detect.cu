@@ -375,17 +375,17 @@ extern "C" int argus_detect(argus_ctx* ctx, const float* diff, const float* diff
     const long nv = (shape.pitch / 4) * (long)shape.h;
     long blocks = (nv + 255) / 256;
     if (blocks > (long)ctx->num_sms * 8) blocks = (long)ctx->num_sms * 8;
-    mask_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+    mask_kernel<<<(unsigned)blocks, 256, 0, s>>>(a); argus_count_launch(1);
     const int lb = ctx->num_sms * 2;
-    union_kernel<<<lb, 256, 0, s>>>(a);
-    flatten_kernel<<<lb, 256, 0, s>>>(a);
-    roots_kernel<<<lb, 256, 0, s>>>(a);
-    stats_kernel<<<lb, 256, 0, s>>>(a);
-    row_hist_kernel<<<lb, 256, 0, s>>>(a);
-    row_scan_kernel<<<1, 1024, 0, s>>>(a);
-    scatter_kernel<<<lb, 256, 0, s>>>(a);
-    row_sort_kernel<<<(shape.h + 255) / 256, 256, 0, s>>>(a);
-    measure_kernel<<<lb, 256, 0, s>>>(a);
-    finish_kernel<<<1, 1, 0, s>>>(a);
+    union_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    flatten_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    roots_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    stats_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    row_hist_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    row_scan_kernel<<<1, 1024, 0, s>>>(a); argus_count_launch(1);
+    scatter_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    row_sort_kernel<<<(shape.h + 255) / 256, 256, 0, s>>>(a); argus_count_launch(1);
+    measure_kernel<<<lb, 256, 0, s>>>(a); argus_count_launch(1);
+    finish_kernel<<<1, 1, 0, s>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }

@@ -1,16 +1,23 @@
 // K3-K5 and a3/a7: stamp selection, basis convolution on stamps, the
-// normal-equation Gram matrix (SIMT FP32, or tcgen05 tensor cores in TF32 /
-// BF16 with FP32 accumulation in TMEM), FP64 Cholesky with one refinement
-// step, and kernel expansion.  The fit is the Alard & Lupton (1998) / Alard
-// (2000) Gaussian-basis least-squares kernel adopted for the direct image
-// subtraction of paper Sec. 4.2 (Table 2).
+// normal-equation Gram matrix (SIMT FP32 with double-float block accumulation,
+// or tcgen05 tensor cores in TF32 / BF16 with FP32 accumulation in TMEM), FP64
+// Cholesky with iterative refinement, and kernel expansion.  The fit is the
+// Alard & Lupton (1998) / Alard (2000) Gaussian-basis least-squares kernel
+// adopted for the direct image subtraction of paper Sec. 4.2 (Table 2).
 //
-// Design rows are stamp pixels; the columns are [X_0, p_k X_n (n >= 1),
+// Conditioning.  The 49-function basis is nearly degenerate: for the full
+// frame workload the Jacobi-scaled normal matrix has condition ~4e9, far
+// beyond what an FP32-accumulated Gram can keep positive definite.  The fit is
+// therefore carried out in an equivalent basis: the functions n >= 1 are
+// orthonormalised in pixel space (B' = B S, S upper triangular from the
+// Cholesky factor of their Gram), which spans the same space, so the least-
+// squares solution is the same; the condition drops to ~1e6.  The solution c
+// in that basis is mapped back to Alard-Lupton coefficients a = S c in FP64.
+//
+// Design rows are stamp pixels; the columns are [X_0, p_k X_m (m >= 1),
 // p_k (background)] scaled by sqrt(w), plus the target sqrt(w) I as one extra
 // column, so the Gram of the augmented design holds M = C^T W C, b = C^T W I
-// and I^T W I at once.  X_n = R (x) B_n is computed separably: every basis
-// function is alpha_n (h_{g,p} (x) h_{g,q}) - beta_n B_0 with 1-D factors
-// h_{g,p}(u) = u^p exp(-u^2 / 2 sigma_g^2).
+// and I^T W I at once.  X_m = R (x) B'_m by direct 2-D convolution.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -138,16 +145,77 @@ __global__ void __launch_bounds__(256) basis_prepare_kernel(BasisDev b, double* 
         }
 }
 
+// Orthonormalise basis functions 1..nb-1 in pixel space (one CTA, FP64):
+// G = B^T B, G = L L^T, S = L^-T (upper triangular), B'_m = sum_n S[n][m] B_n.
+// imgf receives the FP32 images of B'_0 = B_0 and B'_m; S is stored [nb][nb]
+// with S[0][0] = 1.  work holds G / L ((nb-1)^2 doubles).
+__global__ void __launch_bounds__(1024) basis_ortho_kernel(BasisDev b, const double* img, float* imgf, double* S,
+                                                           double* work) {
+    const int nb = b.nb, m1 = nb - 1, kk = b.ks * b.ks, tid = threadIdx.x;
+    double* G = work;                       // [m1][m1], lower triangle becomes L
+    for (int e = tid; e < m1 * m1; e += blockDim.x) {
+        const int i = e / m1, j = e - i * m1;
+        if (j > i) continue;
+        const double* bi = img + (long)(i + 1) * kk;
+        const double* bj = img + (long)(j + 1) * kk;
+        double acc = 0.0;
+        for (int t = 0; t < kk; t++) acc += bi[t] * bj[t];
+        G[i * m1 + j] = acc;
+    }
+    __syncthreads();
+    // Cholesky (column by column, the column's rows in parallel)
+    for (int j = 0; j < m1; j++) {
+        if (tid == 0) {
+            double d = G[j * m1 + j];
+            for (int k = 0; k < j; k++) d -= G[j * m1 + k] * G[j * m1 + k];
+            G[j * m1 + j] = sqrt(d > 0.0 ? d : 1e-300);
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < m1; i += blockDim.x) {
+            double v = G[i * m1 + j];
+            for (int k = 0; k < j; k++) v -= G[i * m1 + k] * G[j * m1 + k];
+            G[i * m1 + j] = v / G[j * m1 + j];
+        }
+        __syncthreads();
+    }
+    // S = L^-T: column m of S solves L^T s = e_m (back substitution)
+    for (int e = tid; e < nb * nb; e += blockDim.x) S[e] = 0.0;
+    __syncthreads();
+    if (tid == 0) S[0] = 1.0;
+    for (int m = tid; m < m1; m += blockDim.x) {
+        for (int i = m; i >= 0; i--) {
+            double v = (i == m) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= m; k++) v -= G[k * m1 + i] * S[(k + 1) * nb + (m + 1)];
+            S[(i + 1) * nb + (m + 1)] = v / G[i * m1 + i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * kk; e += blockDim.x) {
+        const int m = e / kk, t = e - m * kk;
+        double v;
+        if (m == 0) {
+            v = img[t];
+        } else {
+            v = 0.0;
+            for (int n = 1; n <= m; n++) v += S[n * nb + m] * img[(long)n * kk + t];
+        }
+        imgf[e] = (float)v;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// K3: X_n on every stamp pixel, separably, one CTA per stamp.
-// X layout: X[(s * nb + n) * ss + pix], pix = j * stamp + i.
+// K3: X_m = R (x) B'_m on every stamp pixel by direct 2-D convolution, one CTA
+// per stamp.  The reference window and a group of basis images sit in shared
+// memory; each work item is 4 basis functions x 4 stamp pixels (16 FP32
+// accumulators).  X layout: X[(s * nb + m) * ss + pix], pix = j * stamp + i.
 __global__ void __launch_bounds__(256) stamp_conv_kernel(BasisDev b, const float* ref, long pitch, int w, int h,
                                                          const int* centers, const int* n_stamps, int stamp,
-                                                         const float* hrow, const float* ab, float* X) {
+                                                         const float* imgf, int group, float* X) {
     extern __shared__ __align__(16) float sm[];
     const int s = blockIdx.x;
     if (s >= *n_stamps) return;
-    const int ks = b.ks, r = b.r, hs = stamp / 2, WW = stamp + 2 * r, ss = stamp * stamp, nb = b.nb;
+    const int ks = b.ks, r = b.r, kk = ks * ks, hs = stamp / 2, WW = stamp + 2 * r, ss = stamp * stamp;
+    const int nb = b.nb;
     const int xs = centers[2 * s], ys = centers[2 * s + 1];
     float* Xs = X + (long)s * nb * ss;
     const bool valid = xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1;
@@ -155,51 +223,63 @@ __global__ void __launch_bounds__(256) stamp_conv_kernel(BasisDev b, const float
         for (int e = threadIdx.x; e < nb * ss; e += blockDim.x) Xs[e] = 0.0f;
         return;
     }
-    float* Rw = sm;                        // [WW][WW]
-    float* H = Rw + WW * WW;               // [NH][WW][stamp]
-    float* ht = H + b.NH * WW * stamp;     // [NH][ks]
-    float* X0 = ht + b.NH * ks;            // [ss]
+    float* Rw = sm;                  // [WW][WW]
+    float* Bs = Rw + WW * WW;        // [group][kk]
     const int wx0 = xs - hs - r, wy0 = ys - hs - r;
     for (int e = threadIdx.x; e < WW * WW; e += blockDim.x) {
         const int wj = e / WW, wi = e - wj * WW;
         Rw[e] = __ldg(ref + (long)(wy0 + wj) * pitch + wx0 + wi);
     }
-    for (int e = threadIdx.x; e < b.NH * ks; e += blockDim.x) ht[e] = hrow[e];
-    __syncthreads();
-    const int nh = b.NH * WW * stamp;
-    for (int e = threadIdx.x; e < nh; e += blockDim.x) {
-        const int t = e / (WW * stamp), rem = e - t * WW * stamp;
-        const int wj = rem / stamp, i = rem - wj * stamp;
-        const float* rr = Rw + wj * WW + i + 2 * r;
-        const float* hh = ht + t * ks;
-        float acc = 0.0f;
-        for (int iu = 0; iu < ks; iu++) acc = fmaf(hh[iu], rr[-iu], acc);
-        H[e] = acc;
-    }
-    __syncthreads();
-    {
-        const int tp = b.hoff[0], tq = b.hoff[0];
-        const float a0 = ab[0];
-        for (int e = threadIdx.x; e < ss; e += blockDim.x) {
-            const int j = e / stamp, i = e - j * stamp;
-            const float* hq = ht + tq * ks;
-            const float* hp = H + (long)tp * WW * stamp + (j + 2 * r) * stamp + i;
-            float acc = 0.0f;
-            for (int iv = 0; iv < ks; iv++) acc = fmaf(hq[iv], hp[-iv * stamp], acc);
-            X0[e] = a0 * acc;
-            Xs[e] = a0 * acc;
+    const int npq = (ss + 3) / 4;
+    for (int g0 = 0; g0 < nb; g0 += group) {
+        const int gn = min(group, nb - g0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < gn * kk; e += blockDim.x) Bs[e] = __ldg(imgf + (long)g0 * kk + e);
+        __syncthreads();
+        const int nfq = (gn + 3) / 4;
+        for (int item = threadIdx.x; item < nfq * npq; item += blockDim.x) {
+            const int fq = item / npq, pq = item - fq * npq;
+            int off[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int pix = min(pq * 4 + t, ss - 1);
+                const int j = pix / stamp, i = pix - j * stamp;
+                off[t] = (j + 2 * r) * WW + (i + 2 * r);   // window index of R(x, y) + (2r, 2r) shift
+            }
+            const float* bf[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) bf[q] = Bs + (long)min(fq * 4 + q, gn - 1) * kk;
+            float acc[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+#pragma unroll
+                for (int t = 0; t < 4; t++) acc[q][t] = 0.0f;
+            // tap (du, dv) = (iu - r, iv - r): R(x - du, y - dv) = Rw[(j + 2r - iv) * WW + (i + 2r - iu)]
+            for (int iv = 0; iv < ks; iv++) {
+                for (int iu = 0; iu < ks; iu++) {
+                    const int tap = iv * ks + iu, sh = iv * WW + iu;
+                    float rv[4], bv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) rv[t] = Rw[off[t] - sh];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) bv[q] = bf[q][tap];
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+#pragma unroll
+                        for (int t = 0; t < 4; t++) acc[q][t] = fmaf(bv[q], rv[t], acc[q][t]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int m = g0 + fq * 4 + q;
+                if (fq * 4 + q >= gn) break;
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int pix = pq * 4 + t;
+                    if (pix < ss) Xs[(long)m * ss + pix] = acc[q][t];
+                }
+            }
         }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < (nb - 1) * ss; e += blockDim.x) {
-        const int n = 1 + e / ss, pix = e - (n - 1) * ss;
-        const int j = pix / stamp, i = pix - j * stamp;
-        const int g = b.g[n];
-        const float* hq = ht + (b.hoff[g] + b.q[n]) * ks;
-        const float* hp = H + (long)(b.hoff[g] + b.p[n]) * WW * stamp + (j + 2 * r) * stamp + i;
-        float acc = 0.0f;
-        for (int iv = 0; iv < ks; iv++) acc = fmaf(hq[iv], hp[-iv * stamp], acc);
-        Xs[(long)n * ss + pix] = ab[2 * n] * acc - ab[2 * n + 1] * X0[pix];
     }
 }
 
@@ -305,13 +385,20 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(GramArgs g, int ntile) {
     }
     const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
     const long nchunks = (nrows + GK - 1) / GK;
-    float acc[4][4];
+    // per 32-row chunk the products are summed in FP32 (acc), then folded into a
+    // double-float accumulator (hi, lo) with an error-free two-sum
+    float hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
+        for (int j = 0; j < 4; j++) hi[i][j] = lo[i][j] = 0.0f;
     const int ty = tid / 16, tx = tid % 16;
     for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] = 0.0f;
         const long rho0 = ch * GK;
         __syncthreads();
         if (tid < GK) row_meta(g, rho0 + tid, nrows, meta[tid]);
@@ -345,8 +432,19 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(GramArgs g, int ntile) {
 #pragma unroll
                 for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float a = hi[i][j], b = acc[i][j];
+                const float sum = a + b;
+                const float bp = sum - a;
+                lo[i][j] += (a - (sum - bp)) + (b - bp);
+                hi[i][j] = sum;
+            }
     }
     float* out = g.part + (long)blockIdx.x * g.NP * g.NP;
+    float* outl = g.part + (long)(blockIdx.x + gridDim.x) * g.NP * g.NP;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int row = ti * GT + ty * 4 + i;
@@ -354,7 +452,10 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(GramArgs g, int ntile) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int col = tj * GT + tx * 4 + j;
-            if (col < g.NP) out[(long)row * g.NP + col] = acc[i][j];
+            if (col < g.NP) {
+                out[(long)row * g.NP + col] = hi[i][j];
+                outl[(long)row * g.NP + col] = lo[i][j];
+            }
         }
     }
 }
@@ -585,7 +686,7 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* M, int ld,
 __global__ void __launch_bounds__(1024) chol_solve_kernel(const double* L, int ld, int n, const double* rhs,
                                                           int rs, double* x, const double* flag) {
     extern __shared__ double y[];
-    if (flag[0] != 0.0) return;
+    if (flag[0] != 0.0 || flag[1] != 0.0) return;
     const int tid = threadIdx.x;
     for (int i = tid; i < n; i += blockDim.x) y[i] = rhs[(long)i * rs];
     __syncthreads();
@@ -614,7 +715,7 @@ __global__ void __launch_bounds__(256) resid_kernel(GramArgs g, const double* a,
     extern __shared__ __align__(16) double rsm[];   // [8 warps][NP] accumulators
     __shared__ float af[1024];
     __shared__ double wchi[8], wn[8];
-    if (flag[0] != 0.0) return;
+    if (flag[0] != 0.0 || (want_r && flag[1] != 0.0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = tid; j < g.Nc; j += blockDim.x) af[j] = (float)a[j];
     for (int j = tid; j < 8 * g.NP; j += blockDim.x) rsm[j] = 0.0;
@@ -686,8 +787,8 @@ __global__ void __launch_bounds__(256) resid_kernel(GramArgs g, const double* a,
 }
 
 __global__ void resid_reduce_kernel(const double* part, int nparts, int NP, int Nc, double* r, double* chi_n,
-                                    const double* flag) {
-    if (flag[0] != 0.0) return;
+                                    const double* flag, int skip_if_done) {
+    if (flag[0] != 0.0 || (skip_if_done && flag[1] != 0.0)) return;
     for (int j = threadIdx.x; j < Nc + 2; j += blockDim.x) {
         const int col = j < Nc ? j : NP + (j - Nc);
         double s = 0.0;
@@ -697,50 +798,78 @@ __global__ void resid_reduce_kernel(const double* part, int nparts, int NP, int 
     }
 }
 
-__global__ void update_kernel(const double* a0, const double* delta, double* a, int Nc, double* work,
-                              const double* flag) {
+// Refinement state, flag[]: [0] singular, [1] done, [2] previous step, [3] steps
+// applied, [4] last applied step.  A step delta (relative max-norm) is applied
+// unless it is larger than the previous one (the iteration diverges: keep the
+// current iterate and stop); the loop also stops once a step is below 1e-12.
+__global__ void refine_update_kernel(double* a, const double* delta, int Nc, double* flag) {
     __shared__ double mx[2];
-    if (flag[0] != 0.0) return;
-    if (threadIdx.x == 0) { mx[0] = 0.0; mx[1] = 0.0; }
-    __syncthreads();
-    for (int j = threadIdx.x; j < Nc; j += blockDim.x) a[j] = a0[j] + delta[j];
-    __syncthreads();
+    if (flag[0] != 0.0 || flag[1] != 0.0) return;
     if (threadIdx.x == 0) {
         double ms = 0.0, ma = 0.0;
         for (int j = 0; j < Nc; j++) {
             ms = fmax(ms, fabs(delta[j]));
             ma = fmax(ma, fabs(a[j]));
         }
-        work[0] = ma > 0.0 ? ms / ma : 0.0;
+        const double step = ma > 0.0 ? ms / ma : ms;
+        mx[0] = step;
+        mx[1] = (flag[3] > 0.0 && !(step <= flag[2])) ? 1.0 : 0.0;   // diverging (or NaN)
+    }
+    __syncthreads();
+    if (mx[1] != 0.0) {
+        if (threadIdx.x == 0) flag[1] = 1.0;
+        return;
+    }
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) a[j] += delta[j];
+    if (threadIdx.x == 0) {
+        flag[2] = mx[0];
+        flag[3] += 1.0;
+        flag[4] = mx[0];
+        if (mx[0] < 1e-12) flag[1] = 1.0;
     }
 }
 
-__global__ void finalize_kernel(const double* a, int Nc, const double* chi_a0, const double* chi_a,
-                                const double* work, const double* flag, int n_stamps_max, const int* n_stamps,
-                                const int* centers, int stamp, int r, int w, int h, int prec, double* coeffs,
+// Map the solution c of the orthonormalised basis back to Alard-Lupton
+// coefficients (a_{n,k} = sum_m S[n][m] c_{m,k}, FP64) and write the stats.
+__global__ void finalize_kernel(BasisDev b, const double* c, const double* S, const double* flag,
+                                const double* chi_a0, const double* chi_a, int n_stamps_max, const int* n_stamps,
+                                const int* centers, int stamp, int w, int h, int prec, double* coeffs,
                                 argus_fit_stats* st) {
+    const bool bad = flag[0] != 0.0;
+    const int nb = b.nb, Ks = b.Ks, Nc = b.Nc;
     if (threadIdx.x == 0) {
         argus_fit_stats s;
-        const bool bad = flag[0] != 0.0;
         s.chi2 = bad ? 0.0 : chi_a[0];
         s.chi2_a0 = bad ? 0.0 : chi_a0[0];
-        s.max_step = bad ? 0.0 : work[0];
+        s.max_step = bad ? 0.0 : flag[4];
         s.n_pix = bad ? 0 : (long long)chi_a[1];
         s.dof = s.n_pix - Nc;
         s.n_coeffs = Nc;
         s.status = bad ? ARGUS_ERR_SINGULAR : ARGUS_OK;
         int used = 0;
-        const int hs = stamp / 2, ns = min(*n_stamps, n_stamps_max);
+        const int hs = stamp / 2, r = b.r, ns = min(*n_stamps, n_stamps_max);
         for (int i = 0; i < ns; i++) {
             const int xs = centers[2 * i], ys = centers[2 * i + 1];
             used += (xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1);
         }
         s.n_stamps_used = used;
         s.precision = prec;
+        s.refine_iters = bad ? 0 : (int)flag[3];
+        s.pad_ = 0;
         *st = s;
     }
-    if (flag[0] != 0.0) return;
-    for (int j = threadIdx.x; j < Nc; j += blockDim.x) coeffs[j] = a[j];
+    if (bad) return;
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+        double v;
+        if (j == 0 || j >= 1 + (nb - 1) * Ks) {
+            v = c[j];
+        } else {
+            const int n = 1 + (j - 1) / Ks, k = (j - 1) % Ks;
+            v = 0.0;
+            for (int m = n; m < nb; m++) v += S[n * nb + m] * c[1 + (m - 1) * Ks + k];
+        }
+        coeffs[j] = v;
+    }
 }
 
 // a7: K_k(u,v) = sum_n a_{n,k} B_n(u,v) (K_0 also a_0 B_0); bg_k.
@@ -870,7 +999,8 @@ int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st) {
     for (int g = 0; g < b->ngauss; g++) { key.sigma[g] = b->sigma[g]; key.degree[g] = b->degree[g]; }
     key.spatial_degree = b->spatial_degree; key.bg_degree = b->bg_degree;
     if (ctx->basis_memo_valid && same_basis(ctx->basis_memo, key)) return ARGUS_OK;
-    basis_prepare_kernel<<<d.nb, 256, 0, st>>>(d, ctx->basis_img, ctx->basis_imgf, ctx->basis_h, ctx->basis_ab);
+    basis_prepare_kernel<<<d.nb, 256, 0, st>>>(d, ctx->basis_img, ctx->basis_imgf, ctx->basis_h, ctx->basis_ab); argus_count_launch(1);
+    basis_ortho_kernel<<<1, 1024, 0, st>>>(d, ctx->basis_img, ctx->basis_imgf, ctx->basis_S, ctx->L); argus_count_launch(1);
     rc = argus_launch_status();
     if (rc == ARGUS_OK) {
         ctx->basis_memo = key;
@@ -878,6 +1008,10 @@ int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st) {
     }
     return rc;
 }
+
+// Steps of iterative refinement launched after the first solve (each is a
+// no-op once the iteration has converged or started to diverge).
+constexpr int REFINE_MAX = 3;
 
 extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
                                 const uint8_t* flags, argus_shape shape, const int* centers,
@@ -899,32 +1033,37 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     rc = argus_basis_prepare(ctx, basis, st);
     if (rc) return rc;
 
-    const int ss = stamp * stamp, WW = stamp + 2 * d.r;
-    const size_t conv_smem = sizeof(float) * ((size_t)WW * WW + (size_t)d.NH * WW * stamp + (size_t)d.NH * d.ks + ss);
-    if (conv_smem > 200 * 1024) return ARGUS_ERR_UNSUPPORTED;
+    const int ss = stamp * stamp, WW = stamp + 2 * d.r, kk = d.ks * d.ks;
+    int group = (int)((200 * 1024 / sizeof(float) - (size_t)WW * WW) / kk);
+    if (group > d.nb) group = d.nb;
+    if (group < 4) return ARGUS_ERR_UNSUPPORTED;
+    const size_t conv_smem = sizeof(float) * ((size_t)WW * WW + (size_t)group * kk);
     cudaFuncSetAttribute(stamp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
     stamp_conv_kernel<<<max_stamps, 256, conv_smem, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers, n_stamps,
-                                                          stamp, ctx->basis_h, ctx->basis_ab, ctx->X);
+                                                          stamp, ctx->basis_imgf, group, ctx->X); argus_count_launch(1);
     if ((rc = argus_launch_status())) return rc;
 
     GramArgs g;
     g.X = ctx->X; g.sci = sci; g.var = sci_var; g.flags = flags; g.centers = centers; g.n_stamps = n_stamps;
     g.pitch = shape.pitch; g.w = shape.w; g.h = shape.h; g.W = shape.w; g.H = shape.h;
-    g.stamp = stamp; g.ss = ss; g.r = d.r; g.max_stamps = max_stamps; g.nb = d.nb; g.Ks = d.Ks; g.Kb = d.Kb; g.Nc = d.Nc;
+    g.stamp = stamp; g.ss = ss; g.r = d.r; g.max_stamps = max_stamps; g.nb = d.nb; g.Ks = d.Ks; g.Kb = d.Kb;
+    g.Nc = d.Nc;
     g.NP = argus_round_up(d.Nc + 1, 16);
     g.sdeg = d.sdeg; g.bgdeg = d.bgdeg; g.part = ctx->gram_part; g.status = ctx->d_status;
 
     const long max_rows = (long)max_stamps * ss;
+    int part_slots;
     if (precision == ARGUS_PREC_FP32) {
         const int ntile = (g.NP + GT - 1) / GT;
         const int npair = ntile * (ntile + 1) / 2;
         int nslots = ctx->num_sms * 2 / npair;
         if (nslots < 1) nslots = 1;
-        if (nslots > ctx->gram_parts) nslots = ctx->gram_parts;
+        if (nslots > ctx->gram_parts / 2) nslots = ctx->gram_parts / 2;
         const long nch = (max_rows + GK - 1) / GK;
         if (nslots > nch) nslots = (int)nch;
         g.nslots = nslots;
-        gram_simt_kernel<<<dim3(nslots, npair), 256, 0, st>>>(g, ntile);
+        part_slots = 2 * nslots;   // hi and lo halves of the double-float partials
+        gram_simt_kernel<<<dim3(nslots, npair), 256, 0, st>>>(g, ntile); argus_count_launch(1);
     } else {
         const int RB = (g.NP + 127) / 128;
         const int NR = RB * 128;
@@ -934,6 +1073,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         const long nch = (max_rows + TC_KC - 1) / TC_KC;
         if (nslots > nch) nslots = (int)nch;
         g.nslots = nslots;
+        part_slots = nslots;
         const int esz = precision == ARGUS_PREC_BF16 ? 2 : 4;
         size_t smem = 2 * (size_t)NR * TC_KC * esz + sizeof(float) * (TC_KC * META + ARGUS_MAX_NB * TC_KC) +
                       sizeof(int) * (2 * NR + 2) + 64;
@@ -941,37 +1081,42 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
         if (precision == ARGUS_PREC_BF16) {
             cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, NR);
+            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, NR); argus_count_launch(1);
         } else {
             cudaFuncSetAttribute(gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, NR);
+            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, NR); argus_count_launch(1);
         }
     }
     if ((rc = argus_launch_status())) return rc;
     const int NP = g.NP;
-    gram_reduce_kernel<<<ctx->num_sms, 256, 0, st>>>(ctx->gram_part, g.nslots, NP, ctx->M);
+    gram_reduce_kernel<<<ctx->num_sms, 256, 0, st>>>(ctx->gram_part, part_slots, NP, ctx->M); argus_count_launch(1);
 
-    double* flag = ctx->vec + 7 * (size_t)ctx->np_cols;
-    double* a0 = ctx->vec + 1 * (size_t)ctx->np_cols;
-    double* rv = ctx->vec + 2 * (size_t)ctx->np_cols;
-    double* dl = ctx->vec + 3 * (size_t)ctx->np_cols;
-    double* a = ctx->vec + 4 * (size_t)ctx->np_cols;
-    double* work = ctx->vec + 5 * (size_t)ctx->np_cols;   // [0] max step, [2..3] chi/n (a0), [4..5] chi/n (a)
-    cholesky_kernel<<<1, 1024, 0, st>>>(ctx->M, NP, d.Nc, ctx->L, flag, ctx->d_status);
+    const size_t ld = (size_t)ctx->np_cols;
+    double* c = ctx->vec + 1 * ld;      // current solution (orthonormal basis)
+    double* rv = ctx->vec + 2 * ld;     // residual C^T W (I - C c)
+    double* dl = ctx->vec + 3 * ld;     // correction
+    double* chi0 = ctx->vec + 5 * ld;   // chi2, n of the first iterate
+    double* chiw = ctx->vec + 5 * ld + 2;
+    double* chif = ctx->vec + 5 * ld + 4;
+    double* flag = ctx->vec + 7 * ld;   // refinement state
+    if (cudaMemsetAsync(flag, 0, 8 * sizeof(double), st) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cholesky_kernel<<<1, 1024, 0, st>>>(ctx->M, NP, d.Nc, ctx->L, flag, ctx->d_status); argus_count_launch(1);
     const size_t solve_smem = sizeof(double) * NP;
-    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, ctx->M + d.Nc, NP, a0, flag);
+    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, ctx->M + d.Nc, NP, c, flag); argus_count_launch(1);
     int nparts = ctx->num_sms * 2;
     if (nparts > ctx->resid_parts) nparts = ctx->resid_parts;
     const size_t rsmem = sizeof(double) * 8 * NP;
     cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
-    resid_kernel<<<nparts, 256, rsmem, st>>>(g, a0, flag, 1, ctx->resid_part);
-    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, d.Nc, rv, work + 2, flag);
-    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, rv, 1, dl, flag);
-    update_kernel<<<1, 256, 0, st>>>(a0, dl, a, d.Nc, work, flag);
-    resid_kernel<<<nparts, 256, rsmem, st>>>(g, a, flag, 0, ctx->resid_part);
-    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, work + 4, flag);
-    finalize_kernel<<<1, 256, 0, st>>>(a, d.Nc, work + 2, work + 4, work, flag, max_stamps, n_stamps, centers,
-                                       stamp, d.r, shape.w, shape.h, precision, coeffs, stats);
+    for (int it = 0; it < REFINE_MAX; it++) {
+        resid_kernel<<<nparts, 256, rsmem, st>>>(g, c, flag, 1, ctx->resid_part); argus_count_launch(1);
+        resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, d.Nc, rv, it == 0 ? chi0 : chiw, flag, 1); argus_count_launch(1);
+        chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, rv, 1, dl, flag); argus_count_launch(1);
+        refine_update_kernel<<<1, 256, 0, st>>>(c, dl, d.Nc, flag); argus_count_launch(1);
+    }
+    resid_kernel<<<nparts, 256, rsmem, st>>>(g, c, flag, 0, ctx->resid_part); argus_count_launch(1);
+    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, chif, flag, 0); argus_count_launch(1);
+    finalize_kernel<<<1, 256, 0, st>>>(d, c, ctx->basis_S, flag, chi0, chif, max_stamps, n_stamps, centers, stamp,
+                                       shape.w, shape.h, precision, coeffs, stats); argus_count_launch(1);
     return argus_launch_status();
 }
 
@@ -984,7 +1129,7 @@ extern "C" int argus_expand_kernel(argus_ctx* ctx, const argus_basis* basis, con
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = argus_basis_prepare(ctx, basis, st))) return rc;
-    expand_kernel<<<d.Ks, 256, 0, st>>>(d, ctx->basis_img, coeffs, K, bg);
+    expand_kernel<<<d.Ks, 256, 0, st>>>(d, ctx->basis_img, coeffs, K, bg); argus_count_launch(1);
     return argus_launch_status();
 }
 
@@ -1007,7 +1152,7 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     long blocks = (np + 255) / 256;
     if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
     select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x, grid_y,
-                                                    stamp / 2 + khalf, max_peak, iso, iso_frac, ctx->cell_key);
-    select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps);
+                                                    stamp / 2 + khalf, max_peak, iso, iso_frac, ctx->cell_key); argus_count_launch(1);
+    select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps); argus_count_launch(1);
     return argus_launch_status();
 }

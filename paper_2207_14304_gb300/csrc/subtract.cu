@@ -204,7 +204,7 @@ int launch(const SubArgs& a, cudaStream_t st) {
     const size_t smem = sizeof(float) * (2 * SW * SW + KTSZ + KS * KSP);
     cudaFuncSetAttribute(subtract_kernel<KS, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((a.w + TILE - 1) / TILE, (a.h + TILE - 1) / TILE);
-    subtract_kernel<KS, NK><<<grid, THREADS, smem, st>>>(a);
+    subtract_kernel<KS, NK><<<grid, THREADS, smem, st>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }
 

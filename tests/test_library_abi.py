@@ -37,7 +37,7 @@ def test_status_strings_and_struct_sizes():
     assert B.status_string(0) == "ok"
     assert "positive definite" in B.status_string(-5)
     assert C.sizeof(B.argus_source) == 36
-    assert C.sizeof(B.argus_fit_stats) == 56
+    assert C.sizeof(B.argus_fit_stats) == 64
     assert C.sizeof(B.argus_shape) == 16
 
 
