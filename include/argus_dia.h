@@ -222,6 +222,26 @@ int argus_detect(argus_ctx *ctx, const float *diff, const float *diff_var, const
                  argus_shape shape, float nsigma, float psf_sigma, uint8_t *mask,
                  argus_source *out, int cap, int *n_found, argus_stream stream);
 
+/* Stamp selection that allocates nothing, for callers that cannot call
+ * cudaMalloc (a host that reserves all device memory up front, a real-time
+ * loop that must never enter an allocator, or a plugin that is only handed
+ * input and output pointers).  The paper has no counterpart: this is a
+ * deployment variant of argus_select_stamps with the same arguments minus the
+ * context and the same results.  Its scratch (one 64-bit key per grid cell)
+ * is a fixed 32 KiB device array inside the library that every GPU loading the
+ * library keeps until the process exits; grid_x * grid_y above
+ * ARGUS_NOALLOC_MAX_CELLS (4096) returns ARGUS_ERR_CAPACITY.  Runs on the
+ * current device.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race
+ * and must be serialised by the caller; each call clears the part it uses.
+ * ref, flags: device, [h][pitch]; centers: device int [grid_x*grid_y][2];
+ * n_stamps: device int. */
+#define ARGUS_NOALLOC_MAX_CELLS 4096
+int argus_select_stamps_noalloc(const float *ref, const uint8_t *flags, argus_shape shape, int grid_x,
+                                int grid_y, int stamp, int khalf, float max_peak, int iso, float iso_frac,
+                                int *centers, int *n_stamps, argus_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

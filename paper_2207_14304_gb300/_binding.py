@@ -88,6 +88,7 @@ SIGNATURES = {
     "argus_expand_kernel": ([P, C.POINTER(argus_basis), P, P, P, P], I),
     "argus_subtract": ([P, P, P, P, P, P, SH, I, I, I, I, I, I, P, I, P, P, P, P], I),
     "argus_detect": ([P, P, P, P, SH, F, F, P, P, I, P, P], I),
+    "argus_select_stamps_noalloc": ([P, P, SH, I, I, I, I, F, I, F, P, P, P], I),
 }
 
 
@@ -222,6 +223,15 @@ def argus_select_stamps(ctx, ref, flags, shape, grid_x, grid_y, stamp, khalf, ma
                                       int(stamp), int(khalf), float(max_peak), int(iso),
                                       float(iso_frac), _ptr(centers), _ptr(n_stamps),
                                       _stream(stream)), "argus_select_stamps")
+
+
+def argus_select_stamps_noalloc(ref, flags, shape, grid_x, grid_y, stamp, khalf, max_peak, iso,
+                                iso_frac, centers, n_stamps, stream=None):
+    """Context-free stamp selection for callers that cannot allocate device memory."""
+    _check(load().argus_select_stamps_noalloc(_ptr(ref), _ptr(flags), shape, int(grid_x), int(grid_y),
+                                              int(stamp), int(khalf), float(max_peak), int(iso),
+                                              float(iso_frac), _ptr(centers), _ptr(n_stamps),
+                                              _stream(stream)), "argus_select_stamps_noalloc")
 
 
 def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "argus_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -1154,5 +1156,71 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x, grid_y,
                                                     stamp / 2 + khalf, max_peak, iso, iso_frac, ctx->cell_key); argus_count_launch(1);
     select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps); argus_count_launch(1);
+    return argus_launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Stamp selection without a context, for callers that cannot allocate device
+// memory: code running where cudaMalloc is not allowed or not wanted (a host
+// that pre-reserves all GPU memory up front, a real-time loop that must never
+// enter the allocator, or a plugin handed only input and output pointers by
+// its host application).  It runs the same two kernels as
+// argus_select_stamps; their scratch -- one 64-bit key per grid cell -- lives
+// in the file-scope device array below instead of a context.
+//
+// The array is part of the library image: every GPU that loads the library
+// holds these 32 KiB until the process exits.  Host code cannot use the
+// symbol's name as a device address, so the address is looked up once per
+// device with cudaGetSymbolAddress, under a lock, with that device current.
+// That lookup happens on the first call on a device; make that first call
+// before any stream capture.  All calls share the array and it keeps the last
+// call's contents, so each call clears the keys it uses first; calls that
+// overlap on the GPU (different streams, or different host threads) race on
+// it and must be serialised by the caller.
+static __device__ __align__(256) unsigned long long g_select_scratch[ARGUS_NOALLOC_MAX_CELLS];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64];
+int g_noalloc_sms[64];
+}  // namespace
+
+extern "C" int argus_select_stamps_noalloc(const float* ref, const uint8_t* flags, argus_shape shape,
+                                           int grid_x, int grid_y, int stamp, int khalf, float max_peak,
+                                           int iso, float iso_frac, int* centers, int* n_stamps,
+                                           argus_stream stream) {
+    if (!ref || !flags || !centers || !n_stamps) return ARGUS_ERR_ARG;
+    if (grid_x < 1 || grid_y < 1 || stamp < 1 || khalf < 0 || iso < 0 || iso > 64) return ARGUS_ERR_ARG;
+    if ((long)grid_x * grid_y > ARGUS_NOALLOC_MAX_CELLS) return ARGUS_ERR_CAPACITY;
+    if (shape.w <= 0 || shape.h <= 0 || shape.pitch < shape.w) return ARGUS_ERR_ARG;
+    if (shape.pitch % 16) return ARGUS_ERR_ALIGN;
+    if (argus_check_ptr16(ref) || argus_check_ptr16(flags)) return ARGUS_ERR_ALIGN;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ARGUS_ERR_CUDA;
+    void* scratch = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_select_scratch) != cudaSuccess || !p) return ARGUS_ERR_CUDA;
+            int n = 0;
+            if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ARGUS_ERR_CUDA;
+            g_noalloc_sms[dev] = n;
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+    unsigned long long* keys = static_cast<unsigned long long*>(scratch);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ncell = grid_x * grid_y;
+    if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * ncell, st) != cudaSuccess) return ARGUS_ERR_CUDA;
+    const long np = (long)shape.w * shape.h;
+    long blocks = (np + 255) / 256;
+    if (blocks > (long)sms * 16) blocks = (long)sms * 16;
+    select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x, grid_y,
+                                                    stamp / 2 + khalf, max_peak, iso, iso_frac, keys); argus_count_launch(1);
+    select_compact_kernel<<<1, 1024, 0, st>>>(keys, ncell, shape.w, centers, n_stamps); argus_count_launch(1);
     return argus_launch_status();
 }
