@@ -38,6 +38,8 @@ struct argus_ctx {
     float* gram_part;    // [gram_parts][np_cols][np_cols]
     double* M;           // [np_cols][np_cols] reduced normal matrix (+ target column)
     double* L;           // [np_cols][np_cols] Cholesky factor
+    double* Linv;        // [np_cols][np_cols] its inverse
+    double* Dinv;        // [32][32] inverse of the current diagonal block
     double* vec;         // [8][np_cols] b, a0, r, delta, a, work
     int resid_parts;
     double* resid_part;  // [resid_parts][np_cols + 2]
@@ -72,6 +74,8 @@ void argus_count_launch(int n);   // host-side tally of kernel launches
 
 // Inter-unit launchers
 int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st);
+int argus_cholesky_solve_prepare(argus_ctx* ctx, const double* M, int ld, int n, cudaStream_t st);
+void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, double* x, cudaStream_t st);
 int argus_basis_count(const argus_basis* b);
 int argus_nterms(int deg);
 

@@ -649,123 +649,247 @@ __global__ void gram_reduce_kernel(const float* part, int nslots, int NP, double
 }
 
 // ---------------------------------------------------------------------------
-// K5: FP64 Cholesky of M[0:n, 0:n] (leading dimension ld), one CTA.
-// flag[0] != 0 marks a failed factorisation for the kernels that follow.
-__global__ void __launch_bounds__(1024) cholesky_kernel(const double* M, int ld, int n, double* L, double* flag,
-                                                        int* status) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (long e = tid; e < (long)n * ld; e += blockDim.x) {
+// K5: FP64 linear algebra of the normal equations.
+//
+// Blocked right-looking Cholesky with 32-column panels, three launches per
+// panel (no grid-wide waits): the diagonal block is factored and inverted by
+// one CTA in shared memory; the panel below is L_ip = A_ip L_pp^-T (one warp
+// per row); the trailing lower triangle is updated in 16x16 tiles spread over
+// all SMs.  FP64 on this part runs at a fraction of the FP32 rate, so the work
+// is spread over the whole GPU instead of one SM.  L^-1 is then formed
+// explicitly (one warp per column) and every solve is two FP64 GEMVs.
+// flag[0] != 0 marks a failed factorisation for all kernels that follow.
+constexpr int CB = 32;
+
+__global__ void chol_init_kernel(const double* M, int ld, int n, double* L, double* flag) {
+    const long tot = (long)n * ld;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
         const int i = (int)(e / ld), j = (int)(e - (long)i * ld);
         L[e] = (j <= i && j < n) ? M[(long)i * ld + j] : 0.0;
     }
-    if (tid == 0) flag[0] = 0.0;
-    __syncthreads();
-    for (int j = 0; j < n; j++) {
-        const double d = L[(long)j * ld + j];
-        if (!(d > 0.0)) {
-            if (tid == 0) {
-                flag[0] = 1.0;
-                argus_latch(status, ARGUS_ERR_SINGULAR);
-            }
-            return;
-        }
-        const double ljj = sqrt(d);
-        __syncthreads();
-        if (tid == 0) L[(long)j * ld + j] = ljj;
-        const double inv = 1.0 / ljj;
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[(long)i * ld + j] *= inv;
-        __syncthreads();
-        for (int i = j + 1 + warp; i < n; i += nw) {
-            const double lij = L[(long)i * ld + j];
-            double* Li = L + (long)i * ld;
-            for (int k = j + 1 + lane; k <= i; k += 32) Li[k] -= lij * L[(long)k * ld + j];
-        }
-        __syncthreads();
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag[0] = 0.0;
 }
 
-// Solve L L^T x = rhs (rhs read with stride rs), one CTA.  Skips if flag set.
-__global__ void __launch_bounds__(1024) chol_solve_kernel(const double* L, int ld, int n, const double* rhs,
-                                                          int rs, double* x, const double* flag) {
-    extern __shared__ double y[];
-    if (flag[0] != 0.0 || flag[1] != 0.0) return;
+// Factor the pb x pb diagonal block at (p, p) and write its inverse to Dinv (CB x CB).
+__global__ void __launch_bounds__(256) chol_diag_kernel(double* L, int ld, int p, int pb, double* Dinv, double* flag,
+                                                        int* status) {
+    __shared__ double A[CB][CB + 1];
+    __shared__ double Ai[CB][CB + 1];
+    __shared__ int bad;
+    if (flag[0] != 0.0) return;
     const int tid = threadIdx.x;
-    for (int i = tid; i < n; i += blockDim.x) y[i] = rhs[(long)i * rs];
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        A[i][j] = (i < pb && j <= i) ? L[(long)(p + i) * ld + p + j] : 0.0;
+        Ai[i][j] = 0.0;
+    }
     __syncthreads();
-    for (int j = 0; j < n; j++) {
-        const double yj = y[j] / L[(long)j * ld + j];
+    for (int j = 0; j < pb; j++) {
+        if (tid == 0) {
+            const double d = A[j][j];
+            if (!(d > 0.0)) bad = 1;
+            A[j][j] = sqrt(d > 0.0 ? d : 1.0);
+        }
         __syncthreads();
-        for (int i = j + 1 + tid; i < n; i += blockDim.x) y[i] -= L[(long)i * ld + j] * yj;
-        if (tid == 0) y[j] = yj;
+        if (bad) break;
+        for (int i = j + 1 + tid; i < pb; i += blockDim.x) A[i][j] /= A[j][j];
+        __syncthreads();
+        for (int e = tid; e < CB * CB; e += blockDim.x) {
+            const int i = e / CB, k = e % CB;
+            if (i > j && k > j && k <= i && i < pb) A[i][k] -= A[i][j] * A[k][j];
+        }
         __syncthreads();
     }
-    for (int j = n - 1; j >= 0; j--) {
-        const double xj = y[j] / L[(long)j * ld + j];
-        __syncthreads();
-        for (int i = tid; i < j; i += blockDim.x) y[i] -= L[(long)j * ld + i] * xj;
-        if (tid == 0) y[j] = xj;
-        __syncthreads();
+    if (bad) {
+        if (tid == 0) {
+            flag[0] = 1.0;
+            argus_latch(status, ARGUS_ERR_SINGULAR);
+        }
+        return;
     }
-    for (int i = tid; i < n; i += blockDim.x) x[i] = y[i];
+    // inverse of the lower-triangular block: column c by forward substitution
+    if (tid < pb) {
+        const int c = tid;
+        for (int i = c; i < pb; i++) {
+            double v = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; k++) v -= A[i][k] * Ai[k][c];
+            Ai[i][c] = v / A[i][i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < CB * CB; e += blockDim.x) {
+        const int i = e / CB, j = e % CB;
+        if (i < pb && j <= i) L[(long)(p + i) * ld + p + j] = A[i][j];
+        Dinv[e] = (i < pb && j < pb) ? Ai[i][j] : 0.0;
+    }
 }
 
-// Residual pass over all design rows with coefficients a (FP64 in, FP32 model):
-// e = I - c.a; per CTA partial sums of r_j = sum w e c_j (if want_r), chi2 = sum w e^2
-// and the count of weighted rows, in FP64 with a fixed reduction order.
-__global__ void __launch_bounds__(256) resid_kernel(GramArgs g, const double* a, const double* flag, int want_r,
-                                                    double* part) {
-    extern __shared__ __align__(16) double rsm[];   // [8 warps][NP] accumulators
+// L[i, p:p+pb] = A[i, p:p+pb] * Dinv^T for rows i in [p+pb, n): one warp per row.
+__global__ void chol_panel_kernel(double* L, int ld, int n, int p, int pb, const double* Dinv, const double* flag) {
+    if (flag[0] != 0.0) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = p + pb + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += nw) {
+        double* Li = L + (long)i * ld + p;
+        const double a = lane < pb ? Li[lane] : 0.0;
+        double out = 0.0;
+        // out_j = sum_{k <= j} a_k Dinv[j][k]
+        for (int k = 0; k < pb; k++) {
+            const double ak = __shfl_sync(0xffffffffu, a, k);
+            if (lane < pb && k <= lane) out += ak * Dinv[lane * CB + k];
+        }
+        __syncwarp();
+        if (lane < pb) Li[lane] = out;
+    }
+}
+
+// Trailing update A[i][k] -= sum_t L[i][p+t] L[k][p+t], p+pb <= k <= i < n, 16x16 tiles.
+__global__ void __launch_bounds__(256) chol_update_kernel(double* L, int ld, int n, int p, int pb, const double* flag) {
+    __shared__ double Pi[16][CB + 1], Pk[16][CB + 1];
+    if (flag[0] != 0.0) return;
+    const int q0 = p + pb, m = n - q0;
+    const int T = (m + 15) / 16;
+    int t = blockIdx.x, ti = 0;
+    while (t >= ti + 1) { t -= ti + 1; ti++; }   // lower-triangle tile (ti, tk), tk <= ti
+    if (ti >= T) return;
+    const int tk = t;
+    const int i0 = q0 + ti * 16, k0 = q0 + tk * 16;
+    for (int e = threadIdx.x; e < 16 * CB; e += blockDim.x) {
+        const int r = e / CB, c = e % CB;
+        Pi[r][c] = (i0 + r < n && c < pb) ? L[(long)(i0 + r) * ld + p + c] : 0.0;
+        Pk[r][c] = (k0 + r < n && c < pb) ? L[(long)(k0 + r) * ld + p + c] : 0.0;
+    }
+    __syncthreads();
+    const int r = threadIdx.x / 16, c = threadIdx.x % 16;
+    const int i = i0 + r, k = k0 + c;
+    if (i < n && k <= i) {
+        double acc = 0.0;
+#pragma unroll 8
+        for (int u = 0; u < CB; u++) acc += Pi[r][u] * Pk[c][u];
+        L[(long)i * ld + k] -= acc;
+    }
+}
+
+// Linv = L^-1 (lower triangular), one warp per column, column kept in shared memory.
+__global__ void __launch_bounds__(256) chol_inverse_kernel(const double* L, int ld, int n, double* Linv,
+                                                           const double* flag) {
+    extern __shared__ double xs[];   // [8 warps][n]
+    if (flag[0] != 0.0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 8 + warp;
+    if (c >= n) return;
+    double* x = xs + warp * n;
+    for (int i = lane; i < n; i += 32) x[i] = 0.0;
+    __syncwarp();
+    for (int i = c; i < n; i++) {
+        const double* Li = L + (long)i * ld;
+        double v = 0.0;
+        for (int k = c + lane; k < i; k += 32) v += Li[k] * x[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - v) / Li[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) Linv[(long)i * ld + c] = i >= c ? x[i] : 0.0;
+}
+
+// y = Linv b (trans = 0) or y = Linv^T b (trans = 1); one warp per output row.
+// rhs is read with stride rs.  Skips when flag[0] or flag[1] is set.
+__global__ void tri_gemv_kernel(const double* Linv, int ld, int n, const double* rhs, int rs, double* y, int trans,
+                                const double* flag) {
+    if (flag[0] != 0.0 || flag[1] != 0.0) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        double v = 0.0;
+        if (!trans) {
+            for (int k = lane; k <= i; k += 32) v += Linv[(long)i * ld + k] * rhs[(long)k * rs];
+        } else {
+            for (int k = i + lane; k < n; k += 32) v += Linv[(long)k * ld + i] * rhs[(long)k * rs];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) y[i] = v;
+    }
+}
+
+// Residual pass over all design rows with coefficients a (FP64 in, FP32 model).
+// A CTA takes 256 rows at a time (one per thread): each thread forms its
+// row's model and residual e and stages X_m and g_k = w e p_k in shared
+// memory; then r_j = sum_rows c_j w e is a set of 256-term dot products from
+// shared memory, summed in FP32 per tile and in FP64 across tiles.  Also
+// chi2 = sum w e^2 and the count of weighted rows.  Per-CTA partials
+// [NP + 4] are reduced in a fixed order.
+constexpr int RT = 256;
+
+__global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const double* a, const double* flag, int want_r,
+                                                   double* part) {
+    extern __shared__ __align__(16) float rsm[];   // Xs[nb][RT], Gk[Ks + Kb][RT]
     __shared__ float af[1024];
-    __shared__ double wchi[8], wn[8];
+    __shared__ double wchi[RT / 32], wn[RT / 32];
     if (flag[0] != 0.0 || (want_r && flag[1] != 0.0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int j = tid; j < g.Nc; j += blockDim.x) af[j] = (float)a[j];
-    for (int j = tid; j < 8 * g.NP; j += blockDim.x) rsm[j] = 0.0;
-    __syncthreads();
+    float* Xs = rsm;
+    float* Gk = rsm + g.nb * RT;
+    for (int j = tid; j < g.Nc; j += RT) af[j] = (float)a[j];
     const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
-    double chi = 0.0, cnt = 0.0;
     const int nx = 1 + (g.nb - 1) * g.Ks;
-    for (long base = (long)(blockIdx.x * 8 + warp) * 32; base < nrows; base += (long)gridDim.x * 8 * 32) {
-        const long rho = base + lane;
+    double racc[2] = {0.0, 0.0};      // outputs j = tid and j = tid + RT
+    double chi = 0.0, cnt = 0.0;
+    __syncthreads();
+    for (long base = (long)blockIdx.x * RT; base < nrows; base += (long)gridDim.x * RT) {
+        const long rho = base + tid;
         float m[META];
         row_meta(g, rho, nrows, m);
-        const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
         const bool use = m[0] != 0.0f;
-        // model = X_0 a_0 + sum_n X_n sum_k p_k a_{n,k} + sum_k pb_k bg_k
+        const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
         float model = 0.0f;
-        if (use) {
-            const float* Xr = g.X + (long)s * g.nb * g.ss + pix;
-            model = __ldg(Xr) * af[0];
-            for (int n = 1; n < g.nb; n++) {
-                float qn = 0.0f;
+        for (int n = 0; n < g.nb; n++) {
+            const float xv = use ? __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix) : 0.0f;
+            Xs[n * RT + tid] = xv;
+            float qn;
+            if (n == 0) {
+                qn = af[0];
+            } else {
+                qn = 0.0f;
                 for (int k = 0; k < g.Ks; k++) qn = fmaf(m[4 + k], af[1 + (n - 1) * g.Ks + k], qn);
-                model = fmaf(__ldg(Xr + (long)n * g.ss), qn, model);
             }
-            for (int k = 0; k < g.Kb; k++) model = fmaf(m[10 + k], af[nx + k], model);
+            model = fmaf(xv, qn, model);
         }
+        for (int k = 0; k < g.Kb; k++) model = fmaf(m[10 + k], af[nx + k], model);
         const float e = use ? m[3] - model : 0.0f;
         const float we = m[2] * e;
         chi += (double)we * (double)e;
         cnt += use ? 1.0 : 0.0;
+        for (int k = 0; k < g.Ks; k++) Gk[k * RT + tid] = we * m[4 + k];
+        for (int k = 0; k < g.Kb; k++) Gk[(g.Ks + k) * RT + tid] = we * m[10 + k];
+        __syncthreads();
         if (want_r) {
-            const float* Xr = g.X + (long)s * g.nb * g.ss + pix;
-            for (int j = 0; j < g.Nc; j++) {
-                float c = 0.0f;
-                if (use) {
-                    if (j < nx) {
-                        const int n = j == 0 ? 0 : 1 + (j - 1) / g.Ks;
-                        const float xv = __ldg(Xr + (long)n * g.ss);
-                        c = j == 0 ? xv : xv * m[4 + (j - 1) % g.Ks];
-                    } else {
-                        c = m[10 + (j - nx)];
-                    }
-                }
-                float v = c * we;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) rsm[warp * g.NP + j] += (double)v;
+            for (int h = 0; h < 2; h++) {
+                const int j = tid + h * RT;
+                if (j >= g.Nc) continue;
+                const float* xa;
+                const float* gb;
+                if (j < nx) {
+                    const int n = j == 0 ? 0 : 1 + (j - 1) / g.Ks, k = j == 0 ? 0 : (j - 1) % g.Ks;
+                    xa = Xs + n * RT;
+                    gb = Gk + k * RT;
+                } else {
+                    xa = nullptr;
+                    gb = Gk + (g.Ks + (j - nx)) * RT;
+                }
+                float acc = 0.0f;
+                if (xa) {
+                    for (int t = 0; t < RT; t++) acc = fmaf(xa[t], gb[t], acc);
+                } else {
+                    for (int t = 0; t < RT; t++) acc += gb[t];
+                }
+                racc[h] += (double)acc;
             }
         }
+        __syncthreads();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -775,26 +899,32 @@ __global__ void __launch_bounds__(256) resid_kernel(GramArgs g, const double* a,
     if (lane == 0) { wchi[warp] = chi; wn[warp] = cnt; }
     __syncthreads();
     double* out = part + (long)blockIdx.x * (g.NP + 4);
-    for (int j = tid; j < g.Nc; j += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < 8; w++) s += rsm[w * g.NP + j];
-        out[j] = s;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int j = tid + h * RT;
+        if (j < g.Nc) out[j] = want_r ? racc[h] : 0.0;
     }
     if (tid == 0) {
         double c = 0.0, n = 0.0;
-        for (int w = 0; w < 8; w++) { c += wchi[w]; n += wn[w]; }
+        for (int w = 0; w < RT / 32; w++) { c += wchi[w]; n += wn[w]; }
         out[g.NP] = c;
         out[g.NP + 1] = n;
     }
 }
 
+// Column j of the partials summed over parts in a fixed order: one warp per column.
 __global__ void resid_reduce_kernel(const double* part, int nparts, int NP, int Nc, double* r, double* chi_n,
                                     const double* flag, int skip_if_done) {
     if (flag[0] != 0.0 || (skip_if_done && flag[1] != 0.0)) return;
-    for (int j = threadIdx.x; j < Nc + 2; j += blockDim.x) {
-        const int col = j < Nc ? j : NP + (j - Nc);
-        double s = 0.0;
-        for (int p = 0; p < nparts; p++) s += part[(long)p * (NP + 4) + col];
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= Nc + 2) return;
+    const int col = j < Nc ? j : NP + (j - Nc);
+    double s = 0.0;
+    for (int p = lane; p < nparts; p += 32) s += part[(long)p * (NP + 4) + col];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
         if (j < Nc) r[j] = s;
         else chi_n[j - Nc] = s;
     }
@@ -934,6 +1064,58 @@ __global__ void select_kernel(const float* R, const uint8_t* flags, long pitch, 
     }
 }
 
+// Faster form of the same rule for the context path: a byte map of strict
+// local maxima first, then per candidate the isolation window is scanned in
+// Chebyshev rings of growing radius (noise peaks meet a brighter neighbour
+// within a ring or two), reading R only where the map is set.
+__global__ void select_lmax_kernel(const float* R, long pitch, int w, int h, uint8_t* lmax) {
+    const long np = (long)w * h;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < np; e += (long)gridDim.x * blockDim.x) {
+        const int y = (int)(e / w), x = (int)(e - (long)y * w);
+        lmax[e] = is_lmax(R, pitch, w, h, x, y) ? 1 : 0;
+    }
+}
+
+__global__ void select_ring_kernel(const float* R, const uint8_t* flags, const uint8_t* lmax, long pitch, int w, int h,
+                                   int gx, int gy, int m, float max_peak, int iso, float iso_frac,
+                                   unsigned long long* cell_key) {
+    const long np = (long)w * h;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < np; e += (long)gridDim.x * blockDim.x) {
+        if (!lmax[e]) continue;
+        const int y = (int)(e / w), x = (int)(e - (long)y * w);
+        if (x - m < 0 || x + m > w - 1 || y - m < 0 || y + m > h - 1) continue;
+        const float c = R[(long)y * pitch + x];
+        if (!(c < max_peak)) continue;
+        const float thr = iso_frac * c;
+        bool bad = false;
+        for (int rad = 1; rad <= iso && !bad; rad++) {
+            for (int t = 0; t < 8 * rad && !bad; t++) {
+                // walk the ring of Chebyshev radius rad
+                int dx, dy;
+                const int side = 2 * rad;
+                if (t < side) { dx = -rad + t; dy = -rad; }
+                else if (t < 2 * side) { dx = rad; dy = -rad + (t - side); }
+                else if (t < 3 * side) { dx = rad - (t - 2 * side); dy = rad; }
+                else { dx = -rad; dy = rad - (t - 3 * side); }
+                const int xx = x + dx, yy = y + dy;
+                if (xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                if (lmax[(long)yy * w + xx] && R[(long)yy * pitch + xx] > thr) bad = true;
+            }
+        }
+        if (bad) continue;
+        for (int yy = y - m; yy <= y + m && !bad; yy++)
+            for (int xx = x - m; xx <= x + m; xx++)
+                if (flags[(long)yy * pitch + xx]) { bad = true; break; }
+        if (bad) continue;
+        const int cx = (int)(((long)(x + 1) * gx - 1) / w), cy = (int)(((long)(y + 1) * gy - 1) / h);
+        const unsigned bits = __float_as_uint(c);
+        const unsigned ord = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+        const unsigned rank = (unsigned)y * (unsigned)w + (unsigned)x;
+        const unsigned long long key = ((unsigned long long)ord << 32) | (unsigned long long)(0xffffffffu - rank);
+        atomicMax(cell_key + cy * gx + cx, key);
+    }
+}
+
 __global__ void __launch_bounds__(1024) select_compact_kernel(const unsigned long long* cell_key, int ncell, int w,
                                                               int* centers, int* n_out) {
     __shared__ int wsum[32];
@@ -1011,6 +1193,34 @@ int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st) {
     return rc;
 }
 
+// Factor M[0:n,0:n] (ld) into ctx->L and form L^-1 in ctx->Linv; flag = vec row 7.
+int argus_cholesky_solve_prepare(argus_ctx* ctx, const double* M, int ld, int n, cudaStream_t st) {
+    double* flag = ctx->vec + 7 * (size_t)ctx->np_cols;
+    chol_init_kernel<<<ctx->num_sms, 256, 0, st>>>(M, ld, n, ctx->L, flag); argus_count_launch(1);
+    for (int p = 0; p < n; p += CB) {
+        const int pb = min(CB, n - p);
+        chol_diag_kernel<<<1, 256, 0, st>>>(ctx->L, ld, p, pb, ctx->Dinv, flag, ctx->d_status); argus_count_launch(1);
+        const int rest = n - p - pb;
+        if (rest <= 0) break;
+        chol_panel_kernel<<<(rest + 7) / 8, 256, 0, st>>>(ctx->L, ld, n, p, pb, ctx->Dinv, flag); argus_count_launch(1);
+        const int T = (rest + 15) / 16;
+        chol_update_kernel<<<T * (T + 1) / 2, 256, 0, st>>>(ctx->L, ld, n, p, pb, flag); argus_count_launch(1);
+    }
+    const size_t ism = sizeof(double) * 8 * (size_t)n;
+    cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    chol_inverse_kernel<<<(n + 7) / 8, 256, ism, st>>>(ctx->L, ld, n, ctx->Linv, flag); argus_count_launch(1);
+    return argus_launch_status();
+}
+
+// x = (L L^T)^-1 rhs through the explicit inverse: two FP64 GEMVs.
+void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, double* x, cudaStream_t st) {
+    double* flag = ctx->vec + 7 * (size_t)ctx->np_cols;
+    double* z = ctx->vec + 0 * (size_t)ctx->np_cols;
+    const int blocks = (n + 7) / 8;
+    tri_gemv_kernel<<<blocks, 256, 0, st>>>(ctx->Linv, ld, n, rhs, rs, z, 0, flag); argus_count_launch(1);
+    tri_gemv_kernel<<<blocks, 256, 0, st>>>(ctx->Linv, ld, n, z, 1, x, 1, flag); argus_count_launch(1);
+}
+
 // Steps of iterative refinement launched after the first solve (each is a
 // no-op once the iteration has converged or started to diverge).
 constexpr int REFINE_MAX = 3;
@@ -1030,6 +1240,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     rc = make_basis_dev(basis, &d);
     if (rc) return rc;
     if (d.Nc > ctx->max_coeffs) return ARGUS_ERR_ARG;
+    if (d.Nc > 2 * RT) return ARGUS_ERR_UNSUPPORTED;   // the residual pass gives each thread two outputs
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     rc = argus_basis_prepare(ctx, basis, st);
@@ -1102,21 +1313,24 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     double* chif = ctx->vec + 5 * ld + 4;
     double* flag = ctx->vec + 7 * ld;   // refinement state
     if (cudaMemsetAsync(flag, 0, 8 * sizeof(double), st) != cudaSuccess) return ARGUS_ERR_CUDA;
-    cholesky_kernel<<<1, 1024, 0, st>>>(ctx->M, NP, d.Nc, ctx->L, flag, ctx->d_status); argus_count_launch(1);
-    const size_t solve_smem = sizeof(double) * NP;
-    chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, ctx->M + d.Nc, NP, c, flag); argus_count_launch(1);
+    const int n = d.Nc;
+    rc = argus_cholesky_solve_prepare(ctx, ctx->M, NP, n, st);
+    if (rc) return rc;
+    // first solve: c = M^-1 b, b = column N_c of the augmented Gram
+    argus_tri_solve(ctx, NP, n, ctx->M + n, NP, c, st);
     int nparts = ctx->num_sms * 2;
     if (nparts > ctx->resid_parts) nparts = ctx->resid_parts;
-    const size_t rsmem = sizeof(double) * 8 * NP;
+    const size_t rsmem = sizeof(float) * (size_t)(d.nb + d.Ks + d.Kb) * RT;
     cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+    const int rr_blocks = (n + 2 + 7) / 8;
     for (int it = 0; it < REFINE_MAX; it++) {
-        resid_kernel<<<nparts, 256, rsmem, st>>>(g, c, flag, 1, ctx->resid_part); argus_count_launch(1);
-        resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, d.Nc, rv, it == 0 ? chi0 : chiw, flag, 1); argus_count_launch(1);
-        chol_solve_kernel<<<1, 1024, solve_smem, st>>>(ctx->L, NP, d.Nc, rv, 1, dl, flag); argus_count_launch(1);
-        refine_update_kernel<<<1, 256, 0, st>>>(c, dl, d.Nc, flag); argus_count_launch(1);
+        resid_kernel<<<nparts, RT, rsmem, st>>>(g, c, flag, 1, ctx->resid_part); argus_count_launch(1);
+        resid_reduce_kernel<<<rr_blocks, 256, 0, st>>>(ctx->resid_part, nparts, NP, n, rv, it == 0 ? chi0 : chiw, flag, 1); argus_count_launch(1);
+        argus_tri_solve(ctx, NP, n, rv, 1, dl, st);
+        refine_update_kernel<<<1, 256, 0, st>>>(c, dl, n, flag); argus_count_launch(1);
     }
-    resid_kernel<<<nparts, 256, rsmem, st>>>(g, c, flag, 0, ctx->resid_part); argus_count_launch(1);
-    resid_reduce_kernel<<<1, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, chif, flag, 0); argus_count_launch(1);
+    resid_kernel<<<nparts, RT, rsmem, st>>>(g, c, flag, 0, ctx->resid_part); argus_count_launch(1);
+    resid_reduce_kernel<<<rr_blocks, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, chif, flag, 0); argus_count_launch(1);
     finalize_kernel<<<1, 256, 0, st>>>(d, c, ctx->basis_S, flag, chi0, chif, max_stamps, n_stamps, centers, stamp,
                                        shape.w, shape.h, precision, coeffs, stats); argus_count_launch(1);
     return argus_launch_status();
@@ -1153,8 +1367,11 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     const long np = (long)shape.w * shape.h;
     long blocks = (np + 255) / 256;
     if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
-    select_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x, grid_y,
-                                                    stamp / 2 + khalf, max_peak, iso, iso_frac, ctx->cell_key); argus_count_launch(1);
+    uint8_t* lmax = reinterpret_cast<uint8_t*>(ctx->label);   // the label scratch, one byte per pixel
+    select_lmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, shape.pitch, shape.w, shape.h, lmax); argus_count_launch(1);
+    select_ring_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, lmax, shape.pitch, shape.w, shape.h, grid_x,
+                                                         grid_y, stamp / 2 + khalf, max_peak, iso, iso_frac,
+                                                         ctx->cell_key); argus_count_launch(1);
     select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps); argus_count_launch(1);
     return argus_launch_status();
 }
