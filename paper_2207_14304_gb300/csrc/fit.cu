@@ -934,15 +934,25 @@ __global__ void resid_reduce_kernel(const double* part, int nparts, int NP, int 
 // applied, [4] last applied step.  A step delta (relative max-norm) is applied
 // unless it is larger than the previous one (the iteration diverges: keep the
 // current iterate and stop); the loop also stops once a step is below 1e-12.
-__global__ void refine_update_kernel(double* a, const double* delta, int Nc, double* flag) {
+__global__ void __launch_bounds__(256) refine_update_kernel(double* a, const double* delta, int Nc, double* flag) {
+    __shared__ double red[2][8];
     __shared__ double mx[2];
     if (flag[0] != 0.0 || flag[1] != 0.0) return;
+    double ms = 0.0, ma = 0.0;
+    for (int j = threadIdx.x; j < Nc; j += blockDim.x) {
+        ms = fmax(ms, fabs(delta[j]));
+        ma = fmax(ma, fabs(a[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ms = fmax(ms, __shfl_xor_sync(0xffffffffu, ms, o));
+        ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ms; red[1][threadIdx.x >> 5] = ma; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double ms = 0.0, ma = 0.0;
-        for (int j = 0; j < Nc; j++) {
-            ms = fmax(ms, fabs(delta[j]));
-            ma = fmax(ma, fabs(a[j]));
-        }
+        ms = 0.0; ma = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { ms = fmax(ms, red[0][w]); ma = fmax(ma, red[1][w]); }
         const double step = ma > 0.0 ? ms / ma : ms;
         mx[0] = step;
         mx[1] = (flag[3] > 0.0 && !(step <= flag[2])) ? 1.0 : 0.0;   // diverging (or NaN)
@@ -1368,8 +1378,9 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     long blocks = (np + 255) / 256;
     if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
     uint8_t* lmax = reinterpret_cast<uint8_t*>(ctx->label);   // the label scratch, one byte per pixel
+    const long rblocks = (np + 255) / 256;                      // one pixel per thread: latency-bound scans
     select_lmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, shape.pitch, shape.w, shape.h, lmax); argus_count_launch(1);
-    select_ring_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, flags, lmax, shape.pitch, shape.w, shape.h, grid_x,
+    select_ring_kernel<<<(unsigned)rblocks, 256, 0, st>>>(ref, flags, lmax, shape.pitch, shape.w, shape.h, grid_x,
                                                          grid_y, stamp / 2 + khalf, max_peak, iso, iso_frac,
                                                          ctx->cell_key); argus_count_launch(1);
     select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps); argus_count_launch(1);

@@ -119,27 +119,40 @@ __global__ void __launch_bounds__(THREADS) subtract_kernel(SubArgs a) {
 
     // output (lx, ly0 + j), tap (du, dv) = (iu - R, iv - R):
     //   R(x - du, y - dv) = Rs[ly0 + j + 2R - iv][lx + 2R - iu]
+    // The iv taps run in blocks of IVB: each block loads its own window of
+    // ROWS_PER_THREAD + IVB - 1 reference values, which keeps the unrolled body
+    // small enough for the instruction cache.
+    constexpr int IVB = (KS % 7 == 0) ? 7 : ((KS % 5 == 0) ? 5 : KS);
+    constexpr int NW = ROWS_PER_THREAD + IVB - 1;
 #pragma unroll 1
     for (int iu = 0; iu < KS; iu++) {
-        float col[NCOL];
-#pragma unroll
-        for (int m = 0; m < NCOL; m++) col[m] = Rs[(ly0 + m) * SW + lx + 2 * R - iu];
         const float* kt = Kt + iu * KS * NKP;
+        const float* rcol = Rs + ly0 * SW + lx + 2 * R - iu;
+#pragma unroll 1
+        for (int b = 0; b < KS / IVB; b++) {
+            // window row m holds Rs[ly0 + m + 2R - b*IVB - (IVB-1)]
+            const int base = 2 * R - b * IVB - (IVB - 1);
+            float win[NW];
 #pragma unroll
-        for (int iv = 0; iv < KS; iv++) {
-            float kk[NKP];
-            if constexpr (NKP == 1) {
-                kk[0] = kt[iv];
-            } else {
+            for (int m = 0; m < NW; m++) win[m] = rcol[(m + base) * SW];
 #pragma unroll
-                for (int q = 0; q < NKP; q += 4)
-                    *reinterpret_cast<float4*>(kk + q) = *reinterpret_cast<const float4*>(kt + iv * NKP + q);
-            }
+            for (int i = 0; i < IVB; i++) {
+                const int iv = b * IVB + i;
+                float kk[NKP];
+                if constexpr (NKP == 1) {
+                    kk[0] = kt[iv];
+                } else {
 #pragma unroll
-            for (int j = 0; j < ROWS_PER_THREAD; j++) {
-                const float rv = col[j + 2 * R - iv];
+                    for (int q = 0; q < NKP; q += 4)
+                        *reinterpret_cast<float4*>(kk + q) = *reinterpret_cast<const float4*>(kt + iv * NKP + q);
+                }
 #pragma unroll
-                for (int k = 0; k < NK; k++) acc[k][j] = fmaf(kk[k], rv, acc[k][j]);
+                for (int j = 0; j < ROWS_PER_THREAD; j++) {
+                    // row ly0 + j + 2R - iv  ->  window index j + (IVB - 1) - i
+                    const float rv = win[j + (IVB - 1) - i];
+#pragma unroll
+                    for (int k = 0; k < NK; k++) acc[k][j] = fmaf(kk[k], rv, acc[k][j]);
+                }
             }
         }
     }
@@ -149,17 +162,20 @@ __global__ void __launch_bounds__(THREADS) subtract_kernel(SubArgs a) {
     for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = 0.0f;
 #pragma unroll 1
     for (int iu = 0; iu < KS; iu++) {
-        float col[NCOL];
+        const float* vcol = Vs + ly0 * SW + lx + 2 * R - iu;
+#pragma unroll 1
+        for (int b = 0; b < KS / IVB; b++) {
+            const int base = 2 * R - b * IVB - (IVB - 1);
+            float win[NW];
 #pragma unroll
-        for (int m = 0; m < NCOL; m++) col[m] = Vs[(ly0 + m) * SW + lx + 2 * R - iu];
-        float kc[KSP];
+            for (int m = 0; m < NW; m++) win[m] = vcol[(m + base) * SW];
 #pragma unroll
-        for (int q = 0; q < KSP; q += 4)
-            *reinterpret_cast<float4*>(kc + q) = *reinterpret_cast<const float4*>(Kc2 + iu * KSP + q);
+            for (int i = 0; i < IVB; i++) {
+                const float kc = Kc2[iu * KSP + b * IVB + i];
 #pragma unroll
-        for (int iv = 0; iv < KS; iv++)
-#pragma unroll
-            for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = fmaf(kc[iv], col[j + 2 * R - iv], accv[j]);
+                for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = fmaf(kc, win[j + (IVB - 1) - i], accv[j]);
+            }
+        }
     }
 
     // epilogue: spatial combination, background, edge and flag handling
