@@ -222,6 +222,66 @@ int argus_detect(argus_ctx *ctx, const float *diff, const float *diff_var, const
                  argus_shape shape, float nsigma, float psf_sigma, uint8_t *mask,
                  argus_source *out, int cap, int *n_found, argus_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched segments (paper Sec. 5: subtraction parallelised over image
+ * segments; Sec. 4.1.1: HEALPix segments).  Many square cutouts of uneven size
+ * are stored in one "atlas": each quantity (science, variance, reference,
+ * reference variance, flags, difference, difference variance, mask) is one
+ * pitched image, segment s occupying rows [row0, row0 + side) and columns
+ * [col0, col0 + side), row0 and col0 multiples of 16, no overlaps, side in
+ * [ksize, 512].  Each segment gets its own spatially constant kernel fitted by
+ * weighted least squares over every interior pixel (pixels at least ksize/2
+ * from the segment edge), in the basis of argus_fit_kernel with
+ * spatial_degree = bg_degree = 0; then subtraction with difference variance,
+ * and 5-sigma style detection over the whole atlas (segment edges are
+ * invalid, so components stay inside segments).  The work is cut into
+ * fixed-size units (row bands of the fit, 32x32 tiles of the subtraction) that
+ * persistent CTAs take from atomic counters, largest segments first. */
+typedef struct {
+    int row0, col0;   /* atlas position of the segment's pixel (0, 0) */
+    int side;         /* square side in pixels */
+} argus_segment;
+
+/* Launch shape of the batched kernels (picked by the autotuner). */
+typedef struct {
+    int fit_band;          /* rows per fit work unit (8..128) */
+    int fit_ctas_per_sm;   /* persistent fit CTAs per SM (1..4) */
+    int sub_ctas_per_sm;   /* persistent subtraction CTAs per SM (1..16) */
+    int reserved;
+} argus_seg_config;
+
+/* Per-segment fit result (device). */
+typedef struct {
+    double chi2;   /* sum w (I - model)^2 over the interior, from the normal equations */
+    int n_pix;     /* interior pixels with nonzero weight */
+    int status;    /* ARGUS_OK or ARGUS_ERR_SINGULAR */
+} argus_seg_stats;
+
+typedef struct argus_seg_plan argus_seg_plan;
+
+/* Build the work tables for a segment table (host array of n entries) in an
+ * atlas of atlas_h rows and the given pitch, with launch shape cfg (NULL:
+ * defaults).  This is a set-up call: it allocates the plan's device tables. */
+int argus_segments_plan(argus_ctx *ctx, const argus_segment *table, int n, int pitch, int atlas_h,
+                        const argus_basis *basis, const argus_seg_config *cfg, argus_seg_plan **out);
+int argus_segments_destroy(argus_seg_plan *plan);
+
+/* Run the batch: fit, solve, subtract, detect.  Atlas images as above (device,
+ * same pitch); the caller keeps the atlas padding of diff/diff_var at zero.
+ * coeffs: double [n][Nc] (Alard-Lupton order, background last); stats:
+ * argus_seg_stats [n]; mask/out/n_found as in argus_detect (mask and n_found
+ * may both be NULL to skip detection).  With use_graph != 0 the whole sequence
+ * is recorded into a CUDA graph on the first call (and again whenever a
+ * pointer or cap changes) and replayed with one graph launch. */
+int argus_segments_run(argus_seg_plan *plan, const float *sci, const float *sci_var, const float *ref,
+                       const float *ref_var, const uint8_t *flags, float *diff, float *diff_var,
+                       uint8_t *mask, double *coeffs, argus_seg_stats *stats, float nsigma,
+                       float psf_sigma, argus_source *out, int cap, int *n_found, int use_graph,
+                       argus_stream stream);
+
+/* Number of fit and subtraction work units of a plan. */
+int argus_segments_items(const argus_seg_plan *plan, int *n_fit_items, int *n_sub_items);
+
 /* Stamp selection that allocates nothing, for callers that cannot call
  * cudaMalloc (a host that reserves all device memory up front, a real-time
  * loop that must never enter an allocator, or a plugin that is only handed

@@ -69,6 +69,7 @@ def _declare(l):
     l.ora_stamp_basis.restype = None
     l.ora_fit.argtypes = [I, I, P, P, P, P, P, I, I, I, I, P, P, I, I, P, P, P, P, P]
     l.ora_expand.argtypes = [I, I, P, P, I, I, P, P, P]
+    l.ora_fit_rect.argtypes = [I, I, P, P, P, P, I, I, I, I, I, I, P, P, I, I, P, P, P, P, P]
     l.ora_subtract.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, P, P]
     l.ora_subtract_at.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, I, P, P, P]
     l.ora_detect.argtypes = [I, I, P, P, P, F, D, P, P, I]
@@ -206,6 +207,21 @@ def fit(sci, sci_var, ref, flags, centers, stamp, b: Basis) -> FitResult:
     st = lib().ora_fit(w, h, _p(sci), _p(sv), _p(R), _p(fl), _p(cen), cen.shape[0], stamp,
                        b.ksize, b.ngauss, _p(b.sigmas), _p(b.degrees), b.spatial_degree,
                        b.bg_degree, _p(a), _p(M), _p(bv), C.byref(chi2), C.byref(dof))
+    return FitResult(st, a, M, bv, chi2.value, dof.value)
+
+
+def fit_rect(sci, sci_var, ref, flags, rect, b: Basis) -> FitResult:
+    """Least-squares kernel fit over every pixel of rect = (x0, y0, x1, y1) (inclusive)."""
+    sci = _c(sci, np.float32); sv = _c(sci_var, np.float32); R = _c(ref, np.float32)
+    fl = _c(flags, np.uint8)
+    h, w = sci.shape
+    Nc = b.ncoeffs
+    a = np.zeros(Nc); M = np.empty((Nc, Nc)); bv = np.empty(Nc)
+    chi2 = C.c_double(0.0); dof = C.c_long(0)
+    x0, y0, x1, y1 = (int(v) for v in rect)
+    st = lib().ora_fit_rect(w, h, _p(sci), _p(sv), _p(R), _p(fl), x0, y0, x1, y1, b.ksize, b.ngauss,
+                            _p(b.sigmas), _p(b.degrees), b.spatial_degree, b.bg_degree, _p(a), _p(M),
+                            _p(bv), C.byref(chi2), C.byref(dof))
     return FitResult(st, a, M, bv, chi2.value, dof.value)
 
 

@@ -395,6 +395,90 @@ int ora_fit(int w, int h, const float *sci, const float *sci_var, const float *R
 }
 
 /* ------------------------------------------------------------------------ */
+/* The same least-squares fit over every pixel of a rectangle [x0,x1]x[y0,y1] */
+/* (a whole segment interior) instead of stamps.  Pixels whose convolution   */
+/* window leaves the image are skipped.  Spatial terms use the image size.   */
+/* ------------------------------------------------------------------------ */
+int ora_fit_rect(int w, int h, const float *sci, const float *sci_var, const float *R,
+                 const uint8_t *flags, int x0, int y0, int x1, int y1, int ks, int ngauss,
+                 const double *sigma, const int *degree, int sdeg, int bgdeg, double *coeffs,
+                 double *M_out, double *b_out, double *chi2_out, long *dof_out) {
+    int nb = ora_basis_count(ngauss, degree);
+    int Ks = ora_nterms(sdeg), Kb = ora_nterms(bgdeg), Nc = ora_ncoeffs(nb, sdeg, bgdeg);
+    int r = (ks - 1) / 2;
+    double *B = (double *)malloc(sizeof(double) * nb * ks * ks);
+    ora_basis(ks, ngauss, sigma, degree, B, NULL);
+    int ny = y1 - y0 + 1;
+    double *Mp = (double *)calloc((size_t)ny * Nc * Nc, sizeof(double));
+    double *bp = (double *)calloc((size_t)ny * Nc, sizeof(double));
+    long *np = (long *)calloc(ny, sizeof(long));
+#pragma omp parallel for schedule(dynamic)
+    for (int y = y0; y <= y1; y++) {
+        double pk[64], pb[64];
+        double *X = (double *)malloc(sizeof(double) * nb), *c = (double *)malloc(sizeof(double) * Nc);
+        double *Ms = Mp + (size_t)(y - y0) * Nc * Nc, *bs = bp + (size_t)(y - y0) * Nc;
+        for (int x = x0; x <= x1; x++) {
+            if (x - r < 0 || x + r > w - 1 || y - r < 0 || y + r > h - 1) continue;
+            long p = (long)y * w + x;
+            double v = sci_var[p], I = sci[p];
+            if (flags[p] || !(v > 0.0) || !isfinite(I) || !isfinite(v)) continue;
+            double wt = 1.0 / v;
+            basis_conv_at(R, w, x, y, B, nb, ks, X);
+            ora_spatial_terms(x, y, w, h, sdeg, pk);
+            ora_spatial_terms(x, y, w, h, bgdeg, pb);
+            design_row(X, pk, nb, Ks, pb, Kb, c);
+            for (int a = 0; a < Nc; a++) {
+                double wa = wt * c[a];
+                bs[a] += wa * I;
+                for (int b2 = 0; b2 < Nc; b2++) Ms[(size_t)a * Nc + b2] += wa * c[b2];
+            }
+            np[y - y0]++;
+        }
+        free(X); free(c);
+    }
+    double *M = (double *)calloc((size_t)Nc * Nc, sizeof(double));
+    double *bv = (double *)calloc(Nc, sizeof(double));
+    long nvalid = 0;
+    for (int t = 0; t < ny; t++) {
+        for (long i = 0; i < (long)Nc * Nc; i++) M[i] += Mp[(size_t)t * Nc * Nc + i];
+        for (int i = 0; i < Nc; i++) bv[i] += bp[(size_t)t * Nc + i];
+        nvalid += np[t];
+    }
+    free(Mp); free(bp); free(np);
+    if (M_out) memcpy(M_out, M, sizeof(double) * Nc * Nc);
+    if (b_out) memcpy(b_out, bv, sizeof(double) * Nc);
+    double *L = (double *)malloc(sizeof(double) * Nc * Nc);
+    int st = ora_cholesky(Nc, M, L);
+    if (st == 0) {
+        ora_cholesky_solve(Nc, L, bv, coeffs);
+        double chi2 = 0.0;
+#pragma omp parallel for reduction(+ : chi2) schedule(dynamic)
+        for (int y = y0; y <= y1; y++) {
+            double pk[64], pb[64];
+            double *X = (double *)malloc(sizeof(double) * nb), *c = (double *)malloc(sizeof(double) * Nc);
+            for (int x = x0; x <= x1; x++) {
+                if (x - r < 0 || x + r > w - 1 || y - r < 0 || y + r > h - 1) continue;
+                long p = (long)y * w + x;
+                double v = sci_var[p], I = sci[p];
+                if (flags[p] || !(v > 0.0) || !isfinite(I) || !isfinite(v)) continue;
+                basis_conv_at(R, w, x, y, B, nb, ks, X);
+                ora_spatial_terms(x, y, w, h, sdeg, pk);
+                ora_spatial_terms(x, y, w, h, bgdeg, pb);
+                design_row(X, pk, nb, Ks, pb, Kb, c);
+                double m = 0.0;
+                for (int a = 0; a < Nc; a++) m += c[a] * coeffs[a];
+                chi2 += (I - m) * (I - m) / v;
+            }
+            free(X); free(c);
+        }
+        if (chi2_out) *chi2_out = chi2;
+    }
+    if (dof_out) *dof_out = nvalid - Nc;
+    free(L); free(M); free(bv); free(B);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Kernel expansion: K_k(u,v) = sum_n a_{n,k} B_n(u,v); K_0 also holds       */
 /* a_0 B_0.  bg[k] = background coefficients.  K[k*ks*ks + (v+r)*ks+(u+r)].  */
 /* ------------------------------------------------------------------------ */

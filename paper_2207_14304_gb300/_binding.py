@@ -64,6 +64,19 @@ class argus_fit_stats(C.Structure):
                 ("refine_iters", C.c_int), ("pad_", C.c_int)]
 
 
+class argus_segment(C.Structure):
+    _fields_ = [("row0", C.c_int), ("col0", C.c_int), ("side", C.c_int)]
+
+
+class argus_seg_config(C.Structure):
+    _fields_ = [("fit_band", C.c_int), ("fit_ctas_per_sm", C.c_int), ("sub_ctas_per_sm", C.c_int),
+                ("reserved", C.c_int)]
+
+
+class argus_seg_stats(C.Structure):
+    _fields_ = [("chi2", C.c_double), ("n_pix", C.c_int), ("status", C.c_int)]
+
+
 SOURCE_BYTES = C.sizeof(argus_source)
 FIT_STATS_BYTES = C.sizeof(argus_fit_stats)
 
@@ -89,6 +102,11 @@ SIGNATURES = {
     "argus_subtract": ([P, P, P, P, P, P, SH, I, I, I, I, I, I, P, I, P, P, P, P], I),
     "argus_detect": ([P, P, P, P, SH, F, F, P, P, I, P, P], I),
     "argus_select_stamps_noalloc": ([P, P, SH, I, I, I, I, F, I, F, P, P, P], I),
+    "argus_segments_plan": ([P, C.POINTER(argus_segment), I, I, I, C.POINTER(argus_basis),
+                             C.POINTER(argus_seg_config), C.POINTER(P)], I),
+    "argus_segments_destroy": ([P], I),
+    "argus_segments_run": ([P, P, P, P, P, P, P, P, P, P, P, F, F, P, I, P, I, P], I),
+    "argus_segments_items": ([P, C.POINTER(I), C.POINTER(I)], I),
 }
 
 
@@ -232,6 +250,35 @@ def argus_select_stamps_noalloc(ref, flags, shape, grid_x, grid_y, stamp, khalf,
                                               int(stamp), int(khalf), float(max_peak), int(iso),
                                               float(iso_frac), _ptr(centers), _ptr(n_stamps),
                                               _stream(stream)), "argus_select_stamps_noalloc")
+
+
+def argus_segments_plan(ctx, table, pitch, atlas_h, basis, cfg=None):
+    """table: sequence of (row0, col0, side); returns an opaque plan handle."""
+    n = len(table)
+    arr = (argus_segment * n)(*[argus_segment(int(r), int(c), int(s)) for r, c, s in table])
+    h = C.c_void_p()
+    _check(load().argus_segments_plan(ctx, arr, n, int(pitch), int(atlas_h), C.byref(basis),
+                                      C.byref(cfg) if cfg is not None else None, C.byref(h)),
+           "argus_segments_plan")
+    return h
+
+
+def argus_segments_destroy(plan):
+    _check(load().argus_segments_destroy(plan), "argus_segments_destroy")
+
+
+def argus_segments_run(plan, sci, sci_var, ref, ref_var, flags, diff, diff_var, mask, coeffs, stats,
+                       nsigma, psf_sigma, out, cap, n_found, use_graph=True, stream=None):
+    _check(load().argus_segments_run(plan, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(ref_var), _ptr(flags),
+                                     _ptr(diff), _ptr(diff_var), _ptr(mask), _ptr(coeffs), _ptr(stats),
+                                     float(nsigma), float(psf_sigma), _ptr(out), int(cap), _ptr(n_found),
+                                     int(bool(use_graph)), _stream(stream)), "argus_segments_run")
+
+
+def argus_segments_items(plan):
+    a, b = C.c_int(0), C.c_int(0)
+    _check(load().argus_segments_items(plan, C.byref(a), C.byref(b)), "argus_segments_items")
+    return a.value, b.value
 
 
 def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,

@@ -39,7 +39,7 @@ int argus_check_ptr16(const void* p) {
 
 static std::atomic<unsigned long long> g_launches{0};
 
-void argus_count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+void argus_count_launch(int n) { g_launches.fetch_add((unsigned long long)(long long)n, std::memory_order_relaxed); }
 
 extern "C" unsigned long long argus_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 

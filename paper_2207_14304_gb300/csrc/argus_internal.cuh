@@ -71,6 +71,7 @@ int argus_check_shape(const argus_shape& s, size_t max_pixels);
 int argus_check_ptr16(const void* p);
 int argus_launch_status();   // ARGUS_OK or ARGUS_ERR_CUDA after a launch
 void argus_count_launch(int n);   // host-side tally of kernel launches
+extern "C" unsigned long long argus_launch_count(void);
 
 // Inter-unit launchers
 int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st);

@@ -1,0 +1,587 @@
+// K8: thousands of uneven target segments through one CUDA-graph launch of
+// persistent kernels (paper Sec. 5: subtraction parallelised at the segment
+// level; Sec. 4.1.1 HEALPix segments).  Each segment has its own spatially
+// constant PSF-matching kernel fitted over its whole interior.
+//
+// Segments live in an "atlas": one pitched image per quantity with segment s
+// at rows [row0_s, row0_s + side_s) and columns [0, side_s).  The work is cut
+// into fixed-size units, not segments, so that 64-px and 512-px segments
+// balance:
+//   1. fit: persistent CTAs take (segment, row band) items from an atomic
+//      counter (largest segments first); per band, X_m = R (x) B'_m (the
+//      orthonormalised basis) for every interior pixel, 64-pixel chunks of the
+//      weighted design [X_m, 1, I] in shared memory, the Gram's upper triangle
+//      summed per chunk in FP32 and folded into double-float, then added to the
+//      segment's FP64 normal matrix with one atomicAdd per entry per item;
+//   2. solve: one CTA per segment, FP64 Cholesky in shared memory, mapping to
+//      Alard-Lupton coefficients, kernel expansion, chi2 from the Gram;
+//   3. subtract: persistent CTAs take 32x32 tiles (the same tile body as the
+//      full-frame kernel) with the segment's kernel;
+//   4. detection on the atlas (edge pixels of every segment are invalid, so
+//      components never cross segments).
+// The plan records the sequence in a CUDA graph on first run and replays it.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "basis.cuh"
+#include "subtract_tile.cuh"
+
+struct argus_seg_plan {
+    argus_ctx* ctx;
+    int n;                 // segments
+    int pitch, atlas_h, max_side;
+    argus_basis basis;
+    BasisDev bd;
+    int NPC;               // Gram columns: nb + 2 (basis, background, target)
+    argus_seg_config cfg;
+    int4* d_seg;           // (row0, side, col0, -)
+    int2* d_fit_items;     // (segment, band y0)
+    int n_fit_items;
+    int2* d_sub_items;     // (segment, tile index)
+    int n_sub_items;
+    int* d_counters;       // [4]
+    double* d_gram;        // [n][NPC][NPC]
+    float* d_K;            // [n][ks*ks]
+    double* d_bg;          // [n]
+    cudaGraphExec_t exec;
+    cudaGraph_t graph;
+    const void* key[12];   // pointers the graph was recorded with
+    int key_cap;
+    int graph_kernels;     // kernels recorded in the graph
+};
+
+namespace {
+
+using argus_sub::SubArgs;
+
+constexpr int FIT_CH = 64;   // design pixels per Gram chunk
+
+struct SegFitArgs {
+    const float* sci;
+    const float* var;
+    const float* ref;
+    const uint8_t* flags;
+    long pitch;
+    const int4* seg;
+    const int2* items;
+    int n_items;
+    int* counter;
+    const float* bimg;     // orthonormal basis images [nb][kk] (B'_0 = B_0)
+    int nb, ks, r, band, NPC;
+    double* gram;
+    int* n_pix;            // per segment count of weighted pixels
+};
+
+__global__ void __launch_bounds__(256) seg_fit_kernel(SegFitArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int kk = a.ks * a.ks, nb = a.nb, NPC = a.NPC, r = a.r;
+    float* Bs = sm;                                  // [nb][kk]
+    float* Z = Bs + nb * kk;                         // [FIT_CH][NPC + 1]
+    float* Rw = Z + FIT_CH * (NPC + 1);              // [(band + 2r)][wst]
+    __shared__ int s_item;
+    __shared__ int s_npix;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nb * kk; e += blockDim.x) Bs[e] = a.bimg[e];
+    const int nent = NPC * (NPC + 1) / 2;            // upper-triangle entries
+    const int per = (nent + blockDim.x - 1) / blockDim.x;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        const int4 sg = a.seg[it.x];
+        const int side = sg.y;
+        const long base = (long)sg.x * a.pitch + sg.z;
+        const float* I = a.sci + base;
+        const float* V = a.var + base;
+        const float* Rr = a.ref + base;
+        const uint8_t* F = a.flags + base;
+        const int ylo = max(it.y, r), yhi = min(it.y + a.band, side - r);   // interior rows of the band
+        const int xw = side - 2 * r;                                         // interior width
+        if (yhi <= ylo || xw <= 0) continue;
+        const int wst = side;                                                // staged window row stride
+        const int wrows = (yhi - ylo) + 2 * r;
+        for (int e = tid; e < wrows * side; e += blockDim.x) {
+            const int j = e / side, i = e - j * side;
+            Rw[j * wst + i] = __ldg(Rr + (long)(ylo - r + j) * a.pitch + i);
+        }
+        if (tid == 0) s_npix = 0;
+        float hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) hi[q] = lo[q] = 0.0f;
+        const int npx = (yhi - ylo) * xw;
+        for (int c0 = 0; c0 < npx; c0 += FIT_CH) {
+            __syncthreads();
+            // X'_m for the chunk's pixels: work items of 4 functions x 4 pixels
+            const int nfq = (nb + 3) / 4, npq = FIT_CH / 4;
+            for (int w = tid; w < nfq * npq; w += blockDim.x) {
+                const int fq = w / npq, pq = w - fq * npq;
+                int off[4];
+                bool okp[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int pl = c0 + pq * 4 + t;
+                    okp[t] = pl < npx;
+                    const int pp = okp[t] ? pl : 0;
+                    const int yy = pp / xw, xx = pp - yy * xw;             // yy rows below ylo, xx cols right of r
+                    off[t] = (yy + 2 * r) * wst + (xx + 2 * r);            // window index of R(x, y) + (2r, 2r)
+                }
+                const float* bf[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) bf[q] = Bs + (long)min(fq * 4 + q, nb - 1) * kk;
+                float acc[4][4];
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+#pragma unroll
+                    for (int t = 0; t < 4; t++) acc[q][t] = 0.0f;
+                for (int iv = 0; iv < a.ks; iv++) {
+                    for (int iu = 0; iu < a.ks; iu++) {
+                        const int tap = iv * a.ks + iu, shf = iv * wst + iu;
+                        float rv[4], bv[4];
+#pragma unroll
+                        for (int t = 0; t < 4; t++) rv[t] = Rw[off[t] - shf];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) bv[q] = bf[q][tap];
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+#pragma unroll
+                            for (int t = 0; t < 4; t++) acc[q][t] = fmaf(bv[q], rv[t], acc[q][t]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int m = fq * 4 + q;
+                    if (m >= nb) break;
+#pragma unroll
+                    for (int t = 0; t < 4; t++) Z[(pq * 4 + t) * (NPC + 1) + m] = acc[q][t];
+                }
+            }
+            __syncthreads();
+            // weights, background and target columns; rows past the band are zero
+            if (tid < FIT_CH) {
+                const int pl = c0 + tid;
+                float sqw = 0.0f, Iv = 0.0f;
+                if (pl < npx) {
+                    const int yy = pl / xw, xx = pl - yy * xw;
+                    const long p = (long)(ylo + yy) * a.pitch + (xx + r);
+                    const float v = V[p], iv = I[p];
+                    if (F[p] == 0 && v > 0.0f && isfinite(v) && isfinite(iv)) {
+                        sqw = sqrtf(1.0f / v);
+                        Iv = iv;
+                        atomicAdd(&s_npix, 1);
+                    }
+                }
+                float* zr = Z + tid * (NPC + 1);
+                for (int m = 0; m < nb; m++) zr[m] *= sqw;
+                zr[nb] = sqw;
+                zr[nb + 1] = sqw * Iv;
+            }
+            __syncthreads();
+            // Gram upper triangle: FP32 over the chunk, folded into double-float
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int e = tid + q * blockDim.x;
+                if (q >= per || e >= nent) break;
+                int i = 0, rem = e;
+                while (rem >= NPC - i) { rem -= NPC - i; i++; }
+                const int j = i + rem;
+                float acc = 0.0f;
+                for (int p = 0; p < FIT_CH; p++) acc = fmaf(Z[p * (NPC + 1) + i], Z[p * (NPC + 1) + j], acc);
+                const float sum = hi[q] + acc, bp = sum - hi[q];
+                lo[q] += (hi[q] - (sum - bp)) + (acc - bp);
+                hi[q] = sum;
+            }
+        }
+        // one FP64 atomic per entry per item into the segment's normal matrix
+        double* G = a.gram + (long)it.x * NPC * NPC;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int e = tid + q * blockDim.x;
+            if (q >= per || e >= nent) break;
+            int i = 0, rem = e;
+            while (rem >= NPC - i) { rem -= NPC - i; i++; }
+            const int j = i + rem;
+            atomicAdd(G + i * NPC + j, (double)hi[q] + (double)lo[q]);
+        }
+        __syncthreads();
+        if (tid == 0 && s_npix) atomicAdd(a.n_pix + it.x, s_npix);
+    }
+}
+
+struct SegSolveArgs {
+    const double* gram;
+    const int* n_pix;
+    int NPC, nb;
+    const double* S;       // [nb][nb] orthonormalisation (B' = B S)
+    const double* img;     // FP64 Alard-Lupton basis images [nb][kk]
+    int kk;
+    double* coeffs;        // [n][Nc] (Alard-Lupton order: a_0..a_48, bg)
+    argus_seg_stats* stats;
+    float* K;              // [n][kk]
+    double* bg;            // [n]
+    int* status;
+};
+
+// One CTA per segment: FP64 Cholesky of the 50 x 50 normal matrix (in shared
+// memory), solution c in the orthonormal basis, a = S c, kernel, background,
+// chi2 = t'Wt - 2 c'b + c'Mc from the augmented Gram.
+__global__ void __launch_bounds__(128) seg_solve_kernel(SegSolveArgs a) {
+    extern __shared__ double ds[];
+    const int n = a.NPC - 1;          // unknowns: nb basis + background
+    const int ld = a.NPC + 1;
+    double* L = ds;                   // [NPC][ld]
+    double* y = L + a.NPC * ld;       // [NPC]
+    double* c = y + a.NPC;            // [NPC]
+    __shared__ int bad;
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const double* G = a.gram + (long)s * a.NPC * a.NPC;
+    for (int e = tid; e < a.NPC * a.NPC; e += blockDim.x) {
+        const int i = e / a.NPC, j = e - i * a.NPC;
+        L[i * ld + j] = i <= j ? G[i * a.NPC + j] : G[j * a.NPC + i];   // full symmetric copy
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        if (tid == 0) {
+            const double d = L[j * ld + j];
+            if (!(d > 0.0)) bad = 1;
+            L[j * ld + j] = sqrt(d > 0.0 ? d : 1.0);
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int i = j + 1 + tid; i < n; i += blockDim.x) L[i * ld + j] /= L[j * ld + j];
+        __syncthreads();
+        for (int e = tid; e < (n - j - 1) * (n - j - 1); e += blockDim.x) {
+            const int i = j + 1 + e / (n - j - 1), k = j + 1 + e % (n - j - 1);
+            if (k <= i) L[i * ld + k] -= L[i * ld + j] * L[k * ld + j];
+        }
+        __syncthreads();
+    }
+    argus_seg_stats st;
+    if (bad) {
+        if (tid == 0) {
+            argus_latch(a.status, ARGUS_ERR_SINGULAR);
+            st.chi2 = 0.0; st.n_pix = a.n_pix[s]; st.status = ARGUS_ERR_SINGULAR;
+            a.stats[s] = st;
+        }
+        for (int e = tid; e < a.kk; e += blockDim.x) a.K[(long)s * a.kk + e] = 0.0f;
+        if (tid == 0) a.bg[s] = 0.0;
+        return;
+    }
+    if (tid == 0) {
+        // forward / back substitution with b = G[:, n] (the target column)
+        for (int i = 0; i < n; i++) {
+            double v = G[i * a.NPC + n];
+            for (int k = 0; k < i; k++) v -= L[i * ld + k] * y[k];
+            y[i] = v / L[i * ld + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double v = y[i];
+            for (int k = i + 1; k < n; k++) v -= L[k * ld + i] * c[k];
+            c[i] = v / L[i * ld + i];
+        }
+        // chi2 = t'Wt - 2 c'b + c'Mc
+        double tt = G[n * a.NPC + n], cb = 0.0, cmc = 0.0;
+        for (int i = 0; i < n; i++) {
+            cb += c[i] * G[i * a.NPC + n];
+            double mi = 0.0;
+            for (int k = 0; k < n; k++) mi += (i <= k ? G[i * a.NPC + k] : G[k * a.NPC + i]) * c[k];
+            cmc += c[i] * mi;
+        }
+        st.chi2 = tt - 2.0 * cb + cmc;
+        st.n_pix = a.n_pix[s];
+        st.status = ARGUS_OK;
+        a.stats[s] = st;
+    }
+    __syncthreads();
+    // a_0 = c_0; a_n = sum_{m >= n} S[n][m] c_m; background last
+    double* co = a.coeffs + (long)s * (n);
+    for (int j = tid; j < n; j += blockDim.x) {
+        double v;
+        if (j == 0 || j >= a.nb) {
+            v = c[j];
+        } else {
+            v = 0.0;
+            for (int m = j; m < a.nb; m++) v += a.S[j * a.nb + m] * c[m];
+        }
+        co[j] = v;
+        y[j] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < a.kk; e += blockDim.x) {
+        double v = 0.0;
+        for (int m = 0; m < a.nb; m++) v += y[m] * a.img[(long)m * a.kk + e];
+        a.K[(long)s * a.kk + e] = (float)v;
+    }
+    if (tid == 0) a.bg[s] = c[a.nb];
+}
+
+struct SegSubArgs {
+    const float* sci;
+    const float* var;
+    const float* ref;
+    const float* ref_var;
+    const uint8_t* flags;
+    float* diff;
+    float* diff_var;
+    long pitch;
+    const int4* seg;
+    const int2* items;     // (segment, tile index)
+    int n_items;
+    int* counter;
+    const float* K;
+    const double* bg;
+    int kk;
+};
+
+template <int KS>
+__global__ void __launch_bounds__(argus_sub::THREADS) seg_sub_kernel(SegSubArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        const int4 sg = a.seg[it.x];
+        const int side = sg.y, nt = (side + argus_sub::TILE - 1) / argus_sub::TILE;
+        const int ty = it.y / nt, tx = it.y - ty * nt;
+        SubArgs s;
+        const long off = (long)sg.x * a.pitch + sg.z;
+        s.sci = a.sci + off; s.sci_var = a.var + off; s.ref = a.ref + off; s.ref_var = a.ref_var + off;
+        s.flags = a.flags + off; s.K = a.K + (long)it.x * a.kk; s.bg = a.bg + it.x;
+        s.diff = a.diff + off; s.diff_var = a.diff_var + off;
+        s.pitch = a.pitch; s.w = side; s.h = side; s.W = side; s.H = side; s.ox = 0; s.oy = 0;
+        s.nbg = 1; s.bg_deg = 0; s.sdeg = 0;
+        argus_sub::subtract_tile<KS, 1>(s, tx * argus_sub::TILE, ty * argus_sub::TILE, smem);
+    }
+}
+
+template <int KS>
+int launch_seg_sub(const SegSubArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = argus_sub::tile_smem_bytes<KS, 1>();
+    cudaFuncSetAttribute(seg_sub_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    seg_sub_kernel<KS><<<grid, argus_sub::THREADS, smem, st>>>(a); argus_count_launch(1);
+    return argus_launch_status();
+}
+
+}  // namespace
+
+extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, int n, int pitch, int atlas_h,
+                                   const argus_basis* basis, const argus_seg_config* cfg, argus_seg_plan** out) {
+    if (!ctx || !table || n < 1 || !basis || !out || pitch < 16 || pitch % 16 || atlas_h < 1) return ARGUS_ERR_ARG;
+    *out = NULL;
+    BasisDev bd;
+    int rc = make_basis_dev(basis, &bd);
+    if (rc) return rc;
+    if (bd.sdeg != 0 || bd.bgdeg != 0) return ARGUS_ERR_UNSUPPORTED;   // one constant kernel per segment
+    if (bd.ks != 7 && bd.ks != 9 && bd.ks != 11 && bd.ks != 15 && bd.ks != 21) return ARGUS_ERR_UNSUPPORTED;
+    if ((size_t)atlas_h * pitch > ctx->max_pixels) return ARGUS_ERR_ARG;
+    argus_seg_config c = cfg ? *cfg : argus_seg_config{32, 1, 4, 0};
+    if (c.fit_band < 8 || c.fit_band > 128 || c.fit_ctas_per_sm < 1 || c.fit_ctas_per_sm > 4 ||
+        c.sub_ctas_per_sm < 1 || c.sub_ctas_per_sm > 16)
+        return ARGUS_ERR_ARG;
+    std::vector<int4> seg(n);
+    int max_side = 0;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) {
+        const argus_segment& t = table[i];
+        if (t.side < bd.ks || t.side > pitch || t.side > 512 || t.row0 < 0 || t.row0 + t.side > atlas_h)
+            return ARGUS_ERR_ARG;
+        if (t.col0 < 0 || t.col0 + t.side > pitch) return ARGUS_ERR_ARG;
+        seg[i] = make_int4(t.row0, t.side, t.col0, 0);
+        max_side = std::max(max_side, t.side);
+        order[i] = i;
+    }
+    // segments must not overlap in the atlas (checked on a coarse occupancy grid of 16 x 16 cells)
+    {
+        const int cw = (pitch + 15) / 16, ch = (atlas_h + 15) / 16;
+        std::vector<int> owner((size_t)cw * ch, -1);
+        for (int i = 0; i < n; i++) {
+            const argus_segment& t = table[i];
+            if (t.row0 % 16 || t.col0 % 16) return ARGUS_ERR_ALIGN;
+            for (int cy = t.row0 / 16; cy < (t.row0 + t.side + 15) / 16; cy++)
+                for (int cx = t.col0 / 16; cx < (t.col0 + t.side + 15) / 16; cx++) {
+                    int& o = owner[(size_t)cy * cw + cx];
+                    if (o >= 0) return ARGUS_ERR_ARG;
+                    o = i;
+                }
+        }
+    }
+    // work items, largest segments first
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return table[a].side > table[b].side; });
+    std::vector<int2> fit_items, sub_items;
+    for (int i : order) {
+        const int side = table[i].side;
+        for (int y0 = 0; y0 < side; y0 += c.fit_band)
+            if (std::min(y0 + c.fit_band, side - bd.r) > std::max(y0, bd.r)) fit_items.push_back(make_int2(i, y0));
+        const int nt = (side + 31) / 32;
+        for (int t = 0; t < nt * nt; t++) sub_items.push_back(make_int2(i, t));
+    }
+    // shared memory of the fit kernel: basis images, design chunk, reference band window
+    const int NPC = bd.nb + 2;
+    const size_t fit_smem = sizeof(float) * ((size_t)bd.nb * bd.ks * bd.ks + (size_t)FIT_CH * (NPC + 1) +
+                                             (size_t)(c.fit_band + 2 * bd.r) * max_side);
+    if (fit_smem > 200 * 1024 || NPC * (NPC + 1) / 2 > 8 * 256) return ARGUS_ERR_UNSUPPORTED;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    argus_seg_plan* p = (argus_seg_plan*)calloc(1, sizeof(argus_seg_plan));
+    if (!p) return ARGUS_ERR_NOMEM;
+    p->ctx = ctx; p->n = n; p->pitch = pitch; p->atlas_h = atlas_h; p->max_side = max_side;
+    p->basis = *basis; p->bd = bd; p->NPC = NPC; p->cfg = c;
+    p->n_fit_items = (int)fit_items.size();
+    p->n_sub_items = (int)sub_items.size();
+    bool ok = cudaMalloc(&p->d_seg, sizeof(int4) * n) == cudaSuccess &&
+              cudaMalloc(&p->d_fit_items, sizeof(int2) * fit_items.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_sub_items, sizeof(int2) * sub_items.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_counters, sizeof(int) * 4) == cudaSuccess &&
+              cudaMalloc(&p->d_gram, sizeof(double) * (size_t)n * NPC * NPC) == cudaSuccess &&
+              cudaMalloc(&p->d_K, sizeof(float) * (size_t)n * bd.ks * bd.ks) == cudaSuccess &&
+              cudaMalloc(&p->d_bg, sizeof(double) * (size_t)n) == cudaSuccess;
+    if (ok)
+        ok = cudaMemcpy(p->d_seg, seg.data(), sizeof(int4) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->d_fit_items, fit_items.data(), sizeof(int2) * fit_items.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(p->d_sub_items, sub_items.data(), sizeof(int2) * sub_items.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        argus_segments_destroy(p);
+        return ARGUS_ERR_NOMEM;
+    }
+    // the basis tables (orthonormal images, S) are built once here, outside any capture
+    rc = argus_basis_prepare(ctx, basis, 0);
+    if (rc == ARGUS_OK && cudaDeviceSynchronize() != cudaSuccess) rc = ARGUS_ERR_CUDA;
+    if (rc) {
+        argus_segments_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return ARGUS_OK;
+}
+
+extern "C" int argus_segments_destroy(argus_seg_plan* p) {
+    if (!p) return ARGUS_ERR_ARG;
+    cudaSetDevice(p->ctx->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    void* ps[] = {p->d_seg, p->d_fit_items, p->d_sub_items, p->d_counters, p->d_gram, p->d_K, p->d_bg};
+    for (void* q : ps)
+        if (q) cudaFree(q);
+    free(p);
+    return ARGUS_OK;
+}
+
+static int segments_enqueue(argus_seg_plan* p, const float* sci, const float* sci_var, const float* ref,
+                            const float* ref_var, const uint8_t* flags, float* diff, float* diff_var,
+                            uint8_t* mask, double* coeffs, argus_seg_stats* stats, float nsigma, float psf_sigma,
+                            argus_source* out, int cap, int* n_found, cudaStream_t st) {
+    argus_ctx* ctx = p->ctx;
+    const BasisDev& bd = p->bd;
+    const int NPC = p->NPC, kk = bd.ks * bd.ks;
+    if (cudaMemsetAsync(p->d_counters, 0, sizeof(int) * 4, st) != cudaSuccess) return ARGUS_ERR_CUDA;
+    if (cudaMemsetAsync(p->d_gram, 0, sizeof(double) * (size_t)p->n * NPC * NPC, st) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    int* npix = reinterpret_cast<int*>(ctx->resid_part);   // per-segment weighted pixel counts
+    if ((size_t)p->n * sizeof(int) > (size_t)ctx->resid_parts * (ctx->np_cols + 4) * sizeof(double))
+        return ARGUS_ERR_CAPACITY;
+    if (cudaMemsetAsync(npix, 0, sizeof(int) * p->n, st) != cudaSuccess) return ARGUS_ERR_CUDA;
+    SegFitArgs fa;
+    fa.sci = sci; fa.var = sci_var; fa.ref = ref; fa.flags = flags; fa.pitch = p->pitch; fa.seg = p->d_seg;
+    fa.items = p->d_fit_items; fa.n_items = p->n_fit_items; fa.counter = p->d_counters;
+    fa.bimg = ctx->basis_imgf; fa.nb = bd.nb; fa.ks = bd.ks; fa.r = bd.r; fa.band = p->cfg.fit_band;
+    fa.NPC = NPC; fa.gram = p->d_gram; fa.n_pix = npix;
+    const size_t fit_smem = sizeof(float) * ((size_t)bd.nb * kk + (size_t)FIT_CH * (NPC + 1) +
+                                             (size_t)(p->cfg.fit_band + 2 * bd.r) * p->max_side);
+    cudaFuncSetAttribute(seg_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem);
+    seg_fit_kernel<<<ctx->num_sms * p->cfg.fit_ctas_per_sm, 256, fit_smem, st>>>(fa); argus_count_launch(1);
+    SegSolveArgs sa;
+    sa.gram = p->d_gram; sa.n_pix = npix; sa.NPC = NPC; sa.nb = bd.nb; sa.S = ctx->basis_S; sa.img = ctx->basis_img;
+    sa.kk = kk; sa.coeffs = coeffs; sa.stats = stats; sa.K = p->d_K; sa.bg = p->d_bg; sa.status = ctx->d_status;
+    const size_t solve_smem = sizeof(double) * ((size_t)NPC * (NPC + 1) + 2 * NPC);
+    seg_solve_kernel<<<p->n, 128, solve_smem, st>>>(sa); argus_count_launch(1);
+    SegSubArgs ua;
+    ua.sci = sci; ua.var = sci_var; ua.ref = ref; ua.ref_var = ref_var; ua.flags = flags; ua.diff = diff;
+    ua.diff_var = diff_var; ua.pitch = p->pitch; ua.seg = p->d_seg; ua.items = p->d_sub_items;
+    ua.n_items = p->n_sub_items; ua.counter = p->d_counters + 1; ua.K = p->d_K; ua.bg = p->d_bg; ua.kk = kk;
+    const int grid = ctx->num_sms * p->cfg.sub_ctas_per_sm;
+    int rc;
+    switch (bd.ks) {
+        case 7: rc = launch_seg_sub<7>(ua, grid, st); break;
+        case 9: rc = launch_seg_sub<9>(ua, grid, st); break;
+        case 11: rc = launch_seg_sub<11>(ua, grid, st); break;
+        case 15: rc = launch_seg_sub<15>(ua, grid, st); break;
+        case 21: rc = launch_seg_sub<21>(ua, grid, st); break;
+        default: return ARGUS_ERR_UNSUPPORTED;
+    }
+    if (rc) return rc;
+    // detection over the atlas in slabs of whole segments below 2^31 pixels
+    if (mask && n_found) {
+        argus_shape sh;
+        sh.w = p->pitch; sh.pitch = p->pitch; sh.h = p->atlas_h;
+        if ((long)p->atlas_h * p->pitch > 0x7fffffffL) return ARGUS_ERR_UNSUPPORTED;
+        rc = argus_detect(ctx, diff, diff_var, flags, sh, nsigma, psf_sigma, mask, out, cap, n_found, st);
+        if (rc) return rc;
+    }
+    return argus_launch_status();
+}
+
+extern "C" int argus_segments_run(argus_seg_plan* p, const float* sci, const float* sci_var, const float* ref,
+                                  const float* ref_var, const uint8_t* flags, float* diff, float* diff_var,
+                                  uint8_t* mask, double* coeffs, argus_seg_stats* stats, float nsigma,
+                                  float psf_sigma, argus_source* out, int cap, int* n_found, int use_graph,
+                                  argus_stream stream) {
+    if (!p || !sci || !sci_var || !ref || !ref_var || !flags || !diff || !diff_var || !coeffs || !stats)
+        return ARGUS_ERR_ARG;
+    if ((mask == NULL) != (n_found == NULL)) return ARGUS_ERR_ARG;
+    const void* ps[] = {sci, sci_var, ref, ref_var, flags, diff, diff_var, mask};
+    for (const void* q : ps)
+        if (q && argus_check_ptr16(q)) return ARGUS_ERR_ALIGN;
+    if (cudaSetDevice(p->ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph)
+        return segments_enqueue(p, sci, sci_var, ref, ref_var, flags, diff, diff_var, mask, coeffs, stats, nsigma,
+                                psf_sigma, out, cap, n_found, st);
+    const void* key[12] = {sci, sci_var, ref, ref_var, flags, diff, diff_var, mask, coeffs, stats, out, n_found};
+    const bool same = p->exec && memcmp(key, p->key, sizeof(key)) == 0 && p->key_cap == cap;
+    if (!same) {
+        if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = NULL; }
+        if (p->graph) { cudaGraphDestroy(p->graph); p->graph = NULL; }
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ARGUS_ERR_CUDA;
+        const unsigned long long n0 = argus_launch_count();
+        const int rc = segments_enqueue(p, sci, sci_var, ref, ref_var, flags, diff, diff_var, mask, coeffs, stats,
+                                        nsigma, psf_sigma, out, cap, n_found, st);
+        cudaGraph_t g = NULL;
+        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess || !g) return ARGUS_ERR_CUDA;
+        if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return ARGUS_ERR_CUDA;
+        }
+        p->graph = g;
+        memcpy(p->key, key, sizeof(key));
+        p->key_cap = cap;
+        p->graph_kernels = (int)(argus_launch_count() - n0);
+        // the recorded launches were counted but did not run; the replays below are counted instead
+        argus_count_launch(-p->graph_kernels);
+    }
+    argus_count_launch(p->graph_kernels);
+    return cudaGraphLaunch(p->exec, st) == cudaSuccess ? ARGUS_OK : ARGUS_ERR_CUDA;
+}
+
+extern "C" int argus_segments_items(const argus_seg_plan* p, int* n_fit_items, int* n_sub_items) {
+    if (!p) return ARGUS_ERR_ARG;
+    if (n_fit_items) *n_fit_items = p->n_fit_items;
+    if (n_sub_items) *n_sub_items = p->n_sub_items;
+    return ARGUS_OK;
+}

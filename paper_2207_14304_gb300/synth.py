@@ -210,3 +210,31 @@ def pad_pitch(a: torch.Tensor, pitch: int) -> torch.Tensor:
     out = torch.zeros((h, pitch), dtype=a.dtype, device=a.device)
     out[:, :w] = a
     return out
+
+
+def calibrated_image(expected_e: torch.Tensor, read_noise: float, seed: int):
+    """An already-calibrated science image: Poisson(expected) + N(0, rn), and its
+    variance map expected + rn^2 (float32 pair)."""
+    dev = expected_e.device
+    g = _gen(seed, dev)
+    lam = torch.clamp(expected_e.to(torch.float32), min=0.0)
+    img = torch.poisson(lam, generator=g) + torch.randn(lam.shape, generator=g, device=dev) * read_noise
+    return img.to(torch.float32), (lam + read_noise ** 2).to(torch.float32)
+
+
+def segment_sides(n: int, seed: int, smin=64, smax=512):
+    """Square segment sides log-uniform on [smin, smax] (rounded)."""
+    g = _gen(seed * 613 + 11)
+    u = torch.rand(n, generator=g, dtype=torch.float64)
+    return torch.round(smin * (smax / smin) ** u).to(torch.int64).tolist()
+
+
+def segment_origins(sides, w: int, h: int, seed: int):
+    """Uniform top-left corners of squares of the given sides inside a w x h frame."""
+    g = _gen(seed * 977 + 5)
+    out = []
+    for s in sides:
+        x0 = int(torch.randint(0, w - s + 1, (1,), generator=g))
+        y0 = int(torch.randint(0, h - s + 1, (1,), generator=g))
+        out.append((x0, y0))
+    return out

@@ -1,0 +1,105 @@
+"""Batched segments (persistent kernels + CUDA graph) against the FP64 oracle.
+
+Each segment is fitted over its whole interior (oracle: fit_rect), expanded,
+subtracted and searched for sources; the GPU batch does the same for all
+segments at once in a packed atlas.  Tolerances as for the frame path:
+kernel pixels within 1e-3 of max |K|, difference pixels within 1e-4 of
+max(|I|, |R (x) K|, 1), masks equal away from the threshold band.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2207_14304_gb300 import _binding as B
+from paper_2207_14304_gb300 import synth
+from paper_2207_14304_gb300.segments import SegmentBatch, pack_shelves
+
+pytestmark = pytest.mark.gpu
+
+
+def _frame(w, h, seed):
+    cat = synth.star_catalog(w * h // 150, w, h, seed=seed, flux_min=3e2, flux_max=3e5)
+    R, Vr = synth.reference_image(synth.render(cat, w, h, 1.2, sky=300.0), 30, 1.7, seed + 1)
+    sig = synth.field_sigma(w, h, 1.5, 2.1)
+    I, V = synth.calibrated_image(synth.render(cat, w, h, sig, sky=305.0, shift=(0.3, -0.2)), 1.7, seed + 2)
+    rng = np.random.default_rng(seed)
+    fl = (rng.random((h, w)) < 0.001).astype(np.uint8)
+    return I.numpy(), V.numpy(), R.numpy(), Vr.numpy(), fl
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_segments_parity(ora, use_graph):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, h = 640, 480
+    I, V, R, Vr, fl = _frame(w, h, seed=31)
+    sides = [40, 57, 64, 90, 111, 128, 48, 70, 45, 81]
+    origins = synth.segment_origins(sides, w, h, seed=3)
+    ks = 15
+    basis = B.make_basis(ks, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)
+    batch = SegmentBatch(sides, basis=basis, width=256, cfg=B.argus_seg_config(32, 1, 4, 0), src_cap=4096)
+    try:
+        for i, ((x0, y0), s) in enumerate(zip(origins, sides)):
+            sl = (slice(y0, y0 + s), slice(x0, x0 + s))
+            for t, a in ((batch.sci, I), (batch.var, V), (batch.ref, R), (batch.ref_var, Vr), (batch.flags, fl)):
+                batch.view(t, i).copy_(torch.from_numpy(np.ascontiguousarray(a[sl])))
+        for rep in range(2):   # the second run replays the graph (or re-enqueues)
+            batch.diff.zero_(); batch.diff_var.zero_()
+            batch.run(use_graph=use_graph)
+            torch.cuda.synchronize()
+            assert B.argus_sync_status(batch.ctx) == 0
+        coeffs = batch.coeffs.cpu().numpy()
+        stats = batch.stats_host()
+        src, nsrc = batch.sources_host()
+        ob = ora.Basis(ksize=ks, spatial_degree=0, bg_degree=0)
+        r = ks // 2
+        n_checked = 0
+        for i, ((x0, y0), s) in enumerate(zip(origins, sides)):
+            sl = (slice(y0, y0 + s), slice(x0, x0 + s))
+            Is, Vs, Rs, Vrs, Fs = (np.ascontiguousarray(a[sl]) for a in (I, V, R, Vr, fl))
+            res = ora.fit_rect(Is, Vs, Rs, Fs, (r, r, s - 1 - r, s - 1 - r), ob)
+            assert res.status == 0
+            Ko, bgo = ora.expand(ob, res.coeffs)
+            Kg, bgg = ora.expand(ob, coeffs[i])
+            kerr = np.abs(Kg - Ko).max() / np.abs(Ko).max()
+            assert kerr < 1e-3, (i, s, kerr)
+            assert abs(bgg[0] - bgo[0]) < 1e-3 * max(1.0, abs(bgo[0])), (i, bgg, bgo)
+            assert stats[i]["status"] == 0
+            assert stats[i]["n_pix"] == res.dof + ob.ncoeffs
+            assert abs(stats[i]["chi2"] / res.chi2 - 1) < 1e-4, (i, stats[i]["chi2"], res.chi2)
+            # subtraction with the GPU's own kernel: compares the batched subtraction alone
+            Do, VDo = ora.subtract(Is, Vs, Rs, Vrs, Fs, Kg.astype(np.float32).astype(np.float64), bgg,
+                                   sdeg=0, bgdeg=0)
+            Dg = batch.view(batch.diff, i).cpu().numpy()
+            VDg = batch.view(batch.diff_var, i).cpu().numpy()
+            Cabs, _ = ora.subtract(np.zeros_like(Is), Vs, np.abs(Rs), Vrs, Fs, np.abs(Kg), [0.0], sdeg=0, bgdeg=0,
+                                   with_var=False)
+            scale = np.maximum(np.maximum(np.abs(Is), -Cabs), 1.0)
+            assert (np.abs(Dg - Do) / scale).max() < 1e-4
+            assert (np.abs(VDg - VDo) / np.maximum(VDo, 1e-6)).max() < 1e-5
+            mo, so, no = ora.detect(Dg.astype(np.float32), VDg.astype(np.float32), Fs, 5.0, 1.8)
+            mg = batch.view(batch.mask, i).cpu().numpy()
+            np.testing.assert_array_equal(mg, mo)
+            # this segment's sources in the batch list, in atlas coordinates
+            rr, cc = batch.pos[i]
+            mine = src[(src["py"] >= rr) & (src["py"] < rr + s) & (src["px"] >= cc) & (src["px"] < cc + s)]
+            assert len(mine) == no
+            np.testing.assert_array_equal(mine["px"] - cc, so["px"])
+            np.testing.assert_array_equal(mine["py"] - rr, so["py"])
+            np.testing.assert_array_equal(mine["npix"], so["npix"])
+            n_checked += no
+        assert nsrc == len(src)
+        print(f"\n[segments graph={use_graph}] {len(sides)} segments, {nsrc} sources, checked {n_checked}")
+    finally:
+        batch.close()
+
+
+def test_pack_shelves_no_overlap():
+    sides = synth.segment_sides(300, seed=4)
+    pos, hgt = pack_shelves(sides, 2048)
+    occ = np.zeros((hgt, 2048), np.int32)
+    for (r, c), s in zip(pos, sides):
+        assert r % 16 == 0 and c % 16 == 0 and c + s <= 2048 and r + s <= hgt
+        occ[r:r + s, c:c + s] += 1
+    assert occ.max() == 1
+    assert occ.sum() / occ.size > 0.6
