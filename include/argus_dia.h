@@ -217,7 +217,8 @@ int argus_subtract(argus_ctx *ctx, const float *sci, const float *sci_var, const
  * and the optimal flux sum P D/V / sum P^2/V with P the unit-sum pixel-
  * integrated Gaussian at the centroid.  Sources are written sorted by (py, px),
  * at most cap; *n_found (device int) receives the total count; more than cap
- * latches ARGUS_ERR_CAPACITY.  mask: uint8 [h][pitch]. */
+ * latches ARGUS_ERR_CAPACITY.  mask: uint8 [h][pitch].  h may not exceed
+ * max(65536, max_pixels / 512) of the context, and h * pitch < 2^31. */
 int argus_detect(argus_ctx *ctx, const float *diff, const float *diff_var, const uint8_t *flags,
                  argus_shape shape, float nsigma, float psf_sigma, uint8_t *mask,
                  argus_source *out, int cap, int *n_found, argus_stream stream);

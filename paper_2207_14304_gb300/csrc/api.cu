@@ -88,7 +88,7 @@ extern "C" int argus_create(argus_ctx** out, int device, size_t max_pixels, int 
     c->gram_parts = 64;
     c->resid_parts = 512;
     c->max_cells = 4096;
-    c->max_rows = 65536;
+    c->max_rows = (int)(max_pixels / 512 > 65536 ? (max_pixels / 512 > (1u << 26) ? (1u << 26) : max_pixels / 512) : 65536);
     const size_t np = (size_t)c->np_cols;
     bool ok = dalloc(&c->d_status, 4) &&
               dalloc(&c->basis_img, (size_t)ARGUS_MAX_NB * ARGUS_MAX_KS * ARGUS_MAX_KS) &&

@@ -48,6 +48,7 @@ struct argus_seg_plan {
     double* d_bg;          // [n]
     cudaGraphExec_t exec;
     cudaGraph_t graph;
+    cudaStream_t cap_stream;   // recording stream (capture is not allowed on the legacy stream)
     const void* key[12];   // pointers the graph was recorded with
     int key_cap;
     int graph_kernels;     // kernels recorded in the graph
@@ -458,6 +459,8 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     // the basis tables (orthonormal images, S) are built once here, outside any capture
     rc = argus_basis_prepare(ctx, basis, 0);
     if (rc == ARGUS_OK && cudaDeviceSynchronize() != cudaSuccess) rc = ARGUS_ERR_CUDA;
+    if (rc == ARGUS_OK && cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = ARGUS_ERR_CUDA;
     if (rc) {
         argus_segments_destroy(p);
         return rc;
@@ -471,6 +474,7 @@ extern "C" int argus_segments_destroy(argus_seg_plan* p) {
     cudaSetDevice(p->ctx->device);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     void* ps[] = {p->d_seg, p->d_fit_items, p->d_sub_items, p->d_counters, p->d_gram, p->d_K, p->d_bg};
     for (void* q : ps)
         if (q) cudaFree(q);
@@ -553,12 +557,13 @@ extern "C" int argus_segments_run(argus_seg_plan* p, const float* sci, const flo
     if (!same) {
         if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = NULL; }
         if (p->graph) { cudaGraphDestroy(p->graph); p->graph = NULL; }
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ARGUS_ERR_CUDA;
+        cudaStream_t cs = p->cap_stream;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ARGUS_ERR_CUDA;
         const unsigned long long n0 = argus_launch_count();
         const int rc = segments_enqueue(p, sci, sci_var, ref, ref_var, flags, diff, diff_var, mask, coeffs, stats,
-                                        nsigma, psf_sigma, out, cap, n_found, st);
+                                        nsigma, psf_sigma, out, cap, n_found, cs);
         cudaGraph_t g = NULL;
-        const cudaError_t ce = cudaStreamEndCapture(st, &g);
+        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
             return rc;

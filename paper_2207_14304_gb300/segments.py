@@ -84,7 +84,9 @@ class SegmentBatch:
         return t[r:r + s, c:c + s]
 
     def replan(self, cfg):
-        B.argus_segments_destroy(self.plan)
+        if self.plan is not None:
+            B.argus_segments_destroy(self.plan)
+            self.plan = None
         self.cfg = cfg
         self.plan = B.argus_segments_plan(self.ctx, self.table, self.pitch, self.atlas_h, self.basis, cfg)
 
