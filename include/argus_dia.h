@@ -245,7 +245,7 @@ typedef struct {
 
 /* Launch shape of the batched kernels (picked by the autotuner). */
 typedef struct {
-    int fit_band;          /* rows per fit work unit (8..128) */
+    int fit_band;          /* reserved for the fit work-unit height (the kernel uses 8-row bands) */
     int fit_ctas_per_sm;   /* persistent fit CTAs per SM (1..4) */
     int sub_ctas_per_sm;   /* persistent subtraction CTAs per SM (1..16) */
     int reserved;

@@ -58,7 +58,15 @@ namespace {
 
 using argus_sub::SubArgs;
 
-constexpr int FIT_CH = 64;   // design pixels per Gram chunk
+// Fit work unit: a band of FIT_ROWS interior rows of one segment, processed
+// in chunks of FIT_ROWS x 32 pixels.  One warp per group of FG basis
+// functions: each lane owns one pixel column of the chunk and accumulates
+// FIT_ROWS x FG outputs while streaming a window of reference values and
+// broadcast basis taps (stored [tap][function] so FG taps are one vector load).
+constexpr int FIT_ROWS = 8;
+constexpr int FIT_COLS = 32;
+constexpr int FIT_CH = FIT_ROWS * FIT_COLS;   // design pixels per Gram chunk
+constexpr int FG = 8;                         // functions per warp group
 
 struct SegFitArgs {
     const float* sci;
@@ -71,23 +79,40 @@ struct SegFitArgs {
     int n_items;
     int* counter;
     const float* bimg;     // orthonormal basis images [nb][kk] (B'_0 = B_0)
-    int nb, ks, r, band, NPC;
+    int nb, ks, r, NPC, ngroups;
     double* gram;
     int* n_pix;            // per segment count of weighted pixels
 };
 
+template <int KS>
 __global__ void __launch_bounds__(256) seg_fit_kernel(SegFitArgs a) {
+    constexpr int R = (KS - 1) / 2, KK = KS * KS;
+    constexpr int WR = FIT_ROWS + KS - 1;             // window rows per column
     extern __shared__ __align__(16) float sm[];
-    const int kk = a.ks * a.ks, nb = a.nb, NPC = a.NPC, r = a.r;
-    float* Bs = sm;                                  // [nb][kk]
-    float* Z = Bs + nb * kk;                         // [FIT_CH][NPC + 1]
-    float* Rw = Z + FIT_CH * (NPC + 1);              // [(band + 2r)][wst]
+    const int nb = a.nb, NPC = a.NPC, ng = a.ngroups;
+    const int ZS = NPC + 1;                           // Z row stride
+    float* Bt = sm;                                   // [ng][KK][FG] transposed taps
+    float* Z = Bt + ng * KK * FG;                     // [FIT_CH][ZS]
+    float* Rw = Z + FIT_CH * ZS;                      // [WR][512 + 2R]
+    constexpr int WST = 512 + 2 * R;
     __shared__ int s_item;
     __shared__ int s_npix;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < nb * kk; e += blockDim.x) Bs[e] = a.bimg[e];
-    const int nent = NPC * (NPC + 1) / 2;            // upper-triangle entries
-    const int per = (nent + blockDim.x - 1) / blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < ng * KK * FG; e += blockDim.x) {
+        const int f = e % FG, t = (e / FG) % KK, gi = e / (FG * KK);
+        const int m = gi * FG + f;
+        Bt[e] = m < nb ? a.bimg[(long)m * KK + t] : 0.0f;
+    }
+    // Gram blocks: 4x4 entry blocks of the upper triangle of NPC x NPC
+    const int nbk = (NPC + 3) / 4;
+    const int nblk = nbk * (nbk + 1) / 2;
+    int bi = 0, bj = 0;
+    {
+        int rem = tid;
+        while (bi < nbk && rem >= nbk - bi) { rem -= nbk - bi; bi++; }
+        bj = bi + rem;
+    }
+    const bool gram_thread = tid < nblk;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(a.counter, 1);
@@ -98,120 +123,136 @@ __global__ void __launch_bounds__(256) seg_fit_kernel(SegFitArgs a) {
         const int4 sg = a.seg[it.x];
         const int side = sg.y;
         const long base = (long)sg.x * a.pitch + sg.z;
-        const float* I = a.sci + base;
-        const float* V = a.var + base;
-        const float* Rr = a.ref + base;
-        const uint8_t* F = a.flags + base;
-        const int ylo = max(it.y, r), yhi = min(it.y + a.band, side - r);   // interior rows of the band
-        const int xw = side - 2 * r;                                         // interior width
+        const int ylo = max(it.y, R), yhi = min(it.y + FIT_ROWS, side - R);
+        const int xw = side - 2 * R;
         if (yhi <= ylo || xw <= 0) continue;
-        const int wst = side;                                                // staged window row stride
-        const int wrows = (yhi - ylo) + 2 * r;
-        for (int e = tid; e < wrows * side; e += blockDim.x) {
+        // reference window: rows ylo - R .. ylo + FIT_ROWS - 1 + R, all columns
+        for (int e = tid; e < WR * side; e += blockDim.x) {
             const int j = e / side, i = e - j * side;
-            Rw[j * wst + i] = __ldg(Rr + (long)(ylo - r + j) * a.pitch + i);
+            const int yy = ylo - R + j;
+            Rw[j * WST + i] = yy < side ? __ldg(a.ref + base + (long)yy * a.pitch + i) : 0.0f;
         }
         if (tid == 0) s_npix = 0;
-        float hi[8], lo[8];
+        float hi[16], lo[16];
 #pragma unroll
-        for (int q = 0; q < 8; q++) hi[q] = lo[q] = 0.0f;
-        const int npx = (yhi - ylo) * xw;
-        for (int c0 = 0; c0 < npx; c0 += FIT_CH) {
+        for (int q = 0; q < 16; q++) hi[q] = lo[q] = 0.0f;
+        for (int c0 = 0; c0 < xw; c0 += FIT_COLS) {
             __syncthreads();
-            // X'_m for the chunk's pixels: work items of 4 functions x 4 pixels
-            const int nfq = (nb + 3) / 4, npq = FIT_CH / 4;
-            for (int w = tid; w < nfq * npq; w += blockDim.x) {
-                const int fq = w / npq, pq = w - fq * npq;
-                int off[4];
-                bool okp[4];
+            // convolution: warp = function group, lane = column
+            if (warp < ng) {
+                const int xi = min(c0 + lane, xw - 1);   // interior column (clamped; extra lanes discarded)
+                float acc[FIT_ROWS][FG];
 #pragma unroll
-                for (int t = 0; t < 4; t++) {
-                    const int pl = c0 + pq * 4 + t;
-                    okp[t] = pl < npx;
-                    const int pp = okp[t] ? pl : 0;
-                    const int yy = pp / xw, xx = pp - yy * xw;             // yy rows below ylo, xx cols right of r
-                    off[t] = (yy + 2 * r) * wst + (xx + 2 * r);            // window index of R(x, y) + (2r, 2r)
-                }
-                const float* bf[4];
+                for (int j = 0; j < FIT_ROWS; j++)
 #pragma unroll
-                for (int q = 0; q < 4; q++) bf[q] = Bs + (long)min(fq * 4 + q, nb - 1) * kk;
-                float acc[4][4];
+                    for (int f = 0; f < FG; f++) acc[j][f] = 0.0f;
+                const float* bt = Bt + warp * KK * FG;
+#pragma unroll 1
+                for (int iu = 0; iu < KS; iu++) {
+                    // column x - du = (xi + R) - (iu - R) = xi + 2R - iu
+                    float col[WR];
 #pragma unroll
-                for (int q = 0; q < 4; q++)
+                    for (int m = 0; m < WR; m++) col[m] = Rw[m * WST + xi + 2 * R - iu];
 #pragma unroll
-                    for (int t = 0; t < 4; t++) acc[q][t] = 0.0f;
-                for (int iv = 0; iv < a.ks; iv++) {
-                    for (int iu = 0; iu < a.ks; iu++) {
-                        const int tap = iv * a.ks + iu, shf = iv * wst + iu;
-                        float rv[4], bv[4];
+                    for (int iv = 0; iv < KS; iv++) {
+                        float kv[FG];
+                        *reinterpret_cast<float4*>(kv) = *reinterpret_cast<const float4*>(bt + (iv * KS + iu) * FG);
+                        *reinterpret_cast<float4*>(kv + 4) =
+                            *reinterpret_cast<const float4*>(bt + (iv * KS + iu) * FG + 4);
 #pragma unroll
-                        for (int t = 0; t < 4; t++) rv[t] = Rw[off[t] - shf];
+                        for (int j = 0; j < FIT_ROWS; j++) {
+                            // row y - dv = (ylo + j) - (iv - R) -> window row j + 2R - iv
+                            const float rv = col[j + 2 * R - iv];
 #pragma unroll
-                        for (int q = 0; q < 4; q++) bv[q] = bf[q][tap];
-#pragma unroll
-                        for (int q = 0; q < 4; q++)
-#pragma unroll
-                            for (int t = 0; t < 4; t++) acc[q][t] = fmaf(bv[q], rv[t], acc[q][t]);
+                            for (int f = 0; f < FG; f++) acc[j][f] = fmaf(kv[f], rv, acc[j][f]);
+                        }
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int m = fq * 4 + q;
-                    if (m >= nb) break;
+                for (int j = 0; j < FIT_ROWS; j++)
 #pragma unroll
-                    for (int t = 0; t < 4; t++) Z[(pq * 4 + t) * (NPC + 1) + m] = acc[q][t];
-                }
+                    for (int f = 0; f < FG; f++) {
+                        const int m = warp * FG + f;
+                        if (m < nb) Z[(j * FIT_COLS + lane) * ZS + m] = acc[j][f];
+                    }
             }
             __syncthreads();
-            // weights, background and target columns; rows past the band are zero
-            if (tid < FIT_CH) {
-                const int pl = c0 + tid;
+            // weights, background and target columns; pixels outside the band are zero
+            {
+                const int j = tid / FIT_COLS, l = tid % FIT_COLS;
+                const int y = ylo + j, xi = c0 + l;
                 float sqw = 0.0f, Iv = 0.0f;
-                if (pl < npx) {
-                    const int yy = pl / xw, xx = pl - yy * xw;
-                    const long p = (long)(ylo + yy) * a.pitch + (xx + r);
-                    const float v = V[p], iv = I[p];
-                    if (F[p] == 0 && v > 0.0f && isfinite(v) && isfinite(iv)) {
+                if (y < yhi && xi < xw) {
+                    const long p = base + (long)y * a.pitch + (xi + R);
+                    const float v = a.var[p], iv = a.sci[p];
+                    if (a.flags[p] == 0 && v > 0.0f && isfinite(v) && isfinite(iv)) {
                         sqw = sqrtf(1.0f / v);
                         Iv = iv;
                         atomicAdd(&s_npix, 1);
                     }
                 }
-                float* zr = Z + tid * (NPC + 1);
+                float* zr = Z + tid * ZS;
                 for (int m = 0; m < nb; m++) zr[m] *= sqw;
                 zr[nb] = sqw;
                 zr[nb + 1] = sqw * Iv;
+                for (int m = nb + 2; m < ZS; m++) zr[m] = 0.0f;
             }
             __syncthreads();
-            // Gram upper triangle: FP32 over the chunk, folded into double-float
+            // Gram 4x4 block per thread: FP32 over the chunk, folded into double-float
+            if (gram_thread) {
+                float acc[16];
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int e = tid + q * blockDim.x;
-                if (q >= per || e >= nent) break;
-                int i = 0, rem = e;
-                while (rem >= NPC - i) { rem -= NPC - i; i++; }
-                const int j = i + rem;
-                float acc = 0.0f;
-                for (int p = 0; p < FIT_CH; p++) acc = fmaf(Z[p * (NPC + 1) + i], Z[p * (NPC + 1) + j], acc);
-                const float sum = hi[q] + acc, bp = sum - hi[q];
-                lo[q] += (hi[q] - (sum - bp)) + (acc - bp);
-                hi[q] = sum;
+                for (int q = 0; q < 16; q++) acc[q] = 0.0f;
+                for (int p = 0; p < FIT_CH; p++) {
+                    const float* zp = Z + p * ZS;
+                    float zi[4], zj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        zi[u] = (bi * 4 + u < NPC) ? zp[bi * 4 + u] : 0.0f;
+                        zj[u] = (bj * 4 + u < NPC) ? zp[bj * 4 + u] : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+#pragma unroll
+                        for (int v = 0; v < 4; v++) acc[u * 4 + v] = fmaf(zi[u], zj[v], acc[u * 4 + v]);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const float sum = hi[q] + acc[q], bp = sum - hi[q];
+                    lo[q] += (hi[q] - (sum - bp)) + (acc[q] - bp);
+                    hi[q] = sum;
+                }
             }
         }
-        // one FP64 atomic per entry per item into the segment's normal matrix
-        double* G = a.gram + (long)it.x * NPC * NPC;
+        // one FP64 atomic per entry per item into the segment's normal matrix (upper triangle)
+        if (gram_thread) {
+            double* G = a.gram + (long)it.x * NPC * NPC;
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int e = tid + q * blockDim.x;
-            if (q >= per || e >= nent) break;
-            int i = 0, rem = e;
-            while (rem >= NPC - i) { rem -= NPC - i; i++; }
-            const int j = i + rem;
-            atomicAdd(G + i * NPC + j, (double)hi[q] + (double)lo[q]);
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    const int i = bi * 4 + u, j = bj * 4 + v;
+                    if (i < NPC && j < NPC && i <= j) atomicAdd(G + i * NPC + j, (double)hi[u * 4 + v] + (double)lo[u * 4 + v]);
+                }
         }
         __syncthreads();
         if (tid == 0 && s_npix) atomicAdd(a.n_pix + it.x, s_npix);
     }
+}
+
+template <int KS>
+size_t seg_fit_smem(int nb, int NPC) {
+    const int ng = (nb + FG - 1) / FG;
+    return sizeof(float) * ((size_t)ng * KS * KS * FG + (size_t)FIT_CH * (NPC + 1) +
+                            (size_t)(FIT_ROWS + KS - 1) * (512 + KS - 1));
+}
+
+template <int KS>
+int launch_seg_fit(const SegFitArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = seg_fit_smem<KS>(a.nb, a.NPC);
+    cudaFuncSetAttribute(seg_fit_kernel<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    seg_fit_kernel<KS><<<grid, 256, smem, st>>>(a); argus_count_launch(1);
+    return argus_launch_status();
 }
 
 struct SegSolveArgs {
@@ -421,16 +462,17 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     std::vector<int2> fit_items, sub_items;
     for (int i : order) {
         const int side = table[i].side;
-        for (int y0 = 0; y0 < side; y0 += c.fit_band)
-            if (std::min(y0 + c.fit_band, side - bd.r) > std::max(y0, bd.r)) fit_items.push_back(make_int2(i, y0));
+        for (int y0 = bd.r; y0 < side - bd.r; y0 += FIT_ROWS) fit_items.push_back(make_int2(i, y0));
         const int nt = (side + 31) / 32;
         for (int t = 0; t < nt * nt; t++) sub_items.push_back(make_int2(i, t));
     }
-    // shared memory of the fit kernel: basis images, design chunk, reference band window
+    // shared memory of the fit kernel: transposed basis taps, design chunk, reference window
     const int NPC = bd.nb + 2;
-    const size_t fit_smem = sizeof(float) * ((size_t)bd.nb * bd.ks * bd.ks + (size_t)FIT_CH * (NPC + 1) +
-                                             (size_t)(c.fit_band + 2 * bd.r) * max_side);
-    if (fit_smem > 200 * 1024 || NPC * (NPC + 1) / 2 > 8 * 256) return ARGUS_ERR_UNSUPPORTED;
+    const int ng = (bd.nb + FG - 1) / FG;
+    const size_t fit_smem = sizeof(float) * ((size_t)ng * bd.ks * bd.ks * FG + (size_t)FIT_CH * (NPC + 1) +
+                                             (size_t)(FIT_ROWS + bd.ks - 1) * (512 + bd.ks - 1));
+    const int nbk = (NPC + 3) / 4;
+    if (fit_smem > 220 * 1024 || ng > 8 || nbk * (nbk + 1) / 2 > 256) return ARGUS_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     argus_seg_plan* p = (argus_seg_plan*)calloc(1, sizeof(argus_seg_plan));
     if (!p) return ARGUS_ERR_NOMEM;
@@ -499,12 +541,19 @@ static int segments_enqueue(argus_seg_plan* p, const float* sci, const float* sc
     SegFitArgs fa;
     fa.sci = sci; fa.var = sci_var; fa.ref = ref; fa.flags = flags; fa.pitch = p->pitch; fa.seg = p->d_seg;
     fa.items = p->d_fit_items; fa.n_items = p->n_fit_items; fa.counter = p->d_counters;
-    fa.bimg = ctx->basis_imgf; fa.nb = bd.nb; fa.ks = bd.ks; fa.r = bd.r; fa.band = p->cfg.fit_band;
-    fa.NPC = NPC; fa.gram = p->d_gram; fa.n_pix = npix;
-    const size_t fit_smem = sizeof(float) * ((size_t)bd.nb * kk + (size_t)FIT_CH * (NPC + 1) +
-                                             (size_t)(p->cfg.fit_band + 2 * bd.r) * p->max_side);
-    cudaFuncSetAttribute(seg_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_smem);
-    seg_fit_kernel<<<ctx->num_sms * p->cfg.fit_ctas_per_sm, 256, fit_smem, st>>>(fa); argus_count_launch(1);
+    fa.bimg = ctx->basis_imgf; fa.nb = bd.nb; fa.ks = bd.ks; fa.r = bd.r; fa.NPC = NPC;
+    fa.ngroups = (bd.nb + FG - 1) / FG; fa.gram = p->d_gram; fa.n_pix = npix;
+    const int fgrid = ctx->num_sms * p->cfg.fit_ctas_per_sm;
+    int frc;
+    switch (bd.ks) {
+        case 7: frc = launch_seg_fit<7>(fa, fgrid, st); break;
+        case 9: frc = launch_seg_fit<9>(fa, fgrid, st); break;
+        case 11: frc = launch_seg_fit<11>(fa, fgrid, st); break;
+        case 15: frc = launch_seg_fit<15>(fa, fgrid, st); break;
+        case 21: frc = launch_seg_fit<21>(fa, fgrid, st); break;
+        default: return ARGUS_ERR_UNSUPPORTED;
+    }
+    if (frc) return frc;
     SegSolveArgs sa;
     sa.gram = p->d_gram; sa.n_pix = npix; sa.NPC = NPC; sa.nb = bd.nb; sa.S = ctx->basis_S; sa.img = ctx->basis_img;
     sa.kk = kk; sa.coeffs = coeffs; sa.stats = stats; sa.K = p->d_K; sa.bg = p->d_bg; sa.status = ctx->d_status;

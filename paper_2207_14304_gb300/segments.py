@@ -126,12 +126,12 @@ C_SIZE_STATS = 16
 
 
 def candidate_configs():
-    """Launch shapes the autotuner tries: fit band height, persistent CTAs per SM."""
+    """Launch shapes the autotuner tries: persistent CTAs per SM of the fit and of the
+    subtraction kernels (the fit's work unit is a fixed 8-row band)."""
     out = []
-    for band in (16, 32, 64):
-        for fcta in (1, 2):
-            for scta in (4, 8):
-                out.append((band, fcta, scta))
+    for fcta in (1, 2):
+        for scta in (2, 4, 6, 8):
+            out.append((8, fcta, scta))
     return out
 
 
