@@ -74,6 +74,15 @@ def _declare(l):
     l.ora_subtract_at.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, I, P, P, P]
     l.ora_detect.argtypes = [I, I, P, P, P, F, D, P, P, I]
     l.ora_coadd.argtypes = [I, I, I, P, P, I, P, P, P, D, D, I, D, I, P, P, P, P]
+    l.ora_cnn_nparams.restype = L
+    l.ora_cnn_forward.argtypes = [I, P, P, P, P]
+    l.ora_cnn_forward.restype = None
+    l.ora_cnn_backward.argtypes = [I, P, P, P, P, P]
+    l.ora_cnn_backward.restype = None
+    l.ora_cnn_mse.argtypes = [L, P, P, P]
+    l.ora_cnn_mse.restype = D
+    l.ora_adam.argtypes = [L, P, P, P, P, D, D, D, D, I]
+    l.ora_adam.restype = None
     l.ora_num_threads.restype = I
     l.ora_set_threads.argtypes = [I]
 
@@ -286,3 +295,40 @@ def coadd(raw_stack, shifts, *, bias=100, dark=None, flat=None, bpm=None, gain=1
                     float(read_noise), int(sat), float(kappa), int(max_iter), _p(co), _p(va),
                     _p(nu), _p(mg))
     return co, va, nu, mg
+
+
+# --------------------------------------------------------------------------- learned surrogate
+CNN_S, CNN_C = 21, 32
+
+
+def cnn_nparams() -> int:
+    return int(lib().ora_cnn_nparams())
+
+
+def cnn_forward(params, x):
+    """params [P] f64, x [B, 441, 2] -> (y [B, 441], acts [5, B, 441, 32])."""
+    prm = _c(params, np.float64); x = _c(x, np.float64)
+    B = x.shape[0]
+    acts = np.empty((5, B, CNN_S * CNN_S, CNN_C)); y = np.empty((B, CNN_S * CNN_S))
+    lib().ora_cnn_forward(B, _p(prm), _p(x), _p(acts), _p(y))
+    return y, acts
+
+
+def cnn_backward(params, x, acts, dy):
+    prm = _c(params, np.float64); x = _c(x, np.float64); acts = _c(acts, np.float64); dy = _c(dy, np.float64)
+    g = np.empty(cnn_nparams())
+    lib().ora_cnn_backward(x.shape[0], _p(prm), _p(x), _p(acts), _p(dy), _p(g))
+    return g
+
+
+def cnn_mse(y, t):
+    y = _c(y, np.float64); t = _c(t, np.float64)
+    dy = np.empty_like(y)
+    loss = lib().ora_cnn_mse(y.size, _p(y), _p(t), _p(dy))
+    return loss, dy
+
+
+def adam(p, m, v, g, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, step=1):
+    """In-place Adam step on float64 arrays p, m, v."""
+    g = _c(g, np.float64)
+    lib().ora_adam(p.size, _p(p), _p(m), _p(v), _p(g), float(lr), float(b1), float(b2), float(eps), int(step))

@@ -807,3 +807,161 @@ void ora_coadd(int nf, int w, int h, const uint16_t *raw, const float *shifts, i
         free(v); free(vv); free(tmp); free(nv); free(nvv);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned kernel surrogate (the north-star's learned-part reading; no       */
+/* counterpart in the paper).  A CNN maps a stamp pair (science, reference,   */
+/* each 21x21 and divided by the reference stamp sum) to a 21x21 kernel:      */
+/*   h1 = W1 x + b1                       (1x1 conv, 2 -> 32, linear)         */
+/*   h_{l+1} = relu(conv7(h_l; W_l) + b_l), l = 2..5  (7x7, 32 -> 32, 'same' */
+/*                                           zero padding)                    */
+/*   y = W6 h5 + b6                       (1x1 conv, 32 -> 1, linear)         */
+/* Parameter vector (FP64 here), in this order:                              */
+/*   W1[32][2], b1[32], {W_l[7][7][32 in][32 out], b_l[32]} x 4, W6[32], b6   */
+/* conv7: z[y][x][o] = b[o] + sum_{ky,kx,i} W[ky][kx][i][o] h[y+ky-3][x+kx-3][i]*/
+/* Activations are [B][21][21][C] (channels last).                           */
+/* ------------------------------------------------------------------------ */
+#define CNN_S 21
+#define CNN_P (CNN_S * CNN_S)
+#define CNN_C 32
+#define CNN_K 7
+
+long ora_cnn_nparams(void) { return 64 + 32 + 4L * (49 * 1024 + 32) + 32 + 1; }
+
+static void cnn_offsets(long *oW1, long *ob1, long oW[4], long ob[4], long *oW6, long *ob6) {
+    long o = 0;
+    *oW1 = o; o += 64;
+    *ob1 = o; o += 32;
+    for (int l = 0; l < 4; l++) { oW[l] = o; o += 49 * 1024; ob[l] = o; o += 32; }
+    *oW6 = o; o += 32;
+    *ob6 = o;
+}
+
+/* acts: h1..h5 [5][B][P][C] (post-activation); y [B][P]. */
+void ora_cnn_forward(int B, const double *prm, const double *x /*[B][P][2]*/, double *acts, double *y) {
+    long oW1, ob1, oW[4], ob[4], oW6, ob6;
+    cnn_offsets(&oW1, &ob1, oW, ob, &oW6, &ob6);
+    long L = (long)B * CNN_P * CNN_C;
+    double *h1 = acts;
+#pragma omp parallel for
+    for (long q = 0; q < (long)B * CNN_P; q++)
+        for (int o = 0; o < CNN_C; o++)
+            h1[q * CNN_C + o] = prm[ob1 + o] + prm[oW1 + o * 2] * x[q * 2] + prm[oW1 + o * 2 + 1] * x[q * 2 + 1];
+    for (int l = 0; l < 4; l++) {
+        const double *hin = acts + l * L;
+        double *hout = acts + (l + 1) * L;
+        const double *W = prm + oW[l], *bb = prm + ob[l];
+#pragma omp parallel for
+        for (long q = 0; q < (long)B * CNN_P; q++) {
+            int b = (int)(q / CNN_P), p = (int)(q % CNN_P), yy = p / CNN_S, xx = p % CNN_S;
+            for (int o = 0; o < CNN_C; o++) {
+                double z = bb[o];
+                for (int ky = 0; ky < CNN_K; ky++)
+                    for (int kx = 0; kx < CNN_K; kx++) {
+                        int sy = yy + ky - 3, sx = xx + kx - 3;
+                        if (sy < 0 || sx < 0 || sy >= CNN_S || sx >= CNN_S) continue;
+                        const double *hi = hin + ((long)b * CNN_P + sy * CNN_S + sx) * CNN_C;
+                        const double *w = W + ((ky * CNN_K + kx) * CNN_C) * CNN_C + o;
+                        for (int i = 0; i < CNN_C; i++) z += w[i * CNN_C] * hi[i];
+                    }
+                hout[q * CNN_C + o] = z > 0.0 ? z : 0.0;
+            }
+        }
+    }
+    const double *h5 = acts + 4 * L;
+    for (long q = 0; q < (long)B * CNN_P; q++) {
+        double s = prm[ob6];
+        for (int i = 0; i < CNN_C; i++) s += prm[oW6 + i] * h5[q * CNN_C + i];
+        y[q] = s;
+    }
+}
+
+/* Gradient of loss with respect to the parameters given dL/dy (grad zeroed here). */
+void ora_cnn_backward(int B, const double *prm, const double *x, const double *acts, const double *dy,
+                      double *grad) {
+    long oW1, ob1, oW[4], ob[4], oW6, ob6;
+    cnn_offsets(&oW1, &ob1, oW, ob, &oW6, &ob6);
+    long NP = ora_cnn_nparams(), L = (long)B * CNN_P * CNN_C;
+    memset(grad, 0, sizeof(double) * NP);
+    double *dh = (double *)calloc(L, sizeof(double)), *dz = (double *)calloc(L, sizeof(double));
+    const double *h5 = acts + 4 * L;
+    for (long q = 0; q < (long)B * CNN_P; q++) {
+        grad[ob6] += dy[q];
+        for (int i = 0; i < CNN_C; i++) {
+            grad[oW6 + i] += dy[q] * h5[q * CNN_C + i];
+            dh[q * CNN_C + i] = prm[oW6 + i] * dy[q];
+        }
+    }
+    for (int l = 3; l >= 0; l--) {
+        const double *hin = acts + l * L, *hout = acts + (l + 1) * L;
+        const double *W = prm + oW[l];
+        for (long e = 0; e < L; e++) dz[e] = hout[e] > 0.0 ? dh[e] : 0.0;
+        for (long q = 0; q < (long)B * CNN_P; q++)
+            for (int o = 0; o < CNN_C; o++) grad[ob[l] + o] += dz[q * CNN_C + o];
+        /* dW[ky][kx][i][o] = sum_q hin[q + tap][i] dz[q][o] */
+#pragma omp parallel for
+        for (int t = 0; t < 49; t++) {
+            int ky = t / CNN_K, kx = t % CNN_K;
+            for (int i = 0; i < CNN_C; i++)
+                for (int o = 0; o < CNN_C; o++) {
+                    double s = 0.0;
+                    for (int b = 0; b < B; b++)
+                        for (int p = 0; p < CNN_P; p++) {
+                            int yy = p / CNN_S, xx = p % CNN_S, sy = yy + ky - 3, sx = xx + kx - 3;
+                            if (sy < 0 || sx < 0 || sy >= CNN_S || sx >= CNN_S) continue;
+                            s += hin[((long)b * CNN_P + sy * CNN_S + sx) * CNN_C + i] *
+                                 dz[((long)b * CNN_P + p) * CNN_C + o];
+                        }
+                    grad[oW[l] + (t * CNN_C + i) * CNN_C + o] += s;
+                }
+        }
+        /* dh_in[q'][i] = sum over outputs q with q' = q + tap: W[tap][i][o] dz[q][o] */
+        memset(dh, 0, sizeof(double) * L);
+#pragma omp parallel for
+        for (long qs = 0; qs < (long)B * CNN_P; qs++) {
+            int b = (int)(qs / CNN_P), ps = (int)(qs % CNN_P), sy = ps / CNN_S, sx = ps % CNN_S;
+            for (int i = 0; i < CNN_C; i++) {
+                double s = 0.0;
+                for (int ky = 0; ky < CNN_K; ky++)
+                    for (int kx = 0; kx < CNN_K; kx++) {
+                        int yy = sy - ky + 3, xx = sx - kx + 3;
+                        if (yy < 0 || xx < 0 || yy >= CNN_S || xx >= CNN_S) continue;
+                        const double *d = dz + ((long)b * CNN_P + yy * CNN_S + xx) * CNN_C;
+                        const double *w = W + ((ky * CNN_K + kx) * CNN_C + i) * CNN_C;
+                        for (int o = 0; o < CNN_C; o++) s += w[o] * d[o];
+                    }
+                dh[qs * CNN_C + i] = s;
+            }
+        }
+    }
+    /* layer 1 (linear): dW1[o][j] = sum_q x[q][j] dh1[q][o] */
+    for (long q = 0; q < (long)B * CNN_P; q++)
+        for (int o = 0; o < CNN_C; o++) {
+            grad[ob1 + o] += dh[q * CNN_C + o];
+            grad[oW1 + o * 2] += x[q * 2] * dh[q * CNN_C + o];
+            grad[oW1 + o * 2 + 1] += x[q * 2 + 1] * dh[q * CNN_C + o];
+        }
+    free(dh); free(dz);
+}
+
+/* Mean squared error over B*P outputs and its gradient dL/dy. */
+double ora_cnn_mse(long n, const double *y, const double *t, double *dy) {
+    double s = 0.0;
+    for (long i = 0; i < n; i++) {
+        double d = y[i] - t[i];
+        s += d * d;
+        if (dy) dy[i] = 2.0 * d / (double)n;
+    }
+    return s / (double)n;
+}
+
+/* One Adam step (Kingma & Ba 2015), bias-corrected, step >= 1. */
+void ora_adam(long n, double *p, double *m, double *v, const double *g, double lr, double b1, double b2,
+              double eps, int step) {
+    double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+    for (long i = 0; i < n; i++) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

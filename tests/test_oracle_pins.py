@@ -555,3 +555,78 @@ def test_stamp_selection_hand_placed_stars(ora):
     # without the crowding rule (iso = 0) cell (1,0) takes the brightest allowed star
     cen = ora.select_stamps(R, fl, 2, 2, stamp=9, khalf=3, max_peak=3000.0, iso=0)
     assert cen.tolist() == [[15, 15], [60, 28], [50, 55]]
+
+
+# --------------------------------------------------------------------------- learned surrogate (oracle)
+def _cnn_params(seed, scale=0.05):
+    import oracle
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, scale, oracle.cnn_nparams())
+
+
+def _torch_forward(params, x):
+    """The same network written with PyTorch CPU FP64 library convolutions."""
+    import torch.nn.functional as Fnn
+    p = torch.from_numpy(params)
+    o = 0
+    W1 = p[o:o + 64].view(32, 2); o += 64
+    b1 = p[o:o + 32]; o += 32
+    convs = []
+    for _ in range(4):
+        W = p[o:o + 49 * 1024].view(7, 7, 32, 32); o += 49 * 1024
+        b = p[o:o + 32]; o += 32
+        convs.append((W.permute(3, 2, 0, 1).contiguous(), b))
+    W6 = p[o:o + 32]; o += 32
+    b6 = p[o]
+    B = x.shape[0]
+    xt = torch.from_numpy(x).view(B, 21, 21, 2).permute(0, 3, 1, 2)
+    h = Fnn.conv2d(xt, W1.view(32, 2, 1, 1), b1)
+    for W, b in convs:
+        h = torch.relu(Fnn.conv2d(h, W, b, padding=3))
+    y = Fnn.conv2d(h, W6.view(1, 32, 1, 1), b6.view(1))
+    return y.view(B, 441).numpy()
+
+
+def test_cnn_forward_matches_library_convolutions(ora):
+    params = _cnn_params(1)
+    x = np.random.default_rng(2).normal(0, 1, (2, 441, 2))
+    y, acts = ora.cnn_forward(params, x)
+    np.testing.assert_allclose(y, _torch_forward(params, x), rtol=1e-10, atol=1e-12)
+    assert ora.cnn_nparams() == 64 + 32 + 4 * (49 * 1024 + 32) + 32 + 1 == 200_961
+
+
+def test_cnn_backward_matches_finite_differences(ora):
+    params = _cnn_params(3)
+    rng = np.random.default_rng(4)
+    x = rng.normal(0, 1, (1, 441, 2))
+    t = rng.normal(0, 0.1, (1, 441))
+    y, acts = ora.cnn_forward(params, x)
+    loss, dy = ora.cnn_mse(y, t)
+    g = ora.cnn_backward(params, x, acts, dy)
+    # parameters from every tensor: W1, b1, each conv's W and b, W6, b6
+    offs = [0, 64]
+    o = 96
+    for _ in range(4):
+        offs += [o, o + 49 * 1024]
+        o += 49 * 1024 + 32
+    offs += [o, o + 32]
+    n = ora.cnn_nparams()
+    idx = sorted({min(int(v), n - 1) for base in offs for v in base + rng.integers(0, 8, 3)} | {n - 1})
+    h = 1e-6
+    for i in idx:
+        pp = params.copy(); pp[i] += h
+        lp = ora.cnn_mse(ora.cnn_forward(pp, x)[0], t)[0]
+        pm = params.copy(); pm[i] -= h
+        lm = ora.cnn_mse(ora.cnn_forward(pm, x)[0], t)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), abs(g[i])) + 1e-11, (i, fd, g[i])
+
+
+def test_adam_first_step_closed_form(ora):
+    """From zero moments the bias-corrected first step is lr * g / (|g| + eps)."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    p = np.zeros(4); m = np.zeros(4); v = np.zeros(4)
+    ora.adam(p, m, v, g, lr=1e-3, step=1)
+    np.testing.assert_allclose(p, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
