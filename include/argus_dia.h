@@ -283,6 +283,64 @@ int argus_segments_run(argus_seg_plan *plan, const float *sci, const float *sci_
 /* Number of fit and subtraction work units of a plan. */
 int argus_segments_items(const argus_seg_plan *plan, int *n_fit_items, int *n_sub_items);
 
+/* Copy the kernels (float [n][ksize^2]) and backgrounds (double [n]) of the last
+ * run to caller buffers (device; either may be NULL). */
+int argus_segments_kernels(const argus_seg_plan *plan, float *K, double *bg, argus_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned kernel surrogate (the benchmark spec's learned part; the paper has no
+ * counterpart).  A CNN maps a stamp pair (science and reference, 21x21, both
+ * divided by the reference stamp sum) to a 21x21 kernel:
+ *   h1 = W1 x + b1 (1x1, 2 -> 32); h_{l+1} = relu(conv7(h_l) + b_l) for four
+ *   7x7 'same' 32 -> 32 layers; y = W6 h5 + b6 (1x1, 32 -> 1).
+ * 200,961 parameters in the order W1[32][2], b1[32], {W[7][7][32 in][32 out],
+ * b[32]} x 4, W6[32], b6, conv7 taps applied as
+ * z[y][x][o] = b[o] + sum W[ky][kx][i][o] h[y+ky-3][x+kx-3][i] (zero padding).
+ * Inputs x: float [n][441][2]; outputs y: float [n][441] (row-major kernel
+ * pixels, index (v+10)*21 + (u+10)).  Weights are used as BF16 (default) or
+ * FP32 with FP32 accumulation; training keeps FP32 master weights and Adam
+ * moments.  The object owns its activation workspace for up to max_batch
+ * stamps (allocated at creation). */
+typedef struct argus_cnn argus_cnn;
+int argus_cnn_create(argus_cnn **out, int device, int max_batch, unsigned long long seed);
+int argus_cnn_destroy(argus_cnn *net);
+/* Device pointers to the FP32 master parameters and Adam moments (each
+ * [count] floats) and the Adam step, for checkpoints and tests. */
+int argus_cnn_params(argus_cnn *net, float **master, float **adam_m, float **adam_v, long *count, int *step);
+/* Select ARGUS_PREC_BF16 / ARGUS_PREC_FP32 weights, set the Adam step, and
+ * refresh the BF16 copy from the master weights (after a checkpoint load). */
+int argus_cnn_set_state(argus_cnn *net, int precision, int step, argus_stream stream);
+int argus_cnn_forward(argus_cnn *net, const float *x, int n, float *y, argus_stream stream);
+/* dL/dparams for a given dL/dy after argus_cnn_forward on the same x (the
+ * activations are kept); grad_out (device, [count] floats) may be NULL. */
+int argus_cnn_backward(argus_cnn *net, const float *x, const float *dy, int n, float *grad_out,
+                       argus_stream stream);
+/* One training step: forward, MSE against target (float [n][441]), backward,
+ * Adam (beta 0.9, 0.999, eps 1e-8) with learning rate lr; *loss_out (device
+ * double, may be NULL) receives the batch loss. */
+int argus_cnn_train_step(argus_cnn *net, const float *x, const float *target, int n, float lr,
+                         double *loss_out, argus_stream stream);
+/* One Adam step with a given gradient (device, [count] floats). */
+int argus_cnn_adam(argus_cnn *net, const float *grad, float lr, argus_stream stream);
+/* Network inputs from the 21x21 windows of sci and ref centred on centers[s]
+ * (s < min(*n_stamps, max_stamps)), divided by the reference window sum. */
+int argus_cnn_prepare(const float *sci, const float *ref, argus_shape shape, const int *centers,
+                      const int *n_stamps, int max_stamps, float *x, argus_stream stream);
+/* Spatial least squares across stamps: the per-stamp kernels y [n][441]
+ * (at the stamp centres) give K_k (float [Ks][441]) with
+ * y_s = sum_k p_k(x_s, y_s) K_k, normal matrix in FP64. */
+int argus_learned_kernel(argus_ctx *ctx, const float *y, const int *centers, const int *n_stamps,
+                         int max_stamps, int frame_w, int frame_h, int spatial_degree, float *K,
+                         argus_stream stream);
+/* Background polynomial given the kernel K (float [Ks][ksize^2]), by weighted
+ * least squares on the stamp pixels, and chi2 of the result there:
+ * r = I - sum_k p_k (R (x) K_k), bg = argmin sum w (r - sum pb bg)^2.
+ * stats (device) receives chi2, n_pix, dof (n_pix - Ks ksize^2 - Kb). */
+int argus_fit_background(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
+                         const uint8_t *flags, argus_shape shape, const int *centers, const int *n_stamps,
+                         int max_stamps, int stamp, const float *K, int ksize, int spatial_degree,
+                         int bg_degree, double *bg, argus_fit_stats *stats, argus_stream stream);
+
 /* Stamp selection that allocates nothing, for callers that cannot call
  * cudaMalloc (a host that reserves all device memory up front, a real-time
  * loop that must never enter an allocator, or a plugin that is only handed

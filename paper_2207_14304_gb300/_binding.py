@@ -107,6 +107,18 @@ SIGNATURES = {
     "argus_segments_destroy": ([P], I),
     "argus_segments_run": ([P, P, P, P, P, P, P, P, P, P, P, F, F, P, I, P, I, P], I),
     "argus_segments_items": ([P, C.POINTER(I), C.POINTER(I)], I),
+    "argus_segments_kernels": ([P, P, P, P], I),
+    "argus_cnn_create": ([C.POINTER(P), I, I, C.c_ulonglong], I),
+    "argus_cnn_destroy": ([P], I),
+    "argus_cnn_params": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(C.c_long), C.POINTER(I)], I),
+    "argus_cnn_set_state": ([P, I, I, P], I),
+    "argus_cnn_forward": ([P, P, I, P, P], I),
+    "argus_cnn_backward": ([P, P, P, I, P, P], I),
+    "argus_cnn_train_step": ([P, P, P, I, F, P, P], I),
+    "argus_cnn_adam": ([P, P, F, P], I),
+    "argus_cnn_prepare": ([P, P, SH, P, P, I, P, P], I),
+    "argus_learned_kernel": ([P, P, P, P, I, I, I, I, P, P], I),
+    "argus_fit_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
 }
 
 
@@ -279,6 +291,72 @@ def argus_segments_items(plan):
     a, b = C.c_int(0), C.c_int(0)
     _check(load().argus_segments_items(plan, C.byref(a), C.byref(b)), "argus_segments_items")
     return a.value, b.value
+
+
+def argus_segments_kernels(plan, K=None, bg=None, stream=None):
+    _check(load().argus_segments_kernels(plan, _ptr(K), _ptr(bg), _stream(stream)), "argus_segments_kernels")
+
+
+def argus_cnn_create(device=0, max_batch=1024, seed=1):
+    h = C.c_void_p()
+    _check(load().argus_cnn_create(C.byref(h), int(device), int(max_batch), int(seed)), "argus_cnn_create")
+    return h
+
+
+def argus_cnn_destroy(net):
+    _check(load().argus_cnn_destroy(net), "argus_cnn_destroy")
+
+
+def argus_cnn_params(net):
+    """(master, adam_m, adam_v) as device addresses, parameter count, Adam step."""
+    m, a, v = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    n, st = C.c_long(0), C.c_int(0)
+    _check(load().argus_cnn_params(net, C.byref(m), C.byref(a), C.byref(v), C.byref(n), C.byref(st)),
+           "argus_cnn_params")
+    return (m.value, a.value, v.value), n.value, st.value
+
+
+def argus_cnn_set_state(net, precision, step, stream=None):
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(load().argus_cnn_set_state(net, prec, int(step), _stream(stream)), "argus_cnn_set_state")
+
+
+def argus_cnn_forward(net, x, n, y, stream=None):
+    _check(load().argus_cnn_forward(net, _ptr(x), int(n), _ptr(y), _stream(stream)), "argus_cnn_forward")
+
+
+def argus_cnn_backward(net, x, dy, n, grad_out=None, stream=None):
+    _check(load().argus_cnn_backward(net, _ptr(x), _ptr(dy), int(n), _ptr(grad_out), _stream(stream)),
+           "argus_cnn_backward")
+
+
+def argus_cnn_train_step(net, x, target, n, lr, loss_out=None, stream=None):
+    _check(load().argus_cnn_train_step(net, _ptr(x), _ptr(target), int(n), float(lr), _ptr(loss_out),
+                                       _stream(stream)), "argus_cnn_train_step")
+
+
+def argus_cnn_adam(net, grad, lr, stream=None):
+    _check(load().argus_cnn_adam(net, _ptr(grad), float(lr), _stream(stream)), "argus_cnn_adam")
+
+
+def argus_cnn_prepare(sci, ref, shape, centers, n_stamps, max_stamps, x, stream=None):
+    _check(load().argus_cnn_prepare(_ptr(sci), _ptr(ref), shape, _ptr(centers), _ptr(n_stamps), int(max_stamps),
+                                    _ptr(x), _stream(stream)), "argus_cnn_prepare")
+
+
+def argus_learned_kernel(ctx, y, centers, n_stamps, max_stamps, frame_w, frame_h, spatial_degree, K,
+                         stream=None):
+    _check(load().argus_learned_kernel(ctx, _ptr(y), _ptr(centers), _ptr(n_stamps), int(max_stamps),
+                                       int(frame_w), int(frame_h), int(spatial_degree), _ptr(K),
+                                       _stream(stream)), "argus_learned_kernel")
+
+
+def argus_fit_background(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp, K, ksize,
+                         spatial_degree, bg_degree, bg, stats, stream=None):
+    _check(load().argus_fit_background(ctx, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(flags), shape,
+                                       _ptr(centers), _ptr(n_stamps), int(max_stamps), int(stamp), _ptr(K),
+                                       int(ksize), int(spatial_degree), int(bg_degree), _ptr(bg), _ptr(stats),
+                                       _stream(stream)), "argus_fit_background")
 
 
 def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,

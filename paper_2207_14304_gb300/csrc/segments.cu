@@ -639,3 +639,15 @@ extern "C" int argus_segments_items(const argus_seg_plan* p, int* n_fit_items, i
     if (n_sub_items) *n_sub_items = p->n_sub_items;
     return ARGUS_OK;
 }
+
+extern "C" int argus_segments_kernels(const argus_seg_plan* p, float* K, double* bg, argus_stream stream) {
+    if (!p || (!K && !bg)) return ARGUS_ERR_ARG;
+    if (cudaSetDevice(p->ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t kk = (size_t)p->bd.ks * p->bd.ks;
+    if (K && cudaMemcpyAsync(K, p->d_K, sizeof(float) * kk * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    if (bg && cudaMemcpyAsync(bg, p->d_bg, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    return ARGUS_OK;
+}
