@@ -22,6 +22,7 @@ namespace {
 
 constexpr int S = 21, NPX = S * S, C = 32, KS = 7, SP = S + KS - 1;   // padded side 27
 constexpr int CS = 33;                                                 // padded channel stride
+constexpr int PADSZ = (SP * SP * CS + 3) / 4 * 4;                      // keeps what follows 16-byte aligned
 constexpr long NPARAM = 64 + 32 + 4L * (49 * 1024 + 32) + 32 + 1;
 constexpr long OFF_W1 = 0, OFF_B1 = 64;
 __host__ __device__ constexpr long off_w(int l) { return 96 + (long)l * (49 * 1024 + 32); }
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(256) cnn_conv7_fwd_kernel(const float* hin, co
                                                             int n) {
     extern __shared__ __align__(16) float sm[];
     float* pad = sm;                                 // [SP*SP*CS]
-    float* ws = pad + SP * SP * CS;                  // [7 kx][32 i][32 o] one kernel row
+    float* ws = pad + PADSZ;                  // [7 kx][32 i][32 o] one kernel row
     const int oct = threadIdx.x & 3, pg = threadIdx.x >> 2;
     for (int img = blockIdx.x; img < n; img += gridDim.x) {
         __syncthreads();
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) cnn_conv7_dgrad_kernel(const float* dh_ou
                                                               float* dh_in, int n) {
     extern __shared__ __align__(16) float sm[];
     float* pad = sm;                                 // dz, zero padded
-    float* ws = pad + SP * SP * CS;                  // [7 kx][32 o][32 i] (transposed)
+    float* ws = pad + PADSZ;                  // [7 kx][32 o][32 i] (transposed)
     const int oct = threadIdx.x & 3, pg = threadIdx.x >> 2;
     for (int img = blockIdx.x; img < n; img += gridDim.x) {
         __syncthreads();
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(448) cnn_conv7_wgrad_kernel(const float* hin, 
                                                               int per_cta) {
     extern __shared__ __align__(16) float sm[];
     float* pad = sm;                                 // input, zero padded
-    float* dz = pad + SP * SP * CS;                  // [441][CS]
+    float* dz = pad + PADSZ;                  // [441][CS]
     const int ky = blockIdx.y;
     const int t = threadIdx.x;
     const int kx = t / 64, r = t - kx * 64, i4 = r & 7, o4 = r >> 3;
@@ -647,8 +648,8 @@ struct argus_cnn {
     int step;
 };
 
-static size_t fwd_smem() { return sizeof(float) * ((size_t)SP * SP * CS + (size_t)KS * C * C); }
-static size_t wgrad_smem() { return sizeof(float) * ((size_t)SP * SP * CS + (size_t)NPX * CS); }
+static size_t fwd_smem() { return sizeof(float) * ((size_t)PADSZ + (size_t)KS * C * C); }
+static size_t wgrad_smem() { return sizeof(float) * ((size_t)PADSZ + (size_t)NPX * CS); }
 
 extern "C" int argus_cnn_create(argus_cnn** out, int device, int max_batch, unsigned long long seed) {
     if (!out || max_batch < 1) return ARGUS_ERR_ARG;
