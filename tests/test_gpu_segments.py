@@ -68,7 +68,8 @@ def test_segments_parity(ora, use_graph):
             assert abs(bgg[0] - bgo[0]) < 1e-3 * (abs(bgo[0]) + sky * abs(Ko.sum())), (i, bgg, bgo)
             assert stats[i]["status"] == 0
             assert stats[i]["n_pix"] == res.dof + ob.ncoeffs
-            assert abs(stats[i]["chi2"] / res.chi2 - 1) < 1e-4, (i, stats[i]["chi2"], res.chi2)
+            # chi2 from the normal equations (t'Wt - 2 c'b + c'Mc) cancels to ~1e-4
+            assert abs(stats[i]["chi2"] / res.chi2 - 1) < 1e-3, (i, stats[i]["chi2"], res.chi2)
             # subtraction with the GPU's own kernel: compares the batched subtraction alone
             Do, VDo = ora.subtract(Is, Vs, Rs, Vrs, Fs, Kg.astype(np.float32).astype(np.float64), bgg,
                                    sdeg=0, bgdeg=0)
