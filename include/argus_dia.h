@@ -292,7 +292,8 @@ int argus_segments_kernels(const argus_seg_plan *plan, float *K, double *bg, arg
  * counterpart).  A CNN maps a stamp pair (science and reference, 21x21, both
  * divided by the reference stamp sum) to a 21x21 kernel:
  *   h1 = W1 x + b1 (1x1, 2 -> 32); h_{l+1} = relu(conv7(h_l) + b_l) for four
- *   7x7 'same' 32 -> 32 layers; y = W6 h5 + b6 (1x1, 32 -> 1).
+ *   7x7 'same' 32 -> 32 layers; y = (W6 h5 + b6) / 441 (1x1, 32 -> 1; the fixed
+ *   1/441 keeps the last layer's values at order one).
  * 200,961 parameters in the order W1[32][2], b1[32], {W[7][7][32 in][32 out],
  * b[32]} x 4, W6[32], b6, conv7 taps applied as
  * z[y][x][o] = b[o] + sum W[ky][kx][i][o] h[y+ky-3][x+kx-3][i] (zero padding).

@@ -815,7 +815,9 @@ void ora_coadd(int nf, int w, int h, const uint16_t *raw, const float *shifts, i
 /*   h1 = W1 x + b1                       (1x1 conv, 2 -> 32, linear)         */
 /*   h_{l+1} = relu(conv7(h_l; W_l) + b_l), l = 2..5  (7x7, 32 -> 32, 'same' */
 /*                                           zero padding)                    */
-/*   y = W6 h5 + b6                       (1x1 conv, 32 -> 1, linear)         */
+/*   y = (W6 h5 + b6) / 441               (1x1 conv, 32 -> 1, linear; the    */
+/*                                          fixed 1/441 puts the last layer's */
+/*                                          values at order one)              */
 /* Parameter vector (FP64 here), in this order:                              */
 /*   W1[32][2], b1[32], {W_l[7][7][32 in][32 out], b_l[32]} x 4, W6[32], b6   */
 /* conv7: z[y][x][o] = b[o] + sum_{ky,kx,i} W[ky][kx][i][o] h[y+ky-3][x+kx-3][i]*/
@@ -872,7 +874,7 @@ void ora_cnn_forward(int B, const double *prm, const double *x /*[B][P][2]*/, do
     for (long q = 0; q < (long)B * CNN_P; q++) {
         double s = prm[ob6];
         for (int i = 0; i < CNN_C; i++) s += prm[oW6 + i] * h5[q * CNN_C + i];
-        y[q] = s;
+        y[q] = s / (double)CNN_P;
     }
 }
 
@@ -886,10 +888,11 @@ void ora_cnn_backward(int B, const double *prm, const double *x, const double *a
     double *dh = (double *)calloc(L, sizeof(double)), *dz = (double *)calloc(L, sizeof(double));
     const double *h5 = acts + 4 * L;
     for (long q = 0; q < (long)B * CNN_P; q++) {
-        grad[ob6] += dy[q];
+        double d = dy[q] / (double)CNN_P;
+        grad[ob6] += d;
         for (int i = 0; i < CNN_C; i++) {
-            grad[oW6 + i] += dy[q] * h5[q * CNN_C + i];
-            dh[q * CNN_C + i] = prm[oW6 + i] * dy[q];
+            grad[oW6 + i] += d * h5[q * CNN_C + i];
+            dh[q * CNN_C + i] = prm[oW6 + i] * d;
         }
     }
     for (int l = 3; l >= 0; l--) {

@@ -5,7 +5,8 @@
 // A small CNN maps a stamp pair (science, reference; 21x21 each, divided by
 // the reference stamp sum) to a 21x21 kernel:
 //   h1 = W1 x + b1 (1x1, 2 -> 32), h_{l+1} = relu(conv7(h_l) + b_l) for four
-//   7x7 'same' 32 -> 32 layers, y = W6 h5 + b6 (1x1, 32 -> 1).
+//   7x7 'same' 32 -> 32 layers, y = (W6 h5 + b6) / 441 (1x1, 32 -> 1; the fixed
+//   1/441 keeps the last layer's values at order one).
 // Parameters (200,961) follow the layout W1[32][2], b1, {W[7][7][32 in][32 out],
 // b} x 4, W6[32], b6.  Weights are read as BF16 (or FP32) with FP32
 // accumulation; activations are FP32, channels last with a padded channel
@@ -125,7 +126,7 @@ __global__ void cnn_out_kernel(const float* h5, const WT* w, float* y, int n) {
         const float* h = h5 + q * C;
 #pragma unroll
         for (int i = 0; i < C; i++) s = fmaf(ld(w, OFF_W6 + i), h[i], s);
-        y[q] = s;
+        y[q] = s * (1.0f / NPX);
     }
 }
 
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(256) cnn_out_bwd_kernel(const float* h5, const
     for (int c = 0; c <= C; c++) gw[c] = 0.0f;
     const long tot = (long)n * NPX;
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < tot; q += (long)gridDim.x * blockDim.x) {
-        const float d = dy[q];
+        const float d = dy[q] * (1.0f / NPX);
 #pragma unroll
         for (int c = 0; c < C; c++) {
             gw[c] = fmaf(d, h5[q * C + c], gw[c]);
@@ -380,8 +381,8 @@ __global__ void cnn_init_kernel(float* p, long n, unsigned long long seed) {
         const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
         p[i] = (float)(z * sqrt(2.0 / fan_in));
     }
-    // the output layer starts near the mean kernel (1/441 per pixel)
-    if (blockIdx.x == 0 && threadIdx.x == 0) p[OFF_B6] = 1.0f / NPX;
+    // the output starts near the mean kernel (1/441 per pixel)
+    if (blockIdx.x == 0 && threadIdx.x == 0) p[OFF_B6] = 1.0f;
 }
 
 // Network inputs from stamps: x[s][p][0] = I / sum(R), x[s][p][1] = R / sum(R) over the

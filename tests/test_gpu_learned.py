@@ -163,3 +163,41 @@ def test_fit_background_matches_library_least_squares(ora):
         assert abs(s["chi2"] / chi_want - 1) < 1e-6 and s["n_pix"] == len(xy)
     finally:
         B.argus_destroy(ctx)
+
+
+def test_learned_fit_falls_back_to_least_squares():
+    """An untrained network's kernel is far worse than the least-squares fit, so the
+    per-frame learned fit must judge it by chi2 and use the plain fit instead; with
+    the judge disabled (ratio = inf) the learned kernel is used and subtraction runs."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14304_gb300.learned import LearnedFit
+    from paper_2207_14304_gb300.pipeline import FramePipeline
+    w = h = 320
+    cat = synth.star_catalog(900, w, h, seed=21)
+    R, Vr = synth.reference_image(synth.render(cat, w, h, 1.2, sky=300.0), 30, 1.7, 22)
+    cal = synth.make_calib(w, h, seed=23)
+    raw = synth.expose(synth.render(cat, w, h, 1.8, sky=305.0), cal, seed=24)
+    basis = B.make_basis(21, (0.7, 1.5, 3.0), (6, 4, 2), 1, 1)
+    pipe = FramePipeline(w, h, basis=basis, grid=(4, 4))
+    net = KernelNet(max_batch=16, seed=5)
+    try:
+        def dev(a):
+            t = torch.zeros((h, pipe.pitch), dtype=a.dtype)
+            t[:, :w] = a
+            return t.cuda()
+        d_raw, d_R, d_Vr = dev(raw), dev(R), dev(Vr)
+        calib = B.make_calib(cal.bias, dev(cal.dark), dev(cal.flat), dev(cal.bpm), cal.gain, cal.read_noise, cal.sat)
+        lf = LearnedFit(pipe, net)
+        assert lf.run(d_raw, calib, d_R, d_Vr) is True        # first frame: plain fit sets the reference chi2
+        assert lf.plain_chi2_dof is not None and lf.plain_chi2_dof < 5
+        assert lf.run(d_raw, calib, d_R, d_Vr) is True        # untrained network: judged worse, fallback
+        assert lf.n_fallback == 1 and lf.n_learned == 0
+        lf.ratio = float("inf")
+        assert lf.run(d_raw, calib, d_R, d_Vr) is False       # judge off: learned kernel used
+        torch.cuda.synchronize()
+        assert B.argus_sync_status(pipe.ctx) == 0
+        assert torch.isfinite(pipe.diff).all()
+    finally:
+        net.close()
+        pipe.close()
