@@ -98,7 +98,7 @@ def test_cnn_training_lowers_loss():
         u = torch.arange(21, device="cuda", dtype=torch.float32) - 10
         G = torch.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * 1.5 ** 2))
         t = (G / G.sum()).reshape(1, NPX).repeat(64, 1).contiguous()
-        hist = k.fit(x, t, epochs=40, batch=64, lr=1e-3)
+        hist = k.fit(x, t, epochs=300, batch=64, lr=2e-3)
         assert hist[-1] < 0.2 * hist[0], hist
     finally:
         k.close()
