@@ -306,13 +306,177 @@ def run_gpu(args):
         "gpu_launches": int(launches), "sources_last_frame": n_found,
         "variants": var, "clocks": clk,
     }
+    pipe.close()
+    del d_raw, d_R, d_Vr
+    torch.cuda.empty_cache()
+    if args.extras and ws == 1:
+        extras = {}
+        for name, fn in (("coadd", lambda: bench_coadd(device, stream, args.steps, hbm)),
+                         ("segments", lambda: bench_segments(device, stream, args.segment_cameras)),
+                         ("learned", lambda: bench_learned(device, stream, args.train_pairs, args.train_epochs))):
+            try:
+                extras[name] = fn()
+            except Exception as e:   # an extra never invalidates the headline line
+                extras[name] = {"error": repr(e)[:300]}
+            torch.cuda.empty_cache()
+        result["workloads"] = extras
     if rank == 0 and args.cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args)
-    pipe.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def timed_ms(fn, n, stream, device):
+    import torch
+    fn()
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    return e0.elapsed_time(e1) / n
+
+
+def bench_coadd(device, stream, steps, hbm):
+    """30 x 9576x6388 uint16 frames (one 15-min ratchet at 30 s), shifts up to 0.5 px,
+    1 % cosmic rays, 3-sigma clipped mean with fused calibration."""
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    from paper_2207_14304_gb300 import synth
+    nf = 30
+    pitch = synth.pitch_for(W)
+    cat = synth.star_catalog(N_STARS, W, H, seed=3)
+    cal = synth.make_calib(W, H, seed=5, device=device)
+    sh = synth.uniform_shifts(nf, seed=3)
+    stack = torch.zeros((nf, H, pitch), dtype=torch.uint16, device=device)
+    for f in range(nf):
+        e = synth.render(cat, W, H, 1.5, sky=300.0, shift=(-float(sh[f, 0]), -float(sh[f, 1])), device=device,
+                         dtype=torch.float32)
+        stack[f, :, :W] = synth.expose(e, cal, seed=300 + f, cosmic_frac=0.01)
+        del e
+
+    def pad(a):
+        t = torch.zeros((H, pitch), dtype=a.dtype, device=device)
+        t[:, :W] = a
+        return t
+    d_dark, d_flat, d_bpm = pad(cal.dark), pad(cal.flat), pad(cal.bpm)
+    calib = B.make_calib(cal.bias, d_dark, d_flat, d_bpm, cal.gain, cal.read_noise, cal.sat)
+    co = torch.zeros((H, pitch), device=device)
+    va = torch.zeros((H, pitch), device=device)
+    nu = torch.zeros((H, pitch), dtype=torch.uint8, device=device)
+    ctx = B.argus_create(device.index, H * pitch, 16, 64, 1 << 10)
+    try:
+        shifts = sh.to(device)
+        ms = timed_ms(lambda: B.argus_coadd(ctx, stack, nf, B.argus_shape(W, H, pitch), shifts, calib, 3.0, 5, co,
+                                            va, nu, stream), max(3, steps // 10), stream, device)
+        st = B.argus_sync_status(ctx, stream)
+    finally:
+        B.argus_destroy(ctx)
+    bpp = nf * 2 + 9 + 9
+    return {"workload": "30 x 9576x6388 uint16, shifts <= 0.5 px, 1% cosmic rays, kappa 3, 5 iterations",
+            "ms": round(ms, 3), "value": round(W * H / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s (output)",
+            "hbm_bytes_per_px": bpp, "hbm_frac": round(bpp * W * H / (ms / 1e3) / 1e9 / hbm, 4), "status": st}
+
+
+def bench_segments(device, stream, cameras, log=None):
+    """38 cameras x 512 square cutouts (64-512 px, log-uniform) with their own fitted 15x15
+    kernels, through one CUDA-graph launch of the persistent kernels."""
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    from paper_2207_14304_gb300 import synth
+    from paper_2207_14304_gb300.segment_workload import fill_batch
+    from paper_2207_14304_gb300.segments import SegmentBatch, autotune, tuned_config
+    per = 512
+    sides = synth.segment_sides(cameras * per, seed=4)
+    basis = B.make_basis(15, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)
+    key = f"segments_{cameras}x{per}_ks15"
+    cfg = tuned_config(key)
+    batch = SegmentBatch(sides, basis=basis, width=2048, cfg=cfg or B.argus_seg_config(8, 1, 4, 0),
+                         device=device.index)
+    try:
+        t0 = time.time()
+        fill_batch(batch, cameras, per)
+        gen_s = time.time() - t0
+        if cfg is None:
+            cfg = autotune(batch, key, repeats=1)
+        ms = timed_ms(lambda: batch.run(use_graph=True, stream=stream), 3, stream, device)
+        st = B.argus_sync_status(batch.ctx, stream)
+        nsrc = int(batch.n_found[0].item())
+        fit_items, sub_items = B.argus_segments_items(batch.plan)
+    finally:
+        batch.close()
+    px = sum(s * s for s in sides)
+    return {"workload": f"{cameras} cameras x {per} segments, 64-512 px log-uniform, 15x15 kernel per segment",
+            "segments": len(sides), "pixels": px, "ms": round(ms, 3), "value": round(px / 1e6 / (ms / 1e3), 1),
+            "unit": "Mpix/s", "config": {"fit_ctas_per_sm": cfg.fit_ctas_per_sm, "sub_ctas_per_sm": cfg.sub_ctas_per_sm},
+            "work_units": {"fit": fit_items, "subtract": sub_items}, "sources": nsrc, "status": st,
+            "generation_s": round(gen_s, 1)}
+
+
+def bench_learned(device, stream, train_pairs, epochs, log=None):
+    """Learned kernel vs least-squares fit on a 1-s frame (sky 10 e-, reference 1 px PSF):
+    CNN trained on plain-method fits, judged by chi2/dof against the plain fit."""
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    from paper_2207_14304_gb300 import synth
+    from paper_2207_14304_gb300.learned import KernelNet, LearnedFit, training_set
+    from paper_2207_14304_gb300.pipeline import FramePipeline
+    t0 = time.time()
+    x, t, _ = training_set(train_pairs, seed=5, device=device.index)
+    net = KernelNet(device=device.index, max_batch=512, seed=5)
+    hist = net.fit(x, t, epochs=epochs, batch=512, lr=1e-3)
+    train_s = time.time() - t0
+    del x, t
+    g = torch.Generator().manual_seed(50)
+    sig = float(torch.empty(1).uniform_(1.0, 3.0, generator=g))
+    cat = synth.star_catalog(N_STARS, W, H, seed=50, flux_min=1e2 / 30, flux_max=1e6 / 30)
+    R, Vr = synth.reference_image(synth.render(cat, W, H, 1.0, sky=10.0, device=device, dtype=torch.float32),
+                                  30, 1.7, 51)
+    cal = synth.make_calib(W, H, seed=52, device=device)
+    raw = synth.expose(synth.render(cat, W, H, sig, sky=10.0, device=device, dtype=torch.float32), cal, seed=53)
+    basis = B.make_basis(KSIZE, (0.7, 1.5, 3.0), (6, 4, 2), SDEG, BGDEG)
+    pipe = FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, psf_sigma=sig, max_peak=3.0e4, device=device.index)
+    try:
+        pitch = pipe.pitch
+
+        def pad(a):
+            z = torch.zeros((H, pitch), dtype=a.dtype, device=device)
+            z[:, :W] = a
+            return z
+        d_raw, d_R, d_Vr = pad(raw), pad(R), pad(Vr)
+        calib = B.make_calib(cal.bias, pad(cal.dark), pad(cal.flat), pad(cal.bpm), cal.gain, cal.read_noise, cal.sat)
+        del raw, R, Vr
+        lf = LearnedFit(pipe, net)
+        pipe.calibrate(d_raw, calib, stream)
+        pipe.select_stamps(d_R, stream)
+        plain_ms = timed_ms(lambda: pipe.fit(d_R, stream), 3, stream, device)
+        plain = pipe.fit_stats()
+        learned_ms = timed_ms(lambda: lf.learned_kernel(d_R, stream), 3, stream, device)
+        lst = B.fit_stats_from_bytes(lf.stats)
+        ratio = (lst["chi2"] / max(lst["dof"], 1)) / (plain["chi2"] / max(plain["dof"], 1))
+        lf.plain_chi2_dof = plain["chi2"] / max(plain["dof"], 1)
+        frame_ms = timed_ms(lambda: lf.run(d_raw, calib, d_R, d_Vr, stream), 3, stream, device)
+        plain_frame_ms = timed_ms(lambda: pipe.run(d_raw, calib, d_R, d_Vr, stream), 3, stream, device)
+        st = pipe.status(stream)
+    finally:
+        pipe.close()
+        net.close()
+    mpix = W * H / 1e6
+    return {"workload": f"9576x6388 1-s frame (sky 10 e-), science PSF {sig:.2f} px, reference 1.0 px, 400 stamps",
+            "train": {"pairs": train_pairs, "epochs": epochs, "loss_first": hist[0], "loss_last": hist[-1],
+                      "seconds": round(train_s, 1)},
+            "fit_ms": {"plain": round(plain_ms, 3), "learned": round(learned_ms, 3)},
+            "chi2_per_dof": {"plain": plain["chi2"] / max(plain["dof"], 1), "learned": lst["chi2"] / max(lst["dof"], 1),
+                             "ratio": round(ratio, 4)},
+            "fallback_rate": round(lf.n_fallback / max(lf.n_fallback + lf.n_learned, 1), 3),
+            "frame_mpix_s": {"learned_path": round(mpix / (frame_ms / 1e3), 1),
+                             "plain_path": round(mpix / (plain_frame_ms / 1e3), 1)},
+            "equal_chi2_within_2pct": bool(abs(ratio - 1) <= 0.02), "status": st}
 
 
 def load_peaks():
@@ -422,6 +586,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--segment-cameras", type=int, default=38)
+    ap.add_argument("--train-pairs", type=int, default=50_000)
+    ap.add_argument("--train-epochs", type=int, default=6)
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -26,8 +26,8 @@ def fill_batch(batch, cameras: int, per_camera: int, seed: int = 4, w: int = 957
         sig = synth.field_sigma(w, h, 1.3, 2.2)
         I, V = synth.calibrated_image(synth.render(cat, w, h, sig, sky=305.0, device=dev, dtype=torch.float32),
                                       1.7, sd + 2)
-        g = torch.Generator().manual_seed(sd * 31 + 7)
-        fl = (torch.rand((h, w), generator=g) < 1e-4).to(torch.uint8).to(dev)
+        g = torch.Generator(device=dev).manual_seed(sd * 31 + 7)
+        fl = (torch.rand((h, w), generator=g, device=dev) < 1e-4).to(torch.uint8)
         sides = sides_all[k:k + per_camera]
         origins = synth.segment_origins(sides, w, h, seed=sd)
         for j, ((x0, y0), s) in enumerate(zip(origins, sides)):

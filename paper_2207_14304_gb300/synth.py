@@ -232,9 +232,8 @@ def segment_sides(n: int, seed: int, smin=64, smax=512):
 def segment_origins(sides, w: int, h: int, seed: int):
     """Uniform top-left corners of squares of the given sides inside a w x h frame."""
     g = _gen(seed * 977 + 5)
-    out = []
-    for s in sides:
-        x0 = int(torch.randint(0, w - s + 1, (1,), generator=g))
-        y0 = int(torch.randint(0, h - s + 1, (1,), generator=g))
-        out.append((x0, y0))
-    return out
+    s = torch.as_tensor(list(sides), dtype=torch.float64)
+    u = torch.rand(len(s), 2, generator=g, dtype=torch.float64)
+    x0 = torch.floor(u[:, 0] * (w - s + 1)).to(torch.int64).tolist()
+    y0 = torch.floor(u[:, 1] * (h - s + 1)).to(torch.int64).tolist()
+    return list(zip(x0, y0))
