@@ -3,9 +3,11 @@
 // a 15-minute coadd; the clipped mean stands in for the matched filter there),
 // with calibration fused in.
 //
-// One thread per output pixel.  The frame loop is unrolled to the compile-time
-// stack bound NMAX so every per-frame value lives in a register at a static
-// index: invalid or absent frames hold +inf and sort to the end.  A bitonic
+// One thread per output pixel of a 32 x 8 tile.  Per frame, the raw window
+// the tile needs is loaded once, coalesced, and calibrated into shared memory.
+// The frame loop is unrolled to the compile-time stack bound NMAX so every
+// per-frame value lives in a register at a static index: invalid or absent
+// frames hold +inf and sort to the end.  A bitonic
 // network sorts the samples; because rejection |v - c| > kappa*s keeps a
 // value-closed set, the survivors stay one contiguous range [lo, hi) of the
 // sorted array, and every statistic is a predicated pass over static indices.
@@ -73,8 +75,45 @@ __device__ __forceinline__ float median_range(const float (&s)[N], int lo, int h
     return (n & 1) ? b : 0.5f * (a + b);
 }
 
+// One CTA per 32 x 8 output tile.  Phase 1 loads, for every frame, the
+// (33 x 9) window of raw pixels the tile's samples need -- placed at the
+// frame's integer offset -- with coalesced reads (all frames' loads in flight
+// together) and calibrates each pixel once into shared memory: value, or NaN
+// where the pixel is unusable, and variance.  Phase 2: each thread
+// interpolates its samples from four shared values per frame, sorts them in
+// registers and clips; the survivors' variances are recomputed from shared
+// memory in the last pass instead of being held in registers.
+constexpr int CTX = 32, CTY = 8, CWX = CTX + 1, CWY = CTY + 1, CWN = CWX * CWY;
+
+__device__ __forceinline__ float qnan() { return __int_as_float(0x7fffffff); }
+
+// Bilinear sample of one frame from its calibrated window (nested lerps with
+// explicit fused multiply-adds, so that the two evaluations of a sample in the
+// kernel round identically).  Non-finite when a needed pixel is unusable.
+__device__ __forceinline__ float sample(const float* wv, int o, float fx, float fy) {
+    const bool n1 = fx > 0.0f, n2 = fy > 0.0f;
+    const float v00 = wv[o];
+    const float v10 = n1 ? wv[o + 1] : v00;
+    const float v01 = n2 ? wv[o + CWX] : v00;
+    const float v11 = (n1 && n2) ? wv[o + CWX + 1] : (n1 ? v10 : v01);
+    const float top = __fmaf_rn(fx, __fsub_rn(v10, v00), v00);
+    const float bot = __fmaf_rn(fx, __fsub_rn(v11, v01), v01);
+    return __fmaf_rn(fy, __fsub_rn(bot, top), top);
+}
+
+__device__ __forceinline__ float sample_var(const float* wr, int o, float fx, float fy) {
+    const bool n1 = fx > 0.0f, n2 = fy > 0.0f;
+    const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy);
+    const float w2 = (1.0f - fx) * fy, w3 = fx * fy;
+    return w0 * w0 * wr[o] + (n1 ? w1 * w1 * wr[o + 1] : 0.0f) + (n2 ? w2 * w2 * wr[o + CWX] : 0.0f) +
+           (n1 && n2 ? w3 * w3 * wr[o + CWX + 1] : 0.0f);
+}
+
 template <int NMAX>
-__global__ void __launch_bounds__(128) coadd_kernel(CoaddArgs a) {
+__global__ void __launch_bounds__(CTX * CTY) coadd_kernel(CoaddArgs a) {
+    extern __shared__ float4 coadd_smem[];
+    float* wv = reinterpret_cast<float*>(coadd_smem);   // [nf][CWY][CWX] values
+    float* wr = wv + a.nf * CWN;                         // [nf][CWY][CWX] variances
     __shared__ int s_ix[NMAX], s_iy[NMAX];
     __shared__ float s_fx[NMAX], s_fy[NMAX];
     for (int f = threadIdx.x; f < NMAX; f += blockDim.x) {
@@ -89,45 +128,64 @@ __global__ void __launch_bounds__(128) coadd_kernel(CoaddArgs a) {
             s_ix[f] = 0; s_iy[f] = 0; s_fx[f] = 0.0f; s_fy[f] = 0.0f;
         }
     }
-    __syncthreads();
-    const long np = (long)a.w * a.h;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < np; e += (long)gridDim.x * blockDim.x) {
-        const int y = (int)(e / a.w), x = (int)(e - (long)y * a.w);
-        float v[NMAX], vv[NMAX];
+    const int ntx = (a.w + CTX - 1) / CTX, nty = (a.h + CTY - 1) / CTY;
+    const int lx = threadIdx.x % CTX, ly = threadIdx.x / CTX;
+    const int o = ly * CWX + lx;
+    const int tot = a.nf * CWN;
+    constexpr int U = 4;
+    for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+        const int tx0 = (tile % ntx) * CTX, ty0 = (tile / ntx) * CTY;
+        const int x = tx0 + lx, y = ty0 + ly;
+        __syncthreads();   // shifts staged; previous tile's windows consumed
+        for (int e0 = threadIdx.x; e0 < tot; e0 += U * CTX * CTY) {
+            int raw[U];
+            long p[U];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int e = e0 + u * CTX * CTY;
+                const int f = e / CWN, j = e - f * CWN;
+                const int jy = j / CWX, jx = j - jy * CWX;
+                const int gx = tx0 + s_ix[f < a.nf ? f : 0] + jx, gy = ty0 + s_iy[f < a.nf ? f : 0] + jy;
+                in[u] = e < tot && gx >= 0 && gy >= 0 && gx < a.w && gy < a.h;
+                p[u] = in[u] ? (long)gy * a.pitch + gx : 0;
+                raw[u] = in[u] ? (int)__ldg(a.raw + (long)f * a.frame_stride + p[u]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int e = e0 + u * CTX * CTY;
+                if (e >= tot) break;
+                float cv = qnan(), cr = 0.0f;
+                if (in[u]) {
+                    const float fl = a.flat ? __ldg(a.flat + p[u]) : 1.0f;
+                    const bool bad = (a.bpm && __ldg(a.bpm + p[u])) || !(fl > 0.0f) || !(fl <= 3.402823466e38f) ||
+                                     raw[u] >= a.sat;
+                    if (!bad) {
+                        const float ng = (float)(raw[u] - a.bias) * a.gain;
+                        cv = (ng - (a.dark ? __ldg(a.dark + p[u]) : 0.0f)) / fl;
+                        cr = (fmaxf(ng, 0.0f) + a.rn2) / (fl * fl);
+                        if (!(fabsf(cv) <= 3.402823466e38f)) cv = qnan();   // non-finite: unusable
+                    }
+                }
+                wv[e] = cv;
+                wr[e] = cr;
+            }
+        }
+        __syncthreads();
+        if (x >= a.w || y >= a.h) continue;
+        float s[NMAX];
         int n = 0;
 #pragma unroll
         for (int f = 0; f < NMAX; f++) {
-            v[f] = __int_as_float(0x7f800000);   // +inf: absent
-            vv[f] = 0.0f;
+            float sv = __int_as_float(0x7f800000);   // +inf: absent or invalid
             if (f < a.nf) {
-                const int ix = x + s_ix[f], iy = y + s_iy[f];
-                const float fx = s_fx[f], fy = s_fy[f];
-                const bool n1 = fx > 0.0f, n2 = fy > 0.0f;
-                float v00, r00, v10 = 0.0f, r10 = 0.0f, v01 = 0.0f, r01 = 0.0f, v11 = 0.0f, r11 = 0.0f;
-                bool ok = calib_px(a, f, ix, iy, v00, r00);
-                if (ok && n1) ok = calib_px(a, f, ix + 1, iy, v10, r10);
-                if (ok && n2) ok = calib_px(a, f, ix, iy + 1, v01, r01);
-                if (ok && n1 && n2) ok = calib_px(a, f, ix + 1, iy + 1, v11, r11);
-                if (ok) {
-                    if (!n1) v10 = v00;
-                    if (!n2) v01 = v00;
-                    if (!(n1 && n2)) v11 = n1 ? v10 : v01;
-                    const float top = v00 + fx * (v10 - v00);
-                    const float bot = v01 + fx * (v11 - v01);
-                    const float sv = top + fy * (bot - top);
-                    ok = isfinite(sv);
-                    v[f] = ok ? sv : __int_as_float(0x7f800000);
-                    const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy);
-                    const float w2 = (1.0f - fx) * fy, w3 = fx * fy;
-                    vv[f] = w0 * w0 * r00 + (n1 ? w1 * w1 * r10 : 0.0f) + (n2 ? w2 * w2 * r01 : 0.0f) +
-                            (n1 && n2 ? w3 * w3 * r11 : 0.0f);
-                    n += ok ? 1 : 0;
-                }
+                const float v = sample(wv + f * CWN, o, s_fx[f], s_fy[f]);
+                const bool ok = fabsf(v) <= 3.402823466e38f;
+                sv = ok ? v : sv;
+                n += ok ? 1 : 0;
             }
+            s[f] = sv;
         }
-        float s[NMAX];
-#pragma unroll
-        for (int f = 0; f < NMAX; f++) s[f] = v[f];
         bitonic_sort(s);
         int lo = 0, hi = n;
         for (int it = 0; it < a.max_iter && hi > lo; it++) {
@@ -166,23 +224,34 @@ __global__ void __launch_bounds__(128) coadd_kernel(CoaddArgs a) {
         const int cnt = hi - lo;
         const float c = median_range(s, lo, hi);
         const float vlo = pick(s, lo), vhi = pick(s, hi - 1);
-        float sd = 0.0f, sv = 0.0f;
+        float sd = 0.0f, svar = 0.0f;
 #pragma unroll
         for (int i = 0; i < NMAX; i++) sd += (i >= lo && i < hi) ? s[i] - c : 0.0f;
-#pragma unroll
-        for (int f = 0; f < NMAX; f++) sv += (v[f] >= vlo && v[f] <= vhi) ? vv[f] : 0.0f;
+        for (int f = 0; f < a.nf; f++) {
+            const float fx = s_fx[f], fy = s_fy[f];
+            const float v = sample(wv + f * CWN, o, fx, fy);
+            if (v >= vlo && v <= vhi) svar += sample_var(wr + f * CWN, o, fx, fy);
+        }
         a.coadd[p] = c + sd / (float)cnt;
-        a.var[p] = sv / ((float)cnt * (float)cnt);
+        a.var[p] = svar / ((float)cnt * (float)cnt);
         a.n_used[p] = (uint8_t)cnt;
     }
 }
 
 template <int NMAX>
 int launch(const CoaddArgs& a, int sms, cudaStream_t st) {
-    const long np = (long)a.w * a.h;
-    long blocks = (np + 127) / 128;
-    if (blocks > (long)sms * 16) blocks = (long)sms * 16;
-    coadd_kernel<NMAX><<<(unsigned)blocks, 128, 0, st>>>(a); argus_count_launch(1);
+    const size_t smem = (size_t)a.nf * CWN * 2 * sizeof(float);
+    if (cudaFuncSetAttribute(coadd_kernel<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coadd_kernel<NMAX>, CTX * CTY, smem) != cudaSuccess ||
+        per_sm < 1)
+        return ARGUS_ERR_CUDA;
+    const long tiles = (long)((a.w + CTX - 1) / CTX) * ((a.h + CTY - 1) / CTY);
+    long blocks = tiles;
+    if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
+    coadd_kernel<NMAX><<<(unsigned)blocks, CTX * CTY, smem, st>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }
 
