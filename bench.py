@@ -41,14 +41,32 @@ STAMP = 21
 # flags (9 B) are written and read back once between the calibration and subtraction
 # kernels and are not counted (a fused kernel would not move them).
 BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
+# DRAM traffic of one subtract launch, bytes per frame pixel: dram__bytes_read.sum +
+# dram__bytes_write.sum of an ncu capture of a 4096x4096 launch (395.1 MB / 4096^2),
+# scaled by pixels to the frame (the kernel streams its tiles once, so traffic grows in
+# proportion).  It holds only for the kernel sources it was taken on.
+SUBTRACT_TRAFFIC = {"bytes_per_px": 23.55, "sources_sha1": "e2360219614c799b4ef9bb0362a354770ef02db8"}
+SUBTRACT_SOURCES = ("subtract.cu", "subtract_tile.cuh")
+
+
+def subtract_traffic_bytes():
+    import hashlib
+    h = hashlib.sha1()
+    for f in SUBTRACT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_14304_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != SUBTRACT_TRAFFIC["sources_sha1"]:
+        return None
+    return int(SUBTRACT_TRAFFIC["bytes_per_px"] * W * H)
 
 
 def workload_config(precision="fp32"):
-    return {"workload": "full-frame plain DIA, 9576x6388 uint16 IMX455 frame + float32 reference",
+    return {"workload": f"full-frame plain DIA, {W}x{H} uint16 IMX455 frame + float32 reference",
             "frame": [W, H], "stars": N_STARS, "psf_sigma": "1.3-2.2 px (science), 1.2 px (reference)",
             "kernel": KSIZE, "spatial_degree": SDEG, "bg_degree": BGDEG, "basis": "3 Gaussians x degrees (6,4,2)",
             "stamps": GRID[0] * GRID[1], "stamp": STAMP, "normal_equations": precision, "nsigma": 5.0,
-            "l2": "working set > 129 MB L2 per step (raw 122 MB + reference/variances 490 MB); no flush"}
+            "l2": (f"working set {W * H * 10 / 1e6:.0f} MB per step (raw {W * H * 2 / 1e6:.0f} MB + reference and "
+                   f"variances {W * H * 8 / 1e6:.0f} MB) against the 129 MB L2; no flush")}
 
 
 # --------------------------------------------------------------------------- distributed helpers
@@ -296,7 +314,7 @@ def run_gpu(args):
         "config": workload_config(args.precision),
         "roofline": {"bound": "alu", "kernel": "subtract", "achieved": round(achieved, 3),
                      "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
-                     "traffic": None,
+                     "traffic": subtract_traffic_bytes(), "traffic_unit": "bytes per launch (ncu DRAM read+write)",
                      "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz (median SM clock under load)"},
         "hbm_roofline_frac": round(hbm_frac, 4),
         "hbm_bytes_per_px": BYTES_PER_PX,
@@ -311,9 +329,12 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if args.extras and ws == 1:
         extras = {}
+        wanted = set(x for x in args.extras.split(",") if x)
         for name, fn in (("coadd", lambda: bench_coadd(device, stream, args.steps, hbm)),
                          ("segments", lambda: bench_segments(device, stream, args.segment_cameras)),
                          ("learned", lambda: bench_learned(device, stream, args.train_pairs, args.train_epochs))):
+            if name not in wanted:
+                continue
             try:
                 extras[name] = fn()
             except Exception as e:   # an extra never invalidates the headline line
@@ -378,7 +399,7 @@ def bench_coadd(device, stream, steps, hbm):
     finally:
         B.argus_destroy(ctx)
     bpp = nf * 2 + 9 + 9
-    return {"workload": "30 x 9576x6388 uint16, shifts <= 0.5 px, 1% cosmic rays, kappa 3, 5 iterations",
+    return {"workload": f"30 x {W}x{H} uint16, shifts <= 0.5 px, 1% cosmic rays, kappa 3, 5 iterations",
             "ms": round(ms, 3), "value": round(W * H / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s (output)",
             "hbm_bytes_per_px": bpp, "hbm_frac": round(bpp * W * H / (ms / 1e3) / 1e9 / hbm, 4), "status": st}
 
@@ -467,7 +488,7 @@ def bench_learned(device, stream, train_pairs, epochs, log=None):
         pipe.close()
         net.close()
     mpix = W * H / 1e6
-    return {"workload": f"9576x6388 1-s frame (sky 10 e-), science PSF {sig:.2f} px, reference 1.0 px, 400 stamps",
+    return {"workload": f"{W}x{H} 1-s frame (sky 10 e-), science PSF {sig:.2f} px, reference 1.0 px, 400 stamps",
             "train": {"pairs": train_pairs, "epochs": epochs, "loss_first": hist[0], "loss_last": hist[-1],
                       "seconds": round(train_s, 1)},
             "fit_ms": {"plain": round(plain_ms, 3), "learned": round(learned_ms, 3)},
@@ -540,7 +561,7 @@ def oracle_sample(band_rows=48, seed=2, threads=None):
     t_frame = t_cal_full + t_sel + t_fit + t_band * H / band_rows
     return {"value": round(W * H / 1e6 / t_frame, 4), "unit": "Mpix/s", "cores": cores, "kind": "oracle",
             "sample": (f"full calibration ({t_cal_full:.2f} s), stamp selection ({t_sel:.2f} s) and 400-stamp "
-                       f"kernel fit ({t_fit:.2f} s) of one 9576x6388 frame, subtraction+detection on a "
+                       f"kernel fit ({t_fit:.2f} s) of one {W}x{H} frame, subtraction+detection on a "
                        f"{band_rows}-row band ({t_band:.2f} s) scaled x{H / band_rows:.1f} to the frame"),
             "seconds": round(t_cal_full + t_sel + t_fit + t_band, 2)}
 
@@ -586,11 +607,20 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
-    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--extras", default="coadd,segments,learned",
+                    help="comma list of the extra workloads to measure after the headline")
+    ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
+    ap.add_argument("--frame", type=int, nargs=2, metavar=("W", "H"), default=None,
+                    help="smaller frame for profiling captures (star count scaled by area)")
     ap.add_argument("--segment-cameras", type=int, default=38)
     ap.add_argument("--train-pairs", type=int, default=50_000)
     ap.add_argument("--train-epochs", type=int, default=6)
     args = ap.parse_args(argv)
+    if args.frame:
+        global W, H, N_STARS
+        fw, fh = args.frame
+        N_STARS = max(1, int(N_STARS * fw * fh / (W * H)))
+        W, H = fw, fh
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":
