@@ -12,7 +12,7 @@ import torch
 
 from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300 import synth
-from paper_2207_14304_gb300.segments import SegmentBatch, pack_shelves
+from paper_2207_14304_gb300.segments import SegmentBatch
 
 pytestmark = pytest.mark.gpu
 
@@ -95,14 +95,3 @@ def test_segments_parity(ora, use_graph):
         print(f"\n[segments graph={use_graph}] {len(sides)} segments, {nsrc} sources, checked {n_checked}")
     finally:
         batch.close()
-
-
-def test_pack_shelves_no_overlap():
-    sides = synth.segment_sides(300, seed=4)
-    pos, hgt = pack_shelves(sides, 2048)
-    occ = np.zeros((hgt, 2048), np.int32)
-    for (r, c), s in zip(pos, sides):
-        assert r % 16 == 0 and c % 16 == 0 and c + s <= 2048 and r + s <= hgt
-        occ[r:r + s, c:c + s] += 1
-    assert occ.max() == 1
-    assert occ.sum() / occ.size > 0.6

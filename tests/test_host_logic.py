@@ -1,0 +1,140 @@
+"""Host-side logic that needs no GPU: atlas packing, the autotuner's table, the
+bench's multi-rank aggregation (two gloo ranks on the CPU), the reference arm's
+rank handling and the clock-record parsing."""
+from __future__ import annotations
+
+import json
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2207_14304_gb300 import synth  # noqa: E402
+from paper_2207_14304_gb300.segments import candidate_configs, pack_shelves, tuned_config  # noqa: E402
+
+
+def test_pack_shelves_no_overlap():
+    sides = synth.segment_sides(300, seed=4)
+    pos, hgt = pack_shelves(sides, 2048)
+    occ = np.zeros((hgt, 2048), np.int32)
+    for (r, c), s in zip(pos, sides):
+        assert r % 16 == 0 and c % 16 == 0 and c + s <= 2048 and r + s <= hgt
+        occ[r:r + s, c:c + s] += 1
+    assert occ.max() == 1
+    assert occ.sum() / occ.size > 0.6
+
+
+def test_pack_shelves_edge_cases():
+    pos, hgt = pack_shelves([], 2048)
+    assert pos == [] and hgt == 0
+    pos, hgt = pack_shelves([2048], 2048)
+    assert pos == [(0, 0)] and hgt == 2048
+    # equal squares fill shelves left to right, 16-aligned
+    pos, hgt = pack_shelves([40] * 5, 100)
+    assert all(c % 16 == 0 and c + 40 <= 100 for _, c in pos)
+    assert len(set(pos)) == 5
+
+
+def test_tuned_config_table(tmp_path):
+    path = str(tmp_path / "tune.json")
+    assert tuned_config("k", table_path=path) is None
+    json.dump({"k": {"fit_band": 8, "fit_ctas_per_sm": 2, "sub_ctas_per_sm": 6}}, open(path, "w"))
+    c = tuned_config("k", table_path=path)
+    assert (c.fit_band, c.fit_ctas_per_sm, c.sub_ctas_per_sm) == (8, 2, 6)
+    assert tuned_config("other", table_path=path) is None
+    open(path, "w").write("{not json")
+    assert tuned_config("k", table_path=path) is None
+    cands = candidate_configs()
+    assert len(cands) == len(set(cands)) and all(c[0] == 8 for c in cands)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, out_dir):
+    os.environ.update({"RANK": str(rank), "LOCAL_RANK": str(rank), "WORLD_SIZE": str(ws),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    assert bench.dist_env() == (ws, rank, rank)
+    dist = bench.dist_init(ws, "gloo")
+    bench.barrier(dist)
+    # rank r processed 10 units in (r + 1) seconds: the job is timed by the slowest rank
+    value, tmax = bench.aggregate(10.0, float(rank + 1), dist)
+    mx = bench.max_over_ranks(dist, 100.0 - rank, None)
+    bench.barrier(dist)
+    json.dump({"value": value, "tmax": tmax, "max": mx}, open(os.path.join(out_dir, f"r{rank}.json"), "w"))
+    dist.destroy_process_group()
+
+
+def test_aggregate_two_gloo_ranks(tmp_path):
+    ws = 2
+    mp.start_processes(_rank_main, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, join=True,
+                       start_method="spawn")
+    for r in range(ws):
+        d = json.load(open(tmp_path / f"r{r}.json"))
+        assert d["tmax"] == 2.0                    # max over ranks
+        assert d["value"] == pytest.approx(10.0 * ws / 2.0)
+        assert d["max"] == 100.0
+
+
+def test_single_rank_helpers_are_identity():
+    assert bench.max_over_ranks(None, 3.5) == 3.5
+    assert bench.aggregate(10.0, 2.0, None) == (5.0, 2.0)
+    bench.barrier(None)
+
+
+def test_reference_arm_non_zero_rank_does_no_work(monkeypatch, capsys):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    monkeypatch.setattr(bench, "oracle_sample", lambda **k: pytest.fail("rank 1 ran the oracle"))
+    bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"])
+    assert capsys.readouterr().out == ""
+
+
+def test_parse_clocks(tmp_path):
+    p = tmp_path / "clocks.csv"
+    p.write_text(
+        "0, 1900, 2070, 900.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 1950, 2070, 950.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 2000, 2070, 990.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    c = bench.parse_clocks(str(p))
+    assert c["sm_mhz"] == 1950 and c["sm_max_mhz"] == 2070 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    p.write_text("0, 700, 2070, 500, 0x8, Active, Not Active, Not Active, Not Active\n")
+    assert bench.parse_clocks(str(p))["reasons"] == ["hw_slowdown"]
+    p.write_text("")
+    assert bench.parse_clocks(str(p)) is None
+
+
+def test_frame_override_scales_the_workload():
+    saved = (bench.W, bench.H, bench.N_STARS)
+    try:
+        args = []
+        ap_main = bench.main
+
+        def fake_run(a):
+            args.append((bench.W, bench.H, bench.N_STARS, a.extras))
+
+        bench.run_gpu, orig = fake_run, bench.run_gpu
+        try:
+            ap_main(["--frame", "4096", "4096", "--extras", "coadd"])
+        finally:
+            bench.run_gpu = orig
+        w, h, n, extras = args[0]
+        assert (w, h) == (4096, 4096) and n == int(150_000 * 4096 * 4096 / (9576 * 6388))
+        assert extras == "coadd"
+        assert bench.workload_config()["frame"] == [4096, 4096]
+    finally:
+        bench.W, bench.H, bench.N_STARS = saved
