@@ -1084,6 +1084,139 @@ __global__ void select_ring_kernel(const float* R, const uint8_t* flags, const u
     }
 }
 
+// Tiled form for the context path (isolation radius <= 32).  Per 64 x 32
+// tile: R over the tile plus a halo of iso + 1 goes to shared memory; the
+// strict local maxima of the tile plus iso become a masked copy (R there,
+// -inf elsewhere).  The brightest other local maximum within iso of a
+// candidate is the maximum of (a) the row maxima over [x - iso, x + iso] of
+// every window row but the candidate's own and (b) its own row without the
+// candidate; the row maxima are one separable pass (two outputs per thread,
+// sharing the common taps), (a) and (b) are taken for the candidates only.
+// Isolation is then one comparison with iso_frac * c.  Survivors get a
+// warp-wide scan of their flag window and the cell atomicMax.  The decisions
+// are those of the per-pixel rule above.
+constexpr int SEL_TX = 64, SEL_TY = 32, SEL_MAX_ISO = 32;
+
+__host__ __device__ inline size_t select_tile_smem(int iso) {
+    const size_t rw = SEL_TX + 2 * iso + 2, rh = SEL_TY + 2 * iso + 2;
+    const size_t lw = SEL_TX + 2 * iso, lh = SEL_TY + 2 * iso;
+    const size_t a = rw * rh * sizeof(float), b = lh * SEL_TX * sizeof(float);
+    return (a > b ? a : b) + lw * lh * sizeof(float) + 2 * SEL_TX * SEL_TY * sizeof(unsigned short) + 16;
+}
+
+__global__ void __launch_bounds__(256) select_tile_kernel(const float* R, const uint8_t* flags, long pitch, int w,
+                                                          int h, int gx, int gy, int m, float max_peak, int iso,
+                                                          float iso_frac, unsigned long long* cell_key) {
+    extern __shared__ float4 sel_smem[];
+    const int RW = SEL_TX + 2 * iso + 2, RH = SEL_TY + 2 * iso + 2;   // both even
+    const int LW = SEL_TX + 2 * iso, LH = SEL_TY + 2 * iso;
+    const size_t ua = (size_t)RW * RH * sizeof(float), ub = (size_t)LH * SEL_TX * sizeof(float);
+    float* r = reinterpret_cast<float*>(sel_smem);                  // [RH][RW], then reused:
+    float* rowm = reinterpret_cast<float*>(sel_smem);               // [LH][SEL_TX] row maxima
+    float* mv = reinterpret_cast<float*>(reinterpret_cast<char*>(sel_smem) + (ua > ub ? ua : ub));   // [LH][LW]
+    unsigned short* cand = reinterpret_cast<unsigned short*>(mv + (size_t)LW * LH);
+    unsigned short* surv = cand + SEL_TX * SEL_TY;
+    __shared__ int n_cand, n_surv;
+    const int ntx = (w + SEL_TX - 1) / SEL_TX;
+    const int x0 = (int)(blockIdx.x % ntx) * SEL_TX, y0 = (int)(blockIdx.x / ntx) * SEL_TY;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) { n_cand = 0; n_surv = 0; }
+    // 1. R over the tile + (iso + 1)
+    for (int jy = wid; jy < RH; jy += nw) {
+        const int Y = y0 - iso - 1 + jy;
+        const bool yin = Y >= 0 && Y < h;
+        const float* src = R + (long)(yin ? Y : 0) * pitch;
+        for (int jx = lane; jx < RW; jx += 32) {
+            const int X = x0 - iso - 1 + jx;
+            r[jy * RW + jx] = (yin && X >= 0 && X < w) ? __ldg(src + X) : 0.0f;
+        }
+    }
+    __syncthreads();
+    // 2. masked local maxima over the tile + iso
+    const float NEG = __int_as_float(0xff800000);
+    for (int jy = wid; jy < LH; jy += nw) {
+        const int Y = y0 - iso + jy;
+        const bool yin = Y >= 1 && Y <= h - 2;
+        for (int jx = lane; jx < LW; jx += 32) {
+            const int X = x0 - iso + jx;
+            const float* q = r + (jy + 1) * RW + (jx + 1);
+            const float c = q[0];
+            const float nb = fmaxf(fmaxf(fmaxf(q[-RW - 1], q[-RW]), fmaxf(q[-RW + 1], q[-1])),
+                                   fmaxf(fmaxf(q[1], q[RW - 1]), fmaxf(q[RW], q[RW + 1])));
+            // strict maximum: c above every neighbour (a NaN neighbour fails the test)
+            bool l = yin && X >= 1 && X <= w - 2 && isfinite(c) && c > nb;
+            l = l && !(isnan(q[-RW - 1]) || isnan(q[-RW]) || isnan(q[-RW + 1]) || isnan(q[-1]) || isnan(q[1]) ||
+                       isnan(q[RW - 1]) || isnan(q[RW]) || isnan(q[RW + 1]));
+            mv[jy * LW + jx] = l ? c : NEG;
+        }
+    }
+    __syncthreads();
+    // 3. row maxima over [x - iso, x + iso] for every row of the tile + iso, two
+    //    outputs (x, x + 1) per thread from float2 loads; r is dead
+    for (int e = tid; e < LH * (SEL_TX / 2); e += blockDim.x) {
+        const int jy = e >> 5, x = 2 * (e & 31);
+        const float2* q = reinterpret_cast<const float2*>(mv + jy * LW + x);   // taps x .. x + 2 iso + 1
+        const float2 first = q[0], last = q[iso];
+        float core = iso > 0 ? fmaxf(first.y, last.x) : NEG;     // taps x + 1 .. x + 2 iso
+        for (int k = 1; k < iso; k++) {
+            const float2 t = q[k];
+            core = fmaxf(core, fmaxf(t.x, t.y));
+        }
+        *reinterpret_cast<float2*>(rowm + jy * SEL_TX + x) = make_float2(fmaxf(core, first.x), fmaxf(core, last.y));
+    }
+    // 4. candidates: strict local maxima whose stamp window is inside the frame, below max_peak
+    for (int e0 = 0; e0 < SEL_TX * SEL_TY; e0 += blockDim.x) {
+        const int e = e0 + tid;
+        const int y = e / SEL_TX, x = e - y * SEL_TX;
+        const int X = x0 + x, Y = y0 + y;
+        const float c = mv[(y + iso) * LW + x + iso];
+        const bool ok = X - m >= 0 && X + m <= w - 1 && Y - m >= 0 && Y + m <= h - 1 && c > NEG && c < max_peak;
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&n_cand, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) cand[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)e;
+    }
+    __syncthreads();
+    // 5. isolation: the brightest other local maximum within iso
+    for (int i = tid; i < n_cand; i += blockDim.x) {
+        const int e = cand[i];
+        const int y = e / SEL_TX, x = e - y * SEL_TX;
+        const float* own = mv + (y + iso) * LW + x;                // own row, taps x - iso .. x + iso
+        const float c = own[iso];
+        float other = NEG;
+        for (int d = 0; d < iso; d++) {
+            other = fmaxf(other, fmaxf(rowm[(y + d) * SEL_TX + x], rowm[(y + iso + 1 + d) * SEL_TX + x]));
+            other = fmaxf(other, fmaxf(own[d], own[iso + 1 + d]));
+        }
+        if (!(other > iso_frac * c)) surv[atomicAdd(&n_surv, 1)] = (unsigned short)e;
+    }
+    __syncthreads();
+    // 6. flag window, one warp per survivor
+    for (int i = wid; i < n_surv; i += nw) {
+        const int e = surv[i];
+        const int y = e / SEL_TX, x = e - y * SEL_TX;
+        const int X = x0 + x, Y = y0 + y;
+        // the (2m+1)^2 window as independent loads spread over the lanes
+        const int side = 2 * m + 1, nwin = side * side;
+        const uint8_t* base = flags + (long)(Y - m) * pitch + (X - m);
+        unsigned f = 0;
+#pragma unroll 8
+        for (int q = lane; q < nwin; q += 32) {
+            const int qy = q / side;
+            f |= __ldg(base + (long)qy * pitch + (q - qy * side));
+        }
+        if (__any_sync(0xffffffffu, f != 0) || lane != 0) continue;
+        const float c = mv[(y + iso) * LW + x + iso];
+        const int cx = (int)(((long)(X + 1) * gx - 1) / w), cy = (int)(((long)(Y + 1) * gy - 1) / h);
+        const unsigned bits = __float_as_uint(c);
+        const unsigned ord = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+        const unsigned rank = (unsigned)Y * (unsigned)w + (unsigned)X;
+        const unsigned long long key = ((unsigned long long)ord << 32) | (unsigned long long)(0xffffffffu - rank);
+        atomicMax(cell_key + cy * gx + cx, key);
+    }
+}
+
 __global__ void __launch_bounds__(1024) select_compact_kernel(const unsigned long long* cell_key, int ncell, int w,
                                                               int* centers, int* n_out) {
     __shared__ int wsum[32];
@@ -1335,12 +1468,23 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     const long np = (long)shape.w * shape.h;
     long blocks = (np + 255) / 256;
     if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
-    uint8_t* lmax = reinterpret_cast<uint8_t*>(ctx->label);   // the label scratch, one byte per pixel
-    const long rblocks = (np + 255) / 256;                      // one pixel per thread: latency-bound scans
-    select_lmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, shape.pitch, shape.w, shape.h, lmax); argus_count_launch(1);
-    select_ring_kernel<<<(unsigned)rblocks, 256, 0, st>>>(ref, flags, lmax, shape.pitch, shape.w, shape.h, grid_x,
-                                                         grid_y, stamp / 2 + khalf, max_peak, iso, iso_frac,
-                                                         ctx->cell_key); argus_count_launch(1);
+    if (iso <= SEL_MAX_ISO) {
+        const size_t smem = select_tile_smem(iso);
+        if (cudaFuncSetAttribute(select_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return ARGUS_ERR_CUDA;
+        const long tiles = (long)((shape.w + SEL_TX - 1) / SEL_TX) * ((shape.h + SEL_TY - 1) / SEL_TY);
+        select_tile_kernel<<<(unsigned)tiles, 256, smem, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x,
+                                                               grid_y, stamp / 2 + khalf, max_peak, iso, iso_frac,
+                                                               ctx->cell_key); argus_count_launch(1);
+    } else {
+        uint8_t* lmax = reinterpret_cast<uint8_t*>(ctx->label);   // the label scratch, one byte per pixel
+        const long rblocks = (np + 255) / 256;                      // one pixel per thread: latency-bound scans
+        select_lmax_kernel<<<(unsigned)blocks, 256, 0, st>>>(ref, shape.pitch, shape.w, shape.h, lmax); argus_count_launch(1);
+        select_ring_kernel<<<(unsigned)rblocks, 256, 0, st>>>(ref, flags, lmax, shape.pitch, shape.w, shape.h,
+                                                             grid_x, grid_y, stamp / 2 + khalf, max_peak, iso,
+                                                             iso_frac, ctx->cell_key); argus_count_launch(1);
+    }
     select_compact_kernel<<<1, 1024, 0, st>>>(ctx->cell_key, ncell, shape.w, centers, n_stamps); argus_count_launch(1);
     return argus_launch_status();
 }

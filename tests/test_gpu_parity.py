@@ -174,23 +174,88 @@ def _ref_field(w, h, seed, n=300):
     return R.numpy(), Vr.numpy()
 
 
-@pytest.mark.parametrize("w,h,gx,gy", [(300, 260, 4, 3), (257, 129, 5, 2)])
-def test_select_stamps_parity(ora, w, h, gx, gy):
-    R, _ = _ref_field(w, h, seed=w)
+@pytest.mark.parametrize("w,h,gx,gy,iso,iso_frac,max_peak", [
+    (300, 260, 4, 3, 10, 0.1, 3.0e4),
+    (257, 129, 5, 2, 10, 0.1, 3.0e4),      # ragged tiles in x and y
+    (300, 260, 4, 3, 0, 0.1, 3.0e4),       # no isolation window
+    (300, 260, 4, 3, 3, 0.5, 3.0e4),
+    (300, 260, 6, 6, 32, 0.5, 3.0e4),      # widest window of the tiled kernel
+    (300, 260, 4, 3, 40, 0.5, 3.0e4),      # wider: the per-pixel ring kernel
+    (300, 260, 4, 3, 10, 0.1, 1.0e4),      # bright stars excluded by max_peak
+])
+def test_select_stamps_parity(ora, w, h, gx, gy, iso, iso_frac, max_peak):
+    R, _ = _ref_field(w, h, seed=w + iso)
     rng = np.random.default_rng(1)
     fl = (rng.random((h, w)) < 0.0005).astype(np.uint8)
-    co = ora.select_stamps(R, fl, gx, gy, 21, 5, 3.0e4)
+    co = ora.select_stamps(R, fl, gx, gy, 21, 5, max_peak, iso=iso, iso_frac=iso_frac)
     pitch = pitch_for(w)
     ctx = ctx_for(w, h)
     try:
         cen = torch.full((gx * gy, 2), -1, dtype=torch.int32, device="cuda")
         ns = torch.zeros(4, dtype=torch.int32, device="cuda")
         B.argus_select_stamps(ctx, dev_pitched(R), dev_pitched(fl), B.argus_shape(w, h, pitch), gx, gy, 21, 5,
-                              3.0e4, 10, 0.1, cen, ns)
+                              max_peak, iso, iso_frac, cen, ns)
         torch.cuda.synchronize()
         n = int(ns[0].item())
         assert n == len(co) and n > 0
         np.testing.assert_array_equal(cen[:n].cpu().numpy(), co)
+    finally:
+        B.argus_destroy(ctx)
+
+
+def _select_both(ora, R, fl, gx, gy, iso=10, iso_frac=0.1, max_peak=3.0e4):
+    h, w = R.shape
+    co = ora.select_stamps(R, fl, gx, gy, 21, 5, max_peak, iso=iso, iso_frac=iso_frac)
+    ctx = ctx_for(w, h)
+    try:
+        cen = torch.full((gx * gy, 2), -1, dtype=torch.int32, device="cuda")
+        ns = torch.zeros(4, dtype=torch.int32, device="cuda")
+        B.argus_select_stamps(ctx, dev_pitched(R), dev_pitched(fl), B.argus_shape(w, h, pitch_for(w)), gx, gy, 21,
+                              5, max_peak, iso, iso_frac, cen, ns)
+        torch.cuda.synchronize()
+        n = int(ns[0].item())
+        assert n == len(co)
+        np.testing.assert_array_equal(cen[:n].cpu().numpy(), co)
+        return co
+    finally:
+        B.argus_destroy(ctx)
+
+
+def test_select_stamps_frame_smaller_than_a_tile(ora):
+    """80 x 50 frame, smaller than one 64 x 32 tile plus its halo in both directions."""
+    w, h = 80, 50
+    cat = synth.Catalog(torch.tensor([22.3, 55.6, 60.2], dtype=torch.float64),
+                        torch.tensor([20.1, 30.7, 18.4], dtype=torch.float64),
+                        torch.tensor([2e5, 5e4, 1e5], dtype=torch.float64))
+    R = synth.reference_image(synth.render(cat, w, h, 1.2, sky=300.0), 30, 1.7, 9)[0].numpy()
+    co = _select_both(ora, R, np.zeros((h, w), np.uint8), 2, 1)
+    assert [tuple(c) for c in co] == [(22, 20), (60, 18)]
+
+
+def test_select_stamps_ties_and_plateaus(ora):
+    """Equal peaks: the lowest (y, x) wins a cell; a two-pixel plateau is no strict maximum;
+    two equal isolated peaks within iso of each other block one another."""
+    w, h = 200, 120
+    R = np.full((h, w), 300.0, np.float32)
+    for x, y in [(40, 40), (70, 40), (40, 80)]:         # equal peaks in one cell
+        R[y, x] = 5000.0
+    R[60, 150] = R[60, 151] = 8000.0                  # plateau: not a strict maximum
+    R[90, 150] = 9000.0
+    R[95, 155] = 9000.0                               # equal neighbour peak within iso
+    fl = np.zeros((h, w), np.uint8)
+    co = ora.select_stamps(R, fl, 2, 1, 21, 5, 3.0e4, iso=10, iso_frac=0.1)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        cen = torch.full((2, 2), -1, dtype=torch.int32, device="cuda")
+        ns = torch.zeros(4, dtype=torch.int32, device="cuda")
+        B.argus_select_stamps(ctx, dev_pitched(R), dev_pitched(fl), B.argus_shape(w, h, pitch), 2, 1, 21, 5,
+                              3.0e4, 10, 0.1, cen, ns)
+        torch.cuda.synchronize()
+        n = int(ns[0].item())
+        assert n == len(co)
+        np.testing.assert_array_equal(cen[:n].cpu().numpy(), co)
+        assert tuple(co[0]) == (40, 40)
     finally:
         B.argus_destroy(ctx)
 
