@@ -34,12 +34,12 @@ struct argus_ctx {
 
     // fit scratch
     float* X;            // [max_stamps * 31*31][64] basis-convolved stamp pixels
+    float* rowmeta;      // [max_stamps * 31*31][16] per-row design weights of the fit
     int gram_parts;      // number of partial Gram slots
     float* gram_part;    // [gram_parts][np_cols][np_cols]
     double* M;           // [np_cols][np_cols] reduced normal matrix (+ target column)
     double* L;           // [np_cols][np_cols] Cholesky factor
-    double* Linv;        // [np_cols][np_cols] its inverse
-    double* Dinv;        // [32][32] inverse of the current diagonal block
+    double* Dinv;        // [np_cols / 32][32][32] inverses of the 32 x 32 diagonal blocks of L
     double* vec;         // [8][np_cols] b, a0, r, delta, a, work
     int resid_parts;
     double* resid_part;  // [resid_parts][np_cols + 2]
