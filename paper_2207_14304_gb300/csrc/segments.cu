@@ -67,6 +67,7 @@ constexpr int FIT_ROWS = 8;
 constexpr int FIT_COLS = 32;
 constexpr int FIT_CH = FIT_ROWS * FIT_COLS;   // design pixels per Gram chunk
 constexpr int FG = 8;                         // functions per warp group
+constexpr int GRAM_FOLD = 8;                  // pixels per FP32 partial sum of the Gram
 
 struct SegFitArgs {
     const float* sci;
@@ -198,29 +199,37 @@ __global__ void __launch_bounds__(256) seg_fit_kernel(SegFitArgs a) {
                 for (int m = nb + 2; m < ZS; m++) zr[m] = 0.0f;
             }
             __syncthreads();
-            // Gram 4x4 block per thread: FP32 over the chunk, folded into double-float
+            // Gram 4x4 block per thread: FP32 over GRAM_FOLD pixels at a time, each
+            // partial folded into a double-float accumulator (error-free two-sum).
+            // The FP32 partial sums are the only rounding left: with the
+            // conditioning of single-segment normal matrices (~1e4 to 1e5 in the
+            // orthonormal basis) sums over 256 pixels put ~1e-3 on the kernel,
+            // sums over 8 pixels ~1e-4.
             if (gram_thread) {
-                float acc[16];
+                for (int p0 = 0; p0 < FIT_CH; p0 += GRAM_FOLD) {
+                    float acc[16];
 #pragma unroll
-                for (int q = 0; q < 16; q++) acc[q] = 0.0f;
-                for (int p = 0; p < FIT_CH; p++) {
-                    const float* zp = Z + p * ZS;
-                    float zi[4], zj[4];
+                    for (int q = 0; q < 16; q++) acc[q] = 0.0f;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        zi[u] = (bi * 4 + u < NPC) ? zp[bi * 4 + u] : 0.0f;
-                        zj[u] = (bj * 4 + u < NPC) ? zp[bj * 4 + u] : 0.0f;
+                    for (int p = p0; p < p0 + GRAM_FOLD; p++) {
+                        const float* zp = Z + p * ZS;
+                        float zi[4], zj[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            zi[u] = (bi * 4 + u < NPC) ? zp[bi * 4 + u] : 0.0f;
+                            zj[u] = (bj * 4 + u < NPC) ? zp[bj * 4 + u] : 0.0f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+#pragma unroll
+                            for (int v = 0; v < 4; v++) acc[u * 4 + v] = fmaf(zi[u], zj[v], acc[u * 4 + v]);
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
-#pragma unroll
-                        for (int v = 0; v < 4; v++) acc[u * 4 + v] = fmaf(zi[u], zj[v], acc[u * 4 + v]);
-                }
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const float sum = hi[q] + acc[q], bp = sum - hi[q];
-                    lo[q] += (hi[q] - (sum - bp)) + (acc[q] - bp);
-                    hi[q] = sum;
+                    for (int q = 0; q < 16; q++) {
+                        const float sum = hi[q] + acc[q], bp = sum - hi[q];
+                        lo[q] += (hi[q] - (sum - bp)) + (acc[q] - bp);
+                        hi[q] = sum;
+                    }
                 }
             }
         }

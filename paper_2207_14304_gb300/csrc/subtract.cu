@@ -1,22 +1,25 @@
 // K6: full-frame convolution of the reference with the spatially varying
 // PSF-matching kernel, subtraction, and the difference variance (paper Sec. 4.2
-// direct image subtraction, Table 2; noise maps, Sec. 3.2): one CTA per 32x32
-// output tile (see subtract_tile.cuh).
+// direct image subtraction, Table 2; noise maps, Sec. 3.2).
 //
-// The per-pixel work is NK * KS^2 + KS^2 FMAs (3087 at KS = 21, NK = 6), far
-// above the 24 B/px of traffic: the kernel is bound by FP32 issue, not HBM.
+// The per-pixel work is NK * KS^2 + KS^2 multiply-adds (3087 at KS = 21,
+// NK = 6), far above the 25 B/px of traffic: on the FP32 pipes the kernel is
+// bound by instruction issue, not HBM.  For 11x11 and 21x21 kernels the
+// difference image runs on the tensor cores (subtract_tc.cu) and the SIMT
+// tile body (subtract_tile.cuh, one CTA per 32x32 tile) computes only the
+// variance; other sizes use the SIMT body for both.
 #include "subtract_tile.cuh"
 
 namespace {
 using namespace argus_sub;
 
-template <int KS, int NK>
+template <int KS, int NK, bool CONV>
 __global__ void __launch_bounds__(THREADS) subtract_kernel(SubArgs a) {
     extern __shared__ __align__(16) float smem[];
-    subtract_tile<KS, NK>(a, blockIdx.x * TILE, blockIdx.y * TILE, smem);
+    subtract_tile<KS, NK, CONV>(a, blockIdx.x * TILE, blockIdx.y * TILE, smem);
 }
 
-template <int KS, int NK>
+template <int KS, int NK, bool CONV = true>
 int launch(const SubArgs& a, cudaStream_t st) {
     constexpr int R = (KS - 1) / 2;
     constexpr int SW = TILE + 2 * R;
@@ -24,10 +27,26 @@ int launch(const SubArgs& a, cudaStream_t st) {
     constexpr int KSP = (KS + 3) / 4 * 4;
     constexpr int KTSZ = (KS * KS * NKP + 3) / 4 * 4;
     const size_t smem = sizeof(float) * (2 * SW * SW + KTSZ + KS * KSP);
-    cudaFuncSetAttribute(subtract_kernel<KS, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(subtract_kernel<KS, NK, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((a.w + TILE - 1) / TILE, (a.h + TILE - 1) / TILE);
-    subtract_kernel<KS, NK><<<grid, THREADS, smem, st>>>(a); argus_count_launch(1);
+    subtract_kernel<KS, NK, CONV><<<grid, THREADS, smem, st>>>(a); argus_count_launch(1);
     return argus_launch_status();
+}
+
+// Kernel sizes with a tensor-core difference image: the SIMT body computes the
+// variance only, then the tensor-core kernel writes D.
+template <int KS>
+int launch_split(const SubArgs& a, int nk, int* status, cudaStream_t st) {
+    if (a.diff_var) {
+        int rc = ARGUS_ERR_UNSUPPORTED;
+        switch (nk) {
+            case 1: rc = launch<KS, 1, false>(a, st); break;
+            case 3: rc = launch<KS, 3, false>(a, st); break;
+            case 6: rc = launch<KS, 6, false>(a, st); break;
+        }
+        if (rc) return rc;
+    }
+    return argus_subtract_tc(a, KS, nk, status, st);
 }
 
 template <int KS>
@@ -69,9 +88,9 @@ extern "C" int argus_subtract(argus_ctx* ctx, const float* sci, const float* sci
     switch (ksize) {
         case 7: return launch_nk<7>(a, nk, s);
         case 9: return launch_nk<9>(a, nk, s);
-        case 11: return launch_nk<11>(a, nk, s);
+        case 11: return launch_split<11>(a, nk, ctx->d_status, s);
         case 15: return launch_nk<15>(a, nk, s);
-        case 21: return launch_nk<21>(a, nk, s);
+        case 21: return launch_split<21>(a, nk, ctx->d_status, s);
     }
     return ARGUS_ERR_UNSUPPORTED;
 }

@@ -47,7 +47,9 @@ __device__ __forceinline__ void spatial_terms(float xt, float yt, int deg, float
     }
 }
 
-template <int KS, int NK>
+// CONV = false computes only the difference variance (the difference image
+// then comes from the tensor-core kernel).
+template <int KS, int NK, bool CONV = true>
 __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, const int ty0, float* smem) {
     constexpr int R = (KS - 1) / 2;
     constexpr int SW = TILE + 2 * R;             // staged tile side
@@ -71,14 +73,14 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
         float rv = 0.0f, vv = 0.0f;
         if (gy >= 0 && gy < a.h && gx >= 0 && gx < a.w) {
             const long p = (long)gy * a.pitch + gx;
-            rv = __ldg(a.ref + p);
+            if (CONV) rv = __ldg(a.ref + p);
             vv = __ldg(a.ref_var + p);
         }
-        Rs[e] = rv;
+        if (CONV) Rs[e] = rv;
         Vs[e] = vv;
     }
     // kernel taps, transposed to [iu][iv][k]
-    for (int e = tid; e < KS * KS * NKP; e += THREADS) {
+    for (int e = tid; e < (CONV ? KS * KS * NKP : 0); e += THREADS) {
         const int k = e % NKP, t = e / NKP;
         const int iu = t / KS, iv = t - iu * KS;
         Kt[e] = k < NK ? __ldg(a.K + k * KS * KS + iv * KS + iu) : 0.0f;
@@ -120,7 +122,7 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
     constexpr int IVB = (KS % 7 == 0) ? 7 : ((KS % 5 == 0) ? 5 : KS);
     constexpr int NW = ROWS_PER_THREAD + IVB - 1;
 #pragma unroll 1
-    for (int iu = 0; iu < KS; iu++) {
+    for (int iu = 0; iu < (CONV ? KS : 0); iu++) {
         const float* kt = Kt + iu * KS * NKP;
         const float* rcol = Rs + ly0 * SW + lx + 2 * R - iu;
 #pragma unroll 1
@@ -186,6 +188,11 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
         const long p = (long)y * a.pitch + x;
         float D = 0.0f, VD = 0.0f;
         const bool inner = x >= R && y >= R && x <= a.w - 1 - R && y <= a.h - 1 - R;
+        if (!CONV) {
+            if (inner && a.flags[p] == 0) VD = a.sci_var[p] + accv[j];
+            a.diff_var[p] = VD;
+            continue;
+        }
         if (inner && a.flags[p] == 0) {
             const float yt = a.H > 1 ? (float)(2 * (y + a.oy) - (a.H - 1)) / (float)(a.H - 1) : 0.0f;
             float pk[ARGUS_MAX_TERMS];
@@ -217,3 +224,7 @@ constexpr size_t tile_smem_bytes() {
 }
 
 }  // namespace argus_sub
+
+// Difference image on the tensor cores (subtract_tc.cu) for the kernel sizes it
+// is built for; ARGUS_ERR_UNSUPPORTED for the others.
+int argus_subtract_tc(const argus_sub::SubArgs& a, int ksize, int nk, int* status, cudaStream_t st);

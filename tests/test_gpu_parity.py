@@ -86,7 +86,11 @@ def _subtract_case(ora, ks, sdeg, bgdeg, w, h, seed):
 
 
 @pytest.mark.parametrize("ks,sdeg,bgdeg,w,h", [(11, 0, 0, 200, 150), (21, 2, 2, 230, 170), (7, 1, 1, 97, 65),
-                                               (15, 0, 0, 128, 64), (9, 2, 0, 70, 45)])
+                                               (15, 0, 0, 128, 64), (9, 2, 0, 70, 45),
+                                               # tensor-core path: several 128-column strips and 128-row
+                                               # bands with ragged ends, a one-column last strip
+                                               (21, 2, 2, 300, 290), (11, 1, 1, 260, 140), (21, 0, 1, 129, 257),
+                                               (21, 1, 0, 40, 30)])
 def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
     R, I, Vi, Vr, fl, K, bg = _subtract_case(ora, ks, sdeg, bgdeg, w, h, seed=ks * 7 + w)
     Do, Vo = ora.subtract(I, Vi, R, Vr, fl, K.astype(np.float64), bg, sdeg=sdeg, bgdeg=bgdeg)
