@@ -41,12 +41,13 @@ STAMP = 21
 # flags (9 B) are written and read back once between the calibration and subtraction
 # kernels and are not counted (a fused kernel would not move them).
 BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
-# DRAM traffic of one subtract launch, bytes per frame pixel: dram__bytes_read.sum +
-# dram__bytes_write.sum of an ncu capture of a 4096x4096 launch (395.1 MB / 4096^2),
-# scaled by pixels to the frame (the kernel streams its tiles once, so traffic grows in
-# proportion).  It holds only for the kernel sources it was taken on.
-SUBTRACT_TRAFFIC = {"bytes_per_px": 23.55, "sources_sha1": "e2360219614c799b4ef9bb0362a354770ef02db8"}
-SUBTRACT_SOURCES = ("subtract.cu", "subtract_tile.cuh")
+# DRAM traffic of one launch of the tensor-core subtraction kernel, bytes per frame
+# pixel: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture of a 4096x4096
+# launch, scaled by pixels to the frame (the kernel streams its bands once, so traffic
+# grows in proportion).  It holds only for the kernel sources it was taken on (None
+# until a capture of these sources is recorded here).
+SUBTRACT_TRAFFIC = {"bytes_per_px": None, "sources_sha1": None}
+SUBTRACT_SOURCES = ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh")
 
 
 def subtract_traffic_bytes():
@@ -55,7 +56,7 @@ def subtract_traffic_bytes():
     for f in SUBTRACT_SOURCES:
         with open(os.path.join(ROOT, "paper_2207_14304_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != SUBTRACT_TRAFFIC["sources_sha1"]:
+    if SUBTRACT_TRAFFIC["bytes_per_px"] is None or h.hexdigest() != SUBTRACT_TRAFFIC["sources_sha1"]:
         return None
     return int(SUBTRACT_TRAFFIC["bytes_per_px"] * W * H)
 
@@ -229,6 +230,7 @@ def run_gpu(args):
         stage[k] = round(evs[i].elapsed_time(evs[i + 1]), 4)
 
     # timed region: K steps, subtract kernel bracketed by events on its stream
+    var_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sub_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sub_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
@@ -243,8 +245,10 @@ def run_gpu(args):
         pipe.calibrate(d_raw, calib, stream)
         pipe.select_stamps(d_R, stream)
         pipe.fit(d_R, stream)
+        var_s[i].record(stream)
+        pipe.subtract_variance(d_Vr, stream)
         sub_s[i].record(stream)
-        pipe.subtract(d_R, d_Vr, stream)
+        pipe.subtract_difference(d_R, d_Vr, stream)
         sub_e[i].record(stream)
         pipe.detect(stream)
     t1.record(stream)
@@ -258,7 +262,8 @@ def run_gpu(args):
         raise RuntimeError(f"device status {st} ({B.status_string(st)}) in the timed region")
     mpix = W * H / 1e6
     value, tmax = aggregate(mpix * args.steps, elapsed, dist, device)
-    sub_ms = statistics.mean(sub_s[i].elapsed_time(sub_e[i]) for i in range(args.steps))
+    tc_ms = statistics.mean(sub_s[i].elapsed_time(sub_e[i]) for i in range(args.steps))
+    var_ms = statistics.mean(var_s[i].elapsed_time(sub_s[i]) for i in range(args.steps))
 
     # end to end through the public API: pinned host raw frame in, detection list out
     raw_host = d_raw.cpu().pin_memory()
@@ -282,12 +287,19 @@ def run_gpu(args):
     n_found = int(nf_host[0].item())
 
     peaks = load_peaks()
-    # dominant kernel: subtract (FP32 FMA issue bound, see the design notes)
-    flop_px = 2 * ((SDEG + 1) * (SDEG + 2) // 2 * KSIZE * KSIZE + KSIZE * KSIZE)
-    sub_flops = flop_px * W * H
-    achieved = sub_flops / (sub_ms / 1e3) / 1e12
+    # dominant kernel: the tensor-core reference convolution of the subtraction
+    # (difference image).  Algorithmic work: NK * KS^2 multiply-adds per pixel;
+    # the MMAs execute more (BF16 hi/lo x three products, K padded 21 -> 32, N
+    # 126 -> 128, 2R halo rows per 128-row band), reported beside it.
+    nk = (SDEG + 1) * (SDEG + 2) // 2
+    conv_flops = 2 * nk * KSIZE * KSIZE * W * H
+    achieved = conv_flops / (tc_ms / 1e3) / 1e12
+    bands = [min(128, H - y0) for y0 in range(0, H, 128)]
+    executed = 3 * 2 * 128 * 128 * 32 * ((W + 127) // 128) * sum(b + KSIZE - 1 for b in bands)
+    tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1462.0)
     alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x clock
+    var_tflops = 2 * KSIZE * KSIZE * W * H / (var_ms / 1e3) / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)
     step_s = tmax / args.steps
     hbm_frac = BYTES_PER_PX * W * H / step_s / 1e9 / hbm
@@ -317,13 +329,21 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.precision),
-        "roofline": {"bound": "alu", "kernel": "subtract", "achieved": round(achieved, 3),
-                     "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4),
-                     "traffic": subtract_traffic_bytes(), "traffic_unit": "bytes per launch (ncu DRAM read+write)",
-                     "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz (median SM clock under load)"},
+        "roofline": {"bound": "tensor", "kernel": "subtract_tc (reference convolution, difference image)",
+                     "achieved": round(achieved, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
+                     "frac": round(achieved / tensor_peak, 4), "traffic": subtract_traffic_bytes(),
+                     "traffic_unit": "bytes per launch (ncu DRAM read+write)",
+                     "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
+                     "algorithmic": f"{2 * nk * KSIZE * KSIZE} FLOP/px ({nk} spatial terms x {KSIZE}x{KSIZE} taps)",
+                     "executed_tflops": round(executed / (tc_ms / 1e3) / 1e12, 1),
+                     "kernel_ms": round(tc_ms, 4)},
+        "variance_kernel": {"bound": "alu", "ms": round(var_ms, 4), "achieved": round(var_tflops, 3),
+                            "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(var_tflops / alu_peak, 4),
+                            "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz"},
         "hbm_roofline_frac": round(hbm_frac, 4),
         "hbm_bytes_per_px": BYTES_PER_PX,
-        "stage_ms": stage, "subtract_ms": round(sub_ms, 4),
+        "stage_ms": stage, "subtract_ms": round(tc_ms + var_ms, 4),
+        "subtract_detect_mpix_s": round(W * H / 1e6 / ((stage["subtract"] + stage["detect"]) / 1e3), 1),
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(raw_host.numel() * 2),
                 "d2h_bytes_per_step": int(out_host.numel() + nf_host.numel() * 4)},
         "gpu_launches": int(launches), "sources_last_frame": n_found,

@@ -199,7 +199,13 @@ int argus_expand_kernel(argus_ctx *ctx, const argus_basis *basis, const double *
  * frame_h) and frame coordinates (x + ox, y + oy); with spatial_degree > 0,
  * ox and oy must be multiples of 32.  Pixels within r = ksize/2 of an image
  * edge, or with flags != 0, get D = V_D = 0.  K: float [Ks][ksize^2], bg:
- * double [Kb] (device).  diff_var may be NULL.  ksize in {7, 9, 11, 15, 21}. */
+ * double [Kb] (device).  ksize in {7, 9, 11, 15, 21}.  diff_var NULL: the
+ * difference only; diff NULL: the variance only (sci and ref are then not
+ * read); not both.  For 11x11 and 21x21 kernels D is computed on the tensor
+ * cores (BF16 hi/lo operands, three products, FP32 accumulation; relative
+ * error ~1e-6 of the convolved flux), the variance and other sizes in FP32
+ * on the CUDA cores.  A stalled tensor-core pipeline latches
+ * ARGUS_ERR_TIMEOUT. */
 int argus_subtract(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
                    const float *ref_var, const uint8_t *flags, argus_shape shape, int frame_w,
                    int frame_h, int ox, int oy, int ksize, int spatial_degree, const float *K,

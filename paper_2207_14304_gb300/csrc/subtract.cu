@@ -46,11 +46,19 @@ int launch_split(const SubArgs& a, int nk, int* status, cudaStream_t st) {
         }
         if (rc) return rc;
     }
-    return argus_subtract_tc(a, KS, nk, status, st);
+    return a.diff ? argus_subtract_tc(a, KS, nk, status, st) : ARGUS_OK;
 }
 
 template <int KS>
 int launch_nk(const SubArgs& a, int nk, cudaStream_t st) {
+    if (!a.diff) {   // the variance only
+        switch (nk) {
+            case 1: return launch<KS, 1, false>(a, st);
+            case 3: return launch<KS, 3, false>(a, st);
+            case 6: return launch<KS, 6, false>(a, st);
+        }
+        return ARGUS_ERR_UNSUPPORTED;
+    }
     switch (nk) {
         case 1: return launch<KS, 1>(a, st);
         case 3: return launch<KS, 3>(a, st);
@@ -66,7 +74,8 @@ extern "C" int argus_subtract(argus_ctx* ctx, const float* sci, const float* sci
                               int frame_h, int ox, int oy, int ksize, int spatial_degree, const float* K,
                               int bg_degree, const double* bg, float* diff, float* diff_var,
                               argus_stream stream) {
-    if (!ctx || !sci || !sci_var || !ref || !ref_var || !flags || !K || !diff) return ARGUS_ERR_ARG;
+    if (!ctx || !sci_var || !ref_var || !flags || !K || (!diff && !diff_var)) return ARGUS_ERR_ARG;
+    if (diff && (!sci || !ref)) return ARGUS_ERR_ARG;
     if (bg_degree >= 0 && !bg) return ARGUS_ERR_ARG;
     int st = argus_check_shape(shape, ctx->max_pixels);
     if (st) return st;

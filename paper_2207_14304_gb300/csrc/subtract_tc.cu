@@ -23,12 +23,13 @@
 // power of y: the x powers are folded in as each T column is added; the ring
 // shifts by register moves, so the row loop has a single body).  Warps 4-10:
 // producers (source rows arrive by cp.async DP rows ahead; each value is
-// split into BF16 hi/lo once, and the Hankel rows are copied out of the split
-// row with 32-bit loads and byte permutes into the canonical no-swizzle
-// K-major layout, NSTAGE stages).  Warp 11: one thread issues the MMAs.
-// TMEM holds four 128-column accumulators, so the MMAs run up to three rows
-// ahead of the epilogue, which fetches its science and flag rows by cp.async
-// DE rows ahead.  Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT
+// split into BF16 hi/lo once, one row ahead of its use, and the Hankel rows
+// are copied out of the split row with 32-bit loads and byte permutes into
+// the canonical no-swizzle K-major layout, NSTAGE stages; one named barrier
+// per row).  Warp 11: one thread issues the MMAs.  TMEM holds four
+// 128-column accumulators, so the MMAs run up to three rows ahead of the
+// epilogue, which loads its science and flag values four rows ahead into a
+// register queue.  Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT
 // and all roles stop.
 #include <cuda_bf16.h>
 
@@ -45,8 +46,6 @@ constexpr int NSTAGE = 4;                 // Hankel stages
 constexpr int SRCW = TCX + TKC;           // source columns per row
 constexpr int NSRC = 8;                   // fp32 source-row ring
 constexpr int DP = 6;                     // source rows in flight ahead of the one being tiled
-constexpr int NOUT = 8;                   // ring of science/flag rows for the epilogue
-constexpr int DE = 6;                     // output rows in flight ahead of the one being written
 constexpr int NPROD = 224;                // producer threads (warps 4-10)
 constexpr int TC_THREADS = 384;           // warps 0-3 epilogue, 4-10 producers, 11 MMA issuer
 constexpr uint32_t LBO = 128, SBO = 512;  // K-major canonical layout, 32 K per row
@@ -60,11 +59,9 @@ struct TcShared {
     uint8_t ahi[NSTAGE][TILE_BYTES];
     uint8_t alo[NSTAGE][TILE_BYTES];
     float srcf[NSRC][SRCW];
-    alignas(16) uint32_t srch[SRCW / 2 + 4];   // BF16 hi of the current source row, two per word
-    alignas(16) uint32_t srcl[SRCW / 2 + 4];   // BF16 lo
+    alignas(16) uint32_t srch[2][SRCW / 2 + 4];   // BF16 hi of a source row, two per word (double-buffered)
+    alignas(16) uint32_t srcl[2][SRCW / 2 + 4];   // BF16 lo
     uint64_t filled[NSTAGE];
-    float sci[NOUT][TCX];
-    alignas(16) uint8_t flg[NOUT][TCX];
     uint64_t empty[NSTAGE], tfull[NTB], tempty[NTB];
     uint32_t tmem;
     int abort;       // set by any role that timed out
@@ -147,54 +144,79 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     const uint32_t tmem = S.tmem;
 
     if (warp >= 4 && warp < 11) {
-        // ---------------- producers
+        // ---------------- producers: warps 8-10 fetch and split source rows one row
+        // ahead, warps 4-7 build the Hankel tile of the current row (one row m each)
         const int pt = tid - 128;
+        const bool splitter = pt >= TCX;
+        const int ps = pt - TCX;                 // splitter index, 0 .. 95
+        constexpr int NSPLIT = NPROD - TCX;
         // source row rr into its ring slot with cp.async (zero outside the image)
         auto issue_row = [&](int rr) {
-            for (int c = pt; c < SRCW; c += NPROD) {
+            for (int c = ps; c < SRCW; c += NSPLIT) {
                 const int gy = y0 - R + rr, gx = x0 - R + c;
                 const bool in = rr < nsrc && gy >= 0 && gy < a.h && gx >= 0 && gx < a.w;
                 tc::cp_async4(&S.srcf[rr & (NSRC - 1)][c], in ? a.ref + (long)gy * a.pitch + gx : a.ref, in ? 4 : 0);
             }
         };
-        for (int d = 0; d < DP; d++) {
-            issue_row(d);
-            tc::cp_async_commit();
+        // BF16 split of source row rr into buffer rr & 1, two values per word
+        auto split_row = [&](int rr) {
+            const float2* src = reinterpret_cast<const float2*>(S.srcf[rr & (NSRC - 1)]);
+            uint32_t* dh = S.srch[rr & 1];
+            uint32_t* dl = S.srcl[rr & 1];
+            for (int i = ps; i < SRCW / 2; i += NSPLIT) {
+                const float2 v = src[i];
+                __nv_bfloat16 h0, l0, h1, l1;
+                split_bf16(v.x, h0, l0);
+                split_bf16(v.y, h1, l1);
+                dh[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                dl[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+        };
+        if (splitter) {
+            for (int d = 0; d < DP; d++) {
+                issue_row(d);
+                tc::cp_async_commit();
+            }
+            tc::cp_async_wait<DP - 2>();         // rows 0 and 1
         }
+        tc::named_sync(1, NPROD);
+        if (splitter) split_row(0);
+        // One barrier per row.  Before barrier rho: the splitters have split row rho
+        // and hold row rho + 1 landed; the builders have built and fenced row
+        // rho - 1's tile; producer 0 has found stage s(rho) free.  After it,
+        // producer 0 marks stage s(rho - 1) filled, the splitters split row
+        // rho + 1 and fetch row rho + DP + 1, the builders build row rho.
         for (int rho = 0; rho < nsrc; rho++) {
-            issue_row(rho + DP);                 // may be past the band: zero-filled, never used
-            tc::cp_async_commit();
-            tc::cp_async_wait<DP>();             // this thread's copies of row rho have landed
             const int s = rho % NSTAGE, fill = rho / NSTAGE;
             if (pt == 0) {
                 bool ok = !S.abort;
                 if (ok && fill >= 1) ok = wait_or_abort(S, &S.empty[s], (fill - 1) & 1, status);
                 S.pstop = ok ? 0 : 1;
             }
-            tc::named_sync(1, NPROD);            // row rho complete for all producers, stage s free
-            if (S.pstop) break;
-            // BF16 split, once per source value, two values per word
-            const float* src = S.srcf[rho & (NSRC - 1)];
-            for (int i = pt; i < SRCW / 2; i += NPROD) {
-                __nv_bfloat16 h0, l0, h1, l1;
-                split_bf16(src[2 * i], h0, l0);
-                split_bf16(src[2 * i + 1], h1, l1);
-                S.srch[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                S.srcl[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
             tc::named_sync(1, NPROD);
-            // Hankel rows: A[m][u'] = src[m + u'], chunk q = taps 8q .. 8q+7 as four words
-            // taken from src words (m >> 1) + 4q .. + 4 (shifted by one value when m is odd)
-            uint8_t* ah = S.ahi[s];
-            uint8_t* al = S.alo[s];
-            for (int m = pt; m < TCX; m += NPROD) {
+            if (pt == 0 && rho >= 1) tc::mbar_arrive(&S.filled[(rho - 1) % NSTAGE]);
+            if (S.pstop) break;
+            if (splitter) {
+                if (rho + 1 < nsrc) split_row(rho + 1);
+                issue_row(rho + DP);             // may be past the band: zero-filled, never used
+                tc::cp_async_commit();
+                tc::cp_async_wait<DP - 2>();     // row rho + 2 has landed
+            } else {
+                // Hankel row m: A[m][u'] = src[m + u'], chunk q = taps 8q .. 8q+7 as four
+                // words taken from src words (m >> 1) + 4q .. + 4 (shifted by one value
+                // when m is odd)
+                const int m = pt;
+                uint8_t* ah = S.ahi[s];
+                uint8_t* al = S.alo[s];
+                const uint32_t* sh = S.srch[rho & 1];
+                const uint32_t* sl = S.srcl[rho & 1];
                 const int w0 = m >> 1;
                 const uint32_t sel = (m & 1) ? 0x5432u : 0x3210u;
                 uint32_t hw[17], lw[17];
 #pragma unroll
                 for (int k = 0; k < 17; k++) {
-                    hw[k] = S.srch[w0 + k];
-                    lw[k] = S.srcl[w0 + k];
+                    hw[k] = sh[w0 + k];
+                    lw[k] = sl[w0 + k];
                 }
 #pragma unroll
                 for (int q = 0; q < TKC / 8; q++) {
@@ -206,12 +228,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
                         make_uint4(__byte_perm(lw[4 * q], lw[4 * q + 1], sel), __byte_perm(lw[4 * q + 1], lw[4 * q + 2], sel),
                                    __byte_perm(lw[4 * q + 2], lw[4 * q + 3], sel), __byte_perm(lw[4 * q + 3], lw[4 * q + 4], sel));
                 }
+                tc::fence_proxy_async();
             }
-            tc::fence_proxy_async();
-            tc::named_sync(1, NPROD);            // stage s complete
-            if (pt == 0) tc::mbar_arrive(&S.filled[s]);
+            if (rho == nsrc - 1) {               // the last tile: one more barrier to publish it
+                tc::named_sync(1, NPROD);
+                if (pt == 0) tc::mbar_arrive(&S.filled[s]);
+            }
         }
-        tc::cp_async_wait<0>();
+        if (splitter) tc::cp_async_wait<0>();
     } else if (warp == 11) {
         // ---------------- MMA issuer
         if (lane == 0) {
@@ -266,21 +290,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
         for (int i = 0; i < KS; i++)
 #pragma unroll
             for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
-        // science value and flags of output row rr (column x0 + m) into the ring
-        auto issue_out = [&](int rr) {
-            const int y = y0 + rr;
-            const bool in = rr < nout && x < a.w;
-            const int slot = rr & (NOUT - 1);
-            tc::cp_async4(&S.sci[slot][m], in ? a.sci + (long)y * a.pitch + x : a.sci, in ? 4 : 0);
-            if ((m & 3) == 0) {
-                const int nb = rr < nout ? max(0, min(4, a.w - x)) : 0;
-                tc::cp_async4(&S.flg[slot][m], nb ? a.flags + (long)y * a.pitch + x : a.flags, nb);
-            }
+        // science value and flags of output rows eta .. eta + LQ - 1 in a register FIFO,
+        // loaded LQ rows before use
+        constexpr int LQ = 4;
+        float qI[LQ];
+        int qF[LQ];
+        auto load_out = [&](int rr, float& Iv, int& Fv) {
+            const bool in = rr >= 0 && rr < nout && x < a.w;
+            const long pp = in ? (long)(y0 + rr) * a.pitch + x : 0;
+            Iv = in ? __ldg(a.sci + pp) : 0.0f;
+            Fv = in ? (int)__ldg(a.flags + pp) : 1;
         };
-        for (int d = 0; d < DE; d++) {
-            issue_out(d);
-            tc::cp_async_commit();
-        }
+#pragma unroll
+        for (int i = 0; i < LQ; i++) load_out(i - 2 * R, qI[i], qF[i]);
         // ring index i holds output row rho - 2r + i; source row rho adds its
         // column (iv, k) at index iv, row rho - 2r is then complete at index 0
         // and the ring shifts down by one (register moves, one loop body)
@@ -289,17 +311,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
             const int y = y0 + eta;
             const bool out = eta >= 0 && x < a.w && y < a.h;
             const long p = out ? (long)y * a.pitch + x : 0;
-            float I = 0.0f;
-            uint8_t fl = 1;
-            if (eta >= 0) {
-                __syncwarp();                    // ring slot eta + DE was read two rows ago
-                issue_out(eta + DE);
-                tc::cp_async_commit();
-                tc::cp_async_wait<DE>();         // row eta has landed (own copies)
-                __syncwarp();                    // flags copied by the lane that owns the 4-byte group
-                I = S.sci[eta & (NOUT - 1)][m];
-                fl = S.flg[eta & (NOUT - 1)][m];
+            const float I = qI[0];
+            const int fl = qF[0];
+#pragma unroll
+            for (int i = 0; i + 1 < LQ; i++) {
+                qI[i] = qI[i + 1];
+                qF[i] = qF[i + 1];
             }
+            load_out(eta + LQ, qI[LQ - 1], qF[LQ - 1]);
             const int b = rho % NTB;
             bool run = wait_or_abort(S, &S.tfull[b], (rho / NTB) & 1, status);
             run = __all_sync(0xffffffffu, run);
@@ -345,7 +364,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
 #pragma unroll
             for (int j = 0; j < NJ; j++) acc[KS - 1][j] = 0.0f;
         }
-        tc::cp_async_wait<0>();
     }
     tc::fence_before();
     __syncthreads();

@@ -83,6 +83,18 @@ class FramePipeline:
                          self.h, 0, 0, self.basis.ksize, self.basis.spatial_degree, self.K,
                          self.basis.bg_degree, self.bg, self.diff, self.diff_var, stream)
 
+    def subtract_variance(self, ref_var, stream=None):
+        """The difference variance alone (the first half of `subtract`)."""
+        B.argus_subtract(self.ctx, None, self.var, None, ref_var, self.flags, self.shape, self.w,
+                         self.h, 0, 0, self.basis.ksize, self.basis.spatial_degree, self.K,
+                         self.basis.bg_degree, self.bg, None, self.diff_var, stream)
+
+    def subtract_difference(self, ref, ref_var, stream=None):
+        """The difference image alone (the second half of `subtract`)."""
+        B.argus_subtract(self.ctx, self.img, self.var, ref, ref_var, self.flags, self.shape, self.w,
+                         self.h, 0, 0, self.basis.ksize, self.basis.spatial_degree, self.K,
+                         self.basis.bg_degree, self.bg, self.diff, None, stream)
+
     def detect(self, stream=None):
         B.argus_detect(self.ctx, self.diff, self.diff_var, self.flags, self.shape, self.nsigma,
                        self.psf_sigma, self.mask, self.sources, self.src_cap, self.n_found, stream)

@@ -122,6 +122,31 @@ def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
         B.argus_destroy(ctx)
 
 
+@pytest.mark.parametrize("ks,sdeg", [(21, 2), (15, 1)])
+def test_subtract_split_calls(ora, ks, sdeg):
+    """Variance-only and difference-only calls give the combined call's outputs bit for bit."""
+    w, h = 260, 200
+    R, I, Vi, Vr, fl, K, bg = _subtract_case(ora, ks, sdeg, sdeg, w, h, seed=5)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        dI, dVi, dR, dVr, dfl = (dev_pitched(a) for a in (I, Vi, R, Vr, fl))
+        dK = torch.from_numpy(K.reshape(-1)).cuda()
+        dbg = torch.from_numpy(np.asarray(bg, np.float64)).cuda()
+        shape = B.argus_shape(w, h, pitch)
+        D1, V1, D2, V2 = (torch.full((h, pitch), -9.0, device="cuda") for _ in range(4))
+        B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, shape, w, h, 0, 0, ks, sdeg, dK, sdeg, dbg, D1, V1)
+        B.argus_subtract(ctx, None, dVi, None, dVr, dfl, shape, w, h, 0, 0, ks, sdeg, dK, sdeg, dbg, None, V2)
+        assert (D2 == -9.0).all()
+        B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, shape, w, h, 0, 0, ks, sdeg, dK, sdeg, dbg, D2, None)
+        torch.cuda.synchronize()
+        assert torch.equal(D1, D2) and torch.equal(V1, V2)
+        with pytest.raises(B.ArgusError):
+            B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, shape, w, h, 0, 0, ks, sdeg, dK, sdeg, dbg, None, None)
+    finally:
+        B.argus_destroy(ctx)
+
+
 # --------------------------------------------------------------------------- detect
 def _detect_case(w, h, seed, sig=1.6):
     rng = np.random.default_rng(seed)
