@@ -330,7 +330,9 @@ int argus_cnn_train_step(argus_cnn *net, const float *x, const float *target, in
 /* One Adam step with a given gradient (device, [count] floats). */
 int argus_cnn_adam(argus_cnn *net, const float *grad, float lr, argus_stream stream);
 /* Network inputs from the 21x21 windows of sci and ref centred on centers[s]
- * (s < min(*n_stamps, max_stamps)), divided by the reference window sum. */
+ * (s < min(*n_stamps, max_stamps)): each window minus its sky (the mean of its
+ * 80 border pixels), both divided by the sky-subtracted reference window sum
+ * (0 when that sum is not positive).  x: float [n][441][2] (sci, ref). */
 int argus_cnn_prepare(const float *sci, const float *ref, argus_shape shape, const int *centers,
                       const int *n_stamps, int max_stamps, float *x, argus_stream stream);
 /* Spatial least squares across stamps: the per-stamp kernels y [n][441]
@@ -341,7 +343,8 @@ int argus_learned_kernel(argus_ctx *ctx, const float *y, const int *centers, con
                          argus_stream stream);
 /* Background polynomial given the kernel K (float [Ks][ksize^2]), by weighted
  * least squares on the stamp pixels, and chi2 of the result there:
- * r = I - sum_k p_k (R (x) K_k), bg = argmin sum w (r - sum pb bg)^2.
+ * r = I - sum_k p_k (R (x) K_k), bg = argmin sum w (r - sum pb bg)^2; the
+ * model convolution in FP32, the normal-equation sums and the solve in FP64.
  * stats (device) receives chi2, n_pix, dof (n_pix - Ks ksize^2 - Kb). */
 int argus_fit_background(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
                          const uint8_t *flags, argus_shape shape, const int *centers, const int *n_stamps,

@@ -387,6 +387,18 @@ __global__ void cnn_init_kernel(float* p, long n, unsigned long long seed) {
 
 // Network inputs from stamps: x[s][p][0] = I / sum(R), x[s][p][1] = R / sum(R) over the
 // 21x21 window centred on centers[s] (one CTA per stamp).
+// Block-wide sum (blockDim a multiple of 32, at most 256 threads); every thread gets the total.
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[k];
+    return t;
+}
+
 __global__ void __launch_bounds__(256) cnn_prepare_kernel(const float* sci, const float* ref, long pitch, int w,
                                                           int h, const int* centers, const int* n_stamps,
                                                           int max_stamps, float* x) {
@@ -394,24 +406,38 @@ __global__ void __launch_bounds__(256) cnn_prepare_kernel(const float* sci, cons
     const int s = blockIdx.x;
     if (s >= min(*n_stamps, max_stamps)) return;
     const int xs = centers[2 * s], ys = centers[2 * s + 1];
+    // sky of each stamp: mean of its border ring (the outermost pixels); the
+    // inputs are the sky-subtracted stamps over the sky-subtracted reference flux
+    __shared__ float sky[2];
+    float ps = 0.0f, pr = 0.0f;
+    for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
+        const int py = p / S, px = p % S;
+        const int yy = ys - S / 2 + py, xx = xs - S / 2 + px;
+        if ((px == 0 || px == S - 1 || py == 0 || py == S - 1) && xx >= 0 && yy >= 0 && xx < w && yy < h) {
+            ps += sci[(long)yy * pitch + xx];
+            pr += ref[(long)yy * pitch + xx];
+        }
+    }
+    ps = block_sum(ps, red);
+    pr = block_sum(pr, red);
+    if (threadIdx.x == 0) {
+        sky[0] = ps / (float)(4 * S - 4);
+        sky[1] = pr / (float)(4 * S - 4);
+    }
+    __syncthreads();
     float part = 0.0f;
     for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
         const int yy = ys - S / 2 + p / S, xx = xs - S / 2 + p % S;
-        if (xx >= 0 && yy >= 0 && xx < w && yy < h) part += ref[(long)yy * pitch + xx];
+        if (xx >= 0 && yy >= 0 && xx < w && yy < h) part += ref[(long)yy * pitch + xx] - sky[1];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    float tot = 0.0f;
-    for (int k = 0; k < (int)(blockDim.x >> 5); k++) tot += red[k];
-    const float inv = tot != 0.0f ? 1.0f / tot : 0.0f;
+    const float tot = block_sum(part, red);
+    const float inv = tot > 0.0f ? 1.0f / tot : 0.0f;
     for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
         const int yy = ys - S / 2 + p / S, xx = xs - S / 2 + p % S;
         float a = 0.0f, b = 0.0f;
         if (xx >= 0 && yy >= 0 && xx < w && yy < h) {
-            a = sci[(long)yy * pitch + xx] * inv;
-            b = ref[(long)yy * pitch + xx] * inv;
+            a = (sci[(long)yy * pitch + xx] - sky[0]) * inv;
+            b = (ref[(long)yy * pitch + xx] - sky[1]) * inv;
         }
         x[((long)s * NPX + p) * 2] = a;
         x[((long)s * NPX + p) * 2 + 1] = b;
@@ -420,40 +446,39 @@ __global__ void __launch_bounds__(256) cnn_prepare_kernel(const float* sci, cons
 
 // Spatial least squares across stamps (one CTA): the kernel at stamp s is
 // y_s(u,v) = sum_k p_k(x_s, y_s) K_k(u,v); with A = sum_s p p^T (FP64) every
-// kernel pixel solves A K(u,v) = sum_s p y_s(u,v).
+// kernel pixel solves A K(u,v) = sum_s p y_s(u,v).  The stamps' terms are
+// computed once into shared memory; the right-hand sides (sums of at most a
+// few thousand products of terms <= 1 with kernel values) accumulate in FP32,
+// A, its Cholesky factor and the per-pixel solves are FP64.
 __global__ void __launch_bounds__(512) learned_spatial_kernel(const float* y, const int* centers, const int* n_stamps,
                                                               int max_stamps, int W, int H, int sdeg, float* K,
                                                               int* status) {
+    extern __shared__ float pk_s[];          // [max_stamps][6]
     __shared__ double A[6][6], Lc[6][6];
-    __shared__ double pk[64][6];
     __shared__ int bad;
     const int ns = min(*n_stamps, max_stamps);
     const int nk = (sdeg + 1) * (sdeg + 2) / 2;
-    if (threadIdx.x < 36) A[threadIdx.x / 6][threadIdx.x % 6] = 0.0;
     if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    for (int s0 = 0; s0 < ns; s0 += 64) {
-        const int cnt = min(64, ns - s0);
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            const int s = s0 + threadIdx.x;
-            const double xt = W > 1 ? (2.0 * centers[2 * s] - (W - 1)) / (double)(W - 1) : 0.0;
-            const double yt = H > 1 ? (2.0 * centers[2 * s + 1] - (H - 1)) / (double)(H - 1) : 0.0;
-            int k = 0;
-            double xi = 1.0;
-            for (int i = 0; i <= sdeg; i++) {
-                double yj = 1.0;
-                for (int j = 0; j <= sdeg - i; j++) { pk[threadIdx.x][k++] = xi * yj; yj *= yt; }
-                xi *= xt;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+        const double xt = W > 1 ? (2.0 * centers[2 * s] - (W - 1)) / (double)(W - 1) : 0.0;
+        const double yt = H > 1 ? (2.0 * centers[2 * s + 1] - (H - 1)) / (double)(H - 1) : 0.0;
+        int k = 0;
+        double xi = 1.0;
+        for (int i = 0; i <= sdeg; i++) {
+            double yj = 1.0;
+            for (int j = 0; j <= sdeg - i; j++) {
+                pk_s[s * 6 + k++] = (float)(xi * yj);
+                yj *= yt;
             }
+            xi *= xt;
         }
-        __syncthreads();
-        if (threadIdx.x < nk * nk) {
-            const int a = threadIdx.x / nk, b = threadIdx.x % nk;
-            double acc = 0.0;
-            for (int t = 0; t < cnt; t++) acc += pk[t][a] * pk[t][b];
-            A[a][b] += acc;
-        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nk * nk) {
+        const int a = threadIdx.x / nk, b = threadIdx.x % nk;
+        double acc = 0.0;
+        for (int t = 0; t < ns; t++) acc += (double)pk_s[t * 6 + a] * (double)pk_s[t * 6 + b];
+        A[a][b] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -473,18 +498,11 @@ __global__ void __launch_bounds__(512) learned_spatial_kernel(const float* y, co
     __syncthreads();
     if (bad) return;
     for (int p = threadIdx.x; p < NPX; p += blockDim.x) {
-        double rhs[6] = {0, 0, 0, 0, 0, 0};
+        float rhs[6] = {0, 0, 0, 0, 0, 0};
         for (int s = 0; s < ns; s++) {
-            const double v = y[(long)s * NPX + p];
-            const double xt = W > 1 ? (2.0 * centers[2 * s] - (W - 1)) / (double)(W - 1) : 0.0;
-            const double yt = H > 1 ? (2.0 * centers[2 * s + 1] - (H - 1)) / (double)(H - 1) : 0.0;
-            int k = 0;
-            double xi = 1.0;
-            for (int i = 0; i <= sdeg; i++) {
-                double yj = 1.0;
-                for (int j = 0; j <= sdeg - i; j++) { rhs[k++] += xi * yj * v; yj *= yt; }
-                xi *= xt;
-            }
+            const float v = y[(long)s * NPX + p];
+#pragma unroll
+            for (int k = 0; k < 6; k++) rhs[k] = fmaf(pk_s[s * 6 + k], v, rhs[k]);
         }
         double z[6], sol[6];
         for (int i = 0; i < nk; i++) {
@@ -523,46 +541,57 @@ __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sc
                                                                  const int* centers, const int* n_stamps,
                                                                  int max_stamps, int stamp, const float* K, int ksz,
                                                                  int sdeg, int bgdeg, double* part) {
-    __shared__ float Ks[6 * 31 * 31];
+    // shared: the nk kernels and the stamp's reference window (stamp + 2r)^2;
+    // the model convolution runs in FP32, the normal-equation sums in FP64
+    extern __shared__ float bsm[];
     __shared__ double red[8][36 + 6 + 3];
     const int s = blockIdx.x;
     const int nk = (sdeg + 1) * (sdeg + 2) / 2, nb = (bgdeg + 1) * (bgdeg + 2) / 2, kk = ksz * ksz, r = ksz / 2;
+    const int ww = stamp + 2 * r;
+    float* Ks = bsm;
+    float* Rw = bsm + nk * kk;
     double* out = part + (long)s * (36 + 6 + 3);
     const bool live = s < min(*n_stamps, max_stamps);
+    const int xs = live ? centers[2 * s] : 0, ys = live ? centers[2 * s + 1] : 0, hs = stamp / 2;
+    const bool ok = live && xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1;
     for (int e = threadIdx.x; e < nk * kk; e += blockDim.x) Ks[e] = K[e];
+    for (int e = threadIdx.x; ok && e < ww * ww; e += blockDim.x) {
+        const int jy = e / ww, jx = e - jy * ww;
+        Rw[e] = ref[(long)(ys - hs - r + jy) * pitch + (xs - hs - r + jx)];
+    }
     __syncthreads();
     double acc[36 + 6 + 3];
     for (int k = 0; k < 45; k++) acc[k] = 0.0;
-    if (live) {
-        const int xs = centers[2 * s], ys = centers[2 * s + 1], hs = stamp / 2;
-        const bool ok = xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1;
-        for (int p = threadIdx.x; ok && p < stamp * stamp; p += blockDim.x) {
-            const int x = xs - hs + p % stamp, y = ys - hs + p / stamp;
-            const long q = (long)y * pitch + x;
-            const float v = var[q], I = sci[q];
-            if (flags[q] || !(v > 0.0f) || !isfinite(v) || !isfinite(I)) continue;
-            const double wt = 1.0 / (double)v;
-            const double xt = w > 1 ? (2.0 * x - (w - 1)) / (double)(w - 1) : 0.0;
-            const double yt = h > 1 ? (2.0 * y - (h - 1)) / (double)(h - 1) : 0.0;
-            double pk[6], pb[6];
-            terms_d(xt, yt, sdeg, pk);
-            terms_d(xt, yt, bgdeg, pb);
-            double conv = 0.0;
-            for (int k2 = 0; k2 < nk; k2++) {
-                double c = 0.0;
-                for (int iv = 0; iv < ksz; iv++)
-                    for (int iu = 0; iu < ksz; iu++)
-                        c += (double)Ks[k2 * kk + iv * ksz + iu] * ref[(long)(y - (iv - r)) * pitch + (x - (iu - r))];
-                conv += pk[k2] * c;
+    for (int p = threadIdx.x; ok && p < stamp * stamp; p += blockDim.x) {
+        const int px = p % stamp, py = p / stamp;
+        const int x = xs - hs + px, y = ys - hs + py;
+        const long q = (long)y * pitch + x;
+        const float v = var[q], I = sci[q];
+        if (flags[q] || !(v > 0.0f) || !isfinite(v) || !isfinite(I)) continue;
+        const double wt = 1.0 / (double)v;
+        const double xt = w > 1 ? (2.0 * x - (w - 1)) / (double)(w - 1) : 0.0;
+        const double yt = h > 1 ? (2.0 * y - (h - 1)) / (double)(h - 1) : 0.0;
+        double pk[6], pb[6];
+        terms_d(xt, yt, sdeg, pk);
+        terms_d(xt, yt, bgdeg, pb);
+        double conv = 0.0;
+        for (int k2 = 0; k2 < nk; k2++) {
+            // R(x - (iu - r), y - (iv - r)) = Rw[py + 2r - iv][px + 2r - iu]
+            float c = 0.0f;
+            for (int iv = 0; iv < ksz; iv++) {
+                const float* kr = Ks + k2 * kk + iv * ksz;
+                const float* rr = Rw + (py + 2 * r - iv) * ww + px + 2 * r;
+                for (int iu = 0; iu < ksz; iu++) c = fmaf(kr[iu], rr[-iu], c);
             }
-            const double res = (double)I - conv;
-            for (int a = 0; a < nb; a++) {
-                for (int b = 0; b < nb; b++) acc[a * 6 + b] += wt * pb[a] * pb[b];
-                acc[36 + a] += wt * pb[a] * res;
-            }
-            acc[42] += wt * res * res;
-            acc[43] += 1.0;
+            conv += pk[k2] * (double)c;
         }
+        const double res = (double)I - conv;
+        for (int a2 = 0; a2 < nb; a2++) {
+            for (int b2 = 0; b2 < nb; b2++) acc[a2 * 6 + b2] += wt * pb[a2] * pb[b2];
+            acc[36 + a2] += wt * pb[a2] * res;
+        }
+        acc[42] += wt * res * res;
+        acc[43] += 1.0;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int k = 0; k < 45; k++) {
@@ -582,12 +611,17 @@ __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sc
 // Pass 2 (one CTA): sum the partials, solve for bg, chi2 = r'Wr - 2 bg'q + bg'Abg, stats.
 __global__ void learned_bg_solve_kernel(const double* part, int max_stamps, int bgdeg, int n_coeffs, double* bg,
                                         argus_fit_stats* st, int* status) {
+    __shared__ double Ts[45];
+    if (threadIdx.x < 45) {
+        double v = 0.0;
+        for (int s = 0; s < max_stamps; s++) v += part[(long)s * 45 + threadIdx.x];
+        Ts[threadIdx.x] = v;
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     const int nb = (bgdeg + 1) * (bgdeg + 2) / 2;
     double T[45];
-    for (int k = 0; k < 45; k++) T[k] = 0.0;
-    for (int s = 0; s < max_stamps; s++)
-        for (int k = 0; k < 45; k++) T[k] += part[(long)s * 45 + k];
+    for (int k = 0; k < 45; k++) T[k] = Ts[k];
     double L[6][6], z[6], sol[6];
     bool bad = false;
     for (int j = 0; j < nb && !bad; j++) {
@@ -831,8 +865,11 @@ extern "C" int argus_learned_kernel(argus_ctx* ctx, const float* y, const int* c
     if (!ctx || !y || !centers || !n_stamps || !K || max_stamps < 1 || spatial_degree < 0 || spatial_degree > 2)
         return ARGUS_ERR_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
-    learned_spatial_kernel<<<1, 512, 0, (cudaStream_t)stream>>>(y, centers, n_stamps, max_stamps, frame_w, frame_h,
-                                                                spatial_degree, K, ctx->d_status); argus_count_launch(1);
+    const size_t psm = sizeof(float) * 6 * (size_t)max_stamps;
+    if (psm > 160 * 1024) return ARGUS_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(learned_spatial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    learned_spatial_kernel<<<1, 512, psm, (cudaStream_t)stream>>>(y, centers, n_stamps, max_stamps, frame_w, frame_h,
+                                                                  spatial_degree, K, ctx->d_status); argus_count_launch(1);
     return argus_launch_status();
 }
 
@@ -849,11 +886,14 @@ extern "C" int argus_fit_background(argus_ctx* ctx, const float* sci, const floa
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     double* part = ctx->resid_part;
-    learned_bg_partial_kernel<<<max_stamps, 256, 0, st>>>(sci, sci_var, ref, flags, shape.pitch, shape.w, shape.h,
-                                                          centers, n_stamps, max_stamps, stamp, K, ksize,
-                                                          spatial_degree, bg_degree, part); argus_count_launch(1);
     const int nk = (spatial_degree + 1) * (spatial_degree + 2) / 2, nb = (bg_degree + 1) * (bg_degree + 2) / 2;
-    learned_bg_solve_kernel<<<1, 32, 0, st>>>(part, max_stamps, bg_degree, nk * ksize * ksize + nb, bg, stats,
+    const size_t bsm = sizeof(float) * ((size_t)nk * ksize * ksize + (size_t)(stamp + ksize - 1) * (stamp + ksize - 1));
+    if (bsm > 200 * 1024) return ARGUS_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(learned_bg_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    learned_bg_partial_kernel<<<max_stamps, 256, bsm, st>>>(sci, sci_var, ref, flags, shape.pitch, shape.w, shape.h,
+                                                            centers, n_stamps, max_stamps, stamp, K, ksize,
+                                                            spatial_degree, bg_degree, part); argus_count_launch(1);
+    learned_bg_solve_kernel<<<1, 64, 0, st>>>(part, max_stamps, bg_degree, nk * ksize * ksize + nb, bg, stats,
                                               ctx->d_status); argus_count_launch(1);
     return argus_launch_status();
 }

@@ -91,9 +91,12 @@ class KernelNet:
             B.argus_cnn_forward(self.net, x[s:e], e - s, y[s:e])
         return y
 
-    def fit(self, x, target, *, epochs=10, batch=512, lr=1e-3, seed=0, log=None):
-        """Minibatch Adam on the library kernels; returns the per-epoch mean loss."""
+    def fit(self, x, target, *, epochs=10, batch=512, lr=1e-3, lr_end=None, seed=0, log=None):
+        """Minibatch Adam on the library kernels; returns the per-epoch mean loss.
+        With lr_end the rate follows a cosine from lr to lr_end over all steps."""
         n = x.shape[0]
+        total = max(1, epochs * (n // batch))
+        step = 0
         g = torch.Generator(device=self.device)
         g.manual_seed(seed)
         loss = torch.zeros(1, dtype=torch.float64, device=self.device)
@@ -106,7 +109,9 @@ class KernelNet:
                 idx = perm[s:s + batch]
                 xb = x.index_select(0, idx).contiguous()
                 tb = target.index_select(0, idx).contiguous()
-                B.argus_cnn_train_step(self.net, xb, tb, batch, lr, loss)
+                rate = lr if lr_end is None else lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * step / total))
+                B.argus_cnn_train_step(self.net, xb, tb, batch, rate, loss)
+                step += 1
                 tot += loss[0]
                 nb += 1
             hist.append(float(tot.item()) / max(nb, 1))
@@ -115,8 +120,26 @@ class KernelNet:
         return hist
 
 
+TRAIN_CHUNK = 32768   # pairs per batched-segment run (one run's per-segment scratch)
+
+
 def training_set(n, seed=5, device=0, sky=300.0, flux=(1e4, 1e6), sig_ref=1.0, sig_range=(1.0, 3.0),
                  jump_p=0.1, ctx=None):
+    """Seeded stamp pairs and plain-method targets, generated in chunks of at most
+    TRAIN_CHUNK pairs (chunk c uses seed + 1000 c); see `_training_chunk`."""
+    xs, ts, sigs = [], [], []
+    for c, s0 in enumerate(range(0, n, TRAIN_CHUNK)):
+        x, t, sg = _training_chunk(min(TRAIN_CHUNK, n - s0), seed + 1000 * c, device, sky, flux, sig_ref,
+                                   sig_range, jump_p, ctx)
+        xs.append(x)
+        ts.append(t)
+        sigs.append(sg)
+    if len(xs) == 1:
+        return xs[0], ts[0], sigs[0]
+    return torch.cat(xs), torch.cat(ts), np.concatenate(sigs)
+
+
+def _training_chunk(n, seed, device, sky, flux, sig_ref, sig_range, jump_p, ctx):
     """Seeded stamp pairs and plain-method targets.
 
     Each pair is a 41x41 window with one star near its centre; the science PSF
