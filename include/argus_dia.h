@@ -345,11 +345,22 @@ int argus_learned_kernel(argus_ctx *ctx, const float *y, const int *centers, con
  * least squares on the stamp pixels, and chi2 of the result there:
  * r = I - sum_k p_k (R (x) K_k), bg = argmin sum w (r - sum pb bg)^2; the
  * model convolution in FP32, the normal-equation sums and the solve in FP64.
- * stats (device) receives chi2, n_pix, dof (n_pix - Ks ksize^2 - Kb). */
+ * stats (device) receives chi2, n_pix, n_coeffs = Kb and dof = n_pix - Kb (the
+ * kernel is not fitted to these pixels). */
 int argus_fit_background(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
                          const uint8_t *flags, argus_shape shape, const int *centers, const int *n_stamps,
                          int max_stamps, int stamp, const float *K, int ksize, int spatial_degree,
                          int bg_degree, double *bg, argus_fit_stats *stats, argus_stream stream);
+/* As argus_fit_background, with one amplitude per spatial term fitted jointly:
+ * min sum w (I - sum_k alpha_k p_k (R (x) K_k) - sum pb bg)^2 over alpha and
+ * bg; K (device, in/out) is then rescaled, K_k <- alpha_k K_k.  The kernel's
+ * shape is the given one, its flux scale per spatial term is fitted.
+ * n_coeffs = Ks + Kb, dof = n_pix - Ks - Kb. */
+int argus_fit_scale_background(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
+                               const uint8_t *flags, argus_shape shape, const int *centers,
+                               const int *n_stamps, int max_stamps, int stamp, float *K, int ksize,
+                               int spatial_degree, int bg_degree, double *bg, argus_fit_stats *stats,
+                               argus_stream stream);
 
 /* Stamp selection that allocates nothing, for callers that cannot call
  * cudaMalloc (a host that reserves all device memory up front, a real-time

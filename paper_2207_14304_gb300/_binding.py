@@ -119,6 +119,7 @@ SIGNATURES = {
     "argus_cnn_prepare": ([P, P, SH, P, P, I, P, P], I),
     "argus_learned_kernel": ([P, P, P, P, I, I, I, I, P, P], I),
     "argus_fit_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
+    "argus_fit_scale_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
 }
 
 
@@ -357,6 +358,14 @@ def argus_fit_background(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps
                                        _ptr(centers), _ptr(n_stamps), int(max_stamps), int(stamp), _ptr(K),
                                        int(ksize), int(spatial_degree), int(bg_degree), _ptr(bg), _ptr(stats),
                                        _stream(stream)), "argus_fit_background")
+
+
+def argus_fit_scale_background(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp, K,
+                               ksize, spatial_degree, bg_degree, bg, stats, stream=None):
+    _check(load().argus_fit_scale_background(ctx, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(flags), shape,
+                                             _ptr(centers), _ptr(n_stamps), int(max_stamps), int(stamp), _ptr(K),
+                                             int(ksize), int(spatial_degree), int(bg_degree), _ptr(bg), _ptr(stats),
+                                             _stream(stream)), "argus_fit_scale_background")
 
 
 def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,

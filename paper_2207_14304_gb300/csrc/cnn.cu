@@ -533,24 +533,29 @@ __device__ __forceinline__ void terms_d(double xt, double yt, int deg, double* o
     }
 }
 
-// Background given the kernel, on the stamp pixels: r = I - sum_k p_k (R (x) K_k); the
-// background polynomial solves sum w pb pb^T bg = sum w pb r; chi2 = sum w (r - bg)^2.
-// Pass 1 (grid over stamps): per-stamp partial normal equations in FP64.
+// Least squares on the stamp pixels given the kernel K_k, with c_k = R (x) K_k:
+//   background only:     min sum w (I - sum_k p_k c_k - sum_j pb_j bg_j)^2 over bg;
+//   scales + background: min sum w (I - sum_k alpha_k p_k c_k - sum_j pb_j bg_j)^2 over
+//                        alpha and bg, and K_k <- alpha_k K_k.
+// Pass 1 (grid over stamps): per-stamp partial normal equations, layout
+// [A 12x12][rhs 12][t'Wt][n_pix]; the model convolution in FP32, the sums in FP64.
+constexpr int BGN = 12, BGP = BGN * BGN + BGN + 2;
+
 __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sci, const float* var, const float* ref,
                                                                  const uint8_t* flags, long pitch, int w, int h,
                                                                  const int* centers, const int* n_stamps,
                                                                  int max_stamps, int stamp, const float* K, int ksz,
-                                                                 int sdeg, int bgdeg, double* part) {
-    // shared: the nk kernels and the stamp's reference window (stamp + 2r)^2;
-    // the model convolution runs in FP32, the normal-equation sums in FP64
+                                                                 int sdeg, int bgdeg, int scale, double* part) {
+    // shared: the nk kernels and the stamp's reference window (stamp + 2r)^2
     extern __shared__ float bsm[];
-    __shared__ double red[8][36 + 6 + 3];
+    __shared__ double red[8][BGP];
     const int s = blockIdx.x;
     const int nk = (sdeg + 1) * (sdeg + 2) / 2, nb = (bgdeg + 1) * (bgdeg + 2) / 2, kk = ksz * ksz, r = ksz / 2;
+    const int n = scale ? nk + nb : nb;
     const int ww = stamp + 2 * r;
     float* Ks = bsm;
     float* Rw = bsm + nk * kk;
-    double* out = part + (long)s * (36 + 6 + 3);
+    double* out = part + (long)s * BGP;
     const bool live = s < min(*n_stamps, max_stamps);
     const int xs = live ? centers[2 * s] : 0, ys = live ? centers[2 * s + 1] : 0, hs = stamp / 2;
     const bool ok = live && xs - hs - r >= 0 && xs + hs + r <= w - 1 && ys - hs - r >= 0 && ys + hs + r <= h - 1;
@@ -560,8 +565,8 @@ __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sc
         Rw[e] = ref[(long)(ys - hs - r + jy) * pitch + (xs - hs - r + jx)];
     }
     __syncthreads();
-    double acc[36 + 6 + 3];
-    for (int k = 0; k < 45; k++) acc[k] = 0.0;
+    double acc[BGP];
+    for (int k = 0; k < BGP; k++) acc[k] = 0.0;
     for (int p = threadIdx.x; ok && p < stamp * stamp; p += blockDim.x) {
         const int px = p % stamp, py = p / stamp;
         const int x = xs - hs + px, y = ys - hs + py;
@@ -571,7 +576,7 @@ __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sc
         const double wt = 1.0 / (double)v;
         const double xt = w > 1 ? (2.0 * x - (w - 1)) / (double)(w - 1) : 0.0;
         const double yt = h > 1 ? (2.0 * y - (h - 1)) / (double)(h - 1) : 0.0;
-        double pk[6], pb[6];
+        double pk[6], pb[6], z[BGN];
         terms_d(xt, yt, sdeg, pk);
         terms_d(xt, yt, bgdeg, pb);
         double conv = 0.0;
@@ -583,89 +588,101 @@ __global__ void __launch_bounds__(256) learned_bg_partial_kernel(const float* sc
                 const float* rr = Rw + (py + 2 * r - iv) * ww + px + 2 * r;
                 for (int iu = 0; iu < ksz; iu++) c = fmaf(kr[iu], rr[-iu], c);
             }
+            if (scale) z[k2] = pk[k2] * (double)c;
             conv += pk[k2] * (double)c;
         }
-        const double res = (double)I - conv;
-        for (int a2 = 0; a2 < nb; a2++) {
-            for (int b2 = 0; b2 < nb; b2++) acc[a2 * 6 + b2] += wt * pb[a2] * pb[b2];
-            acc[36 + a2] += wt * pb[a2] * res;
+        for (int j = 0; j < nb; j++) z[(scale ? nk : 0) + j] = pb[j];
+        const double t = scale ? (double)I : (double)I - conv;
+        for (int a2 = 0; a2 < n; a2++) {
+            const double wz = wt * z[a2];
+            for (int b2 = 0; b2 < n; b2++) acc[a2 * BGN + b2] += wz * z[b2];
+            acc[BGN * BGN + a2] += wz * t;
         }
-        acc[42] += wt * res * res;
-        acc[43] += 1.0;
+        acc[BGN * BGN + BGN] += wt * t * t;
+        acc[BGN * BGN + BGN + 1] += 1.0;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < 45; k++) {
+    for (int k = 0; k < BGP; k++) {
         double v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[wid][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 45) {
+    for (int k = threadIdx.x; k < BGP; k += blockDim.x) {
         double v = 0.0;
-        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) v += red[w8][threadIdx.x];
-        out[threadIdx.x] = v;
+        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) v += red[w8][k];
+        out[k] = v;
     }
 }
 
-// Pass 2 (one CTA): sum the partials, solve for bg, chi2 = r'Wr - 2 bg'q + bg'Abg, stats.
-__global__ void learned_bg_solve_kernel(const double* part, int max_stamps, int bgdeg, int n_coeffs, double* bg,
-                                        argus_fit_stats* st, int* status) {
-    __shared__ double Ts[45];
-    if (threadIdx.x < 45) {
+// Pass 2 (one CTA): sum the partials, Cholesky solve of the n x n system
+// (FP64), chi2 = t'Wt - 2 sol'rhs + sol'A sol, stats; with scale, K_k <- alpha_k K_k.
+__global__ void __launch_bounds__(256) learned_bg_solve_kernel(const double* part, int max_stamps, int sdeg, int bgdeg,
+                                                              int scale, float* K, int kk, double* bg,
+                                                              argus_fit_stats* st, int* status) {
+    __shared__ double T[BGP];
+    __shared__ double alpha[6];
+    __shared__ int bad_s;
+    for (int k = threadIdx.x; k < BGP; k += blockDim.x) {
         double v = 0.0;
-        for (int s = 0; s < max_stamps; s++) v += part[(long)s * 45 + threadIdx.x];
-        Ts[threadIdx.x] = v;
+        for (int s = 0; s < max_stamps; s++) v += part[(long)s * BGP + k];
+        T[k] = v;
     }
+    const int nk = (sdeg + 1) * (sdeg + 2) / 2, nb = (bgdeg + 1) * (bgdeg + 2) / 2;
+    const int n = scale ? nk + nb : nb;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const int nb = (bgdeg + 1) * (bgdeg + 2) / 2;
-    double T[45];
-    for (int k = 0; k < 45; k++) T[k] = Ts[k];
-    double L[6][6], z[6], sol[6];
-    bool bad = false;
-    for (int j = 0; j < nb && !bad; j++) {
-        double d = T[j * 6 + j];
-        for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k];
-        if (!(d > 0.0)) { bad = true; break; }
-        L[j][j] = sqrt(d);
-        for (int i = j + 1; i < nb; i++) {
-            double v = T[i * 6 + j];
-            for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
-            L[i][j] = v / L[j][j];
+    if (threadIdx.x == 0) {
+        double L[BGN][BGN], z[BGN], sol[BGN];
+        bool bad = false;
+        for (int j = 0; j < n && !bad; j++) {
+            double d = T[j * BGN + j];
+            for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k];
+            if (!(d > 0.0)) { bad = true; break; }
+            L[j][j] = sqrt(d);
+            for (int i = j + 1; i < n; i++) {
+                double v = T[i * BGN + j];
+                for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
+                L[i][j] = v / L[j][j];
+            }
+        }
+        argus_fit_stats o;
+        o.chi2_a0 = 0.0; o.max_step = 0.0; o.refine_iters = 0; o.pad_ = 0; o.precision = -1; o.n_stamps_used = 0;
+        o.n_coeffs = n;
+        o.n_pix = (long long)T[BGN * BGN + BGN + 1];
+        o.dof = o.n_pix - n;
+        bad_s = bad ? 1 : 0;
+        if (bad) {
+            argus_latch(status, ARGUS_ERR_SINGULAR);
+            o.status = ARGUS_ERR_SINGULAR;
+            o.chi2 = 0.0;
+            *st = o;
+        } else {
+            for (int i = 0; i < n; i++) {
+                double v = T[BGN * BGN + i];
+                for (int k = 0; k < i; k++) v -= L[i][k] * z[k];
+                z[i] = v / L[i][i];
+            }
+            for (int i = n - 1; i >= 0; i--) {
+                double v = z[i];
+                for (int k = i + 1; k < n; k++) v -= L[k][i] * sol[k];
+                sol[i] = v / L[i][i];
+            }
+            double chi2 = T[BGN * BGN + BGN];
+            for (int i = 0; i < n; i++) {
+                chi2 -= 2.0 * sol[i] * T[BGN * BGN + i];
+                for (int j = 0; j < n; j++) chi2 += sol[i] * T[i * BGN + j] * sol[j];
+            }
+            for (int j = 0; j < nb; j++) bg[j] = sol[(scale ? nk : 0) + j];
+            for (int k = 0; k < nk; k++) alpha[k] = scale ? sol[k] : 1.0;
+            o.chi2 = chi2;
+            o.status = ARGUS_OK;
+            *st = o;
         }
     }
-    argus_fit_stats s;
-    s.chi2_a0 = 0.0; s.max_step = 0.0; s.refine_iters = 0; s.pad_ = 0; s.precision = -1; s.n_stamps_used = 0;
-    s.n_coeffs = n_coeffs;
-    s.n_pix = (long long)T[43];
-    s.dof = s.n_pix - n_coeffs;
-    if (bad) {
-        argus_latch(status, ARGUS_ERR_SINGULAR);
-        s.status = ARGUS_ERR_SINGULAR;
-        s.chi2 = 0.0;
-        *st = s;
-        return;
-    }
-    for (int i = 0; i < nb; i++) {
-        double v = T[36 + i];
-        for (int k = 0; k < i; k++) v -= L[i][k] * z[k];
-        z[i] = v / L[i][i];
-    }
-    for (int i = nb - 1; i >= 0; i--) {
-        double v = z[i];
-        for (int k = i + 1; k < nb; k++) v -= L[k][i] * sol[k];
-        sol[i] = v / L[i][i];
-    }
-    double chi2 = T[42];
-    for (int i = 0; i < nb; i++) {
-        chi2 -= 2.0 * sol[i] * T[36 + i];
-        for (int j = 0; j < nb; j++) chi2 += sol[i] * T[i * 6 + j] * sol[j];
-        bg[i] = sol[i];
-    }
-    s.chi2 = chi2;
-    s.status = ARGUS_OK;
-    *st = s;
+    __syncthreads();
+    if (scale && !bad_s)
+        for (int e = threadIdx.x; e < nk * kk; e += blockDim.x) K[e] = (float)(alpha[e / kk] * (double)K[e]);
 }
 
 }  // namespace
@@ -873,27 +890,45 @@ extern "C" int argus_learned_kernel(argus_ctx* ctx, const float* y, const int* c
     return argus_launch_status();
 }
 
-extern "C" int argus_fit_background(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
-                                    const uint8_t* flags, argus_shape shape, const int* centers, const int* n_stamps,
-                                    int max_stamps, int stamp, const float* K, int ksize, int spatial_degree,
-                                    int bg_degree, double* bg, argus_fit_stats* stats, argus_stream stream) {
+static int fit_background_impl(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
+                               const uint8_t* flags, argus_shape shape, const int* centers, const int* n_stamps,
+                               int max_stamps, int stamp, float* K, int ksize, int spatial_degree, int bg_degree,
+                               int scale, double* bg, argus_fit_stats* stats, cudaStream_t st) {
     if (!ctx || !sci || !sci_var || !ref || !flags || !centers || !n_stamps || !K || !bg || !stats) return ARGUS_ERR_ARG;
-    if (max_stamps < 1 || max_stamps > ctx->resid_parts * (ctx->np_cols + 4) / 45 || ksize < 3 || ksize > 31 ||
-        !(ksize & 1) || spatial_degree < 0 || spatial_degree > 2 || bg_degree < 0 || bg_degree > 2 || stamp < 1)
+    if (max_stamps < 1 || (size_t)max_stamps * BGP > (size_t)ctx->resid_parts * (ctx->np_cols + 4) || ksize < 3 ||
+        ksize > 31 || !(ksize & 1) || spatial_degree < 0 || spatial_degree > 2 || bg_degree < 0 || bg_degree > 2 ||
+        stamp < 1)
         return ARGUS_ERR_ARG;
     int rc = argus_check_shape(shape, ctx->max_pixels);
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
-    cudaStream_t st = (cudaStream_t)stream;
     double* part = ctx->resid_part;
-    const int nk = (spatial_degree + 1) * (spatial_degree + 2) / 2, nb = (bg_degree + 1) * (bg_degree + 2) / 2;
+    const int nk = (spatial_degree + 1) * (spatial_degree + 2) / 2;
     const size_t bsm = sizeof(float) * ((size_t)nk * ksize * ksize + (size_t)(stamp + ksize - 1) * (stamp + ksize - 1));
     if (bsm > 200 * 1024) return ARGUS_ERR_UNSUPPORTED;
     cudaFuncSetAttribute(learned_bg_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
     learned_bg_partial_kernel<<<max_stamps, 256, bsm, st>>>(sci, sci_var, ref, flags, shape.pitch, shape.w, shape.h,
                                                             centers, n_stamps, max_stamps, stamp, K, ksize,
-                                                            spatial_degree, bg_degree, part); argus_count_launch(1);
-    learned_bg_solve_kernel<<<1, 64, 0, st>>>(part, max_stamps, bg_degree, nk * ksize * ksize + nb, bg, stats,
-                                              ctx->d_status); argus_count_launch(1);
+                                                            spatial_degree, bg_degree, scale, part); argus_count_launch(1);
+    learned_bg_solve_kernel<<<1, 256, 0, st>>>(part, max_stamps, spatial_degree, bg_degree, scale, K, ksize * ksize,
+                                               bg, stats, ctx->d_status); argus_count_launch(1);
     return argus_launch_status();
+}
+
+extern "C" int argus_fit_background(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
+                                    const uint8_t* flags, argus_shape shape, const int* centers, const int* n_stamps,
+                                    int max_stamps, int stamp, const float* K, int ksize, int spatial_degree,
+                                    int bg_degree, double* bg, argus_fit_stats* stats, argus_stream stream) {
+    return fit_background_impl(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,
+                               const_cast<float*>(K), ksize, spatial_degree, bg_degree, 0, bg, stats,
+                               (cudaStream_t)stream);
+}
+
+extern "C" int argus_fit_scale_background(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
+                                          const uint8_t* flags, argus_shape shape, const int* centers,
+                                          const int* n_stamps, int max_stamps, int stamp, float* K, int ksize,
+                                          int spatial_degree, int bg_degree, double* bg, argus_fit_stats* stats,
+                                          argus_stream stream) {
+    return fit_background_impl(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp, K, ksize,
+                               spatial_degree, bg_degree, 1, bg, stats, (cudaStream_t)stream);
 }

@@ -8,8 +8,9 @@ segment path), `KernelNet.fit` trains on them, and `LearnedFit` runs the
 per-frame learned fit with the least-squares fit as fallback and judge:
 
   argus_cnn_prepare -> argus_cnn_forward -> argus_learned_kernel (spatial LS
-  across stamps) -> argus_fit_background (background and chi2 on the stamps);
-  if chi2/dof > 1.1 x the last plain fit's chi2/dof, argus_fit_kernel runs.
+  across stamps) -> argus_fit_scale_background (one flux scale per spatial
+  term and the background by least squares, chi2 on the stamps); if chi2/dof >
+  1.1 x the last plain fit's chi2/dof, argus_fit_kernel runs.
 """
 from __future__ import annotations
 
@@ -211,10 +212,11 @@ def _training_chunk(n, seed, device, sky, flux, sig_ref, sig_range, jump_p, ctx)
 class LearnedFit:
     """Per-frame learned kernel with the least-squares fit as fallback and judge."""
 
-    def __init__(self, pipe, net: KernelNet, *, ratio=1.1):
+    def __init__(self, pipe, net: KernelNet, *, ratio=1.1, fit_scale=True):
         self.pipe = pipe              # a FramePipeline (its basis must have ksize 21)
         self.net = net
         self.ratio = float(ratio)
+        self.fit_scale = bool(fit_scale)   # fit one flux scale per spatial term with the background
         if pipe.basis.ksize != STAMP:
             raise ValueError("the learned kernel is 21x21")
         self.x = torch.zeros((pipe.max_stamps, NPX, 2), dtype=torch.float32, device=pipe.device)
@@ -231,9 +233,9 @@ class LearnedFit:
         B.argus_cnn_forward(self.net.net, self.x, p.max_stamps, self.y, stream)
         B.argus_learned_kernel(p.ctx, self.y, p.centers, p.n_stamps, p.max_stamps, p.w, p.h,
                                p.basis.spatial_degree, p.K, stream)
-        B.argus_fit_background(p.ctx, p.img, p.var, ref, p.flags, p.shape, p.centers, p.n_stamps, p.max_stamps,
-                               p.stamp, p.K, p.basis.ksize, p.basis.spatial_degree, p.basis.bg_degree, p.bg,
-                               self.stats, stream)
+        fit = B.argus_fit_scale_background if self.fit_scale else B.argus_fit_background
+        fit(p.ctx, p.img, p.var, ref, p.flags, p.shape, p.centers, p.n_stamps, p.max_stamps, p.stamp, p.K,
+            p.basis.ksize, p.basis.spatial_degree, p.basis.bg_degree, p.bg, self.stats, stream)
 
     def plain(self, ref, stream=None):
         self.pipe.fit(ref, stream)

@@ -167,6 +167,54 @@ def test_fit_background_matches_library_least_squares(ora):
         B.argus_destroy(ctx)
 
 
+def test_fit_scale_background_recovers_scales(ora):
+    """A kernel given at the wrong flux scale per spatial term is rescaled by the joint
+    least squares: I = sum_k p_k R (x) (s_k K_k) + bg exactly, so the fit returns s_k, bg
+    and chi2 = 0 (FP32-model level)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, h = 300, 260
+    cat = synth.star_catalog(300, w, h, seed=8, flux_min=1e3, flux_max=1e5)
+    R = synth.render(cat, w, h, 1.2, sky=300.0).numpy().astype(np.float32)
+    rng = np.random.default_rng(6)
+    K = (rng.normal(0, 1e-3, (6, 21, 21))).astype(np.float32)
+    K[0, 10, 10] += 1.0
+    scales = np.array([1.02, 0.97, 1.05, 0.9, 1.1, 0.95])
+    bg_true = np.array([3.0, 1.0, -0.5, 0.7, 0.2, -0.3])
+    cen = np.array([(60, 60), (150, 80), (240, 200), (100, 180), (200, 120), (60, 200)], np.int32)
+    # science = the exact model with the true scales (oracle, FP64)
+    Ktrue = (K * scales[:, None, None]).astype(np.float64)
+    I0 = np.zeros((h, w), np.float32)
+    xy = np.array([(x, y) for y in range(h) for x in range(w)], np.int32)
+    D, _ = ora.subtract_at(xy, I0, np.ones_like(I0), R, np.zeros_like(R), np.zeros((h, w), np.uint8), Ktrue,
+                           bg_true, sdeg=2, bgdeg=2)
+    I = (-D).reshape(h, w).astype(np.float32)          # I = model (D = 0 - model)
+    V = np.full_like(I, 25.0)
+    fl = np.zeros((h, w), np.uint8)
+    pitch = pitch_for(w)
+    ctx = B.argus_create(0, h * pitch, 64, 64, 1 << 10)
+    try:
+        def dev(a):
+            t = torch.zeros((h, pitch), dtype=torch.from_numpy(a).dtype)
+            t[:, :w] = torch.from_numpy(a)
+            return t.cuda()
+        bg = torch.zeros(6, dtype=torch.float64, device="cuda")
+        st = torch.zeros(128, dtype=torch.uint8, device="cuda")
+        dK = torch.from_numpy(K.reshape(-1).copy()).cuda()
+        B.argus_fit_scale_background(ctx, dev(I), dev(V), dev(R), dev(fl), B.argus_shape(w, h, pitch),
+                                     torch.from_numpy(cen).cuda(), torch.tensor([6, 0, 0, 0], dtype=torch.int32).cuda(),
+                                     6, 21, dK, 21, 2, 2, bg, st)
+        torch.cuda.synchronize()
+        s = B.fit_stats_from_bytes(st)
+        assert s["status"] == 0 and s["n_coeffs"] == 12 and s["dof"] == s["n_pix"] - 12
+        Kout = dK.cpu().numpy().reshape(6, 21, 21)
+        np.testing.assert_allclose(Kout, K * scales[:, None, None], rtol=1e-4, atol=1e-7)
+        np.testing.assert_allclose(bg.cpu().numpy(), bg_true, atol=2e-3)
+        assert s["chi2"] < 1e-4 * s["n_pix"]
+    finally:
+        B.argus_destroy(ctx)
+
+
 def test_learned_fit_falls_back_to_least_squares():
     """An untrained network's kernel is far worse than the least-squares fit, so the
     per-frame learned fit must judge it by chi2 and use the plain fit instead; with
