@@ -54,14 +54,15 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
     constexpr int R = (KS - 1) / 2;
     constexpr int SW = TILE + 2 * R;             // staged tile side
     constexpr int NKP = NK == 1 ? 1 : (NK <= 4 ? 4 : 8);
-    constexpr int NCOL = ROWS_PER_THREAD + KS - 1;
     constexpr int KSP = (KS + 3) / 4 * 4;
     constexpr int KTSZ = (KS * KS * NKP + 3) / 4 * 4;   // keeps Kc2 16-byte aligned
 
-    float* Rs = smem;                             // [SW][SW], SW even
-    float* Vs = Rs + SW * SW;                     // [SW][SW]
-    float* Kt = Vs + SW * SW;                     // [KS][KS][NKP]
-    float* Kc2 = Kt + KTSZ;                       // [KS][KSP]
+    // CONV: Rs [SW][SW], Vs [SW][SW], Kt [KS][KS][NKP], Kc2 [KS][KSP];
+    // variance only: Vs [SW][SW], Kc2 [KS][KSP]  (SW even, Kc2 16-byte aligned)
+    float* Rs = smem;
+    float* Vs = CONV ? Rs + SW * SW : smem;
+    float* Kt = Vs + SW * SW;
+    float* Kc2 = CONV ? Kt + KTSZ : Vs + SW * SW;
 
     const int tid = threadIdx.x;
     __syncthreads();   // the previous tile's readers are done with shared memory
@@ -158,7 +159,7 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
 #pragma unroll
     for (int j = 0; j < ROWS_PER_THREAD; j++) accv[j] = 0.0f;
 #pragma unroll 1
-    for (int iu = 0; iu < KS; iu++) {
+    for (int iu = 0; iu < (a.diff_var ? KS : 0); iu++) {   // no variance output: skipped
         const float* vcol = Vs + ly0 * SW + lx + 2 * R - iu;
 #pragma unroll 1
         for (int b = 0; b < KS / IVB; b++) {
@@ -213,14 +214,14 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
 }
 
 
-template <int KS, int NK>
+template <int KS, int NK, bool CONV = true>
 constexpr size_t tile_smem_bytes() {
     constexpr int R = (KS - 1) / 2;
     constexpr int SW = TILE + 2 * R;
     constexpr int NKP = NK == 1 ? 1 : (NK <= 4 ? 4 : 8);
     constexpr int KSP = (KS + 3) / 4 * 4;
     constexpr int KTSZ = (KS * KS * NKP + 3) / 4 * 4;
-    return sizeof(float) * (2 * SW * SW + KTSZ + KS * KSP);
+    return CONV ? sizeof(float) * (2 * SW * SW + KTSZ + KS * KSP) : sizeof(float) * (SW * SW + KS * KSP);
 }
 
 }  // namespace argus_sub
