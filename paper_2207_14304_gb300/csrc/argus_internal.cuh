@@ -35,6 +35,7 @@ struct argus_ctx {
     // fit scratch
     float* X;            // [max_stamps * 31*31][64] basis-convolved stamp pixels
     float* rowmeta;      // [max_stamps * 31*31][16] per-row design weights of the fit
+    float* design;       // [max_stamps * 31*31 rounded up to 32][np_cols] weighted design matrix (FP32)
     int gram_parts;      // number of partial Gram slots
     float* gram_part;    // [gram_parts][np_cols][np_cols]
     double* M;           // [np_cols][np_cols] reduced normal matrix (+ target column)

@@ -348,83 +348,103 @@ __global__ void __launch_bounds__(256) row_weights_kernel(GramArgs g, float* rw)
     }
 }
 
-// K4 (FP32): SIMT Gram on 64x64 tiles of the upper triangle.  Per 32-row
-// chunk each thread stages 8 design values of A (and of B off the diagonal)
-// from X and the row weights; the next chunk's loads are issued before the
-// current chunk's FMAs (double-buffered shared memory, one barrier per chunk).
+// The weighted design matrix C [rows][NP] (FP32, row-major), materialised once
+// per fit: C[rho][j] = sqrt(w) p_k X_n (n >= 0), sqrt(w) pb_k (background),
+// sqrt(w) I (target), 0 (padding); rows past the stamp count are zero up to the
+// next multiple of 32.  One CTA per 32 rows stages the rows' weights and basis
+// values in shared memory and writes whole rows (coalesced).
 constexpr int GT = 64;
 constexpr int GK = 32;
 
-__global__ void __launch_bounds__(256, 3) gram_simt_kernel(GramArgs g, const float* rw, int ntile) {
+__global__ void __launch_bounds__(256) design_kernel(GramArgs g, const float* rw, float* C) {
+    extern __shared__ int dsm[];
+    int* cn = dsm;                                   // [NP] basis index, or -1
+    int* cs = dsm + g.NP;                            // [NP] weight slot, or -1 (padding)
+    __shared__ float w[GK][RMETA];
+    __shared__ float xv[GK][ARGUS_MAX_NB + 1];
+    for (int j = threadIdx.x; j < g.NP; j += blockDim.x) {
+        int n, k;
+        col_code(g, j, n, k);
+        cn[j] = n >= 0 ? n : -1;
+        cs[j] = n >= 0 ? k : (n == -100 ? 12 : (n == -200 ? -1 : 6 + (-1 - n)));
+    }
+    const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
+    const long nchunks = (nrows + GK - 1) / GK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const long rho0 = ch * GK;
+        __syncthreads();
+        // weights: two rows per warp per step (row warp * 2 + (lane >> 4), slot lane & 15)
+        for (int k = warp * 2 + (lane >> 4); k < GK; k += 16) {
+            const long rho = rho0 + k;
+            w[k][lane & 15] = rho < nrows ? rw[rho * RMETA + (lane & 15)] : 0.0f;
+        }
+        // basis values: lane = row within the chunk (coalesced over pixels), warp strides over n
+        {
+            const long rho = rho0 + lane;
+            const bool in = rho < nrows;
+            const int s = in ? (int)(rho / g.ss) : 0;
+            const int pix = in ? (int)(rho - (long)s * g.ss) : 0;
+            const float* xs = g.X + (long)s * g.nb * g.ss + pix;
+            for (int n = warp; n < g.nb; n += 8) xv[lane][n] = in ? __ldg(xs + (long)n * g.ss) : 0.0f;
+        }
+        __syncthreads();
+        // one warp per row, lanes along the columns (coalesced writes)
+        for (int k = warp; k < GK; k += 8) {
+            float* crow = C + (rho0 + k) * g.NP;
+            for (int j = lane; j < g.NP; j += 32) {
+                const int n = cn[j], sl = cs[j];
+                const float wt = sl >= 0 ? w[k][sl] : 0.0f;
+                // X of skipped stamps holds no defined values: a zero weight gives 0
+                crow[j] = (n >= 0 && wt != 0.0f) ? wt * xv[k][n] : wt;
+            }
+        }
+    }
+}
+
+// K4 (FP32): C^T C on 64x64 tiles of the upper triangle, 4x4 outputs per
+// thread.  Grid (tile pair, slot): the pairs that read one row chunk are
+// launched side by side, so a chunk comes from DRAM about once and from L2 for
+// the other pairs.  The 32-row chunks of A and B stream in by 16-byte cp.async,
+// double-buffered; per chunk the FP32 products are summed and folded into a
+// double-float accumulator (error-free two-sum).
+__global__ void __launch_bounds__(256, 3) gram_cp_kernel(GramArgs g, const float* C, int ntile) {
     __shared__ __align__(16) float As[2][GK][GT + 4];
     __shared__ __align__(16) float Bs[2][GK][GT + 4];
-    __shared__ int cn[2][GT], cw[2][GT];
-    // upper-triangle tile pair
-    int pr = blockIdx.y, ti = 0;
+    int pr = blockIdx.x, ti = 0;
     while (pr >= ntile - ti) { pr -= ntile - ti; ti++; }
     const int tj = ti + pr;
     const bool diag = ti == tj;
     const int tid = threadIdx.x;
-    for (int c = tid; c < 2 * GT; c += blockDim.x) {
-        const int which = c / GT, jj = c % GT;
-        int n, k;
-        col_code(g, (which ? tj : ti) * GT + jj, n, k);
-        cn[which][jj] = n >= 0 ? n : -1;                       // basis image, or none
-        cw[which][jj] = n >= 0 ? k : (n == -100 ? 12 : (n == -200 ? -1 : 6 + (-1 - n)));
-    }
-    __syncthreads();
+    const int slot = blockIdx.y, nslots = gridDim.y;
     const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
     const long nchunks = (nrows + GK - 1) / GK;
-    const int sk = tid & 31, cg = tid >> 5;   // staging: row sk, columns cg*8 .. cg*8+7
-    float pa[8], pb[8];
-    auto fetch = [&](long ch) {
-        const long rho = ch * GK + sk;
-        const bool in = rho < nrows;
-        const int s = in ? (int)(rho / g.ss) : 0;
-        const int pix = in ? (int)(rho - (long)s * g.ss) : 0;
-        const float* w = rw + (in ? rho : 0) * RMETA;
-        const float* xs = g.X + (long)s * g.nb * g.ss + pix;
-        // every load is issued unconditionally (X rows of skipped stamps hold
-        // no defined values: a zero weight selects 0 instead of multiplying)
+    auto load = [&](int buf, long ch) {
 #pragma unroll
-        for (int cc = 0; cc < 8; cc++) {
-            const int jj = cg * 8 + cc;
-            const int sa = cw[0][jj], na = cn[0][jj], sb = cw[1][jj], nb = cn[1][jj];
-            const float wa = __ldg(w + (sa >= 0 ? sa : 15));
-            const float xa = __ldg(xs + (long)(na >= 0 ? na : 0) * g.ss);
-            const float wb = __ldg(w + (sb >= 0 ? sb : 15));
-            const float xb = __ldg(xs + (long)(nb >= 0 ? nb : 0) * g.ss);
-            const float va = na >= 0 ? wa * xa : wa;
-            const float vb = nb >= 0 ? wb * xb : wb;
-            pa[cc] = (in && sa >= 0 && wa != 0.0f) ? va : 0.0f;
-            pb[cc] = (!diag && in && sb >= 0 && wb != 0.0f) ? vb : 0.0f;
+        for (int h = 0; h < 2; h++) {
+            const int idx = tid + h * 256;       // 32 rows x 16 float4 per operand
+            const int row = idx >> 4, c4 = idx & 15;
+            const long rbase = (ch * GK + row) * g.NP;
+            const int ca = ti * GT + 4 * c4, cb = tj * GT + 4 * c4;
+            tc::cp_async16(&As[buf][row][4 * c4], C + rbase + (ca < g.NP ? ca : 0), ca < g.NP ? 16 : 0);
+            if (!diag) tc::cp_async16(&Bs[buf][row][4 * c4], C + rbase + (cb < g.NP ? cb : 0), cb < g.NP ? 16 : 0);
         }
     };
-    auto stash = [&](int buf) {
-#pragma unroll
-        for (int cc = 0; cc < 8; cc++) {
-            As[buf][sk][cg * 8 + cc] = pa[cc];
-            if (!diag) Bs[buf][sk][cg * 8 + cc] = pb[cc];
-        }
-    };
-    // per 32-row chunk the products are summed in FP32 (acc), then folded into a
-    // double-float accumulator (hi, lo) with an error-free two-sum
     float hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) hi[i][j] = lo[i][j] = 0.0f;
     const int ty = tid / 16, tx = tid % 16;
-    long ch = blockIdx.x;
-    if (ch < nchunks) {
-        fetch(ch);
-        stash(0);
-    }
-    __syncthreads();
-    for (int it = 0; ch < nchunks; ch += gridDim.x, it++) {
+    long ch = slot;
+    if (ch < nchunks) load(0, ch);
+    tc::cp_async_commit();
+    for (int it = 0; ch < nchunks; ch += nslots, it++) {
         const int cur = it & 1;
-        const long nx = ch + gridDim.x;
-        if (nx < nchunks) fetch(nx);
+        if (ch + nslots < nchunks) load(cur ^ 1, ch + nslots);
+        tc::cp_async_commit();
+        tc::cp_async_wait<1>();                  // chunk ch has landed (own copies)
+        __syncthreads();
         const float(*Ab)[GT + 4] = As[cur];
         const float(*Bb)[GT + 4] = diag ? As[cur] : Bs[cur];
         float acc[4][4];
@@ -452,11 +472,11 @@ __global__ void __launch_bounds__(256, 3) gram_simt_kernel(GramArgs g, const flo
                 lo[i][j] += (a - (sum - bp)) + (b - bp);
                 hi[i][j] = sum;
             }
-        if (nx < nchunks) stash(cur ^ 1);
-        __syncthreads();
+        __syncthreads();                         // buffer cur is free for the load two chunks on
     }
-    float* out = g.part + (long)blockIdx.x * g.NP * g.NP;
-    float* outl = g.part + (long)(blockIdx.x + gridDim.x) * g.NP * g.NP;
+    tc::cp_async_wait<0>();
+    float* out = g.part + (long)slot * g.NP * g.NP;
+    float* outl = g.part + (long)(slot + nslots) * g.NP * g.NP;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int row = ti * GT + ty * 4 + i;
@@ -1480,7 +1500,8 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         long rwb = (rows_alloc + 255) / 256;
         if (rwb > (long)ctx->num_sms * 8) rwb = (long)ctx->num_sms * 8;
         row_weights_kernel<<<(unsigned)rwb, 256, 0, st>>>(g, ctx->rowmeta); argus_count_launch(1);
-        gram_simt_kernel<<<dim3(nslots, npair), 256, 0, st>>>(g, ctx->rowmeta, ntile); argus_count_launch(1);
+        design_kernel<<<ctx->num_sms * 4, 256, sizeof(int) * 2 * g.NP, st>>>(g, ctx->rowmeta, ctx->design); argus_count_launch(1);
+        gram_cp_kernel<<<dim3(npair, nslots), 256, 0, st>>>(g, ctx->design, ntile); argus_count_launch(1);
     } else {
         const int RB = (g.NP + 127) / 128;
         const int NR = RB * 128;

@@ -140,6 +140,12 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
                  : "memory");
 }
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned);
+// src_bytes 0 or 16 (0: zero-fill, nothing read).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
