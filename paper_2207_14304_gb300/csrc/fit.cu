@@ -321,6 +321,96 @@ __device__ __forceinline__ float design_value(const GramArgs& g, int n, int k, c
     return m[0] * m[10 + (-1 - n)];
 }
 
+// K3, register-blocked form for 21x21 stamps: three stamps side by side per
+// CTA (63 columns over two lane-halves), warp g owns basis functions
+// 4g .. 4g+3 (warp-uniform basis loads are broadcasts), a thread owns one
+// column and all 21 rows of its four functions (84 accumulators).  Per tap
+// column the 41 window values of the thread's column are loaded once, then
+// KS taps x 21 rows x 4 functions of FMAs: ~93 % of the issued instructions.
+constexpr int SC_ST = 21, SC_NS = 3;
+
+template <int KS>
+__global__ void __launch_bounds__(416, 1) stamp_conv_fast_kernel(BasisDev b, const float* ref, long pitch, int w,
+                                                                 int h, const int* centers, const int* n_stamps,
+                                                                 const float* imgf, float* X) {
+    constexpr int R = KS / 2, WW = SC_ST + 2 * R, SS = SC_ST * SC_ST, KK = KS * KS;
+    extern __shared__ __align__(16) float scs[];
+    float* Rw = scs;                               // [SC_NS][WW][WW]
+    float* Bs = Rw + SC_NS * WW * WW;              // [nb][KK]
+    __shared__ int valid_s[SC_NS];
+    const int nb = b.nb;
+    const int ns = *n_stamps;
+    const int s0 = blockIdx.x * SC_NS;
+    if (s0 >= ns) return;
+    if (threadIdx.x < SC_NS) {
+        const int s = s0 + threadIdx.x, hs = SC_ST / 2;
+        int v = 0;
+        if (s < ns) {
+            const int xs = centers[2 * s], ys = centers[2 * s + 1];
+            v = xs - hs - R >= 0 && xs + hs + R <= w - 1 && ys - hs - R >= 0 && ys + hs + R <= h - 1;
+        }
+        valid_s[threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < SC_NS * WW * WW; e += blockDim.x) {
+        const int t = e / (WW * WW), rem = e - t * WW * WW;
+        const int wj = rem / WW, wi = rem - wj * WW;
+        float v = 0.0f;
+        if (valid_s[t]) {
+            const int s = s0 + t;
+            const int wx0 = centers[2 * s] - SC_ST / 2 - R, wy0 = centers[2 * s + 1] - SC_ST / 2 - R;
+            v = __ldg(ref + (long)(wy0 + wj) * pitch + wx0 + wi);
+        }
+        Rw[e] = v;
+    }
+    for (int e = threadIdx.x; e < nb * KK; e += blockDim.x) Bs[e] = __ldg(imgf + e);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp;                           // function group
+    if (4 * g >= nb) return;
+    for (int half = 0; half < 2; half++) {
+        const int c = half * 32 + lane;           // column of the 63-wide strip
+        const bool live = c < SC_NS * SC_ST;
+        const int t = live ? c / SC_ST : 0, i = live ? c - t * SC_ST : 0;
+        const float* rw = Rw + t * WW * WW;
+        float acc[SC_ST][4];
+#pragma unroll
+        for (int j = 0; j < SC_ST; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
+        const float* bf[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) bf[q] = Bs + min(4 * g + q, nb - 1) * KK;
+        // tap (iu, iv): R(x - iu + R, y - iv + R) = Rw[j + 2R - iv][i + 2R - iu]
+#pragma unroll 1
+        for (int iu = 0; iu < KS; iu++) {
+            float win[WW];
+#pragma unroll
+            for (int m = 0; m < WW; m++) win[m] = rw[m * WW + i + 2 * R - iu];
+#pragma unroll
+            for (int iv = 0; iv < KS; iv++) {
+                float bv[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) bv[q] = bf[q][iv * KS + iu];
+#pragma unroll
+                for (int j = 0; j < SC_ST; j++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) acc[j][q] = fmaf(bv[q], win[j + 2 * R - iv], acc[j][q]);
+            }
+        }
+        if (live && s0 + t < ns) {
+            float* Xs = X + (long)(s0 + t) * nb * SS;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int m = 4 * g + q;
+                if (m < nb)
+#pragma unroll
+                    for (int j = 0; j < SC_ST; j++) Xs[(long)m * SS + j * SC_ST + i] = valid_s[t] ? acc[j][q] : 0.0f;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Per-row design weights, computed once per fit for every design row:
 // [0, 6) sqrt(w) p_k, [6, 12) sqrt(w) pb_k, [12] sqrt(w) I, the rest 0; all 0
@@ -1467,6 +1557,21 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     if (rc) return rc;
 
     const int ss = stamp * stamp, WW = stamp + 2 * d.r, kk = d.ks * d.ks;
+    if (stamp == SC_ST && (d.ks == 21 || d.ks == 11) && d.nb <= 52) {
+        // 13 warps x 4 functions cover up to 52 basis functions
+        const size_t fsm = sizeof(float) * ((size_t)SC_NS * WW * WW + (size_t)d.nb * kk);
+        const int nblk = (max_stamps + SC_NS - 1) / SC_NS;
+        if (d.ks == 21) {
+            cudaFuncSetAttribute(stamp_conv_fast_kernel<21>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            stamp_conv_fast_kernel<21><<<nblk, 416, fsm, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers,
+                                                               n_stamps, ctx->basis_imgf, ctx->X); argus_count_launch(1);
+        } else {
+            cudaFuncSetAttribute(stamp_conv_fast_kernel<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            stamp_conv_fast_kernel<11><<<nblk, 416, fsm, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers,
+                                                               n_stamps, ctx->basis_imgf, ctx->X); argus_count_launch(1);
+        }
+        if ((rc = argus_launch_status())) return rc;
+    } else {
     int group = (int)((200 * 1024 / sizeof(float) - (size_t)WW * WW) / kk);
     if (group > d.nb) group = d.nb;
     if (group < 4) return ARGUS_ERR_UNSUPPORTED;
@@ -1475,6 +1580,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     stamp_conv_kernel<<<max_stamps, 256, conv_smem, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers, n_stamps,
                                                           stamp, ctx->basis_imgf, group, ctx->X); argus_count_launch(1);
     if ((rc = argus_launch_status())) return rc;
+    }
 
     GramArgs g;
     g.X = ctx->X; g.sci = sci; g.var = sci_var; g.flags = flags; g.centers = centers; g.n_stamps = n_stamps;
