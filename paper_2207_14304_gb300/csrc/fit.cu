@@ -313,13 +313,6 @@ __device__ __forceinline__ void col_code(const GramArgs& g, int j, int& n, int& 
     n = -200; k = 0;
 }
 
-__device__ __forceinline__ float design_value(const GramArgs& g, int n, int k, const float* m, float xv) {
-    // xv = sqrt(w) * X_n at this row (only used for n >= 0)
-    if (n >= 0) return n == 0 ? xv : xv * m[4 + k];
-    if (n == -100) return m[1];
-    if (n == -200) return 0.0f;
-    return m[0] * m[10 + (-1 - n)];
-}
 
 // K3, register-blocked form for 21x21 stamps: three stamps side by side per
 // CTA (63 columns over two lane-halves), warp g owns basis functions
@@ -603,7 +596,7 @@ __device__ __forceinline__ uint32_t to_tf32(float a) {
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
+__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, const float* C, int NR) {
     constexpr int ESZ = FMT == 1 ? 2 : 4;          // bytes per element
     constexpr int E = 16 / ESZ;                    // elements per 16-byte core-matrix row
     constexpr int KQ = TC_KC / E;                  // core matrices along K per stage
@@ -613,11 +606,7 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t stage_bytes = (uint32_t)NR * TC_KC * ESZ;
     uint8_t* stage0 = smem_raw;
-    float* meta = reinterpret_cast<float*>(smem_raw + 2 * stage_bytes);            // [32][16]
-    float* Xsm = meta + TC_KC * META;                                               // [nb][32]
-    int* cn = reinterpret_cast<int*>(Xsm + ARGUS_MAX_NB * TC_KC);                   // [NR]
-    int* ck = cn + NR;                                                              // [NR]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(ck + NR + ((NR & 1) ? 1 : 0));     // [2]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * stage_bytes);       // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -627,12 +616,6 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
     uint32_t ncols = 32;
     while ((int)ncols < NPt) ncols <<= 1;
 
-    for (int j = tid; j < NR; j += blockDim.x) {
-        int n, k;
-        col_code(g, j, n, k);
-        cn[j] = n;
-        ck[j] = k;
-    }
     if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
     if (tid == 0) {
         tc::mbar_init(&mbar[0], 1);
@@ -655,19 +638,6 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
         uint8_t* sb = stage0 + st * stage_bytes;
         const long rho0 = ch * TC_KC;
         __syncthreads();
-        if (tid < TC_KC) row_meta(g, rho0 + tid, nrows, meta + tid * META);
-        __syncthreads();
-        for (int e = tid; e < g.nb * TC_KC; e += blockDim.x) {
-            const int n = e / TC_KC, k = e - n * TC_KC;
-            const long rho = rho0 + k;
-            const float sqw = meta[k * META];
-            float xv = 0.0f;
-            if (sqw != 0.0f) {
-                const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
-                xv = sqw * __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix);
-            }
-            Xsm[n * TC_KC + k] = xv;
-        }
         // the MMAs that last read this stage must be complete before it is rewritten
         if (it >= 2) {
             if (!tc::mbar_wait_bounded(&mbar[st], ((it >> 1) - 1) & 1, TC_WAIT_LIMIT)) *abort_flag = 1;
@@ -676,12 +646,11 @@ __global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, int NR) {
         if (*abort_flag) break;
         for (int e = tid; e < NR * KQ; e += blockDim.x) {
             const int kq = e / NR, i = e - kq * NR;
-            const int n = cn[i], kk = ck[i];
             float v[E];
 #pragma unroll
-            for (int t = 0; t < E; t++) {
-                const int k = kq * E + t;
-                v[t] = design_value(g, n, kk, meta + k * META, n >= 0 ? Xsm[n * TC_KC + k] : 0.0f);
+            for (int t = 0; t < E; t++) {   // rows of the weighted design matrix (zero past the rows)
+                const long rho = rho0 + kq * E + t;
+                v[t] = i < NPt ? __ldg(C + rho * NPt + i) : 0.0f;
             }
             uint4 pk;
             if constexpr (FMT == 1) {
@@ -1592,6 +1561,13 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
 
     const long max_rows = (long)max_stamps * ss;
     int part_slots;
+    // per-row weights and the weighted design matrix, for every precision
+    {
+        long rwb = (max_rows + 255) / 256;
+        if (rwb > (long)ctx->num_sms * 8) rwb = (long)ctx->num_sms * 8;
+        row_weights_kernel<<<(unsigned)rwb, 256, 0, st>>>(g, ctx->rowmeta); argus_count_launch(1);
+        design_kernel<<<ctx->num_sms * 4, 256, sizeof(int) * 2 * g.NP, st>>>(g, ctx->rowmeta, ctx->design); argus_count_launch(1);
+    }
     if (precision == ARGUS_PREC_FP32) {
         const int ntile = (g.NP + GT - 1) / GT;
         const int npair = ntile * (ntile + 1) / 2;
@@ -1602,11 +1578,6 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         if (nslots > nch) nslots = (int)nch;
         g.nslots = nslots;
         part_slots = 2 * nslots;   // hi and lo halves of the double-float partials
-        const long rows_alloc = (long)max_stamps * ss;
-        long rwb = (rows_alloc + 255) / 256;
-        if (rwb > (long)ctx->num_sms * 8) rwb = (long)ctx->num_sms * 8;
-        row_weights_kernel<<<(unsigned)rwb, 256, 0, st>>>(g, ctx->rowmeta); argus_count_launch(1);
-        design_kernel<<<ctx->num_sms * 4, 256, sizeof(int) * 2 * g.NP, st>>>(g, ctx->rowmeta, ctx->design); argus_count_launch(1);
         gram_cp_kernel<<<dim3(npair, nslots), 256, 0, st>>>(g, ctx->design, ntile); argus_count_launch(1);
     } else {
         const int RB = (g.NP + 127) / 128;
@@ -1619,16 +1590,15 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         g.nslots = nslots;
         part_slots = nslots;
         const int esz = precision == ARGUS_PREC_BF16 ? 2 : 4;
-        size_t smem = 2 * (size_t)NR * TC_KC * esz + sizeof(float) * (TC_KC * META + ARGUS_MAX_NB * TC_KC) +
-                      sizeof(int) * (2 * NR + 2) + 64;
+        size_t smem = 2 * (size_t)NR * TC_KC * esz + 64;
         if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: each holds up to 512 TMEM columns
         if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
         if (precision == ARGUS_PREC_BF16) {
             cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, NR); argus_count_launch(1);
+            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, ctx->design, NR); argus_count_launch(1);
         } else {
             cudaFuncSetAttribute(gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, NR); argus_count_launch(1);
+            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, ctx->design, NR); argus_count_launch(1);
         }
     }
     if ((rc = argus_launch_status())) return rc;
