@@ -1264,130 +1264,239 @@ __global__ void select_ring_kernel(const float* R, const uint8_t* flags, const u
     }
 }
 
-// Tiled form for the context path (isolation radius <= 32).  Per 64 x 32
-// tile: R over the tile plus a halo of iso + 1 goes to shared memory; the
-// strict local maxima of the tile plus iso become a masked copy (R there,
-// -inf elsewhere).  The brightest other local maximum within iso of a
-// candidate is the maximum of (a) the row maxima over [x - iso, x + iso] of
-// every window row but the candidate's own and (b) its own row without the
-// candidate; the row maxima are one separable pass (two outputs per thread,
-// sharing the common taps), (a) and (b) are taken for the candidates only.
-// Isolation is then one comparison with iso_frac * c.  Survivors get a
-// warp-wide scan of their flag window and the cell atomicMax.  The decisions
-// are those of the per-pixel rule above.
-constexpr int SEL_TX = 64, SEL_TY = 32, SEL_MAX_ISO = 32;
+// Tiled form for the context path (isolation radius <= 32), same decisions as
+// the per-pixel rule above.  One CTA per 128 x 64 tile:
+//  1. R over the tile plus a halo of iso + 1 is copied to shared memory with
+//     16-byte cp.async (rows start on a 4-float boundary; outside the frame 0).
+//  2. Strict local maxima over the tile plus a QR-pixel halo (QR = min(3, iso))
+//     become a masked copy mv (R there, -inf elsewhere), four rows per thread
+//     from separable 3-wide maxima; NaN neighbours propagate through max.NaN,
+//     so a pixel next to a NaN is never a maximum.  Candidates (maxima of the
+//     tile with their stamp window in the frame, below max_peak) are listed in
+//     the same pass; a tile holds at most one strict maximum per 2 x 2 block.
+//  3. Each candidate is tested against the other maxima within QR (the
+//     (2 QR + 1)^2 - 1 taps of mv): in a star field most fail here.
+//  4. One warp per remaining candidate scans the rest of the isolation window
+//     in R, testing the local-maximum rule only where R exceeds iso_frac * c,
+//     then the flag window (32-bit loads), then the cell atomicMax.
+constexpr int SEL_TX = 128, SEL_TY = 64, SEL_QR = 3, SEL_MAX_ISO = 32, SEL_THREADS = 512;
+constexpr int SEL_LIST = SEL_TX * SEL_TY / 4;
 
-__host__ __device__ inline size_t select_tile_smem(int iso) {
-    const size_t rw = SEL_TX + 2 * iso + 2, rh = SEL_TY + 2 * iso + 2;
-    const size_t lw = SEL_TX + 2 * iso, lh = SEL_TY + 2 * iso;
-    const size_t a = rw * rh * sizeof(float), b = lh * SEL_TX * sizeof(float);
-    return (a > b ? a : b) + lw * lh * sizeof(float) + 2 * SEL_TX * SEL_TY * sizeof(unsigned short) + 16;
+struct SelGeom {
+    int qr, ox, rw, rh, mw, mh;
+};
+
+__host__ __device__ inline SelGeom sel_geom(int iso) {
+    SelGeom g;
+    g.qr = iso < SEL_QR ? iso : SEL_QR;
+    g.ox = (4 - ((iso + 1) & 3)) & 3;                     // r column 0 is frame x0 - iso - 1 - ox
+    g.rw = (SEL_TX + 2 * iso + 2 + g.ox + 3) & ~3;
+    g.rh = SEL_TY + 2 * iso + 2;
+    g.mw = SEL_TX + 2 * g.qr;
+    g.mh = SEL_TY + 2 * g.qr;
+    return g;
 }
 
-__global__ void __launch_bounds__(256) select_tile_kernel(const float* R, const uint8_t* flags, long pitch, int w,
-                                                          int h, int gx, int gy, int m, float max_peak, int iso,
-                                                          float iso_frac, unsigned long long* cell_key) {
+// r is followed by SEL_RPAD spare rows: the last strip of step 2 reads past the
+// staged rows (into values it discards) without a bounds test.
+constexpr int SEL_RPAD = 4;
+
+__host__ __device__ inline size_t select_tile_smem(int iso) {
+    const SelGeom g = sel_geom(iso);
+    return sizeof(float) * ((size_t)g.rw * (g.rh + SEL_RPAD) + (size_t)g.mw * g.mh) +
+           2 * SEL_LIST * sizeof(unsigned short);
+}
+
+// Taps of the Chebyshev rings of radius 1 .. SEL_MAX_ISO around a pixel, ring by
+// ring: ring rho holds entries (2 rho - 1)^2 - 1 .. (2 rho + 1)^2 - 2 as (dx, dy).
+struct SelRing {
+    alignas(16) signed char d[2 * ((2 * SEL_MAX_ISO + 1) * (2 * SEL_MAX_ISO + 1) - 1)];
+};
+constexpr SelRing make_sel_ring() {
+    SelRing t{};
+    int k = 0;
+    for (int rho = 1; rho <= SEL_MAX_ISO; rho++)
+        for (int s = 0; s < 8 * rho; s++) {
+            const int side = 2 * rho;
+            int dx = -rho, dy = rho - (s - 3 * side);
+            if (s < side) { dx = -rho + s; dy = -rho; }
+            else if (s < 2 * side) { dx = rho; dy = -rho + (s - side); }
+            else if (s < 3 * side) { dx = rho - (s - 2 * side); dy = rho; }
+            t.d[2 * k] = (signed char)dx;
+            t.d[2 * k + 1] = (signed char)dy;
+            k++;
+        }
+    return t;
+}
+__device__ const SelRing g_sel_ring = make_sel_ring();
+
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+template <int QR>
+__global__ void __launch_bounds__(SEL_THREADS, 2) select_tile_kernel(const float* R, const uint8_t* flags, long pitch,
+                                                                    int w, int h, int gx, int gy, int m,
+                                                                    float max_peak, int iso, float iso_frac,
+                                                                    unsigned long long* cell_key) {
+    constexpr int MW = SEL_TX + 2 * QR, MH = SEL_TY + 2 * QR;
     extern __shared__ float4 sel_smem[];
-    const int RW = SEL_TX + 2 * iso + 2, RH = SEL_TY + 2 * iso + 2;   // both even
-    const int LW = SEL_TX + 2 * iso, LH = SEL_TY + 2 * iso;
-    const size_t ua = (size_t)RW * RH * sizeof(float), ub = (size_t)LH * SEL_TX * sizeof(float);
-    float* r = reinterpret_cast<float*>(sel_smem);                  // [RH][RW], then reused:
-    float* rowm = reinterpret_cast<float*>(sel_smem);               // [LH][SEL_TX] row maxima
-    float* mv = reinterpret_cast<float*>(reinterpret_cast<char*>(sel_smem) + (ua > ub ? ua : ub));   // [LH][LW]
-    unsigned short* cand = reinterpret_cast<unsigned short*>(mv + (size_t)LW * LH);
-    unsigned short* surv = cand + SEL_TX * SEL_TY;
+    const SelGeom g = sel_geom(iso);
+    float* r = reinterpret_cast<float*>(sel_smem);              // [rh][rw]
+    float* mv = r + g.rw * (g.rh + SEL_RPAD);                    // [MH][MW]
+    unsigned short* cand = reinterpret_cast<unsigned short*>(mv + MW * MH);
+    unsigned short* surv = cand + SEL_LIST;
     __shared__ int n_cand, n_surv;
     const int ntx = (w + SEL_TX - 1) / SEL_TX;
     const int x0 = (int)(blockIdx.x % ntx) * SEL_TX, y0 = (int)(blockIdx.x / ntx) * SEL_TY;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = SEL_THREADS / 32;
+    const int XS = x0 - iso - 1 - g.ox, YS = y0 - iso - 1;      // frame position of r[0][0]
     if (tid == 0) { n_cand = 0; n_surv = 0; }
-    // 1. R over the tile + (iso + 1)
-    for (int jy = wid; jy < RH; jy += nw) {
-        const int Y = y0 - iso - 1 + jy;
-        const bool yin = Y >= 0 && Y < h;
-        const float* src = R + (long)(yin ? Y : 0) * pitch;
-        for (int jx = lane; jx < RW; jx += 32) {
-            const int X = x0 - iso - 1 + jx;
-            r[jy * RW + jx] = (yin && X >= 0 && X < w) ? __ldg(src + X) : 0.0f;
+    // 1. stage R in 16-byte chunks; XS is a multiple of 4, so a chunk is inside or
+    //    outside the frame but for the one that holds column w (partly zero-filled)
+    {
+        const int cpr = g.rw >> 2, n = cpr * g.rh;
+        const int sy = SEL_THREADS / cpr, sc = SEL_THREADS - sy * cpr;
+        int jy = tid / cpr, jc = tid - jy * cpr;
+        for (int e = tid; e < n; e += SEL_THREADS) {
+            const int Y = YS + jy, X = XS + 4 * jc;
+            int nb = 0;
+            if (Y >= 0 && Y < h && X >= 0 && X < w) nb = 4 * min(4, w - X);
+            tc::cp_async16(r + jy * g.rw + 4 * jc, nb ? R + (long)Y * pitch + X : R, nb);
+            jc += sc;
+            jy += sy;
+            if (jc >= cpr) { jc -= cpr; jy++; }
+        }
+        tc::cp_async_commit();
+        tc::cp_async_wait<0>();
+    }
+    __syncthreads();
+    // 2. masked strict local maxima over the tile + QR, four rows per item, and the
+    //    candidate list
+    const float NEG = __int_as_float(0xff800000), INF = __int_as_float(0x7f800000);
+    {
+        const int cx = iso + 1 + g.ox - QR, cy = iso + 1 - QR;     // r position of mv[0][0]
+        constexpr int NSTRIP = (MH + 3) / 4, N = MW * NSTRIP;
+        constexpr int SS = SEL_THREADS / MW, SX = SEL_THREADS - SS * MW;
+        int js = tid / MW, jx = tid - js * MW;
+        for (int e = tid; e < N; e += SEL_THREADS) {
+            const int jy0 = 4 * js;
+            const float* q = r + (cy + jy0 - 1) * g.rw + (cx + jx);
+            float h3[6], lft[6], rgt[6], ctr[6];
+#pragma unroll
+            for (int t = 0; t < 6; t++) {
+                const float* qt = q + t * g.rw;
+                lft[t] = qt[-1];
+                ctr[t] = qt[0];
+                rgt[t] = qt[1];
+                h3[t] = fmax_nan(fmax_nan(lft[t], ctr[t]), rgt[t]);
+            }
+            const int X = x0 - QR + jx, x = jx - QR;
+            const bool xin = X >= 1 && X <= w - 2;
+            const bool xc = x >= 0 && x < SEL_TX && X - m >= 0 && X + m <= w - 1;
+            // candidates of this strip: at most two (vertical neighbours are never both maxima)
+            int nc = 0, e0 = 0, e1 = 0;
+#pragma unroll
+            for (int t = 1; t <= 4; t++) {
+                const int jy = jy0 + t - 1, y = jy - QR;
+                const int Y = y0 + y;
+                const float c = ctr[t];
+                const float nb = fmax_nan(fmax_nan(h3[t - 1], h3[t + 1]), fmax_nan(lft[t], rgt[t]));
+                const bool l = jy < MH && xin && Y >= 1 && Y <= h - 2 && c > nb && c < INF;
+                if (jy < MH) mv[jy * MW + jx] = l ? c : NEG;
+                if (l && xc && y >= 0 && y < SEL_TY && Y - m >= 0 && Y + m <= h - 1 && c < max_peak) {
+                    const int ev = y * SEL_TX + x;
+                    if (nc == 0) e0 = ev; else e1 = ev;
+                    nc++;
+                }
+            }
+            // warp-aggregated append: nc = b0 + 2 b1 per lane
+            const unsigned act = __activemask();
+            const unsigned b0 = __ballot_sync(act, nc & 1), b1 = __ballot_sync(act, nc & 2);
+            if (b0 | b1) {
+                const int leader = __ffs(act) - 1;
+                const unsigned lt = (1u << lane) - 1u;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&n_cand, __popc(b0) + 2 * __popc(b1));
+                base = __shfl_sync(act, base, leader) + __popc(b0 & lt) + 2 * __popc(b1 & lt);
+                if (nc > 0) cand[base] = (unsigned short)e0;
+                if (nc > 1) cand[base + 1] = (unsigned short)e1;
+            }
+            jx += SX;
+            js += SS;
+            if (jx >= MW) { jx -= MW; js++; }
         }
     }
     __syncthreads();
-    // 2. masked local maxima over the tile + iso
-    const float NEG = __int_as_float(0xff800000);
-    for (int jy = wid; jy < LH; jy += nw) {
-        const int Y = y0 - iso + jy;
-        const bool yin = Y >= 1 && Y <= h - 2;
-        for (int jx = lane; jx < LW; jx += 32) {
-            const int X = x0 - iso + jx;
-            const float* q = r + (jy + 1) * RW + (jx + 1);
-            const float c = q[0];
-            const float nb = fmaxf(fmaxf(fmaxf(q[-RW - 1], q[-RW]), fmaxf(q[-RW + 1], q[-1])),
-                                   fmaxf(fmaxf(q[1], q[RW - 1]), fmaxf(q[RW], q[RW + 1])));
-            // strict maximum: c above every neighbour (a NaN neighbour fails the test)
-            bool l = yin && X >= 1 && X <= w - 2 && isfinite(c) && c > nb;
-            l = l && !(isnan(q[-RW - 1]) || isnan(q[-RW]) || isnan(q[-RW + 1]) || isnan(q[-1]) || isnan(q[1]) ||
-                       isnan(q[RW - 1]) || isnan(q[RW]) || isnan(q[RW + 1]));
-            mv[jy * LW + jx] = l ? c : NEG;
-        }
-    }
-    __syncthreads();
-    // 3. row maxima over [x - iso, x + iso] for every row of the tile + iso, two
-    //    outputs (x, x + 1) per thread from float2 loads; r is dead
-    for (int e = tid; e < LH * (SEL_TX / 2); e += blockDim.x) {
-        const int jy = e >> 5, x = 2 * (e & 31);
-        const float2* q = reinterpret_cast<const float2*>(mv + jy * LW + x);   // taps x .. x + 2 iso + 1
-        const float2 first = q[0], last = q[iso];
-        float core = iso > 0 ? fmaxf(first.y, last.x) : NEG;     // taps x + 1 .. x + 2 iso
-        for (int k = 1; k < iso; k++) {
-            const float2 t = q[k];
-            core = fmaxf(core, fmaxf(t.x, t.y));
-        }
-        *reinterpret_cast<float2*>(rowm + jy * SEL_TX + x) = make_float2(fmaxf(core, first.x), fmaxf(core, last.y));
-    }
-    // 4. candidates: strict local maxima whose stamp window is inside the frame, below max_peak
-    for (int e0 = 0; e0 < SEL_TX * SEL_TY; e0 += blockDim.x) {
-        const int e = e0 + tid;
-        const int y = e / SEL_TX, x = e - y * SEL_TX;
-        const int X = x0 + x, Y = y0 + y;
-        const float c = mv[(y + iso) * LW + x + iso];
-        const bool ok = X - m >= 0 && X + m <= w - 1 && Y - m >= 0 && Y + m <= h - 1 && c > NEG && c < max_peak;
-        const unsigned bal = __ballot_sync(0xffffffffu, ok);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&n_cand, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok) cand[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)e;
-    }
-    __syncthreads();
-    // 5. isolation: the brightest other local maximum within iso
-    for (int i = tid; i < n_cand; i += blockDim.x) {
+    // 3. the other maxima within QR
+    for (int i = tid; i < n_cand; i += SEL_THREADS) {
         const int e = cand[i];
         const int y = e / SEL_TX, x = e - y * SEL_TX;
-        const float* own = mv + (y + iso) * LW + x;                // own row, taps x - iso .. x + iso
-        const float c = own[iso];
+        const float* q = mv + y * MW + x;                          // window corner (y - QR, x - QR)
+        const float c = q[QR * MW + QR];
         float other = NEG;
-        for (int d = 0; d < iso; d++) {
-            other = fmaxf(other, fmaxf(rowm[(y + d) * SEL_TX + x], rowm[(y + iso + 1 + d) * SEL_TX + x]));
-            other = fmaxf(other, fmaxf(own[d], own[iso + 1 + d]));
-        }
+#pragma unroll
+        for (int dy = 0; dy <= 2 * QR; dy++)
+#pragma unroll
+            for (int dx = 0; dx <= 2 * QR; dx++)
+                if (dy != QR || dx != QR) other = fmaxf(other, q[dy * MW + dx]);
         if (!(other > iso_frac * c)) surv[atomicAdd(&n_surv, 1)] = (unsigned short)e;
     }
     __syncthreads();
-    // 6. flag window, one warp per survivor
+    // 4. one warp per survivor: rest of the isolation window, flag window, cell key
+    const int side = 2 * iso + 1, fside = 2 * m + 1;
     for (int i = wid; i < n_surv; i += nw) {
         const int e = surv[i];
         const int y = e / SEL_TX, x = e - y * SEL_TX;
         const int X = x0 + x, Y = y0 + y;
-        // the (2m+1)^2 window as independent loads spread over the lanes
-        const int side = 2 * m + 1, nwin = side * side;
-        const uint8_t* base = flags + (long)(Y - m) * pitch + (X - m);
+        const float c = mv[(y + QR) * MW + x + QR];
+        const float thr = iso_frac * c;
+        bool bad = false;
+        if (iso > QR) {
+            // rings QR + 1 .. iso, 32 taps per step, nearest first: a noise peak meets
+            // a brighter maximum within a step or two
+            const float* qc = r + (y + iso + 1) * g.rw + (x + iso + 1 + g.ox);   // the candidate
+            const char2* ring = reinterpret_cast<const char2*>(g_sel_ring.d);
+            const int p1 = side * side - 1;
+            for (int pb = (2 * QR + 1) * (2 * QR + 1) - 1; pb < p1; pb += 32) {
+                const int p = pb + lane;
+                bool b = false;
+                if (p < p1) {
+                    const char2 d = __ldg(ring + p);
+                    const float* q = qc + d.y * g.rw + d.x;
+                    const float v = *q;
+                    const int XX = X + d.x, YY = Y + d.y;
+                    if (v > thr && v < INF && XX >= 1 && XX <= w - 2 && YY >= 1 && YY <= h - 2) {
+                        const float nb = fmax_nan(fmax_nan(fmax_nan(q[-g.rw - 1], q[-g.rw]), fmax_nan(q[-g.rw + 1], q[-1])),
+                                                  fmax_nan(fmax_nan(q[1], q[g.rw - 1]), fmax_nan(q[g.rw], q[g.rw + 1])));
+                        b = v > nb;
+                    }
+                }
+                if (__any_sync(0xffffffffu, b)) { bad = true; break; }
+            }
+        }
+        if (bad) continue;
+        // flag window rows Y - m .. Y + m, bytes X - m .. X + m, as aligned 32-bit words
+        // (rows are 16-byte aligned and the words end inside the row's pitch)
+        const int wa = (X - m) & ~3, nwr = (((X + m) & ~3) - wa) / 4 + 1;
+        const int sr = 32 / nwr, sc = 32 - sr * nwr;
+        int ry = lane / nwr, rc = lane - ry * nwr;
         unsigned f = 0;
-#pragma unroll 8
-        for (int q = lane; q < nwin; q += 32) {
-            const int qy = q / side;
-            f |= __ldg(base + (long)qy * pitch + (q - qy * side));
+#pragma unroll 4
+        for (int t = lane; t < nwr * fside; t += 32) {
+            const int xa = wa + 4 * rc;
+            unsigned v = __ldg(reinterpret_cast<const unsigned*>(flags + (long)(Y - m + ry) * pitch + xa));
+            const int lo = X - m - xa, hi = X + m - xa;                      // byte range inside this word
+            if (lo > 0) v &= 0xffffffffu << (8 * lo);
+            if (hi < 3) v &= 0xffffffffu >> (8 * (3 - hi));
+            f |= v;
+            rc += sc;
+            ry += sr;
+            if (rc >= nwr) { rc -= nwr; ry++; }
         }
         if (__any_sync(0xffffffffu, f != 0) || lane != 0) continue;
-        const float c = mv[(y + iso) * LW + x + iso];
         const int cx = (int)(((long)(X + 1) * gx - 1) / w), cy = (int)(((long)(Y + 1) * gy - 1) / h);
         const unsigned bits = __float_as_uint(c);
         const unsigned ord = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
@@ -1395,6 +1504,21 @@ __global__ void __launch_bounds__(256) select_tile_kernel(const float* R, const 
         const unsigned long long key = ((unsigned long long)ord << 32) | (unsigned long long)(0xffffffffu - rank);
         atomicMax(cell_key + cy * gx + cx, key);
     }
+}
+
+template <int QR>
+int launch_select_tile(const float* ref, const uint8_t* flags, const argus_shape& shape, int grid_x, int grid_y,
+                       int m, float max_peak, int iso, float iso_frac, unsigned long long* keys, cudaStream_t st) {
+    const size_t smem = select_tile_smem(iso);
+    if (cudaFuncSetAttribute(select_tile_kernel<QR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    const long tiles = (long)((shape.w + SEL_TX - 1) / SEL_TX) * ((shape.h + SEL_TY - 1) / SEL_TY);
+    select_tile_kernel<QR><<<(unsigned)tiles, SEL_THREADS, smem, st>>>(ref, flags, shape.pitch, shape.w, shape.h,
+                                                                       grid_x, grid_y, m, max_peak, iso, iso_frac,
+                                                                       keys);
+    argus_count_launch(1);
+    return ARGUS_OK;
 }
 
 __global__ void __launch_bounds__(1024) select_compact_kernel(const unsigned long long* cell_key, int ncell, int w,
@@ -1669,14 +1793,12 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
     long blocks = (np + 255) / 256;
     if (blocks > (long)ctx->num_sms * 16) blocks = (long)ctx->num_sms * 16;
     if (iso <= SEL_MAX_ISO) {
-        const size_t smem = select_tile_smem(iso);
-        if (cudaFuncSetAttribute(select_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return ARGUS_ERR_CUDA;
-        const long tiles = (long)((shape.w + SEL_TX - 1) / SEL_TX) * ((shape.h + SEL_TY - 1) / SEL_TY);
-        select_tile_kernel<<<(unsigned)tiles, 256, smem, st>>>(ref, flags, shape.pitch, shape.w, shape.h, grid_x,
-                                                               grid_y, stamp / 2 + khalf, max_peak, iso, iso_frac,
-                                                               ctx->cell_key); argus_count_launch(1);
+        const int m = stamp / 2 + khalf;
+        rc = iso == 0   ? launch_select_tile<0>(ref, flags, shape, grid_x, grid_y, m, max_peak, iso, iso_frac, ctx->cell_key, st)
+             : iso == 1 ? launch_select_tile<1>(ref, flags, shape, grid_x, grid_y, m, max_peak, iso, iso_frac, ctx->cell_key, st)
+             : iso == 2 ? launch_select_tile<2>(ref, flags, shape, grid_x, grid_y, m, max_peak, iso, iso_frac, ctx->cell_key, st)
+                        : launch_select_tile<3>(ref, flags, shape, grid_x, grid_y, m, max_peak, iso, iso_frac, ctx->cell_key, st);
+        if (rc) return rc;
     } else {
         uint8_t* lmax = reinterpret_cast<uint8_t*>(ctx->label);   // the label scratch, one byte per pixel
         const long rblocks = (np + 255) / 256;                      // one pixel per thread: latency-bound scans

@@ -141,7 +141,7 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc, int src_
                  : "memory");
 }
 // 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned);
-// src_bytes 0 or 16 (0: zero-fill, nothing read).
+// reads src_bytes (0..16) bytes and zero-fills the rest.
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
                  : "memory");

@@ -208,6 +208,9 @@ def _ref_field(w, h, seed, n=300):
     (257, 129, 5, 2, 10, 0.1, 3.0e4),      # ragged tiles in x and y
     (300, 260, 4, 3, 0, 0.1, 3.0e4),       # no isolation window
     (300, 260, 4, 3, 3, 0.5, 3.0e4),
+    (300, 260, 4, 3, 1, 0.1, 3.0e4),       # window inside the quick-test radius
+    (300, 260, 4, 3, 4, 0.1, 3.0e4),       # one ring past the quick-test radius
+    (700, 390, 8, 5, 10, 0.1, 3.0e4),      # several 128 x 64 tiles, ragged in both directions
     (300, 260, 6, 6, 32, 0.5, 3.0e4),      # widest window of the tiled kernel
     (300, 260, 4, 3, 40, 0.5, 3.0e4),      # wider: the per-pixel ring kernel
     (300, 260, 4, 3, 10, 0.1, 1.0e4),      # bright stars excluded by max_peak
@@ -251,7 +254,7 @@ def _select_both(ora, R, fl, gx, gy, iso=10, iso_frac=0.1, max_peak=3.0e4):
 
 
 def test_select_stamps_frame_smaller_than_a_tile(ora):
-    """80 x 50 frame, smaller than one 64 x 32 tile plus its halo in both directions."""
+    """80 x 50 frame, smaller than one 128 x 64 tile plus its halo in both directions."""
     w, h = 80, 50
     cat = synth.Catalog(torch.tensor([22.3, 55.6, 60.2], dtype=torch.float64),
                         torch.tensor([20.1, 30.7, 18.4], dtype=torch.float64),
@@ -259,6 +262,27 @@ def test_select_stamps_frame_smaller_than_a_tile(ora):
     R = synth.reference_image(synth.render(cat, w, h, 1.2, sky=300.0), 30, 1.7, 9)[0].numpy()
     co = _select_both(ora, R, np.zeros((h, w), np.uint8), 2, 1)
     assert [tuple(c) for c in co] == [(22, 20), (60, 18)]
+
+
+def test_select_stamps_nan_and_inf_pixels(ora):
+    """NaN and infinite reference pixels: never maxima, and a maximum next to one is no
+    strict maximum (NaN compares false), matching the per-pixel rule."""
+    w, h = 420, 300
+    R, _ = _ref_field(w, h, seed=77, n=400)
+    rng = np.random.default_rng(5)
+    bad = rng.random((h, w)) < 0.003
+    R[bad] = np.nan
+    R[rng.random((h, w)) < 0.0005] = np.inf
+    R[rng.random((h, w)) < 0.0005] = -np.inf
+    # NaN beside the brightest pixel of a few bright stars
+    ys, xs = np.unravel_index(np.argsort(np.nan_to_num(R, nan=0, posinf=0, neginf=0), axis=None)[-40:], R.shape)
+    for y, x in list(zip(ys, xs))[::4]:
+        if 1 <= x < w - 1:
+            R[y, x + 1] = np.nan
+    fl = (rng.random((h, w)) < 0.0005).astype(np.uint8)
+    for iso in (0, 3, 10):
+        co = _select_both(ora, R, fl, 6, 4, iso=iso)
+        assert len(co) > 0
 
 
 def test_select_stamps_ties_and_plateaus(ora):
