@@ -11,26 +11,32 @@
 // is one tcgen05 MMA of M = 128, N = 128 (KS * NK <= 128 columns used),
 // K = 32.  T holds every contribution of that source row to the output rows
 // rs - r .. rs + r: column (iv, k) belongs to output row rs + iv - r.  The
-// epilogue warps add T into a ring of KS pending output rows (one register
-// set per row) and finish a row once its last source row is in.  Operands are BF16
-// hi/lo pairs (v = hi + lo, each rounded to nearest) and every product is
-// hi*hi + hi*lo + lo*hi, accumulated in FP32 in TMEM: the dropped lo*lo
+// epilogue warps add T into a ring of pending output rows (one register set
+// per row) and finish a row once its last source row is in.  Operands are
+// BF16 hi/lo pairs (v = hi + lo, each rounded to nearest) and every product
+// is hi*hi + hi*lo + lo*hi, accumulated in FP32 in TMEM: the dropped lo*lo
 // term is below 2^-16 relative, well inside FP32-level agreement.
+//
+// A is stored once per source row as its 19 distinct core matrices: in the
+// canonical no-swizzle K-major layout the core matrix of row group i and K
+// group j holds A[8i + a][8j + b] = R(x0 - r + 8(i + j) + a + b, rs), a
+// function of i + j, so the descriptor's row-group stride equals its K-group
+// stride (both 128 bytes) and group (i, j) reads the matrix stored at i + j.
 //
 // CTA: 128 columns x a band of TCY output rows, streaming the band's
 // TCY + 2r source rows.  Warps 0-3: epilogue, one output column per thread
 // and TMEM lane, holding the ring of pending rows in registers (one sum per
-// power of y: the x powers are folded in as each T column is added; the ring
-// shifts by register moves, so the row loop has a single body).  Warps 4-10:
-// producers (source rows arrive by cp.async DP rows ahead; each value is
-// split into BF16 hi/lo once, one row ahead of its use, and the Hankel rows
-// are copied out of the split row with 32-bit loads and byte permutes into
-// the canonical no-swizzle K-major layout, NSTAGE stages; one named barrier
-// per row).  Warp 11: one thread issues the MMAs.  TMEM holds four
-// 128-column accumulators, so the MMAs run up to three rows ahead of the
-// epilogue, which loads its science and flag values four rows ahead into a
-// register queue.  Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT
-// and all roles stop.
+// power of y: the x powers are folded in as each T column is added).  The
+// row loop is unrolled U = 3 times with a ring of KS + U - 1 entries that
+// shifts by U, so the ring moves once per U rows.  Science values and flag
+// words reach shared memory by cp.async LQ rows ahead, each thread fetching
+// its own column.  Warps 4-9: producers (source rows arrive by 16-byte
+// cp.async DP rows ahead; each value is split into BF16 hi/lo once, one row
+// ahead of its use; 152 threads then write the 19 core matrices with 32-bit
+// loads and byte permutes, NSTAGE stages; one named barrier per row).  Warp
+// 10: one thread issues the MMAs.  TMEM holds four 128-column accumulators, so
+// the MMAs run up to three rows ahead of the epilogue.  Every wait is
+// bounded; a timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_bf16.h>
 
 #include "subtract_tile.cuh"
@@ -39,28 +45,36 @@
 namespace {
 using namespace argus_sub;
 
-constexpr int TCX = 128;                  // output columns per CTA (MMA M)
-constexpr int TCY = 128;                  // output rows per CTA band
-constexpr int TKC = 32;                   // MMA K: taps u', padded
-constexpr int NSTAGE = 4;                 // Hankel stages
-constexpr int SRCW = TCX + TKC;           // source columns per row
-constexpr int NSRC = 8;                   // fp32 source-row ring
-constexpr int DP = 6;                     // source rows in flight ahead of the one being tiled
-constexpr int NPROD = 224;                // producer threads (warps 4-10)
-constexpr int TC_THREADS = 384;           // warps 0-3 epilogue, 4-10 producers, 11 MMA issuer
-constexpr uint32_t LBO = 128, SBO = 512;  // K-major canonical layout, 32 K per row
-constexpr uint32_t TILE_BYTES = 128 * TKC * 2;
+constexpr int TCX = 128;                     // output columns per CTA (MMA M)
+constexpr int TCY = 128;                     // output rows per CTA band
+constexpr int TKC = 32;                      // MMA K: taps u', padded
+constexpr int NCM = TCX / 8 + TKC / 8 - 1;   // distinct core matrices of one Hankel tile
+constexpr uint32_t A_BYTES = NCM * 128;      // one operand (hi or lo) of one source row
+constexpr uint32_t B_BYTES = 128 * TKC * 2;
+constexpr int NSTAGE = 8;                    // Hankel stages
+constexpr int SRCW = TCX + TKC;              // source values per row
+constexpr int SRCC = SRCW / 4 + 1;           // 16-byte chunks staged per row (one spare for the offset)
+constexpr int NSRC = 8;                      // fp32 source-row ring
+constexpr int DP = 6;                        // source rows in flight ahead of the one being tiled
+constexpr int NBUILD = NCM * 8;              // one builder thread per core-matrix row
+constexpr int NPROD = (NBUILD + 31) / 32 * 32;   // producer threads (warps 4-8)
+constexpr int MMA_WARP = 4 + NPROD / 32;     // warps 9 and 10 issue the MMAs of even and odd rows
+constexpr int TC_THREADS = (MMA_WARP + 2) * 32;   // warps 0-3 epilogue, 4-8 producers, 9-10 MMA issuers
+constexpr uint32_t LBO = 128, SBO_A = 128, SBO_B = 512;
 constexpr long long WAIT_LIMIT = 2000000000LL;   // ~1 s of SM clock
-constexpr int NTB = 4;                    // TMEM accumulator buffers of 128 columns
+constexpr int NTB = 4;                       // TMEM accumulator buffers of 128 columns
+constexpr int LQ = 4, NQ = 8;                // science/flag rows fetched LQ ahead into an NQ-slot ring
+constexpr int U = 3;                         // epilogue rows per ring shift
+static_assert(MMA_WARP == 9 && TC_THREADS == 352 && SRCC <= NPROD, "warp roles");
 
 struct TcShared {
-    uint8_t bhi[TILE_BYTES];
-    uint8_t blo[TILE_BYTES];
-    uint8_t ahi[NSTAGE][TILE_BYTES];
-    uint8_t alo[NSTAGE][TILE_BYTES];
-    float srcf[NSRC][SRCW];
-    alignas(16) uint32_t srch[2][SRCW / 2 + 4];   // BF16 hi of a source row, two per word (double-buffered)
-    alignas(16) uint32_t srcl[2][SRCW / 2 + 4];   // BF16 lo
+    uint8_t bhi[B_BYTES];
+    uint8_t blo[B_BYTES];
+    uint8_t ahi[NSTAGE][A_BYTES];
+    uint8_t alo[NSTAGE][A_BYTES];
+    alignas(16) float srcf[NSRC][SRCC * 4];
+    alignas(16) float qI[NQ][TCX];                // science values of output rows, by row & (NQ - 1)
+    alignas(16) uint32_t qF[NQ][TCX];             // the 32-bit word holding each output pixel's flag byte
     uint64_t filled[NSTAGE];
     uint64_t empty[NSTAGE], tfull[NTB], tempty[NTB];
     uint32_t tmem;
@@ -69,7 +83,7 @@ struct TcShared {
 };
 
 __device__ __forceinline__ uint32_t canon_off(int row, int kk) {
-    return (uint32_t)(row >> 3) * SBO + (uint32_t)(kk >> 3) * LBO + (uint32_t)(row & 7) * 16 + (uint32_t)(kk & 7) * 2;
+    return (uint32_t)(row >> 3) * SBO_B + (uint32_t)(kk >> 3) * LBO + (uint32_t)(row & 7) * 16 + (uint32_t)(kk & 7) * 2;
 }
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -77,7 +91,23 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// Two floats rounded to BF16 and packed, v0 in the low half.
+__device__ __forceinline__ uint32_t bf16x2_rn(float v0, float v1) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
+    return d;
+}
+
+// hi/lo split of a pair (hi = rn(v), lo = rn(v - hi)), each packed two per word.
+__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+    hi = bf16x2_rn(v0, v1);
+    lo = bf16x2_rn(v0 - __uint_as_float(hi << 16), v1 - __uint_as_float(hi & 0xffff0000u));
+}
+
+// One try first (the common case: the phase is already complete), then a
+// bounded wait that also gives up once another role has aborted.
 __device__ __forceinline__ bool wait_or_abort(TcShared& S, uint64_t* bar, uint32_t parity, int* status) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
     if (S.abort) return false;
     if (!tc::mbar_wait_bounded(bar, parity, WAIT_LIMIT)) {
         S.abort = 1;
@@ -87,20 +117,13 @@ __device__ __forceinline__ bool wait_or_abort(TcShared& S, uint64_t* bar, uint32
     return true;
 }
 
-// Background polynomial sum_k c_k p_k (p_k = x^i y^j, i + j <= deg, ordered i then
-// j: 1, y, y^2, x, x y, x^2), written out so nothing is indexed at run time.
-__device__ __forceinline__ float background(const float (&c)[6], int nbg, float xt, float yt) {
-    if (nbg == 6) return fmaf(c[5], xt * xt, fmaf(c[4], xt * yt, fmaf(c[3], xt, fmaf(c[2], yt * yt, fmaf(c[1], yt, c[0])))));
-    if (nbg == 3) return fmaf(c[2], xt, fmaf(c[1], yt, c[0]));
-    if (nbg == 1) return c[0];
-    return 0.0f;
-}
-
 template <int KS, int NK>
 __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, int* status) {
     constexpr int R = (KS - 1) / 2;
-    constexpr int NCOL = KS * NK;   // used MMA columns, <= 128
+    constexpr int NCOL = KS * NK;                // used MMA columns, <= 128
+    constexpr int SOFF = (4 - R % 4) % 4;        // srcf[.][SOFF + c] = R(x0 - R + c)
     static_assert(NCOL <= 128 && KS <= TKC, "tile shape");
+    static_assert(SOFF + SRCW <= SRCC * 4, "staged row");
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     TcShared& S = *reinterpret_cast<TcShared*>(
         tc_smem_raw + ((1024 - (tc::smem_u32(tc_smem_raw) & 1023)) & 1023));
@@ -109,7 +132,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     const int nout = min(TCY, a.h - y0);
     const int nsrc = nout + 2 * R;   // source rows y0 - R .. y0 + nout - 1 + R
 
-    // ---- set-up: B (hi/lo) from the kernel taps, barriers, TMEM, first source rows
+    // ---- set-up: B (hi/lo) from the kernel taps, barriers, TMEM
     // B column n = iv * NK + k
     for (int e = tid; e < 128 * TKC; e += TC_THREADS) {
         const int n = e / TKC, u = e - n * TKC;
@@ -143,49 +166,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     tc::fence_after();
     const uint32_t tmem = S.tmem;
 
-    if (warp >= 4 && warp < 11) {
-        // ---------------- producers: warps 8-10 fetch and split source rows one row
-        // ahead, warps 4-7 build the Hankel tile of the current row (one row m each)
+    if (warp >= 4 && warp < MMA_WARP) {
+        // ---------------- producers.  Row t of the stored A operand (16 bytes) holds
+        // the 8 values R(x0 - R + t + b), b = 0..7: core matrix t >> 3, its row t & 7.
+        // Producer t < NBUILD writes row t of the current source row from the staged
+        // floats (each value is split into hi/lo where it is used); producers
+        // c < SRCC fetch chunk c of source row rho + DP.
         const int pt = tid - 128;
-        const bool splitter = pt >= TCX;
-        const int ps = pt - TCX;                 // splitter index, 0 .. 95
-        constexpr int NSPLIT = NPROD - TCX;
-        // source row rr into its ring slot with cp.async (zero outside the image)
-        auto issue_row = [&](int rr) {
-            for (int c = ps; c < SRCW; c += NSPLIT) {
-                const int gy = y0 - R + rr, gx = x0 - R + c;
-                const bool in = rr < nsrc && gy >= 0 && gy < a.h && gx >= 0 && gx < a.w;
-                tc::cp_async4(&S.srcf[rr & (NSRC - 1)][c], in ? a.ref + (long)gy * a.pitch + gx : a.ref, in ? 4 : 0);
+        const int XS = x0 - R - SOFF;            // frame column of srcf[.][0], a multiple of 4
+        // chunk pt of source row rr into its ring slot (zero outside the image; the
+        // chunk holding column w is partly zero-filled)
+        auto issue = [&](int rr) {
+            if (pt < SRCC) {
+                const int gy = y0 - R + rr, X = XS + 4 * pt;
+                const int nb = (rr < nsrc && gy >= 0 && gy < a.h && X >= 0 && X < a.w) ? 4 * min(4, a.w - X) : 0;
+                tc::cp_async16(&S.srcf[rr & (NSRC - 1)][4 * pt], nb ? a.ref + (long)gy * a.pitch + X : a.ref, nb);
             }
+            tc::cp_async_commit();
         };
-        // BF16 split of source row rr into buffer rr & 1, two values per word
-        auto split_row = [&](int rr) {
-            const float2* src = reinterpret_cast<const float2*>(S.srcf[rr & (NSRC - 1)]);
-            uint32_t* dh = S.srch[rr & 1];
-            uint32_t* dl = S.srcl[rr & 1];
-            for (int i = ps; i < SRCW / 2; i += NSPLIT) {
-                const float2 v = src[i];
-                __nv_bfloat16 h0, l0, h1, l1;
-                split_bf16(v.x, h0, l0);
-                split_bf16(v.y, h1, l1);
-                dh[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                dl[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-        };
-        if (splitter) {
-            for (int d = 0; d < DP; d++) {
-                issue_row(d);
-                tc::cp_async_commit();
-            }
-            tc::cp_async_wait<DP - 2>();         // rows 0 and 1
-        }
-        tc::named_sync(1, NPROD);
-        if (splitter) split_row(0);
-        // One barrier per row.  Before barrier rho: the splitters have split row rho
-        // and hold row rho + 1 landed; the builders have built and fenced row
+        for (int d = 0; d < DP; d++) issue(d);
+        tc::cp_async_wait<DP - 2>();             // rows 0 and 1
+        // One barrier per row.  Before barrier rho: every producer holds its chunk
+        // of row rho + 1 landed and has written and fenced its part of row
         // rho - 1's tile; producer 0 has found stage s(rho) free.  After it,
-        // producer 0 marks stage s(rho - 1) filled, the splitters split row
-        // rho + 1 and fetch row rho + DP + 1, the builders build row rho.
+        // producer 0 marks stage s(rho - 1) filled, the producers fetch row
+        // rho + DP and build row rho.
         for (int rho = 0; rho < nsrc; rho++) {
             const int s = rho % NSTAGE, fill = rho / NSTAGE;
             if (pt == 0) {
@@ -196,53 +201,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
             tc::named_sync(1, NPROD);
             if (pt == 0 && rho >= 1) tc::mbar_arrive(&S.filled[(rho - 1) % NSTAGE]);
             if (S.pstop) break;
-            if (splitter) {
-                if (rho + 1 < nsrc) split_row(rho + 1);
-                issue_row(rho + DP);             // may be past the band: zero-filled, never used
-                tc::cp_async_commit();
-                tc::cp_async_wait<DP - 2>();     // row rho + 2 has landed
-            } else {
-                // Hankel row m: A[m][u'] = src[m + u'], chunk q = taps 8q .. 8q+7 as four
-                // words taken from src words (m >> 1) + 4q .. + 4 (shifted by one value
-                // when m is odd)
-                const int m = pt;
-                uint8_t* ah = S.ahi[s];
-                uint8_t* al = S.alo[s];
-                const uint32_t* sh = S.srch[rho & 1];
-                const uint32_t* sl = S.srcl[rho & 1];
-                const int w0 = m >> 1;
-                const uint32_t sel = (m & 1) ? 0x5432u : 0x3210u;
-                uint32_t hw[17], lw[17];
+            issue(rho + DP);                     // may be past the band: zero-filled, never used
+            if (pt < NBUILD) {
+                const float* src = S.srcf[rho & (NSRC - 1)] + SOFF + pt;
+                float v[8];
 #pragma unroll
-                for (int k = 0; k < 17; k++) {
-                    hw[k] = sh[w0 + k];
-                    lw[k] = sl[w0 + k];
-                }
+                for (int k = 0; k < 8; k++) v[k] = src[k];
+                uint32_t hw[4], lw[4];
 #pragma unroll
-                for (int q = 0; q < TKC / 8; q++) {
-                    const uint32_t off = canon_off(m, 8 * q);
-                    *reinterpret_cast<uint4*>(ah + off) =
-                        make_uint4(__byte_perm(hw[4 * q], hw[4 * q + 1], sel), __byte_perm(hw[4 * q + 1], hw[4 * q + 2], sel),
-                                   __byte_perm(hw[4 * q + 2], hw[4 * q + 3], sel), __byte_perm(hw[4 * q + 3], hw[4 * q + 4], sel));
-                    *reinterpret_cast<uint4*>(al + off) =
-                        make_uint4(__byte_perm(lw[4 * q], lw[4 * q + 1], sel), __byte_perm(lw[4 * q + 1], lw[4 * q + 2], sel),
-                                   __byte_perm(lw[4 * q + 2], lw[4 * q + 3], sel), __byte_perm(lw[4 * q + 3], lw[4 * q + 4], sel));
-                }
+                for (int k = 0; k < 4; k++) split_pair(v[2 * k], v[2 * k + 1], hw[k], lw[k]);
+                *reinterpret_cast<uint4*>(S.ahi[s] + 16 * pt) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(S.alo[s] + 16 * pt) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 tc::fence_proxy_async();
             }
+            tc::cp_async_wait<DP - 2>();         // own chunk of row rho + 2 has landed
             if (rho == nsrc - 1) {               // the last tile: one more barrier to publish it
                 tc::named_sync(1, NPROD);
                 if (pt == 0) tc::mbar_arrive(&S.filled[s]);
             }
         }
-        if (splitter) tc::cp_async_wait<0>();
-    } else if (warp == 11) {
-        // ---------------- MMA issuer
+        tc::cp_async_wait<0>();
+    } else if (warp >= MMA_WARP) {
+        // ---------------- MMA issuers: warp MMA_WARP + q takes the rows rho = q mod 2
+        // (its own stages and TMEM buffers; the issuing thread is held for about
+        // the MMAs' execution time, so two issuers keep the tensor pipe fed while
+        // each waits on its barriers)
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(1, 128, 128);
             const uint32_t bh = tc::smem_u32(S.bhi), bl = tc::smem_u32(S.blo);
             int issued = 0;
-            for (int rho = 0; rho < nsrc; rho++) {
+            for (int rho = warp - MMA_WARP; rho < nsrc; rho += 2) {
                 const int s = rho % NSTAGE, b = rho % NTB;
                 if (!wait_or_abort(S, &S.filled[s], (rho / NSTAGE) & 1, status)) break;
                 if (rho >= NTB && !wait_or_abort(S, &S.tempty[b], (rho / NTB - 1) & 1, status)) break;
@@ -250,19 +238,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
                 const uint32_t ahs = tc::smem_u32(S.ahi[s]), als = tc::smem_u32(S.alo[s]);
                 const uint32_t d = tmem + (uint32_t)(b * 128);
 #pragma unroll
-                for (int kh = 0; kh < 2; kh++) {   // two K = 16 halves
+                for (int kh = 0; kh < 2; kh++) {   // two K = 16 halves: K groups 2 kh, 2 kh + 1
                     const uint32_t ko = kh * 2 * LBO;
-                    tc::mma_bf16(d, tc::smem_desc(ahs + ko, LBO, SBO), tc::smem_desc(bh + ko, LBO, SBO), idesc,
-                                 kh > 0 ? 1u : 0u);
-                    tc::mma_bf16(d, tc::smem_desc(ahs + ko, LBO, SBO), tc::smem_desc(bl + ko, LBO, SBO), idesc, 1u);
-                    tc::mma_bf16(d, tc::smem_desc(als + ko, LBO, SBO), tc::smem_desc(bh + ko, LBO, SBO), idesc, 1u);
+                    const uint64_t ad_h = tc::smem_desc(ahs + ko, LBO, SBO_A), ad_l = tc::smem_desc(als + ko, LBO, SBO_A);
+                    const uint64_t bd_h = tc::smem_desc(bh + ko, LBO, SBO_B), bd_l = tc::smem_desc(bl + ko, LBO, SBO_B);
+                    tc::mma_bf16(d, ad_h, bd_h, idesc, kh > 0 ? 1u : 0u);
+                    tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
+                    tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
                 }
                 tc::commit(&S.empty[s]);
                 tc::commit(&S.tfull[b]);
                 issued = rho + 1;
             }
             // every issued MMA must land before TMEM is released (a commit
-            // tracks all earlier MMAs of this thread, so the last one suffices)
+            // tracks all earlier MMAs of this thread, so its last one suffices)
             if (issued > 0) {
                 const int last = issued - 1;
                 if (!tc::mbar_wait_bounded(&S.tfull[last % NTB], (last / NTB) & 1, WAIT_LIMIT)) {
@@ -276,94 +265,126 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
         // ---------------- epilogue: output column x0 + tid
         const int m = tid, x = x0 + m;
         const float xt = a.W > 1 ? (float)(2 * (x + a.ox) - (a.W - 1)) / (float)(a.W - 1) : 0.0f;
-        float bgc[6];
-#pragma unroll
-        for (int k = 0; k < 6; k++) bgc[k] = k < a.nbg ? (float)a.bg[k] : 0.0f;
+        // yt = 2 (y + oy) / (H - 1) - 1; the background as B0 + B1 yt + B2 yt^2 with the
+        // x terms of this column folded into B0 and B1
+        const float ysc = a.H > 1 ? 2.0f / (float)(a.H - 1) : 0.0f;
+        const float yof = a.H > 1 ? -1.0f : 0.0f;
+        float B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+        if (a.nbg == 6) {
+            B0 = fmaf((float)a.bg[5], xt * xt, fmaf((float)a.bg[3], xt, (float)a.bg[0]));
+            B1 = fmaf((float)a.bg[4], xt, (float)a.bg[1]);
+            B2 = (float)a.bg[2];
+        } else if (a.nbg == 3) {
+            B0 = fmaf((float)a.bg[2], xt, (float)a.bg[0]);
+            B1 = (float)a.bg[1];
+        } else if (a.nbg == 1) {
+            B0 = (float)a.bg[0];
+        }
+        const bool xin = x >= R && x <= a.w - 1 - R;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
         // p_k = xt^i yt^j: the xt^i factor is fixed for this column, so each T
         // column enters the ring already multiplied by it and the ring keeps
         // one sum per power of yt (NJ = degree + 1) instead of one per term
         constexpr int NJ = NK == 1 ? 1 : (NK == 3 ? 2 : 3);
+        constexpr int RL = KS + U - 1;
         const float xp[3] = {1.0f, xt, xt * xt};
-        float acc[KS][NJ];
+        float acc[RL][NJ];
 #pragma unroll
-        for (int i = 0; i < KS; i++)
+        for (int i = 0; i < RL; i++)
 #pragma unroll
             for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
-        // science value and flags of output rows eta .. eta + LQ - 1 in a register FIFO,
-        // loaded LQ rows before use
-        constexpr int LQ = 4;
-        float qI[LQ];
-        int qF[LQ];
-        auto load_out = [&](int rr, float& Iv, int& Fv) {
-            const bool in = rr >= 0 && rr < nout && x < a.w;
-            const long pp = in ? (long)(y0 + rr) * a.pitch + x : 0;
-            Iv = in ? __ldg(a.sci + pp) : 0.0f;
-            Fv = in ? (int)__ldg(a.flags + pp) : 1;
+        // science value and flag word of output row eta into slot eta & (NQ - 1),
+        // one cp.async group per row (the pitch is a multiple of 16, so the flag
+        // byte sits at byte x & 3 of its word)
+        auto fetch = [&](int eta) {
+            const bool in = eta >= 0 && eta < nout && x < a.w;
+            const long p = in ? (long)(y0 + eta) * a.pitch + x : 0;
+            const int slot = eta & (NQ - 1);
+            tc::cp_async4(&S.qI[slot][m], a.sci + p, in ? 4 : 0);
+            tc::cp_async4(&S.qF[slot][m], a.flags + (p & ~3L), in ? 4 : 0);
+            tc::cp_async_commit();
         };
+        const int fsh = 8 * (x & 3);
+#pragma unroll 1
+        for (int i = 0; i < LQ; i++) fetch(i - 2 * R);
+        // ring index i holds output row rb - 2r + i for the current block start rb;
+        // source row rb + u adds its column (iv, k) at index u + iv, and output row
+        // rb + u - 2r is then complete at index u
+        bool run = true;
+#pragma unroll 1
+        for (int rb = 0; rb < nsrc && run; rb += U) {
 #pragma unroll
-        for (int i = 0; i < LQ; i++) load_out(i - 2 * R, qI[i], qF[i]);
-        // ring index i holds output row rho - 2r + i; source row rho adds its
-        // column (iv, k) at index iv, row rho - 2r is then complete at index 0
-        // and the ring shifts down by one (register moves, one loop body)
-        for (int rho = 0; rho < nsrc; rho++) {
-            const int eta = rho - 2 * R;
-            const int y = y0 + eta;
-            const bool out = eta >= 0 && x < a.w && y < a.h;
-            const long p = out ? (long)y * a.pitch + x : 0;
-            const float I = qI[0];
-            const int fl = qF[0];
+            for (int u = 0; u < U; u++) {
+                const int rho = rb + u;
+                if (rho < nsrc && run) {
+                    const int eta = rho - 2 * R;
+                    fetch(eta + LQ);
+                    const int b = rho % NTB;
+                    // lane 0 waits (fewer pollers on the barrier), the warp follows
+                    bool ok = true;
+                    if (lane == 0) ok = wait_or_abort(S, &S.tfull[b], (rho / NTB) & 1, status);
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) {
+                        run = false;
+                    } else {
+                        tc::fence_after();
 #pragma unroll
-            for (int i = 0; i + 1 < LQ; i++) {
-                qI[i] = qI[i + 1];
-                qF[i] = qF[i + 1];
-            }
-            load_out(eta + LQ, qI[LQ - 1], qF[LQ - 1]);
-            const int b = rho % NTB;
-            bool run = wait_or_abort(S, &S.tfull[b], (rho / NTB) & 1, status);
-            run = __all_sync(0xffffffffu, run);
-            if (!run) break;
-            tc::fence_after();
+                        for (int c2 = 0; c2 < 4; c2++) {
+                            if (c2 * 32 < NCOL) {
+                                uint32_t r0[16], r1[16];
+                                tc::tmem_ld16_nowait(tl + (uint32_t)(b * 128 + c2 * 32), r0);
+                                if (c2 * 32 + 16 < NCOL) {
+                                    tc::tmem_ld16_nowait(tl + (uint32_t)(b * 128 + c2 * 32 + 16), r1);
+                                } else {
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-                if (c * 16 < NCOL) {
-                    float v[16];
-                    tc::tmem_ld16(tl + (uint32_t)(b * 128 + c * 16), v);
+                                    for (int j = 0; j < 16; j++) r1[j] = 0u;
+                                }
+                                tc::tmem_wait_ld(r0, r1);
 #pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int n = c * 16 + j;
-                        if (n < NCOL) {
-                            const int iv = n / NK, k = n - iv * NK;
-                            // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
-                            const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
-                            const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
-                            acc[iv][tj] = fmaf(xp[ti], v[j], acc[iv][tj]);
+                                for (int j = 0; j < 32; j++) {
+                                    const int n = c2 * 32 + j;
+                                    if (n < NCOL) {
+                                        const int iv = n / NK, k = n - iv * NK;
+                                        // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
+                                        const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
+                                        const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
+                                        const float v = __uint_as_float(j < 16 ? r0[j] : r1[j - 16]);
+                                        acc[u + iv][tj] = fmaf(xp[ti], v, acc[u + iv][tj]);
+                                    }
+                                }
+                            }
+                        }
+                        tc::fence_before();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&S.tempty[b]);
+                        tc::cp_async_wait<LQ>();         // row eta's group has landed
+                        if (eta >= 0 && eta < nout && x < a.w) {
+                            const int slot = eta & (NQ - 1);
+                            const float I = S.qI[slot][m];
+                            const uint32_t fl = (S.qF[slot][m] >> fsh) & 0xffu;
+                            const int y = y0 + eta;
+                            const float yt = fmaf((float)(y + a.oy), ysc, yof);
+                            // model = (acc0 + B0) + (acc1 + B1) yt + (acc2 + B2) yt^2
+                            float c2 = B2, c1 = B1;
+                            if constexpr (NJ > 2) c2 += acc[u][2];
+                            if constexpr (NJ > 1) c1 += acc[u][1];
+                            const float model = fmaf(fmaf(c2, yt, c1), yt, acc[u][0] + B0);
+                            const bool inner = xin && y >= R && y <= a.h - 1 - R && fl == 0;
+                            a.diff[(long)y * a.pitch + x] = inner ? I - model : 0.0f;
                         }
                     }
                 }
             }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&S.tempty[b]);
-            if (out) {
-                float D = 0.0f;
-                const bool inner = x >= R && y >= R && x <= a.w - 1 - R && y <= a.h - 1 - R;
-                if (inner && fl == 0) {
-                    const float yt = a.H > 1 ? (float)(2 * (y + a.oy) - (a.H - 1)) / (float)(a.H - 1) : 0.0f;
-                    float conv = acc[0][0];
-                    if constexpr (NJ > 1) conv = fmaf(acc[0][1], yt, conv);
-                    if constexpr (NJ > 2) conv = fmaf(acc[0][2], yt * yt, conv);
-                    D = I - conv - background(bgc, a.nbg, xt, yt);
-                }
-                a.diff[p] = D;
-            }
 #pragma unroll
-            for (int i = 0; i + 1 < KS; i++)
+            for (int i = 0; i + U < RL; i++)
 #pragma unroll
-                for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + 1][j];
+                for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + U][j];
 #pragma unroll
-            for (int j = 0; j < NJ; j++) acc[KS - 1][j] = 0.0f;
+            for (int i = RL - U; i < RL; i++)
+#pragma unroll
+                for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
         }
+        tc::cp_async_wait<0>();
     }
     tc::fence_before();
     __syncthreads();
