@@ -289,15 +289,18 @@ def run_gpu(args):
     peaks = load_peaks()
     # dominant kernel: the tensor-core reference convolution of the subtraction
     # (difference image).  Algorithmic work: NK * KS^2 multiply-adds per pixel;
-    # the MMAs execute more (BF16 hi/lo x three products, K padded 21 -> 32, N
-    # 126 -> 128, 2R halo rows per 128-row band), reported beside it.
+    # the MMAs execute more (BF16 hi/lo x three products, K padded 21 -> 24, one
+    # M=128 x N=16*ceil((KS-1+4)*NK/16) MMA group per source row, source rows in
+    # blocks of 4 with 2R halo rows per 128-row band), reported beside it.
     nk = (SDEG + 1) * (SDEG + 2) // 2
     conv_flops = 2 * nk * KSIZE * KSIZE * W * H
     achieved = conv_flops / (tc_ms / 1e3) / 1e12
     bands = [min(128, H - y0) for y0 in range(0, H, 128)]
-    executed = 3 * 2 * 128 * 128 * 32 * ((W + 127) // 128) * sum(b + KSIZE - 1 for b in bands)
+    n_mma = 16 * (((KSIZE - 1 + 4) * nk + 15) // 16)
+    k_row = 16 if KSIZE <= 16 else 24          # taps 16..23 of a row pair share one K = 16 MMA
+    executed = 3 * 2 * 128 * n_mma * k_row * ((W + 127) // 128) * sum(4 * ((b + KSIZE - 1 + 3) // 4) for b in bands)
     tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1462.0)
+    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)   # sampled, else the maximum
     alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x clock
     var_tflops = 2 * KSIZE * KSIZE * W * H / (var_ms / 1e3) / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)

@@ -9,8 +9,9 @@
 //   T[m][(j, k)] = sum_g sum_{u'} A_g[m][u'] B_g[u'][(j, k)],
 //   A_g[m][u'] = R(x0 + m - r + u', rho0 + g)          (a Hankel matrix, u' < 32),
 //   B_g[u'][(j, k)] = K_k[j - g][KS - 1 - u']          (zero unless 0 <= j - g < KS),
-// four tcgen05 MMA groups of M = 128, N = (KS - 1 + G) * NK (144 for a 21 x 21
-// kernel of degree 2), K = 32.  Column (j, k) is the contribution of the block
+// tcgen05 MMAs of M = 128, N = (KS - 1 + G) * NK (144 for a 21 x 21 kernel of
+// degree 2): K = 16 per row for taps 0..15, and one K = 16 MMA per row pair for
+// taps 16..23, whose K groups are taken from the two rows' operands.  Column (j, k) is the contribution of the block
 // to output row rho0 - 2r + j for term k: shifting B by g rows of taps makes the
 // four source rows land on the columns of the output rows they feed, so the
 // MMAs do part of the sum over iv and the epilogue reads 36 instead of 126
@@ -75,6 +76,7 @@ struct TcCfg {
     static constexpr int TSTRIDE = (N + 31) / 32 * 32;      // TMEM columns per accumulator
     static constexpr uint32_t B_BYTES = (uint32_t)N / 8 * SBO_B;   // one B_g operand
     static_assert(N <= 256 && NTB * TSTRIDE <= 512, "MMA shape");
+    static_assert(KS <= 24 && G % 2 == 0, "taps 16..23 of row pairs share one MMA");
 };
 
 template <int KS, int NK>
@@ -248,19 +250,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
                 if (blk >= NTB && !wait_or_abort(S, &S.tempty[tb], (blk / NTB - 1) & 1, status)) break;
                 tc::fence_after();
                 const uint32_t d = tmem + (uint32_t)(tb * C::TSTRIDE);
+                // taps u' = 0..15 of each source row: one K = 16 MMA per row (K groups 0, 1)
 #pragma unroll
                 for (int g = 0; g < G; g++) {
-                    const uint32_t ahs = tc::smem_u32(S.ahi[s][g]), als = tc::smem_u32(S.alo[s][g]);
-                    const uint32_t bh = tc::smem_u32(S.b[g][0]), bl = tc::smem_u32(S.b[g][1]);
+                    const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
+                    const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
+                    const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[g][0]), LBO, SBO_B);
+                    const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[g][1]), LBO, SBO_B);
+                    tc::mma_bf16(d, ad_h, bd_h, idesc, g ? 1u : 0u);
+                    tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
+                    tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
+                }
+                // taps 16..23 of two source rows in one K = 16 MMA: K group 0 is group 2
+                // of row g, K group 1 group 2 of row g + 1 (the K-group stride is the
+                // distance between the two rows' operands)
 #pragma unroll
-                    for (int kh = 0; kh < 2; kh++) {   // two K = 16 halves: K groups 2 kh, 2 kh + 1
-                        const uint32_t ko = kh * 2 * LBO;
-                        const uint64_t ad_h = tc::smem_desc(ahs + ko, LBO, SBO_A), ad_l = tc::smem_desc(als + ko, LBO, SBO_A);
-                        const uint64_t bd_h = tc::smem_desc(bh + ko, LBO, SBO_B), bd_l = tc::smem_desc(bl + ko, LBO, SBO_B);
-                        tc::mma_bf16(d, ad_h, bd_h, idesc, (g | kh) ? 1u : 0u);
-                        tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
-                        tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
-                    }
+                for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
+                    const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                    const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                    const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
+                    const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[g][1]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
+                    tc::mma_bf16(d, ad_h, bd_h, idesc, 1u);
+                    tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
+                    tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
                 }
                 tc::commit(&S.empty[s]);
                 tc::commit(&S.tfull[tb]);
