@@ -194,7 +194,7 @@ int argus_expand_kernel(argus_ctx *ctx, const argus_basis *basis, const double *
  * Sec. 3.2):
  *   D   = sci - sum_k p_k(x,y) sum_{u,v} K_k(u,v) ref(x-u, y-v) - sum_k bg_k p_k(x,y)
  *   V_D = sci_var + sum_{u,v} Kc(u,v)^2 ref_var(x-u, y-v),
- * Kc = sum_k p_k(xc,yc) K_k at the centre of the 32x32 tile (frame
+ * Kc = sum_k p_k(xc,yc) K_k at the centre of the 128x128 tile (frame
  * coordinates) holding (x,y).  Spatial terms use frame size (frame_w,
  * frame_h) and frame coordinates (x + ox, y + oy); with spatial_degree > 0,
  * ox and oy must be multiples of 32.  Pixels within r = ksize/2 of an image

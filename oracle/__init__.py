@@ -244,7 +244,7 @@ def expand(b: Basis, coeffs):
 
 
 def subtract(sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=None, origin=(0, 0),
-             var_tile=32, with_var=True):
+             var_tile=128, with_var=True):
     """Full-image D (and V_D).  K [Ks, ks, ks], bg [Kb]; frame = (W, H) for spatial terms."""
     sci = _c(sci, np.float32); sv = _c(sci_var, np.float32); R = _c(ref, np.float32)
     Rv = _c(ref_var, np.float32); fl = _c(flags, np.uint8)
@@ -258,7 +258,7 @@ def subtract(sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=Non
 
 
 def subtract_at(xy, sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=None,
-                origin=(0, 0), var_tile=32):
+                origin=(0, 0), var_tile=128):
     sci = _c(sci, np.float32); sv = _c(sci_var, np.float32); R = _c(ref, np.float32)
     Rv = _c(ref_var, np.float32); fl = _c(flags, np.uint8)
     K = _c(K, np.float64); bg = _c(np.atleast_1d(bg), np.float64); xy = _c(xy, np.int32)

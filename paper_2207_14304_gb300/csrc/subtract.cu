@@ -29,7 +29,7 @@ int launch(const SubArgs& a, cudaStream_t st) {
 }
 
 // Difference variance alone, V_D = V_I + (Kc^2 (x) V_ref), Kc the kernel at the
-// centre of the 32x32 tile (the same definition as the per-tile body).  One CTA
+// centre of the VAR_TILE tile (the same definition as the per-tile body).  One CTA
 // of 64 threads per tile: thread (lx, half) owns column lx, rows 16*half ..
 // +15.  V_ref is staged column-major (column stride 60 floats: a 16-byte load
 // per lane is conflict-free within each quarter-warp), so a thread's 16 + KS - 1
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(64) variance_kernel(SubArgs a) {
     }
     {
         float pc[ARGUS_MAX_TERMS];
-        const float xc = (float)(((tx0 + a.ox) / TILE) * TILE) + 0.5f * (TILE - 1);
-        const float yc = (float)(((ty0 + a.oy) / TILE) * TILE) + 0.5f * (TILE - 1);
+        const float xc = (float)(((tx0 + a.ox) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
+        const float yc = (float)(((ty0 + a.oy) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
         const float xt = a.W > 1 ? (2.0f * xc - (float)(a.W - 1)) / (float)(a.W - 1) : 0.0f;
         const float yt = a.H > 1 ? (2.0f * yc - (float)(a.H - 1)) / (float)(a.H - 1) : 0.0f;
         spatial_terms(xt, yt, a.sdeg, pc);
@@ -123,12 +123,16 @@ int launch_var(const SubArgs& a, cudaStream_t st) {
 // variance only, then the tensor-core kernel writes D.
 template <int KS>
 int launch_split(const SubArgs& a, int nk, int* status, cudaStream_t st) {
+    if (nk != 1 && nk != 3 && nk != 6) return ARGUS_ERR_UNSUPPORTED;
     if (a.diff_var) {
-        int rc = ARGUS_ERR_UNSUPPORTED;
-        switch (nk) {
-            case 1: rc = launch_var<KS, 1>(a, st); break;
-            case 3: rc = launch_var<KS, 3>(a, st); break;
-            case 6: rc = launch_var<KS, 6>(a, st); break;
+        // the variance on the tensor cores when the frame origin is on the variance-tile grid
+        int rc = argus_subtract_var_tc(a, KS, status, st);
+        if (rc == ARGUS_ERR_UNSUPPORTED) {
+            switch (nk) {
+                case 1: rc = launch_var<KS, 1>(a, st); break;
+                case 3: rc = launch_var<KS, 3>(a, st); break;
+                case 6: rc = launch_var<KS, 6>(a, st); break;
+            }
         }
         if (rc) return rc;
     }

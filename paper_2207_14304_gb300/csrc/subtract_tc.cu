@@ -34,10 +34,11 @@
 // TCY + 2r source rows in blocks of G.  Warps 0-3: epilogue, one output
 // column per thread and TMEM lane.  Science values and flag words reach
 // shared memory by cp.async two blocks ahead, each thread fetching its own
-// column.  Warps 4-8: producers (source rows arrive by 16-byte cp.async two
-// blocks ahead; 152 threads write the A operands of a block, splitting each
-// value into hi/lo where it is used; NSB block stages; one named barrier per
-// block).  Warps 9-10: one thread each issues the MMAs of alternate blocks.
+// column.  Warps 4-8: producers, each warp on its own (it stages its window
+// of the source rows by 16-byte cp.async two blocks ahead, writes its 32 rows
+// of the A operands of a block, splitting each value into hi/lo where it is
+// used, and arrives on the stage's barrier; NSB block stages).  Warps 9-10:
+// one thread each issues the MMAs of alternate blocks.
 // TMEM holds NTB accumulators.  Every wait is bounded; a timeout latches
 // ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_bf16.h>
@@ -55,18 +56,19 @@ constexpr int G = 4;                         // source rows per block
 constexpr int NCM = TCX / 8 + TKC / 8 - 1;   // distinct core matrices of one Hankel tile
 constexpr uint32_t A_BYTES = NCM * 128;      // one operand (hi or lo) of one source row
 constexpr int NSB = 3;                       // block stages of A
-constexpr int SRCW = TCX + TKC;              // source values per row
-constexpr int SRCC = SRCW / 4 + 1;           // 16-byte chunks staged per row (one spare for the offset)
 constexpr int NSRC = 4 * G;                  // fp32 source-row ring: four blocks
 constexpr int NBUILD = NCM * 8;              // one producer thread per stored operand row
+constexpr int PCH = 11;                      // 16-byte chunks of a producer warp's window (32 + 7 values + offset)
+constexpr int PWIN = PCH * 4;
 constexpr int NPROD = (NBUILD + 31) / 32 * 32;   // producer threads (warps 4-8)
-constexpr int MMA_WARP = 4 + NPROD / 32;     // warps 9 and 10 issue the MMAs of even and odd blocks
+constexpr int NPW = NPROD / 32;              // producer warps
+constexpr int MMA_WARP = 4 + NPW;            // warps 9 and 10 issue the MMAs of even and odd blocks
 constexpr int TC_THREADS = (MMA_WARP + 2) * 32;
 constexpr uint32_t LBO = 128, SBO_A = 128, SBO_B = 512;
 constexpr long long WAIT_LIMIT = 2000000000LL;   // ~1 s of SM clock
 constexpr int NTB = 3;                       // TMEM accumulators
 constexpr int NQ = 4 * G;                    // science/flag rows in shared memory: four blocks
-static_assert(MMA_WARP == 9 && TC_THREADS == 352 && SRCC <= NPROD, "warp roles");
+static_assert(MMA_WARP == 9 && TC_THREADS == 352, "warp roles");
 
 template <int KS, int NK>
 struct TcCfg {
@@ -76,21 +78,22 @@ struct TcCfg {
     static constexpr int TSTRIDE = (N + 31) / 32 * 32;      // TMEM columns per accumulator
     static constexpr uint32_t B_BYTES = (uint32_t)N / 8 * SBO_B;   // one B_g operand
     static_assert(N <= 256 && NTB * TSTRIDE <= 512, "MMA shape");
+    static_assert(NK != 1 || (2 * N <= 256 && NTB * 2 * N <= 512), "one-term MMA of width 2N");
     static_assert(KS <= 24 && G % 2 == 0, "taps 16..23 of row pairs share one MMA");
 };
 
-template <int KS, int NK>
+template <int KS, int NK, bool VAR>
 struct TcShared {
-    uint8_t b[G][2][TcCfg<KS, NK>::B_BYTES];    // B_g, hi and lo
+    uint8_t b[VAR ? 2 : 1][G][2][TcCfg<KS, NK>::B_BYTES];   // B_g, hi and lo (VAR: one set per strip parity)
     uint8_t ahi[NSB][G][A_BYTES];
     uint8_t alo[NSB][G][A_BYTES];
-    alignas(16) float srcf[NSRC][SRCC * 4];
+    alignas(16) float wsrc[NPW][NSRC][PWIN];    // each producer warp's staged source windows
     alignas(16) float qI[NQ][TCX];              // science values of output rows, by row & (NQ - 1)
     alignas(16) uint32_t qF[NQ][TCX];           // the 32-bit word holding each output pixel's flag byte
     uint64_t filled[NSB], empty[NSB], tfull[NTB], tempty[NTB];
+    uint64_t bready[2], bfree[2];               // VAR: B set written / no longer read by the MMAs
     uint32_t tmem;
     int abort;       // set by any role that timed out
-    int pstop;       // producers' common decision, written by producer 0 between barriers
 };
 
 __device__ __forceinline__ uint32_t canon_off(int row, int kk) {
@@ -129,45 +132,91 @@ __device__ __forceinline__ bool wait_or_abort(SH& S, uint64_t* bar, uint32_t par
     return true;
 }
 
-template <int KS, int NK>
+// VAR = false: the difference image (NK spatial terms, background, D = I - model).
+// VAR = true: the convolution of the difference variance, sum Kc^2 V_ref with Kc the
+// kernel at the centre of the CTA's VAR_TILE x VAR_TILE variance tile (one term),
+// V_D = V_I + that sum; the CTA's strip then has to lie in one variance tile.
+template <int KS, int NK, bool VAR>
 __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, int* status) {
     using C = TcCfg<KS, NK>;
-    using Sh = TcShared<KS, NK>;
+    using Sh = TcShared<KS, NK, VAR>;
+    static_assert(!VAR || NK == 1, "the variance convolution has one term");
+    static_assert(TCX == VAR_TILE && TCY == VAR_TILE, "one variance tile per strip");
+    const float* src_img = VAR ? a.ref_var : a.ref;   // convolved image
+    const float* obs = VAR ? a.sci_var : a.sci;       // observed image the model is compared with
+    float* outp = VAR ? a.diff_var : a.diff;
     constexpr int R = (KS - 1) / 2;
-    constexpr int SOFF = (4 - R % 4) % 4;        // srcf[.][SOFF + c] = R(x0 - R + c)
-    static_assert(KS <= TKC && SOFF + SRCW <= SRCC * 4, "tile shape");
+    constexpr int TS = VAR ? 2 * C::N : C::TSTRIDE;   // TMEM columns per accumulator
+    constexpr int SOFF = (4 - R % 4) % 4;        // wsrc[pw][.][SOFF + c] = R(x0 - R + 32 pw + c)
+    static_assert(KS <= TKC && SOFF + 31 + 8 <= PWIN, "tile shape");
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     Sh& S = *reinterpret_cast<Sh*>(tc_smem_raw + ((1024 - (tc::smem_u32(tc_smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * TCY;
-    const int nout = min(TCY, a.h - y0);
-    const int nsrc = nout + 2 * R;               // source rows y0 - R .. y0 + nout - 1 + R
-    const int nblk = (nsrc + G - 1) / G;         // rows past nsrc are zero
+    // work items: strips of TCX columns x TCY rows, item = by * gx + bx, taken by the
+    // CTAs round robin (one CTA per SM); B is built once (difference image) or per
+    // strip by the producers into one of two sets (variance: it depends on the strip's
+    // variance tile)
+    const int gx = (a.w + TCX - 1) / TCX, nitems = gx * ((a.h + TCY - 1) / TCY);
+    auto geom = [&](int item, int& x0, int& y0, int& nout, int& nblk) {
+        const int by = item / gx;
+        x0 = (item - by * gx) * TCX;
+        y0 = by * TCY;
+        nout = min(TCY, a.h - y0);
+        nblk = (nout + 2 * R + G - 1) / G;       // source rows y0 - R .. y0 + nout - 1 + R; rows past them are zero
+    };
 
     // ---- set-up: B_g (hi/lo) from the kernel taps, barriers, TMEM
-    // B_g column n = j * NK + k holds K_k[j - g][KS - 1 - u']
-    for (int e = tid; e < G * C::N * TKC; e += TC_THREADS) {
-        const int g = e / (C::N * TKC), r = e - g * (C::N * TKC);
-        const int n = r / TKC, u = r - n * TKC;
-        const int j = n / NK, k = n - j * NK, iv = j - g;
-        float v = 0.0f;
-        if (n < C::NCOL && u < KS && iv >= 0 && iv < KS) v = __ldg(a.K + k * KS * KS + iv * KS + (KS - 1 - u));
-        __nv_bfloat16 hi, lo;
-        split_bf16(v, hi, lo);
-        *reinterpret_cast<__nv_bfloat16*>(S.b[g][0] + canon_off(n, u)) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(S.b[g][1] + canon_off(n, u)) = lo;
-    }
+    // B_g column n = j * NK + k holds K_k[j - g][KS - 1 - u'] (VAR: Kc^2[j - g][KS - 1 - u'],
+    // Kc the kernel at the centre of the strip's variance tile); threads first .. first +
+    // count - 1 write set bs
+    auto build_b = [&](int item, int bs, int first, int count) {
+        float pc[ARGUS_MAX_TERMS];
+        int nkt = NK;
+        if (VAR) {
+            int x0, y0, nout, nblk;
+            geom(item, x0, y0, nout, nblk);
+            const float xc = (float)(((x0 + a.ox) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
+            const float yc = (float)(((y0 + a.oy) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
+            const float xt = a.W > 1 ? (2.0f * xc - (float)(a.W - 1)) / (float)(a.W - 1) : 0.0f;
+            const float yt = a.H > 1 ? (2.0f * yc - (float)(a.H - 1)) / (float)(a.H - 1) : 0.0f;
+            spatial_terms(xt, yt, a.sdeg, pc);
+            nkt = (a.sdeg + 1) * (a.sdeg + 2) / 2;
+        }
+        for (int e = tid - first; e < G * C::N * TKC; e += count) {
+            const int g = e / (C::N * TKC), r = e - g * (C::N * TKC);
+            const int n = r / TKC, u = r - n * TKC;
+            const int j = n / NK, k = n - j * NK, iv = j - g;
+            float v = 0.0f;
+            if (n < C::NCOL && u < KS && iv >= 0 && iv < KS) {
+                if (VAR) {
+                    float kc = 0.0f;
+                    for (int q = 0; q < nkt; q++) kc = fmaf(pc[q], __ldg(a.K + q * KS * KS + iv * KS + (KS - 1 - u)), kc);
+                    v = kc * kc;
+                } else {
+                    v = __ldg(a.K + k * KS * KS + iv * KS + (KS - 1 - u));
+                }
+            }
+            __nv_bfloat16 hi, lo;
+            split_bf16(v, hi, lo);
+            *reinterpret_cast<__nv_bfloat16*>(S.b[bs][g][0] + canon_off(n, u)) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(S.b[bs][g][1] + canon_off(n, u)) = lo;
+        }
+    };
+    if (!VAR) build_b(0, 0, 0, TC_THREADS);
     if (tid == 0) {
         for (int s = 0; s < NSB; s++) {
-            tc::mbar_init(&S.filled[s], 1);
+            tc::mbar_init(&S.filled[s], NPW);   // one arrival per producer warp
             tc::mbar_init(&S.empty[s], 1);
         }
         for (int b = 0; b < NTB; b++) {
             tc::mbar_init(&S.tfull[b], 1);
             tc::mbar_init(&S.tempty[b], 4);   // one arrival per epilogue warp
         }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&S.bready[b], NPW);  // one arrival per producer warp
+            tc::mbar_init(&S.bfree[b], 2);     // one commit per MMA issuer
+        }
         S.abort = 0;
-        S.pstop = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tc::tmem_alloc(&S.tmem, 512);
@@ -176,107 +225,150 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = S.tmem;
+    // every role walks the same items and blocks; gb counts blocks over the items and
+    // drives the stage and TMEM rings and their barrier phases
 
     if (warp >= 4 && warp < MMA_WARP) {
-        // ---------------- producers.  Producer t < NBUILD writes 16-byte row t of the
-        // A operands of each source row of a block, R(x0 - R + t + b), b = 0..7, from
-        // the staged floats; producers c < SRCC fetch chunk c of the source rows two
-        // blocks ahead, one cp.async group per block.
-        const int pt = tid - 128;
-        const int XS = x0 - R - SOFF;            // frame column of srcf[.][0], a multiple of 4
-        auto issue = [&](int blk) {
-            if (pt < SRCC) {
-                const int X = XS + 4 * pt;
-                const bool xin = X >= 0 && X < a.w;
-#pragma unroll
-                for (int g = 0; g < G; g++) {
-                    const int rr = blk * G + g, gy = y0 - R + rr;
-                    const int nb = (xin && rr < nsrc && gy >= 0 && gy < a.h) ? 4 * min(4, a.w - X) : 0;
-                    tc::cp_async16(&S.srcf[rr & (NSRC - 1)][4 * pt], nb ? a.ref + (long)gy * a.pitch + X : a.ref, nb);
-                }
-            }
-            tc::cp_async_commit();
-        };
-        issue(0);
-        issue(1);
-        tc::cp_async_wait<1>();                  // block 0
-        // One barrier per block.  Before barrier blk: every producer holds its chunks
-        // of block blk landed and has written and fenced its part of block blk - 1;
-        // producer 0 has found stage s(blk) free.  After it, producer 0 marks stage
-        // s(blk - 1) filled, the producers fetch block blk + 2 and build block blk.
-        for (int blk = 0; blk < nblk; blk++) {
-            const int s = blk % NSB, fill = blk / NSB;
-            if (pt == 0) {
-                bool ok = !S.abort;
-                if (ok && fill >= 1) ok = wait_or_abort(S, &S.empty[s], (fill - 1) & 1, status);
-                S.pstop = ok ? 0 : 1;
-            }
-            tc::named_sync(1, NPROD);
-            if (pt == 0 && blk >= 1) tc::mbar_arrive(&S.filled[(blk - 1) % NSB]);
-            if (S.pstop) break;
-            issue(blk + 2);                      // may be past the band: zero-filled, never used
-            if (pt < NBUILD) {
-#pragma unroll
-                for (int g = 0; g < G; g++) {
-                    const float* src = S.srcf[(blk * G + g) & (NSRC - 1)] + SOFF + pt;
-                    float v[8];
-#pragma unroll
-                    for (int k = 0; k < 8; k++) v[k] = src[k];
-                    uint32_t hw[4], lw[4];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) split_pair(v[2 * k], v[2 * k + 1], hw[k], lw[k]);
-                    *reinterpret_cast<uint4*>(S.ahi[s][g] + 16 * pt) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(S.alo[s][g] + 16 * pt) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                }
+        // ---------------- producers: each warp works on its own, with no barrier between
+        // warps.  Lane l of producer warp pw writes 16-byte row t = 32 pw + l (t < NBUILD)
+        // of the A operands of each source row of a block, R(x0 - R + t + b), b = 0..7.
+        // The warp stages the source values it needs (its 44-float window of each row,
+        // 11 16-byte chunks) itself, two blocks ahead, one cp.async group per block;
+        // after its writes and a proxy fence, lane 0 arrives on the stage's filled
+        // barrier (one arrival per producer warp).
+        const int pw = warp - 4, t = 32 * pw + lane;
+        float (*wsrc)[PWIN] = S.wsrc[pw];
+        bool run = true;
+        int gb = 0, li = 0;
+        for (int item = blockIdx.x; item < nitems && run; item += gridDim.x, li++) {
+            int x0, y0, nout, nblk;
+            geom(item, x0, y0, nout, nblk);
+            const int nsrc = nout + 2 * R;
+            if (VAR) {   // this strip's B set, once the MMAs of the strip two back are done with it
+                bool ok = true;
+                if (lane == 0 && li >= 2) ok = wait_or_abort(S, &S.bfree[li & 1], ((li - 2) >> 1) & 1, status);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) { run = false; break; }
+                build_b(item, li & 1, 128, NPROD);
                 tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.bready[li & 1]);
             }
-            tc::cp_async_wait<1>();              // own chunks of block blk + 1 have landed
-            if (blk == nblk - 1) {               // the last block: one more barrier to publish it
-                tc::named_sync(1, NPROD);
-                if (pt == 0) tc::mbar_arrive(&S.filled[s]);
+            const int XS = x0 - R - SOFF + 32 * pw;   // frame column of wsrc[pw][.][0], a multiple of 4
+            auto issue = [&](int blk) {
+                for (int q = lane; q < G * PCH; q += 32) {
+                    const int g = q / PCH, c = q - g * PCH;
+                    const int rr = blk * G + g, gy = y0 - R + rr, X = XS + 4 * c;
+                    const int nb = (X >= 0 && X < a.w && rr < nsrc && gy >= 0 && gy < a.h) ? 4 * min(4, a.w - X) : 0;
+                    tc::cp_async16(&wsrc[rr & (NSRC - 1)][4 * c], nb ? src_img + (long)gy * a.pitch + X : src_img, nb);
+                }
+                tc::cp_async_commit();
+            };
+            issue(0);
+            issue(1);
+            tc::cp_async_wait<1>();              // block 0 (own copies)
+            __syncwarp();                        // ... and the other lanes' copies are visible
+            for (int blk = 0; blk < nblk; blk++, gb++) {
+                const int s = gb % NSB, fill = gb / NSB;
+                bool ok = true;
+                if (lane == 0 && fill >= 1) ok = wait_or_abort(S, &S.empty[s], (fill - 1) & 1, status);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) { run = false; break; }
+                issue(blk + 2);                  // may be past the band: zero-filled, never used
+                if (t < NBUILD) {
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        const float* src = wsrc[(blk * G + g) & (NSRC - 1)] + SOFF + lane;
+                        float v[8];
+#pragma unroll
+                        for (int k = 0; k < 8; k++) v[k] = src[k];
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int k = 0; k < 4; k++) split_pair(v[2 * k], v[2 * k + 1], hw[k], lw[k]);
+                        *reinterpret_cast<uint4*>(S.ahi[s][g] + 16 * t) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(S.alo[s][g] + 16 * t) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                    tc::fence_proxy_async();
+                }
+                tc::cp_async_wait<1>();          // block blk + 1 (own copies)
+                __syncwarp();                    // writes, fences and copies of all lanes done
+                if (lane == 0) tc::mbar_arrive(&S.filled[s]);
             }
+            tc::cp_async_wait<0>();              // the zero-filled copies past the strip land before the
+            __syncwarp();                        // next strip's copies reuse their slots
         }
-        tc::cp_async_wait<0>();
     } else if (warp >= MMA_WARP) {
-        // ---------------- MMA issuers: warp MMA_WARP + q takes the blocks blk = q mod 2
+        // ---------------- MMA issuers: warp MMA_WARP + q takes the blocks gb = q mod 2
         // (the issuing thread is held for about the MMAs' execution time, so two
         // issuers keep the tensor pipe fed while each waits on its barriers)
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(1, 128, C::N);
-            int issued = -1;
-            for (int blk = warp - MMA_WARP; blk < nblk; blk += 2) {
-                const int s = blk % NSB, tb = blk % NTB;
-                if (!wait_or_abort(S, &S.filled[s], (blk / NSB) & 1, status)) break;
-                if (blk >= NTB && !wait_or_abort(S, &S.tempty[tb], (blk / NTB - 1) & 1, status)) break;
-                tc::fence_after();
-                const uint32_t d = tmem + (uint32_t)(tb * C::TSTRIDE);
-                // taps u' = 0..15 of each source row: one K = 16 MMA per row (K groups 0, 1)
+            const uint32_t idesc2 = tc::instr_desc(1, 128, 2 * C::N);
+            int issued = -1, gb = 0, li = 0;
+            bool run = true;
+            for (int item = blockIdx.x; item < nitems && run; item += gridDim.x, li++) {
+                int x0, y0, nout, nblk;
+                geom(item, x0, y0, nout, nblk);
+                const int bs = VAR ? (li & 1) : 0;
+                if (VAR && !wait_or_abort(S, &S.bready[bs], (li >> 1) & 1, status)) { run = false; break; }
+                for (int blk = 0; blk < nblk; blk++, gb++) {
+                    if ((gb & 1) != warp - MMA_WARP) continue;
+                    const int s = gb % NSB, tb = gb % NTB;
+                    if (!wait_or_abort(S, &S.filled[s], (gb / NSB) & 1, status)) { run = false; break; }
+                    if (gb >= NTB && !wait_or_abort(S, &S.tempty[tb], (gb / NTB - 1) & 1, status)) { run = false; break; }
+                    tc::fence_after();
+                    const uint32_t d = tmem + (uint32_t)(tb * TS);
+                    if constexpr (VAR) {
+                        // one term: hi*hi and hi*lo in one MMA of width 2N (B's hi rows are
+                        // followed by its lo rows), lo*hi in one of width N; the epilogue
+                        // adds the two halves
 #pragma unroll
-                for (int g = 0; g < G; g++) {
-                    const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
-                    const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
-                    const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[g][0]), LBO, SBO_B);
-                    const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[g][1]), LBO, SBO_B);
-                    tc::mma_bf16(d, ad_h, bd_h, idesc, g ? 1u : 0u);
-                    tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
-                    tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
-                }
-                // taps 16..23 of two source rows in one K = 16 MMA: K group 0 is group 2
-                // of row g, K group 1 group 2 of row g + 1 (the K-group stride is the
-                // distance between the two rows' operands)
+                        for (int g = 0; g < G; g++) {
+                            const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
+                            const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
+                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]), LBO, SBO_B);
+                            tc::mma_bf16(d, ad_h, bd, idesc2, g ? 1u : 0u);
+                            tc::mma_bf16(d, ad_l, bd, idesc, 1u);
+                        }
 #pragma unroll
-                for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
-                    const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                    const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                    const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
-                    const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[g][1]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
-                    tc::mma_bf16(d, ad_h, bd_h, idesc, 1u);
-                    tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
-                    tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
+                        for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
+                            const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                            const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
+                            tc::mma_bf16(d, ad_h, bd, idesc2, 1u);
+                            tc::mma_bf16(d, ad_l, bd, idesc, 1u);
+                        }
+                    } else {
+                    // taps u' = 0..15 of each source row: one K = 16 MMA per row (K groups 0, 1)
+#pragma unroll
+                    for (int g = 0; g < G; g++) {
+                        const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
+                        const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
+                        const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]), LBO, SBO_B);
+                        const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[bs][g][1]), LBO, SBO_B);
+                        tc::mma_bf16(d, ad_h, bd_h, idesc, g ? 1u : 0u);
+                        tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
+                        tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
+                    }
+                    // taps 16..23 of two source rows in one K = 16 MMA: K group 0 is group 2
+                    // of row g, K group 1 group 2 of row g + 1 (the K-group stride is the
+                    // distance between the two rows' operands)
+#pragma unroll
+                    for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
+                        const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                        const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
+                        const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
+                        const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[bs][g][1]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
+                        tc::mma_bf16(d, ad_h, bd_h, idesc, 1u);
+                        tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
+                        tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
+                    }
+                    }
+                    tc::commit(&S.empty[s]);
+                    tc::commit(&S.tfull[tb]);
+                    issued = gb;
                 }
-                tc::commit(&S.empty[s]);
-                tc::commit(&S.tfull[tb]);
-                issued = blk;
+                // this issuer's MMAs of the strip done: its B set may be rewritten (both
+                // issuers have blocks in every strip: a strip has at least 6)
+                if (VAR && run) tc::commit(&S.bfree[bs]);
             }
             // every issued MMA must land before TMEM is released (a commit
             // tracks all earlier MMAs of this thread, so its last one suffices)
@@ -289,127 +381,151 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
         }
         __syncwarp();
     } else if (warp < 4) {
-        // ---------------- epilogue: output column x0 + tid
-        const int m = tid, x = x0 + m;
-        const float xt = a.W > 1 ? (float)(2 * (x + a.ox) - (a.W - 1)) / (float)(a.W - 1) : 0.0f;
-        // yt = 2 (y + oy) / (H - 1) - 1; the background as B0 + B1 yt + B2 yt^2 with the
-        // x terms of this column folded into B0 and B1
-        const float ysc = a.H > 1 ? 2.0f / (float)(a.H - 1) : 0.0f;
+        // ---------------- epilogue: output column x0 + tid of each strip
+        const int m = tid;
+        const float ysc = a.H > 1 ? 2.0f / (float)(a.H - 1) : 0.0f;   // yt = 2 (y + oy) / (H - 1) - 1
         const float yof = a.H > 1 ? -1.0f : 0.0f;
-        float B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
-        if (a.nbg == 6) {
-            B0 = fmaf((float)a.bg[5], xt * xt, fmaf((float)a.bg[3], xt, (float)a.bg[0]));
-            B1 = fmaf((float)a.bg[4], xt, (float)a.bg[1]);
-            B2 = (float)a.bg[2];
-        } else if (a.nbg == 3) {
-            B0 = fmaf((float)a.bg[2], xt, (float)a.bg[0]);
-            B1 = (float)a.bg[1];
-        } else if (a.nbg == 1) {
-            B0 = (float)a.bg[0];
-        }
-        const bool xin = x >= R && x <= a.w - 1 - R;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        // p_k = xt^i yt^j: the xt^i factor is fixed for this column, so each T
-        // column enters the ring already multiplied by it and the ring keeps
-        // one sum per power of yt (NJ = degree + 1) instead of one per term
+        // p_k = xt^i yt^j: the xt^i factor is fixed for a column, so each T column
+        // enters the ring already multiplied by it and the ring keeps one sum per
+        // power of yt (NJ = degree + 1) instead of one per term
         constexpr int NJ = NK == 1 ? 1 : (NK == 3 ? 2 : 3);
         constexpr int RL = C::NJB;
-        const float xp[3] = {1.0f, xt, xt * xt};
-        float acc[RL][NJ];
-#pragma unroll
-        for (int i = 0; i < RL; i++)
-#pragma unroll
-            for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
-        // science values and flag words of the output rows of block blk (rows
-        // blk G - 2R + i) into slots row & (NQ - 1), one cp.async group per block (the
-        // pitch is a multiple of 16, so the flag byte sits at byte x & 3 of its word)
-        auto fetch = [&](int blk) {
-#pragma unroll
-            for (int i = 0; i < G; i++) {
-                const int eta = blk * G - 2 * R + i;
-                const bool in = eta >= 0 && eta < nout && x < a.w;
-                const long p = in ? (long)(y0 + eta) * a.pitch + x : 0;
-                const int slot = eta & (NQ - 1);
-                tc::cp_async4(&S.qI[slot][m], a.sci + p, in ? 4 : 0);
-                tc::cp_async4(&S.qF[slot][m], a.flags + (p & ~3L), in ? 4 : 0);
+        bool run = true;
+        int gb = 0;
+        for (int item = blockIdx.x; item < nitems && run; item += gridDim.x) {
+            int x0, y0, nout, nblk;
+            geom(item, x0, y0, nout, nblk);
+            const int x = x0 + m;
+            const float xt = a.W > 1 ? (float)(2 * (x + a.ox) - (a.W - 1)) / (float)(a.W - 1) : 0.0f;
+            // the background as B0 + B1 yt + B2 yt^2 with the x terms of this column
+            // folded into B0 and B1
+            float B0 = 0.0f, B1 = 0.0f, B2 = 0.0f;
+            if (VAR) {
+            } else if (a.nbg == 6) {
+                B0 = fmaf((float)a.bg[5], xt * xt, fmaf((float)a.bg[3], xt, (float)a.bg[0]));
+                B1 = fmaf((float)a.bg[4], xt, (float)a.bg[1]);
+                B2 = (float)a.bg[2];
+            } else if (a.nbg == 3) {
+                B0 = fmaf((float)a.bg[2], xt, (float)a.bg[0]);
+                B1 = (float)a.bg[1];
+            } else if (a.nbg == 1) {
+                B0 = (float)a.bg[0];
             }
-            tc::cp_async_commit();
-        };
-        const int fsh = 8 * (x & 3);
-        fetch(0);
-        fetch(1);
-        // ring index i holds output row blk G - 2R + i; block blk adds its column (i, k)
-        // at index i, after which indices 0 .. G-1 are complete and the ring shifts by G
-#pragma unroll 1
-        for (int blk = 0; blk < nblk; blk++) {
-            fetch(blk + 2);
-            const int tb = blk % NTB;
-            // lane 0 waits (fewer pollers on the barrier), the warp follows
-            bool ok = true;
-            if (lane == 0) ok = wait_or_abort(S, &S.tfull[tb], (blk / NTB) & 1, status);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc::fence_after();
-            constexpr int NCH = (C::NCOL + 15) / 16;   // 16-column chunks
+            const bool xin = x >= R && x <= a.w - 1 - R;
+            const float xp[3] = {1.0f, VAR ? 1.0f : xt, VAR ? 1.0f : xt * xt};
+            float acc[RL][NJ];
 #pragma unroll
-            for (int c3 = 0; c3 < NCH; c3 += 3) {
-                uint32_t r[3][16];
-#pragma unroll
-                for (int q = 0; q < 3; q++) {
-                    if (c3 + q < NCH) {
-                        tc::tmem_ld16_nowait(tl + (uint32_t)(tb * C::TSTRIDE + (c3 + q) * 16), r[q]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 16; j++) r[q][j] = 0u;
-                    }
-                }
-                tc::tmem_wait_ld(r[0], r[1], r[2]);
-#pragma unroll
-                for (int q = 0; q < 3; q++)
-#pragma unroll
-                    for (int j = 0; j < 16; j++) {
-                        const int n = (c3 + q) * 16 + j;
-                        if (n < C::NCOL) {
-                            const int jj = n / NK, k = n - jj * NK;
-                            // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
-                            const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
-                            const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
-                            acc[jj][tj] = fmaf(xp[ti], __uint_as_float(r[q][j]), acc[jj][tj]);
-                        }
-                    }
-            }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&S.tempty[tb]);
-            tc::cp_async_wait<2>();              // this block's science rows have landed
-#pragma unroll
-            for (int i = 0; i < G; i++) {
-                const int eta = blk * G - 2 * R + i;
-                if (eta >= 0 && eta < nout && x < a.w) {
-                    const int slot = eta & (NQ - 1);
-                    const float I = S.qI[slot][m];
-                    const uint32_t fl = (S.qF[slot][m] >> fsh) & 0xffu;
-                    const int y = y0 + eta;
-                    const float yt = fmaf((float)(y + a.oy), ysc, yof);
-                    // model = (acc0 + B0) + (acc1 + B1) yt + (acc2 + B2) yt^2
-                    float c2 = B2, c1 = B1;
-                    if constexpr (NJ > 2) c2 += acc[i][2];
-                    if constexpr (NJ > 1) c1 += acc[i][1];
-                    const float model = fmaf(fmaf(c2, yt, c1), yt, acc[i][0] + B0);
-                    const bool inner = xin && y >= R && y <= a.h - 1 - R && fl == 0;
-                    a.diff[(long)y * a.pitch + x] = inner ? I - model : 0.0f;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i + G < RL; i++)
-#pragma unroll
-                for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + G][j];
-#pragma unroll
-            for (int i = RL - G; i < RL; i++)
+            for (int i = 0; i < RL; i++)
 #pragma unroll
                 for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
-        }
-        tc::cp_async_wait<0>();
+            // science values and flag words of the output rows of block blk (rows
+            // blk G - 2R + i) into slots row & (NQ - 1), one cp.async group per block
+            // (the pitch is a multiple of 16, so the flag byte sits at byte x & 3 of its word)
+            auto fetch = [&](int blk) {
+#pragma unroll
+                for (int i = 0; i < G; i++) {
+                    const int eta = blk * G - 2 * R + i;
+                    const bool in = eta >= 0 && eta < nout && x < a.w;
+                    const long p = in ? (long)(y0 + eta) * a.pitch + x : 0;
+                    const int slot = eta & (NQ - 1);
+                    tc::cp_async4(&S.qI[slot][m], obs + p, in ? 4 : 0);
+                    tc::cp_async4(&S.qF[slot][m], a.flags + (p & ~3L), in ? 4 : 0);
+                }
+                tc::cp_async_commit();
+            };
+            const int fsh = 8 * (x & 3);
+            fetch(0);
+            fetch(1);
+            // ring index i holds output row blk G - 2R + i; block blk adds its column (i, k)
+            // at index i, after which indices 0 .. G-1 are complete and the ring shifts by G
+#pragma unroll 1
+            for (int blk = 0; blk < nblk; blk++, gb++) {
+                fetch(blk + 2);
+                const int tb = gb % NTB;
+                // lane 0 waits (fewer pollers on the barrier), the warp follows
+                bool ok = true;
+                if (lane == 0) ok = wait_or_abort(S, &S.tfull[tb], (gb / NTB) & 1, status);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) { run = false; break; }
+                tc::fence_after();
+                if constexpr (VAR) {
+                    // column j of the term is the sum of columns j and N + j
+                    constexpr int NCV = C::N / 16;
+#pragma unroll
+                    for (int c = 0; c < NCV; c++) {
+                        uint32_t r0[16], r1[16];
+                        tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + c * 16), r0);
+                        tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + C::N + c * 16), r1);
+                        tc::tmem_wait_ld(r0, r1);
+#pragma unroll
+                        for (int j = 0; j < 16; j++)
+                            if (c * 16 + j < C::NCOL)
+                                acc[c * 16 + j][0] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
+                    }
+                }
+                constexpr int NCH = VAR ? 0 : (C::NCOL + 15) / 16;   // 16-column chunks
+#pragma unroll
+                for (int c3 = 0; c3 < NCH; c3 += 3) {
+                    uint32_t r[3][16];
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        if (c3 + q < NCH) {
+                            tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + (c3 + q) * 16), r[q]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; j++) r[q][j] = 0u;
+                        }
+                    }
+                    tc::tmem_wait_ld(r[0], r[1], r[2]);
+#pragma unroll
+                    for (int q = 0; q < 3; q++)
+#pragma unroll
+                        for (int j = 0; j < 16; j++) {
+                            const int n = (c3 + q) * 16 + j;
+                            if (n < C::NCOL) {
+                                const int jj = n / NK, k = n - jj * NK;
+                                // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
+                                const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
+                                const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
+                                acc[jj][tj] = fmaf(xp[ti], __uint_as_float(r[q][j]), acc[jj][tj]);
+                            }
+                        }
+                }
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&S.tempty[tb]);
+                tc::cp_async_wait<2>();          // this block's science rows have landed
+#pragma unroll
+                for (int i = 0; i < G; i++) {
+                    const int eta = blk * G - 2 * R + i;
+                    if (eta >= 0 && eta < nout && x < a.w) {
+                        const int slot = eta & (NQ - 1);
+                        const float I = S.qI[slot][m];
+                        const uint32_t fl = (S.qF[slot][m] >> fsh) & 0xffu;
+                        const int y = y0 + eta;
+                        const float yt = fmaf((float)(y + a.oy), ysc, yof);
+                        // model = (acc0 + B0) + (acc1 + B1) yt + (acc2 + B2) yt^2
+                        float c2 = B2, c1 = B1;
+                        if constexpr (NJ > 2) c2 += acc[i][2];
+                        if constexpr (NJ > 1) c1 += acc[i][1];
+                        const float model = fmaf(fmaf(c2, yt, c1), yt, acc[i][0] + B0);
+                        const bool inner = xin && y >= R && y <= a.h - 1 - R && fl == 0;
+                        if (VAR) outp[(long)y * a.pitch + x] = inner ? I + acc[i][0] : 0.0f;
+                        else outp[(long)y * a.pitch + x] = inner ? I - model : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i + G < RL; i++)
+#pragma unroll
+                    for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + G][j];
+#pragma unroll
+                for (int i = RL - G; i < RL; i++)
+#pragma unroll
+                    for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
+            }
+            tc::cp_async_wait<0>();              // the zero-filled fetches past the strip land before
+        }                                        // the next strip's fetches reuse their slots
     }
     tc::fence_before();
     __syncthreads();
@@ -417,16 +533,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-template <int KS, int NK>
+template <int KS, int NK, bool VAR>
 int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
     // more than half the shared memory: one CTA per SM, which holds all 512 TMEM columns
-    size_t smem = sizeof(TcShared<KS, NK>) + 1024;
+    size_t smem = sizeof(TcShared<KS, NK, VAR>) + 1024;
     if (smem < 116 * 1024) smem = 116 * 1024;
-    if (cudaFuncSetAttribute(subtract_tc_kernel<KS, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(subtract_tc_kernel<KS, NK, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return ARGUS_ERR_CUDA;
-    dim3 grid((a.w + TCX - 1) / TCX, (a.h + TCY - 1) / TCY);
-    subtract_tc_kernel<KS, NK><<<grid, TC_THREADS, smem, st>>>(a, status); argus_count_launch(1);
+    const int nitems = ((a.w + TCX - 1) / TCX) * ((a.h + TCY - 1) / TCY);
+    // persistent: one CTA per SM walks the strips (the set-up once per SM)
+    int grid = nitems, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    if (grid > sms) grid = sms;
+    subtract_tc_kernel<KS, NK, VAR><<<grid, TC_THREADS, smem, st>>>(a, status); argus_count_launch(1);
     return argus_launch_status();
 }
 
@@ -436,14 +558,24 @@ int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
 // returns ARGUS_ERR_UNSUPPORTED for the others (the caller uses the SIMT body).
 int argus_subtract_tc(const SubArgs& a, int ksize, int nk, int* status, cudaStream_t st) {
     if (ksize == 21) {
-        if (nk == 1) return launch_tc<21, 1>(a, status, st);
-        if (nk == 3) return launch_tc<21, 3>(a, status, st);
-        if (nk == 6) return launch_tc<21, 6>(a, status, st);
+        if (nk == 1) return launch_tc<21, 1, false>(a, status, st);
+        if (nk == 3) return launch_tc<21, 3, false>(a, status, st);
+        if (nk == 6) return launch_tc<21, 6, false>(a, status, st);
     }
     if (ksize == 11) {
-        if (nk == 1) return launch_tc<11, 1>(a, status, st);
-        if (nk == 3) return launch_tc<11, 3>(a, status, st);
-        if (nk == 6) return launch_tc<11, 6>(a, status, st);
+        if (nk == 1) return launch_tc<11, 1, false>(a, status, st);
+        if (nk == 3) return launch_tc<11, 3, false>(a, status, st);
+        if (nk == 6) return launch_tc<11, 6, false>(a, status, st);
     }
+    return ARGUS_ERR_UNSUPPORTED;
+}
+
+// Difference variance on the tensor cores (the sum Kc^2 (x) V_ref, one variance tile
+// per CTA): for the kernel sizes it is built for and frame origins on the
+// VAR_TILE grid; ARGUS_ERR_UNSUPPORTED otherwise (the caller uses the SIMT kernel).
+int argus_subtract_var_tc(const SubArgs& a, int ksize, int* status, cudaStream_t st) {
+    if (a.ox % VAR_TILE || a.oy % VAR_TILE) return ARGUS_ERR_UNSUPPORTED;
+    if (ksize == 21) return launch_tc<21, 1, true>(a, status, st);
+    if (ksize == 11) return launch_tc<11, 1, true>(a, status, st);
     return ARGUS_ERR_UNSUPPORTED;
 }

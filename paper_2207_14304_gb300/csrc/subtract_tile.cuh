@@ -4,10 +4,10 @@
 // segment kernel (segments.cu).
 //
 //   D   = I - sum_k p_k(x,y) (R (x) K_k)(x,y) - sum_k bg_k p_k(x,y)
-//   V_D = V_I + (Kc^2 (x) V_ref)(x,y),  Kc the kernel at the 32x32 tile centre
+//   V_D = V_I + (Kc^2 (x) V_ref)(x,y),  Kc the kernel at the centre of the VAR_TILE tile
 //
-// One CTA owns one 32x32 output tile, which is also the variance tile, so the
-// squared tile-centre kernel is built once per tile.  The reference and its
+// One CTA owns one 32x32 output tile, which lies inside one variance tile, so
+// the squared tile-centre kernel is built once per CTA.  The reference and its
 // variance are staged with their halo in shared memory; each of the 128
 // threads computes a column strip of 8 outputs for all NK spatial terms.
 #pragma once
@@ -16,6 +16,10 @@
 namespace argus_sub {
 
 constexpr int TILE = 32;
+// The difference variance uses the kernel at the centre of the VAR_TILE x
+// VAR_TILE frame tile holding the pixel (a multiple of TILE, so the 32x32
+// output tiles nest in it).
+constexpr int VAR_TILE = 128;
 constexpr int ROWS_PER_THREAD = 8;
 constexpr int THREADS = 128;
 
@@ -89,8 +93,8 @@ __device__ __forceinline__ void subtract_tile(const SubArgs& a, const int tx0, c
     // squared kernel at the tile centre (frame coordinates)
     {
         float pc[ARGUS_MAX_TERMS];
-        const float xc = (float)(((tx0 + a.ox) / TILE) * TILE) + 0.5f * (TILE - 1);
-        const float yc = (float)(((ty0 + a.oy) / TILE) * TILE) + 0.5f * (TILE - 1);
+        const float xc = (float)(((tx0 + a.ox) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
+        const float yc = (float)(((ty0 + a.oy) / VAR_TILE) * VAR_TILE) + 0.5f * (VAR_TILE - 1);
         const float xt = a.W > 1 ? (2.0f * xc - (float)(a.W - 1)) / (float)(a.W - 1) : 0.0f;
         const float yt = a.H > 1 ? (2.0f * yc - (float)(a.H - 1)) / (float)(a.H - 1) : 0.0f;
         spatial_terms(xt, yt, a.sdeg, pc);
@@ -229,3 +233,6 @@ constexpr size_t tile_smem_bytes() {
 // Difference image on the tensor cores (subtract_tc.cu) for the kernel sizes it
 // is built for; ARGUS_ERR_UNSUPPORTED for the others.
 int argus_subtract_tc(const argus_sub::SubArgs& a, int ksize, int nk, int* status, cudaStream_t st);
+// Difference variance on the tensor cores for the kernel sizes and frame origins it
+// is built for; ARGUS_ERR_UNSUPPORTED for the others.
+int argus_subtract_var_tc(const argus_sub::SubArgs& a, int ksize, int* status, cudaStream_t st);
