@@ -46,11 +46,11 @@ BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
 # launch, scaled by pixels to the frame (the kernel streams its bands once, so traffic
 # grows in proportion).  It holds only for the kernel sources it was taken on (None
 # until a capture of these sources is recorded here).
-SUBTRACT_TRAFFIC = {"bytes_per_px": 11.5117, "sources_sha1": "e78e62998911e89f778bce7b3ac374ac26dcd870",
+SUBTRACT_TRAFFIC = {"bytes_per_px": 11.5141, "sources_sha1": "0d0f7188dc2ca7dab265bd2b8875f9d1be7c35af",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh")}
 # the same for the difference-variance kernel (V_I, V_ref and flags in, V_D out)
-VARIANCE_TRAFFIC = {"bytes_per_px": 11.6048, "sources_sha1": "f8e8d846eb6d56fe2398b1c7c5a7f8e414a5e7e0",
-                    "sources": ("subtract.cu", "subtract_tile.cuh")}
+VARIANCE_TRAFFIC = {"bytes_per_px": 11.5570, "sources_sha1": "d566ef6679a314d32918d72e157465423610fd63",
+                    "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh", "subtract.cu")}
 
 
 def traffic_bytes(rec):
@@ -301,10 +301,13 @@ def run_gpu(args):
     bands = [min(128, H - y0) for y0 in range(0, H, 128)]
     n_mma = 16 * (((KSIZE - 1 + 4) * nk + 15) // 16)
     k_row = 16 if KSIZE <= 16 else 24          # taps 16..23 of a row pair share one K = 16 MMA
-    executed = 3 * 2 * 128 * n_mma * k_row * ((W + 127) // 128) * sum(4 * ((b + KSIZE - 1 + 3) // 4) for b in bands)
+    src_rows = ((W + 127) // 128) * sum(4 * ((b + KSIZE - 1 + 3) // 4) for b in bands)
+    executed = 3 * 2 * 128 * n_mma * k_row * src_rows
+    # the variance: one term of width N1 = 16*ceil((KS-1+4)/16), MMAs of width 2 N1 (hi*hi, hi*lo)
+    # and N1 (lo*hi)
+    n1 = 16 * ((KSIZE - 1 + 4 + 15) // 16)
+    executed_var = 2 * 128 * 3 * n1 * k_row * src_rows
     tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    clk_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)   # sampled, else the maximum
-    alu_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12          # FP32 FMA lanes x 2 FLOP x clock
     var_tflops = 2 * KSIZE * KSIZE * W * H / (var_ms / 1e3) / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)
     step_s = tmax / args.steps
@@ -319,12 +322,13 @@ def run_gpu(args):
                         "algorithmic": f"{2 * nk * KSIZE * KSIZE} FLOP/px ({nk} spatial terms x {KSIZE}x{KSIZE} taps)",
                         "executed_tflops": round(executed / (tc_ms / 1e3) / 1e12, 1),
                         "kernel_ms": round(tc_ms, 4)},
-        "variance": {"bound": "alu", "kernel": "variance (tile-centre kernel squared (x) V_ref)",
-                     "achieved": round(var_tflops, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                     "frac": round(var_tflops / alu_peak, 4), "traffic": traffic_bytes(VARIANCE_TRAFFIC),
+        "variance": {"bound": "tensor", "kernel": "subtract_tc variance (tile-centre kernel squared (x) V_ref)",
+                     "achieved": round(var_tflops, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
+                     "frac": round(var_tflops / tensor_peak, 4), "traffic": traffic_bytes(VARIANCE_TRAFFIC),
                      "traffic_unit": "bytes per launch (ncu DRAM read+write)",
-                     "peak_source": f"derived: 152 SMs x 128 FP32 FMA/clk x 2 x {clk_mhz:.0f} MHz",
+                     "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
                      "algorithmic": f"{2 * KSIZE * KSIZE} FLOP/px ({KSIZE}x{KSIZE} squared taps)",
+                     "executed_tflops": round(executed_var / (var_ms / 1e3) / 1e12, 1),
                      "kernel_ms": round(var_ms, 4)},
     }
 
