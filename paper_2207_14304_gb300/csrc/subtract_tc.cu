@@ -55,7 +55,10 @@ constexpr int TKC = 32;                      // MMA K: taps u', padded
 constexpr int G = 4;                         // source rows per block
 constexpr int NCM = TCX / 8 + TKC / 8 - 1;   // distinct core matrices of one Hankel tile
 constexpr uint32_t A_BYTES = NCM * 128;      // one operand (hi or lo) of one source row
-constexpr int NSB = 3;                       // block stages of A
+// block stages of A: three for the difference image; two for the variance, whose
+// CTAs run two per SM (see launch_tc)
+template <bool VAR>
+__host__ __device__ constexpr int nsb() { return VAR ? 2 : 3; }
 constexpr int NSRC = 4 * G;                  // fp32 source-row ring: four blocks
 constexpr int NBUILD = NCM * 8;              // one producer thread per stored operand row
 constexpr int PCH = 11;                      // 16-byte chunks of a producer warp's window (32 + 7 values + offset)
@@ -85,12 +88,12 @@ struct TcCfg {
 template <int KS, int NK, bool VAR>
 struct TcShared {
     uint8_t b[VAR ? 2 : 1][G][2][TcCfg<KS, NK>::B_BYTES];   // B_g, hi and lo (VAR: one set per strip parity)
-    uint8_t ahi[NSB][G][A_BYTES];
-    uint8_t alo[NSB][G][A_BYTES];
+    uint8_t ahi[nsb<VAR>()][G][A_BYTES];
+    uint8_t alo[nsb<VAR>()][G][A_BYTES];
     alignas(16) float wsrc[NPW][NSRC][PWIN];    // each producer warp's staged source windows
     alignas(16) float qI[NQ][TCX];              // science values of output rows, by row & (NQ - 1)
     alignas(16) uint32_t qF[NQ][TCX];           // the 32-bit word holding each output pixel's flag byte
-    uint64_t filled[NSB], empty[NSB], tfull[NTB], tempty[NTB];
+    uint64_t filled[nsb<VAR>()], empty[nsb<VAR>()], tfull[NTB], tempty[NTB];
     uint64_t bready[2], bfree[2];               // VAR: B set written / no longer read by the MMAs
     uint32_t tmem;
     int abort;       // set by any role that timed out
@@ -137,9 +140,10 @@ __device__ __forceinline__ bool wait_or_abort(SH& S, uint64_t* bar, uint32_t par
 // kernel at the centre of the CTA's VAR_TILE x VAR_TILE variance tile (one term),
 // V_D = V_I + that sum; the CTA's strip then has to lie in one variance tile.
 template <int KS, int NK, bool VAR>
-__global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, int* status) {
+__global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(SubArgs a, int* status) {
     using C = TcCfg<KS, NK>;
     using Sh = TcShared<KS, NK, VAR>;
+    constexpr int NSB = nsb<VAR>();
     static_assert(!VAR || NK == 1, "the variance convolution has one term");
     static_assert(TCX == VAR_TILE && TCY == VAR_TILE, "one variance tile per strip");
     const float* src_img = VAR ? a.ref_var : a.ref;   // convolved image
@@ -219,7 +223,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tc::tmem_alloc(&S.tmem, 512);
+    constexpr uint32_t TMEM_COLS = VAR ? 256 : 512;   // the variance: two CTAs per SM share TMEM
+    if (warp == 0) tc::tmem_alloc(&S.tmem, TMEM_COLS);
     tc::fence_proxy_async();   // B tiles written through the generic proxy
     tc::fence_before();
     __syncthreads();
@@ -530,14 +535,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) subtract_tc_kernel(SubArgs a, i
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 template <int KS, int NK, bool VAR>
 int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
-    // more than half the shared memory: one CTA per SM, which holds all 512 TMEM columns
+    // the difference image: more than half the shared memory, so one CTA per SM, which
+    // holds all 512 TMEM columns; the variance: two CTAs per SM with 256 columns each
     size_t smem = sizeof(TcShared<KS, NK, VAR>) + 1024;
-    if (smem < 116 * 1024) smem = 116 * 1024;
+    if (!VAR && smem < 116 * 1024) smem = 116 * 1024;
+    if (VAR && smem > 113 * 1024) return ARGUS_ERR_UNSUPPORTED;
     if (cudaFuncSetAttribute(subtract_tc_kernel<KS, NK, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return ARGUS_ERR_CUDA;
@@ -547,7 +554,7 @@ int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return ARGUS_ERR_CUDA;
-    if (grid > sms) grid = sms;
+    if (grid > (VAR ? 2 : 1) * sms) grid = (VAR ? 2 : 1) * sms;
     subtract_tc_kernel<KS, NK, VAR><<<grid, TC_THREADS, smem, st>>>(a, status); argus_count_launch(1);
     return argus_launch_status();
 }
