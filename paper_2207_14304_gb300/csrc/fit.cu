@@ -858,8 +858,12 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double* L, int ld, int 
         }
     }
     if (lane < pb) {
-        if (ident) Dinv[lane * CB + (row - rest)] = x;
-        else Li[lane] = x;
+        if (ident) {
+            Dinv[lane * CB + (row - rest)] = x;
+        } else {
+            Li[lane] = x;
+            L[(long)(p + lane) * ld + (p + pb + row)] = x;   // mirrored into the upper triangle for the backward solve
+        }
     }
     if (ident && lane >= pb) Dinv[lane * CB + (row - rest)] = 0.0;
     if (ident && row - rest == pb - 1) {
@@ -905,7 +909,8 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // CTA of 32 warps: per 32-row block, warp w forms row w's remainder
 // (rhs minus the already solved blocks) and then the block's solution is the
 // product with the stored inverse of its diagonal block.  Forward with L,
-// backward with L^T.  Skips when flag[0] or flag[1] is set.
+// backward with L^T, read by rows from the upper triangle where the panel
+// kernel mirrors L's off-diagonal blocks.  Skips when flag[0] or flag[1] is set.
 __global__ void __launch_bounds__(1024) tri_solve_kernel(const double* L, int ld, int n, const double* Dinv,
                                                          const double* rhs, int rs, double* x, const double* flag) {
     extern __shared__ double ts[];   // y [n], then x [n]
@@ -935,7 +940,8 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const double* L, int ld
         const int i = p * CB + warp;
         double t = 0.0;
         if (i < n) {
-            for (int k = (p + 1) * CB + lane; k < n; k += 32) t += L[(long)k * ld + i] * xs[k];
+            const double* Ui = L + (long)i * ld;   // row i of L^T (the mirrored upper triangle)
+            for (int k = (p + 1) * CB + lane; k < n; k += 32) t += Ui[k] * xs[k];
             t = warp_sum_d(t);
         }
         if (lane == 0) tt[warp] = i < n ? y[i] - t : 0.0;
@@ -1598,7 +1604,8 @@ int argus_basis_prepare(argus_ctx* ctx, const argus_basis* b, cudaStream_t st) {
     return rc;
 }
 
-// Factor M[0:n,0:n] (ld) into ctx->L, keeping the inverses of its diagonal blocks in ctx->Dinv; flag = vec row 7.
+// Factor M[0:n,0:n] (ld) into ctx->L (lower triangle; the off-diagonal blocks also mirrored
+// into the upper triangle), keeping the inverses of its diagonal blocks in ctx->Dinv; flag = vec row 7.
 int argus_cholesky_solve_prepare(argus_ctx* ctx, const double* M, int ld, int n, cudaStream_t st) {
     double* flag = ctx->vec + 7 * (size_t)ctx->np_cols;
     double* rdiag = ctx->vec + 6 * (size_t)ctx->np_cols;
