@@ -46,10 +46,10 @@ BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
 # launch, scaled by pixels to the frame (the kernel streams its bands once, so traffic
 # grows in proportion).  It holds only for the kernel sources it was taken on (None
 # until a capture of these sources is recorded here).
-SUBTRACT_TRAFFIC = {"bytes_per_px": 11.5141, "sources_sha1": "0d0f7188dc2ca7dab265bd2b8875f9d1be7c35af",
+SUBTRACT_TRAFFIC = {"bytes_per_px": 11.5154, "sources_sha1": "536df032bb20ae0c62729b277def8fd5a9a4b1b7",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh")}
 # the same for the difference-variance kernel (V_I, V_ref and flags in, V_D out)
-VARIANCE_TRAFFIC = {"bytes_per_px": 11.5570, "sources_sha1": "d566ef6679a314d32918d72e157465423610fd63",
+VARIANCE_TRAFFIC = {"bytes_per_px": 11.6997, "sources_sha1": "96a37579244ae1c0ee90a6fdf10f351af3ee8208",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh", "subtract.cu")}
 
 
