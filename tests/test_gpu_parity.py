@@ -122,6 +122,36 @@ def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
         B.argus_destroy(ctx)
 
 
+@pytest.mark.parametrize("ox,oy", [(128, 256), (32, 64)])
+def test_subtract_sub_rectangle_of_a_frame(ora, ox, oy):
+    """A 260x190 rectangle at (ox, oy) of a 768x640 frame: spatial terms and variance tiles in
+    frame coordinates; (128, 256) takes the tensor-core variance, (32, 64) the FP32 one."""
+    ks, sdeg, bgdeg, w, h, W, H = 21, 2, 2, 260, 190, 768, 640
+    R, I, Vi, Vr, fl, K, bg = _subtract_case(ora, ks, sdeg, bgdeg, w, h, seed=ox + oy)
+    Do, Vo = ora.subtract(I, Vi, R, Vr, fl, K.astype(np.float64), bg, sdeg=sdeg, bgdeg=bgdeg,
+                          frame=(W, H), origin=(ox, oy))
+    Kabs = np.abs(K).sum(0, keepdims=True).astype(np.float64)
+    Cabs, _ = ora.subtract(np.zeros_like(I), Vi, np.abs(R), Vr, fl, Kabs, [0.0], sdeg=0, bgdeg=0,
+                           with_var=False)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        dI, dVi, dR, dVr, dfl = (dev_pitched(a) for a in (I, Vi, R, Vr, fl))
+        dK = torch.from_numpy(K.reshape(-1)).cuda()
+        dbg = torch.from_numpy(np.asarray(bg, np.float64)).cuda()
+        D = torch.full((h, pitch), -9.0, device="cuda")
+        VD = torch.full((h, pitch), -9.0, device="cuda")
+        B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, B.argus_shape(w, h, pitch), W, H, ox, oy, ks, sdeg, dK,
+                         bgdeg, dbg, D, VD)
+        torch.cuda.synchronize()
+        Dg, Vg = host(D, w), host(VD, w)
+        scale = np.maximum(np.maximum(np.abs(I), -Cabs), 1.0)
+        assert assert_rel(Dg, Do, scale, 1e-4, "D") < 1e-5
+        assert_rel(Vg, Vo, np.maximum(Vo, 1e-6), 1e-5, "V_D")
+    finally:
+        B.argus_destroy(ctx)
+
+
 @pytest.mark.parametrize("ks,sdeg", [(21, 2), (15, 1)])
 def test_subtract_split_calls(ora, ks, sdeg):
     """Variance-only and difference-only calls give the combined call's outputs bit for bit."""

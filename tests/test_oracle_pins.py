@@ -366,6 +366,34 @@ def test_difference_variance_matches_empirical_noise(ora):
     assert abs(inner.var() / Vd[5:-5, 5:-5].mean() - 1) < 0.01
 
 
+def test_difference_variance_tile_centre_kernel(ora):
+    """Spatially varying kernel: V_D in each 128x128 tile is V_I plus V_ref convolved with the
+    square of the kernel taken at the tile centre (c = 128 t + 63.5), checked per quadrant against
+    the library convolution; var_tile = 1 is the per-pixel kernel."""
+    w = h = 256
+    rng = np.random.default_rng(9)
+    K = rng.normal(size=(6, 5, 5)) * np.array([1.0, 0.3, 0.2, 0.3, 0.1, 0.2])[:, None, None]
+    Vi = rng.uniform(1, 5, size=(h, w)).astype(np.float32)
+    Vr = rng.uniform(0, 3, size=(h, w)).astype(np.float32)
+    z = np.zeros((h, w), np.float32)
+    _, Vd = ora.subtract(z, Vi, z, Vr, np.zeros((h, w), np.uint8), K, [0.0], sdeg=2, bgdeg=0)
+
+    def kc(xc, yc):
+        xt, yt = (2 * xc - (w - 1)) / (w - 1), (2 * yc - (h - 1)) / (h - 1)
+        pk = [xt ** i * yt ** j for i in range(3) for j in range(3 - i)]
+        return sum(pk[k] * K[k] for k in range(6))
+    for ty in range(2):
+        for tx in range(2):
+            want = Vi.astype(np.float64) + _conv(Vr.astype(np.float64), kc(128 * tx + 63.5, 128 * ty + 63.5) ** 2)
+            ys, xs = slice(max(2, 128 * ty), min(h - 2, 128 * ty + 128)), slice(max(2, 128 * tx), min(w - 2, 128 * tx + 128))
+            np.testing.assert_allclose(Vd[ys, xs], want[ys, xs], rtol=1e-11)
+    xy = np.array([[40, 200], [130, 10]], np.int32)
+    _, V1 = ora.subtract_at(xy, z, Vi, z, Vr, np.zeros((h, w), np.uint8), K, [0.0], sdeg=2, bgdeg=0, var_tile=1)
+    for (x, y), v in zip(xy, V1):
+        want = float(Vi[y, x]) + float((_conv(Vr.astype(np.float64), kc(float(x), float(y)) ** 2))[y, x])
+        assert abs(v - want) < 1e-9 * want
+
+
 # --------------------------------------------------------------------------- detect
 def test_detect_spike_connectivity_and_order(ora):
     w, h = 40, 30
