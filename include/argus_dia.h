@@ -203,9 +203,10 @@ int argus_expand_kernel(argus_ctx *ctx, const argus_basis *basis, const double *
  * difference only; diff NULL: the variance only (sci and ref are then not
  * read); not both.  For 11x11 and 21x21 kernels D is computed on the tensor
  * cores (BF16 hi/lo operands, three products, FP32 accumulation; relative
- * error ~1e-6 of the convolved flux), the variance and other sizes in FP32
- * on the CUDA cores.  A stalled tensor-core pipeline latches
- * ARGUS_ERR_TIMEOUT. */
+ * error ~1e-6 of the convolved flux), and so is the variance when ox and oy
+ * are multiples of 128 (one variance tile per 128x128 work strip); the
+ * variance otherwise and the other kernel sizes run in FP32 on the CUDA
+ * cores.  A stalled tensor-core pipeline latches ARGUS_ERR_TIMEOUT. */
 int argus_subtract(argus_ctx *ctx, const float *sci, const float *sci_var, const float *ref,
                    const float *ref_var, const uint8_t *flags, argus_shape shape, int frame_w,
                    int frame_h, int ox, int oy, int ksize, int spatial_degree, const float *K,
