@@ -964,8 +964,8 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const double* L, int ld
 // [NP + 4] are reduced in a fixed order.
 constexpr int RT = 256;
 
-__global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const double* a, const double* flag, int want_r,
-                                                   double* part) {
+__global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const float* rw, const double* a, const double* flag,
+                                                   int want_r, double* part) {
     extern __shared__ __align__(16) float rsm[];   // Xs[nb][RT], Gk[Ks + Kb][RT]
     __shared__ float af[1024];
     __shared__ double wchi[RT / 32], wn[RT / 32];
@@ -981,30 +981,38 @@ __global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const double* a, 
     __syncthreads();
     for (long base = (long)blockIdx.x * RT; base < nrows; base += (long)gridDim.x * RT) {
         const long rho = base + tid;
-        float m[META];
-        row_meta(g, rho, nrows, m);
-        const bool use = m[0] != 0.0f;
+        // the row's weights from the per-fit table: sqrt(w) p_k, sqrt(w) pb_k, sqrt(w) I
+        // (all zero for unweighted rows; p_0 = 1, so o[0] = sqrt(w))
+        float o[RMETA];
+        if (rho < nrows) {
+            const float4* src = reinterpret_cast<const float4*>(rw + rho * RMETA);
+#pragma unroll
+            for (int q = 0; q < 4; q++) *reinterpret_cast<float4*>(o + 4 * q) = __ldg(src + q);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RMETA; q++) o[q] = 0.0f;
+        }
+        const bool use = o[0] > 0.0f;
         const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
-        float model = 0.0f;
+        float model = 0.0f;   // sqrt(w) times the model
         for (int n = 0; n < g.nb; n++) {
             const float xv = use ? __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix) : 0.0f;
             Xs[n * RT + tid] = xv;
             float qn;
             if (n == 0) {
-                qn = af[0];
+                qn = af[0] * o[0];
             } else {
                 qn = 0.0f;
-                for (int k = 0; k < g.Ks; k++) qn = fmaf(m[4 + k], af[1 + (n - 1) * g.Ks + k], qn);
+                for (int k = 0; k < g.Ks; k++) qn = fmaf(o[k], af[1 + (n - 1) * g.Ks + k], qn);
             }
             model = fmaf(xv, qn, model);
         }
-        for (int k = 0; k < g.Kb; k++) model = fmaf(m[10 + k], af[nx + k], model);
-        const float e = use ? m[3] - model : 0.0f;
-        const float we = m[2] * e;
-        chi += (double)we * (double)e;
+        for (int k = 0; k < g.Kb; k++) model = fmaf(o[6 + k], af[nx + k], model);
+        const float ew = use ? o[12] - model : 0.0f;   // sqrt(w) (I - model)
+        chi += (double)ew * (double)ew;
         cnt += use ? 1.0 : 0.0;
-        for (int k = 0; k < g.Ks; k++) Gk[k * RT + tid] = we * m[4 + k];
-        for (int k = 0; k < g.Kb; k++) Gk[(g.Ks + k) * RT + tid] = we * m[10 + k];
+        for (int k = 0; k < g.Ks; k++) Gk[k * RT + tid] = ew * o[k];
+        for (int k = 0; k < g.Kb; k++) Gk[(g.Ks + k) * RT + tid] = ew * o[6 + k];
         __syncthreads();
         if (want_r) {
 #pragma unroll
@@ -1756,12 +1764,12 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
     const int rr_blocks = (n + 2 + 7) / 8;
     for (int it = 0; it < REFINE_MAX; it++) {
-        resid_kernel<<<nparts, RT, rsmem, st>>>(g, c, flag, 1, ctx->resid_part); argus_count_launch(1);
+        resid_kernel<<<nparts, RT, rsmem, st>>>(g, ctx->rowmeta, c, flag, 1, ctx->resid_part); argus_count_launch(1);
         resid_reduce_kernel<<<rr_blocks, 256, 0, st>>>(ctx->resid_part, nparts, NP, n, rv, it == 0 ? chi0 : chiw, flag, 1); argus_count_launch(1);
         argus_tri_solve(ctx, NP, n, rv, 1, dl, st);
         refine_update_kernel<<<1, 256, 0, st>>>(c, dl, n, flag); argus_count_launch(1);
     }
-    resid_kernel<<<nparts, RT, rsmem, st>>>(g, c, flag, 0, ctx->resid_part); argus_count_launch(1);
+    resid_kernel<<<nparts, RT, rsmem, st>>>(g, ctx->rowmeta, c, flag, 0, ctx->resid_part); argus_count_launch(1);
     resid_reduce_kernel<<<rr_blocks, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, chif, flag, 0); argus_count_launch(1);
     finalize_kernel<<<1, 256, 0, st>>>(d, c, ctx->basis_S, flag, chi0, chif, max_stamps, n_stamps, centers, stamp,
                                        shape.w, shape.h, precision, coeffs, stats); argus_count_launch(1);
