@@ -197,6 +197,11 @@ def run_gpu(args):
     pipe = FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, precision=args.precision,
                          psf_sigma=1.8, device=local)
     pitch = pipe.pitch
+    # frames in flight: each has its own pipeline (buffers and library context) and stream,
+    # so one frame's latency-bound fit overlaps the next frame's calibration and selection
+    nfl = max(1, args.frames_in_flight)
+    pipes = [pipe] + [FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, precision=args.precision,
+                                    psf_sigma=1.8, device=local) for _ in range(nfl - 1)]
 
     def pad(a):
         t = torch.zeros((H, pitch), dtype=a.dtype, device=device)
@@ -232,10 +237,12 @@ def run_gpu(args):
     for i, k in enumerate(["calibrate", "select_stamps", "fit", "subtract", "detect"]):
         stage[k] = round(evs[i].elapsed_time(evs[i + 1]), 4)
 
-    # timed region: K steps, subtract kernel bracketed by events on its stream
-    var_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sub_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    sub_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    streams = [stream] + [torch.cuda.Stream(device) for _ in range(nfl - 1)]
+    for p, s in zip(pipes[1:], streams[1:]):   # warm the other pipelines too
+        p.run(d_raw, calib, d_R, d_Vr, s)
+    torch.cuda.synchronize(device)
+
+    # timed region: K steps, frame i on pipeline and stream i mod nfl
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local, os.path.join(tempfile.gettempdir(), f"argus_clocks_rank{rank}_{os.getpid()}.csv")) \
@@ -244,7 +251,40 @@ def run_gpu(args):
     torch.cuda.synchronize(device)
     n0 = B.argus_launch_count()
     t0.record(stream)
+    for s in streams[1:]:
+        s.wait_event(t0)
     for i in range(args.steps):
+        p, s = pipes[i % nfl], streams[i % nfl]
+        p.calibrate(d_raw, calib, s)
+        p.select_stamps(d_R, s)
+        p.fit(d_R, s)
+        p.subtract_variance(d_Vr, s)
+        p.subtract_difference(d_R, d_Vr, s)
+        p.detect(s)
+    for s in streams[1:]:
+        stream.wait_stream(s)
+    t1.record(stream)
+    torch.cuda.synchronize(device)
+    launches = B.argus_launch_count() - n0
+    barrier(dist, device)
+    clk = clocks.stop() if clocks else None
+    elapsed = t0.elapsed_time(t1) / 1e3
+    for p in pipes:
+        st = p.status(stream)
+        if st != 0:
+            raise RuntimeError(f"device status {st} ({B.status_string(st)}) in the timed region")
+    mpix = W * H / 1e6
+    value, tmax = aggregate(mpix * args.steps, elapsed, dist, device)
+
+    # the two subtraction kernels timed on their own: the same steps on one stream (with
+    # frames in flight their launches share the GPU with the next frame's work), events
+    # around each kernel on its stream
+    kk = max(5, args.steps // 4)
+    var_s = [torch.cuda.Event(enable_timing=True) for _ in range(kk)]
+    sub_s = [torch.cuda.Event(enable_timing=True) for _ in range(kk)]
+    sub_e = [torch.cuda.Event(enable_timing=True) for _ in range(kk)]
+    torch.cuda.synchronize(device)
+    for i in range(kk):
         pipe.calibrate(d_raw, calib, stream)
         pipe.select_stamps(d_R, stream)
         pipe.fit(d_R, stream)
@@ -254,36 +294,36 @@ def run_gpu(args):
         pipe.subtract_difference(d_R, d_Vr, stream)
         sub_e[i].record(stream)
         pipe.detect(stream)
-    t1.record(stream)
     torch.cuda.synchronize(device)
-    launches = B.argus_launch_count() - n0
-    barrier(dist, device)
-    clk = clocks.stop() if clocks else None
-    elapsed = t0.elapsed_time(t1) / 1e3
-    st = pipe.status(stream)
-    if st != 0:
-        raise RuntimeError(f"device status {st} ({B.status_string(st)}) in the timed region")
-    mpix = W * H / 1e6
-    value, tmax = aggregate(mpix * args.steps, elapsed, dist, device)
-    tc_ms = statistics.mean(sub_s[i].elapsed_time(sub_e[i]) for i in range(args.steps))
-    var_ms = statistics.mean(var_s[i].elapsed_time(sub_s[i]) for i in range(args.steps))
+    tc_ms = statistics.mean(sub_s[i].elapsed_time(sub_e[i]) for i in range(kk))
+    ktiming = f"CUDA events around the launch on its stream, mean of {kk} steps of the workload on one stream"
+    var_ms = statistics.mean(var_s[i].elapsed_time(sub_s[i]) for i in range(kk))
 
     # end to end through the public API: pinned host raw frame in, detection list out
     raw_host = d_raw.cpu().pin_memory()
-    out_host = torch.empty(pipe.sources.numel(), dtype=torch.uint8).pin_memory()
-    nf_host = torch.empty(4, dtype=torch.int32).pin_memory()
+    d_raws = [d_raw] + [torch.empty_like(d_raw) for _ in range(nfl - 1)]
+    out_host = [torch.empty(pipe.sources.numel(), dtype=torch.uint8).pin_memory() for _ in range(nfl)]
+    nf_hosts = [torch.empty(4, dtype=torch.int32).pin_memory() for _ in range(nfl)]
     ke = max(3, args.steps // 4)
     barrier(dist, device)
     torch.cuda.synchronize(device)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(ke):
-        d_raw.copy_(raw_host, non_blocking=True)
-        pipe.run(d_raw, calib, d_R, d_Vr, stream)
-        nf_host.copy_(pipe.n_found, non_blocking=True)
-        out_host.copy_(pipe.sources, non_blocking=True)
+    for s in streams[1:]:
+        s.wait_event(e0)
+    for i in range(ke):
+        j = i % nfl
+        p, s = pipes[j], streams[j]
+        with torch.cuda.stream(s):
+            d_raws[j].copy_(raw_host, non_blocking=True)
+            p.run(d_raws[j], calib, d_R, d_Vr, s)
+            nf_hosts[j].copy_(p.n_found, non_blocking=True)
+            out_host[j].copy_(p.sources, non_blocking=True)
+    for s in streams[1:]:
+        stream.wait_stream(s)
     e1.record(stream)
+    nf_host = nf_hosts[(ke - 1) % nfl]
     torch.cuda.synchronize(device)
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e_value, _ = aggregate(mpix * ke, e2e_s, dist, device)
@@ -321,7 +361,7 @@ def run_gpu(args):
                         "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
                         "algorithmic": f"{2 * nk * KSIZE * KSIZE} FLOP/px ({nk} spatial terms x {KSIZE}x{KSIZE} taps)",
                         "executed_tflops": round(executed / (tc_ms / 1e3) / 1e12, 1),
-                        "kernel_ms": round(tc_ms, 4)},
+                        "kernel_ms": round(tc_ms, 4), "kernel_timing": ktiming},
         "variance": {"bound": "tensor", "kernel": "subtract_tc variance (tile-centre kernel squared (x) V_ref)",
                      "achieved": round(var_tflops, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
                      "frac": round(var_tflops / tensor_peak, 4), "traffic": traffic_bytes(VARIANCE_TRAFFIC),
@@ -329,7 +369,7 @@ def run_gpu(args):
                      "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
                      "algorithmic": f"{2 * KSIZE * KSIZE} FLOP/px ({KSIZE}x{KSIZE} squared taps)",
                      "executed_tflops": round(executed_var / (var_ms / 1e3) / 1e12, 1),
-                     "kernel_ms": round(var_ms, 4)},
+                     "kernel_ms": round(var_ms, 4), "kernel_timing": ktiming},
     }
 
     var = {}
@@ -356,7 +396,7 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args.precision),
+        "config": {**workload_config(args.precision), "frames_in_flight": nfl},
         # the dominant kernel of the step (the larger of the two subtraction kernels)
         "roofline": dict(kernels["subtract_tc"] if tc_ms >= var_ms else kernels["variance"]),
         "kernels": kernels,
@@ -365,7 +405,7 @@ def run_gpu(args):
         "stage_ms": stage, "subtract_ms": round(tc_ms + var_ms, 4),
         "subtract_detect_mpix_s": round(W * H / 1e6 / ((stage["subtract"] + stage["detect"]) / 1e3), 1),
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(raw_host.numel() * 2),
-                "d2h_bytes_per_step": int(out_host.numel() + nf_host.numel() * 4)},
+                "d2h_bytes_per_step": int(out_host[0].numel() + nf_host.numel() * 4)},
         "gpu_launches": int(launches), "sources_last_frame": n_found,
         "variants": var, "clocks": clk,
     }
@@ -659,6 +699,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--band-rows", type=int, default=48)
+    ap.add_argument("--frames-in-flight", type=int, default=2,
+                    help="frames processed concurrently, each on its own pipeline and stream")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
