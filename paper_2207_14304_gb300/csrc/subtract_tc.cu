@@ -10,18 +10,24 @@
 //   A_g[m][u'] = R(x0 + m - r + u', rho0 + g)          (a Hankel matrix, u' < 32),
 //   B_g[u'][(j, k)] = K_k[j - g][KS - 1 - u']          (zero unless 0 <= j - g < KS),
 // tcgen05 MMAs of M = 128, N = (KS - 1 + G) * NK (144 for a 21 x 21 kernel of
-// degree 2): K = 16 per row for taps 0..15, and one K = 16 MMA per row pair for
-// taps 16..23, whose K groups are taken from the two rows' operands.  Column (j, k) is the contribution of the block
-// to output row rho0 - 2r + j for term k: shifting B by g rows of taps makes the
-// four source rows land on the columns of the output rows they feed, so the
-// MMAs do part of the sum over iv and the epilogue reads 36 instead of 126
-// columns per source row.  The epilogue warps add T into a ring of KS - 1 + G
-// pending output rows (one register set per row and power of y: the x powers
-// are folded in as each column is added), then output rows rho0 - 2r ..
-// rho0 - 2r + 3 are complete and the ring shifts by G.  Operands are BF16 hi/lo
-// pairs (v = hi + lo, each rounded to nearest) and every product is hi*hi +
-// hi*lo + lo*hi, accumulated in FP32 in TMEM: the dropped lo*lo term is below
-// 2^-16 relative, well inside FP32-level agreement.
+// degree 2): K = 16 per row for taps 0..15, and one K = 16 MMA per row pair
+// for taps 16..23, whose K groups are taken from the two rows' operands.
+// Column (j, k) is the contribution of the block to output row rho0 - 2r + j
+// for term k: shifting B by g rows of taps makes the four source rows land on
+// the columns of the output rows they feed, so the MMAs do part of the sum
+// over iv and the epilogue reads 36 instead of 126 columns per source row.
+// The epilogue warps add T into a ring of KS - 1 + G pending output rows (one
+// register set per row and power of y: the x powers are folded in as each
+// column is added), then output rows rho0 - 2r .. rho0 - 2r + 3 are complete
+// and the ring shifts by G.  Operands are BF16 hi/lo pairs (v = hi + lo, each
+// rounded to nearest) and every product is hi*hi + hi*lo + lo*hi, accumulated
+// in FP32 in TMEM: the dropped lo*lo term is below 2^-16 relative, well
+// inside FP32-level agreement.
+//
+// The same kernel with one term (VAR) computes the convolution of the
+// difference variance, sum Kc^2 (x) V_ref, with Kc the kernel at the centre of
+// the strip's 128 x 128 variance tile: A from V_ref, B_g from Kc^2 (rebuilt per
+// strip into one of two sets), V_D = V_I + the sum.
 //
 // A is stored once per source row as its 19 distinct core matrices: in the
 // canonical no-swizzle K-major layout the core matrix of row group i and K
@@ -30,17 +36,18 @@
 // stride (both 128 bytes) and 16-byte row t of the stored operand is simply
 // R(x0 - r + t + b), b = 0..7.
 //
-// CTA: 128 columns x a band of TCY output rows, streaming the band's
-// TCY + 2r source rows in blocks of G.  Warps 0-3: epilogue, one output
-// column per thread and TMEM lane.  Science values and flag words reach
-// shared memory by cp.async two blocks ahead, each thread fetching its own
-// column.  Warps 4-8: producers, each warp on its own (it stages its window
-// of the source rows by 16-byte cp.async two blocks ahead, writes its 32 rows
-// of the A operands of a block, splitting each value into hi/lo where it is
-// used, and arrives on the stage's barrier; NSB block stages).  Warps 9-10:
-// one thread each issues the MMAs of alternate blocks.
-// TMEM holds NTB accumulators.  Every wait is bounded; a timeout latches
-// ARGUS_ERR_TIMEOUT and all roles stop.
+// Persistent CTAs walk the strips of 128 columns x a band of TCY output rows,
+// streaming each band's TCY + 2r source rows in blocks of G (the difference
+// image: one CTA of 352 threads per SM; the variance: two).  Warps 0-3:
+// epilogue, one output column per thread and TMEM lane; science values and
+// flag words reach shared memory by cp.async two blocks ahead, each thread
+// fetching its own column.  Warps 4-8: producers, each warp on its own (it
+// stages its window of the source rows by 16-byte cp.async two blocks ahead,
+// writes its 32 rows of the A operands of a block, splitting each value into
+// hi/lo where it is used, and arrives on the stage's barrier).  Warps 9-10: one
+// thread each issues the MMAs of alternate blocks.  TMEM holds NTB
+// accumulators.  Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and
+// all roles stop.
 #include <cuda_bf16.h>
 
 #include "subtract_tile.cuh"
