@@ -295,8 +295,8 @@ int argus_segments_items(const argus_seg_plan *plan, int *n_fit_items, int *n_su
 int argus_segments_kernels(const argus_seg_plan *plan, float *K, double *bg, argus_stream stream);
 
 /* ---------------------------------------------------------------------------
- * Learned kernel surrogate (the benchmark spec's learned part; the paper has no
- * counterpart).  A CNN maps a stamp pair (science and reference, 21x21, both
+ * Learned kernel surrogate (a learned stand-in for the least-squares kernel
+ * fit, with the fit kept as fallback and judge; the paper has no counterpart).  A CNN maps a stamp pair (science and reference, 21x21, both
  * divided by the reference stamp sum) to a 21x21 kernel:
  *   h1 = W1 x + b1 (1x1, 2 -> 32); h_{l+1} = relu(conv7(h_l) + b_l) for four
  *   7x7 'same' 32 -> 32 layers; y = (W6 h5 + b6) / 441 (1x1, 32 -> 1; the fixed
