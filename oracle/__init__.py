@@ -85,6 +85,9 @@ def _declare(l):
     l.ora_adam.restype = None
     l.ora_num_threads.restype = I
     l.ora_set_threads.argtypes = [I]
+    l.ora_minipix.argtypes = [I, I, P, I, P, I, P, P]
+    l.ora_minipix.restype = I
+    l.ora_lowres.argtypes = [I, I, P, P, I, P]
 
 
 def _p(a):
@@ -332,3 +335,24 @@ def adam(p, m, v, g, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, step=1):
     """In-place Adam step on float64 arrays p, m, v."""
     g = _c(g, np.float64)
     lib().ora_adam(p.size, _p(p), _p(m), _p(v), _p(g), float(lr), float(b1), float(b2), float(eps), int(step))
+
+
+def minipix(img, cell, targets):
+    """Sparse stamping: (out f32 [h][w], keep u8 [ceil(h/cell)][ceil(w/cell)], kept cells)."""
+    img = _c(img, np.float32)
+    h, w = img.shape
+    t = _c(np.asarray(targets, np.int32).reshape(-1, 2), np.int32)
+    out = np.empty((h, w), np.float32)
+    keep = np.empty(((h + cell - 1) // cell, (w + cell - 1) // cell), np.uint8)
+    n = lib().ora_minipix(w, h, _p(img), int(cell), _p(t), t.shape[0], _p(out), _p(keep))
+    return out, keep, n
+
+
+def lowres(img, flags, f):
+    """Block mean of the valid pixels, FP64 [ceil(h/f)][ceil(w/f)]."""
+    img = _c(img, np.float32)
+    h, w = img.shape
+    fl = None if flags is None else _c(flags, np.uint8)
+    out = np.empty(((h + f - 1) // f, (w + f - 1) // f))
+    lib().ora_lowres(w, h, _p(img), None if fl is None else _p(fl), int(f), _p(out))
+    return out

@@ -10,7 +10,8 @@
  * The paper names the steps (calibration: dark subtraction, flat fielding and
  * bad-pixel masking, Sec. 4.1 "Image Management"; GPU-resident calibration and
  * noise maps, Sec. 3.2 "Compute Nodes"; coaddition, Sec. 4.1.3; direct image
- * subtraction and transient detection, Sec. 4.2 "Transient Alerts" and Table 2)
+ * subtraction and transient detection, Sec. 4.2 "Transient Alerts" and Table 2;
+ * minipix stamping and low-resolution maps, Sec. 3.3 "Sparse Image Segments")
  * but prints no formula for any of them.  Each function below states the
  * definition it computes.  Where the paper leaves the method open, the
  * Alard & Lupton (1998) / Alard (2000) Gaussian-basis least-squares kernel fit
@@ -967,4 +968,52 @@ void ora_adam(long n, double *p, double *m, double *v, const double *g, double l
         v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
         p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sparse "minipix" stamping (Sec. 3.3, Sparse Image Segments): within an   */
+/* image, square cells of cell x cell pixels stand for the NSIDE=16384      */
+/* minipix of a segment; a cell is kept when a science target (x, y) lies   */
+/* in it, and every pixel of the other cells is set to zero.  keep[cy * ncx */
+/* + cx] = 1 for kept cells (ncx = ceil(w / cell)); partial cells at the    */
+/* right and bottom edges hold the pixels that exist.  Targets outside the  */
+/* image are ignored.  Returns the number of kept cells.                    */
+/* ------------------------------------------------------------------------ */
+int ora_minipix(int w, int h, const float *img, int cell, const int *targets, int n, float *out,
+                uint8_t *keep) {
+    int ncx = (w + cell - 1) / cell, ncy = (h + cell - 1) / cell;
+    memset(keep, 0, (size_t)ncx * ncy);
+    for (int t = 0; t < n; t++) {
+        int x = targets[2 * t], y = targets[2 * t + 1];
+        if (x < 0 || y < 0 || x >= w || y >= h) continue;
+        keep[(y / cell) * ncx + x / cell] = 1;
+    }
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++)
+            out[(long)y * w + x] = keep[(y / cell) * ncx + x / cell] ? img[(long)y * w + x] : 0.0f;
+    int kept = 0;
+    for (int c = 0; c < ncx * ncy; c++) kept += keep[c];
+    return kept;
+}
+
+/* Low-resolution map (Sec. 2, segments at 10x reduced resolution): out[Y][X] */
+/* is the mean of the valid pixels (flags == 0 where flags are given, finite */
+/* values) of the f x f block at (f X, f Y); partial blocks at the right and */
+/* bottom edges average the pixels they hold; 0 where a block has none.      */
+/* out is [ceil(h / f)][ceil(w / f)], sums in FP64.                           */
+void ora_lowres(int w, int h, const float *img, const uint8_t *flags, int f, double *out) {
+    int ow = (w + f - 1) / f, oh = (h + f - 1) / f;
+    for (int Y = 0; Y < oh; Y++)
+        for (int X = 0; X < ow; X++) {
+            double s = 0.0;
+            long n = 0;
+            for (int y = Y * f; y < Y * f + f && y < h; y++)
+                for (int x = X * f; x < X * f + f && x < w; x++) {
+                    float v = img[(long)y * w + x];
+                    if ((flags && flags[(long)y * w + x]) || !isfinite(v)) continue;
+                    s += v;
+                    n++;
+                }
+            out[(long)Y * ow + X] = n ? s / (double)n : 0.0;
+        }
 }

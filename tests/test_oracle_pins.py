@@ -9,6 +9,7 @@ transient candidates (Sec. 4.2), clipped coaddition (Sec. 4.1.3).
 import json
 import math
 import os
+import warnings
 
 import numpy as np
 import pytest
@@ -658,3 +659,76 @@ def test_adam_first_step_closed_form(ora):
     np.testing.assert_allclose(p, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+# --------------------------------------------------------------------------- sparse segments
+# Sec. 3.3 (Sparse Image Segments) and Sec. 2 (low-resolution segments at 10x
+# reduced resolution).
+def _cells_mask(w, h, cell, targets):
+    """Kept-cell mask by set membership and np.repeat, a different route from the
+    oracle's per-pixel division."""
+    ncx, ncy = -(-w // cell), -(-h // cell)
+    m = np.zeros((ncy, ncx), np.uint8)
+    for x, y in targets:
+        if 0 <= x < w and 0 <= y < h:
+            m[y // cell, x // cell] = 1
+    full = np.repeat(np.repeat(m, cell, 0), cell, 1)[:h, :w]
+    return m, full
+
+
+@pytest.mark.parametrize("w,h,cell", [(64, 48, 8), (101, 77, 9), (37, 5, 16)])
+def test_minipix_matches_repeated_cell_mask(ora, w, h, cell):
+    rng = np.random.default_rng(w * h)
+    img = rng.normal(100, 10, (h, w)).astype(np.float32)
+    t = np.stack([rng.integers(-3, w + 3, 25), rng.integers(-3, h + 3, 25)], 1)
+    out, keep, n = ora.minipix(img, cell, t)
+    m, full = _cells_mask(w, h, cell, t)
+    np.testing.assert_array_equal(keep, m)
+    assert n == len({(y // cell, x // cell) for x, y in t if 0 <= x < w and 0 <= y < h})
+    np.testing.assert_array_equal(out, np.where(full == 1, img, np.float32(0)))
+
+
+def test_minipix_special_cases(ora):
+    rng = np.random.default_rng(1)
+    img = rng.normal(0, 1, (30, 40)).astype(np.float32)
+    out, keep, n = ora.minipix(img, 10, np.zeros((0, 2), np.int32))
+    assert n == 0 and not out.any() and not keep.any()
+    every = [(x, y) for y in range(0, 30, 10) for x in range(0, 40, 10)]
+    out, keep, n = ora.minipix(img, 10, every)
+    assert n == 12 and keep.all()
+    np.testing.assert_array_equal(out, img)
+    out, keep, n = ora.minipix(img, 10, [(39, 29), (39, 29), (40, 0), (0, -1)])
+    assert n == 1 and keep[2, 3] == 1 and keep.sum() == 1
+    np.testing.assert_array_equal(out[20:, 30:], img[20:, 30:])
+    assert not out[:20].any() and not out[:, :30].any()
+
+
+@pytest.mark.parametrize("w,h,f", [(50, 30, 10), (47, 23, 10), (9, 9, 4), (13, 7, 1)])
+def test_lowres_matches_nanmean_of_padded_blocks(ora, w, h, f):
+    rng = np.random.default_rng(w + 7 * h)
+    img = rng.normal(300, 20, (h, w)).astype(np.float32)
+    img[rng.random((h, w)) < 0.03] = np.nan
+    flags = (rng.random((h, w)) < 0.05).astype(np.uint8)
+    ow, oh = -(-w // f), -(-h // f)
+    pad = np.full((oh * f, ow * f), np.nan)
+    pad[:h, :w] = np.where(flags == 0, img.astype(np.float64), np.nan)
+    blocks = pad.reshape(oh, f, ow, f).transpose(0, 2, 1, 3).reshape(oh, ow, f * f)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", RuntimeWarning)      # all-NaN blocks -> 0 below
+        ref = np.nanmean(blocks, axis=2)
+    ref[np.isnan(ref)] = 0.0
+    np.testing.assert_allclose(ora.lowres(img, flags, f), ref, rtol=1e-14, atol=0)
+
+
+def test_lowres_ramp_constant_and_empty_blocks(ora):
+    w, h, f = 47, 23, 10
+    x = np.tile(np.arange(w, dtype=np.float32), (h, 1))
+    lo = ora.lowres(x, None, f)
+    for X in range(lo.shape[1]):
+        nb = min(f, w - X * f)                        # mean of X f .. X f + nb - 1
+        np.testing.assert_allclose(lo[:, X], X * f + (nb - 1) / 2.0, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(ora.lowres(np.full((h, w), 7.25, np.float32), None, f), 7.25)
+    flags = np.ones((h, w), np.uint8)
+    flags[0, 0] = 0
+    lo = ora.lowres(np.full((h, w), 3.0, np.float32), flags, f)
+    assert lo[0, 0] == 3.0 and not lo.ravel()[1:].any()
