@@ -417,7 +417,8 @@ def run_gpu(args):
         wanted = set(x for x in args.extras.split(",") if x)
         for name, fn in (("coadd", lambda: bench_coadd(device, stream, args.steps, hbm)),
                          ("segments", lambda: bench_segments(device, stream, args.segment_cameras)),
-                         ("learned", lambda: bench_learned(device, stream, args.train_pairs, args.train_epochs))):
+                         ("learned", lambda: bench_learned(device, stream, args.train_pairs, args.train_epochs)),
+                         ("sparse", lambda: bench_sparse(device, stream, hbm))):
             if name not in wanted:
                 continue
             try:
@@ -446,6 +447,24 @@ def timed_ms(fn, n, stream, device):
     e1.record(stream)
     torch.cuda.synchronize(device)
     return e0.elapsed_time(e1) / n
+
+
+def call_ms(fn, n, stream, device):
+    """Median over n calls of one call's device time (CUDA events on the launching
+    stream, the device synchronised before each call)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(n):
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
 
 
 def bench_coadd(device, stream, steps, hbm):
@@ -522,6 +541,66 @@ def bench_segments(device, stream, cameras, log=None):
             "unit": "Mpix/s", "config": {"fit_ctas_per_sm": cfg.fit_ctas_per_sm, "sub_ctas_per_sm": cfg.sub_ctas_per_sm},
             "work_units": {"fit": fit_items, "subtract": sub_items}, "sources": nsrc, "status": st,
             "generation_s": round(gen_s, 1)}
+
+
+def bench_sparse(device, stream, hbm):
+    """Minipix stamping (9-pixel cells ~ the NSIDE=16384 minipix at 1.38 arcsec/px,
+    4600 catalogue targets ~ 1e7 sources over 19,370 sq deg seen by one 9 sq deg
+    camera, 400 detections) and the 10x low-resolution map of one 9576x6388 frame."""
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    from paper_2207_14304_gb300 import synth
+    cell, factor, n_cat, n_det = 9, 10, 4600, 400
+    pitch = synth.pitch_for(W)
+    cat = synth.star_catalog(N_STARS, W, H, seed=21)
+    g = torch.Generator(device=device)
+    g.manual_seed(21)
+    img = torch.zeros((H, pitch), device=device)
+    img[:, :W] = synth.render(cat, W, H, 1.5, sky=300.0, device=device, dtype=torch.float32)
+    img[:, :W] += torch.randn((H, W), generator=g, device=device) * 18.0
+    flags = torch.zeros((H, pitch), dtype=torch.uint8, device=device)
+    flags[:, :W] = (torch.rand((H, W), generator=g, device=device) < 1e-4).to(torch.uint8)
+    tx = cat.x[:n_cat].round().clamp(0, W - 1).to(torch.int32)
+    ty = cat.y[:n_cat].round().clamp(0, H - 1).to(torch.int32)
+    targets = torch.stack([tx, ty], 1).contiguous().to(device)
+    src = torch.zeros((n_det, B.SOURCE_BYTES // 4), dtype=torch.int32, device=device)
+    src[:, 7] = torch.randint(0, W, (n_det,), generator=g, device=device, dtype=torch.int32)   # px
+    src[:, 8] = torch.randint(0, H, (n_det,), generator=g, device=device, dtype=torch.int32)   # py
+    n_src = torch.tensor([n_det], dtype=torch.int32, device=device)
+    ncx, ncy = -(-W // cell), -(-H // cell)
+    cap = 1 << 14
+    keep = torch.zeros((ncy, ncx), dtype=torch.uint8, device=device)
+    out = torch.empty((H, pitch), device=device)
+    packed = torch.empty((cap, cell * cell), device=device)
+    cidx = torch.empty(cap, dtype=torch.int32, device=device)
+    nk = torch.zeros(4, dtype=torch.int32, device=device)
+    ow, oh = -(-W // factor), -(-H // factor)
+    lpitch = synth.pitch_for(ow)
+    low = torch.empty((oh, lpitch), device=device)
+    shape = B.argus_shape(W, H, pitch)
+    ctx = B.argus_create(device.index, H * pitch, 16, 64, 1 << 10)
+    try:
+        # inputs (245 MB image) exceed L2, so successive calls do not reuse cached pixels
+        mp_ms = call_ms(lambda: B.argus_minipix(ctx, img, shape, cell, targets, n_cat, src, n_src, n_det, keep, out,
+                                                packed, cidx, cap, nk, stream), 20, stream, device)
+        lr_ms = call_ms(lambda: B.argus_lowres(ctx, img, flags, shape, factor, low, lpitch, stream), 20, stream,
+                        device)
+        st = B.argus_sync_status(ctx, stream)
+        kept = int(nk[0].item())
+    finally:
+        B.argus_destroy(ctx)
+    npx = H * pitch
+    kept_px = kept * cell * cell
+    mp_bytes = 4 * npx + 8 * kept_px + ncx * ncy * 4      # out write, kept reads + packed writes, keep map
+    lr_bytes = 5 * npx + 4 * oh * ow                      # image + flags read, map written
+    return {"workload": f"{W}x{H} frame, {cell}-px minipix cells, {n_cat} catalogue targets + {n_det} detections; "
+                        f"{factor}x low-resolution map",
+            "minipix": {"ms": round(mp_ms, 4), "value": round(W * H / 1e6 / (mp_ms / 1e3), 1), "unit": "Mpix/s",
+                        "kept_cells": kept, "kept_frac": round(kept / (ncx * ncy), 5),
+                        "hbm_bytes": mp_bytes, "hbm_frac": round(mp_bytes / (mp_ms / 1e3) / 1e9 / hbm, 4)},
+            "lowres": {"ms": round(lr_ms, 4), "value": round(W * H / 1e6 / (lr_ms / 1e3), 1), "unit": "Mpix/s",
+                       "hbm_bytes": lr_bytes, "hbm_frac": round(lr_bytes / (lr_ms / 1e3) / 1e9 / hbm, 4)},
+            "status": st}
 
 
 def bench_learned(device, stream, train_pairs, epochs, log=None):
@@ -704,7 +783,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
-    ap.add_argument("--extras", default="coadd,segments,learned",
+    ap.add_argument("--extras", default="coadd,segments,learned,sparse",
                     help="comma list of the extra workloads to measure after the headline")
     ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
     ap.add_argument("--frame", type=int, nargs=2, metavar=("W", "H"), default=None,

@@ -383,6 +383,46 @@ int argus_select_stamps_noalloc(const float *ref, const uint8_t *flags, argus_sh
                                 int grid_y, int stamp, int khalf, float max_peak, int iso, float iso_frac,
                                 int *centers, int *n_stamps, argus_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Sparse and low-resolution segment products (paper Sec. 3.3 "Sparse Image
+ * Segments"; Sec. 2, data products 1c and 1d).
+ *
+ * Minipix stamping: the image is cut into square cells of cell x cell pixels
+ * (the minipix of a segment; ncx = ceil(w / cell), ncy = ceil(h / cell), cell
+ * (cx, cy) holding pixels [cx cell, cx cell + cell) x [cy cell, cy cell + cell)
+ * clipped to the image).  A cell is kept when a science target lies in it:
+ * the catalogue targets (device int [n_targets][2], pixel (x, y)) and the
+ * peak pixels (px, py) of the first min(*n_sources, sources_cap) records of a
+ * detection list (device argus_source array and device count, as written by
+ * argus_detect; sources may be NULL with sources_cap 0).  Targets outside the
+ * image are ignored.  Every pixel of a cell that is not kept is set to 0.
+ *   keep:       device uint8 [ncy][ncx] (no pitch), 1 = kept, 0 = zeroed.
+ *   out:        nullable, device float [h][pitch]: img where kept, else 0;
+ *               columns w .. pitch-1 are set to 0.  May not alias img.
+ *   packed:     nullable, device float [cap][cell * cell]: the kept cells in
+ *               ascending cell index cy * ncx + cx, each row-major, pixels
+ *               outside the image 0;  cell_index: device int [cap], the cell
+ *               index of each packed cell (nullable only with packed NULL).
+ *   n_kept:     device int, the number of kept cells; more than cap latches
+ *               ARGUS_ERR_CAPACITY and only the first cap are packed.
+ * 1 <= cell <= 256; n_targets >= 0.  Results are exact copies (bit-exact). */
+int argus_minipix(argus_ctx *ctx, const float *img, argus_shape shape, int cell, const int *targets,
+                  int n_targets, const argus_source *sources, const int *n_sources, int sources_cap,
+                  uint8_t *keep, float *out, float *packed, int *cell_index, int cap, int *n_kept,
+                  argus_stream stream);
+
+/* Low-resolution map (paper Sec. 2, product 1d: 10x reduced resolution,
+ * 13.8 arcsec per pixel): out[Y][X] = mean of the valid pixels of the factor x
+ * factor block starting at (factor X, factor Y), valid = flags == 0 (flags
+ * nullable: all pixels) and the value finite; partial blocks at the right and
+ * bottom edges average the pixels they hold; 0 where a block has none.  out:
+ * device float [ceil(h / factor)][out_pitch], out_pitch >= ceil(w / factor),
+ * 16-byte aligned.  Sums are FP32 (column sums of factor pixels, then factor
+ * column sums), so |out - exact| <= (2 factor + 1) 2^-24 mean|v| over the
+ * block.  1 <= factor <= 64. */
+int argus_lowres(argus_ctx *ctx, const float *img, const uint8_t *flags, argus_shape shape, int factor,
+                 float *out, long out_pitch, argus_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -120,6 +120,8 @@ SIGNATURES = {
     "argus_learned_kernel": ([P, P, P, P, I, I, I, I, P, P], I),
     "argus_fit_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
     "argus_fit_scale_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
+    "argus_minipix": ([P, P, SH, I, P, I, P, P, I, P, P, P, P, I, P, P], I),
+    "argus_lowres": ([P, P, P, SH, I, P, C.c_long, P], I),
 }
 
 
@@ -395,6 +397,18 @@ def argus_detect(ctx, diff, diff_var, flags, shape, nsigma, psf_sigma, mask, out
     _check(load().argus_detect(ctx, _ptr(diff), _ptr(diff_var), _ptr(flags), shape, float(nsigma),
                                float(psf_sigma), _ptr(mask), _ptr(out), int(cap), _ptr(n_found),
                                _stream(stream)), "argus_detect")
+
+
+def argus_minipix(ctx, img, shape, cell, targets, n_targets, sources, n_sources, sources_cap, keep, out,
+                  packed, cell_index, cap, n_kept, stream=None):
+    _check(load().argus_minipix(ctx, _ptr(img), shape, int(cell), _ptr(targets), int(n_targets), _ptr(sources),
+                                _ptr(n_sources), int(sources_cap), _ptr(keep), _ptr(out), _ptr(packed),
+                                _ptr(cell_index), int(cap), _ptr(n_kept), _stream(stream)), "argus_minipix")
+
+
+def argus_lowres(ctx, img, flags, shape, factor, out, out_pitch, stream=None):
+    _check(load().argus_lowres(ctx, _ptr(img), _ptr(flags), shape, int(factor), _ptr(out), int(out_pitch),
+                               _stream(stream)), "argus_lowres")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):
