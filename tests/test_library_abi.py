@@ -50,3 +50,8 @@ def test_host_argument_checks_need_no_gpu():
     sh = B.argus_shape(10, 10, 10)   # pitch not a multiple of 16
     cal = B.make_calib()
     assert lib.argus_calibrate(None, None, sh, C.byref(cal), None, None, None, None) == B.ARGUS_ERR_ARG
+    sh = B.argus_shape(64, 8, 64)
+    # sparse products: NULL context, bad cell size / factor
+    assert lib.argus_minipix(None, None, sh, 9, None, 0, None, None, 0, None, None, None, None, 0, None,
+                             None) == B.ARGUS_ERR_ARG
+    assert lib.argus_lowres(None, None, None, sh, 10, None, 16, None) == B.ARGUS_ERR_ARG
