@@ -24,6 +24,8 @@ ARGUS_ERR_SINGULAR = -5
 ARGUS_ERR_CAPACITY = -6
 ARGUS_ERR_TIMEOUT = -7
 ARGUS_ERR_UNSUPPORTED = -8
+ARGUS_FLAG_BAD, ARGUS_FLAG_SAT = 1, 2
+ARGUS_MASK_POS, ARGUS_MASK_NEG, ARGUS_MASK_INVALID = 1, 2, 4
 
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
 FLAG_BAD, FLAG_SAT = 1, 2
