@@ -330,47 +330,10 @@ def run_gpu(args):
     n_found = int(nf_host[0].item())
 
     peaks = load_peaks()
-    # dominant kernel: the tensor-core reference convolution of the subtraction
-    # (difference image).  Algorithmic work: NK * KS^2 multiply-adds per pixel;
-    # the MMAs execute more (BF16 hi/lo x three products, K padded 21 -> 24, one
-    # M=128 x N=16*ceil((KS-1+4)*NK/16) MMA group per source row, source rows in
-    # blocks of 4 with 2R halo rows per 128-row band), reported beside it.
-    nk = (SDEG + 1) * (SDEG + 2) // 2
-    conv_flops = 2 * nk * KSIZE * KSIZE * W * H
-    achieved = conv_flops / (tc_ms / 1e3) / 1e12
-    bands = [min(128, H - y0) for y0 in range(0, H, 128)]
-    n_mma = 16 * (((KSIZE - 1 + 4) * nk + 15) // 16)
-    k_row = 16 if KSIZE <= 16 else 24          # taps 16..23 of a row pair share one K = 16 MMA
-    src_rows = ((W + 127) // 128) * sum(4 * ((b + KSIZE - 1 + 3) // 4) for b in bands)
-    executed = 3 * 2 * 128 * n_mma * k_row * src_rows
-    # the variance: one term of width N1 = 16*ceil((KS-1+4)/16), MMAs of width 2 N1 (hi*hi, hi*lo)
-    # and N1 (lo*hi)
-    n1 = 16 * ((KSIZE - 1 + 4 + 15) // 16)
-    executed_var = 2 * 128 * 3 * n1 * k_row * src_rows
-    tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    var_tflops = 2 * KSIZE * KSIZE * W * H / (var_ms / 1e3) / 1e12
     hbm = peaks.get("hbm_gbs", 6800.0)
     step_s = tmax / args.steps
     hbm_frac = BYTES_PER_PX * W * H / step_s / 1e9 / hbm
-
-    kernels = {
-        "subtract_tc": {"bound": "tensor", "kernel": "subtract_tc (reference convolution, difference image)",
-                        "achieved": round(achieved, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
-                        "frac": round(achieved / tensor_peak, 4), "traffic": traffic_bytes(SUBTRACT_TRAFFIC),
-                        "traffic_unit": "bytes per launch (ncu DRAM read+write)",
-                        "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
-                        "algorithmic": f"{2 * nk * KSIZE * KSIZE} FLOP/px ({nk} spatial terms x {KSIZE}x{KSIZE} taps)",
-                        "executed_tflops": round(executed / (tc_ms / 1e3) / 1e12, 1),
-                        "kernel_ms": round(tc_ms, 4), "kernel_timing": ktiming},
-        "variance": {"bound": "tensor", "kernel": "subtract_tc variance (tile-centre kernel squared (x) V_ref)",
-                     "achieved": round(var_tflops, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
-                     "frac": round(var_tflops / tensor_peak, 4), "traffic": traffic_bytes(VARIANCE_TRAFFIC),
-                     "traffic_unit": "bytes per launch (ncu DRAM read+write)",
-                     "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
-                     "algorithmic": f"{2 * KSIZE * KSIZE} FLOP/px ({KSIZE}x{KSIZE} squared taps)",
-                     "executed_tflops": round(executed_var / (var_ms / 1e3) / 1e12, 1),
-                     "kernel_ms": round(var_ms, 4), "kernel_timing": ktiming},
-    }
+    kernels = kernel_rooflines(tc_ms, var_ms, ktiming, peaks)
 
     var = {}
     if args.variants and ws == 1:
@@ -433,6 +396,58 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+VAR_BYTES_PER_PX = 4 + 4 + 1 + 4      # V_I, V_ref, flags read; V_D written
+
+
+def kernel_rooflines(tc_ms, var_ms, ktiming, peaks):
+    """Roofline entries of the two subtraction kernels of one full frame.
+
+    Difference image: NK * KS^2 multiply-adds per pixel against 13 bytes (I, R,
+    flags in, D out), 407 FLOP/B at 21x21 and degree 2 -- above the ridge of the
+    measured peaks (1719.5 TFLOP/s / 6777 GB/s = 254 FLOP/B), so the tensor roof
+    binds.  The MMAs execute more (BF16 hi/lo x three products, K padded 21 -> 24,
+    one M=128 x N=16*ceil((KS-1+4)*NK/16) MMA group per source row, source rows in
+    blocks of 4 with 2R halo rows per 128-row band), reported beside it.
+    Variance: KS^2 multiply-adds per pixel against 13 bytes, 68 FLOP/B -- below
+    the ridge, so the HBM roof binds: achieved = 13 B/px / kernel time."""
+    nk = (SDEG + 1) * (SDEG + 2) // 2
+    conv_flops = 2 * nk * KSIZE * KSIZE * W * H
+    achieved = conv_flops / (tc_ms / 1e3) / 1e12
+    bands = [min(128, H - y0) for y0 in range(0, H, 128)]
+    n_mma = 16 * (((KSIZE - 1 + 4) * nk + 15) // 16)
+    k_row = 16 if KSIZE <= 16 else 24          # taps 16..23 of a row pair share one K = 16 MMA
+    src_rows = ((W + 127) // 128) * sum(4 * ((b + KSIZE - 1 + 3) // 4) for b in bands)
+    executed = 3 * 2 * 128 * n_mma * k_row * src_rows
+    # the variance: one term of width N1 = 16*ceil((KS-1+4)/16), MMAs of width 2 N1 (hi*hi, hi*lo)
+    # and N1 (lo*hi)
+    n1 = 16 * ((KSIZE - 1 + 4 + 15) // 16)
+    executed_var = 2 * 128 * 3 * n1 * k_row * src_rows
+    tensor_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    var_tflops = 2 * KSIZE * KSIZE * W * H / (var_ms / 1e3) / 1e12
+    var_gbs = VAR_BYTES_PER_PX * W * H / (var_ms / 1e3) / 1e9
+    return {
+        "subtract_tc": {"bound": "tensor", "kernel": "subtract_tc (reference convolution, difference image)",
+                        "achieved": round(achieved, 3), "peak": round(tensor_peak, 1), "unit": "TFLOP/s",
+                        "frac": round(achieved / tensor_peak, 4), "traffic": traffic_bytes(SUBTRACT_TRAFFIC),
+                        "traffic_unit": "bytes per launch (ncu DRAM read+write)",
+                        "peak_source": "measured, MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM, sustained)",
+                        "algorithmic": f"{2 * nk * KSIZE * KSIZE} FLOP/px ({nk} spatial terms x {KSIZE}x{KSIZE} taps)",
+                        "executed_tflops": round(executed / (tc_ms / 1e3) / 1e12, 1),
+                        "kernel_ms": round(tc_ms, 4), "kernel_timing": ktiming},
+        "variance": {"bound": "hbm", "kernel": "subtract_tc variance (tile-centre kernel squared (x) V_ref)",
+                     "achieved": round(var_gbs, 1), "peak": round(hbm, 1), "unit": "GB/s",
+                     "frac": round(var_gbs / hbm, 4), "traffic": traffic_bytes(VARIANCE_TRAFFIC),
+                     "traffic_unit": "bytes per launch (ncu DRAM read+write)",
+                     "peak_source": "measured, MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)",
+                     "algorithmic": (f"{VAR_BYTES_PER_PX} B/px (V_I, V_ref, flags in; V_D out); "
+                                     f"{2 * KSIZE * KSIZE} FLOP/px ({KSIZE}x{KSIZE} squared taps)"),
+                     "tflops": round(var_tflops, 3), "tensor_frac": round(var_tflops / tensor_peak, 4),
+                     "executed_tflops": round(executed_var / (var_ms / 1e3) / 1e12, 1),
+                     "kernel_ms": round(var_ms, 4), "kernel_timing": ktiming},
+    }
 
 
 def timed_ms(fn, n, stream, device):

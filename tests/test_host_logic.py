@@ -138,3 +138,21 @@ def test_frame_override_scales_the_workload():
         assert bench.workload_config()["frame"] == [4096, 4096]
     finally:
         bench.W, bench.H, bench.N_STARS = saved
+
+
+def test_kernel_rooflines_pick_the_binding_roof():
+    """Difference image above the ridge of the measured peaks (tensor), variance below
+    it (HBM): achieved = algorithmic work / kernel time, frac = achieved / peak."""
+    import bench
+    peaks = {"hbm_gbs": 6777.0, "bf16_tflops_sustained": 1719.5}
+    k = bench.kernel_rooflines(0.848, 0.888, "events", peaks)
+    npx = bench.W * bench.H
+    d, v = k["subtract_tc"], k["variance"]
+    assert d["bound"] == "tensor" and d["unit"] == "TFLOP/s"
+    assert abs(d["achieved"] - 2 * 6 * 441 * npx / 0.848e-3 / 1e12) < 1e-3
+    assert abs(d["frac"] - d["achieved"] / 1719.5) < 1e-4
+    assert v["bound"] == "hbm" and v["unit"] == "GB/s" and v["peak"] == 6777.0
+    assert abs(v["achieved"] - 13 * npx / 0.888e-3 / 1e9) < 0.1
+    assert abs(v["frac"] - v["achieved"] / 6777.0) < 1e-4
+    ridge = 1719.5e12 / 6777e9
+    assert 2 * 6 * 441 / 13 > ridge > 2 * 441 / bench.VAR_BYTES_PER_PX
