@@ -423,6 +423,27 @@ int argus_minipix(argus_ctx *ctx, const float *img, argus_shape shape, int cell,
 int argus_lowres(argus_ctx *ctx, const float *img, const uint8_t *flags, argus_shape shape, int factor,
                  float *out, long out_pitch, argus_stream stream);
 
+/* Median-filtered background map (paper Table 2, GPU stage "Median-filtered
+ * background map"; background maps kept with the calibration frames, Sec. 3.2).
+ * The paper names the map only; this is the mesh estimate:
+ *   1. boxes of box x box pixels from (0, 0), ncx = ceil(w / box) by
+ *      ncy = ceil(h / box); edge boxes hold the pixels that exist;
+ *   2. each box's value is the median of its valid pixels (flags == 0 where
+ *      flags are given, and finite; an even count takes the mean of the two
+ *      middle values, in FP64, so the value is exact); a box whose valid count
+ *      is below min_frac (compared in float) of its pixels has no value;
+ *   3. mesh (device double [ncy][ncx], 8-byte aligned) receives the median of
+ *      the values that exist in each box's filt x filt neighbourhood of boxes,
+ *      clipped at the mesh edges; a box with none in reach takes the median of
+ *      all box values (0 if no box has one);
+ *   4. map (nullable, device float [h][pitch]) receives the bilinear
+ *      interpolation of the mesh between box centres (the mean pixel coordinate
+ *      of each box), constant beyond the outermost centres, in FP32; columns
+ *      w .. pitch-1 are set to 0.
+ * 8 <= box <= 64; filt odd, 1 <= filt <= 7; 0 <= min_frac <= 1. */
+int argus_background(argus_ctx *ctx, const float *img, const uint8_t *flags, argus_shape shape, int box,
+                     int filt, float min_frac, double *mesh, float *map, argus_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,7 @@ SIGNATURES = {
     "argus_fit_scale_background": ([P, P, P, P, P, SH, P, P, I, I, P, I, I, I, P, P, P], I),
     "argus_minipix": ([P, P, SH, I, P, I, P, P, I, P, P, P, P, I, P, P], I),
     "argus_lowres": ([P, P, P, SH, I, P, C.c_long, P], I),
+    "argus_background": ([P, P, P, SH, I, I, F, P, P, P], I),
 }
 
 
@@ -411,6 +412,11 @@ def argus_minipix(ctx, img, shape, cell, targets, n_targets, sources, n_sources,
 def argus_lowres(ctx, img, flags, shape, factor, out, out_pitch, stream=None):
     _check(load().argus_lowres(ctx, _ptr(img), _ptr(flags), shape, int(factor), _ptr(out), int(out_pitch),
                                _stream(stream)), "argus_lowres")
+
+
+def argus_background(ctx, img, flags, shape, box, filt, min_frac, mesh, map_=None, stream=None):
+    _check(load().argus_background(ctx, _ptr(img), _ptr(flags), shape, int(box), int(filt), float(min_frac),
+                                   _ptr(mesh), _ptr(map_), _stream(stream)), "argus_background")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):

@@ -55,3 +55,4 @@ def test_host_argument_checks_need_no_gpu():
     assert lib.argus_minipix(None, None, sh, 9, None, 0, None, None, 0, None, None, None, None, 0, None,
                              None) == B.ARGUS_ERR_ARG
     assert lib.argus_lowres(None, None, None, sh, 10, None, 16, None) == B.ARGUS_ERR_ARG
+    assert lib.argus_background(None, None, None, sh, 64, 3, 0.5, None, None, None) == B.ARGUS_ERR_ARG
