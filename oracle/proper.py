@@ -21,8 +21,12 @@ Conventions (readings of the method, shared by the GPU path):
 - transforms are numpy's unnormalised forward FFT and its inverse, so a
   unit-sum PSF has P_hat(0) = 1 and white noise of per-pixel variance v has
   E|eps_hat(k)|^2 = v * npix;
-- where a denominator vanishes (every PSF transform is 0 at that frequency)
-  the quotient is set to 0.
+- a frequency where every PSF transform has modulus below eps (default 1e-8;
+  the PSFs have unit sum, so |P(0)| = 1) carries no proper statistic: D,
+  P_D and the ZOGY score S, and the proper coadd R and its PSF P_R, are 0
+  there (the score coadd, a plain correlation, keeps every frequency).  Below that floor the transforms of sampled PSFs are
+  set by the FFT's own rounding (about 1e-16 in FP64, 1e-7 in FP32), so the
+  quotient is not a property of the inputs; the floor makes it one.
 """
 from __future__ import annotations
 
@@ -48,7 +52,7 @@ def _safe_div(num, den):
     return out
 
 
-def zogy(N, R, Pn, Pr, Fn, Fr, sn, sr):
+def zogy(N, R, Pn, Pr, Fn, Fr, sn, sr, eps=1e-8):
     """Proper image subtraction of a new image N against a reference R.
 
     With hats for DFTs and the PSFs placed on the tile:
@@ -70,6 +74,7 @@ def zogy(N, R, Pn, Pr, Fn, Fr, sn, sr):
     N_h = np.fft.fft2(N)
     R_h = np.fft.fft2(R)
     den = np.sqrt(sn * sn * Fr * Fr * np.abs(Pr_h) ** 2 + sr * sr * Fn * Fn * np.abs(Pn_h) ** 2)
+    den[np.maximum(np.abs(Pn_h), np.abs(Pr_h)) < eps] = 0.0          # no statistic below the floor
     D_h = _safe_div(Fr * Pr_h * N_h - Fn * Pn_h * R_h, den)
     F_D = Fr * Fn / np.sqrt(sn * sn * Fr * Fr + sr * sr * Fn * Fn)
     PD_h = _safe_div(Fr * Fn * Pr_h * Pn_h, F_D * den)
@@ -80,7 +85,7 @@ def zogy(N, R, Pn, Pr, Fn, Fr, sn, sr):
     return {"D": D, "P_D": P_D, "F_D": F_D, "S": S, "sigma_S": sigma_S}
 
 
-def proper_coadd(images, psfs, F, sigma):
+def proper_coadd(images, psfs, F, sigma, eps=1e-8):
     """Proper coaddition of registered images M_j with PSFs P_j, zero points F_j
     and background noise sigma_j.
 
@@ -98,14 +103,17 @@ def proper_coadd(images, psfs, F, sigma):
     shape = images[0].shape
     S_h = np.zeros(shape, np.complex128)
     den2 = np.zeros(shape)
+    pmax = np.zeros(shape)
     varS = 0.0
     for M, P, f, s in zip(images, psfs, F, sigma):
         P_t = psf_on_tile(P, shape)
         P_h = np.fft.fft2(P_t)
         S_h += (f / (s * s)) * np.conj(P_h) * np.fft.fft2(M)
         den2 += (f * f) / (s * s) * np.abs(P_h) ** 2
+        pmax = np.maximum(pmax, np.abs(P_h))
         varS += (f * f) / (s * s) * np.sum(P_t * P_t)
     den = np.sqrt(den2)
+    den[pmax < eps] = 0.0                                             # no statistic below the floor
     F_R = float(np.sqrt(sum((f * f) / (s * s) for f, s in zip(F, sigma))))
     return {"S": np.fft.ifft2(S_h).real, "R": np.fft.ifft2(_safe_div(S_h, den)).real, "F_R": F_R,
             "P_R": np.fft.ifft2(den / F_R).real, "sigma_S": float(np.sqrt(varS))}

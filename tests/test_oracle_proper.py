@@ -123,6 +123,25 @@ def test_zogy_noise_is_white_with_unit_variance():
     assert out["S"].std() == pytest.approx(out["sigma_S"], rel=0.05)
 
 
+def test_zogy_frequencies_below_the_floor_carry_nothing():
+    """Wide PSFs on a 256^2 tile: where both PSF transforms are below eps the
+    difference has no power; elsewhere its noise stays white with unit variance,
+    so the per-pixel variance is the kept fraction of the frequencies."""
+    shape = (256, 256)
+    rng = np.random.default_rng(11)
+    sn, sr = 5.0, 2.0
+    Pn, Pr = _gauss(3.2), _gauss(2.8)
+    out = proper.zogy(rng.normal(0, sn, shape), rng.normal(0, sr, shape), Pn, Pr, 1.0, 1.0, sn, sr)
+    big = np.maximum(np.abs(np.fft.fft2(proper.psf_on_tile(Pn, shape))),
+                     np.abs(np.fft.fft2(proper.psf_on_tile(Pr, shape)))) >= 1e-8
+    kept = big.mean()
+    assert 0.2 < kept < 0.9
+    Dh = np.fft.fft2(out["D"])
+    assert np.abs(Dh[~big]).max() < 1e-9 * np.abs(Dh).max()
+    assert np.abs(np.fft.fft2(out["P_D"])[~big]).max() < 1e-12
+    assert out["D"].var() == pytest.approx(kept, abs=0.03)
+
+
 def test_zogy_swapping_images_negates_the_difference():
     rng = np.random.default_rng(4)
     N, R = rng.normal(0, 2, (32, 40)), rng.normal(0, 1, (32, 40))
