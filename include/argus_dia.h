@@ -444,6 +444,44 @@ int argus_lowres(argus_ctx *ctx, const float *img, const uint8_t *flags, argus_s
 int argus_background(argus_ctx *ctx, const float *img, const uint8_t *flags, argus_shape shape, int box,
                      int filt, float min_frac, double *mesh, float *map, argus_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * ZOGY proper image subtraction on square tiles (paper Sec. 4.2: ZOGY for
+ * base cadence and deep coadds; the statistic of Zackay, Ofek & Gal-Yam 2016).
+ * Each tile is T x T pixels of the new image N and the registered reference R
+ * (background-subtracted; pixels off the frame are 0), taken as periodic.
+ * With hats for unnormalised 2-D DFTs and the PSF stamps placed with their
+ * centre at pixel (0, 0) (wrapping around):
+ *   den = sqrt(sn^2 Fr^2 |Pr|^2 + sr^2 Fn^2 |Pn|^2),   F_D = Fr Fn / sqrt(sn^2 Fr^2 + sr^2 Fn^2)
+ *   D   = IDFT[(Fr Pr N - Fn Pn R) / den]        proper difference, unit-variance white noise
+ *   P_D = IDFT[Fr Fn Pr Pn / (F_D den)]          its PSF (unit sum)
+ *   S   = IDFT[F_D D conj(P_D)]                  point-source score, per-pixel sigma_S = F_D ||P_D||_2
+ * with D, P_D and S set to 0 at frequencies where max(|Pn|, |Pr|) < eps (the
+ * PSFs have unit sum; below the floor their transforms are rounding; 1e-8 is
+ * the reference value).  Images and the pointwise step are FP32, the PSF
+ * transforms FP64.  A plan owns the transform buffers (48 bytes per tile
+ * pixel) and the twiddle tables of one tile size. */
+typedef struct argus_zogy_plan argus_zogy_plan;
+
+typedef struct {
+    int x0, y0;      /* frame position of the tile's pixel (0, 0) */
+    float Fn, Fr;    /* flux zero points of the new image and the reference */
+    float sn, sr;    /* their background noise (standard deviation per pixel) */
+} argus_zogy_tile;
+
+/* tile in {256, 512, 1024}; 1 <= max_tiles <= 65536.  Allocates on `device`. */
+int argus_zogy_plan_create(int device, int tile, int max_tiles, argus_zogy_plan **plan);
+int argus_zogy_plan_destroy(argus_zogy_plan *plan);
+
+/* N, R: device float [h][pitch] (one shape); tiles: device argus_zogy_tile
+ * [n_tiles]; psf_n, psf_r: device float [n_tiles][psf_size][psf_size], odd
+ * psf_size <= 63; D, S and P_D (nullable): device float [n_tiles][T][T];
+ * sigma_S (nullable): device double [n_tiles].  1 <= n_tiles <= max_tiles.
+ * Calls on one plan must not overlap. */
+int argus_zogy(argus_zogy_plan *plan, const float *N, const float *R, argus_shape shape,
+               const argus_zogy_tile *tiles, int n_tiles, const float *psf_n, const float *psf_r,
+               int psf_size, float eps, float *D, float *S, float *P_D, double *sigma_S,
+               argus_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

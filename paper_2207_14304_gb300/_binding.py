@@ -125,6 +125,9 @@ SIGNATURES = {
     "argus_minipix": ([P, P, SH, I, P, I, P, P, I, P, P, P, P, I, P, P], I),
     "argus_lowres": ([P, P, P, SH, I, P, C.c_long, P], I),
     "argus_background": ([P, P, P, SH, I, I, F, P, P, P], I),
+    "argus_zogy_plan_create": ([I, I, I, C.POINTER(P)], I),
+    "argus_zogy_plan_destroy": ([P], I),
+    "argus_zogy": ([P, P, P, SH, P, I, P, P, I, F, P, P, P, P, P], I),
 }
 
 
@@ -417,6 +420,28 @@ def argus_lowres(ctx, img, flags, shape, factor, out, out_pitch, stream=None):
 def argus_background(ctx, img, flags, shape, box, filt, min_frac, mesh, map_=None, stream=None):
     _check(load().argus_background(ctx, _ptr(img), _ptr(flags), shape, int(box), int(filt), float(min_frac),
                                    _ptr(mesh), _ptr(map_), _stream(stream)), "argus_background")
+
+
+ZOGY_TILE_DTYPE = [("x0", "<i4"), ("y0", "<i4"), ("Fn", "<f4"), ("Fr", "<f4"), ("sn", "<f4"), ("sr", "<f4")]
+
+
+def zogy_plan_create(device: int, tile: int, max_tiles: int):
+    plan = P()
+    _check(load().argus_zogy_plan_create(int(device), int(tile), int(max_tiles), C.byref(plan)),
+           "argus_zogy_plan_create")
+    return plan
+
+
+def zogy_plan_destroy(plan):
+    _check(load().argus_zogy_plan_destroy(plan), "argus_zogy_plan_destroy")
+
+
+def argus_zogy(plan, N, R, shape, tiles, n_tiles, psf_n, psf_r, psf_size, eps, D, S, P_D=None, sigma_S=None,
+               stream=None):
+    """tiles: a device uint8 tensor holding n_tiles records of ZOGY_TILE_DTYPE."""
+    _check(load().argus_zogy(plan, _ptr(N), _ptr(R), shape, _ptr(tiles), int(n_tiles), _ptr(psf_n), _ptr(psf_r),
+                             int(psf_size), float(eps), _ptr(D), _ptr(S), _ptr(P_D), _ptr(sigma_S),
+                             _stream(stream)), "argus_zogy")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):

@@ -1,0 +1,311 @@
+// ZOGY proper image subtraction on square tiles (paper Sec. 4.2: ZOGY at base
+// cadence and in deep coadds; the statistic of Zackay, Ofek & Gal-Yam 2016).
+//
+// Per tile (T x T, periodic), with hats for DFTs:
+//   1. pack:    z1 = N + i R (FP32), z2 = P_n + i P_r (FP64; the PSF stamps
+//               placed with their centre at (0, 0), wrapping around);
+//   2. forward: 2-D FFTs of z1 (FP32) and z2 (FP64) -- one complex transform
+//               carries two real images, separated through the conjugate
+//               symmetry X(k) = (Z(k) + conj Z(-k)) / 2, Y(k) = (Z(k) - conj Z(-k)) / 2i;
+//   3. combine: per frequency pair (k, -k), one thread:
+//                 den  = sqrt(sn^2 Fr^2 |Pr|^2 + sr^2 Fn^2 |Pn|^2)
+//                 D    = (Fr Pr N - Fn Pn R) / den
+//                 P_D  = Fr Fn Pr Pn / (F_D den),   F_D = Fr Fn / sqrt(sn^2 Fr^2 + sr^2 Fn^2)
+//                 S    = F_D D conj(P_D)
+//               all 0 where max(|Pn|, |Pr|) < eps (decided in FP64; below that
+//               floor the PSF transforms are rounding); the result is written
+//               as W = D + i S (both real images, so one inverse transform
+//               returns D in the real part and S in the imaginary part), and
+//               sum |P_D|^2 per tile (FP64) gives sigma_S = F_D ||P_D||_2;
+//   4. inverse: 2-D FFT of W (and of P_D when asked for), divided by T^2.
+// The PSF transforms are FP64 so that the floor decisions and the small
+// transforms near it are those of an FP64 reference; the images and the
+// combine are FP32.
+#include "argus_internal.cuh"
+#include "fft.cuh"
+
+#include <cmath>
+#include <cstdlib>
+
+struct argus_zogy_plan {
+    int device;
+    int tile;
+    int max_tiles;
+    float2* z1;       // [max_tiles][T][T]
+    double2* z2;      // [max_tiles][T][T]
+    float2* z3;       // [max_tiles][T][T] (P_D)
+    double* psd;      // [max_tiles] sum |P_D(k)|^2
+    float2* tw32;     // [T] e^{-2 pi i m / T}
+    double2* tw64;
+};
+
+namespace {
+
+struct ZArgs {
+    const float* N;
+    const float* R;
+    long pitch;
+    int w, h;
+    const argus_zogy_tile* tiles;
+    int n_tiles;
+    const float* psf_n;
+    const float* psf_r;
+    int ps;
+    double eps2;
+    float2* z1;
+    double2* z2;
+    float2* z3;
+    double* psd;
+    float* D;
+    float* S;
+    float* PD;
+    double* sigma_S;
+};
+
+template <int T>
+__global__ void __launch_bounds__(256) zogy_pack_kernel(ZArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / (T * T));
+        const int q = (int)(e - (long)t * T * T);
+        const int y = q / T, x = q - (q / T) * T;
+        const int gx = a.tiles[t].x0 + x, gy = a.tiles[t].y0 + y;
+        float n = 0.0f, r = 0.0f;
+        if (gx >= 0 && gy >= 0 && gx < a.w && gy < a.h) {       // pixels off the frame are 0
+            const long p = (long)gy * a.pitch + gx;
+            n = a.N[p];
+            r = a.R[p];
+        }
+        a.z1[e] = make_float2(n, r);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) zogy_psf_kernel(ZArgs a) {
+    const int pp = a.ps * a.ps, hh = a.ps / 2;
+    const long total = (long)a.n_tiles * pp;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / pp);
+        const int i = (int)(e - (long)t * pp);
+        const int v = i / a.ps, u = i - v * a.ps;
+        const int yy = (v - hh + T) & (T - 1), xx = (u - hh + T) & (T - 1);
+        a.z2[(long)t * T * T + yy * T + xx] = make_double2((double)a.psf_n[e], (double)a.psf_r[e]);
+    }
+}
+
+__device__ __forceinline__ float2 f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <int T>
+__global__ void __launch_bounds__(256) zogy_combine_kernel(ZArgs a) {
+    __shared__ double red[8];
+    const long total = (long)a.n_tiles * T * T;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // one frequency per thread
+    double psd = 0.0;
+    int t = -1;
+    if (e < total) {
+        t = (int)(e / (T * T));
+        const int q = (int)(e - (long)t * T * T);
+        const int ky = q / T, kx = q - ky * T;
+        const int pq = ((T - ky) & (T - 1)) * T + ((T - kx) & (T - 1));
+        if (pq >= q) {                                   // the pair (q, pq) is this thread's
+            const long base = (long)t * T * T;
+            const float2 A = a.z1[base + q], B = a.z1[base + pq];
+            const double2 C = a.z2[base + q], E = a.z2[base + pq];
+            // N = (A + conj B) / 2, R = (A - conj B) / 2i
+            const float2 Nh = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+            const float2 Rh = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+            const double2 Pn = make_double2(0.5 * (C.x + E.x), 0.5 * (C.y - E.y));
+            const double2 Pr = make_double2(0.5 * (C.y + E.y), -0.5 * (C.x - E.x));
+            const double mn = Pn.x * Pn.x + Pn.y * Pn.y, mr = Pr.x * Pr.x + Pr.y * Pr.y;
+            const argus_zogy_tile tp = a.tiles[t];
+            const float Fn = tp.Fn, Fr = tp.Fr, sn = tp.sn, sr = tp.sr;
+            const float FD = Fr * Fn / sqrtf(sn * sn * Fr * Fr + sr * sr * Fn * Fn);
+            float2 Dh = make_float2(0.0f, 0.0f), PD = make_float2(0.0f, 0.0f);
+            const float2 pn = f2(Pn), pr = f2(Pr);
+            const float den = sqrtf(sn * sn * Fr * Fr * (pr.x * pr.x + pr.y * pr.y) +
+                                    sr * sr * Fn * Fn * (pn.x * pn.x + pn.y * pn.y));
+            if ((mn >= a.eps2 || mr >= a.eps2) && den > 0.0f) {
+                // Fr Pr N - Fn Pn R
+                const float2 u = make_float2(Fr * (pr.x * Nh.x - pr.y * Nh.y) - Fn * (pn.x * Rh.x - pn.y * Rh.y),
+                                             Fr * (pr.x * Nh.y + pr.y * Nh.x) - Fn * (pn.x * Rh.y + pn.y * Rh.x));
+                Dh = make_float2(u.x / den, u.y / den);
+                const float g = Fr * Fn / (FD * den);
+                PD = make_float2(g * (pr.x * pn.x - pr.y * pn.y), g * (pr.x * pn.y + pr.y * pn.x));
+            }
+            // S = F_D D conj(P_D)
+            const float2 Sh = make_float2(FD * (Dh.x * PD.x + Dh.y * PD.y), FD * (Dh.y * PD.x - Dh.x * PD.y));
+            // W = D + i S at q; conj(D) + i conj(S) at -q
+            a.z1[base + q] = make_float2(Dh.x - Sh.y, Dh.y + Sh.x);
+            if (pq != q) a.z1[base + pq] = make_float2(Dh.x + Sh.y, Sh.x - Dh.y);
+            if (a.z3) {
+                a.z3[base + q] = PD;
+                if (pq != q) a.z3[base + pq] = make_float2(PD.x, -PD.y);
+            }
+            psd = ((double)PD.x * PD.x + (double)PD.y * PD.y) * (pq != q ? 2.0 : 1.0);
+        }
+    }
+    // per-tile sum of |P_D|^2: a CTA of 256 frequencies lies in one tile (T^2 % 256 == 0)
+    for (int o = 16; o > 0; o >>= 1) psd += __shfl_xor_sync(0xffffffffu, psd, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = psd;
+    __syncthreads();
+    if (threadIdx.x == 0 && t >= 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; i++) s += red[i];
+        atomicAdd(a.psd + t, s);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) zogy_unpack_kernel(ZArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    const float inv = 1.0f / ((float)T * (float)T);                  // a power of two: exact
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const float2 w = a.z1[e];
+        a.D[e] = w.x * inv;
+        a.S[e] = w.y * inv;
+        if (a.PD) a.PD[e] = a.z3[e].x * inv;
+    }
+}
+
+template <int T>
+__global__ void zogy_sigma_kernel(ZArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tiles) return;
+    const argus_zogy_tile tp = a.tiles[t];
+    const double Fn = tp.Fn, Fr = tp.Fr, sn = tp.sn, sr = tp.sr;
+    const double FD = Fr * Fn / sqrt(sn * sn * Fr * Fr + sr * sr * Fn * Fn);
+    a.sigma_S[t] = FD * sqrt(a.psd[t] / ((double)T * T));
+}
+
+template <int T, int S, typename R>
+void fft2d(typename fft::Cx<R>::T* d, int n, const typename fft::Cx<R>::T* tw, cudaStream_t s) {
+    using Sh = fft::Shape<T, R>;
+    const unsigned blocks = (unsigned)n * (T / Sh::SEQ);
+    fft::fft_pass_kernel<T, S, false, R><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, n, tw);
+    fft::fft_pass_kernel<T, S, true, R><<<blocks, Sh::THREADS, Sh::SMEM, s>>>(d, n, tw);
+    argus_count_launch(2);
+}
+
+template <int T>
+bool set_smem() {
+    bool ok = true;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, -1, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fft::Shape<T, float>::SMEM) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, -1, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fft::Shape<T, float>::SMEM) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, 1, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fft::Shape<T, float>::SMEM) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, 1, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fft::Shape<T, float>::SMEM) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, -1, false, double>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft::Shape<T, double>::SMEM) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(fft::fft_pass_kernel<T, -1, true, double>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft::Shape<T, double>::SMEM) == cudaSuccess;
+    return ok;
+}
+
+template <int T>
+int run(argus_zogy_plan* p, ZArgs& a, cudaStream_t s) {
+    const long total = (long)a.n_tiles * T * T;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    unsigned g2 = grid > 152u * 16u ? 152u * 16u : grid;
+    if (cudaMemsetAsync(p->z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+    if (cudaMemsetAsync(p->psd, 0, (size_t)a.n_tiles * sizeof(double), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+    zogy_pack_kernel<T><<<g2, 256, 0, s>>>(a);
+    const long pp = (long)a.n_tiles * a.ps * a.ps;
+    zogy_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
+    argus_count_launch(2);
+    fft2d<T, -1, float>(p->z1, a.n_tiles, p->tw32, s);
+    fft2d<T, -1, double>(p->z2, a.n_tiles, p->tw64, s);
+    zogy_combine_kernel<T><<<grid, 256, 0, s>>>(a);
+    argus_count_launch(1);
+    fft2d<T, 1, float>(p->z1, a.n_tiles, p->tw32, s);
+    if (a.PD) fft2d<T, 1, float>(p->z3, a.n_tiles, p->tw32, s);
+    zogy_unpack_kernel<T><<<g2, 256, 0, s>>>(a);
+    argus_count_launch(1);
+    if (a.sigma_S) {
+        zogy_sigma_kernel<T><<<(a.n_tiles + 127) / 128, 128, 0, s>>>(a);
+        argus_count_launch(1);
+    }
+    return argus_launch_status();
+}
+
+}  // namespace
+
+extern "C" int argus_zogy_plan_create(int device, int tile, int max_tiles, argus_zogy_plan** out) {
+    if (!out || (tile != 256 && tile != 512 && tile != 1024) || max_tiles < 1 || max_tiles > 65536)
+        return ARGUS_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    const bool smem_ok = tile == 256 ? set_smem<256>() : tile == 512 ? set_smem<512>() : set_smem<1024>();
+    if (!smem_ok) return ARGUS_ERR_CUDA;
+    argus_zogy_plan* p = (argus_zogy_plan*)calloc(1, sizeof(argus_zogy_plan));
+    if (!p) return ARGUS_ERR_NOMEM;
+    p->device = device;
+    p->tile = tile;
+    p->max_tiles = max_tiles;
+    const size_t n = (size_t)max_tiles * tile * tile;
+    bool ok = cudaMalloc((void**)&p->z1, n * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->z2, n * sizeof(double2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->z3, n * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->psd, (size_t)max_tiles * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->tw32, (size_t)tile * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->tw64, (size_t)tile * sizeof(double2)) == cudaSuccess;
+    if (ok) {
+        // twiddles e^{-2 pi i m / T} in double on the host, rounded once to float
+        double2* h64 = (double2*)malloc((size_t)tile * sizeof(double2));
+        float2* h32 = (float2*)malloc((size_t)tile * sizeof(float2));
+        ok = h64 && h32;
+        if (ok) {
+            const double two_pi = 6.283185307179586476925286766559;
+            for (int m = 0; m < tile; m++) {
+                const double ang = two_pi * (double)m / (double)tile;
+                h64[m] = make_double2(std::cos(ang), -std::sin(ang));
+                h32[m] = make_float2((float)h64[m].x, (float)h64[m].y);
+            }
+            ok = cudaMemcpy(p->tw64, h64, (size_t)tile * sizeof(double2), cudaMemcpyHostToDevice) == cudaSuccess &&
+                 cudaMemcpy(p->tw32, h32, (size_t)tile * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        free(h64);
+        free(h32);
+    }
+    if (!ok) {
+        cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
+        free(p);
+        return ARGUS_ERR_NOMEM;
+    }
+    *out = p;
+    return ARGUS_OK;
+}
+
+extern "C" int argus_zogy_plan_destroy(argus_zogy_plan* p) {
+    if (!p) return ARGUS_ERR_ARG;
+    cudaSetDevice(p->device);
+    cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
+    free(p);
+    return ARGUS_OK;
+}
+
+extern "C" int argus_zogy(argus_zogy_plan* plan, const float* N, const float* R, argus_shape shape,
+                          const argus_zogy_tile* tiles, int n_tiles, const float* psf_n, const float* psf_r,
+                          int psf_size, float eps, float* D, float* S, float* P_D, double* sigma_S,
+                          argus_stream stream) {
+    if (!plan || !N || !R || !tiles || !psf_n || !psf_r || !D || !S || n_tiles < 1 || n_tiles > plan->max_tiles)
+        return ARGUS_ERR_ARG;
+    if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
+    int st = argus_check_shape(shape, (size_t)-1);
+    if (st) return st;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    ZArgs a;
+    a.N = N; a.R = R; a.pitch = shape.pitch; a.w = shape.w; a.h = shape.h;
+    a.tiles = tiles; a.n_tiles = n_tiles; a.psf_n = psf_n; a.psf_r = psf_r; a.ps = psf_size;
+    a.eps2 = (double)eps * (double)eps;
+    a.z1 = plan->z1; a.z2 = plan->z2; a.z3 = P_D ? plan->z3 : nullptr; a.psd = plan->psd;
+    a.D = D; a.S = S; a.PD = P_D; a.sigma_S = sigma_S;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (plan->tile) {
+        case 256: return run<256>(plan, a, s);
+        case 512: return run<512>(plan, a, s);
+        default: return run<1024>(plan, a, s);
+    }
+}

@@ -1,0 +1,99 @@
+"""ZOGY on the GPU (Sec. 4.2) against the FP64 oracle, tile by tile.
+
+Tolerances, from the FP32 rounding of the image transforms (the PSF
+transforms are FP64): with u = 2^-24 and the unit
+  e = u log2(T^2) (||N||_2 / s_n + ||R||_2 / s_r) / T
+(the rms rounding of a T^2-point FP32 FFT carried through the quotient, whose
+gain is at most 1/s_n and 1/s_r), |dD| <= 8 e and |dS| <= 8 e F_D ||P_D||_1
+(S filters D with F_D P_D); an FP32 emulation of the same algorithm (numpy's
+single-precision FFT) stays within 1.4 e and 3.1 e F_D ||P_D||_1 on these
+tiles.  P_D within 64 u max|P_D|, sigma_S within 1e-6 relative.
+
+The kernels have not run on a GPU yet, so the file is skipped until they have.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2207_14304_gb300 import _binding as B
+from paper_2207_14304_gb300.synth import pitch_for
+from tests.gpu_helpers import F32_EPS, dev_pitched
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="ZOGY kernels not yet run on a GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+
+
+def _gauss(sig, half=15):
+    u = np.arange(-half, half + 1)
+    g = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * sig * sig))
+    return (g / g.sum()).astype(np.float32)
+
+
+def _frame(w, h, seed, sn, sr, psf_n, psf_r, Fn, Fr):
+    from oracle import proper
+    rng = np.random.default_rng(seed)
+    sky = np.zeros((h, w))
+    n = w * h // 130
+    np.add.at(sky, (rng.integers(0, h, n), rng.integers(0, w, n)), 1e2 * 1e4 ** rng.random(n))
+    conv = lambda img, P: np.fft.ifft2(np.fft.fft2(img) * np.fft.fft2(proper.psf_on_tile(P, img.shape))).real
+    N = (Fn * conv(sky, psf_n) + rng.normal(0, sn, (h, w))).astype(np.float32)
+    R = (Fr * conv(sky, psf_r) + rng.normal(0, sr, (h, w))).astype(np.float32)
+    return N, R
+
+
+@pytest.mark.parametrize("T,origins", [(256, [(0, 0), (300, 100), (520, 260)]), (512, [(64, 32)]),
+                                       (1024, [(0, 0)])])
+def test_zogy_parity(ora, T, origins):
+    from oracle import proper
+    w, h = 800, 600 if T < 1024 else 1024
+    w = max(w, T)
+    specs = [(1.05, 1.0, 18.0, 3.3, 2.0, 1.2), (0.9, 1.1, 10.0, 4.0, 1.3, 1.6), (1.0, 1.0, 7.0, 7.0, 2.2, 2.2)]
+    N, R = _frame(w, h, seed=T, sn=12.0, sr=3.0, psf_n=_gauss(1.8), psf_r=_gauss(1.3), Fn=1.0, Fr=1.0)
+    rec = np.zeros(len(origins), B.ZOGY_TILE_DTYPE)
+    pn = np.zeros((len(origins), 31, 31), np.float32)
+    pr = np.zeros_like(pn)
+    for i, (x0, y0) in enumerate(origins):
+        Fn, Fr, sn, sr, gn, gr = specs[i % len(specs)]
+        rec[i] = (x0, y0, Fn, Fr, sn, sr)
+        pn[i], pr[i] = _gauss(gn), _gauss(gr)
+    nt = len(origins)
+    plan = B.zogy_plan_create(0, T, 4)
+    try:
+        pitch = pitch_for(w)
+        dN, dR = dev_pitched(N), dev_pitched(R)
+        d_rec = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+        D = torch.full((nt, T, T), -7.0, device="cuda")
+        S = torch.full((nt, T, T), -7.0, device="cuda")
+        PD = torch.full((nt, T, T), -7.0, device="cuda")
+        sig = torch.zeros(nt, dtype=torch.float64, device="cuda")
+        B.argus_zogy(plan, dN, dR, B.argus_shape(w, h, pitch), d_rec, nt, torch.from_numpy(pn).cuda(),
+                     torch.from_numpy(pr).cuda(), 31, 1e-8, D, S, PD, sig)
+        torch.cuda.synchronize()
+        D, S, PD, sig = D.cpu().numpy(), S.cpu().numpy(), PD.cpu().numpy(), sig.cpu().numpy()
+    finally:
+        B.zogy_plan_destroy(plan)
+    for i, (x0, y0) in enumerate(origins):
+        Fn, Fr, sn, sr = (float(rec[i][k]) for k in ("Fn", "Fr", "sn", "sr"))
+        tN = np.zeros((T, T), np.float32)
+        tR = np.zeros((T, T), np.float32)
+        ys, xs = slice(y0, min(y0 + T, h)), slice(x0, min(x0 + T, w))
+        tN[: ys.stop - y0, : xs.stop - x0] = N[ys, xs]
+        tR[: ys.stop - y0, : xs.stop - x0] = R[ys, xs]
+        o = proper.zogy(tN, tR, pn[i].astype(np.float64), pr[i].astype(np.float64), Fn, Fr, sn, sr)
+        e = F32_EPS * math.log2(T * T) * (np.linalg.norm(tN) / sn + np.linalg.norm(tR) / sr) / T
+        dD = np.abs(D[i] - o["D"]).max()
+        sS = e * o["F_D"] * np.abs(o["P_D"]).sum()
+        dS = np.abs(S[i] - o["S"]).max()
+        print(f"\n[zogy T={T} tile {i}] |dD| {dD:.2e} = {dD / e:.2f} e   |dS| = {dS / sS:.2f} e F_D |P_D|_1")
+        assert dD <= 8 * e
+        assert dS <= 8 * sS
+        assert np.abs(PD[i] - o["P_D"]).max() <= 64 * F32_EPS * np.abs(o["P_D"]).max()
+        assert abs(sig[i] / o["sigma_S"] - 1) < 1e-6
