@@ -9,30 +9,34 @@
 
 #include <cuda_runtime.h>
 
+// the butterflies and the pass are host-callable too, so that a CPU driver can
+// run the same code thread by thread
+#define FFT_HD __host__ __device__ __forceinline__
+
 namespace fft {
 
 template <typename R> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
 
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename C> FFT_HD C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> FFT_HD C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> FFT_HD C cmul(C a, C b) {
     return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
+template <typename C> FFT_HD C cconj(C a) { return {a.x, -a.y}; }
 // a * (s i), s = -1 (forward) or +1 (inverse)
-template <int S, typename C> __device__ __forceinline__ C cmul_i(C a) {
+template <int S, typename C> FFT_HD C cmul_i(C a) {
     return S < 0 ? C{a.y, -a.x} : C{-a.y, a.x};
 }
 
-template <int S, typename C> __device__ __forceinline__ void dft2(C* v) {
+template <int S, typename C> FFT_HD void dft2(C* v) {
     const C a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
 
-template <int S, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+template <int S, typename C> FFT_HD void dft4(C& a0, C& a1, C& a2, C& a3) {
     const C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = cmul_i<S>(csub(a1, a3));
     a0 = cadd(t0, t2);
     a1 = cadd(t1, t3);
@@ -40,7 +44,7 @@ template <int S, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, 
     a3 = csub(t1, t3);
 }
 
-template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
+template <int S, typename C> FFT_HD void dft8(C* v) {
     using R = decltype(v[0].x);
     C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
     C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
@@ -61,7 +65,7 @@ template <int S, typename C> __device__ __forceinline__ void dft8(C* v) {
 // multiplies by e^{S 2 pi i r k / (Ns RAD)} (k = j mod Ns) and writes the
 // RAD-point DFT to b[(j / Ns) Ns RAD + k + r Ns].  tw[m] = e^{-2 pi i m / T}.
 template <int T, int RAD, int S, typename C>
-__device__ __forceinline__ void stockham_pass(const C* a, C* b, const C* tw, int Ns, int lane, int nlanes) {
+FFT_HD void stockham_pass(const C* a, C* b, const C* tw, int Ns, int lane, int nlanes) {
     for (int j = lane; j < T / RAD; j += nlanes) {
         C v[RAD];
         const int k = j & (Ns - 1);

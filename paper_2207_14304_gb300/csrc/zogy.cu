@@ -93,7 +93,40 @@ __global__ void __launch_bounds__(256) zogy_psf_kernel(ZArgs a) {
     }
 }
 
-__device__ __forceinline__ float2 f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__host__ __device__ __forceinline__ float2 f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// The pointwise step for one frequency pair: A = z1(k), B = z1(-k), C = z2(k),
+// E = z2(-k).  Writes W(k) = D + i S and W(-k) = conj D + i conj S, P_D(k) and
+// returns |P_D(k)|^2 (host-callable, so a CPU driver can run the same code).
+__host__ __device__ __forceinline__ void zogy_pair(float2 A, float2 B, double2 C, double2 E, argus_zogy_tile tp,
+                                                   double eps2, float2& Wq, float2& Wp, float2& PD, double& p2) {
+    // N = (A + conj B) / 2, R = (A - conj B) / 2i
+    const float2 Nh = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+    const float2 Rh = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+    const double2 Pn = make_double2(0.5 * (C.x + E.x), 0.5 * (C.y - E.y));
+    const double2 Pr = make_double2(0.5 * (C.y + E.y), -0.5 * (C.x - E.x));
+    const double mn = Pn.x * Pn.x + Pn.y * Pn.y, mr = Pr.x * Pr.x + Pr.y * Pr.y;
+    const float Fn = tp.Fn, Fr = tp.Fr, sn = tp.sn, sr = tp.sr;
+    const float FD = Fr * Fn / sqrtf(sn * sn * Fr * Fr + sr * sr * Fn * Fn);
+    float2 Dh = make_float2(0.0f, 0.0f);
+    PD = make_float2(0.0f, 0.0f);
+    const float2 pn = f2(Pn), pr = f2(Pr);
+    const float den = sqrtf(sn * sn * Fr * Fr * (pr.x * pr.x + pr.y * pr.y) +
+                            sr * sr * Fn * Fn * (pn.x * pn.x + pn.y * pn.y));
+    if ((mn >= eps2 || mr >= eps2) && den > 0.0f) {
+        // Fr Pr N - Fn Pn R
+        const float2 u = make_float2(Fr * (pr.x * Nh.x - pr.y * Nh.y) - Fn * (pn.x * Rh.x - pn.y * Rh.y),
+                                     Fr * (pr.x * Nh.y + pr.y * Nh.x) - Fn * (pn.x * Rh.y + pn.y * Rh.x));
+        Dh = make_float2(u.x / den, u.y / den);
+        const float g = Fr * Fn / (FD * den);
+        PD = make_float2(g * (pr.x * pn.x - pr.y * pn.y), g * (pr.x * pn.y + pr.y * pn.x));
+    }
+    // S = F_D D conj(P_D)
+    const float2 Sh = make_float2(FD * (Dh.x * PD.x + Dh.y * PD.y), FD * (Dh.y * PD.x - Dh.x * PD.y));
+    Wq = make_float2(Dh.x - Sh.y, Dh.y + Sh.x);
+    Wp = make_float2(Dh.x + Sh.y, Sh.x - Dh.y);
+    p2 = (double)PD.x * PD.x + (double)PD.y * PD.y;
+}
 
 template <int T>
 __global__ void __launch_bounds__(256) zogy_combine_kernel(ZArgs a) {
@@ -109,39 +142,17 @@ __global__ void __launch_bounds__(256) zogy_combine_kernel(ZArgs a) {
         const int pq = ((T - ky) & (T - 1)) * T + ((T - kx) & (T - 1));
         if (pq >= q) {                                   // the pair (q, pq) is this thread's
             const long base = (long)t * T * T;
-            const float2 A = a.z1[base + q], B = a.z1[base + pq];
-            const double2 C = a.z2[base + q], E = a.z2[base + pq];
-            // N = (A + conj B) / 2, R = (A - conj B) / 2i
-            const float2 Nh = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-            const float2 Rh = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-            const double2 Pn = make_double2(0.5 * (C.x + E.x), 0.5 * (C.y - E.y));
-            const double2 Pr = make_double2(0.5 * (C.y + E.y), -0.5 * (C.x - E.x));
-            const double mn = Pn.x * Pn.x + Pn.y * Pn.y, mr = Pr.x * Pr.x + Pr.y * Pr.y;
-            const argus_zogy_tile tp = a.tiles[t];
-            const float Fn = tp.Fn, Fr = tp.Fr, sn = tp.sn, sr = tp.sr;
-            const float FD = Fr * Fn / sqrtf(sn * sn * Fr * Fr + sr * sr * Fn * Fn);
-            float2 Dh = make_float2(0.0f, 0.0f), PD = make_float2(0.0f, 0.0f);
-            const float2 pn = f2(Pn), pr = f2(Pr);
-            const float den = sqrtf(sn * sn * Fr * Fr * (pr.x * pr.x + pr.y * pr.y) +
-                                    sr * sr * Fn * Fn * (pn.x * pn.x + pn.y * pn.y));
-            if ((mn >= a.eps2 || mr >= a.eps2) && den > 0.0f) {
-                // Fr Pr N - Fn Pn R
-                const float2 u = make_float2(Fr * (pr.x * Nh.x - pr.y * Nh.y) - Fn * (pn.x * Rh.x - pn.y * Rh.y),
-                                             Fr * (pr.x * Nh.y + pr.y * Nh.x) - Fn * (pn.x * Rh.y + pn.y * Rh.x));
-                Dh = make_float2(u.x / den, u.y / den);
-                const float g = Fr * Fn / (FD * den);
-                PD = make_float2(g * (pr.x * pn.x - pr.y * pn.y), g * (pr.x * pn.y + pr.y * pn.x));
-            }
-            // S = F_D D conj(P_D)
-            const float2 Sh = make_float2(FD * (Dh.x * PD.x + Dh.y * PD.y), FD * (Dh.y * PD.x - Dh.x * PD.y));
-            // W = D + i S at q; conj(D) + i conj(S) at -q
-            a.z1[base + q] = make_float2(Dh.x - Sh.y, Dh.y + Sh.x);
-            if (pq != q) a.z1[base + pq] = make_float2(Dh.x + Sh.y, Sh.x - Dh.y);
+            float2 Wq, Wp, PD;
+            double p2;
+            zogy_pair(a.z1[base + q], a.z1[base + pq], a.z2[base + q], a.z2[base + pq], a.tiles[t], a.eps2, Wq, Wp,
+                      PD, p2);
+            a.z1[base + q] = Wq;
+            if (pq != q) a.z1[base + pq] = Wp;
             if (a.z3) {
                 a.z3[base + q] = PD;
                 if (pq != q) a.z3[base + pq] = make_float2(PD.x, -PD.y);
             }
-            psd = ((double)PD.x * PD.x + (double)PD.y * PD.y) * (pq != q ? 2.0 : 1.0);
+            psd = p2 * (pq != q ? 2.0 : 1.0);
         }
     }
     // per-tile sum of |P_D|^2: a CTA of 256 frequencies lies in one tile (T^2 % 256 == 0)
