@@ -1,0 +1,95 @@
+"""The kernels' own arithmetic on the CPU: the FFT butterflies and Stockham
+passes (csrc/fft.cuh) and the ZOGY per-frequency step (csrc/zogy.cu) are
+host-callable; small drivers (tests/host_drivers) compiled by nvcc as host
+code run them thread by thread with the kernels' load/store mapping, against
+numpy's FFT and the FP64 ZOGY oracle (Sec. 4.2).  Needs nvcc, no GPU."""
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2207_14304_gb300", "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+DRV = os.path.join(ROOT, "tests", "host_drivers")
+F32 = 2.0 ** -24
+TILE_DTYPE = [("x0", "<i4"), ("y0", "<i4"), ("Fn", "<f4"), ("Fr", "<f4"), ("sn", "<f4"), ("sr", "<f4")]
+
+
+@pytest.fixture(scope="module")
+def drivers(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    d = tmp_path_factory.mktemp("host_drivers")
+    for name in ("host_fft", "host_zogy"):
+        subprocess.check_call([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                               "-I", CSRC, "-I", INCLUDE, "-I", DRV, "-o", str(d / name),
+                               os.path.join(DRV, name + ".cu")])
+    return d
+
+
+@pytest.mark.parametrize("T", [256, 512])
+@pytest.mark.parametrize("dbl", [0, 1])
+def test_fft_passes_match_numpy(drivers, T, dbl):
+    rng = np.random.default_rng(T + dbl)
+    dt = np.complex128 if dbl else np.complex64
+    x = (rng.normal(size=(2, T, T)) + 1j * rng.normal(size=(2, T, T))).astype(dt)
+    x.tofile(drivers / "in.bin")
+    for sign in (-1, 1):
+        subprocess.check_call([str(drivers / "host_fft"), str(T), str(dbl), "2", str(sign),
+                               str(drivers / "in.bin"), str(drivers / "out.bin")])
+        y = np.fromfile(drivers / "out.bin", dtype=dt).reshape(2, T, T)
+        x64 = x.astype(np.complex128)
+        ref = np.fft.fft2(x64) if sign < 0 else np.fft.ifft2(x64) * T * T
+        err = np.abs(y - ref).max() / np.abs(ref).max()
+        # FP32: a few ulps times log2(T^2); FP64 the same in double
+        assert err < 8 * (2.0 ** -53 if dbl else F32) * math.log2(T * T), (sign, err)
+
+
+def _gauss(sig, half=15):
+    u = np.arange(-half, half + 1)
+    g = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * sig * sig))
+    return (g / g.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("T,spec", [(256, (1.05, 1.0, 18.0, 3.3, 2.0, 1.2)), (256, (0.9, 1.1, 10.0, 4.0, 1.3, 1.6)),
+                                    (256, (1.0, 1.0, 5.0, 0.0, 1.5, 1.5)), (256, (1.0, 1.0, 4.0, 2.0, 3.5, 3.0)),
+                                    (512, (1.0, 1.0, 12.0, 3.0, 1.8, 1.3))])
+def test_zogy_step_matches_the_oracle(drivers, T, spec):
+    """D within 8 e, S within 8 e F_D ||P_D||_1, P_D within 64 ulps of its maximum,
+    sigma_S within 1e-6 (the bars of the GPU test; e is its FP32 error unit).
+    Includes a noiseless reference and PSFs wide enough for the frequency floor."""
+    from oracle import proper
+    Fn, Fr, sn, sr, gn, gr = spec
+    rng = np.random.default_rng(T + int(10 * gn))
+    pn, pr = _gauss(gn), _gauss(gr)
+    sky = np.zeros((T, T))
+    n = T * T // 130
+    np.add.at(sky, (rng.integers(0, T, n), rng.integers(0, T, n)), 1e2 * 1e4 ** rng.random(n))
+    conv = lambda img, P: np.fft.ifft2(np.fft.fft2(img) * np.fft.fft2(proper.psf_on_tile(P, img.shape))).real
+    N = (Fn * conv(sky, pn) + rng.normal(0, max(sn, 1.0), (T, T))).astype(np.float32)
+    R = (Fr * conv(sky, pr) + rng.normal(0, max(sr, 0.5), (T, T))).astype(np.float32)
+    d = drivers / f"zogy_{T}_{gn}_{sr}"
+    d.mkdir(exist_ok=True)
+    np.array([31, 0], np.int32).tofile(d / "hdr.bin")
+    rec = np.zeros(1, TILE_DTYPE)
+    rec[0] = (0, 0, Fn, Fr, sn, sr)
+    rec.tofile(d / "tile.bin")
+    for name, a in (("N", N), ("R", R), ("pn", pn), ("pr", pr)):
+        a.tofile(d / f"{name}.bin")
+    subprocess.check_call([str(drivers / "host_zogy"), str(T), str(d)])
+    D = np.fromfile(d / "D.bin", np.float32).reshape(T, T)
+    S = np.fromfile(d / "S.bin", np.float32).reshape(T, T)
+    P = np.fromfile(d / "P.bin", np.float32).reshape(T, T)
+    sig = np.fromfile(d / "sig.bin", np.float64)[0]
+    f = lambda v: float(np.float32(v))
+    o = proper.zogy(N, R, pn.astype(np.float64), pr.astype(np.float64), f(Fn), f(Fr), f(sn), f(sr))
+    e = F32 * math.log2(T * T) * (np.linalg.norm(N) / sn + (np.linalg.norm(R) / sr if sr > 0 else 0.0)) / T
+    assert np.abs(D - o["D"]).max() <= 8 * e
+    assert np.abs(S - o["S"]).max() <= 8 * e * o["F_D"] * np.abs(o["P_D"]).sum()
+    assert np.abs(P - o["P_D"]).max() <= 64 * F32 * np.abs(o["P_D"]).max()
+    assert abs(sig / o["sigma_S"] - 1) < 1e-6
