@@ -445,6 +445,10 @@ int argus_background(argus_ctx *ctx, const float *img, const uint8_t *flags, arg
                      int filt, float min_frac, double *mesh, float *map, argus_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Proper-image statistics on square tiles: ZOGY subtraction and proper
+ * coaddition share one plan (transform buffers, 64 bytes per tile pixel, and
+ * the twiddle tables of one tile size).
+ *
  * ZOGY proper image subtraction on square tiles (paper Sec. 4.2: ZOGY for
  * base cadence and deep coadds; the statistic of Zackay, Ofek & Gal-Yam 2016).
  * Each tile is T x T pixels of the new image N and the registered reference R
@@ -458,9 +462,8 @@ int argus_background(argus_ctx *ctx, const float *img, const uint8_t *flags, arg
  * with D, P_D and S set to 0 at frequencies where max(|Pn|, |Pr|) < eps (the
  * PSFs have unit sum; below the floor their transforms are rounding; 1e-8 is
  * the reference value).  Images and the pointwise step are FP32, the PSF
- * transforms FP64.  A plan owns the transform buffers (48 bytes per tile
- * pixel) and the twiddle tables of one tile size. */
-typedef struct argus_zogy_plan argus_zogy_plan;
+ * transforms FP64. */
+typedef struct argus_proper_plan argus_proper_plan;
 
 typedef struct {
     int x0, y0;      /* frame position of the tile's pixel (0, 0) */
@@ -469,18 +472,40 @@ typedef struct {
 } argus_zogy_tile;
 
 /* tile in {256, 512, 1024}; 1 <= max_tiles <= 65536.  Allocates on `device`. */
-int argus_zogy_plan_create(int device, int tile, int max_tiles, argus_zogy_plan **plan);
-int argus_zogy_plan_destroy(argus_zogy_plan *plan);
+int argus_proper_plan_create(int device, int tile, int max_tiles, argus_proper_plan **plan);
+int argus_proper_plan_destroy(argus_proper_plan *plan);
 
 /* N, R: device float [h][pitch] (one shape); tiles: device argus_zogy_tile
  * [n_tiles]; psf_n, psf_r: device float [n_tiles][psf_size][psf_size], odd
  * psf_size <= 63; D, S and P_D (nullable): device float [n_tiles][T][T];
  * sigma_S (nullable): device double [n_tiles].  1 <= n_tiles <= max_tiles.
  * Calls on one plan must not overlap. */
-int argus_zogy(argus_zogy_plan *plan, const float *N, const float *R, argus_shape shape,
+int argus_zogy(argus_proper_plan *plan, const float *N, const float *R, argus_shape shape,
                const argus_zogy_tile *tiles, int n_tiles, const float *psf_n, const float *psf_r,
                int psf_size, float eps, float *D, float *S, float *P_D, double *sigma_S,
                argus_stream stream);
+
+/* Proper coaddition (paper Sec. 4.1.3: per-image matched filtering of
+ * pre-aligned tiles; the statistic of Zackay & Ofek 2017) on the tiles of a
+ * stack of registered, background-subtracted frames M_j with PSFs P_j (per
+ * tile and frame), zero points F_j and background noise s_j:
+ *   S   = IDFT[sum_j (F_j / s_j^2) conj(P_j) M_j]      score coadd (the matched-filter sum)
+ *   den = sqrt(sum_j F_j^2 / s_j^2 |P_j|^2),   F_R = sqrt(sum_j F_j^2 / s_j^2)
+ *   R   = IDFT[S / den]                            proper coadd, unit-variance white noise
+ *   P_R = IDFT[den / F_R]                          its PSF (unit sum)
+ * with R and P_R 0 at frequencies where max_j |P_j| < eps (S keeps every
+ * frequency); sigma_S = sqrt(sum_j F_j^2 / s_j^2 sum P_j^2) per tile.
+ * stack: device float [n_frames][h][pitch] (one shape; pixels off the frame
+ * are 0); origins: device int [n_tiles][2] (tile pixel (0, 0) in the frame);
+ * F, sigma: device float [n_frames] (a frame with sigma <= 0 is left out);
+ * psfs: device float [n_tiles][n_frames][psf_size][psf_size], odd psf_size
+ * <= 63; S, R, P_R (nullable): device float [n_tiles][T][T]; F_R (nullable):
+ * device double [1]; sigma_S (nullable): device double [n_tiles].
+ * 1 <= n_frames <= 64.  Frames go through the transforms in pairs. */
+int argus_proper_coadd(argus_proper_plan *plan, const float *stack, int n_frames, argus_shape shape,
+                       const int *origins, int n_tiles, const float *F, const float *sigma, const float *psfs,
+                       int psf_size, float eps, float *S, float *R, float *P_R, double *F_R, double *sigma_S,
+                       argus_stream stream);
 
 #ifdef __cplusplus
 }

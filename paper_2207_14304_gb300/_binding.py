@@ -125,9 +125,10 @@ SIGNATURES = {
     "argus_minipix": ([P, P, SH, I, P, I, P, P, I, P, P, P, P, I, P, P], I),
     "argus_lowres": ([P, P, P, SH, I, P, C.c_long, P], I),
     "argus_background": ([P, P, P, SH, I, I, F, P, P, P], I),
-    "argus_zogy_plan_create": ([I, I, I, C.POINTER(P)], I),
-    "argus_zogy_plan_destroy": ([P], I),
+    "argus_proper_plan_create": ([I, I, I, C.POINTER(P)], I),
+    "argus_proper_plan_destroy": ([P], I),
     "argus_zogy": ([P, P, P, SH, P, I, P, P, I, F, P, P, P, P, P], I),
+    "argus_proper_coadd": ([P, P, I, SH, P, I, P, P, P, I, F, P, P, P, P, P, P], I),
 }
 
 
@@ -425,15 +426,15 @@ def argus_background(ctx, img, flags, shape, box, filt, min_frac, mesh, map_=Non
 ZOGY_TILE_DTYPE = [("x0", "<i4"), ("y0", "<i4"), ("Fn", "<f4"), ("Fr", "<f4"), ("sn", "<f4"), ("sr", "<f4")]
 
 
-def zogy_plan_create(device: int, tile: int, max_tiles: int):
+def proper_plan_create(device: int, tile: int, max_tiles: int):
     plan = P()
-    _check(load().argus_zogy_plan_create(int(device), int(tile), int(max_tiles), C.byref(plan)),
-           "argus_zogy_plan_create")
+    _check(load().argus_proper_plan_create(int(device), int(tile), int(max_tiles), C.byref(plan)),
+           "argus_proper_plan_create")
     return plan
 
 
-def zogy_plan_destroy(plan):
-    _check(load().argus_zogy_plan_destroy(plan), "argus_zogy_plan_destroy")
+def proper_plan_destroy(plan):
+    _check(load().argus_proper_plan_destroy(plan), "argus_proper_plan_destroy")
 
 
 def argus_zogy(plan, N, R, shape, tiles, n_tiles, psf_n, psf_r, psf_size, eps, D, S, P_D=None, sigma_S=None,
@@ -442,6 +443,13 @@ def argus_zogy(plan, N, R, shape, tiles, n_tiles, psf_n, psf_r, psf_size, eps, D
     _check(load().argus_zogy(plan, _ptr(N), _ptr(R), shape, _ptr(tiles), int(n_tiles), _ptr(psf_n), _ptr(psf_r),
                              int(psf_size), float(eps), _ptr(D), _ptr(S), _ptr(P_D), _ptr(sigma_S),
                              _stream(stream)), "argus_zogy")
+
+
+def argus_proper_coadd(plan, stack, n_frames, shape, origins, n_tiles, F, sigma, psfs, psf_size, eps, S, R, P_R=None,
+                       F_R=None, sigma_S=None, stream=None):
+    _check(load().argus_proper_coadd(plan, _ptr(stack), int(n_frames), shape, _ptr(origins), int(n_tiles), _ptr(F),
+                                     _ptr(sigma), _ptr(psfs), int(psf_size), float(eps), _ptr(S), _ptr(R),
+                                     _ptr(P_R), _ptr(F_R), _ptr(sigma_S), _stream(stream)), "argus_proper_coadd")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):

@@ -1,5 +1,8 @@
-// ZOGY proper image subtraction on square tiles (paper Sec. 4.2: ZOGY at base
-// cadence and in deep coadds; the statistic of Zackay, Ofek & Gal-Yam 2016).
+// Proper-image statistics on square tiles: ZOGY subtraction (below) and the
+// proper coadd (after it) share one plan and the FFT kernels of fft.cuh.
+//
+// ZOGY proper image subtraction (paper Sec. 4.2: ZOGY at base cadence and in
+// deep coadds; the statistic of Zackay, Ofek & Gal-Yam 2016).
 //
 // Per tile (T x T, periodic), with hats for DFTs:
 //   1. pack:    z1 = N + i R (FP32), z2 = P_n + i P_r (FP64; the PSF stamps
@@ -27,13 +30,14 @@
 #include <cmath>
 #include <cstdlib>
 
-struct argus_zogy_plan {
+struct argus_proper_plan {
     int device;
     int tile;
     int max_tiles;
     float2* z1;       // [max_tiles][T][T]
     double2* z2;      // [max_tiles][T][T]
-    float2* z3;       // [max_tiles][T][T] (P_D)
+    float2* z3;       // [max_tiles][T][T] (ZOGY: P_D; coadd: the score accumulator, then P_R)
+    double2* z4;      // [max_tiles][T][T] (coadd: sum F^2/s^2 |P|^2 and max |P|^2)
     double* psd;      // [max_tiles] sum |P_D(k)|^2
     float2* tw32;     // [T] e^{-2 pi i m / T}
     double2* tw64;
@@ -216,7 +220,7 @@ bool set_smem() {
 }
 
 template <int T>
-int run(argus_zogy_plan* p, ZArgs& a, cudaStream_t s) {
+int run(argus_proper_plan* p, ZArgs& a, cudaStream_t s) {
     const long total = (long)a.n_tiles * T * T;
     const unsigned grid = (unsigned)((total + 255) / 256);
     unsigned g2 = grid > 152u * 16u ? 152u * 16u : grid;
@@ -241,16 +245,232 @@ int run(argus_zogy_plan* p, ZArgs& a, cudaStream_t s) {
     return argus_launch_status();
 }
 
+// ---------------------------------------------------------------------------
+// Proper coaddition (paper Sec. 4.1.3: a per-image matched filter; the
+// statistic of Zackay & Ofek 2017).  Frames go through the transforms in
+// pairs (M_j + i M_{j+1}, P_j + i P_{j+1}); per frequency the accumulators
+// hold the score S = sum_j (F_j / s_j^2) conj(P_j) M_j (FP32) and, in FP64,
+// den^2 = sum_j F_j^2 / s_j^2 |P_j|^2 and max_j |P_j|^2.  Then
+//   R = S / den (0 below the frequency floor), W = S + i R -> one inverse
+//   transform gives the score coadd (real part) and the proper coadd
+//   (imaginary part);  P_R = IDFT[den / F_R],  F_R = sqrt(sum_j F_j^2 / s_j^2).
+
+struct CArgs {
+    const float* stack;     // [n_frames][h][pitch]
+    long frame_stride;
+    long pitch;
+    int w, h;
+    const int* origins;     // [n_tiles][2]
+    int n_tiles;
+    const float* F;         // [n_frames]
+    const float* sig;       // [n_frames]
+    int n_frames;
+    const float* psfs;      // [n_tiles][n_frames][ps][ps]
+    int ps;
+    int j0;                 // first frame of the pair in flight
+    double eps2;
+    float2* z1;
+    double2* z2;
+    float2* acc;            // score accumulator, then the P_R spectrum
+    double2* acc2;          // (den^2, max |P|^2)
+    float* S;
+    float* R;
+    float* PR;
+    double* F_R;
+    double* sigma_S;
+};
+
+// Frame j's matched-filter weights: F / s^2 for the score, F^2 / s^2 for den^2
+// (a frame with s <= 0, or past the last frame, has none).
+__host__ __device__ __forceinline__ void frame_weights(const float* F, const float* sig, int n, int j, float& w,
+                                                       double& a) {
+    w = 0.0f;
+    a = 0.0;
+    if (j < n && sig[j] > 0.0f) {
+        w = F[j] / (sig[j] * sig[j]);
+        a = (double)F[j] * F[j] / ((double)sig[j] * sig[j]);
+    }
+}
+
+// Accumulate one frame pair at frequency k: A = z1(k), B = z1(-k), C = z2(k),
+// E = z2(-k) (host-callable, so a CPU driver can run the same code).
+__host__ __device__ __forceinline__ void coadd_accum_point(float2 A, float2 B, double2 C, double2 E, float w0,
+                                                           float w1, double a0, double a1, float2& acc,
+                                                           double2& acc2) {
+    const float2 M0 = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+    const float2 M1 = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+    const double2 P0 = make_double2(0.5 * (C.x + E.x), 0.5 * (C.y - E.y));
+    const double2 P1 = make_double2(0.5 * (C.y + E.y), -0.5 * (C.x - E.x));
+    const float2 p0 = f2(P0), p1 = f2(P1);
+    // conj(P) M
+    acc.x += w0 * (p0.x * M0.x + p0.y * M0.y) + w1 * (p1.x * M1.x + p1.y * M1.y);
+    acc.y += w0 * (p0.x * M0.y - p0.y * M0.x) + w1 * (p1.x * M1.y - p1.y * M1.x);
+    const double q0 = P0.x * P0.x + P0.y * P0.y, q1 = P1.x * P1.x + P1.y * P1.y;
+    acc2.x += a0 * q0 + a1 * q1;
+    double m = acc2.y;
+    if (a0 > 0.0 && q0 > m) m = q0;
+    if (a1 > 0.0 && q1 > m) m = q1;
+    acc2.y = m;
+}
+
+// The last step at frequency k: W = S + i R and the P_R spectrum.
+__host__ __device__ __forceinline__ void coadd_final_point(float2 Sh, double2 acc2, double FR, double eps2, float2& W,
+                                                           float2& PRh) {
+    const double den = sqrt(acc2.x);
+    float2 Rh = make_float2(0.0f, 0.0f);
+    PRh = make_float2(0.0f, 0.0f);
+    if (acc2.y >= eps2 && den > 0.0) {
+        const float d = (float)den;
+        Rh = make_float2(Sh.x / d, Sh.y / d);
+        PRh = make_float2((float)(den / FR), 0.0f);
+    }
+    W = make_float2(Sh.x - Rh.y, Sh.y + Rh.x);
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) coadd_pack_kernel(CArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    const bool two = a.j0 + 1 < a.n_frames;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / (T * T));
+        const int q = (int)(e - (long)t * T * T);
+        const int gx = a.origins[2 * t] + (q % T), gy = a.origins[2 * t + 1] + q / T;
+        float m0 = 0.0f, m1 = 0.0f;
+        if (gx >= 0 && gy >= 0 && gx < a.w && gy < a.h) {       // pixels off the frame are 0
+            const long p = (long)gy * a.pitch + gx;
+            m0 = a.stack[a.j0 * a.frame_stride + p];
+            if (two) m1 = a.stack[(a.j0 + 1) * a.frame_stride + p];
+        }
+        a.z1[e] = make_float2(m0, m1);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) coadd_psf_kernel(CArgs a) {
+    const int pp = a.ps * a.ps, hh = a.ps / 2;
+    const long total = (long)a.n_tiles * pp;
+    const bool two = a.j0 + 1 < a.n_frames;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / pp);
+        const int i = (int)(e - (long)t * pp);
+        const int v = i / a.ps, u = i - v * a.ps;
+        const int yy = (v - hh + T) & (T - 1), xx = (u - hh + T) & (T - 1);
+        const float* pt = a.psfs + ((long)t * a.n_frames + a.j0) * pp;
+        a.z2[(long)t * T * T + yy * T + xx] = make_double2((double)pt[i], two ? (double)pt[pp + i] : 0.0);
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) coadd_accum_kernel(CArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    float w0, w1;
+    double a0, a1;
+    frame_weights(a.F, a.sig, a.n_frames, a.j0, w0, a0);
+    frame_weights(a.F, a.sig, a.n_frames, a.j0 + 1, w1, a1);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / (T * T));
+        const int q = (int)(e - (long)t * T * T);
+        const int ky = q / T, kx = q - ky * T;
+        const long base = (long)t * T * T;
+        const long pe = base + ((T - ky) & (T - 1)) * T + ((T - kx) & (T - 1));
+        float2 acc = a.acc[e];
+        double2 acc2 = a.acc2[e];
+        coadd_accum_point(a.z1[e], a.z1[pe], a.z2[e], a.z2[pe], w0, w1, a0, a1, acc, acc2);
+        a.acc[e] = acc;
+        a.acc2[e] = acc2;
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) coadd_final_kernel(CArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    double fr2 = 0.0;
+    for (int j = 0; j < a.n_frames; j++) {
+        float w;
+        double aj;
+        frame_weights(a.F, a.sig, a.n_frames, j, w, aj);
+        fr2 += aj;
+    }
+    const double FR = sqrt(fr2);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        float2 W, PRh;
+        coadd_final_point(a.acc[e], a.acc2[e], FR, a.eps2, W, PRh);
+        a.z1[e] = W;
+        a.acc[e] = PRh;
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) coadd_unpack_kernel(CArgs a) {
+    const long total = (long)a.n_tiles * T * T;
+    const float inv = 1.0f / ((float)T * (float)T);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const float2 w = a.z1[e];
+        a.S[e] = w.x * inv;
+        a.R[e] = w.y * inv;
+        if (a.PR) a.PR[e] = a.acc[e].x * inv;
+    }
+}
+
+// sigma_S per tile (sqrt(sum_j F_j^2 / s_j^2 sum P_tj^2)) and F_R, one thread per tile.
+__global__ void coadd_norm_kernel(CArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tiles) return;
+    const int pp = a.ps * a.ps;
+    double v = 0.0, fr2 = 0.0;
+    for (int j = 0; j < a.n_frames; j++) {
+        float w;
+        double aj;
+        frame_weights(a.F, a.sig, a.n_frames, j, w, aj);
+        const float* pt = a.psfs + ((long)t * a.n_frames + j) * pp;
+        double s2 = 0.0;
+        for (int i = 0; i < pp; i++) s2 += (double)pt[i] * pt[i];
+        v += aj * s2;
+        fr2 += aj;
+    }
+    if (a.sigma_S) a.sigma_S[t] = sqrt(v);
+    if (a.F_R && t == 0) *a.F_R = sqrt(fr2);
+}
+
+template <int T>
+int run_coadd(argus_proper_plan* p, CArgs& a, cudaStream_t s) {
+    const long total = (long)a.n_tiles * T * T;
+    long g = (total + 255) / 256;
+    const unsigned grid = (unsigned)(g > 152L * 16 ? 152L * 16 : g);
+    if (cudaMemsetAsync(a.acc, 0, (size_t)total * sizeof(float2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+    if (cudaMemsetAsync(a.acc2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+    const long pp = (long)a.n_tiles * a.ps * a.ps;
+    for (int j0 = 0; j0 < a.n_frames; j0 += 2) {
+        a.j0 = j0;
+        if (cudaMemsetAsync(a.z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+        coadd_pack_kernel<T><<<grid, 256, 0, s>>>(a);
+        coadd_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
+        argus_count_launch(2);
+        fft2d<T, -1, float>(a.z1, a.n_tiles, p->tw32, s);
+        fft2d<T, -1, double>(a.z2, a.n_tiles, p->tw64, s);
+        coadd_accum_kernel<T><<<grid, 256, 0, s>>>(a);
+        argus_count_launch(1);
+    }
+    coadd_final_kernel<T><<<grid, 256, 0, s>>>(a);
+    argus_count_launch(1);
+    fft2d<T, 1, float>(a.z1, a.n_tiles, p->tw32, s);
+    if (a.PR) fft2d<T, 1, float>(a.acc, a.n_tiles, p->tw32, s);
+    coadd_unpack_kernel<T><<<grid, 256, 0, s>>>(a);
+    coadd_norm_kernel<<<(a.n_tiles + 127) / 128, 128, 0, s>>>(a);
+    argus_count_launch(2);
+    return argus_launch_status();
+}
+
 }  // namespace
 
-extern "C" int argus_zogy_plan_create(int device, int tile, int max_tiles, argus_zogy_plan** out) {
+extern "C" int argus_proper_plan_create(int device, int tile, int max_tiles, argus_proper_plan** out) {
     if (!out || (tile != 256 && tile != 512 && tile != 1024) || max_tiles < 1 || max_tiles > 65536)
         return ARGUS_ERR_ARG;
     *out = nullptr;
     if (cudaSetDevice(device) != cudaSuccess) return ARGUS_ERR_CUDA;
     const bool smem_ok = tile == 256 ? set_smem<256>() : tile == 512 ? set_smem<512>() : set_smem<1024>();
     if (!smem_ok) return ARGUS_ERR_CUDA;
-    argus_zogy_plan* p = (argus_zogy_plan*)calloc(1, sizeof(argus_zogy_plan));
+    argus_proper_plan* p = (argus_proper_plan*)calloc(1, sizeof(argus_proper_plan));
     if (!p) return ARGUS_ERR_NOMEM;
     p->device = device;
     p->tile = tile;
@@ -259,6 +479,7 @@ extern "C" int argus_zogy_plan_create(int device, int tile, int max_tiles, argus
     bool ok = cudaMalloc((void**)&p->z1, n * sizeof(float2)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&p->z2, n * sizeof(double2)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&p->z3, n * sizeof(float2)) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&p->z4, n * sizeof(double2)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&p->psd, (size_t)max_tiles * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&p->tw32, (size_t)tile * sizeof(float2)) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&p->tw64, (size_t)tile * sizeof(double2)) == cudaSuccess;
@@ -281,7 +502,7 @@ extern "C" int argus_zogy_plan_create(int device, int tile, int max_tiles, argus
         free(h32);
     }
     if (!ok) {
-        cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
+        cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->z4); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
         free(p);
         return ARGUS_ERR_NOMEM;
     }
@@ -289,15 +510,15 @@ extern "C" int argus_zogy_plan_create(int device, int tile, int max_tiles, argus
     return ARGUS_OK;
 }
 
-extern "C" int argus_zogy_plan_destroy(argus_zogy_plan* p) {
+extern "C" int argus_proper_plan_destroy(argus_proper_plan* p) {
     if (!p) return ARGUS_ERR_ARG;
     cudaSetDevice(p->device);
-    cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
+    cudaFree(p->z1); cudaFree(p->z2); cudaFree(p->z3); cudaFree(p->z4); cudaFree(p->psd); cudaFree(p->tw32); cudaFree(p->tw64);
     free(p);
     return ARGUS_OK;
 }
 
-extern "C" int argus_zogy(argus_zogy_plan* plan, const float* N, const float* R, argus_shape shape,
+extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* R, argus_shape shape,
                           const argus_zogy_tile* tiles, int n_tiles, const float* psf_n, const float* psf_r,
                           int psf_size, float eps, float* D, float* S, float* P_D, double* sigma_S,
                           argus_stream stream) {
@@ -318,5 +539,30 @@ extern "C" int argus_zogy(argus_zogy_plan* plan, const float* N, const float* R,
         case 256: return run<256>(plan, a, s);
         case 512: return run<512>(plan, a, s);
         default: return run<1024>(plan, a, s);
+    }
+}
+
+extern "C" int argus_proper_coadd(argus_proper_plan* plan, const float* stack, int n_frames, argus_shape shape,
+                                  const int* origins, int n_tiles, const float* F, const float* sigma,
+                                  const float* psfs, int psf_size, float eps, float* S, float* R, float* P_R,
+                                  double* F_R, double* sigma_S, argus_stream stream) {
+    if (!plan || !stack || !origins || !F || !sigma || !psfs || !S || !R || n_tiles < 1 ||
+        n_tiles > plan->max_tiles || n_frames < 1 || n_frames > ARGUS_MAX_FRAMES)
+        return ARGUS_ERR_ARG;
+    if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
+    int st = argus_check_shape(shape, (size_t)-1);
+    if (st) return st;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    CArgs a;
+    a.stack = stack; a.frame_stride = (long)shape.h * shape.pitch; a.pitch = shape.pitch;
+    a.w = shape.w; a.h = shape.h; a.origins = origins; a.n_tiles = n_tiles; a.F = F; a.sig = sigma;
+    a.n_frames = n_frames; a.psfs = psfs; a.ps = psf_size; a.j0 = 0; a.eps2 = (double)eps * (double)eps;
+    a.z1 = plan->z1; a.z2 = plan->z2; a.acc = plan->z3; a.acc2 = plan->z4;
+    a.S = S; a.R = R; a.PR = P_R; a.F_R = F_R; a.sigma_S = sigma_S;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (plan->tile) {
+        case 256: return run_coadd<256>(plan, a, s);
+        case 512: return run_coadd<512>(plan, a, s);
+        default: return run_coadd<1024>(plan, a, s);
     }
 }

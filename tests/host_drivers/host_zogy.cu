@@ -7,7 +7,7 @@
 #include <cstring>
 #include <cmath>
 #include <vector>
-#include "zogy.cu"
+#include "proper.cu"
 #include "host_pass.h"
 
 // library helpers the translation unit references (host driver only)

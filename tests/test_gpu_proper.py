@@ -1,11 +1,13 @@
-"""ZOGY on the GPU (Sec. 4.2) against the FP64 oracle, tile by tile.
+"""ZOGY (Sec. 4.2) and the proper coadd (Sec. 4.1.3) on the GPU against the FP64
+oracle, tile by tile.
 
 Tolerances, from the FP32 rounding of the image transforms (the PSF
 transforms are FP64): with u = 2^-24 and the unit
   e = u log2(T^2) (||N||_2 / s_n + ||R||_2 / s_r) / T
 (the rms rounding of a T^2-point FP32 FFT carried through the quotient, whose
-gain is at most 1/s_n and 1/s_r), |dD| <= 8 e and |dS| <= 8 e F_D ||P_D||_1
-(S filters D with F_D P_D); an FP32 emulation of the same algorithm (numpy's
+gain is at most 1/s_n and 1/s_r), |dD| <= 8 e and |dS| <= 8 (e F_D ||P_D||_1 +
+u log2(T^2) ||D||_2 / T) (S filters D with F_D P_D and shares D's inverse
+transform); an FP32 emulation of the same algorithm (numpy's
 single-precision FFT) stays within 1.4 e and 3.1 e F_D ||P_D||_1 on these
 tiles.  P_D within 64 u max|P_D|, sigma_S within 1e-6 relative.
 
@@ -21,7 +23,7 @@ from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300.synth import pitch_for
 from tests.gpu_helpers import F32_EPS, dev_pitched
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="ZOGY kernels not yet run on a GPU")]
+pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="proper-image kernels not yet run on a GPU")]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -65,7 +67,7 @@ def test_zogy_parity(ora, T, origins):
         rec[i] = (x0, y0, Fn, Fr, sn, sr)
         pn[i], pr[i] = _gauss(gn), _gauss(gr)
     nt = len(origins)
-    plan = B.zogy_plan_create(0, T, 4)
+    plan = B.proper_plan_create(0, T, 4)
     try:
         pitch = pitch_for(w)
         dN, dR = dev_pitched(N), dev_pitched(R)
@@ -79,7 +81,7 @@ def test_zogy_parity(ora, T, origins):
         torch.cuda.synchronize()
         D, S, PD, sig = D.cpu().numpy(), S.cpu().numpy(), PD.cpu().numpy(), sig.cpu().numpy()
     finally:
-        B.zogy_plan_destroy(plan)
+        B.proper_plan_destroy(plan)
     for i, (x0, y0) in enumerate(origins):
         Fn, Fr, sn, sr = (float(rec[i][k]) for k in ("Fn", "Fr", "sn", "sr"))
         tN = np.zeros((T, T), np.float32)
@@ -90,10 +92,62 @@ def test_zogy_parity(ora, T, origins):
         o = proper.zogy(tN, tR, pn[i].astype(np.float64), pr[i].astype(np.float64), Fn, Fr, sn, sr)
         e = F32_EPS * math.log2(T * T) * (np.linalg.norm(tN) / sn + np.linalg.norm(tR) / sr) / T
         dD = np.abs(D[i] - o["D"]).max()
-        sS = e * o["F_D"] * np.abs(o["P_D"]).sum()
+        # S filters D with F_D P_D and shares D's inverse transform
+        sS = e * o["F_D"] * np.abs(o["P_D"]).sum() + F32_EPS * math.log2(T * T) * np.linalg.norm(o["D"]) / T
         dS = np.abs(S[i] - o["S"]).max()
         print(f"\n[zogy T={T} tile {i}] |dD| {dD:.2e} = {dD / e:.2f} e   |dS| = {dS / sS:.2f} e F_D |P_D|_1")
         assert dD <= 8 * e
         assert dS <= 8 * sS
         assert np.abs(PD[i] - o["P_D"]).max() <= 64 * F32_EPS * np.abs(o["P_D"]).max()
         assert abs(sig[i] / o["sigma_S"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("T,J", [(256, 3), (512, 2)])
+def test_proper_coadd_parity(ora, T, J):
+    """Proper coadd (Sec. 4.1.3) through the entry point against the oracle per tile:
+    R within 8 e_R, S within 8 e_S (the units of tests/test_host_kernels.py), P_R
+    within 64 ulps of its maximum, F_R and sigma_S within 1e-6."""
+    from oracle import proper
+    w, h = 700, 600
+    rng = np.random.default_rng(T + J)
+    sky = np.zeros((h, w))
+    n = w * h // 150
+    np.add.at(sky, (rng.integers(0, h, n), rng.integers(0, w, n)), 1e2 * 1e4 ** rng.random(n))
+    conv = lambda img, P: np.fft.ifft2(np.fft.fft2(img) * np.fft.fft2(proper.psf_on_tile(P, img.shape))).real
+    origins = [(0, 0), (400, 300)] if T == 256 else [(100, 50)]
+    nt = len(origins)
+    gs = [1.2, 1.9, 1.5][:J]
+    F = np.array([1.0, 0.8, 1.2][:J], np.float32)
+    sg = np.array([5.0, 9.0, 4.0][:J], np.float32)
+    frames = [(f * conv(sky, _gauss(g)) + rng.normal(0, s, (h, w))).astype(np.float32) for g, f, s in zip(gs, F, sg)]
+    psfs = np.stack([np.stack([_gauss(g + 0.1 * t) for g in gs]) for t in range(nt)])     # [nt][J][31][31]
+    pitch = pitch_for(w)
+    plan = B.proper_plan_create(0, T, 4)
+    try:
+        stack = torch.zeros((J, h, pitch), device="cuda")
+        for j in range(J):
+            stack[j, :, :w] = torch.from_numpy(frames[j]).cuda()
+        d_org = torch.tensor(origins, dtype=torch.int32, device="cuda")
+        S = torch.full((nt, T, T), -7.0, device="cuda")
+        R = torch.full((nt, T, T), -7.0, device="cuda")
+        PR = torch.full((nt, T, T), -7.0, device="cuda")
+        FR = torch.zeros(1, dtype=torch.float64, device="cuda")
+        sig = torch.zeros(nt, dtype=torch.float64, device="cuda")
+        B.argus_proper_coadd(plan, stack, J, B.argus_shape(w, h, pitch), d_org, nt, torch.from_numpy(F).cuda(),
+                             torch.from_numpy(sg).cuda(), torch.from_numpy(psfs).cuda(), 31, 1e-8, S, R, PR, FR, sig)
+        torch.cuda.synchronize()
+        S, R, PR, FR, sig = (t.cpu().numpy() for t in (S, R, PR, FR, sig))
+    finally:
+        B.proper_plan_destroy(plan)
+    for i, (x0, y0) in enumerate(origins):
+        Ms = [np.ascontiguousarray(f[y0:y0 + T, x0:x0 + T]) for f in frames]
+        Ps = [psfs[i, j].astype(np.float64) for j in range(J)]
+        o = proper.proper_coadd(Ms, Ps, [float(f) for f in F], [float(s) for s in sg])
+        lg = F32_EPS * math.log2(T * T) / T
+        eR = lg * sum(np.linalg.norm(M) / s for M, s in zip(Ms, sg))
+        eS = lg * (sum(f / s ** 2 * np.abs(P).sum() * np.linalg.norm(M) for M, P, f, s in zip(Ms, Ps, F, sg))
+                   + np.linalg.norm(o["R"]))
+        assert np.abs(R[i] - o["R"]).max() <= 8 * eR
+        assert np.abs(S[i] - o["S"]).max() <= 8 * eS
+        assert np.abs(PR[i] - o["P_R"]).max() <= 64 * F32_EPS * np.abs(o["P_R"]).max()
+        assert abs(FR[0] / o["F_R"] - 1) < 1e-6 and abs(sig[i] / o["sigma_S"] - 1) < 1e-6

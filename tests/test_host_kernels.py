@@ -1,5 +1,5 @@
 """The kernels' own arithmetic on the CPU: the FFT butterflies and Stockham
-passes (csrc/fft.cuh) and the ZOGY per-frequency step (csrc/zogy.cu) are
+passes (csrc/fft.cuh) and the per-frequency steps of ZOGY and the proper coadd (csrc/proper.cu) are
 host-callable; small drivers (tests/host_drivers) compiled by nvcc as host
 code run them thread by thread with the kernels' load/store mapping, against
 numpy's FFT and the FP64 ZOGY oracle (Sec. 4.2).  Needs nvcc, no GPU."""
@@ -25,7 +25,7 @@ def drivers(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     d = tmp_path_factory.mktemp("host_drivers")
-    for name in ("host_fft", "host_zogy"):
+    for name in ("host_fft", "host_zogy", "host_coadd"):
         subprocess.check_call([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
                                "-I", CSRC, "-I", INCLUDE, "-I", DRV, "-o", str(d / name),
                                os.path.join(DRV, name + ".cu")])
@@ -89,7 +89,53 @@ def test_zogy_step_matches_the_oracle(drivers, T, spec):
     f = lambda v: float(np.float32(v))
     o = proper.zogy(N, R, pn.astype(np.float64), pr.astype(np.float64), f(Fn), f(Fr), f(sn), f(sr))
     e = F32 * math.log2(T * T) * (np.linalg.norm(N) / sn + (np.linalg.norm(R) / sr if sr > 0 else 0.0)) / T
+    sS = e * o["F_D"] * np.abs(o["P_D"]).sum()
+    print(f"\n[zogy T={T}] |dD| = {np.abs(D - o['D']).max() / e:.2f} e  |dS| = {np.abs(S - o['S']).max() / sS:.2f} e_S")
     assert np.abs(D - o["D"]).max() <= 8 * e
-    assert np.abs(S - o["S"]).max() <= 8 * e * o["F_D"] * np.abs(o["P_D"]).sum()
+    assert np.abs(S - o["S"]).max() <= 8 * sS
     assert np.abs(P - o["P_D"]).max() <= 64 * F32 * np.abs(o["P_D"]).max()
     assert abs(sig / o["sigma_S"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("T,J,eps_psf", [(256, 3, False), (256, 4, True), (512, 2, False)])
+def test_proper_coadd_step_matches_the_oracle(drivers, T, J, eps_psf):
+    """R within 8 e_R, e_R = u log2(T^2) sum_j ||M_j||_2 / s_j / T (the quotient's gain is at
+    most 1/s_j per frame); S within 8 e_S, e_S = u log2(T^2) (sum_j F_j/s_j^2 ||P_j||_1 ||M_j||_2
+    + ||R||_2) / T (the last term: S and R share one inverse transform);
+    P_R within 64 ulps of its maximum; F_R and sigma_S within 1e-6.  An odd frame count
+    exercises the unpaired last frame; eps_psf adds wide PSFs so the frequency floor acts."""
+    from oracle import proper
+    rng = np.random.default_rng(T + J)
+    sky = np.zeros((T, T))
+    n = T * T // 150
+    np.add.at(sky, (rng.integers(0, T, n), rng.integers(0, T, n)), 1e2 * 1e4 ** rng.random(n))
+    conv = lambda img, P: np.fft.ifft2(np.fft.fft2(img) * np.fft.fft2(proper.psf_on_tile(P, img.shape))).real
+    sig_psf = [1.2, 1.9, 1.5, 2.4][:J] if not eps_psf else [3.4, 3.8, 1.3, 3.1][:J]
+    Ps = [_gauss(g) for g in sig_psf]
+    F = np.array([1.0, 0.8, 1.2, 0.95][:J], np.float32)
+    sg = np.array([5.0, 9.0, 4.0, 6.0][:J], np.float32)
+    Ms = [(f * conv(sky, P) + rng.normal(0, s, (T, T))).astype(np.float32) for P, f, s in zip(Ps, F, sg)]
+    d = drivers / f"coadd_{T}_{J}_{int(eps_psf)}"
+    d.mkdir(exist_ok=True)
+    np.array([J, 31], np.int32).tofile(d / "hdr.bin")
+    np.stack(Ms).tofile(d / "M.bin")
+    np.stack(Ps).tofile(d / "P.bin")
+    F.tofile(d / "F.bin")
+    sg.tofile(d / "sig.bin")
+    subprocess.check_call([str(drivers / "host_coadd"), str(T), str(d)])
+    S = np.fromfile(d / "S.bin", np.float32).reshape(T, T)
+    R = np.fromfile(d / "R.bin", np.float32).reshape(T, T)
+    PR = np.fromfile(d / "PR.bin", np.float32).reshape(T, T)
+    FR, sigS = np.fromfile(d / "norms.bin", np.float64)
+    o = proper.proper_coadd(Ms, [P.astype(np.float64) for P in Ps], [float(f) for f in F], [float(s) for s in sg])
+    lg = F32 * math.log2(T * T) / T
+    eR = lg * sum(np.linalg.norm(M) / s for M, s in zip(Ms, sg))
+    # S shares the inverse transform with R, whose rounding (about ||R||_2 / T) it also carries
+    eS = lg * (sum(f / s ** 2 * np.abs(P).sum() * np.linalg.norm(M) for M, P, f, s in zip(Ms, Ps, F, sg))
+               + np.linalg.norm(o["R"]))
+    print(f"\n[coadd T={T} J={J}] |dR| = {np.abs(R - o['R']).max() / eR:.2f} e_R  |dS| = "
+          f"{np.abs(S - o['S']).max() / eS:.2f} e_S")
+    assert np.abs(R - o["R"]).max() <= 8 * eR
+    assert np.abs(S - o["S"]).max() <= 8 * eS
+    assert np.abs(PR - o["P_R"]).max() <= 64 * F32 * np.abs(o["P_R"]).max()
+    assert abs(FR / o["F_R"] - 1) < 1e-6 and abs(sigS / o["sigma_S"] - 1) < 1e-6
