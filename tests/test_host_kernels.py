@@ -1,8 +1,9 @@
 """The kernels' own arithmetic on the CPU: the FFT butterflies and Stockham
-passes (csrc/fft.cuh) and the per-frequency steps of ZOGY and the proper coadd (csrc/proper.cu) are
-host-callable; small drivers (tests/host_drivers) compiled by nvcc as host
-code run them thread by thread with the kernels' load/store mapping, against
-numpy's FFT and the FP64 ZOGY oracle (Sec. 4.2).  Needs nvcc, no GPU."""
+passes (csrc/fft.cuh) and the per-frequency steps of ZOGY and the proper
+coadd (csrc/proper.cu) are host-callable; small drivers (tests/host_drivers)
+compiled by nvcc as host code run them thread by thread with the kernels'
+load/store mapping, against numpy's FFT and the FP64 proper-image oracle
+(ZOGY, Sec. 4.2; proper coadd, Sec. 4.1.3).  Needs nvcc, no GPU."""
 import math
 import os
 import shutil
