@@ -16,6 +16,8 @@
 //      four pixels per thread.
 #include "argus_internal.cuh"
 
+#include <cstring>
+
 namespace {
 
 constexpr int BM_THREADS = 256;
@@ -34,22 +36,117 @@ struct BgArgs {
     float min_frac;
 };
 
-__device__ __forceinline__ unsigned key32(float v) {
-    const unsigned u = __float_as_uint(v);
+// Bit patterns on host and device (the host side serves the CPU checks).
+__host__ __device__ __forceinline__ unsigned f32_bits(float v) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(v);
+#else
+    unsigned u;
+    memcpy(&u, &v, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float bits_f32(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float v;
+    memcpy(&v, &u, 4);
+    return v;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long f64_bits(double v) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double bits_f64(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double v;
+    memcpy(&v, &u, 8);
+    return v;
+#endif
+}
+
+// Order-preserving keys: a < b (as numbers, -0 before +0) iff key(a) < key(b).
+__host__ __device__ __forceinline__ unsigned key32(float v) {
+    const unsigned u = f32_bits(v);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
-
-__device__ __forceinline__ float unkey32(unsigned k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+__host__ __device__ __forceinline__ float unkey32(unsigned k) {
+    return bits_f32((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
-
-__device__ __forceinline__ unsigned long long key64(double v) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+__host__ __device__ __forceinline__ unsigned long long key64(double v) {
+    const unsigned long long u = f64_bits(v);
     return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
+__host__ __device__ __forceinline__ double unkey64(unsigned long long k) {
+    return bits_f64((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k);
+}
 
-__device__ __forceinline__ double unkey64(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+// One thread's share of a box: pixels tid, tid + 256, ... of the box as keys
+// (ok = valid); returns the count of valid pixels.
+__host__ __device__ __forceinline__ int box_load(const BgArgs& a, int bx, int by, int tid, unsigned* key, bool* ok) {
+    const int x0 = bx * a.box, y0 = by * a.box;
+    const int bw = min(a.box, a.w - x0), bh = min(a.box, a.h - y0);
+    const int npx = bw * bh;
+    int nv = 0;
+#pragma unroll
+    for (int j = 0; j < BM_MAX_PER; j++) {
+        const int i = tid + j * BM_THREADS;
+        ok[j] = false;
+        key[j] = 0;
+        if (i < npx) {
+            const int yy = i / bw, xx = i - yy * bw;
+            const long p = (long)(y0 + yy) * a.pitch + x0 + xx;
+            const float v = a.img[p];
+            if (isfinite(v) && (!a.flags || a.flags[p] == 0)) {
+                ok[j] = true;
+                key[j] = key32(v);
+                nv++;
+            }
+        }
+    }
+    return nv;
+}
+
+// One thread's histogram contribution of a radix pass: add(bin) for each of its
+// keys that matches the prefix decided so far.
+template <typename Add>
+__host__ __device__ __forceinline__ void box_hist(const unsigned* key, const bool* ok, unsigned mask, unsigned prefix,
+                                                  int shift, Add add) {
+#pragma unroll
+    for (int j = 0; j < BM_MAX_PER; j++)
+        if (ok[j] && (key[j] & mask) == prefix) add((int)((key[j] >> shift) & 255u));
+}
+
+// One thread's count of keys <= k1 and its smallest key above k1.
+__host__ __device__ __forceinline__ void box_le_min(const unsigned* key, const bool* ok, unsigned k1, int& le,
+                                                    unsigned& m) {
+    le = 0;
+    m = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < BM_MAX_PER; j++) {
+        if (!ok[j]) continue;
+        if (key[j] <= k1) le++;
+        else m = min(m, key[j]);
+    }
+}
+
+// The median from the middle keys: n odd -> k1 == k2.
+__host__ __device__ __forceinline__ double median_of_keys(unsigned k1, unsigned k2) {
+    return 0.5 * ((double)unkey32(k1) + (double)unkey32(k2));
+}
+
+// Whether a box with n valid pixels of npx has a value.
+__host__ __device__ __forceinline__ bool box_has_value(int n, int npx, float min_frac) {
+    return n > 0 && (float)n >= min_frac * (float)npx;
 }
 
 // Block-wide sum of an int (every thread receives it); `red` holds 32 ints.
@@ -106,40 +203,19 @@ __global__ void __launch_bounds__(BM_THREADS) box_median_kernel(BgArgs a) {
     __shared__ int sh[2];
     __shared__ unsigned umin[32];
     const int bx = blockIdx.x, by = blockIdx.y;
-    const int x0 = bx * a.box, y0 = by * a.box;
-    const int bw = min(a.box, a.w - x0), bh = min(a.box, a.h - y0);
-    const int npx = bw * bh;
+    const int npx = min(a.box, a.w - bx * a.box) * min(a.box, a.h - by * a.box);
     unsigned key[BM_MAX_PER];
     bool ok[BM_MAX_PER];
-    int nv = 0;
-#pragma unroll
-    for (int j = 0; j < BM_MAX_PER; j++) {
-        const int i = threadIdx.x + j * BM_THREADS;
-        ok[j] = false;
-        key[j] = 0;
-        if (i < npx) {
-            const int yy = i / bw, xx = i - yy * bw;
-            const long p = (long)(y0 + yy) * a.pitch + x0 + xx;
-            const float v = a.img[p];
-            if (isfinite(v) && (!a.flags || a.flags[p] == 0)) {
-                ok[j] = true;
-                key[j] = key32(v);
-                nv++;
-            }
-        }
-    }
-    const int n = block_sum(nv, red);
+    const int n = block_sum(box_load(a, bx, by, threadIdx.x, key, ok), red);
     double out = __longlong_as_double(0x7ff8000000000000ll);     // NaN: no value
-    if (n > 0 && (float)n >= a.min_frac * (float)npx) {
+    if (box_has_value(n, npx, a.min_frac)) {
         // k-th smallest key for k1 = (n - 1) / 2
         int k = (n - 1) / 2;
         unsigned prefix = 0, mask = 0;
         for (int shift = 24; shift >= 0; shift -= 8) {
             for (int i = threadIdx.x; i < 256; i += BM_THREADS) hist[i] = 0;
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < BM_MAX_PER; j++)
-                if (ok[j] && (key[j] & mask) == prefix) atomicAdd(&hist[(key[j] >> shift) & 255u], 1);
+            box_hist(key, ok, mask, prefix, shift, [&](int b) { atomicAdd(&hist[b], 1); });
             __syncthreads();
             const int b = pick_bin(hist, k, sh);
             prefix |= (unsigned)b << shift;
@@ -149,14 +225,9 @@ __global__ void __launch_bounds__(BM_THREADS) box_median_kernel(BgArgs a) {
         unsigned k2 = k1;
         if ((n & 1) == 0) {
             // the next order statistic: k1 again if it repeats, else the smallest key above it
-            int le = 0;
-            unsigned m = 0xffffffffu;
-#pragma unroll
-            for (int j = 0; j < BM_MAX_PER; j++) {
-                if (!ok[j]) continue;
-                if (key[j] <= k1) le++;
-                else m = min(m, key[j]);
-            }
+            int le;
+            unsigned m;
+            box_le_min(key, ok, k1, le, m);
             const int nle = block_sum(le, red);
             m = __reduce_min_sync(0xffffffffu, m);
             if ((threadIdx.x & 31) == 0) umin[threadIdx.x >> 5] = m;
@@ -165,7 +236,7 @@ __global__ void __launch_bounds__(BM_THREADS) box_median_kernel(BgArgs a) {
             for (int i = 0; i < BM_THREADS / 32; i++) mm = min(mm, umin[i]);
             k2 = nle >= n / 2 + 1 ? k1 : mm;
         }
-        out = 0.5 * ((double)unkey32(k1) + (double)unkey32(k2));
+        out = median_of_keys(k1, k2);
     }
     if (threadIdx.x == 0) a.raw[(long)by * a.nx + bx] = out;
 }
@@ -227,16 +298,16 @@ __global__ void __launch_bounds__(FILL_THREADS) mesh_fill_kernel(BgArgs a) {
     if (threadIdx.x == 0) *a.fill = 0.5 * (unkey64(k1) + unkey64(k2));
 }
 
-__global__ void __launch_bounds__(256) mesh_filter_kernel(BgArgs a) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.nx * a.ny) return;
-    const int cy = c / a.nx, cx = c - cy * a.nx;
-    const int r = a.filt / 2;
+// The filtered value of box (cx, cy): the median of the values that exist in its
+// filt x filt neighbourhood, else `fill`.
+__host__ __device__ __forceinline__ double filter_cell(const double* raw, int nx, int ny, int cx, int cy, int filt,
+                                                       double fill) {
+    const int r = filt / 2;
     double v[49];
     int n = 0;
-    for (int y = max(0, cy - r); y <= min(a.ny - 1, cy + r); y++) {
-        for (int x = max(0, cx - r); x <= min(a.nx - 1, cx + r); x++) {
-            const double t = a.raw[(long)y * a.nx + x];
+    for (int y = max(0, cy - r); y <= min(ny - 1, cy + r); y++) {
+        for (int x = max(0, cx - r); x <= min(nx - 1, cx + r); x++) {
+            const double t = raw[(long)y * nx + x];
             if (isnan(t)) continue;
             int i = n++;                           // insertion into the sorted prefix
             while (i > 0 && v[i - 1] > t) {
@@ -246,12 +317,19 @@ __global__ void __launch_bounds__(256) mesh_filter_kernel(BgArgs a) {
             v[i] = t;
         }
     }
-    a.mesh[c] = n ? 0.5 * (v[(n - 1) / 2] + v[n / 2]) : *a.fill;
+    return n ? 0.5 * (v[(n - 1) / 2] + v[n / 2]) : fill;
+}
+
+__global__ void __launch_bounds__(256) mesh_filter_kernel(BgArgs a) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.nx * a.ny) return;
+    const int cy = c / a.nx, cx = c - cy * a.nx;
+    a.mesh[c] = filter_cell(a.raw, a.nx, a.ny, cx, cy, a.filt, *a.fill);
 }
 
 // Interpolation coordinate along one axis: lower box index i (upper i + 1) and
 // weight t of the upper one, clamped beyond the outermost centres.
-__device__ __forceinline__ void axis_weight(int p, int n, int box, int nb, int& i, float& t) {
+__host__ __device__ __forceinline__ void axis_weight(int p, int n, int box, int nb, int& i, float& t) {
     if (nb == 1) {
         i = 0;
         t = 0.0f;
@@ -266,6 +344,16 @@ __device__ __forceinline__ void axis_weight(int p, int n, int box, int nb, int& 
     const int e1 = min((i + 2) * box, n);
     const float c1 = 0.5f * (float)((i + 1) * box + e1 - 1);
     t = fminf(fmaxf(((float)p - c0) / (c1 - c0), 0.0f), 1.0f);
+}
+
+// Bilinear value from the mesh row r0 (lower box ix, next box ix + jx, next row
+// + jy) in FP32.
+__host__ __device__ __forceinline__ float bilinear(const double* r0, int ix, int jx, int jy, float tx, float ty) {
+    const float m00 = (float)r0[ix], m01 = (float)r0[ix + jx];
+    const float m10 = (float)r0[jy + ix], m11 = (float)r0[jy + ix + jx];
+    const float top = m00 + (m01 - m00) * tx;
+    const float bot = m10 + (m11 - m10) * tx;
+    return top + (bot - top) * ty;
 }
 
 __global__ void __launch_bounds__(256) interp_kernel(BgArgs a) {
@@ -284,13 +372,7 @@ __global__ void __launch_bounds__(256) interp_kernel(BgArgs a) {
         const double* r0 = a.mesh + (long)iy * a.nx;
         float o[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float m00 = (float)r0[ix[k]], m01 = (float)r0[ix[k] + jx];
-            const float m10 = (float)r0[jy + ix[k]], m11 = (float)r0[jy + ix[k] + jx];
-            const float top = m00 + (m01 - m00) * tx[k];
-            const float bot = m10 + (m11 - m10) * tx[k];
-            o[k] = x0 + k < a.w ? top + (bot - top) * ty : 0.0f;
-        }
+        for (int k = 0; k < 4; k++) o[k] = x0 + k < a.w ? bilinear(r0, ix[k], jx, jy, tx[k], ty) : 0.0f;
         *reinterpret_cast<float4*>(a.map + (long)y * a.pitch + x0) = make_float4(o[0], o[1], o[2], o[3]);
     }
 }

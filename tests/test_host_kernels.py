@@ -3,7 +3,9 @@ passes (csrc/fft.cuh) and the per-frequency steps of ZOGY and the proper
 coadd (csrc/proper.cu) are host-callable; small drivers (tests/host_drivers)
 compiled by nvcc as host code run them thread by thread with the kernels'
 load/store mapping, against numpy's FFT and the FP64 proper-image oracle
-(ZOGY, Sec. 4.2; proper coadd, Sec. 4.1.3).  Needs nvcc, no GPU."""
+(ZOGY, Sec. 4.2; proper coadd, Sec. 4.1.3); the background-map kernels'
+per-thread code (box medians by radix select, mesh filter, bilinear map;
+Table 2) likewise against its oracle.  Needs nvcc, no GPU."""
 import math
 import os
 import shutil
@@ -26,7 +28,7 @@ def drivers(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     d = tmp_path_factory.mktemp("host_drivers")
-    for name in ("host_fft", "host_zogy", "host_coadd"):
+    for name in ("host_fft", "host_zogy", "host_coadd", "host_background"):
         subprocess.check_call([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
                                "-I", CSRC, "-I", INCLUDE, "-I", DRV, "-o", str(d / name),
                                os.path.join(DRV, name + ".cu")])
@@ -140,3 +142,45 @@ def test_proper_coadd_step_matches_the_oracle(drivers, T, J, eps_psf):
     assert np.abs(S - o["S"]).max() <= 8 * eS
     assert np.abs(PR - o["P_R"]).max() <= 64 * F32 * np.abs(o["P_R"]).max()
     assert abs(FR / o["F_R"] - 1) < 1e-6 and abs(sigS / o["sigma_S"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("w,h,box,filt,frac,use_flags", [
+    (640, 384, 64, 3, 0.5, True), (1000, 37, 64, 3, 0.5, True), (517, 300, 32, 5, 0.5, True),
+    (130, 129, 9, 1, 0.5, True), (64, 64, 64, 3, 0.5, False), (8, 8, 8, 7, 0.5, True), (400, 300, 32, 3, 0.99, False),
+    (400, 300, 32, 3, 0.5, "left")])
+def test_background_steps_match_the_oracle(drivers, w, h, box, filt, frac, use_flags):
+    """Box medians and the filtered mesh bit-exact, the FP32 map within 8 ulps of the
+    largest mesh value ("left": the left 150 columns flagged, so boxes without a value
+    take the filter's neighbours or the fill)."""
+    from oracle import background as bgo
+    rng = np.random.default_rng(w + h + box)
+    y, x = np.mgrid[0:h, 0:w]
+    img = (300 + 0.01 * x - 0.02 * y + rng.normal(0, 15, (h, w))).astype(np.float32)
+    for _ in range(w * h // 500):
+        cy, cx = rng.integers(0, h), rng.integers(0, w)
+        img[max(0, cy - 2):cy + 3, max(0, cx - 2):cx + 3] += rng.uniform(100, 3e4)
+    img.flat[3::997] = np.nan
+    img.flat[5::1999] = np.inf
+    img.flat[7::1499] = -0.0
+    fl = (rng.random((h, w)) < 0.02).astype(np.uint8)
+    if use_flags == "left":
+        fl[:] = 0
+        fl[:, :150] = 1
+    elif not use_flags:
+        fl[:] = 0
+    d = drivers / f"bg_{w}_{h}_{box}_{filt}_{frac}_{use_flags}"
+    d.mkdir(exist_ok=True)
+    np.array([w, h, box, filt, 1 if use_flags else 0], np.int32).tofile(d / "hdr.bin")
+    np.array([frac], np.float32).tofile(d / "frac.bin")
+    img.tofile(d / "img.bin")
+    fl.tofile(d / "flags.bin")
+    subprocess.check_call([str(drivers / "host_background"), str(d)])
+    ny, nx = -(-h // box), -(-w // box)
+    raw = np.fromfile(d / "raw.bin").reshape(ny, nx)
+    mesh = np.fromfile(d / "mesh.bin").reshape(ny, nx)
+    m = np.fromfile(d / "map.bin", np.float32).reshape(h, w)
+    f = fl if use_flags else None
+    np.testing.assert_array_equal(raw, bgo.box_medians(img, f, box, frac))
+    omesh, omap = bgo.background_map(img, f, box=box, filt=filt, min_frac=frac)
+    np.testing.assert_array_equal(mesh, omesh)
+    assert np.abs(m - omap).max() <= 8 * F32 * np.abs(omesh).max()
