@@ -507,6 +507,35 @@ int argus_proper_coadd(argus_proper_plan *plan, const float *stack, int n_frames
                        int psf_size, float eps, float *S, float *R, float *P_R, double *F_R, double *sigma_S,
                        argus_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * HEALPix segmentation (paper Sec. 3.3 "Image Segmentation": frames are
+ * reprojected into HEALPix NSIDE=256 segments; Table 2, GPU stage "Image
+ * segmentation and resampling to HEALPix grid").  A segment is one nested
+ * HEALPix pixel at nside_seg; its image is the 2^k x 2^k grid of the pixels at
+ * NSIDE nside_seg 2^k inside it: image column c, row r is face pixel
+ * (X 2^k + c, Y 2^k + r), (X, Y) the segment's face coordinates (ix from the
+ * even bits of the in-face nested index, iy from the odd bits).  Each image
+ * pixel takes the frame value at its pixel centre through the gnomonic WCS
+ * below, by bilinear interpolation written as nested lerps; it is covered
+ * when the position lies in [0, w-1] x [0, h-1] and every neighbour with a
+ * nonzero weight is unflagged and finite, else 0 with coverage 0.  Geometry
+ * in FP64, output FP32. */
+typedef struct {
+    double alpha0, delta0;   /* tangent point (radians) */
+    double scale;            /* radians per pixel */
+    double rot;              /* x = cx + (cos rot xi + sin rot eta) / scale,
+                                y = cy + (-sin rot xi + cos rot eta) / scale,
+                                xi east, eta north in the tangent plane */
+    double cx, cy;           /* pixel coordinates of the tangent point */
+} argus_wcs;
+
+/* frame, flags (nullable): device [h][pitch]; segs: device int64 [n_seg] nested
+ * indices at nside_seg (a power of two <= 2^17, nside_seg 2^k <= 2^29, k <= 12);
+ * out: device float [n_seg][2^k][2^k]; coverage (nullable): device uint8, same. */
+int argus_healpix_resample(const float *frame, const uint8_t *flags, argus_shape shape, argus_wcs wcs,
+                           int nside_seg, int k, const long long *segs, int n_seg, float *out,
+                           uint8_t *coverage, argus_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

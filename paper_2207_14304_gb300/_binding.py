@@ -89,6 +89,11 @@ I = C.c_int
 F = C.c_float
 SH = argus_shape
 
+
+class argus_wcs(C.Structure):
+    _fields_ = [("alpha0", C.c_double), ("delta0", C.c_double), ("scale", C.c_double), ("rot", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double)]
+
 # entry point -> argument types
 SIGNATURES = {
     "argus_status_string": ([I], C.c_char_p),
@@ -129,6 +134,7 @@ SIGNATURES = {
     "argus_proper_plan_destroy": ([P], I),
     "argus_zogy": ([P, P, P, SH, P, I, P, P, I, F, P, P, P, P, P], I),
     "argus_proper_coadd": ([P, P, I, SH, P, I, P, P, P, I, F, P, P, P, P, P, P], I),
+    "argus_healpix_resample": ([P, P, SH, argus_wcs, I, I, P, I, P, P, P], I),
 }
 
 
@@ -450,6 +456,15 @@ def argus_proper_coadd(plan, stack, n_frames, shape, origins, n_tiles, F, sigma,
     _check(load().argus_proper_coadd(plan, _ptr(stack), int(n_frames), shape, _ptr(origins), int(n_tiles), _ptr(F),
                                      _ptr(sigma), _ptr(psfs), int(psf_size), float(eps), _ptr(S), _ptr(R),
                                      _ptr(P_R), _ptr(F_R), _ptr(sigma_S), _stream(stream)), "argus_proper_coadd")
+
+
+def argus_healpix_resample(frame, flags, shape, wcs, nside_seg, k, segs, n_seg, out, coverage=None, stream=None):
+    """wcs: argus_wcs or a tuple (alpha0, delta0, scale, rot, cx, cy)."""
+    if not isinstance(wcs, argus_wcs):
+        wcs = argus_wcs(*[float(v) for v in wcs])
+    _check(load().argus_healpix_resample(_ptr(frame), _ptr(flags), shape, wcs, int(nside_seg), int(k), _ptr(segs),
+                                         int(n_seg), _ptr(out), _ptr(coverage), _stream(stream)),
+           "argus_healpix_resample")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):

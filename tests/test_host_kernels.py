@@ -5,7 +5,8 @@ compiled by nvcc as host code run them thread by thread with the kernels'
 load/store mapping, against numpy's FFT and the FP64 proper-image oracle
 (ZOGY, Sec. 4.2; proper coadd, Sec. 4.1.3); the background-map kernels'
 per-thread code (box medians by radix select, mesh filter, bilinear map;
-Table 2) likewise against its oracle.  Needs nvcc, no GPU."""
+Table 2) and the HEALPix resampler's per-pixel code (Sec. 3.3) likewise
+against their oracles.  Needs nvcc, no GPU."""
 import math
 import os
 import shutil
@@ -28,7 +29,7 @@ def drivers(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     d = tmp_path_factory.mktemp("host_drivers")
-    for name in ("host_fft", "host_zogy", "host_coadd", "host_background"):
+    for name in ("host_fft", "host_zogy", "host_coadd", "host_background", "host_healpix"):
         subprocess.check_call([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
                                "-I", CSRC, "-I", INCLUDE, "-I", DRV, "-o", str(d / name),
                                os.path.join(DRV, name + ".cu")])
@@ -184,3 +185,49 @@ def test_background_steps_match_the_oracle(drivers, w, h, box, filt, frac, use_f
     omesh, omap = bgo.background_map(img, f, box=box, filt=filt, min_frac=frac)
     np.testing.assert_array_equal(mesh, omesh)
     assert np.abs(m - omap).max() <= 8 * F32 * np.abs(omesh).max()
+
+
+def _segments_in_view(wcs, w, h, nside_seg, n, rng):
+    """n random segments whose centres fall inside the frame (found from the oracle's
+    own pixel centres at nside_seg)."""
+    from oracle import healpix as hp
+    p = np.arange(12 * nside_seg * nside_seg)
+    x, y = hp.gnomonic(hp.xyf2vec(*hp.nest2xyf(p, nside_seg)[:2], hp.nest2xyf(p, nside_seg)[2], nside_seg), *wcs)
+    ok = np.isfinite(x)
+    inside = p[ok & (x > 0) & (y > 0) & (x < w - 1) & (y < h - 1)]
+    edge = p[ok & (x > -3) & (x < 0) & (y > 0) & (y < h - 1)]          # centre just off the left edge
+    return np.concatenate([rng.choice(inside, size=min(n, inside.size), replace=False), edge[:1]])
+
+
+@pytest.mark.parametrize("nside_seg,k,delta0,use_flags", [(64, 4, 0.4, True), (32, 5, 1.45, False),
+                                                          (128, 3, -0.7, True)])
+def test_healpix_resampling_matches_the_oracle(drivers, nside_seg, k, delta0, use_flags):
+    """Coverage bit-exact and values within 4 ulps of the largest frame value, for segments
+    around and across the frame edge (a polar-cap field at delta0 = 1.45 included)."""
+    from oracle import healpix as hp
+    rng = np.random.default_rng(nside_seg + k)
+    w, h = 700, 500
+    scale = 2.0 * math.sqrt(4 * math.pi / (12.0 * (nside_seg << k) ** 2))        # ~2 segment pixels per frame pixel
+    wcs = (0.9, delta0, scale, 0.25, (w - 1) / 2 + 0.3, (h - 1) / 2 - 0.2)
+    yy, xx = np.mgrid[0:h, 0:w]
+    frame = (300 + 0.05 * xx + rng.normal(0, 10, (h, w))).astype(np.float32)
+    frame.flat[11::701] = np.nan
+    fl = (rng.random((h, w)) < 0.01).astype(np.uint8) if use_flags else np.zeros((h, w), np.uint8)
+    segs = _segments_in_view(wcs, w, h, nside_seg, 6, rng).astype(np.int64)
+    d = drivers / f"hp_{nside_seg}_{k}_{delta0}"
+    d.mkdir(exist_ok=True)
+    np.array([w, h, nside_seg, k, segs.size, 1 if use_flags else 0], np.int32).tofile(d / "hdr.bin")
+    np.array(wcs, np.float64).tofile(d / "wcs.bin")
+    segs.tofile(d / "segs.bin")
+    frame.tofile(d / "frame.bin")
+    fl.tofile(d / "flags.bin")
+    subprocess.check_call([str(drivers / "host_healpix"), str(d)])
+    m = 1 << k
+    out = np.fromfile(d / "out.bin", np.float32).reshape(-1, m, m)
+    cov = np.fromfile(d / "cov.bin", np.uint8).reshape(-1, m, m)
+    tol = 4 * F32 * float(np.nanmax(np.abs(frame)))
+    for i, s in enumerate(segs):
+        o, oc = hp.resample_segment(frame, fl if use_flags else None, int(s), nside_seg, k, wcs)
+        np.testing.assert_array_equal(cov[i], oc)
+        assert np.abs(out[i] - o).max() <= tol
+    assert cov[:-1].any() and cov[-1].any() and not cov[-1].all()     # the edge segment is partly covered

@@ -76,3 +76,12 @@ def test_proper_coadd_argument_checks_need_no_gpu():
     sh = B.argus_shape(64, 8, 64)
     assert lib.argus_proper_coadd(None, None, 2, sh, None, 1, None, None, None, 31, 1e-8, None, None, None, None,
                                   None, None) == B.ARGUS_ERR_ARG
+
+
+def test_healpix_argument_checks_need_no_gpu():
+    from paper_2207_14304_gb300 import _binding as B
+    lib = B.load()
+    sh = B.argus_shape(64, 8, 64)
+    wcs = B.argus_wcs(0.0, 0.0, 1e-5, 0.0, 32.0, 4.0)
+    assert lib.argus_healpix_resample(None, None, sh, wcs, 256, 9, None, 1, None, None, None) == B.ARGUS_ERR_ARG
+    assert C.sizeof(B.argus_wcs) == 48
