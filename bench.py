@@ -663,7 +663,7 @@ def bench_learned(device, stream, train_pairs, epochs, log=None):
         lst = B.fit_stats_from_bytes(lf.stats)
         ratio = (lst["chi2"] / max(lst["dof"], 1)) / (plain["chi2"] / max(plain["dof"], 1))
         lf.plain_chi2_dof = plain["chi2"] / max(plain["dof"], 1)
-        lf.ratio = float("inf")     # learned path as measured: the judge keeps the learned kernel
+        lf.ratio = float("inf")     # learned path as measured: the chi2 check keeps the learned kernel
         frame_ms = timed_ms(lambda: lf.run(d_raw, calib, d_R, d_Vr, stream), 3, stream, device)
         n_learned_src = int(pipe.n_found[0].item())
         lf.ratio = 1.1

@@ -810,9 +810,10 @@ void ora_coadd(int nf, int w, int h, const uint16_t *raw, const float *shifts, i
 }
 
 /* ------------------------------------------------------------------------ */
-/* Learned kernel surrogate (the north-star's learned-part reading; no       */
-/* counterpart in the paper).  A CNN maps a stamp pair (science, reference,   */
-/* each 21x21 and divided by the reference stamp sum) to a 21x21 kernel:      */
+/* Learned kernel surrogate (a learned stand-in for the least-squares fit;  */
+/* no counterpart in the paper).  A CNN maps a stamp pair (science and      */
+/* reference, each 21x21 and divided by the reference stamp sum) to a 21x21 */
+/* kernel:                                                                    */
 /*   h1 = W1 x + b1                       (1x1 conv, 2 -> 32, linear)         */
 /*   h_{l+1} = relu(conv7(h_l; W_l) + b_l), l = 2..5  (7x7, 32 -> 32, 'same' */
 /*                                           zero padding)                    */

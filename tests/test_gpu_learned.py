@@ -218,7 +218,7 @@ def test_fit_scale_background_recovers_scales(ora):
 def test_learned_fit_falls_back_to_least_squares():
     """An untrained network's kernel is far worse than the least-squares fit, so the
     per-frame learned fit must judge it by chi2 and use the plain fit instead; with
-    the judge disabled (ratio = inf) the learned kernel is used and subtraction runs."""
+    the chi2 check disabled (ratio = inf) the learned kernel is used and subtraction runs."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2207_14304_gb300.learned import LearnedFit
