@@ -381,7 +381,11 @@ def run_gpu(args):
         for name, fn in (("coadd", lambda: bench_coadd(device, stream, args.steps, hbm)),
                          ("segments", lambda: bench_segments(device, stream, args.segment_cameras)),
                          ("learned", lambda: bench_learned(device, stream, args.train_pairs, args.train_epochs)),
-                         ("sparse", lambda: bench_sparse(device, stream, hbm))):
+                         ("sparse", lambda: bench_sparse(device, stream, hbm)),
+                         ("background", lambda: bench_background(device, stream, hbm)),
+                         ("healpix", lambda: bench_healpix(device, stream, hbm)),
+                         ("zogy", lambda: bench_zogy(device, stream, hbm)),
+                         ("proper_coadd", lambda: bench_proper_coadd(device, stream, hbm))):
             if name not in wanted:
                 continue
             try:
@@ -618,6 +622,151 @@ def bench_sparse(device, stream, hbm):
             "status": st}
 
 
+def _star_frame(device, seed, sigma=1.5, sky=300.0, noise=18.0):
+    """A rendered 9576x6388 star field with Gaussian noise, pitched, and sparse flags."""
+    import torch
+    from paper_2207_14304_gb300 import synth
+    pitch = synth.pitch_for(W)
+    cat = synth.star_catalog(N_STARS, W, H, seed=seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    img = torch.zeros((H, pitch), device=device)
+    img[:, :W] = synth.render(cat, W, H, sigma, sky=sky, device=device, dtype=torch.float32)
+    img[:, :W] += torch.randn((H, W), generator=g, device=device) * noise
+    flags = torch.zeros((H, pitch), dtype=torch.uint8, device=device)
+    flags[:, :W] = (torch.rand((H, W), generator=g, device=device) < 1e-4).to(torch.uint8)
+    return img, flags, pitch
+
+
+def bench_background(device, stream, hbm):
+    """Median-filtered background map of one 9576x6388 frame: 64-px boxes, 3x3 mesh filter.
+    Opt-in (--extras background)."""
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    img, flags, pitch = _star_frame(device, 31)
+    box = 64
+    mesh = torch.zeros((-(-H // box), -(-W // box)), dtype=torch.float64, device=device)
+    bmap = torch.empty((H, pitch), device=device)
+    ctx = B.argus_create(device.index, H * pitch, 16, 64, 1 << 10)
+    try:
+        ms = call_ms(lambda: B.argus_background(ctx, img, flags, B.argus_shape(W, H, pitch), box, 3, 0.5, mesh, bmap,
+                                                stream), 20, stream, device)
+        st = B.argus_sync_status(ctx, stream)
+    finally:
+        B.argus_destroy(ctx)
+    nbytes = (4 + 1 + 4) * H * pitch                     # image and flags read, map written
+    return {"workload": f"{W}x{H} frame, {box}-px boxes, 3x3 mesh median filter, bilinear map",
+            "ms": round(ms, 4), "value": round(W * H / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s",
+            "hbm_bytes": nbytes, "hbm_frac": round(nbytes / (ms / 1e3) / 1e9 / hbm, 4), "status": st}
+
+
+def bench_healpix(device, stream, hbm):
+    """Every NSIDE=256 segment whose centre falls in a 9576x6388 frame at 1.38 arcsec/px
+    (gnomonic WCS at RA 60 deg, Dec 30 deg), resampled to 512x512 segment images (k = 9).
+    Opt-in (--extras healpix)."""
+    import math
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    img, flags, pitch = _star_frame(device, 32)
+    nside, k = 256, 9
+    shape = B.argus_shape(W, H, pitch)
+    wcs = (math.radians(60.0), math.radians(30.0), math.radians(1.38 / 3600.0), 0.1, (W - 1) / 2, (H - 1) / 2)
+    # the segments whose centre falls in the frame: resample every NSIDE-256 pixel at k = 0
+    every = torch.arange(12 * nside * nside, dtype=torch.int64, device=device)
+    centre = torch.empty(every.numel(), device=device)
+    ccov = torch.empty(every.numel(), dtype=torch.uint8, device=device)
+    B.argus_healpix_resample(img, None, shape, wcs, nside, 0, every, every.numel(), centre, ccov, stream)
+    torch.cuda.synchronize(device)
+    d_segs = every[ccov.bool()].contiguous()
+    n_seg = int(d_segs.numel())
+    m = 1 << k
+    out = torch.empty((n_seg, m, m), device=device)
+    cov = torch.empty((n_seg, m, m), dtype=torch.uint8, device=device)
+    ms = call_ms(lambda: B.argus_healpix_resample(img, flags, shape, wcs, nside, k, d_segs, n_seg, out, cov, stream),
+                 10, stream, device)
+    covered = float(cov.float().mean().item())
+    npx = n_seg * m * m
+    nbytes = npx * (4 + 1) + (4 + 1) * W * H              # outputs written, the frame and flags read once
+    return {"workload": f"{n_seg} NSIDE-{nside} segments of {m}x{m} (k = {k}) from a {W}x{H} frame at 1.38 arcsec/px",
+            "ms": round(ms, 4), "value": round(npx / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s (segment pixels)",
+            "covered_frac": round(covered, 4), "hbm_bytes": nbytes,
+            "hbm_frac": round(nbytes / (ms / 1e3) / 1e9 / hbm, 4)}
+
+
+def _gauss_psf(sig, half=15):
+    import numpy as np
+    u = np.arange(-half, half + 1)
+    g = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * sig * sig))
+    return (g / g.sum()).astype(np.float32)
+
+
+def bench_zogy(device, stream, hbm):
+    """ZOGY on 512x512 tiles covering a 9576x6388 frame (18 x 12 tiles), per-tile Gaussian PSFs
+    (new 1.3-2.2 px, reference 1.2 px). Opt-in (--extras zogy)."""
+    import numpy as np
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    N, _, pitch = _star_frame(device, 33, sigma=1.8)
+    R, _, _ = _star_frame(device, 33, sigma=1.2, noise=3.0)
+    T = 512
+    org = [(x, y) for y in range(0, H - T + 1, T) for x in range(0, W - T + 1, T)]
+    nt = len(org)
+    rec = np.zeros(nt, B.ZOGY_TILE_DTYPE)
+    pn = np.zeros((nt, 31, 31), np.float32)
+    pr = np.zeros_like(pn)
+    for i, (x0, y0) in enumerate(org):
+        rec[i] = (x0, y0, 1.0, 1.0, 18.0, 3.0)
+        pn[i] = _gauss_psf(1.3 + 0.9 * i / max(nt - 1, 1))
+        pr[i] = _gauss_psf(1.2)
+    plan = B.proper_plan_create(device.index, T, nt)
+    try:
+        d_rec = torch.from_numpy(rec.view(np.uint8).copy()).to(device)
+        dpn, dpr = torch.from_numpy(pn).to(device), torch.from_numpy(pr).to(device)
+        D = torch.empty((nt, T, T), device=device)
+        S = torch.empty((nt, T, T), device=device)
+        sig = torch.empty(nt, dtype=torch.float64, device=device)
+        ms = call_ms(lambda: B.argus_zogy(plan, N, R, B.argus_shape(W, H, pitch), d_rec, nt, dpn, dpr, 31, 1e-8, D, S,
+                                          None, sig, stream), 5, stream, device)
+    finally:
+        B.proper_plan_destroy(plan)
+    npx = nt * T * T
+    return {"workload": f"{nt} tiles of {T}x{T} from a {W}x{H} frame, per-tile PSFs", "ms": round(ms, 3),
+            "value": round(npx / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s", "ms_per_tile": round(ms / nt, 4)}
+
+
+def bench_proper_coadd(device, stream, hbm):
+    """Proper coadd of 30 frames on 512x512 tiles of a 9576x6388 field (18 x 12 tiles).
+    Opt-in (--extras proper_coadd)."""
+    import numpy as np
+    import torch
+    from paper_2207_14304_gb300 import _binding as B
+    J, T = 30, 512
+    frames = []
+    for j in range(J):
+        f, _, pitch = _star_frame(device, 40 + j, sigma=1.4 + 0.02 * j)
+        frames.append(f)
+    stack = torch.stack(frames)
+    del frames
+    org = [(x, y) for y in range(0, H - T + 1, T) for x in range(0, W - T + 1, T)]
+    nt = len(org)
+    psfs = np.stack([np.stack([_gauss_psf(1.4 + 0.02 * j) for j in range(J)]) for _ in range(nt)])
+    plan = B.proper_plan_create(device.index, T, nt)
+    try:
+        d_org = torch.tensor(org, dtype=torch.int32, device=device)
+        F = torch.ones(J, device=device)
+        sg = torch.full((J,), 18.0, device=device)
+        d_psf = torch.from_numpy(psfs).to(device)
+        S = torch.empty((nt, T, T), device=device)
+        R = torch.empty((nt, T, T), device=device)
+        ms = call_ms(lambda: B.argus_proper_coadd(plan, stack, J, B.argus_shape(W, H, pitch), d_org, nt, F, sg, d_psf,
+                                                  31, 1e-8, S, R, None, None, None, stream), 3, stream, device)
+    finally:
+        B.proper_plan_destroy(plan)
+    npx = nt * T * T
+    return {"workload": f"{J} frames x {nt} tiles of {T}x{T}", "ms": round(ms, 3),
+            "value": round(npx / 1e6 / (ms / 1e3), 1), "unit": "Mpix/s (coadd pixels)"}
+
+
 def bench_learned(device, stream, train_pairs, epochs, log=None):
     """Learned kernel vs least-squares fit on a 1-s frame (sky 10 e-, reference 1 px PSF):
     CNN trained on plain-method fits, judged by chi2/dof against the plain fit."""
@@ -799,7 +948,8 @@ def main(argv=None):
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
     ap.add_argument("--extras", default="coadd,segments,learned,sparse",
-                    help="comma list of the extra workloads to measure after the headline")
+                    help="comma list of the extra workloads to measure after the headline "
+                         "(also: background, healpix, zogy, proper_coadd)")
     ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
     ap.add_argument("--frame", type=int, nargs=2, metavar=("W", "H"), default=None,
                     help="smaller frame for profiling captures (star count scaled by area)")
