@@ -477,9 +477,13 @@ int argus_proper_plan_destroy(argus_proper_plan *plan);
 
 /* N, R: device float [h][pitch] (one shape); tiles: device argus_zogy_tile
  * [n_tiles]; psf_n, psf_r: device float [n_tiles][psf_size][psf_size], odd
- * psf_size <= 63; D, S and P_D (nullable): device float [n_tiles][T][T];
- * sigma_S (nullable): device double [n_tiles].  1 <= n_tiles <= max_tiles.
- * Calls on one plan must not overlap. */
+ * psf_size <= 63, or both NULL to reuse the PSF transforms of the last call on
+ * this plan that gave PSFs (PSFs change per pointing, frames per exposure; the
+ * FP64 transforms are the costliest part of a call) -- then n_tiles may not
+ * exceed that call's, and a proper-coadd call in between discards them;
+ * D, S and P_D (nullable): device float [n_tiles][T][T]; sigma_S (nullable):
+ * device double [n_tiles].  1 <= n_tiles <= max_tiles.  Calls on one plan must
+ * not overlap. */
 int argus_zogy(argus_proper_plan *plan, const float *N, const float *R, argus_shape shape,
                const argus_zogy_tile *tiles, int n_tiles, const float *psf_n, const float *psf_r,
                int psf_size, float eps, float *D, float *S, float *P_D, double *sigma_S,

@@ -445,7 +445,8 @@ def proper_plan_destroy(plan):
 
 def argus_zogy(plan, N, R, shape, tiles, n_tiles, psf_n, psf_r, psf_size, eps, D, S, P_D=None, sigma_S=None,
                stream=None):
-    """tiles: a device uint8 tensor holding n_tiles records of ZOGY_TILE_DTYPE."""
+    """tiles: a device uint8 tensor holding n_tiles records of ZOGY_TILE_DTYPE; psf_n and
+    psf_r both None reuse the PSF transforms of the plan's last call that gave PSFs."""
     _check(load().argus_zogy(plan, _ptr(N), _ptr(R), shape, _ptr(tiles), int(n_tiles), _ptr(psf_n), _ptr(psf_r),
                              int(psf_size), float(eps), _ptr(D), _ptr(S), _ptr(P_D), _ptr(sigma_S),
                              _stream(stream)), "argus_zogy")

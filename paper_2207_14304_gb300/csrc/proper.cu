@@ -34,6 +34,7 @@ struct argus_proper_plan {
     int device;
     int tile;
     int max_tiles;
+    int psf_tiles;    // tiles whose ZOGY PSF transforms z2 holds (0 after a coadd call)
     float2* z1;       // [max_tiles][T][T]
     double2* z2;      // [max_tiles][T][T]
     float2* z3;       // [max_tiles][T][T] (ZOGY: P_D; coadd: the score accumulator, then P_R)
@@ -224,14 +225,17 @@ int run(argus_proper_plan* p, ZArgs& a, cudaStream_t s) {
     const long total = (long)a.n_tiles * T * T;
     const unsigned grid = (unsigned)((total + 255) / 256);
     unsigned g2 = grid > 152u * 16u ? 152u * 16u : grid;
-    if (cudaMemsetAsync(p->z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
     if (cudaMemsetAsync(p->psd, 0, (size_t)a.n_tiles * sizeof(double), s) != cudaSuccess) return ARGUS_ERR_CUDA;
     zogy_pack_kernel<T><<<g2, 256, 0, s>>>(a);
-    const long pp = (long)a.n_tiles * a.ps * a.ps;
-    zogy_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
-    argus_count_launch(2);
+    argus_count_launch(1);
     fft2d<T, -1, float>(p->z1, a.n_tiles, p->tw32, s);
-    fft2d<T, -1, double>(p->z2, a.n_tiles, p->tw64, s);
+    if (a.psf_n) {                 // new PSFs: place and transform them (else z2 holds the last ones)
+        if (cudaMemsetAsync(p->z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+        const long pp = (long)a.n_tiles * a.ps * a.ps;
+        zogy_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
+        argus_count_launch(1);
+        fft2d<T, -1, double>(p->z2, a.n_tiles, p->tw64, s);
+    }
     zogy_combine_kernel<T><<<grid, 256, 0, s>>>(a);
     argus_count_launch(1);
     fft2d<T, 1, float>(p->z1, a.n_tiles, p->tw32, s);
@@ -522,8 +526,9 @@ extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* 
                           const argus_zogy_tile* tiles, int n_tiles, const float* psf_n, const float* psf_r,
                           int psf_size, float eps, float* D, float* S, float* P_D, double* sigma_S,
                           argus_stream stream) {
-    if (!plan || !N || !R || !tiles || !psf_n || !psf_r || !D || !S || n_tiles < 1 || n_tiles > plan->max_tiles)
-        return ARGUS_ERR_ARG;
+    if (!plan || !N || !R || !tiles || !D || !S || n_tiles < 1 || n_tiles > plan->max_tiles) return ARGUS_ERR_ARG;
+    if (!psf_n != !psf_r) return ARGUS_ERR_ARG;
+    if (!psf_n && n_tiles > plan->psf_tiles) return ARGUS_ERR_ARG;     // nothing to reuse for these tiles
     if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
     int st = argus_check_shape(shape, (size_t)-1);
     if (st) return st;
@@ -535,11 +540,14 @@ extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* 
     a.z1 = plan->z1; a.z2 = plan->z2; a.z3 = P_D ? plan->z3 : nullptr; a.psd = plan->psd;
     a.D = D; a.S = S; a.PD = P_D; a.sigma_S = sigma_S;
     cudaStream_t s = (cudaStream_t)stream;
+    int rc;
     switch (plan->tile) {
-        case 256: return run<256>(plan, a, s);
-        case 512: return run<512>(plan, a, s);
-        default: return run<1024>(plan, a, s);
+        case 256: rc = run<256>(plan, a, s); break;
+        case 512: rc = run<512>(plan, a, s); break;
+        default: rc = run<1024>(plan, a, s); break;
     }
+    if (psf_n) plan->psf_tiles = rc == ARGUS_OK ? n_tiles : 0;
+    return rc;
 }
 
 extern "C" int argus_proper_coadd(argus_proper_plan* plan, const float* stack, int n_frames, argus_shape shape,
@@ -558,6 +566,7 @@ extern "C" int argus_proper_coadd(argus_proper_plan* plan, const float* stack, i
     a.w = shape.w; a.h = shape.h; a.origins = origins; a.n_tiles = n_tiles; a.F = F; a.sig = sigma;
     a.n_frames = n_frames; a.psfs = psfs; a.ps = psf_size; a.j0 = 0; a.eps2 = (double)eps * (double)eps;
     a.z1 = plan->z1; a.z2 = plan->z2; a.acc = plan->z3; a.acc2 = plan->z4;
+    plan->psf_tiles = 0;                                   // z2 is about to hold frame PSFs
     a.S = S; a.R = R; a.PR = P_R; a.F_R = F_R; a.sigma_S = sigma_S;
     cudaStream_t s = (cudaStream_t)stream;
     switch (plan->tile) {

@@ -154,3 +154,39 @@ def test_proper_coadd_parity(ora, T, J):
         assert np.abs(S[i] - o["S"]).max() <= 8 * eS
         assert np.abs(PR[i] - o["P_R"]).max() <= 64 * F32_EPS * np.abs(o["P_R"]).max()
         assert abs(FR[0] / o["F_R"] - 1) < 1e-6 and abs(sig[i] / o["sigma_S"] - 1) < 1e-6
+
+
+def test_zogy_reuses_psf_transforms_and_coadd_discards_them(ora):
+    """A call without PSFs gives the outputs of the call that supplied them, bit for bit;
+    after a proper-coadd call on the plan it is refused."""
+    T, w, h = 256, 600, 400
+    N, R = _frame(w, h, seed=5, sn=12.0, sr=3.0, psf_n=_gauss(1.8), psf_r=_gauss(1.3), Fn=1.0, Fr=1.0)
+    rec = np.zeros(2, B.ZOGY_TILE_DTYPE)
+    rec[0] = (0, 0, 1.0, 1.0, 12.0, 3.0)
+    rec[1] = (300, 100, 1.0, 1.0, 12.0, 3.0)
+    pn = np.stack([_gauss(1.8), _gauss(1.9)])
+    pr = np.stack([_gauss(1.3), _gauss(1.3)])
+    pitch = pitch_for(w)
+    plan = B.proper_plan_create(0, T, 2)
+    try:
+        dN, dR = dev_pitched(N), dev_pitched(R)
+        d_rec = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+        sh = B.argus_shape(w, h, pitch)
+        D1 = torch.empty((2, T, T), device="cuda")
+        S1 = torch.empty((2, T, T), device="cuda")
+        D2 = torch.empty((2, T, T), device="cuda")
+        S2 = torch.empty((2, T, T), device="cuda")
+        B.argus_zogy(plan, dN, dR, sh, d_rec, 2, torch.from_numpy(pn).cuda(), torch.from_numpy(pr).cuda(), 31, 1e-8,
+                     D1, S1)
+        B.argus_zogy(plan, dN, dR, sh, d_rec, 2, None, None, 31, 1e-8, D2, S2)
+        torch.cuda.synchronize()
+        assert torch.equal(D1, D2) and torch.equal(S1, S2)
+        stack = dN.unsqueeze(0).contiguous()
+        org = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+        one = torch.ones(1, device="cuda")
+        B.argus_proper_coadd(plan, stack, 1, sh, org, 1, one, one, torch.from_numpy(pn[:1]).cuda(), 31, 1e-8,
+                             torch.empty((1, T, T), device="cuda"), torch.empty((1, T, T), device="cuda"))
+        with pytest.raises(B.ArgusError):
+            B.argus_zogy(plan, dN, dR, sh, d_rec, 2, None, None, 31, 1e-8, D2, S2)
+    finally:
+        B.proper_plan_destroy(plan)
