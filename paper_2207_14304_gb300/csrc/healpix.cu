@@ -1,13 +1,15 @@
 // Frame to HEALPix segment resampling (paper Sec. 3.3 "Image Segmentation";
 // Table 2, GPU stage "Image segmentation and resampling to HEALPix grid").
 //
-// One thread per segment-image pixel: the segment's nested index gives its
-// base face and face coordinates (X, Y); image pixel (column c, row r) is the
-// HEALPix pixel (X 2^k + c, Y 2^k + r) at NSIDE_seg 2^k, whose centre (the
-// ring / longitude formulas of the nested layout) is projected into the frame
-// by the gnomonic WCS and the frame is interpolated there (bilinear, nested
-// lerps, coverage as in the coadd).  The geometry is FP64 (a 9576-pixel frame
-// needs positions to 1e-9 of the field); the output is FP32.
+// The segment's nested index gives its base face and face coordinates (X, Y);
+// image pixel (column c, row r) is the HEALPix pixel (X 2^k + c, Y 2^k + r) at
+// NSIDE_seg 2^k, whose centre (the ring / longitude formulas of the nested
+// layout) is projected into the frame by the gnomonic WCS and the frame is
+// interpolated there (bilinear, nested lerps, coverage as in the coadd).  The
+// geometry is FP64 (a 9576-pixel frame needs positions to 1e-9 of the field);
+// the output is FP32.  Exact path: one thread per pixel.  Row path (k >= 6):
+// one warp per row, exact positions at four nodes per 64-pixel piece and a
+// cubic between them in the equatorial belt (see healpix_rows_kernel).
 #include "argus_internal.cuh"
 
 #include <cmath>
@@ -113,6 +115,113 @@ __host__ __device__ __forceinline__ bool hp_bilinear(const HpArgs& a, double x, 
     return true;
 }
 
+// Row interpolation (the fast path).  Along a segment-image row in the
+// equatorial belt the frame position is a smooth function of the column: on
+// pieces of 64 pixels a cubic through the exact FP64 positions at columns
+// 0, 21, 42, 63 of the piece reproduces it to a few 1e-8 pixel.  Newton form:
+// d[0] = f0, d[1] = f[t0,t1], d[2] = f[t0,t1,t2], d[3] = f[t0..t3].
+constexpr int HP_PIECE = 64;
+__host__ __device__ __forceinline__ int hp_node(int j) { return j == 0 ? 0 : (j == 1 ? 21 : (j == 2 ? 42 : 63)); }
+
+__host__ __device__ __forceinline__ void hp_cubic_coeffs(const double* f, double* d) {
+    const double f01 = (f[1] - f[0]) / 21.0, f12 = (f[2] - f[1]) / 21.0, f23 = (f[3] - f[2]) / 21.0;
+    const double f012 = (f12 - f01) / 42.0, f123 = (f23 - f12) / 42.0;
+    d[0] = f[0];
+    d[1] = f01;
+    d[2] = f012;
+    d[3] = (f123 - f012) / 63.0;
+}
+
+__host__ __device__ __forceinline__ double hp_cubic_eval(const double* d, double t) {
+    return d[0] + t * (d[1] + (t - 21.0) * (d[2] + (t - 42.0) * d[3]));
+}
+
+// Whether a whole segment-image row lies in the equatorial belt (where the
+// row interpolation is used): ring indices of its two end pixels in [N, 3N].
+__host__ __device__ __forceinline__ bool hp_row_in_belt(const HpArgs& a, long long seg, int r) {
+    const long long N = a.nside_seg;
+    const long long face = seg / (N * N);
+    if (seg < 0 || face >= 12) return false;
+    const long long ipf = seg - face * N * N;
+    long long X = 0, Y = 0;
+    for (int b = 0; (1LL << b) < N; b++) {
+        X |= ((ipf >> (2 * b)) & 1LL) << b;
+        Y |= ((ipf >> (2 * b + 1)) & 1LL) << b;
+    }
+    const long long nside = N << a.k, m = 1LL << a.k;
+    const long long jrll = face < 4 ? 2 : (face < 8 ? 3 : 4);
+    const long long iy = (Y << a.k) + r;
+    const long long jr0 = jrll * nside - (X << a.k) - iy - 1;         // column 0
+    const long long jr1 = jr0 - (m - 1);                              // column m - 1
+    return jr1 >= nside && jr0 <= 3 * nside;
+}
+
+// One warp per segment-image row (k >= 6): in the belt, lanes compute the
+// exact positions of the four nodes of eight pieces at once and each lane
+// evaluates 16 pixels of its piece from the cubic; elsewhere (and for pieces
+// with a node behind the tangent plane) every pixel takes the exact path.
+__global__ void __launch_bounds__(256) healpix_rows_kernel(HpArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long m = 1L << a.k;
+    const long rows = (long)a.n_seg * m;
+    const int npieces = (int)(m / HP_PIECE);
+    const long warps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long wr = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wr < rows; wr += warps) {
+        const long s = wr / m;
+        const int r = (int)(wr - s * m);
+        const long long seg = a.segs[s];
+        float* orow = a.out + wr * m;
+        uint8_t* crow = a.cov ? a.cov + wr * m : nullptr;
+        if (!hp_row_in_belt(a, seg, r)) {
+            for (int c = lane; c < m; c += 32) {
+                double x, y;
+                float v = 0.0f;
+                const bool ok = hp_pixel_xy(a, seg, c, r, x, y) && hp_bilinear(a, x, y, v);
+                orow[c] = ok ? v : 0.0f;
+                if (crow) crow[c] = ok ? 1 : 0;
+            }
+            continue;
+        }
+        for (int pg = 0; pg < npieces; pg += 8) {
+            const int p = pg + (lane >> 2), j = lane & 3;
+            double xn = 0.0, yn = 0.0;
+            bool okn = false;
+            if (p < npieces) okn = hp_pixel_xy(a, seg, p * HP_PIECE + hp_node(j), r, xn, yn);
+            // the piece's four nodes from lanes 4 (lane / 4) + 0..3
+            double fx[4], fy[4];
+            bool all = true;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int src = (lane & ~3) + q;
+                fx[q] = __shfl_sync(0xffffffffu, xn, src);
+                fy[q] = __shfl_sync(0xffffffffu, yn, src);
+                all = all && __shfl_sync(0xffffffffu, okn ? 1 : 0, src);
+            }
+            if (p >= npieces) continue;                 // no barrier or shuffle below
+            double dx[4], dy[4];
+            hp_cubic_coeffs(fx, dx);
+            hp_cubic_coeffs(fy, dy);
+            for (int i = 0; i < HP_PIECE / 4; i++) {
+                const int t = 4 * i + j;
+                const int c = p * HP_PIECE + t;
+                double x, y;
+                bool ok;
+                if (all) {
+                    x = hp_cubic_eval(dx, (double)t);
+                    y = hp_cubic_eval(dy, (double)t);
+                    ok = true;
+                } else {
+                    ok = hp_pixel_xy(a, seg, c, r, x, y);
+                }
+                float v = 0.0f;
+                ok = ok && hp_bilinear(a, x, y, v);
+                orow[c] = ok ? v : 0.0f;
+                if (crow) crow[c] = ok ? 1 : 0;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) healpix_resample_kernel(HpArgs a) {
     const long m = 1L << a.k;
     const long total = (long)a.n_seg * m * m;
@@ -156,10 +265,17 @@ extern "C" int argus_healpix_resample(const float* frame, const uint8_t* flags, 
     a.frame = frame; a.flags = flags; a.pitch = shape.pitch; a.w = shape.w; a.h = shape.h;
     a.segs = segs; a.n_seg = n_seg; a.nside_seg = nside_seg; a.k = k; a.out = out; a.cov = coverage;
     hp_fill_wcs(a, wcs);
-    const long total = (long)n_seg << (2 * k);
-    long blocks = (total + 255) / 256;
-    if (blocks > 152L * 32) blocks = 152L * 32;
-    healpix_resample_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    if (k >= 6) {                                  // rows of whole 64-pixel pieces: row interpolation
+        const long rows = (long)n_seg << k;
+        long blocks = (rows + 7) / 8;                  // 8 warps (rows) per CTA
+        if (blocks > 152L * 32) blocks = 152L * 32;
+        healpix_rows_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    } else {
+        const long total = (long)n_seg << (2 * k);
+        long blocks = (total + 255) / 256;
+        if (blocks > 152L * 32) blocks = 152L * 32;
+        healpix_resample_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    }
     argus_count_launch(1);
     return argus_launch_status();
 }

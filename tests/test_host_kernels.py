@@ -200,10 +200,13 @@ def _segments_in_view(wcs, w, h, nside_seg, n, rng):
 
 
 @pytest.mark.parametrize("nside_seg,k,delta0,use_flags", [(64, 4, 0.4, True), (32, 5, 1.45, False),
-                                                          (128, 3, -0.7, True)])
+                                                          (128, 3, -0.7, True), (256, 6, 0.3, True),
+                                                          (128, 7, -0.5, False), (64, 6, 1.2, True),
+                                                          (256, 9, 0.1, False)])
 def test_healpix_resampling_matches_the_oracle(drivers, nside_seg, k, delta0, use_flags):
     """Coverage bit-exact and values within 4 ulps of the largest frame value, for segments
-    around and across the frame edge (a polar-cap field at delta0 = 1.45 included)."""
+    around and across the frame edge (a polar-cap field at delta0 = 1.45 included); k >= 6
+    takes the row path (cubic between exact nodes) in the equatorial belt."""
     from oracle import healpix as hp
     rng = np.random.default_rng(nside_seg + k)
     w, h = 700, 500
