@@ -1,6 +1,8 @@
 """HEALPix segmentation on the GPU (Sec. 3.3; Table 2 GPU stage "Image
 segmentation and resampling to HEALPix grid") against the FP64 oracle:
-coverage bit-exact, values within 4 ulps of the largest frame value.
+coverage bit-exact, values within 4 ulps of the largest frame value, on both
+the exact per-pixel path (k < 6, polar-cap rows) and the row path (k >= 6 in
+the equatorial belt).
 
 The kernel has not run on a GPU yet, so the file is skipped until it has.
 """
@@ -27,7 +29,8 @@ def _lib():
     B.load()
 
 
-@pytest.mark.parametrize("nside_seg,k,delta0", [(64, 4, 0.4), (256, 6, -0.3), (32, 5, 1.45)])
+@pytest.mark.parametrize("nside_seg,k,delta0", [(64, 4, 0.4), (256, 6, -0.3), (32, 5, 1.45), (256, 9, 0.2),
+                                               (128, 7, 1.1)])
 def test_healpix_resample_parity(ora, nside_seg, k, delta0):
     from oracle import healpix as hp
     rng = np.random.default_rng(nside_seg + k)
