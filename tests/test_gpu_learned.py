@@ -33,6 +33,18 @@ def _tensors(n=200_961):
     return out
 
 
+def _test_weights(seed):
+    """He-normal weights and small biases drawn by the test (never read back from the
+    library), FP32."""
+    rng = np.random.default_rng(seed)
+    fan = {"W1": 2, "W6": 32, **{f"W{l + 2}": 49 * 32 for l in range(4)}}
+    out = np.empty(200_961, np.float32)
+    for nm, sl in _tensors():
+        n = sl.stop - sl.start
+        out[sl] = (rng.normal(0, np.sqrt(2.0 / fan[nm]), n) if nm in fan else rng.normal(0, 0.01, n))
+    return out
+
+
 @pytest.fixture(scope="module")
 def net():
     if not torch.cuda.is_available():
@@ -45,11 +57,12 @@ def net():
 
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 2e-2)])
 def test_cnn_forward_backward_parity(ora, net, prec, tol):
-    net.set_precision(prec)
-    w = net.tensors()[0]
-    if prec == "bf16":   # the oracle gets the weights the GPU computes with (BF16-consistent)
-        w = w.to(torch.bfloat16).to(torch.float32)
-    master = w.cpu().numpy().astype(np.float64)
+    w32 = _test_weights(11)
+    net.tensors()[0].copy_(torch.from_numpy(w32).cuda())          # the test's weights into the network
+    net.set_precision(prec)                                          # refreshes the BF16 copy from them
+    if prec == "bf16":   # the oracle gets the BF16-rounded weights the GPU computes with, rounded on the host
+        w32 = torch.from_numpy(w32).to(torch.bfloat16).to(torch.float32).numpy()
+    master = w32.astype(np.float64)
     rng = np.random.default_rng(1)
     x = rng.normal(0, 1, (3, NPX, 2)).astype(np.float32)
     dy = rng.normal(0, 1e-3, (3, NPX)).astype(np.float32)
@@ -73,15 +86,21 @@ def test_cnn_forward_backward_parity(ora, net, prec, tol):
 
 
 def test_cnn_adam_step_matches_oracle(ora, net):
-    master, m, v = (t.clone() for t in net.tensors())
-    step0 = net.step
+    """Parameters, moments, step and gradient all drawn by the test and loaded into the
+    network; one library Adam step against the oracle's."""
     rng = np.random.default_rng(2)
-    gr = rng.normal(0, 1e-2, master.numel()).astype(np.float32)
+    n = 200_961
+    p0 = _test_weights(3)
+    m0 = rng.normal(0, 1e-3, n).astype(np.float32)
+    v0 = rng.uniform(0, 1e-5, n).astype(np.float32)
+    step0 = 7
+    for t, a in zip(net.tensors(), (p0, m0, v0)):
+        t.copy_(torch.from_numpy(a).cuda())
+    B.argus_cnn_set_state(net.net, net.precision, step0)
+    gr = rng.normal(0, 1e-2, n).astype(np.float32)
     B.argus_cnn_adam(net.net, torch.from_numpy(gr).cuda(), 1e-3)
     torch.cuda.synchronize()
-    p = master.cpu().numpy().astype(np.float64)
-    mm = m.cpu().numpy().astype(np.float64)
-    vv = v.cpu().numpy().astype(np.float64)
+    p, mm, vv = p0.astype(np.float64), m0.astype(np.float64), v0.astype(np.float64)
     ora.adam(p, mm, vv, gr.astype(np.float64), lr=1e-3, step=step0 + 1)
     after = net.tensors()[0].cpu().numpy()
     np.testing.assert_allclose(after, p, rtol=1e-5, atol=1e-8)

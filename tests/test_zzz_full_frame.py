@@ -24,7 +24,7 @@ import pytest
 import torch
 
 from paper_2207_14304_gb300 import _binding as B
-from tests.gpu_helpers import F32_EPS, assert_rel
+from tests.gpu_helpers import F32_EPS, assert_rel, check_detection_properties
 
 pytestmark = pytest.mark.gpu
 
@@ -45,37 +45,6 @@ def _calib_scale(n, cal):
         sI = np.where(ok, (ng + np.abs(dark)) / np.abs(flat), 1.0)
         sV = np.where(ok, (ng + cal["rn"] ** 2) / flat.astype(np.float64) ** 2, 1.0)
     return sI, sV
-
-
-def check_detection_properties(D, VD, fl, mask, src, n_found, nsigma):
-    """The detection checks above, on host arrays (float32 D, VD; uint8 fl, mask)."""
-    import scipy.ndimage as ndi
-    valid = (fl == 0) & (VD > 0) & np.isfinite(D) & np.isfinite(VD)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        S = np.where(valid, D / np.sqrt(VD), np.float32(0)).astype(np.float32)
-    m = np.where(valid, (S >= nsigma) * B.ARGUS_MASK_POS + (S <= -nsigma) * B.ARGUS_MASK_NEG,
-                 B.ARGUS_MASK_INVALID).astype(np.uint8)
-    np.testing.assert_array_equal(mask, m)
-    eight = np.ones((3, 3), bool)
-    lab_p, n_p = ndi.label(m == B.ARGUS_MASK_POS, structure=eight)
-    lab_n, n_n = ndi.label(m == B.ARGUS_MASK_NEG, structure=eight)
-    assert n_found == n_p + n_n
-    keys = list(zip(src["py"], src["px"]))
-    assert keys == sorted(keys)
-    A = np.abs(S)
-    for lab, sign in ((lab_p, 1), (lab_n, -1)):
-        sel = src[src["sign"] == sign]
-        if len(sel) == 0:
-            continue
-        ids = lab[sel["py"], sel["px"]]
-        assert (ids > 0).all()
-        sizes = np.bincount(lab.ravel())
-        np.testing.assert_array_equal(sel["npix"], sizes[ids])
-        peaks = ndi.maximum_position(A, lab, ids)     # first maximum in raster order
-        np.testing.assert_array_equal(np.array(peaks, dtype=np.int64).reshape(-1, 2),
-                                      np.stack([sel["py"], sel["px"]], 1))
-        np.testing.assert_array_equal(sel["peak_snr"], S[sel["py"], sel["px"]])
-    return n_p, n_n
 
 
 def test_full_frame_path_against_the_oracle(ora):
