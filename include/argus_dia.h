@@ -294,6 +294,15 @@ int argus_segments_items(const argus_seg_plan *plan, int *n_fit_items, int *n_su
  * run to caller buffers (device; either may be NULL). */
 int argus_segments_kernels(const argus_seg_plan *plan, float *K, double *bg, argus_stream stream);
 
+/* The subtraction of argus_segments_run alone, with given kernels (device
+ * float [n][ksize^2], row-major, the layout argus_segments_kernels returns)
+ * and backgrounds (device double [n]) in place of fitted ones -- kernels kept
+ * from an earlier exposure, or a reference's kernels in a test.  They replace
+ * the plan's stored kernels.  Not graph-captured; no detection. */
+int argus_segments_subtract(argus_seg_plan *plan, const float *sci, const float *sci_var, const float *ref,
+                            const float *ref_var, const uint8_t *flags, const float *K, const double *bg,
+                            float *diff, float *diff_var, argus_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Learned kernel surrogate (a learned stand-in for the least-squares kernel
  * fit, with the fit kept as fallback and judge; the paper has no counterpart).  A CNN maps a stamp pair (science and reference, 21x21, both

@@ -114,6 +114,7 @@ SIGNATURES = {
     "argus_segments_destroy": ([P], I),
     "argus_segments_run": ([P, P, P, P, P, P, P, P, P, P, P, F, F, P, I, P, I, P], I),
     "argus_segments_items": ([P, C.POINTER(I), C.POINTER(I)], I),
+    "argus_segments_subtract": ([P, P, P, P, P, P, P, P, P, P, P], I),
     "argus_segments_kernels": ([P, P, P, P], I),
     "argus_cnn_create": ([C.POINTER(P), I, I, C.c_ulonglong], I),
     "argus_cnn_destroy": ([P], I),
@@ -466,6 +467,12 @@ def argus_healpix_resample(frame, flags, shape, wcs, nside_seg, k, segs, n_seg, 
     _check(load().argus_healpix_resample(_ptr(frame), _ptr(flags), shape, wcs, int(nside_seg), int(k), _ptr(segs),
                                          int(n_seg), _ptr(out), _ptr(coverage), _stream(stream)),
            "argus_healpix_resample")
+
+
+def argus_segments_subtract(plan, sci, sci_var, ref, ref_var, flags, K, bg, diff, diff_var, stream=None):
+    _check(load().argus_segments_subtract(plan, _ptr(sci), _ptr(sci_var), _ptr(ref), _ptr(ref_var), _ptr(flags),
+                                          _ptr(K), _ptr(bg), _ptr(diff), _ptr(diff_var), _stream(stream)),
+           "argus_segments_subtract")
 
 
 def sources_from_bytes(buf: torch.Tensor, n: int):

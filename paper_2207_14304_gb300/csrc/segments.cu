@@ -660,3 +660,33 @@ extern "C" int argus_segments_kernels(const argus_seg_plan* p, float* K, double*
         return ARGUS_ERR_CUDA;
     return ARGUS_OK;
 }
+
+extern "C" int argus_segments_subtract(argus_seg_plan* p, const float* sci, const float* sci_var, const float* ref,
+                                       const float* ref_var, const uint8_t* flags, const float* K, const double* bg,
+                                       float* diff, float* diff_var, argus_stream stream) {
+    if (!p || !sci || !sci_var || !ref || !ref_var || !flags || !K || !bg || !diff || !diff_var) return ARGUS_ERR_ARG;
+    const void* ps[] = {sci, sci_var, ref, ref_var, flags, diff, diff_var};
+    for (const void* q : ps)
+        if (argus_check_ptr16(q)) return ARGUS_ERR_ALIGN;
+    if (cudaSetDevice(p->ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int kk = p->bd.ks * p->bd.ks;
+    // the given kernels and backgrounds replace the plan's fitted ones
+    if (cudaMemcpyAsync(p->d_K, K, sizeof(float) * (size_t)kk * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->d_bg, bg, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(p->d_counters, 0, sizeof(int) * 4, st) != cudaSuccess)
+        return ARGUS_ERR_CUDA;
+    SegSubArgs ua;
+    ua.sci = sci; ua.var = sci_var; ua.ref = ref; ua.ref_var = ref_var; ua.flags = flags; ua.diff = diff;
+    ua.diff_var = diff_var; ua.pitch = p->pitch; ua.seg = p->d_seg; ua.items = p->d_sub_items;
+    ua.n_items = p->n_sub_items; ua.counter = p->d_counters + 1; ua.K = p->d_K; ua.bg = p->d_bg; ua.kk = kk;
+    const int grid = p->ctx->num_sms * p->cfg.sub_ctas_per_sm;
+    switch (p->bd.ks) {
+        case 7: return launch_seg_sub<7>(ua, grid, st);
+        case 9: return launch_seg_sub<9>(ua, grid, st);
+        case 11: return launch_seg_sub<11>(ua, grid, st);
+        case 15: return launch_seg_sub<15>(ua, grid, st);
+        case 21: return launch_seg_sub<21>(ua, grid, st);
+        default: return ARGUS_ERR_UNSUPPORTED;
+    }
+}

@@ -10,8 +10,13 @@ with the oracle's kernel) within the unit-test bars (1e-4 of max(|I|,
 |R (x) K|, 1); 1e-5 relative) plus what the kernel and background bars allow
 (|dK| <= 1e-3 max|K| per pixel times the window sums of |R| and of V_ref);
 detection is checked on the GPU's own atlas by properties that hold at any
-size (threshold mask, 8-connected components, peaks, sizes, order).
+size (threshold mask, 8-connected components, peaks, sizes, order).  The
+batched subtraction alone, given the oracle's kernels, is compared at the
+unit-test bars (argus_segments_subtract; skipped unless ARGUS_GPU_NEW=1 until
+it has run on a GPU).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -105,5 +110,57 @@ def test_segments_parity(ora, use_graph):
                                               batch.flags.cpu().numpy(), batch.mask.cpu().numpy(), src, nsrc, 5.0)
         n_checked = n_p + n_n
         print(f"\n[segments graph={use_graph}] {len(sides)} segments, {nsrc} sources, checked {n_checked}")
+    finally:
+        batch.close()
+
+
+@pytest.mark.skipif(os.environ.get("ARGUS_GPU_NEW") != "1",
+                    reason="argus_segments_subtract not yet run on a GPU")
+def test_segments_subtract_with_the_oracles_kernels(ora):
+    """The batched subtraction alone, given the oracle's kernels and backgrounds, against
+    the oracle's difference and variance at the unit-test bars (1e-4 of max(|I|,
+    |R (x) K|, 1); 1e-5 relative)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, h = 640, 480
+    I, V, R, Vr, fl = _frame(w, h, seed=32)
+    sides = [40, 57, 64, 90, 111, 128, 48, 70]
+    origins = synth.segment_origins(sides, w, h, seed=4)
+    ks = 15
+    r = ks // 2
+    basis = B.make_basis(ks, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)
+    ob = ora.Basis(ksize=ks, spatial_degree=0, bg_degree=0)
+    batch = SegmentBatch(sides, basis=basis, width=256, cfg=B.argus_seg_config(32, 1, 4, 0), src_cap=4096)
+    try:
+        Ks, bgs = [], []
+        for i, ((x0, y0), s) in enumerate(zip(origins, sides)):
+            sl = (slice(y0, y0 + s), slice(x0, x0 + s))
+            for t, a in ((batch.sci, I), (batch.var, V), (batch.ref, R), (batch.ref_var, Vr), (batch.flags, fl)):
+                batch.view(t, i).copy_(torch.from_numpy(np.ascontiguousarray(a[sl])))
+            res = ora.fit_rect(*(np.ascontiguousarray(a[sl]) for a in (I, V, R)), np.ascontiguousarray(fl[sl]),
+                               (r, r, s - 1 - r, s - 1 - r), ob)
+            Ko, bgo = ora.expand(ob, res.coeffs)
+            Ks.append(Ko.astype(np.float32).reshape(-1))
+            bgs.append(float(bgo[0]))
+        dK = torch.from_numpy(np.stack(Ks)).cuda()
+        dbg = torch.tensor(bgs, dtype=torch.float64, device="cuda")
+        batch.diff.fill_(-9.0)
+        batch.diff_var.fill_(-9.0)
+        B.argus_segments_subtract(batch.plan, batch.sci, batch.var, batch.ref, batch.ref_var, batch.flags, dK, dbg,
+                                  batch.diff, batch.diff_var)
+        torch.cuda.synchronize()
+        assert B.argus_sync_status(batch.ctx) == 0
+        for i, ((x0, y0), s) in enumerate(zip(origins, sides)):
+            sl = (slice(y0, y0 + s), slice(x0, x0 + s))
+            Is, Vs, Rs, Vrs, Fs = (np.ascontiguousarray(a[sl]) for a in (I, V, R, Vr, fl))
+            K64 = Ks[i].reshape(1, ks, ks).astype(np.float64)
+            Do, VDo = ora.subtract(Is, Vs, Rs, Vrs, Fs, K64, [bgs[i]], sdeg=0, bgdeg=0)
+            Cabs, _ = ora.subtract(np.zeros_like(Is), Vs, np.abs(Rs), Vrs, Fs, np.abs(K64), [0.0], sdeg=0, bgdeg=0,
+                                   with_var=False)
+            Dg = batch.view(batch.diff, i).cpu().numpy()
+            VDg = batch.view(batch.diff_var, i).cpu().numpy()
+            scale = np.maximum(np.maximum(np.abs(Is), -Cabs), 1.0)
+            assert (np.abs(Dg - Do) / scale).max() < 1e-4, i
+            assert (np.abs(VDg - VDo) / np.maximum(VDo, 1e-6)).max() < 1e-5, i
     finally:
         batch.close()
