@@ -455,7 +455,7 @@ int argus_background(argus_ctx *ctx, const float *img, const uint8_t *flags, arg
 
 /* ---------------------------------------------------------------------------
  * Proper-image statistics on square tiles: ZOGY subtraction and proper
- * coaddition share one plan (transform buffers, 64 bytes per tile pixel, and
+ * coaddition share one plan (transform buffers, 48 bytes per tile pixel, and
  * the twiddle tables of one tile size).
  *
  * ZOGY proper image subtraction on square tiles (paper Sec. 4.2: ZOGY for
