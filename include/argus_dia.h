@@ -485,18 +485,20 @@ int argus_proper_plan_create(int device, int tile, int max_tiles, argus_proper_p
 int argus_proper_plan_destroy(argus_proper_plan *plan);
 
 /* N, R: device float [h][pitch] (one shape); tiles: device argus_zogy_tile
- * [n_tiles]; psf_n, psf_r: device float [n_tiles][psf_size][psf_size], odd
- * psf_size <= 63, or both NULL to reuse the PSF transforms of the last call on
- * this plan that gave PSFs (PSFs change per pointing, frames per exposure; the
- * FP64 transforms are the costliest part of a call) -- then n_tiles may not
- * exceed that call's, and a proper-coadd call in between discards them;
+ * [n_tiles]; psf_n, psf_r: device float [n_tiles][psf_size][psf_size] with
+ * psf_per_tile = 1, or one pair [psf_size][psf_size] shared by every tile with
+ * psf_per_tile = 0 (one FP64 transform instead of n_tiles); odd psf_size <= 63;
+ * or both NULL to reuse the PSF transforms of the last call on this plan that
+ * gave PSFs (PSFs change per pointing, frames per exposure; the FP64 transforms
+ * are the costliest part of a call) -- with the same psf_per_tile, n_tiles not
+ * above that call's, and no proper-coadd call in between (it discards them);
  * D, S and P_D (nullable): device float [n_tiles][T][T]; sigma_S (nullable):
  * device double [n_tiles].  1 <= n_tiles <= max_tiles.  Calls on one plan must
  * not overlap. */
 int argus_zogy(argus_proper_plan *plan, const float *N, const float *R, argus_shape shape,
                const argus_zogy_tile *tiles, int n_tiles, const float *psf_n, const float *psf_r,
-               int psf_size, float eps, float *D, float *S, float *P_D, double *sigma_S,
-               argus_stream stream);
+               int psf_size, int psf_per_tile, float eps, float *D, float *S, float *P_D,
+               double *sigma_S, argus_stream stream);
 
 /* Proper coaddition (paper Sec. 4.1.3: per-image matched filtering of
  * pre-aligned tiles; the statistic of Zackay & Ofek 2017) on the tiles of a
@@ -511,14 +513,16 @@ int argus_zogy(argus_proper_plan *plan, const float *N, const float *R, argus_sh
  * stack: device float [n_frames][h][pitch] (one shape; pixels off the frame
  * are 0); origins: device int [n_tiles][2] (tile pixel (0, 0) in the frame);
  * F, sigma: device float [n_frames] (a frame with sigma <= 0 is left out);
- * psfs: device float [n_tiles][n_frames][psf_size][psf_size], odd psf_size
- * <= 63; S, R, P_R (nullable): device float [n_tiles][T][T]; F_R (nullable):
+ * psfs: device float [n_tiles][n_frames][psf_size][psf_size] with
+ * psf_per_tile = 1, or [n_frames][psf_size][psf_size] shared by every tile with
+ * psf_per_tile = 0 (one FP64 transform per frame instead of one per tile and
+ * frame); odd psf_size <= 63; S, R, P_R (nullable): device float [n_tiles][T][T]; F_R (nullable):
  * device double [1]; sigma_S (nullable): device double [n_tiles].
  * 1 <= n_frames <= 64.  Frames go through the transforms in pairs. */
 int argus_proper_coadd(argus_proper_plan *plan, const float *stack, int n_frames, argus_shape shape,
                        const int *origins, int n_tiles, const float *F, const float *sigma, const float *psfs,
-                       int psf_size, float eps, float *S, float *R, float *P_R, double *F_R, double *sigma_S,
-                       argus_stream stream);
+                       int psf_size, int psf_per_tile, float eps, float *S, float *R, float *P_R, double *F_R,
+                       double *sigma_S, argus_stream stream);
 
 /* ---------------------------------------------------------------------------
  * HEALPix segmentation (paper Sec. 3.3 "Image Segmentation": frames are

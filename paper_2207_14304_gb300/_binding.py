@@ -133,8 +133,8 @@ SIGNATURES = {
     "argus_background": ([P, P, P, SH, I, I, F, P, P, P], I),
     "argus_proper_plan_create": ([I, I, I, C.POINTER(P)], I),
     "argus_proper_plan_destroy": ([P], I),
-    "argus_zogy": ([P, P, P, SH, P, I, P, P, I, F, P, P, P, P, P], I),
-    "argus_proper_coadd": ([P, P, I, SH, P, I, P, P, P, I, F, P, P, P, P, P, P], I),
+    "argus_zogy": ([P, P, P, SH, P, I, P, P, I, I, F, P, P, P, P, P], I),
+    "argus_proper_coadd": ([P, P, I, SH, P, I, P, P, P, I, I, F, P, P, P, P, P, P], I),
     "argus_healpix_resample": ([P, P, SH, argus_wcs, I, I, P, I, P, P, P], I),
 }
 
@@ -445,19 +445,22 @@ def proper_plan_destroy(plan):
 
 
 def argus_zogy(plan, N, R, shape, tiles, n_tiles, psf_n, psf_r, psf_size, eps, D, S, P_D=None, sigma_S=None,
-               stream=None):
+               stream=None, psf_per_tile=True):
     """tiles: a device uint8 tensor holding n_tiles records of ZOGY_TILE_DTYPE; psf_n and
-    psf_r both None reuse the PSF transforms of the plan's last call that gave PSFs."""
+    psf_r both None reuse the PSF transforms of the plan's last call that gave PSFs;
+    psf_per_tile False: one PSF pair shared by every tile."""
     _check(load().argus_zogy(plan, _ptr(N), _ptr(R), shape, _ptr(tiles), int(n_tiles), _ptr(psf_n), _ptr(psf_r),
-                             int(psf_size), float(eps), _ptr(D), _ptr(S), _ptr(P_D), _ptr(sigma_S),
-                             _stream(stream)), "argus_zogy")
+                             int(psf_size), 1 if psf_per_tile else 0, float(eps), _ptr(D), _ptr(S), _ptr(P_D),
+                             _ptr(sigma_S), _stream(stream)), "argus_zogy")
 
 
 def argus_proper_coadd(plan, stack, n_frames, shape, origins, n_tiles, F, sigma, psfs, psf_size, eps, S, R, P_R=None,
-                       F_R=None, sigma_S=None, stream=None):
+                       F_R=None, sigma_S=None, stream=None, psf_per_tile=True):
+    """psf_per_tile False: psfs holds one PSF per frame, shared by every tile."""
     _check(load().argus_proper_coadd(plan, _ptr(stack), int(n_frames), shape, _ptr(origins), int(n_tiles), _ptr(F),
-                                     _ptr(sigma), _ptr(psfs), int(psf_size), float(eps), _ptr(S), _ptr(R),
-                                     _ptr(P_R), _ptr(F_R), _ptr(sigma_S), _stream(stream)), "argus_proper_coadd")
+                                     _ptr(sigma), _ptr(psfs), int(psf_size), 1 if psf_per_tile else 0, float(eps),
+                                     _ptr(S), _ptr(R), _ptr(P_R), _ptr(F_R), _ptr(sigma_S), _stream(stream)),
+           "argus_proper_coadd")
 
 
 def argus_healpix_resample(frame, flags, shape, wcs, nside_seg, k, segs, n_seg, out, coverage=None, stream=None):

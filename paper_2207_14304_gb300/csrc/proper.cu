@@ -34,7 +34,7 @@ struct argus_proper_plan {
     int device;
     int tile;
     int max_tiles;
-    int psf_tiles;    // tiles whose ZOGY PSF transforms z2 holds (0 after a coadd call)
+    int psf_tiles;    // ZOGY PSF transforms z2 holds: that many tiles', -1 one shared pair, 0 none
     float2* z1;       // [max_tiles][T][T]
     double2* z2;      // [max_tiles][T][T]
     float2* z3;       // [max_tiles][T][T] (ZOGY: P_D; coadd: the score accumulator, then P_R)
@@ -56,6 +56,7 @@ struct ZArgs {
     const float* psf_n;
     const float* psf_r;
     int ps;
+    int psf_tiles;            // tiles with their own PSF pair: n_tiles, or 1 when all share one
     double eps2;
     float2* z1;
     double2* z2;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(256) zogy_pack_kernel(ZArgs a) {
 template <int T>
 __global__ void __launch_bounds__(256) zogy_psf_kernel(ZArgs a) {
     const int pp = a.ps * a.ps, hh = a.ps / 2;
-    const long total = (long)a.n_tiles * pp;
+    const long total = (long)a.psf_tiles * pp;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         const int t = (int)(e / pp);
         const int i = (int)(e - (long)t * pp);
@@ -147,9 +148,10 @@ __global__ void __launch_bounds__(256) zogy_combine_kernel(ZArgs a) {
         const int pq = ((T - ky) & (T - 1)) * T + ((T - kx) & (T - 1));
         if (pq >= q) {                                   // the pair (q, pq) is this thread's
             const long base = (long)t * T * T;
+            const long pbase = a.psf_tiles == 1 ? 0 : base;          // one shared PSF pair, or the tile's
             float2 Wq, Wp, PD;
             double p2;
-            zogy_pair(a.z1[base + q], a.z1[base + pq], a.z2[base + q], a.z2[base + pq], a.tiles[t], a.eps2, Wq, Wp,
+            zogy_pair(a.z1[base + q], a.z1[base + pq], a.z2[pbase + q], a.z2[pbase + pq], a.tiles[t], a.eps2, Wq, Wp,
                       PD, p2);
             a.z1[base + q] = Wq;
             if (pq != q) a.z1[base + pq] = Wp;
@@ -230,11 +232,12 @@ int run(argus_proper_plan* p, ZArgs& a, cudaStream_t s) {
     argus_count_launch(1);
     fft2d<T, -1, float>(p->z1, a.n_tiles, p->tw32, s);
     if (a.psf_n) {                 // new PSFs: place and transform them (else z2 holds the last ones)
-        if (cudaMemsetAsync(p->z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
-        const long pp = (long)a.n_tiles * a.ps * a.ps;
+        const long ptotal = (long)a.psf_tiles * T * T;
+        if (cudaMemsetAsync(p->z2, 0, (size_t)ptotal * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+        const long pp = (long)a.psf_tiles * a.ps * a.ps;
         zogy_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
         argus_count_launch(1);
-        fft2d<T, -1, double>(p->z2, a.n_tiles, p->tw64, s);
+        fft2d<T, -1, double>(p->z2, a.psf_tiles, p->tw64, s);
     }
     zogy_combine_kernel<T><<<grid, 256, 0, s>>>(a);
     argus_count_launch(1);
@@ -269,8 +272,9 @@ struct CArgs {
     const float* F;         // [n_frames]
     const float* sig;       // [n_frames]
     int n_frames;
-    const float* psfs;      // [n_tiles][n_frames][ps][ps]
+    const float* psfs;      // [psf_tiles][n_frames][ps][ps]
     int ps;
+    int psf_tiles;          // n_tiles, or 1 when every tile shares a frame's PSF
     int j0;                 // first frame of the pair in flight
     double eps2;
     float2* z1;
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(256) coadd_pack_kernel(CArgs a) {
 template <int T>
 __global__ void __launch_bounds__(256) coadd_psf_kernel(CArgs a) {
     const int pp = a.ps * a.ps, hh = a.ps / 2;
-    const long total = (long)a.n_tiles * pp;
+    const long total = (long)a.psf_tiles * pp;
     const bool two = a.j0 + 1 < a.n_frames;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         const int t = (int)(e / pp);
@@ -377,9 +381,10 @@ __global__ void __launch_bounds__(256) coadd_accum_kernel(CArgs a) {
         const int ky = q / T, kx = q - ky * T;
         const long base = (long)t * T * T;
         const long pe = base + ((T - ky) & (T - 1)) * T + ((T - kx) & (T - 1));
+        const long pb = a.psf_tiles == 1 ? base : 0;                 // shared PSFs live in tile 0
         float2 acc = a.acc[e];
         double2 acc2 = a.acc2[e];
-        coadd_accum_point(a.z1[e], a.z1[pe], a.z2[e], a.z2[pe], w0, w1, a0, a1, acc, acc2);
+        coadd_accum_point(a.z1[e], a.z1[pe], a.z2[e - pb], a.z2[pe - pb], w0, w1, a0, a1, acc, acc2);
         a.acc[e] = acc;
         a.acc2[e] = acc2;
     }
@@ -426,7 +431,7 @@ __global__ void coadd_norm_kernel(CArgs a) {
         float w;
         double aj;
         frame_weights(a.F, a.sig, a.n_frames, j, w, aj);
-        const float* pt = a.psfs + ((long)t * a.n_frames + j) * pp;
+        const float* pt = a.psfs + ((long)(a.psf_tiles == 1 ? 0 : t) * a.n_frames + j) * pp;
         double s2 = 0.0;
         for (int i = 0; i < pp; i++) s2 += (double)pt[i] * pt[i];
         v += aj * s2;
@@ -443,15 +448,16 @@ int run_coadd(argus_proper_plan* p, CArgs& a, cudaStream_t s) {
     const unsigned grid = (unsigned)(g > 152L * 16 ? 152L * 16 : g);
     if (cudaMemsetAsync(a.acc, 0, (size_t)total * sizeof(float2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
     if (cudaMemsetAsync(a.acc2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
-    const long pp = (long)a.n_tiles * a.ps * a.ps;
+    const long pp = (long)a.psf_tiles * a.ps * a.ps;
+    const long ptotal = (long)a.psf_tiles * T * T;
     for (int j0 = 0; j0 < a.n_frames; j0 += 2) {
         a.j0 = j0;
-        if (cudaMemsetAsync(a.z2, 0, (size_t)total * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
+        if (cudaMemsetAsync(a.z2, 0, (size_t)ptotal * sizeof(double2), s) != cudaSuccess) return ARGUS_ERR_CUDA;
         coadd_pack_kernel<T><<<grid, 256, 0, s>>>(a);
         coadd_psf_kernel<T><<<(unsigned)((pp + 255) / 256), 256, 0, s>>>(a);
         argus_count_launch(2);
         fft2d<T, -1, float>(a.z1, a.n_tiles, p->tw32, s);
-        fft2d<T, -1, double>(a.z2, a.n_tiles, p->tw64, s);
+        fft2d<T, -1, double>(a.z2, a.psf_tiles, p->tw64, s);
         coadd_accum_kernel<T><<<grid, 256, 0, s>>>(a);
         argus_count_launch(1);
     }
@@ -524,11 +530,12 @@ extern "C" int argus_proper_plan_destroy(argus_proper_plan* p) {
 
 extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* R, argus_shape shape,
                           const argus_zogy_tile* tiles, int n_tiles, const float* psf_n, const float* psf_r,
-                          int psf_size, float eps, float* D, float* S, float* P_D, double* sigma_S,
-                          argus_stream stream) {
+                          int psf_size, int psf_per_tile, float eps, float* D, float* S, float* P_D,
+                          double* sigma_S, argus_stream stream) {
     if (!plan || !N || !R || !tiles || !D || !S || n_tiles < 1 || n_tiles > plan->max_tiles) return ARGUS_ERR_ARG;
-    if (!psf_n != !psf_r) return ARGUS_ERR_ARG;
-    if (!psf_n && n_tiles > plan->psf_tiles) return ARGUS_ERR_ARG;     // nothing to reuse for these tiles
+    if (!psf_n != !psf_r || (psf_per_tile != 0 && psf_per_tile != 1)) return ARGUS_ERR_ARG;
+    // what the plan holds: psf_tiles > 0 tiles of their own, -1 one shared pair, 0 nothing
+    if (!psf_n && (psf_per_tile ? n_tiles > plan->psf_tiles : plan->psf_tiles != -1)) return ARGUS_ERR_ARG;
     if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
     int st = argus_check_shape(shape, (size_t)-1);
     if (st) return st;
@@ -536,6 +543,7 @@ extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* 
     ZArgs a;
     a.N = N; a.R = R; a.pitch = shape.pitch; a.w = shape.w; a.h = shape.h;
     a.tiles = tiles; a.n_tiles = n_tiles; a.psf_n = psf_n; a.psf_r = psf_r; a.ps = psf_size;
+    a.psf_tiles = psf_per_tile ? n_tiles : 1;
     a.eps2 = (double)eps * (double)eps;
     a.z1 = plan->z1; a.z2 = plan->z2; a.z3 = P_D ? plan->z3 : nullptr; a.psd = plan->psd;
     a.D = D; a.S = S; a.PD = P_D; a.sigma_S = sigma_S;
@@ -546,22 +554,25 @@ extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* 
         case 512: rc = run<512>(plan, a, s); break;
         default: rc = run<1024>(plan, a, s); break;
     }
-    if (psf_n) plan->psf_tiles = rc == ARGUS_OK ? n_tiles : 0;
+    if (psf_n) plan->psf_tiles = rc != ARGUS_OK ? 0 : (psf_per_tile ? n_tiles : -1);
     return rc;
 }
 
 extern "C" int argus_proper_coadd(argus_proper_plan* plan, const float* stack, int n_frames, argus_shape shape,
                                   const int* origins, int n_tiles, const float* F, const float* sigma,
-                                  const float* psfs, int psf_size, float eps, float* S, float* R, float* P_R,
+                                  const float* psfs, int psf_size, int psf_per_tile, float eps, float* S,
+                                  float* R, float* P_R,
                                   double* F_R, double* sigma_S, argus_stream stream) {
     if (!plan || !stack || !origins || !F || !sigma || !psfs || !S || !R || n_tiles < 1 ||
         n_tiles > plan->max_tiles || n_frames < 1 || n_frames > ARGUS_MAX_FRAMES)
         return ARGUS_ERR_ARG;
     if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
+    if (psf_per_tile != 0 && psf_per_tile != 1) return ARGUS_ERR_ARG;
     int st = argus_check_shape(shape, (size_t)-1);
     if (st) return st;
     if (cudaSetDevice(plan->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     CArgs a;
+    a.psf_tiles = psf_per_tile ? n_tiles : 1;
     a.stack = stack; a.frame_stride = (long)shape.h * shape.pitch; a.pitch = shape.pitch;
     a.w = shape.w; a.h = shape.h; a.origins = origins; a.n_tiles = n_tiles; a.F = F; a.sig = sigma;
     a.n_frames = n_frames; a.psfs = psfs; a.ps = psf_size; a.j0 = 0; a.eps2 = (double)eps * (double)eps;

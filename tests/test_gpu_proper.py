@@ -190,3 +190,46 @@ def test_zogy_reuses_psf_transforms_and_coadd_discards_them(ora):
             B.argus_zogy(plan, dN, dR, sh, d_rec, 2, None, None, 31, 1e-8, D2, S2)
     finally:
         B.proper_plan_destroy(plan)
+
+
+def test_shared_psfs_match_per_tile_copies(ora):
+    """One PSF (pair) shared by every tile gives, bit for bit, what the same PSF copied
+    into every tile gives, for ZOGY (also when reused) and for the proper coadd."""
+    T, w, h, nt = 256, 700, 500, 3
+    N, R = _frame(w, h, seed=6, sn=12.0, sr=3.0, psf_n=_gauss(1.8), psf_r=_gauss(1.3), Fn=1.0, Fr=1.0)
+    rec = np.zeros(nt, B.ZOGY_TILE_DTYPE)
+    for i, (x0, y0) in enumerate([(0, 0), (300, 100), (420, 240)]):
+        rec[i] = (x0, y0, 1.0, 1.0, 12.0, 3.0)
+    pn, pr = _gauss(1.8), _gauss(1.3)
+    pitch = pitch_for(w)
+    sh = B.argus_shape(w, h, pitch)
+    plan = B.proper_plan_create(0, T, nt)
+    try:
+        dN, dR = dev_pitched(N), dev_pitched(R)
+        d_rec = torch.from_numpy(rec.view(np.uint8).copy()).cuda()
+        out = [torch.empty((nt, T, T), device="cuda") for _ in range(6)]
+        B.argus_zogy(plan, dN, dR, sh, d_rec, nt, torch.from_numpy(np.stack([pn] * nt)).cuda(),
+                     torch.from_numpy(np.stack([pr] * nt)).cuda(), 31, 1e-8, out[0], out[1])
+        B.argus_zogy(plan, dN, dR, sh, d_rec, nt, torch.from_numpy(pn).cuda(), torch.from_numpy(pr).cuda(), 31, 1e-8,
+                     out[2], out[3], psf_per_tile=False)
+        B.argus_zogy(plan, dN, dR, sh, d_rec, nt, None, None, 31, 1e-8, out[4], out[5], psf_per_tile=False)
+        torch.cuda.synchronize()
+        for a, b in ((0, 2), (1, 3), (0, 4), (1, 5)):
+            assert torch.equal(out[a], out[b]), (a, b)
+        with pytest.raises(B.ArgusError):       # per-tile reuse after a shared call: nothing to reuse
+            B.argus_zogy(plan, dN, dR, sh, d_rec, nt, None, None, 31, 1e-8, out[4], out[5])
+        J = 3
+        stack = torch.stack([dN, dR, dN]).contiguous()
+        org = torch.tensor([(0, 0), (300, 100), (420, 240)], dtype=torch.int32, device="cuda")
+        F = torch.ones(J, device="cuda")
+        sg = torch.tensor([12.0, 3.0, 12.0], device="cuda")
+        ps = np.stack([_gauss(g) for g in (1.8, 1.3, 1.6)])
+        S1, R1, S2, R2 = (torch.empty((nt, T, T), device="cuda") for _ in range(4))
+        B.argus_proper_coadd(plan, stack, J, sh, org, nt, F, sg, torch.from_numpy(np.stack([ps] * nt)).cuda(), 31, 1e-8,
+                             S1, R1)
+        B.argus_proper_coadd(plan, stack, J, sh, org, nt, F, sg, torch.from_numpy(ps).cuda(), 31, 1e-8, S2, R2,
+                             psf_per_tile=False)
+        torch.cuda.synchronize()
+        assert torch.equal(S1, S2) and torch.equal(R1, R2)
+    finally:
+        B.proper_plan_destroy(plan)

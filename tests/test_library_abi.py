@@ -59,7 +59,7 @@ def test_host_argument_checks_need_no_gpu():
     plan = C.c_void_p()
     assert lib.argus_proper_plan_create(0, 300, 4, C.byref(plan)) == B.ARGUS_ERR_ARG      # tile not a power of two
     assert lib.argus_proper_plan_destroy(None) == B.ARGUS_ERR_ARG
-    assert lib.argus_zogy(None, None, None, sh, None, 1, None, None, 31, 1e-8, None, None, None, None,
+    assert lib.argus_zogy(None, None, None, sh, None, 1, None, None, 31, 1, 1e-8, None, None, None, None,
                           None) == B.ARGUS_ERR_ARG
     assert C.sizeof(C.c_int) * 2 + C.sizeof(C.c_float) * 4 == np_zogy_tile_itemsize()
 
@@ -74,7 +74,7 @@ def test_proper_coadd_argument_checks_need_no_gpu():
     from paper_2207_14304_gb300 import _binding as B
     lib = B.load()
     sh = B.argus_shape(64, 8, 64)
-    assert lib.argus_proper_coadd(None, None, 2, sh, None, 1, None, None, None, 31, 1e-8, None, None, None, None,
+    assert lib.argus_proper_coadd(None, None, 2, sh, None, 1, None, None, None, 31, 1, 1e-8, None, None, None, None,
                                   None, None) == B.ARGUS_ERR_ARG
 
 
