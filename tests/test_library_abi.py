@@ -85,3 +85,21 @@ def test_healpix_argument_checks_need_no_gpu():
     wcs = B.argus_wcs(0.0, 0.0, 1e-5, 0.0, 32.0, 4.0)
     assert lib.argus_healpix_resample(None, None, sh, wcs, 256, 9, None, 1, None, None, None) == B.ARGUS_ERR_ARG
     assert C.sizeof(B.argus_wcs) == 48
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every entry point the binding declares takes as many arguments as its prototype."""
+    from paper_2207_14304_gb300 import _binding as B
+    txt = ""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt += re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(argus_\w+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        protos[m.group(1)] = len(params)
+    checked = 0
+    for name, (args, _) in B.SIGNATURES.items():
+        if name in protos:
+            assert protos[name] == len(args), (name, protos[name], len(args))
+            checked += 1
+    assert checked >= 30
