@@ -383,7 +383,9 @@ int argus_fit_scale_background(argus_ctx *ctx, const float *sci, const float *sc
  * ARGUS_NOALLOC_MAX_CELLS (4096) returns ARGUS_ERR_CAPACITY.  Runs on the
  * current device.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race
+ * capture.  That address is kept until the process exits, so the entry point
+ * must not be called after a reset of the device (cudaDeviceReset or a torn-
+ * down primary context).  All calls share the array, so calls that overlap on the GPU race
  * and must be serialised by the caller; each call clears the part it uses.
  * ref, flags: device, [h][pitch]; centers: device int [grid_x*grid_y][2];
  * n_stamps: device int. */

@@ -1831,16 +1831,19 @@ extern "C" int argus_select_stamps(argus_ctx* ctx, const float* ref, const uint8
 // memory: code running where cudaMalloc is not allowed or not wanted (a host
 // that pre-reserves all GPU memory up front, a real-time loop that must never
 // enter the allocator, or a plugin handed only input and output pointers by
-// its host application).  It runs the same two kernels as
-// argus_select_stamps; their scratch -- one 64-bit key per grid cell -- lives
-// in the file-scope device array below instead of a context.
+// its host application).  It runs the per-pixel selection kernel (the same
+// rule as argus_select_stamps' tiled kernels) and the same compaction kernel;
+// their scratch -- one 64-bit key per grid cell -- lives in the file-scope
+// device array below instead of a context.
 //
 // The array is part of the library image: every GPU that loads the library
 // holds these 32 KiB until the process exits.  Host code cannot use the
 // symbol's name as a device address, so the address is looked up once per
 // device with cudaGetSymbolAddress, under a lock, with that device current.
 // That lookup happens on the first call on a device; make that first call
-// before any stream capture.  All calls share the array and it keeps the last
+// before any stream capture.  The address is then kept until the process
+// exits: after a device reset (cudaDeviceReset, or the primary context torn
+// down) it is stale, so do not call this entry point after one.  All calls share the array and it keeps the last
 // call's contents, so each call clears the keys it uses first; calls that
 // overlap on the GPU (different streams, or different host threads) race on
 // it and must be serialised by the caller.

@@ -528,6 +528,13 @@ extern "C" int argus_proper_plan_destroy(argus_proper_plan* p) {
     return ARGUS_OK;
 }
 
+// May a call without PSFs reuse the transforms a plan holds?  held: the plan's psf_tiles
+// (> 0 that many tiles' own pairs, -1 one shared pair, 0 none).  A per-tile call needs at
+// least n_tiles per-tile pairs; a shared call needs the shared pair.
+__host__ __device__ inline bool zogy_psf_reuse_ok(int held, int psf_per_tile, int n_tiles) {
+    return psf_per_tile ? (held >= 1 && n_tiles <= held) : held == -1;
+}
+
 extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* R, argus_shape shape,
                           const argus_zogy_tile* tiles, int n_tiles, const float* psf_n, const float* psf_r,
                           int psf_size, int psf_per_tile, float eps, float* D, float* S, float* P_D,
@@ -535,7 +542,7 @@ extern "C" int argus_zogy(argus_proper_plan* plan, const float* N, const float* 
     if (!plan || !N || !R || !tiles || !D || !S || n_tiles < 1 || n_tiles > plan->max_tiles) return ARGUS_ERR_ARG;
     if (!psf_n != !psf_r || (psf_per_tile != 0 && psf_per_tile != 1)) return ARGUS_ERR_ARG;
     // what the plan holds: psf_tiles > 0 tiles of their own, -1 one shared pair, 0 nothing
-    if (!psf_n && (psf_per_tile ? n_tiles > plan->psf_tiles : plan->psf_tiles != -1)) return ARGUS_ERR_ARG;
+    if (!psf_n && !zogy_psf_reuse_ok(plan->psf_tiles, psf_per_tile, n_tiles)) return ARGUS_ERR_ARG;
     if (psf_size < 1 || (psf_size & 1) == 0 || psf_size > 63 || !(eps >= 0.0f)) return ARGUS_ERR_ARG;
     int st = argus_check_shape(shape, (size_t)-1);
     if (st) return st;

@@ -74,6 +74,12 @@ void run(const char* dir) {
 }
 
 int main(int argc, char** argv) {
+    if (argc == 2 && !strcmp(argv[1], "reuse")) {       // the PSF-reuse argument check, one line per case
+        for (int held = -1; held <= 3; held++)
+            for (int per = 0; per <= 1; per++)
+                for (int n = 1; n <= 4; n++) printf("%d %d %d %d\n", held, per, n, (int)zogy_psf_reuse_ok(held, per, n));
+        return 0;
+    }
     const int T = atoi(argv[1]);
     if (T == 256) run<256>(argv[2]); else if (T == 512) run<512>(argv[2]); else run<1024>(argv[2]);
     return 0;

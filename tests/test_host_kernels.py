@@ -101,6 +101,20 @@ def test_zogy_step_matches_the_oracle(drivers, T, spec):
     assert abs(sig / o["sigma_S"] - 1) < 1e-6
 
 
+def test_zogy_psf_reuse_rule(drivers):
+    """A ZOGY call without PSFs reuses what the plan holds: per-tile pairs for at least as many
+    tiles (held >= n_tiles >= 1), or the one shared pair (held = -1).  A shared pair never serves
+    a per-tile call, and an empty plan (held = 0) serves nothing."""
+    out = subprocess.check_output([str(drivers / "host_zogy"), "reuse"]).decode().split("\n")
+    seen = 0
+    for line in filter(None, out):
+        held, per, n, ok = map(int, line.split())
+        want = (held >= n) if per else (held == -1)
+        assert ok == int(want), (held, per, n, ok)
+        seen += 1
+    assert seen == 5 * 2 * 4
+
+
 @pytest.mark.parametrize("T,J,eps_psf", [(256, 3, False), (256, 4, True), (512, 2, False)])
 def test_proper_coadd_step_matches_the_oracle(drivers, T, J, eps_psf):
     """R within 8 e_R, e_R = u log2(T^2) sum_j ||M_j||_2 / s_j / T (the quotient's gain is at
