@@ -5,7 +5,6 @@ the largest mesh value.
 
 The kernels have not run on a GPU yet, so the file is skipped until they have.
 """
-import os
 
 import numpy as np
 import pytest
@@ -15,9 +14,7 @@ from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300.synth import pitch_for
 from tests.gpu_helpers import F32_EPS, ctx_for, dev_pitched
 
-# skipped by default until the kernels have passed on a GPU; ARGUS_GPU_NEW=1 runs them
-pytestmark = [pytest.mark.gpu, pytest.mark.skipif(os.environ.get("ARGUS_GPU_NEW") != "1",
-                                                 reason="background kernels not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -7,7 +7,6 @@ the equatorial belt).
 The kernel has not run on a GPU yet, so the file is skipped until it has.
 """
 import math
-import os
 
 import numpy as np
 import pytest
@@ -17,9 +16,7 @@ from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300.synth import pitch_for
 from tests.gpu_helpers import F32_EPS, dev_pitched
 
-# skipped by default until the kernels have passed on a GPU; ARGUS_GPU_NEW=1 runs them
-pytestmark = [pytest.mark.gpu, pytest.mark.skipif(os.environ.get("ARGUS_GPU_NEW") != "1",
-                                                 reason="HEALPix kernel not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -14,7 +14,6 @@ tiles.  P_D within 64 u max|P_D|, sigma_S within 1e-6 relative.
 The kernels have not run on a GPU yet, so the file is skipped until they have.
 """
 import math
-import os
 
 import numpy as np
 import pytest
@@ -24,9 +23,7 @@ from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300.synth import pitch_for
 from tests.gpu_helpers import F32_EPS, dev_pitched
 
-# skipped by default until the kernels have passed on a GPU; ARGUS_GPU_NEW=1 runs them
-pytestmark = [pytest.mark.gpu, pytest.mark.skipif(os.environ.get("ARGUS_GPU_NEW") != "1",
-                                                 reason="proper-image kernels not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module", autouse=True)

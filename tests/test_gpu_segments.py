@@ -12,10 +12,8 @@ with the oracle's kernel) within the unit-test bars (1e-4 of max(|I|,
 detection is checked on the GPU's own atlas by properties that hold at any
 size (threshold mask, 8-connected components, peaks, sizes, order).  The
 batched subtraction alone, given the oracle's kernels, is compared at the
-unit-test bars (argus_segments_subtract; skipped unless ARGUS_GPU_NEW=1 until
-it has run on a GPU).
+unit-test bars (argus_segments_subtract).
 """
-import os
 
 import numpy as np
 import pytest
@@ -114,8 +112,6 @@ def test_segments_parity(ora, use_graph):
         batch.close()
 
 
-@pytest.mark.skipif(os.environ.get("ARGUS_GPU_NEW") != "1",
-                    reason="argus_segments_subtract not yet run on a GPU")
 def test_segments_subtract_with_the_oracles_kernels(ora):
     """The batched subtraction alone, given the oracle's kernels and backgrounds, against
     the oracle's difference and variance at the unit-test bars (1e-4 of max(|I|,
