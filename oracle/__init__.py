@@ -70,8 +70,8 @@ def _declare(l):
     l.ora_fit.argtypes = [I, I, P, P, P, P, P, I, I, I, I, P, P, I, I, P, P, P, P, P]
     l.ora_expand.argtypes = [I, I, P, P, I, I, P, P, P]
     l.ora_fit_rect.argtypes = [I, I, P, P, P, P, I, I, I, I, I, I, P, P, I, I, P, P, P, P, P]
-    l.ora_subtract.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, P, P]
-    l.ora_subtract_at.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, I, P, P, P]
+    l.ora_subtract.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, P, P]
+    l.ora_subtract_at.argtypes = [I, I, I, I, I, I, P, P, P, P, P, I, I, P, I, P, I, P, P, P]
     l.ora_detect.argtypes = [I, I, P, P, P, F, D, P, P, I]
     l.ora_coadd.argtypes = [I, I, I, P, P, I, P, P, P, D, D, I, D, I, P, P, P, P]
     l.ora_cnn_nparams.restype = L
@@ -247,8 +247,9 @@ def expand(b: Basis, coeffs):
 
 
 def subtract(sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=None, origin=(0, 0),
-             var_tile=128, with_var=True):
-    """Full-image D (and V_D).  K [Ks, ks, ks], bg [Kb]; frame = (W, H) for spatial terms."""
+             with_var=True):
+    """Full-image D (and V_D = V_I + sum K_xy^2 V_ref with the kernel K_xy at each pixel).
+    K [Ks, ks, ks], bg [Kb]; frame = (W, H) for spatial terms."""
     sci = _c(sci, np.float32); sv = _c(sci_var, np.float32); R = _c(ref, np.float32)
     Rv = _c(ref_var, np.float32); fl = _c(flags, np.uint8)
     K = _c(K, np.float64); bg = _c(np.atleast_1d(bg), np.float64)
@@ -256,12 +257,12 @@ def subtract(sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=Non
     W, H = frame if frame is not None else (w, h)
     Dd = np.empty((h, w)); Vd = np.empty((h, w)) if with_var else None
     lib().ora_subtract(w, h, W, H, origin[0], origin[1], _p(sci), _p(sv), _p(R), _p(Rv), _p(fl),
-                       K.shape[-1], sdeg, _p(K), bgdeg, _p(bg), var_tile, _p(Dd), _p(Vd))
+                       K.shape[-1], sdeg, _p(K), bgdeg, _p(bg), _p(Dd), _p(Vd))
     return Dd, Vd
 
 
 def subtract_at(xy, sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, frame=None,
-                origin=(0, 0), var_tile=128):
+                origin=(0, 0)):
     sci = _c(sci, np.float32); sv = _c(sci_var, np.float32); R = _c(ref, np.float32)
     Rv = _c(ref_var, np.float32); fl = _c(flags, np.uint8)
     K = _c(K, np.float64); bg = _c(np.atleast_1d(bg), np.float64); xy = _c(xy, np.int32)
@@ -270,7 +271,7 @@ def subtract_at(xy, sci, sci_var, ref, ref_var, flags, K, bg, *, sdeg, bgdeg, fr
     n = xy.shape[0]
     Dd = np.empty(n); Vd = np.empty(n)
     lib().ora_subtract_at(w, h, W, H, origin[0], origin[1], _p(sci), _p(sv), _p(R), _p(Rv),
-                          _p(fl), K.shape[-1], sdeg, _p(K), bgdeg, _p(bg), var_tile, n, _p(xy),
+                          _p(fl), K.shape[-1], sdeg, _p(K), bgdeg, _p(bg), n, _p(xy),
                           _p(Dd), _p(Vd))
     return Dd, Vd
 

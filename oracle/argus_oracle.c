@@ -505,22 +505,22 @@ void ora_expand(int ks, int ngauss, const double *sigma, const int *degree, int 
 /* the Alard-Lupton reading) and difference variance (noise maps, Sec. 3.2). */
 /*   D(x,y)  = I - sum_k p_k(x,y) sum_{u,v} K_k(u,v) R(x-u,y-v) - B(x,y)     */
 /*   B(x,y)  = sum_k bg_k p_k(x,y)                                           */
-/*   V_D     = V_I + sum_{u,v} Kc(u,v)^2 V_ref(x-u,y-v)                       */
-/*   Kc      = sum_k p_k(xc,yc) K_k, (xc,yc) the centre of the vt x vt tile   */
-/*             holding (x,y): xc = floor(x/vt)*vt + (vt-1)/2.                 */
+/*   V_D     = V_I + sum_{u,v} K_xy(u,v)^2 V_ref(x-u,y-v)                     */
+/*   K_xy    = sum_k p_k(x,y) K_k, the kernel at the pixel itself: the        */
+/*             variance of D for independent noise in I and R.               */
 /* Pixels within r of an edge, or with flags != 0, get D = V_D = 0.          */
 /* Spatial terms use the frame size (W,H) and frame coordinates x+ox, y+oy.  */
 /* ------------------------------------------------------------------------ */
 static void subtract_px(int w, int h, int W, int H, int ox, int oy, const float *sci,
                         const float *sci_var, const float *R, const float *Rv,
                         const uint8_t *flags, int ks, int sdeg, const double *K, int bgdeg,
-                        const double *bg, int vt, int x, int y, double *Dp, double *Vp) {
+                        const double *bg, int x, int y, double *Dp, double *Vp) {
     int r = (ks - 1) / 2, kk = ks * ks, Ks = ora_nterms(sdeg), Kb = ora_nterms(bgdeg);
     long p = (long)y * w + x;
     if (x < r || y < r || x > w - 1 - r || y > h - 1 - r || (flags && flags[p])) {
         *Dp = 0.0; if (Vp) *Vp = 0.0; return;
     }
-    double pk[64], pb[64], pc[64];
+    double pk[64], pb[64];
     ora_spatial_terms(x + ox, y + oy, W, H, sdeg, pk);
     ora_spatial_terms(x + ox, y + oy, W, H, bgdeg, pb);
     double conv = 0.0;
@@ -536,15 +536,12 @@ static void subtract_px(int w, int h, int W, int H, int ox, int oy, const float 
     for (int k = 0; k < Kb; k++) bgv += bg[k] * pb[k];
     *Dp = (double)sci[p] - conv - bgv;
     if (Vp) {
-        double xc = (double)((x + ox) / vt) * vt + (vt - 1) / 2.0;
-        double yc = (double)((y + oy) / vt) * vt + (vt - 1) / 2.0;
-        ora_spatial_terms(xc, yc, W, H, sdeg, pc);
         double vs = 0.0;
         for (int v = -r; v <= r; v++)
             for (int u = -r; u <= r; u++) {
-                double kc = 0.0;
-                for (int k = 0; k < Ks; k++) kc += pc[k] * K[(long)k * kk + (v + r) * ks + (u + r)];
-                vs += kc * kc * (double)Rv[(long)(y - v) * w + (x - u)];
+                double kxy = 0.0;
+                for (int k = 0; k < Ks; k++) kxy += pk[k] * K[(long)k * kk + (v + r) * ks + (u + r)];
+                vs += kxy * kxy * (double)Rv[(long)(y - v) * w + (x - u)];
             }
         *Vp = (double)sci_var[p] + vs;
     }
@@ -552,13 +549,13 @@ static void subtract_px(int w, int h, int W, int H, int ox, int oy, const float 
 
 void ora_subtract(int w, int h, int W, int H, int ox, int oy, const float *sci,
                   const float *sci_var, const float *R, const float *Rv, const uint8_t *flags,
-                  int ks, int sdeg, const double *K, int bgdeg, const double *bg, int vt,
+                  int ks, int sdeg, const double *K, int bgdeg, const double *bg,
                   double *D, double *VD) {
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             long p = (long)y * w + x;
-            subtract_px(w, h, W, H, ox, oy, sci, sci_var, R, Rv, flags, ks, sdeg, K, bgdeg, bg, vt,
+            subtract_px(w, h, W, H, ox, oy, sci, sci_var, R, Rv, flags, ks, sdeg, K, bgdeg, bg,
                         x, y, D + p, VD ? VD + p : NULL);
         }
 }
@@ -566,11 +563,11 @@ void ora_subtract(int w, int h, int W, int H, int ox, int oy, const float *sci,
 /* The same definition evaluated at n listed pixels xy[2i], xy[2i+1]. */
 void ora_subtract_at(int w, int h, int W, int H, int ox, int oy, const float *sci,
                      const float *sci_var, const float *R, const float *Rv, const uint8_t *flags,
-                     int ks, int sdeg, const double *K, int bgdeg, const double *bg, int vt,
+                     int ks, int sdeg, const double *K, int bgdeg, const double *bg,
                      int n, const int *xy, double *D, double *VD) {
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; i++)
-        subtract_px(w, h, W, H, ox, oy, sci, sci_var, R, Rv, flags, ks, sdeg, K, bgdeg, bg, vt,
+        subtract_px(w, h, W, H, ox, oy, sci, sci_var, R, Rv, flags, ks, sdeg, K, bgdeg, bg,
                     xy[2 * i], xy[2 * i + 1], D + i, VD ? VD + i : NULL);
 }
 

@@ -14,7 +14,8 @@ import torch
 from paper_2207_14304_gb300 import _binding as B
 from paper_2207_14304_gb300 import synth
 from paper_2207_14304_gb300.synth import pitch_for
-from tests.gpu_helpers import F32_EPS, assert_rel, ctx_for, dev_pitched, host
+from tests.gpu_helpers import (F32_EPS, VD_RTOL, assert_rel, assert_variance, ctx_for, dev_pitched, host,
+                               psf_matching_field, tile_rule_allowance)
 
 pytestmark = pytest.mark.gpu
 
@@ -115,9 +116,52 @@ def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
         scale = np.maximum(np.maximum(np.abs(I), -Cabs), 1.0)
         e = assert_rel(Dg, Do, scale, 1e-4, "D")
         assert e < 1e-5, e       # FP32 accumulation is far inside the 1e-4 bound
-        assert_rel(Vg, Vo, np.maximum(Vo, 1e-6), 1e-5, "V_D")
+        # V_D against the exact per-pixel definition: FP32 arithmetic plus the tile rule's
+        # allowance (these kernels change by O(1) across a frame of a few hundred pixels, far
+        # faster than a PSF field, so the allowance is what carries the comparison here)
+        xy = np.stack(np.meshgrid(np.arange(w), np.arange(h)), -1).reshape(-1, 2)
+        assert_variance(Vg[xy[:, 1], xy[:, 0]], Vo[xy[:, 1], xy[:, 0]],
+                        tile_rule_allowance(K, sdeg, Vr, xy, (w, h)))
         if pitch > w:
             assert (D[:, w:] == -9.0).all()
+    finally:
+        B.argus_destroy(ctx)
+
+
+@pytest.mark.parametrize("ox,oy", [(0, 0), (8832, 5760), (4000, 3010)])
+def test_subtract_variance_on_a_psf_matching_field(ora, ox, oy):
+    """Rectangles of a 9576x6388 frame with the kernel field of a PSF that widens from 1.3 to
+    2.2 px towards the corners and a 30-frame-deep reference (V_ref = V_I / 30): the GPU's
+    V_D within 1e-3 of the exact per-pixel definition (the bar set by the detection margin),
+    and within FP32 arithmetic plus the tile rule's allowance pixel by pixel.  (0, 0) and
+    (8832, 5760) are on the 128 grid (tensor-core variance), (4000, 3010) is not (FP32)."""
+    ks, sdeg, W, H, w, h = 21, 2, 9576, 6388, 600, 500
+    rng = np.random.default_rng(ox + oy)
+    K = psf_matching_field(ks, W, H)
+    R = rng.normal(300, 3, (h, w)).astype(np.float32)
+    I = rng.normal(305, 17, (h, w)).astype(np.float32)
+    Vi = rng.uniform(250, 400, (h, w)).astype(np.float32)
+    Vr = (Vi / 30 * rng.uniform(0.8, 1.2, (h, w))).astype(np.float32)
+    fl = (rng.random((h, w)) < 0.001).astype(np.uint8)
+    pitch = pitch_for(w)
+    ctx = ctx_for(w, h)
+    try:
+        dI, dVi, dR, dVr, dfl = (dev_pitched(a) for a in (I, Vi, R, Vr, fl))
+        dK = torch.from_numpy(K.astype(np.float32).reshape(-1)).cuda()
+        dbg = torch.zeros(1, dtype=torch.float64, device="cuda")
+        D = torch.full((h, pitch), -9.0, device="cuda")
+        VD = torch.full((h, pitch), -9.0, device="cuda")
+        B.argus_subtract(ctx, dI, dVi, dR, dVr, dfl, B.argus_shape(w, h, pitch), W, H, ox, oy, ks, sdeg, dK,
+                         0, dbg, D, VD)
+        torch.cuda.synchronize()
+        Vg = host(VD, w)
+        xy = np.stack([rng.integers(0, w, 20000), rng.integers(0, h, 20000)], 1).astype(np.int32)
+        _, Vo = ora.subtract_at(xy, I, Vi, R, Vr, fl, K.astype(np.float32).astype(np.float64), [0.0], sdeg=sdeg,
+                                bgdeg=0, frame=(W, H), origin=(ox, oy))
+        Vs = Vg[xy[:, 1], xy[:, 0]]
+        e = assert_variance(Vs, Vo, tile_rule_allowance(K.astype(np.float32), sdeg, Vr, xy, (W, H), (ox, oy)))
+        print(f"\n[V_D on a PSF field at ({ox}, {oy})] worst |dV| / V_D {e:.2e}")
+        assert e <= VD_RTOL
     finally:
         B.argus_destroy(ctx)
 
@@ -147,7 +191,9 @@ def test_subtract_sub_rectangle_of_a_frame(ora, ox, oy):
         Dg, Vg = host(D, w), host(VD, w)
         scale = np.maximum(np.maximum(np.abs(I), -Cabs), 1.0)
         assert assert_rel(Dg, Do, scale, 1e-4, "D") < 1e-5
-        assert_rel(Vg, Vo, np.maximum(Vo, 1e-6), 1e-5, "V_D")
+        xy = np.stack(np.meshgrid(np.arange(w), np.arange(h)), -1).reshape(-1, 2)
+        assert_variance(Vg[xy[:, 1], xy[:, 0]], Vo[xy[:, 1], xy[:, 0]],
+                        tile_rule_allowance(K, sdeg, Vr, xy, (W, H), (ox, oy)))
     finally:
         B.argus_destroy(ctx)
 

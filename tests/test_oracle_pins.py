@@ -367,32 +367,67 @@ def test_difference_variance_matches_empirical_noise(ora):
     assert abs(inner.var() / Vd[5:-5, 5:-5].mean() - 1) < 0.01
 
 
-def test_difference_variance_tile_centre_kernel(ora):
-    """Spatially varying kernel: V_D in each 128x128 tile is V_I plus V_ref convolved with the
-    square of the kernel taken at the tile centre (c = 128 t + 63.5), checked per quadrant against
-    the library convolution; var_tile = 1 is the per-pixel kernel."""
-    w = h = 256
+def test_difference_variance_two_tap_kernel_closed_form(ora):
+    """A kernel with two taps per spatial term, K_k = c_k at (0, 0) and d_k at (1, 0), varying
+    with degree 2: at every pixel V_D = V_I + V_ref(x, y) c(x, y)^2 + V_ref(x - 1, y) d(x, y)^2,
+    c(x, y) = sum_k c_k p_k(x, y) written out term by term (1, y, y^2, x, x y, x^2)."""
+    w, h, ks = 50, 40, 3
     rng = np.random.default_rng(9)
-    K = rng.normal(size=(6, 5, 5)) * np.array([1.0, 0.3, 0.2, 0.3, 0.1, 0.2])[:, None, None]
+    c = np.array([1.0, 0.4, -0.3, 0.5, 0.2, -0.6])
+    d = np.array([0.3, -0.2, 0.1, 0.25, -0.15, 0.05])
+    K = np.zeros((6, ks, ks))
+    K[:, 1, 1] = c            # tap (u, v) = (0, 0)
+    K[:, 1, 2] = d            # tap (u, v) = (1, 0): multiplies R(x - 1, y)
     Vi = rng.uniform(1, 5, size=(h, w)).astype(np.float32)
     Vr = rng.uniform(0, 3, size=(h, w)).astype(np.float32)
     z = np.zeros((h, w), np.float32)
     _, Vd = ora.subtract(z, Vi, z, Vr, np.zeros((h, w), np.uint8), K, [0.0], sdeg=2, bgdeg=0)
+    for y in range(1, h - 1):
+        for x in range(1, w - 1):
+            X, Y = (2 * x - (w - 1)) / (w - 1), (2 * y - (h - 1)) / (h - 1)
+            cxy = c[0] + c[1] * Y + c[2] * Y * Y + c[3] * X + c[4] * X * Y + c[5] * X * X
+            dxy = d[0] + d[1] * Y + d[2] * Y * Y + d[3] * X + d[4] * X * Y + d[5] * X * X
+            want = float(Vi[y, x]) + float(Vr[y, x]) * cxy ** 2 + float(Vr[y, x - 1]) * dxy ** 2
+            assert abs(Vd[y, x] - want) <= 1e-12 * want, (x, y)
 
-    def kc(xc, yc):
-        xt, yt = (2 * xc - (w - 1)) / (w - 1), (2 * yc - (h - 1)) / (h - 1)
-        pk = [xt ** i * yt ** j for i in range(3) for j in range(3 - i)]
-        return sum(pk[k] * K[k] for k in range(6))
-    for ty in range(2):
-        for tx in range(2):
-            want = Vi.astype(np.float64) + _conv(Vr.astype(np.float64), kc(128 * tx + 63.5, 128 * ty + 63.5) ** 2)
-            ys, xs = slice(max(2, 128 * ty), min(h - 2, 128 * ty + 128)), slice(max(2, 128 * tx), min(w - 2, 128 * tx + 128))
-            np.testing.assert_allclose(Vd[ys, xs], want[ys, xs], rtol=1e-11)
-    xy = np.array([[40, 200], [130, 10]], np.int32)
-    _, V1 = ora.subtract_at(xy, z, Vi, z, Vr, np.zeros((h, w), np.uint8), K, [0.0], sdeg=2, bgdeg=0, var_tile=1)
-    for (x, y), v in zip(xy, V1):
-        want = float(Vi[y, x]) + float((_conv(Vr.astype(np.float64), kc(float(x), float(y)) ** 2))[y, x])
-        assert abs(v - want) < 1e-9 * want
+
+def test_difference_variance_per_pixel_matches_monte_carlo(ora):
+    """V_D is the variance of D: for independent Gaussian noise in I and R (variance maps V_I,
+    V_ref), the empirical variance of D over 3000 draws matches V_D pixel by pixel, with a
+    degree-2 kernel whose sum K_xy^2 changes several-fold across the frame (a kernel taken at
+    one point, or constant over large tiles, fails this)."""
+    w = h = 40
+    ks, r = 5, 2
+    rng = np.random.default_rng(19)
+    u = np.arange(-r, r + 1)
+    G = np.exp(-(u[None, :] ** 2 + u[:, None] ** 2) / (2 * 0.9 ** 2))
+    K = np.zeros((6, ks, ks))
+    K[0] = G / G.sum()
+    K[3] = 0.6 * K[0]                                       # x: the kernel's scale grows along x
+    K[1] = 0.3 * np.roll(K[0], 1, axis=1)                   # y: a shifted component
+    K[5] = 0.2 * K[0]
+    Vi = rng.uniform(2, 6, size=(h, w)).astype(np.float32)
+    Vr = rng.uniform(1, 4, size=(h, w)).astype(np.float32)
+    fl = np.zeros((h, w), np.uint8)
+    _, Vd = ora.subtract(np.zeros((h, w), np.float32), Vi, np.zeros((h, w), np.float32), Vr, fl, K, [0.0],
+                         sdeg=2, bgdeg=0)
+    n = 3000
+    s2 = np.zeros((h, w))
+    sdi, sdr = np.sqrt(Vi.astype(np.float64)), np.sqrt(Vr.astype(np.float64))
+    for _ in range(n):
+        I = (rng.normal(size=(h, w)) * sdi).astype(np.float32)
+        R = (rng.normal(size=(h, w)) * sdr).astype(np.float32)
+        D, _ = ora.subtract(I, Vi, R, Vr, fl, K, [0.0], sdeg=2, bgdeg=0, with_var=False)
+        s2 += D * D
+    inner = (slice(r, h - r), slice(r, w - r))
+    ratio = (s2 / n)[inner] / Vd[inner]
+    term = (Vd - Vi)[inner]
+    assert term.max() / term.min() > 3                     # the convolved-reference term varies
+    # one pixel: relative std sqrt(2/n) = 2.6 %; 4.5 sigma over 1296 pixels
+    assert np.abs(ratio - 1).max() < 4.5 * math.sqrt(2 / n), np.abs(ratio - 1).max()
+    # 6x6 blocks of pixels: the mean ratio of each within 1.5 %
+    blocks = ratio[:36, :36].reshape(6, 6, 6, 6).mean(axis=(1, 3))
+    assert np.abs(blocks - 1).max() < 0.015, np.abs(blocks - 1).max()
 
 
 # --------------------------------------------------------------------------- detect

@@ -24,7 +24,7 @@ import pytest
 import torch
 
 from paper_2207_14304_gb300 import _binding as B
-from tests.gpu_helpers import F32_EPS, assert_rel, check_detection_properties
+from tests.gpu_helpers import F32_EPS, VD_RTOL, assert_rel, assert_variance, check_detection_properties, tile_rule_allowance
 
 pytestmark = pytest.mark.gpu
 
@@ -140,7 +140,11 @@ def test_full_frame_path_against_the_oracle(ora):
         np.testing.assert_array_equal(Vg[zero], 0.0)
         scale = np.maximum(np.maximum(np.abs(I32[xy[:, 1], xy[:, 0]]), -Cn), 1.0)
         assert assert_rel(Dg, Do, scale, 1e-4, "D") < 1e-5
-        assert_rel(Vg, Vo, np.maximum(Vo, 1e-6), 1e-5, "V_D")
+        # V_D: the exact per-pixel definition, within FP32 arithmetic plus the tile rule's
+        # allowance at every sampled pixel, and within the detection-margin bar overall
+        ev = assert_variance(Vg, Vo, tile_rule_allowance(K32, sdeg, Vr, xy, (W, H)))
+        print(f"[full frame] V_D worst |dV| / V_D {ev:.2e}")
+        assert ev <= VD_RTOL
         del D2, VD2
 
         # --- detection on the pipeline's own difference image
