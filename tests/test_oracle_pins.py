@@ -210,6 +210,95 @@ def test_fit_normal_equations_brute_force_toy(ora):
     assert res.dof == 25 - 4
 
 
+def test_fit_rect_normal_equations_brute_force_toy(ora):
+    """Whole-rectangle fit (the segment fit), 3 basis functions on a 5x5 kernel: M, b and dof
+    equal C^T W C, C^T W I and n - N_c with C built from scipy convolutions over every pixel of
+    the inclusive rectangle [6, 12] x [4, 9], one flagged pixel and one of zero variance left out."""
+    w, h = 20, 16
+    b = ora.Basis(ksize=5, sigmas=(1.0,), degrees=(1,))
+    B, _ = ora.basis(b)
+    rng = np.random.default_rng(14)
+    R = rng.uniform(100, 200, size=(h, w)).astype(np.float32)
+    I = rng.uniform(100, 200, size=(h, w)).astype(np.float32)
+    V = rng.uniform(1, 4, size=(h, w)).astype(np.float32)
+    fl = np.zeros((h, w), np.uint8)
+    fl[5, 8] = 1
+    V[7, 11] = 0.0
+    res = ora.fit_rect(I, V, R, fl, (6, 4, 12, 9), b)
+    assert res.status == 0
+    Xs = [_conv(R.astype(np.float64), B[n]) for n in range(3)]
+    C, W, T = [], [], []
+    for y in range(4, 10):
+        for x in range(6, 13):
+            if (y, x) in ((5, 8), (7, 11)):
+                continue
+            C.append([Xs[0][y, x], Xs[1][y, x], Xs[2][y, x], 1.0])
+            W.append(1.0 / float(V[y, x])); T.append(float(I[y, x]))
+    C, W, T = np.array(C), np.array(W), np.array(T, np.float64)
+    assert len(C) == 7 * 6 - 2
+    np.testing.assert_allclose(res.M, C.T @ (W[:, None] * C), rtol=1e-12)
+    np.testing.assert_allclose(res.b, C.T @ (W * T), rtol=1e-12)
+    assert res.dof == len(C) - 4
+    a = np.linalg.solve(C.T @ (W[:, None] * C), C.T @ (W * T))
+    np.testing.assert_allclose(res.coeffs, a, rtol=1e-9, atol=1e-12)
+    assert abs(res.chi2 - float((W * (T - C @ a) ** 2).sum())) <= 1e-9 * res.chi2
+
+
+def test_fit_rect_recovers_in_span_kernel(ora):
+    """I = R (x) K + bg over a 90x70 image with K in the 49-function span (15x15): the fit over
+    the interior rectangle recovers the coefficients to 1e-9 (float32-exact integer images,
+    so the only error is FP64 round-off) and chi^2 is ~0."""
+    w, h, ks = 90, 70, 15
+    b = ora.Basis(ksize=ks)
+    B, _ = ora.basis(b)
+    rng = np.random.default_rng(3)
+    R = rng.integers(0, 64, size=(h, w)).astype(np.float64)
+    a = np.zeros(b.ncoeffs)
+    a[0] = 1.0
+    a[1:49] = rng.normal(0, 0.05, 48)
+    a[49] = 4.0
+    K = np.tensordot(a[:49], B, 1)
+    I = _conv(R, K) + a[49]
+    r = ks // 2
+    # float32 images at the boundary: fit the float32-rounded I, compare with FP64 least squares
+    I32 = I.astype(np.float32)
+    res = ora.fit_rect(I32, np.ones_like(I32), R.astype(np.float32), np.zeros((h, w), np.uint8),
+                       (r, r, w - 1 - r, h - 1 - r), b)
+    assert res.status == 0
+    ys, xs = np.mgrid[r:h - r, r:w - r]
+    Xs = np.stack([_conv(R, B[n])[r:h - r, r:w - r].ravel() for n in range(49)] + [np.ones(xs.size)], 1)
+    sol = np.linalg.lstsq(Xs, I32[r:h - r, r:w - r].astype(np.float64).ravel(), rcond=None)[0]
+    np.testing.assert_allclose(res.coeffs, sol, rtol=0, atol=1e-9 * np.abs(sol).max())
+    np.testing.assert_allclose(res.coeffs, a, rtol=0, atol=1e-5)   # float32 rounding of I only
+    Kfit, bg = ora.expand(b, res.coeffs)
+    assert np.abs(Kfit[0] - K).max() < 1e-5 * np.abs(K).max()
+
+
+def test_fit_rect_touching_the_margin_skips_edge_pixels(ora):
+    """A rectangle that reaches the image edge: pixels within r of the edge (whose convolution
+    window leaves the image) are skipped, so the fit over [0, w-1] x [0, h-1] equals the fit
+    over the interior [r, w-1-r] x [r, h-1-r] exactly, and dof counts the interior only."""
+    w, h, ks = 40, 30, 7
+    b = ora.Basis(ksize=ks, sigmas=(0.8, 1.6), degrees=(2, 1))
+    rng = np.random.default_rng(21)
+    R = rng.uniform(50, 150, size=(h, w)).astype(np.float32)
+    I = rng.uniform(50, 150, size=(h, w)).astype(np.float32)
+    V = rng.uniform(1, 3, size=(h, w)).astype(np.float32)
+    fl = np.zeros((h, w), np.uint8)
+    r = ks // 2
+    full = ora.fit_rect(I, V, R, fl, (0, 0, w - 1, h - 1), b)
+    inner = ora.fit_rect(I, V, R, fl, (r, r, w - 1 - r, h - 1 - r), b)
+    np.testing.assert_array_equal(full.M, inner.M)
+    np.testing.assert_array_equal(full.b, inner.b)
+    np.testing.assert_array_equal(full.coeffs, inner.coeffs)
+    assert full.dof == inner.dof == (w - 2 * r) * (h - 2 * r) - b.ncoeffs
+    # one pixel in from the margin on the left only: exactly one more column of pixels
+    wider = ora.fit_rect(I, V, R, fl, (r - 1, r, w - 1 - r, h - 1 - r), b)
+    assert wider.dof == inner.dof
+    narrower = ora.fit_rect(I, V, R, fl, (r + 1, r, w - 1 - r, h - 1 - r), b)
+    assert narrower.dof == inner.dof - (h - 2 * r)
+
+
 def test_fit_spatially_varying_kernel_and_background(ora):
     w, h = 160, 128
     b = ora.Basis(ksize=9, sigmas=(0.8, 1.8), degrees=(2, 1), spatial_degree=2, bg_degree=1)
