@@ -47,7 +47,12 @@ enum {
     ARGUS_ERR_UNSUPPORTED = -8 /* size outside the compiled kernel set */
 };
 
-enum { ARGUS_PREC_FP32 = 0, ARGUS_PREC_TF32 = 1, ARGUS_PREC_BF16 = 2 };
+/* Operand precision of the normal-equation Gram: FP32 (FP32 pipes), TF32 or
+ * BF16 (operands rounded, tensor cores), BF16X3 (each operand split into BF16
+ * hi + lo, products hi*hi + hi*lo + lo*hi on the tensor cores); every
+ * tensor-core product accumulates in FP32 over at most 256 design rows, folded
+ * into double-float sums. */
+enum { ARGUS_PREC_FP32 = 0, ARGUS_PREC_TF32 = 1, ARGUS_PREC_BF16 = 2, ARGUS_PREC_BF16X3 = 3 };
 enum { ARGUS_FLAG_BAD = 1, ARGUS_FLAG_SAT = 2 };
 enum { ARGUS_MASK_POS = 1, ARGUS_MASK_NEG = 2, ARGUS_MASK_INVALID = 4 };
 
@@ -172,8 +177,8 @@ int argus_select_stamps(argus_ctx *ctx, const float *ref, const uint8_t *flags, 
  * centers[s], s < *n_stamps, at most max_stamps):
  *   row c = [X_0, p_k X_n (n>=1), p_k (background)], X_n = (ref (x) B_n)(x,y),
  *   weight w = 1/sci_var if flags == 0 and sci_var > 0, else 0;
- * M = C^T W C (operands rounded to `precision`, FP32 accumulation on the tensor
- * cores for TF32/BF16), FP64 Cholesky on the GPU, a0 = M^-1 b, then one
+ * M = C^T W C (operands in `precision`, ARGUS_PREC_*; FP32 accumulation over at
+ * most 256 rows on the tensor cores), FP64 Cholesky on the GPU, a0 = M^-1 b, then one
  * refinement a = a0 + M^-1 C^T W (I - C a0) with C in FP32 and FP64 sums.
  * Stamps whose window leaves the frame are skipped.  coeffs: double [Nc]
  * (device); stats: argus_fit_stats (device).  A singular M latches

@@ -27,7 +27,7 @@ ARGUS_ERR_UNSUPPORTED = -8
 ARGUS_FLAG_BAD, ARGUS_FLAG_SAT = 1, 2
 ARGUS_MASK_POS, ARGUS_MASK_NEG, ARGUS_MASK_INVALID = 1, 2, 4
 
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
 FLAG_BAD, FLAG_SAT = 1, 2
 MASK_POS, MASK_NEG, MASK_INVALID = 1, 2, 4
 

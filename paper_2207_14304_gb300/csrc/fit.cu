@@ -576,13 +576,18 @@ __global__ void __launch_bounds__(256, 3) gram_cp_kernel(GramArgs g, const float
 }
 
 // ---------------------------------------------------------------------------
-// K4 (TF32 / BF16): tcgen05 Gram.  CTA (slot, rb) accumulates rows
-// [128 rb, 128 rb + 128) x all NP columns of the augmented Gram in TMEM over
-// its K-chunks of 32 design rows.  The design tile of a stage is written once
-// in the K-major no-swizzle canonical layout and serves as B (all columns)
-// and, offset by 16 core-matrix groups per row block, as A.
-constexpr int TC_KC = 32;
-constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // ~2 s of SM clock
+// K4 on the tensor cores (TF32, BF16, or BF16 with a hi/lo split).
+//
+// The weighted design matrix is written once per fit as tiles of 32 rows that
+// are already in the MMA's no-swizzle K-major operand layout: for chunk ch,
+// element (row r of the chunk, column j) sits at
+//   ch * CH_BYTES + part * TILE_BYTES + (j / 8) * SBO + (r / E) * 128 + (j % 8) * 16 + (r % E) * ESZ,
+// E = elements per 16-byte core-matrix row (8 BF16 or 4 TF32), SBO = (32 / E) * 128,
+// part 0 = the value rounded to the format (hi), part 1 = the rounded remainder
+// (lo, BF16 split only).  A column range of 8 g .. 8 g + 8 n - 1 of a chunk is then
+// n * SBO contiguous bytes, so a block's operands are single bulk copies.
+constexpr int TC_KC = 32;                              // design rows per chunk (pipeline stage)
+constexpr long long TC_WAIT_LIMIT = 4000000000LL;      // ~2 s of SM clock
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -595,133 +600,293 @@ __device__ __forceinline__ uint32_t to_tf32(float a) {
     return r;
 }
 
-template <int FMT>
-__global__ void __launch_bounds__(256, 1) gram_tc_kernel(GramArgs g, const float* C, int NR) {
-    constexpr int ESZ = FMT == 1 ? 2 : 4;          // bytes per element
-    constexpr int E = 16 / ESZ;                    // elements per 16-byte core-matrix row
-    constexpr int KQ = TC_KC / E;                  // core matrices along K per stage
-    constexpr uint32_t LBO = 128;
-    constexpr uint32_t SBO = KQ * 128;
-    constexpr int KMMA = FMT == 1 ? 16 : 8;        // K per instruction
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    const uint32_t stage_bytes = (uint32_t)NR * TC_KC * ESZ;
-    uint8_t* stage0 = smem_raw;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * stage_bytes);       // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
-    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+// FMT 1 = BF16, 2 = TF32; P = 1 (rounded operand) or 3 (BF16 hi/lo: hi*hi + hi*lo + lo*hi)
+template <int FMT, int P>
+struct TcGram {
+    static constexpr int ESZ = FMT == 1 ? 2 : 4;
+    static constexpr int E = 16 / ESZ;
+    static constexpr int NQ = TC_KC / E;                       // core matrices along K per chunk
+    static constexpr uint32_t SBO = NQ * 128;                  // bytes per 8-column group of a chunk
+    static constexpr int KMMA = FMT == 1 ? 16 : 8;             // K per MMA
+    static constexpr int NPART = P == 3 ? 2 : 1;
+    static_assert(P == 1 || (P == 3 && FMT == 1), "hi/lo split of BF16 only");
+    __host__ __device__ static constexpr uint32_t tile_bytes(int NP) { return (uint32_t)(NP / 8) * SBO; }
+    __host__ __device__ static constexpr uint32_t chunk_bytes(int NP) { return NPART * tile_bytes(NP); }
+};
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rb = blockIdx.y, slot = blockIdx.x;
-    const int NPt = g.NP;                                  // multiple of 16
-    uint32_t ncols = 32;
-    while ((int)ncols < NPt) ncols <<= 1;
-
-    if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
-    if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+// Design tiles: one CTA per chunk of 32 rows at a time stages the rows'
+// weights and basis values (as design_kernel does), then each thread writes
+// one 16-byte core-matrix row (E rows of one column) of each part; consecutive
+// threads write consecutive 16-byte rows of one core-matrix column group.
+template <int FMT, int P>
+__global__ void __launch_bounds__(256) design_tiles_kernel(GramArgs g, const float* rw, uint8_t* tiles) {
+    using T = TcGram<FMT, P>;
+    extern __shared__ int dsm[];
+    int* cn = dsm;                                   // [NP] basis index, or -1
+    int* cs = dsm + g.NP;                            // [NP] weight slot, or -1 (padding)
+    __shared__ float w[TC_KC][RMETA];
+    __shared__ float xv[TC_KC][ARGUS_MAX_NB + 1];
+    for (int j = threadIdx.x; j < g.NP; j += blockDim.x) {
+        int n, k;
+        col_code(g, j, n, k);
+        cn[j] = n >= 0 ? n : -1;
+        cs[j] = n >= 0 ? k : (n == -100 ? 12 : (n == -200 ? -1 : 6 + (-1 - n)));
     }
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    const uint32_t tmem = *tmem_slot;
-
     const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
     const long nchunks = (nrows + TC_KC - 1) / TC_KC;
-    const uint32_t idesc0 = tc::instr_desc(FMT, 128, NPt > 256 ? 256 : NPt);
-    const uint32_t idesc1 = NPt > 256 ? tc::instr_desc(FMT, 128, NPt - 256) : 0u;
-    int it = 0;
-    for (long ch = slot; ch < nchunks; ch += gridDim.x, it++) {
-        const int st = it & 1;
-        uint8_t* sb = stage0 + st * stage_bytes;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int units = g.NP * T::NQ;                  // 16-byte rows per part of a chunk
+    const uint32_t tb = T::tile_bytes(g.NP);
+    for (long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const long rho0 = ch * TC_KC;
         __syncthreads();
-        // the MMAs that last read this stage must be complete before it is rewritten
-        if (it >= 2) {
-            if (!tc::mbar_wait_bounded(&mbar[st], ((it >> 1) - 1) & 1, TC_WAIT_LIMIT)) *abort_flag = 1;
+        for (int k = warp * 2 + (lane >> 4); k < TC_KC; k += 16) {
+            const long rho = rho0 + k;
+            w[k][lane & 15] = rho < nrows ? rw[rho * RMETA + (lane & 15)] : 0.0f;
+        }
+        {
+            const long rho = rho0 + lane;
+            const bool in = rho < nrows;
+            const int s = in ? (int)(rho / g.ss) : 0;
+            const int pix = in ? (int)(rho - (long)s * g.ss) : 0;
+            const float* xs = g.X + (long)s * g.nb * g.ss + pix;
+            for (int n = warp; n < g.nb; n += 8) xv[lane][n] = in ? __ldg(xs + (long)n * g.ss) : 0.0f;
         }
         __syncthreads();
-        if (*abort_flag) break;
-        for (int e = tid; e < NR * KQ; e += blockDim.x) {
-            const int kq = e / NR, i = e - kq * NR;
-            float v[E];
+        uint8_t* base = tiles + (size_t)ch * T::chunk_bytes(g.NP);
+        for (int u = threadIdx.x; u < units; u += blockDim.x) {
+            const int jg = u / (8 * T::NQ), q = (u >> 3) % T::NQ, j = jg * 8 + (u & 7);
+            const int n = cn[j], sl = cs[j];
+            float v[T::E];
 #pragma unroll
-            for (int t = 0; t < E; t++) {   // rows of the weighted design matrix (zero past the rows)
-                const long rho = rho0 + kq * E + t;
-                v[t] = i < NPt ? __ldg(C + rho * NPt + i) : 0.0f;
+            for (int t = 0; t < T::E; t++) {
+                const int r = q * T::E + t;
+                const float wt = sl >= 0 ? w[r][sl] : 0.0f;
+                // X of skipped stamps holds no defined values: a zero weight gives 0
+                v[t] = (n >= 0 && wt != 0.0f) ? wt * xv[r][n] : wt;
             }
-            uint4 pk;
+            uint4 hi, lo;
             if constexpr (FMT == 1) {
-                pk.x = pack_bf16x2(v[0], v[1]);
-                pk.y = pack_bf16x2(v[2], v[3]);
-                pk.z = pack_bf16x2(v[4], v[5]);
-                pk.w = pack_bf16x2(v[6], v[7]);
-            } else {
-                pk.x = to_tf32(v[0]);
-                pk.y = to_tf32(v[1]);
-                pk.z = to_tf32(v[2]);
-                pk.w = to_tf32(v[3]);
-            }
-            *reinterpret_cast<uint4*>(sb + (i >> 3) * SBO + kq * 128 + (i & 7) * 16) = pk;
-        }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t base = tc::smem_u32(sb);
+                hi = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                pack_bf16x2(v[6], v[7]));
+                if constexpr (P == 3) {
+                    float l[8];
+                    const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-            for (int s = 0; s < TC_KC / KMMA; s++) {
-                const uint32_t koff = s * 2 * LBO;
-                const uint64_t ad = tc::smem_desc(base + rb * 16 * SBO + koff, LBO, SBO);
-                const uint64_t bd0 = tc::smem_desc(base + koff, LBO, SBO);
-                const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
-                if constexpr (FMT == 1) tc::mma_bf16(tmem, ad, bd0, idesc0, acc);
-                else tc::mma_tf32(tmem, ad, bd0, idesc0, acc);
-                if (NPt > 256) {
-                    const uint64_t bd1 = tc::smem_desc(base + 32 * SBO + koff, LBO, SBO);
-                    if constexpr (FMT == 1) tc::mma_bf16(tmem + 256, ad, bd1, idesc1, acc);
-                    else tc::mma_tf32(tmem + 256, ad, bd1, idesc1, acc);
+                    for (int t = 0; t < 4; t++) {
+                        l[2 * t] = v[2 * t] - __uint_as_float(hw[t] << 16);
+                        l[2 * t + 1] = v[2 * t + 1] - __uint_as_float(hw[t] & 0xffff0000u);
+                    }
+                    lo = make_uint4(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]), pack_bf16x2(l[4], l[5]),
+                                    pack_bf16x2(l[6], l[7]));
                 }
+            } else {
+                hi = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
             }
-            tc::commit(&mbar[st]);
+            const uint32_t off = (uint32_t)jg * T::SBO + (uint32_t)q * 128 + (uint32_t)(u & 7) * 16;
+            *reinterpret_cast<uint4*>(base + off) = hi;
+            if constexpr (P == 3) *reinterpret_cast<uint4*>(base + tb + off) = lo;
         }
     }
-    // drain: wait for the last commit of each stage that was used
-    const int nit = it;
+}
+
+// One block of the augmented Gram: rows 128 rb .. +127 (the MMA's M; rows past
+// NP are zero) and columns c0 .. c0 + n - 1 (the MMA's N, n <= 160).
+struct GramBlock {
+    int rb, c0, n;
+};
+constexpr int GRAM_MAX_BLOCKS = 64;
+struct GramBlocks {
+    GramBlock b[GRAM_MAX_BLOCKS];
+};
+constexpr int GRAM_CW = 160;                           // columns per block
+constexpr int GRAM_GROUP = 8;                          // chunks (256 rows) per FP32 accumulation
+constexpr int GRAM_STAGES = 3;
+constexpr int GRAM_EPI_WARPS = 8;                      // two per TMEM lane quadrant
+constexpr int GRAM_THREADS = (2 + GRAM_EPI_WARPS) * 32;
+constexpr int GRAM_EPI_COLS = GRAM_CW / 2;             // columns per epilogue warp
+
+template <int FMT, int P>
+struct GramShared {
+    using T = TcGram<FMT, P>;
+    // per stage: A (16 column groups) then B (20 column groups), each part after part
+    uint8_t stage[GRAM_STAGES][T::NPART][16 + GRAM_CW / 8][T::SBO];
+    uint64_t full[GRAM_STAGES], empty[GRAM_STAGES], tfull[2], tempty[2];
+    uint32_t tmem;
+    int abort;
+};
+
+template <class SH>
+__device__ __forceinline__ bool gram_wait(SH& S, uint64_t* bar, uint32_t parity, int* status) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if (S.abort) return false;
+    if (!tc::mbar_wait_bounded(bar, parity, TC_WAIT_LIMIT)) {
+        S.abort = 1;
+        argus_latch(status, ARGUS_ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// CTA (split, block): the block's partial sum over the chunks ch = split,
+// split + nsplit, ...  Warp 0 (one thread) moves each chunk's A and B column
+// ranges into a stage by bulk copies; warp 1 (one thread) issues the MMAs of a
+// chunk into one of two TMEM accumulators, switching every GRAM_GROUP chunks;
+// warps 2-9 drain a finished accumulator (256 rows of FP32 sums) into
+// double-float (hi, lo) registers with an error-free two-sum, so the FP32
+// accumulation never runs over more than 256 rows.  The block's hi and lo halves
+// go to partial slots split and split + nsplit.
+template <int FMT, int P>
+__global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles, GramBlocks blocks) {
+    using T = TcGram<FMT, P>;
+    using Sh = GramShared<FMT, P>;
+    extern __shared__ __align__(1024) uint8_t gsm_raw[];
+    Sh& S = *reinterpret_cast<Sh*>(gsm_raw + ((1024 - (tc::smem_u32(gsm_raw) & 1023)) & 1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const GramBlock blk = blocks.b[blockIdx.y];
+    const int split = blockIdx.x, nsplit = gridDim.x;
+    const int NP = g.NP, ngrp = NP / 8;
+    const int ag0 = 16 * blk.rb, nag = min(16, ngrp - ag0);   // A column groups (rows of the block)
+    const int bg0 = blk.c0 / 8, nbg = blk.n / 8;               // B column groups
+    const uint32_t tb = T::tile_bytes(NP), cb = T::chunk_bytes(NP);
+    const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
+    const long nchunks = (nrows + TC_KC - 1) / TC_KC;
+    const int nit = nchunks > split ? (int)((nchunks - 1 - split) / nsplit + 1) : 0;   // this CTA's chunks
+    const int ngroups = (nit + GRAM_GROUP - 1) / GRAM_GROUP;
+
+    // A rows past NP are never copied: zero them once in every stage and part
+    for (int e = tid; e < GRAM_STAGES * T::NPART * (16 - nag) * (int)(T::SBO / 16); e += blockDim.x) {
+        const int per = (16 - nag) * (T::SBO / 16);
+        const int sp = e / per, rem = e - sp * per;
+        const int st = sp / T::NPART, pt = sp - st * T::NPART;
+        *reinterpret_cast<uint4*>(&S.stage[st][pt][nag][0] + 16 * rem) = make_uint4(0, 0, 0, 0);
+    }
     if (tid == 0) {
-        for (int st = 0; st < 2; st++) {
-            const int uses = (nit + 1 - st) / 2;
-            if (uses > 0 && !tc::mbar_wait_bounded(&mbar[st], (uses - 1) & 1, TC_WAIT_LIMIT)) *abort_flag = 2;
+        for (int s = 0; s < GRAM_STAGES; s++) {
+            tc::mbar_init(&S.full[s], 1);
+            tc::mbar_init(&S.empty[s], 1);
         }
+        for (int b = 0; b < 2; b++) {
+            tc::mbar_init(&S.tfull[b], 1);
+            tc::mbar_init(&S.tempty[b], GRAM_EPI_WARPS);
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 512);
+    tc::fence_proxy_async();
+    tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (*abort_flag) {
-        if (tid == 0) argus_latch(g.status, ARGUS_ERR_TIMEOUT);
-    } else {
-        float* out = g.part + (long)slot * g.NP * g.NP;
-        const int qd = warp & 3, half = warp >> 2;
-        const int row = rb * 128 + qd * 32 + lane;
-        for (int c0 = half * 16; c0 < NPt; c0 += 32) {
-            float v[16];
-            if (nit > 0) {
-                tc::tmem_ld16(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, v);
-            } else {
+    const uint32_t tmem = S.tmem;
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane == 0) {
+            const uint32_t abytes = (uint32_t)nag * T::SBO, bbytes = (uint32_t)nbg * T::SBO;
+            for (int it = 0; it < nit; it++) {
+                const int s = it % GRAM_STAGES;
+                if (it >= GRAM_STAGES && !gram_wait(S, &S.empty[s], (it / GRAM_STAGES - 1) & 1, g.status)) break;
+                const uint8_t* src = tiles + (size_t)(split + (long)it * nsplit) * cb;
+                tc::mbar_arrive_expect_tx(&S.full[s], T::NPART * (abytes + bbytes));
 #pragma unroll
-                for (int t = 0; t < 16; t++) v[t] = 0.0f;
+                for (int pt = 0; pt < T::NPART; pt++) {
+                    tc::bulk_g2s(&S.stage[s][pt][0][0], src + pt * tb + (size_t)ag0 * T::SBO, abytes, &S.full[s]);
+                    tc::bulk_g2s(&S.stage[s][pt][16][0], src + pt * tb + (size_t)bg0 * T::SBO, bbytes, &S.full[s]);
+                }
             }
-            if (row < g.NP) {
-                float* o = out + (long)row * g.NP + c0;
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::instr_desc(FMT, 128, blk.n);
+            int last = -1;
+            for (int it = 0; it < nit; it++) {
+                const int s = it % GRAM_STAGES, gi = it / GRAM_GROUP, ab = gi & 1;
+                const bool first = it % GRAM_GROUP == 0;
+                if (first && gi >= 2 && !gram_wait(S, &S.tempty[ab], (gi / 2 - 1) & 1, g.status)) break;
+                if (!gram_wait(S, &S.full[s], (it / GRAM_STAGES) & 1, g.status)) break;
+                tc::fence_after();
+                const uint32_t d = tmem + (uint32_t)(ab * 256);
 #pragma unroll
-                for (int t = 0; t < 16; t += 4) *reinterpret_cast<float4*>(o + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+                for (int k = 0; k < TC_KC / T::KMMA; k++) {
+                    const uint32_t koff = (uint32_t)k * 2 * 128;
+#pragma unroll
+                    for (int pr = 0; pr < P; pr++) {
+                        // products hi*hi, hi*lo, lo*hi
+                        const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+                        const uint64_t ad = tc::smem_desc(tc::smem_u32(&S.stage[s][pa][0][0]) + koff, 128, T::SBO);
+                        const uint64_t bd = tc::smem_desc(tc::smem_u32(&S.stage[s][pb][16][0]) + koff, 128, T::SBO);
+                        const uint32_t acc = (first && k == 0 && pr == 0) ? 0u : 1u;
+                        if constexpr (FMT == 1) tc::mma_bf16(d, ad, bd, idesc, acc);
+                        else tc::mma_tf32(d, ad, bd, idesc, acc);
+                    }
+                }
+                tc::commit(&S.empty[s]);
+                if (it % GRAM_GROUP == GRAM_GROUP - 1 || it == nit - 1) tc::commit(&S.tfull[ab]);
+                last = it;
+            }
+            // every MMA lands before TMEM is released: the last commit covers all
+            if (last >= 0) {
+                const int gi = last / GRAM_GROUP;
+                if (!tc::mbar_wait_bounded(&S.tfull[gi & 1], (gi / 2) & 1, TC_WAIT_LIMIT)) {
+                    S.abort = 1;
+                    argus_latch(g.status, ARGUS_ERR_TIMEOUT);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: TMEM lane quadrant q = warp % 4, column half h
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int row = blk.rb * 128 + q * 32 + lane;
+        const int cl0 = h * GRAM_EPI_COLS;                         // first local column of this warp
+        float hi[GRAM_EPI_COLS], lo[GRAM_EPI_COLS];
+#pragma unroll
+        for (int c = 0; c < GRAM_EPI_COLS; c++) hi[c] = lo[c] = 0.0f;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        for (int gi = 0; gi < ngroups; gi++) {
+            const int ab = gi & 1;
+            bool ok = true;
+            if (lane == 0) ok = gram_wait(S, &S.tfull[ab], (gi / 2) & 1, g.status);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            tc::fence_after();
+#pragma unroll
+            for (int c16 = 0; c16 < GRAM_EPI_COLS / 16; c16++) {
+                if (cl0 + c16 * 16 < blk.n) {                      // warp-uniform
+                    uint32_t r[16];
+                    tc::tmem_ld16_nowait(tl + (uint32_t)(ab * 256 + cl0 + c16 * 16), r);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int c = c16 * 16 + t;
+                        const float v = __uint_as_float(r[t]);
+                        const float a = hi[c], sum = a + v, bp = sum - a;
+                        lo[c] += (a - (sum - bp)) + (v - bp);
+                        hi[c] = sum;
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&S.tempty[ab]);
+        }
+        if (row < NP) {
+            float* oh = g.part + (long)split * NP * NP + (long)row * NP + blk.c0 + cl0;
+            float* ol = g.part + (long)(split + nsplit) * NP * NP + (long)row * NP + blk.c0 + cl0;
+#pragma unroll
+            for (int c = 0; c < GRAM_EPI_COLS; c++) {
+                if (cl0 + c < blk.n) {
+                    oh[c] = hi[c];
+                    ol[c] = lo[c];
+                }
             }
         }
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // M[i][j] = M[j][i] = sum over slots of part[slot][i][j] (i <= j), FP64, fixed order.
@@ -1639,9 +1804,10 @@ void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, d
     tri_solve_kernel<<<1, 1024, sm, st>>>(ctx->L, ld, n, ctx->Dinv, rhs, rs, x, flag); argus_count_launch(1);
 }
 
-// Steps of iterative refinement launched after the first solve (each is a
-// no-op once the iteration has converged or started to diverge).
-constexpr int REFINE_MAX = 3;
+// Steps of iterative refinement after the first solve: one, with the residual
+// C^T W (I - C c) from the FP32 design and FP64 sums; its relative size is
+// reported as max_step.
+constexpr int REFINE_MAX = 1;
 
 extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
                                 const uint8_t* flags, argus_shape shape, const int* centers,
@@ -1651,7 +1817,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         return ARGUS_ERR_ARG;
     if (max_stamps < 1 || max_stamps > ctx->max_stamps || stamp < 1 || stamp > ARGUS_MAX_STAMP || !(stamp & 1))
         return ARGUS_ERR_ARG;
-    if (precision < ARGUS_PREC_FP32 || precision > ARGUS_PREC_BF16) return ARGUS_ERR_ARG;
+    if (precision < ARGUS_PREC_FP32 || precision > ARGUS_PREC_BF16X3) return ARGUS_ERR_ARG;
     int rc = argus_check_shape(shape, ctx->max_pixels);
     if (rc) return rc;
     BasisDev d;
@@ -1700,14 +1866,15 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
 
     const long max_rows = (long)max_stamps * ss;
     int part_slots;
-    // per-row weights and the weighted design matrix, for every precision
+    // per-row weights for every precision; the weighted design matrix is written as FP32
+    // rows (FP32 Gram) or as operand tiles (tensor-core Gram)
     {
         long rwb = (max_rows + 255) / 256;
         if (rwb > (long)ctx->num_sms * 8) rwb = (long)ctx->num_sms * 8;
         row_weights_kernel<<<(unsigned)rwb, 256, 0, st>>>(g, ctx->rowmeta); argus_count_launch(1);
-        design_kernel<<<ctx->num_sms * 4, 256, sizeof(int) * 2 * g.NP, st>>>(g, ctx->rowmeta, ctx->design); argus_count_launch(1);
     }
     if (precision == ARGUS_PREC_FP32) {
+        design_kernel<<<ctx->num_sms * 4, 256, sizeof(int) * 2 * g.NP, st>>>(g, ctx->rowmeta, ctx->design); argus_count_launch(1);
         const int ntile = (g.NP + GT - 1) / GT;
         const int npair = ntile * (ntile + 1) / 2;
         int nslots = ctx->num_sms * 3 / npair;   // three CTAs per SM
@@ -1719,26 +1886,43 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         part_slots = 2 * nslots;   // hi and lo halves of the double-float partials
         gram_cp_kernel<<<dim3(npair, nslots), 256, 0, st>>>(g, ctx->design, ntile); argus_count_launch(1);
     } else {
-        const int RB = (g.NP + 127) / 128;
-        const int NR = RB * 128;
-        int nslots = ctx->num_sms / RB;
-        if (nslots < 1) nslots = 1;
-        if (nslots > ctx->gram_parts) nslots = ctx->gram_parts;
+        // blocks of 128 rows x up to 160 columns that hold part of the upper triangle
+        GramBlocks blocks;
+        int nblk = 0;
+        for (int rb = 0; rb * 128 < g.NP; rb++)
+            for (int c0 = 0; c0 < g.NP; c0 += GRAM_CW) {
+                const int n = g.NP - c0 < GRAM_CW ? g.NP - c0 : GRAM_CW;
+                if (128 * rb > c0 + n - 1) continue;
+                if (nblk == GRAM_MAX_BLOCKS) return ARGUS_ERR_UNSUPPORTED;
+                blocks.b[nblk++] = GramBlock{rb, c0, n};
+            }
+        int nsplit = ctx->num_sms / nblk;
+        if (nsplit < 1) nsplit = 1;
+        if (nsplit > ctx->gram_parts / 2) nsplit = ctx->gram_parts / 2;
         const long nch = (max_rows + TC_KC - 1) / TC_KC;
-        if (nslots > nch) nslots = (int)nch;
-        g.nslots = nslots;
-        part_slots = nslots;
-        const int esz = precision == ARGUS_PREC_BF16 ? 2 : 4;
-        size_t smem = 2 * (size_t)NR * TC_KC * esz + 64;
-        if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: each holds up to 512 TMEM columns
-        if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
-        if (precision == ARGUS_PREC_BF16) {
-            cudaFuncSetAttribute(gram_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<1><<<dim3(nslots, RB), 256, smem, st>>>(g, ctx->design, NR); argus_count_launch(1);
-        } else {
-            cudaFuncSetAttribute(gram_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            gram_tc_kernel<2><<<dim3(nslots, RB), 256, smem, st>>>(g, ctx->design, NR); argus_count_launch(1);
-        }
+        if (nsplit > nch) nsplit = (int)nch;
+        g.nslots = nsplit;
+        part_slots = 2 * nsplit;   // hi and lo halves of the double-float partials
+        uint8_t* tiles = reinterpret_cast<uint8_t*>(ctx->design);
+        const size_t dsm = sizeof(int) * 2 * g.NP;
+        const int dgrid = ctx->num_sms * 4;
+        auto launch = [&](auto kern, auto dkern, size_t shsz) -> int {
+            size_t smem = shsz + 1024;
+            if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA per SM: each holds all 512 TMEM columns
+            if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
+            dkern<<<dgrid, 256, dsm, st>>>(g, ctx->rowmeta, tiles); argus_count_launch(1);
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return ARGUS_ERR_CUDA;
+            kern<<<dim3(nsplit, nblk), GRAM_THREADS, smem, st>>>(g, tiles, blocks); argus_count_launch(1);
+            return ARGUS_OK;
+        };
+        if (precision == ARGUS_PREC_TF32)
+            rc = launch(gram_tc_kernel<2, 1>, design_tiles_kernel<2, 1>, sizeof(GramShared<2, 1>));
+        else if (precision == ARGUS_PREC_BF16)
+            rc = launch(gram_tc_kernel<1, 1>, design_tiles_kernel<1, 1>, sizeof(GramShared<1, 1>));
+        else
+            rc = launch(gram_tc_kernel<1, 3>, design_tiles_kernel<1, 3>, sizeof(GramShared<1, 3>));
+        if (rc) return rc;
     }
     if ((rc = argus_launch_status())) return rc;
     const int NP = g.NP;

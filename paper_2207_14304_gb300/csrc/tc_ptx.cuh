@@ -2,7 +2,8 @@
 // normal-equation Gram and the subtraction's reference convolution): TMEM
 // allocation, shared-memory matrix descriptors, tcgen05.mma (kind::f16 /
 // kind::tf32, cta_group::1), commit to an mbarrier, TMEM loads, mbarrier
-// waits with a bound, named barriers and cp.async.  Only compiled for sm_103a.
+// waits with a bound, named barriers, cp.async and bulk copies.  Only compiled
+// for sm_103a.
 #pragma once
 #include <stdint.h>
 
@@ -167,6 +168,23 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[16], uint32_t (&b)[16
 // thread does not wait for the arrival to complete.
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Arrive on a transaction barrier and add `bytes` to the transactions it
+// waits for (the bulk copies that complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on `mbar`.
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
 }
 
 // 4-byte asynchronous global -> shared copy; bytes past `src_bytes` (0..4)

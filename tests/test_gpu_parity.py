@@ -3,9 +3,11 @@ on seeded inputs that span several tiles and a ragged tail.
 
 Tolerances (written per test): integer and flag outputs bit-exact; calibrated
 pixels within 4 float32 ulps of the operand magnitude; difference pixels within
-1e-4 of max(|I|, |R (x) K|, 1) per pixel; difference variance within 1e-5
-relative; detection masks bit-exact (the S/N decision is taken in float on both
-sides); kernel pixels within 1e-3 of max |K| (FP32 normal equations).
+1e-4 of max(|I|, |R (x) K|, 1) per pixel; difference variance against its exact
+per-pixel definition within 1e-5 relative plus the allowance of the kernels'
+128-px tile rule, and within 1e-3 relative on PSF-matching fields; detection masks
+bit-exact (the S/N decision is taken in float on both sides); kernel pixels within
+1e-3 of max |K| at every normal-equation precision.
 """
 import numpy as np
 import pytest
@@ -128,13 +130,13 @@ def test_subtract_parity(ora, ks, sdeg, bgdeg, w, h):
         B.argus_destroy(ctx)
 
 
-@pytest.mark.parametrize("ox,oy", [(0, 0), (8832, 5760), (4000, 3010)])
+@pytest.mark.parametrize("ox,oy", [(0, 0), (8832, 5760), (4000, 3008)])
 def test_subtract_variance_on_a_psf_matching_field(ora, ox, oy):
     """Rectangles of a 9576x6388 frame with the kernel field of a PSF that widens from 1.3 to
     2.2 px towards the corners and a 30-frame-deep reference (V_ref = V_I / 30): the GPU's
     V_D within 1e-3 of the exact per-pixel definition (the bar set by the detection margin),
     and within FP32 arithmetic plus the tile rule's allowance pixel by pixel.  (0, 0) and
-    (8832, 5760) are on the 128 grid (tensor-core variance), (4000, 3010) is not (FP32)."""
+    (8832, 5760) are on the 128 grid (tensor-core variance), (4000, 3008) is not (FP32)."""
     ks, sdeg, W, H, w, h = 21, 2, 9576, 6388, 600, 500
     rng = np.random.default_rng(ox + oy)
     K = psf_matching_field(ks, W, H)
@@ -408,9 +410,14 @@ def ora_cal(raw, cal):
                             bpm=cal.bpm.numpy(), gain=cal.gain, read_noise=cal.read_noise, sat=cal.sat)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
-@pytest.mark.parametrize("w,h,ks,sdeg,grid", [(256, 256, 11, 0, (4, 4)), (320, 288, 11, 2, (6, 5))])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("w,h,ks,sdeg,grid", [(256, 256, 11, 0, (4, 4)), (320, 288, 11, 2, (6, 5)),
+                                              (480, 400, 21, 2, (6, 5))])
 def test_fit_parity(ora, prec, w, h, ks, sdeg, grid):
+    """The fit at every Gram precision against the FP64 oracle: a singular Gram fails the test;
+    kernel pixels within 1e-3 of max|K| (the primary, basis-independent bar), background
+    within 1e-3, chi^2 within the bar of each precision; the coefficient error is printed.
+    (256, 256) has 50 unknowns, the others 295 (degree-2 kernel and background)."""
     R, Vr, I, V, fl, raw, cal = _fit_field(w, h, seed=w + ks, sdeg=sdeg)
     b = ora.Basis(ksize=ks, spatial_degree=sdeg, bg_degree=sdeg)
     cen = ora.select_stamps(R, fl, grid[0], grid[1], 21, ks // 2, 3.0e4)
@@ -438,29 +445,20 @@ def test_fit_parity(ora, prec, w, h, ks, sdeg, grid):
         torch.cuda.synchronize()
         status = B.argus_sync_status(ctx)
         st = B.fit_stats_from_bytes(stats)
-        if prec != "fp32" and status == B.ARGUS_ERR_SINGULAR:
-            # a low-precision Gram of this near-degenerate design may lose definiteness;
-            # that outcome is reported through the status, never silently
-            assert st["status"] == B.ARGUS_ERR_SINGULAR
-            print(f"\n[fit {prec} {w}x{h} ks{ks} sdeg{sdeg}] Gram not positive definite in {prec}")
-            return
-        assert status == 0
+        assert status == 0, f"{prec}: status {status} ({B.status_string(status)})"
         a = coeffs.cpu().numpy()
         Kg = K.cpu().numpy().reshape(Ks, ks, ks)
         kerr = np.abs(Kg - Ko).max() / np.abs(Ko).max()
-        aerr = np.linalg.norm(a - res.coeffs) / np.linalg.norm(res.coeffs)
+        aerr = np.abs(a - res.coeffs).max() / np.abs(res.coeffs).max()
         print(f"\n[fit {prec} {w}x{h} ks{ks} sdeg{sdeg}] kernel-pixel err {kerr:.2e}  coeff err {aerr:.2e}  "
               f"chi2 {st['chi2']:.8g} vs {res.chi2:.8g}  chi2(a0) {st['chi2_a0']:.8g}  "
               f"steps {st['refine_iters']} last {st['max_step']:.2e}")
         assert st["status"] == 0 and st["n_coeffs"] == Nc and st["n_stamps_used"] == len(cen)
-        assert st["dof"] == res.dof
+        assert st["dof"] == res.dof and st["refine_iters"] == 1
         assert st["chi2"] >= res.chi2 * (1 - 1e-6)          # the oracle's solution minimises chi2
-        if prec == "fp32":
-            assert abs(st["chi2"] / res.chi2 - 1) < 1e-6
-            assert kerr < 1e-3
-            np.testing.assert_allclose(bg.cpu().numpy(), bgo, rtol=0, atol=1e-3 * max(1.0, np.abs(bgo).max()))
-        else:
-            assert abs(st["chi2"] / res.chi2 - 1) < 1e-2
+        assert kerr < 1e-3
+        np.testing.assert_allclose(bg.cpu().numpy(), bgo, rtol=0, atol=1e-3 * max(1.0, np.abs(bgo).max()))
+        assert abs(st["chi2"] / res.chi2 - 1) < (1e-6 if prec in ("fp32", "bf16x3") else 1e-4)
     finally:
         B.argus_destroy(ctx)
 
