@@ -337,7 +337,9 @@ def run_gpu(args):
 
     var = {}
     if args.variants and ws == 1:
-        for prec in ("tf32", "bf16"):
+        # whole frames, one at a time, with each normal-equation precision (fp32 included, for
+        # comparison on equal terms); fit_ms is the fit stage alone
+        for prec in ("fp32", "tf32", "bf16", "bf16_split"):
             pv = FramePipeline(W, H, basis=basis, stamp=STAMP, grid=GRID, precision=prec, psf_sigma=1.8,
                                device=local, ctx=pipe.ctx)
             for _ in range(2):
@@ -350,8 +352,15 @@ def run_gpu(args):
             for _ in range(kv):
                 pv.run(d_raw, calib, d_R, d_Vr, stream)
             a1.record(stream)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(kv):
+                pv.fit(d_R, stream)
+            f1.record(stream)
             torch.cuda.synchronize(device)
-            var[prec] = round(mpix * kv / (a0.elapsed_time(a1) / 1e3), 2)
+            var[prec] = {"mpix_s": round(mpix * kv / (a0.elapsed_time(a1) / 1e3), 2),
+                         "fit_ms": round(f0.elapsed_time(f1) / kv, 4)}
             if pv.status(stream) != 0:
                 var[prec] = None
 
@@ -945,7 +954,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16_split"])
     ap.add_argument("--band-rows", type=int, default=48)
     ap.add_argument("--frames-in-flight", type=int, default=2,
                     help="frames processed concurrently, each on its own pipeline and stream")

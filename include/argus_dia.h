@@ -47,12 +47,13 @@ enum {
     ARGUS_ERR_UNSUPPORTED = -8 /* size outside the compiled kernel set */
 };
 
-/* Operand precision of the normal-equation Gram: FP32 (FP32 pipes), TF32 or
- * BF16 (operands rounded, tensor cores), BF16X3 (each operand split into BF16
- * hi + lo, products hi*hi + hi*lo + lo*hi on the tensor cores); every
- * tensor-core product accumulates in FP32 over at most 256 design rows, folded
+/* Operand precision of the normal-equation Gram: FP32 (FP32 pipes); TF32 or
+ * BF16 (each design value rounded once, tensor cores); BF16_SPLIT (each value
+ * split into BF16 hi + lo, all four products hi*hi + hi*lo + lo*hi + lo*lo on the
+ * tensor cores: the Gram of the design rounded to 16 significant bits).  The
+ * tensor-core products accumulate in FP32 over at most 256 design rows, folded
  * into double-float sums. */
-enum { ARGUS_PREC_FP32 = 0, ARGUS_PREC_TF32 = 1, ARGUS_PREC_BF16 = 2, ARGUS_PREC_BF16X3 = 3 };
+enum { ARGUS_PREC_FP32 = 0, ARGUS_PREC_TF32 = 1, ARGUS_PREC_BF16 = 2, ARGUS_PREC_BF16_SPLIT = 3 };
 enum { ARGUS_FLAG_BAD = 1, ARGUS_FLAG_SAT = 2 };
 enum { ARGUS_MASK_POS = 1, ARGUS_MASK_NEG = 2, ARGUS_MASK_INVALID = 4 };
 
@@ -120,6 +121,10 @@ typedef struct {
 
 /* Human-readable name of a status code. */
 const char *argus_status_string(int status);
+
+/* Text of the last CUDA runtime error that made a call of this host thread
+ * return ARGUS_ERR_CUDA ("cudaErrorName: description"; "" if none). */
+const char *argus_last_cuda_error(void);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side tally, all contexts).  The difference of two readings counts

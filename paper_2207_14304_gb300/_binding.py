@@ -27,7 +27,7 @@ ARGUS_ERR_UNSUPPORTED = -8
 ARGUS_FLAG_BAD, ARGUS_FLAG_SAT = 1, 2
 ARGUS_MASK_POS, ARGUS_MASK_NEG, ARGUS_MASK_INVALID = 1, 2, 4
 
-PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16_split": 3}
 FLAG_BAD, FLAG_SAT = 1, 2
 MASK_POS, MASK_NEG, MASK_INVALID = 1, 2, 4
 
@@ -35,7 +35,13 @@ MASK_POS, MASK_NEG, MASK_INVALID = 1, 2, 4
 class ArgusError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
-        super().__init__(f"{what}: argus status {code} ({status_string(code)})")
+        detail = ""
+        if code == ARGUS_ERR_CUDA:
+            try:
+                detail = f" [{load(False).argus_last_cuda_error().decode()}]"
+            except Exception:
+                pass
+        super().__init__(f"{what}: argus status {code} ({status_string(code)}){detail}")
 
 
 class argus_shape(C.Structure):
@@ -98,6 +104,7 @@ class argus_wcs(C.Structure):
 SIGNATURES = {
     "argus_status_string": ([I], C.c_char_p),
     "argus_launch_count": ([], C.c_ulonglong),
+    "argus_last_cuda_error": ([], C.c_char_p),
     "argus_create": ([C.POINTER(P), I, C.c_size_t, I, I, I], I),
     "argus_destroy": ([P], I),
     "argus_sync_status": ([P, P], I),

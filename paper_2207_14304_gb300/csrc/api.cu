@@ -9,6 +9,8 @@
 
 #include <atomic>
 
+#include <cstdio>
+
 #include "argus_internal.cuh"
 
 extern "C" const char* argus_status_string(int s) {
@@ -43,9 +45,20 @@ void argus_count_launch(int n) { g_launches.fetch_add((unsigned long long)(long 
 
 extern "C" unsigned long long argus_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int argus_launch_status() {
-    return cudaGetLastError() == cudaSuccess ? ARGUS_OK : ARGUS_ERR_CUDA;
+// The last CUDA error a call of this thread met, as "name: description".
+static thread_local char g_last_cuda_error[256] = "";
+
+int argus_cuda_fail(cudaError_t e) {
+    snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return ARGUS_ERR_CUDA;
 }
+
+int argus_launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ARGUS_OK : argus_cuda_fail(e);
+}
+
+extern "C" const char* argus_last_cuda_error(void) { return g_last_cuda_error; }
 
 template <typename T>
 static bool dalloc(T** p, size_t n) {

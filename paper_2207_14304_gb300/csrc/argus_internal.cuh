@@ -71,6 +71,7 @@ __device__ __forceinline__ void argus_latch(int* st, int code) { atomicCAS(st, 0
 int argus_check_shape(const argus_shape& s, size_t max_pixels);
 int argus_check_ptr16(const void* p);
 int argus_launch_status();   // ARGUS_OK or ARGUS_ERR_CUDA after a launch
+int argus_cuda_fail(cudaError_t e);   // records e for argus_last_cuda_error, returns ARGUS_ERR_CUDA
 void argus_count_launch(int n);   // host-side tally of kernel launches
 extern "C" unsigned long long argus_launch_count(void);
 

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(256, 3) gram_cp_kernel(GramArgs g, const float
 }
 
 // ---------------------------------------------------------------------------
-// K4 on the tensor cores (TF32, BF16, or BF16 with a hi/lo split).
+// K4 on the tensor cores (TF32, BF16, or BF16 split into hi + lo).
 //
 // The weighted design matrix is written once per fit as tiles of 32 rows that
 // are already in the MMA's no-swizzle K-major operand layout: for chunk ch,
@@ -600,7 +600,12 @@ __device__ __forceinline__ uint32_t to_tf32(float a) {
     return r;
 }
 
-// FMT 1 = BF16, 2 = TF32; P = 1 (rounded operand) or 3 (BF16 hi/lo: hi*hi + hi*lo + lo*hi)
+// FMT 1 = BF16, 2 = TF32; P = 1 (rounded operand) or 4 (BF16 hi + lo split, all four
+// products hi*hi + hi*lo + lo*hi + lo*lo).  Either way the result is the exact Gram
+// (up to FP32 accumulation) of a design perturbed by its rounding: positive
+// semi-definite and consistent.  Dropping lo*lo would subtract the PSD matrix
+// sum lo lo^T instead, which moves near-degenerate directions of the normal
+// matrix towards singularity (measured: worse than one rounded operand).
 template <int FMT, int P>
 struct TcGram {
     static constexpr int ESZ = FMT == 1 ? 2 : 4;
@@ -608,8 +613,8 @@ struct TcGram {
     static constexpr int NQ = TC_KC / E;                       // core matrices along K per chunk
     static constexpr uint32_t SBO = NQ * 128;                  // bytes per 8-column group of a chunk
     static constexpr int KMMA = FMT == 1 ? 16 : 8;             // K per MMA
-    static constexpr int NPART = P == 3 ? 2 : 1;
-    static_assert(P == 1 || (P == 3 && FMT == 1), "hi/lo split of BF16 only");
+    static constexpr int NPART = P == 4 ? 2 : 1;
+    static_assert(P == 1 || (P == 4 && FMT == 1), "hi/lo split of BF16 only");
     __host__ __device__ static constexpr uint32_t tile_bytes(int NP) { return (uint32_t)(NP / 8) * SBO; }
     __host__ __device__ static constexpr uint32_t chunk_bytes(int NP) { return NPART * tile_bytes(NP); }
 };
@@ -669,7 +674,7 @@ __global__ void __launch_bounds__(256) design_tiles_kernel(GramArgs g, const flo
             if constexpr (FMT == 1) {
                 hi = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
                                 pack_bf16x2(v[6], v[7]));
-                if constexpr (P == 3) {
+                if constexpr (P == 4) {
                     float l[8];
                     const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
@@ -685,13 +690,13 @@ __global__ void __launch_bounds__(256) design_tiles_kernel(GramArgs g, const flo
             }
             const uint32_t off = (uint32_t)jg * T::SBO + (uint32_t)q * 128 + (uint32_t)(u & 7) * 16;
             *reinterpret_cast<uint4*>(base + off) = hi;
-            if constexpr (P == 3) *reinterpret_cast<uint4*>(base + tb + off) = lo;
+            if constexpr (P == 4) *reinterpret_cast<uint4*>(base + tb + off) = lo;
         }
     }
 }
 
 // One block of the augmented Gram: rows 128 rb .. +127 (the MMA's M; rows past
-// NP are zero) and columns c0 .. c0 + n - 1 (the MMA's N, n <= 160).
+// NP are zero) and columns c0 .. c0 + n - 1 (the MMA's N, n <= GRAM_CW).
 struct GramBlock {
     int rb, c0, n;
 };
@@ -699,7 +704,9 @@ constexpr int GRAM_MAX_BLOCKS = 64;
 struct GramBlocks {
     GramBlock b[GRAM_MAX_BLOCKS];
 };
-constexpr int GRAM_CW = 160;                           // columns per block
+// 128 columns per block: an epilogue thread then holds 2 x 64 accumulators; ten
+// warps put three on some SM partitions, which caps a thread at 168 registers
+constexpr int GRAM_CW = 128;                           // columns per block
 constexpr int GRAM_GROUP = 8;                          // chunks (256 rows) per FP32 accumulation
 constexpr int GRAM_STAGES = 3;
 constexpr int GRAM_EPI_WARPS = 8;                      // two per TMEM lane quadrant
@@ -709,7 +716,7 @@ constexpr int GRAM_EPI_COLS = GRAM_CW / 2;             // columns per epilogue w
 template <int FMT, int P>
 struct GramShared {
     using T = TcGram<FMT, P>;
-    // per stage: A (16 column groups) then B (20 column groups), each part after part
+    // per stage: A (16 column groups) then B (GRAM_CW / 8 column groups), part after part
     uint8_t stage[GRAM_STAGES][T::NPART][16 + GRAM_CW / 8][T::SBO];
     uint64_t full[GRAM_STAGES], empty[GRAM_STAGES], tfull[2], tempty[2];
     uint32_t tmem;
@@ -737,7 +744,7 @@ __device__ __forceinline__ bool gram_wait(SH& S, uint64_t* bar, uint32_t parity,
 // accumulation never runs over more than 256 rows.  The block's hi and lo halves
 // go to partial slots split and split + nsplit.
 template <int FMT, int P>
-__global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles, GramBlocks blocks) {
+__global__ void __launch_bounds__(GRAM_THREADS, 1) gram_tc_kernel(GramArgs g, const uint8_t* tiles, GramBlocks blocks) {
     using T = TcGram<FMT, P>;
     using Sh = GramShared<FMT, P>;
     extern __shared__ __align__(1024) uint8_t gsm_raw[];
@@ -773,7 +780,7 @@ __global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tc::tmem_alloc(&S.tmem, 512);
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 2 * GRAM_CW);
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -807,14 +814,14 @@ __global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles
                 if (first && gi >= 2 && !gram_wait(S, &S.tempty[ab], (gi / 2 - 1) & 1, g.status)) break;
                 if (!gram_wait(S, &S.full[s], (it / GRAM_STAGES) & 1, g.status)) break;
                 tc::fence_after();
-                const uint32_t d = tmem + (uint32_t)(ab * 256);
+                const uint32_t d = tmem + (uint32_t)(ab * GRAM_CW);
 #pragma unroll
                 for (int k = 0; k < TC_KC / T::KMMA; k++) {
                     const uint32_t koff = (uint32_t)k * 2 * 128;
 #pragma unroll
                     for (int pr = 0; pr < P; pr++) {
-                        // products hi*hi, hi*lo, lo*hi
-                        const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+                        // products hi*hi, hi*lo, lo*hi, lo*lo
+                        const int pa = pr >> 1, pb = pr & 1;
                         const uint64_t ad = tc::smem_desc(tc::smem_u32(&S.stage[s][pa][0][0]) + koff, 128, T::SBO);
                         const uint64_t bd = tc::smem_desc(tc::smem_u32(&S.stage[s][pb][16][0]) + koff, 128, T::SBO);
                         const uint32_t acc = (first && k == 0 && pr == 0) ? 0u : 1u;
@@ -855,7 +862,7 @@ __global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles
             for (int c16 = 0; c16 < GRAM_EPI_COLS / 16; c16++) {
                 if (cl0 + c16 * 16 < blk.n) {                      // warp-uniform
                     uint32_t r[16];
-                    tc::tmem_ld16_nowait(tl + (uint32_t)(ab * 256 + cl0 + c16 * 16), r);
+                    tc::tmem_ld16_nowait(tl + (uint32_t)(ab * GRAM_CW + cl0 + c16 * 16), r);
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int t = 0; t < 16; t++) {
@@ -886,7 +893,7 @@ __global__ void __maxnreg__(200) gram_tc_kernel(GramArgs g, const uint8_t* tiles
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * GRAM_CW);
 }
 
 // M[i][j] = M[j][i] = sum over slots of part[slot][i][j] (i <= j), FP64, fixed order.
@@ -1817,7 +1824,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         return ARGUS_ERR_ARG;
     if (max_stamps < 1 || max_stamps > ctx->max_stamps || stamp < 1 || stamp > ARGUS_MAX_STAMP || !(stamp & 1))
         return ARGUS_ERR_ARG;
-    if (precision < ARGUS_PREC_FP32 || precision > ARGUS_PREC_BF16X3) return ARGUS_ERR_ARG;
+    if (precision < ARGUS_PREC_FP32 || precision > ARGUS_PREC_BF16_SPLIT) return ARGUS_ERR_ARG;
     int rc = argus_check_shape(shape, ctx->max_pixels);
     if (rc) return rc;
     BasisDev d;
@@ -1886,7 +1893,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         part_slots = 2 * nslots;   // hi and lo halves of the double-float partials
         gram_cp_kernel<<<dim3(npair, nslots), 256, 0, st>>>(g, ctx->design, ntile); argus_count_launch(1);
     } else {
-        // blocks of 128 rows x up to 160 columns that hold part of the upper triangle
+        // blocks of 128 rows x up to GRAM_CW columns that hold part of the upper triangle
         GramBlocks blocks;
         int nblk = 0;
         for (int rb = 0; rb * 128 < g.NP; rb++)
@@ -1908,11 +1915,10 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         const int dgrid = ctx->num_sms * 4;
         auto launch = [&](auto kern, auto dkern, size_t shsz) -> int {
             size_t smem = shsz + 1024;
-            if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA per SM: each holds all 512 TMEM columns
             if (smem > 227 * 1024) return ARGUS_ERR_UNSUPPORTED;
             dkern<<<dgrid, 256, dsm, st>>>(g, ctx->rowmeta, tiles); argus_count_launch(1);
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-                return ARGUS_ERR_CUDA;
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return argus_cuda_fail(e);
             kern<<<dim3(nsplit, nblk), GRAM_THREADS, smem, st>>>(g, tiles, blocks); argus_count_launch(1);
             return ARGUS_OK;
         };
@@ -1921,7 +1927,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         else if (precision == ARGUS_PREC_BF16)
             rc = launch(gram_tc_kernel<1, 1>, design_tiles_kernel<1, 1>, sizeof(GramShared<1, 1>));
         else
-            rc = launch(gram_tc_kernel<1, 3>, design_tiles_kernel<1, 3>, sizeof(GramShared<1, 3>));
+            rc = launch(gram_tc_kernel<1, 4>, design_tiles_kernel<1, 4>, sizeof(GramShared<1, 4>));
         if (rc) return rc;
     }
     if ((rc = argus_launch_status())) return rc;

