@@ -961,9 +961,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")
-    ap.add_argument("--extras", default="coadd,segments,learned,sparse",
-                    help="comma list of the extra workloads to measure after the headline "
-                         "(also: background, healpix, zogy, proper_coadd)")
+    ap.add_argument("--extras", default="coadd,segments,learned,sparse,background,healpix,zogy,proper_coadd",
+                    help="comma list of the extra workloads to measure after the headline")
     ap.add_argument("--no-extras", dest="extras", action="store_const", const="")
     ap.add_argument("--frame", type=int, nargs=2, metavar=("W", "H"), default=None,
                     help="smaller frame for profiling captures (star count scaled by area)")

@@ -37,17 +37,23 @@ def _frame(w, h, seed):
     return I.numpy(), V.numpy(), R.numpy(), Vr.numpy(), fl
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_segments_parity(ora, use_graph):
+SMALL = (640, 480, [40, 57, 64, 90, 111, 128, 48, 70, 45, 81], 256)
+# the batched workload's size range: squares of 64 to 512 px, uneven sides (a ragged atlas of
+# several shelves), the largest one pixel short of and exactly at 512
+LARGE = (1400, 1100, [512, 256, 300, 77, 64, 419, 128, 511, 97, 333], 1024)
+
+
+@pytest.mark.parametrize("use_graph,case", [(True, SMALL), (False, SMALL), (True, LARGE)],
+                         ids=["graph-small", "direct-small", "graph-large"])
+def test_segments_parity(ora, use_graph, case):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    w, h = 640, 480
-    I, V, R, Vr, fl = _frame(w, h, seed=31)
-    sides = [40, 57, 64, 90, 111, 128, 48, 70, 45, 81]
+    w, h, sides, width = case
+    I, V, R, Vr, fl = _frame(w, h, seed=31 + w)
     origins = synth.segment_origins(sides, w, h, seed=3)
     ks = 15
     basis = B.make_basis(ks, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)
-    batch = SegmentBatch(sides, basis=basis, width=256, cfg=B.argus_seg_config(32, 1, 4, 0), src_cap=4096)
+    batch = SegmentBatch(sides, basis=basis, width=width, cfg=B.argus_seg_config(32, 1, 4, 0), src_cap=16384)
     try:
         for i, ((x0, y0), s) in enumerate(zip(origins, sides)):
             sl = (slice(y0, y0 + s), slice(x0, x0 + s))
@@ -103,7 +109,7 @@ def test_segments_parity(ora, use_graph):
             assert (np.abs(Dg - Do) <= 1e-4 * scale + dK * (-boxR) + dbg).all(), i
             assert (np.abs(VDg - VDo) <= 1e-5 * VDo + dK * (2 * kmax + dK) * (-boxV)).all(), i
         # detection on the GPU's own atlas
-        assert nsrc <= 4096
+        assert nsrc <= 16384
         n_p, n_n = check_detection_properties(batch.diff.cpu().numpy(), batch.diff_var.cpu().numpy(),
                                               batch.flags.cpu().numpy(), batch.mask.cpu().numpy(), src, nsrc, 5.0)
         n_checked = n_p + n_n
