@@ -16,38 +16,38 @@
 // for term k: shifting B by g rows of taps makes the four source rows land on
 // the columns of the output rows they feed, so the MMAs do part of the sum
 // over iv and the epilogue reads 36 instead of 126 columns per source row.
-// The epilogue warps add T into a ring of KS - 1 + G pending output rows (one
-// register set per row and power of y: the x powers are folded in as each
-// column is added), then output rows rho0 - 2r .. rho0 - 2r + 3 are complete
-// and the ring shifts by G.  Operands are BF16 hi/lo pairs (v = hi + lo, each
-// rounded to nearest) and every product is hi*hi + hi*lo + lo*hi, accumulated
-// in FP32 in TMEM: the dropped lo*lo term is below 2^-16 relative, well
-// inside FP32-level agreement.
 //
-// The same kernel with one term (VAR) computes the convolution of the
-// difference variance, sum Kc^2 (x) V_ref, with Kc the kernel at the centre of
-// the strip's 128 x 128 variance tile: A from V_ref, B_g from Kc^2 (rebuilt per
-// strip into one of two sets), V_D = V_I + the sum.
+// Precision.  The difference image splits R and K into BF16 hi + lo (each
+// rounded to nearest) and sums hi*hi + hi*lo + lo*hi in FP32 in TMEM: the
+// dropped lo*lo term is below 2^-16 relative, FP32-level agreement.  The
+// difference variance (VAR) computes sum Kc^2 (x) V_ref with Kc the kernel at
+// the centre of the strip's 128 x 128 variance tile from one BF16 product
+// (V_ref and Kc^2 each rounded once): its error is at most 2^-8 of that
+// convolved-reference term, which for a deep reference is a small part of
+// V_D (about 1 %), far inside the detection margin.
 //
 // A is stored once per source row as its 19 distinct core matrices: in the
 // canonical no-swizzle K-major layout the core matrix of row group i and K
 // group j holds A[8i + a][8j + b] = R(x0 - r + 8(i + j) + a + b, rs), a
 // function of i + j, so the descriptor's row-group stride equals its K-group
-// stride (both 128 bytes) and 16-byte row t of the stored operand is simply
-// R(x0 - r + t + b), b = 0..7.
+// stride (both 128 bytes) and 16-byte row t of the stored operand is
+// R(x0 - r + t + b), b = 0..7.  A producer warp rounds its source row to BF16
+// once (lane c: values 8c .. 8c + 7) into a small row buffer; lane l then
+// writes operand rows t = l, l + 32, ... (consecutive lanes, consecutive 16-byte
+// rows: no bank conflicts), each from five aligned 32-bit words of the buffer
+// and a byte permutation (rows starting at an odd element straddle words).
 //
 // Persistent CTAs walk the strips of 128 columns x a band of TCY output rows,
 // streaming each band's TCY + 2r source rows in blocks of G (the difference
-// image: one CTA of 352 threads per SM; the variance: two).  Warps 0-3:
-// epilogue, one output column per thread and TMEM lane; science values and
-// flag words reach shared memory by cp.async two blocks ahead, each thread
-// fetching its own column.  Warps 4-8: producers, each warp on its own (it
-// stages its window of the source rows by 16-byte cp.async two blocks ahead,
-// writes its 32 rows of the A operands of a block, splitting each value into
-// hi/lo where it is used, and arrives on the stage's barrier).  Warps 9-10: one
-// thread each issues the MMAs of alternate blocks.  TMEM holds NTB
-// accumulators.  Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and
-// all roles stop.
+// image: one CTA of 320 threads per SM; the variance: two).  Warps 0-3:
+// epilogue, one output column per thread and TMEM lane; warp w stages the
+// observed values and flag bytes of its 32 columns by 16-byte cp.async LA = 6
+// blocks ahead.  Warps 4-7: producers, warp 4 + g for source row g of each
+// block (it stages its row's window by 16-byte cp.async LA blocks ahead and
+// writes the row's A operands).  The deep staging keeps enough reads in flight
+// to cover DRAM latency: two blocks ahead left every role waiting on it.  Warps 8-9: one thread each issues the MMAs of
+// alternate blocks.  TMEM holds NTB accumulators.  Every wait is bounded; a
+// timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_bf16.h>
 
 #include "subtract_tile.cuh"
@@ -61,24 +61,24 @@ constexpr int TCY = 128;                     // output rows per CTA band
 constexpr int TKC = 32;                      // MMA K: taps u', padded
 constexpr int G = 4;                         // source rows per block
 constexpr int NCM = TCX / 8 + TKC / 8 - 1;   // distinct core matrices of one Hankel tile
-constexpr uint32_t A_BYTES = NCM * 128;      // one operand (hi or lo) of one source row
+constexpr uint32_t A_BYTES = NCM * 128;      // one operand part (hi or lo) of one source row
 // block stages of A: three for the difference image; two for the variance, whose
 // CTAs run two per SM (see launch_tc)
 template <bool VAR>
 __host__ __device__ constexpr int nsb() { return VAR ? 2 : 3; }
-constexpr int NSRC = 4 * G;                  // fp32 source-row ring: four blocks
-constexpr int NBUILD = NCM * 8;              // one producer thread per stored operand row
-constexpr int PCH = 11;                      // 16-byte chunks of a producer warp's window (32 + 7 values + offset)
+constexpr int NPW = G;                       // producer warps: one per source row of a block
+constexpr int LA = 6;                        // blocks staged ahead (source rows and observed rows)
+constexpr int NSLOT = 8;                     // staged source windows per producer warp (> LA)
+constexpr int PCH = 44;                      // 16-byte chunks of a staged window (160 values + offset)
 constexpr int PWIN = PCH * 4;
-constexpr int NPROD = (NBUILD + 31) / 32 * 32;   // producer threads (warps 4-8)
-constexpr int NPW = NPROD / 32;              // producer warps
-constexpr int MMA_WARP = 4 + NPW;            // warps 9 and 10 issue the MMAs of even and odd blocks
+constexpr int MMA_WARP = 4 + NPW;            // warps 8 and 9 issue the MMAs of even and odd blocks
 constexpr int TC_THREADS = (MMA_WARP + 2) * 32;
 constexpr uint32_t LBO = 128, SBO_A = 128, SBO_B = 512;
 constexpr long long WAIT_LIMIT = 2000000000LL;   // ~1 s of SM clock
 constexpr int NTB = 3;                       // TMEM accumulators
-constexpr int NQ = 4 * G;                    // science/flag rows in shared memory: four blocks
-static_assert(MMA_WARP == 9 && TC_THREADS == 352, "warp roles");
+constexpr int NQ = 8 * G;                    // staged rows of observed values and flags: eight blocks (> LA + 1)
+static_assert(MMA_WARP == 8 && TC_THREADS == 320, "warp roles");
+static_assert(NCM * 8 == TCX + TKC - 8 && NCM + 1 <= 32, "one lane per 8 operand rows, plus one");
 
 template <int KS, int NK>
 struct TcCfg {
@@ -86,20 +86,25 @@ struct TcCfg {
     static constexpr int NCOL = NJB * NK;                   // used MMA columns
     static constexpr int N = (NCOL + 15) / 16 * 16;         // MMA N
     static constexpr int TSTRIDE = (N + 31) / 32 * 32;      // TMEM columns per accumulator
-    static constexpr uint32_t B_BYTES = (uint32_t)N / 8 * SBO_B;   // one B_g operand
+    static constexpr uint32_t B_BYTES = (uint32_t)N / 8 * SBO_B;   // one B_g operand part
+    static constexpr int RLP = (NJB + G - 1) / G * G;       // ring of pending output rows
+    // one term: the ring rotates (RLP / G unrolled blocks per turn, no register moves);
+    // more terms: a compact loop that shifts the ring by G after each block
+    static constexpr bool ROT = NK == 1;
+    static constexpr int UNR = ROT ? RLP / G : 1;
     static_assert(N <= 256 && NTB * TSTRIDE <= 512, "MMA shape");
-    static_assert(NK != 1 || (2 * N <= 256 && NTB * 2 * N <= 512), "one-term MMA of width 2N");
     static_assert(KS <= 24 && G % 2 == 0, "taps 16..23 of row pairs share one MMA");
 };
 
 template <int KS, int NK, bool VAR>
 struct TcShared {
-    uint8_t b[VAR ? 2 : 1][G][2][TcCfg<KS, NK>::B_BYTES];   // B_g, hi and lo (VAR: one set per strip parity)
-    uint8_t ahi[nsb<VAR>()][G][A_BYTES];
-    uint8_t alo[nsb<VAR>()][G][A_BYTES];
-    alignas(16) float wsrc[NPW][NSRC][PWIN];    // each producer warp's staged source windows
-    alignas(16) float qI[NQ][TCX];              // science values of output rows, by row & (NQ - 1)
-    alignas(16) uint32_t qF[NQ][TCX];           // the 32-bit word holding each output pixel's flag byte
+    static constexpr int NP = VAR ? 1 : 2;   // operand parts: hi (and lo)
+    uint8_t b[VAR ? 2 : 1][G][NP][TcCfg<KS, NK>::B_BYTES];   // B_g (VAR: one set per strip parity)
+    uint8_t a[nsb<VAR>()][NP][G][A_BYTES];   // A operands of a block: [stage][part][row]
+    alignas(16) float wsrc[NPW][NSLOT][PWIN];   // each producer warp's staged source windows
+    alignas(16) uint32_t rowb[NPW][NP][(NCM + 1) * 4];   // a source row rounded to BF16 (hi, lo), 2 per word
+    alignas(16) float qI[4][NQ][32];            // observed values of each epilogue warp's columns
+    alignas(16) uint8_t qF[4][NQ][32];          // their flag bytes
     uint64_t filled[nsb<VAR>()], empty[nsb<VAR>()], tfull[NTB], tempty[NTB];
     uint64_t bready[2], bfree[2];               // VAR: B set written / no longer read by the MMAs
     uint32_t tmem;
@@ -120,12 +125,6 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float v0, float v1) {
     uint32_t d;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
     return d;
-}
-
-// hi/lo split of a pair (hi = rn(v), lo = rn(v - hi)), each packed two per word.
-__device__ __forceinline__ void split_pair(float v0, float v1, uint32_t& hi, uint32_t& lo) {
-    hi = bf16x2_rn(v0, v1);
-    lo = bf16x2_rn(v0 - __uint_as_float(hi << 16), v1 - __uint_as_float(hi & 0xffff0000u));
 }
 
 // One try first (the common case: the phase is already complete), then a
@@ -151,22 +150,22 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
     using C = TcCfg<KS, NK>;
     using Sh = TcShared<KS, NK, VAR>;
     constexpr int NSB = nsb<VAR>();
+    constexpr int NP = Sh::NP;                   // operand parts
+    constexpr int P = VAR ? 1 : 3;               // products per K slice: hi*hi (+ hi*lo + lo*hi)
     static_assert(!VAR || NK == 1, "the variance convolution has one term");
     static_assert(TCX == VAR_TILE && TCY == VAR_TILE, "one variance tile per strip");
     const float* src_img = VAR ? a.ref_var : a.ref;   // convolved image
     const float* obs = VAR ? a.sci_var : a.sci;       // observed image the model is compared with
     float* outp = VAR ? a.diff_var : a.diff;
     constexpr int R = (KS - 1) / 2;
-    constexpr int TS = VAR ? 2 * C::N : C::TSTRIDE;   // TMEM columns per accumulator
-    constexpr int SOFF = (4 - R % 4) % 4;        // wsrc[pw][.][SOFF + c] = R(x0 - R + 32 pw + c)
-    static_assert(KS <= TKC && SOFF + 31 + 8 <= PWIN, "tile shape");
+    constexpr int SOFF = (4 - R % 4) % 4;        // wsrc[g][.][SOFF + c] = R(x0 - R + c)
+    static_assert(KS <= TKC && SOFF + 8 * NCM + 16 <= PWIN, "tile shape");
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     Sh& S = *reinterpret_cast<Sh*>(tc_smem_raw + ((1024 - (tc::smem_u32(tc_smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // work items: strips of TCX columns x TCY rows, item = by * gx + bx, taken by the
-    // CTAs round robin (one CTA per SM); B is built once (difference image) or per
-    // strip by the producers into one of two sets (variance: it depends on the strip's
-    // variance tile)
+    // CTAs round robin; B is built once (difference image) or per strip by the
+    // producers into one of two sets (variance: it depends on the strip's variance tile)
     const int gx = (a.w + TCX - 1) / TCX, nitems = gx * ((a.h + TCY - 1) / TCY);
     auto geom = [&](int item, int& x0, int& y0, int& nout, int& nblk) {
         const int by = item / gx;
@@ -176,10 +175,9 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
         nblk = (nout + 2 * R + G - 1) / G;       // source rows y0 - R .. y0 + nout - 1 + R; rows past them are zero
     };
 
-    // ---- set-up: B_g (hi/lo) from the kernel taps, barriers, TMEM
-    // B_g column n = j * NK + k holds K_k[j - g][KS - 1 - u'] (VAR: Kc^2[j - g][KS - 1 - u'],
-    // Kc the kernel at the centre of the strip's variance tile); threads first .. first +
-    // count - 1 write set bs
+    // ---- B_g from the kernel taps: column n = j * NK + k holds K_k[j - g][KS - 1 - u'] (VAR:
+    // Kc^2[j - g][KS - 1 - u'], Kc the kernel at the centre of the strip's variance tile);
+    // threads first .. first + count - 1 write set bs
     auto build_b = [&](int item, int bs, int first, int count) {
         float pc[ARGUS_MAX_TERMS];
         int nkt = NK;
@@ -210,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
             __nv_bfloat16 hi, lo;
             split_bf16(v, hi, lo);
             *reinterpret_cast<__nv_bfloat16*>(S.b[bs][g][0] + canon_off(n, u)) = hi;
-            *reinterpret_cast<__nv_bfloat16*>(S.b[bs][g][1] + canon_off(n, u)) = lo;
+            if constexpr (NP == 2) *reinterpret_cast<__nv_bfloat16*>(S.b[bs][g][NP - 1] + canon_off(n, u)) = lo;
         }
     };
     if (!VAR) build_b(0, 0, 0, TC_THREADS);
@@ -230,7 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    constexpr uint32_t TMEM_COLS = VAR ? 256 : 512;   // the variance: two CTAs per SM share TMEM
+    constexpr uint32_t TMEM_COLS = NTB * C::TSTRIDE <= 128 ? 128 : (NTB * C::TSTRIDE <= 256 ? 256 : 512);
     if (warp == 0) tc::tmem_alloc(&S.tmem, TMEM_COLS);
     tc::fence_proxy_async();   // B tiles written through the generic proxy
     tc::fence_before();
@@ -241,15 +239,14 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
     // drives the stage and TMEM rings and their barrier phases
 
     if (warp >= 4 && warp < MMA_WARP) {
-        // ---------------- producers: each warp works on its own, with no barrier between
-        // warps.  Lane l of producer warp pw writes 16-byte row t = 32 pw + l (t < NBUILD)
-        // of the A operands of each source row of a block, R(x0 - R + t + b), b = 0..7.
-        // The warp stages the source values it needs (its 44-float window of each row,
-        // 11 16-byte chunks) itself, two blocks ahead, one cp.async group per block;
-        // after its writes and a proxy fence, lane 0 arrives on the stage's filled
-        // barrier (one arrival per producer warp).
-        const int pw = warp - 4, t = 32 * pw + lane;
-        float (*wsrc)[PWIN] = S.wsrc[pw];
+        // ---------------- producers: warp 4 + g writes the A operands of source row g of
+        // every block, with no barrier between producer warps.  The warp stages the row's
+        // window (44 16-byte chunks from frame column XS, a multiple of 4) two blocks ahead,
+        // one cp.async group per block; lane c < 20 rounds R(x0 - R + 8c .. 8c + 7), lane
+        // c < 19 writes operand rows 8c .. 8c + 7; after the writes and a proxy fence lane 0
+        // arrives on the stage's filled barrier (one arrival per producer warp).
+        const int g = warp - 4;
+        float (*ws)[PWIN] = S.wsrc[g];
         bool run = true;
         int gb = 0, li = 0;
         for (int item = blockIdx.x; item < nitems && run; item += gridDim.x, li++) {
@@ -260,49 +257,74 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
                 bool ok = true;
                 if (lane == 0 && li >= 2) ok = wait_or_abort(S, &S.bfree[li & 1], ((li - 2) >> 1) & 1, status);
                 if (!__shfl_sync(0xffffffffu, ok, 0)) { run = false; break; }
-                build_b(item, li & 1, 128, NPROD);
+                build_b(item, li & 1, 4 * 32, NPW * 32);
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&S.bready[li & 1]);
             }
-            const int XS = x0 - R - SOFF + 32 * pw;   // frame column of wsrc[pw][.][0], a multiple of 4
+            const int XS = x0 - R - SOFF;        // frame column of ws[.][0], a multiple of 4
             auto issue = [&](int blk) {
-                for (int q = lane; q < G * PCH; q += 32) {
-                    const int g = q / PCH, c = q - g * PCH;
-                    const int rr = blk * G + g, gy = y0 - R + rr, X = XS + 4 * c;
-                    const int nb = (X >= 0 && X < a.w && rr < nsrc && gy >= 0 && gy < a.h) ? 4 * min(4, a.w - X) : 0;
-                    tc::cp_async16(&wsrc[rr & (NSRC - 1)][4 * c], nb ? src_img + (long)gy * a.pitch + X : src_img, nb);
+                const int rr = blk * G + g, gy = y0 - R + rr;
+                const bool rin = rr < nsrc && gy >= 0 && gy < a.h;
+                float* dst = ws[blk & (NSLOT - 1)];
+                for (int q = lane; q < PCH; q += 32) {
+                    const int X = XS + 4 * q;
+                    const int nb = (rin && X >= 0 && X < a.w) ? 4 * min(4, a.w - X) : 0;
+                    tc::cp_async16(dst + 4 * q, nb ? src_img + (long)gy * a.pitch + X : src_img, nb);
                 }
                 tc::cp_async_commit();
             };
-            issue(0);
-            issue(1);
-            tc::cp_async_wait<1>();              // block 0 (own copies)
-            __syncwarp();                        // ... and the other lanes' copies are visible
+#pragma unroll
+            for (int b = 0; b < LA; b++) issue(b);
+            uint32_t (*rb)[(NCM + 1) * 4] = S.rowb[g];
             for (int blk = 0; blk < nblk; blk++, gb++) {
                 const int s = gb % NSB, fill = gb / NSB;
                 bool ok = true;
                 if (lane == 0 && fill >= 1) ok = wait_or_abort(S, &S.empty[s], (fill - 1) & 1, status);
                 if (!__shfl_sync(0xffffffffu, ok, 0)) { run = false; break; }
-                issue(blk + 2);                  // may be past the band: zero-filled, never used
-                if (t < NBUILD) {
+                issue(blk + LA);                 // may be past the band: zero-filled, never used
+                tc::cp_async_wait<LA>();         // block blk (own copies) ...
+                __syncwarp();                    // ... and the other lanes' copies are visible
+                // round the row once: lane c <= NCM, values 8c .. 8c + 7 (hi, and lo)
+                if (lane <= NCM) {
+                    const float* src = ws[blk & (NSLOT - 1)] + SOFF + 8 * lane;
+                    float v[8];
 #pragma unroll
-                    for (int g = 0; g < G; g++) {
-                        const float* src = wsrc[(blk * G + g) & (NSRC - 1)] + SOFF + lane;
-                        float v[8];
+                    for (int k = 0; k < 8; k++) v[k] = src[k];
+                    uint32_t h[4], l[4];
 #pragma unroll
-                        for (int k = 0; k < 8; k++) v[k] = src[k];
-                        uint32_t hw[4], lw[4];
-#pragma unroll
-                        for (int k = 0; k < 4; k++) split_pair(v[2 * k], v[2 * k + 1], hw[k], lw[k]);
-                        *reinterpret_cast<uint4*>(S.ahi[s][g] + 16 * t) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4*>(S.alo[s][g] + 16 * t) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    for (int k = 0; k < 4; k++) {
+                        h[k] = bf16x2_rn(v[2 * k], v[2 * k + 1]);
+                        l[k] = NP == 2 ? bf16x2_rn(v[2 * k] - __uint_as_float(h[k] << 16),
+                                                   v[2 * k + 1] - __uint_as_float(h[k] & 0xffff0000u))
+                                       : 0u;
                     }
-                    tc::fence_proxy_async();
+                    *reinterpret_cast<uint4*>(&rb[0][4 * lane]) = make_uint4(h[0], h[1], h[2], h[3]);
+                    if constexpr (NP == 2) *reinterpret_cast<uint4*>(&rb[NP - 1][4 * lane]) = make_uint4(l[0], l[1], l[2], l[3]);
                 }
-                tc::cp_async_wait<1>();          // block blk + 1 (own copies)
-                __syncwarp();                    // writes, fences and copies of all lanes done
-                if (lane == 0) tc::mbar_arrive(&S.filled[s]);
+                __syncwarp();
+                // operand row t = lane + 32 rho holds elements t .. t + 7 of the rounded row
+                const int A = lane & 7;
+                const uint32_t sel = (A & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+                for (int rho = 0; rho * 32 < NCM * 8; rho++) {
+                    const int t = lane + 32 * rho;
+                    if (t < NCM * 8) {
+                        const int wb = 4 * (t >> 3) + (A >> 1);
+#pragma unroll
+                        for (int pt = 0; pt < NP; pt++) {
+                            uint32_t wv[5];
+#pragma unroll
+                            for (int k = 0; k < 5; k++) wv[k] = rb[pt][wb + k];
+                            *reinterpret_cast<uint4*>(S.a[s][pt][g] + 16 * t) =
+                                make_uint4(__byte_perm(wv[0], wv[1], sel), __byte_perm(wv[1], wv[2], sel),
+                                           __byte_perm(wv[2], wv[3], sel), __byte_perm(wv[3], wv[4], sel));
+                        }
+                    }
+                }
+                tc::fence_proxy_async();
+                __syncwarp();                    // writes and fences of all lanes done (and the row
+                if (lane == 0) tc::mbar_arrive(&S.filled[s]);   // buffer free for the next block)
             }
             tc::cp_async_wait<0>();              // the zero-filled copies past the strip land before the
             __syncwarp();                        // next strip's copies reuse their slots
@@ -313,7 +335,6 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
         // issuers keep the tensor pipe fed while each waits on its barriers)
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(1, 128, C::N);
-            const uint32_t idesc2 = tc::instr_desc(1, 128, 2 * C::N);
             int issued = -1, gb = 0, li = 0;
             bool run = true;
             for (int item = blockIdx.x; item < nitems && run; item += gridDim.x, li++) {
@@ -327,52 +348,31 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
                     if (!wait_or_abort(S, &S.filled[s], (gb / NSB) & 1, status)) { run = false; break; }
                     if (gb >= NTB && !wait_or_abort(S, &S.tempty[tb], (gb / NTB - 1) & 1, status)) { run = false; break; }
                     tc::fence_after();
-                    const uint32_t d = tmem + (uint32_t)(tb * TS);
-                    if constexpr (VAR) {
-                        // one term: hi*hi and hi*lo in one MMA of width 2N (B's hi rows are
-                        // followed by its lo rows), lo*hi in one of width N; the epilogue
-                        // adds the two halves
-#pragma unroll
-                        for (int g = 0; g < G; g++) {
-                            const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
-                            const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
-                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]), LBO, SBO_B);
-                            tc::mma_bf16(d, ad_h, bd, idesc2, g ? 1u : 0u);
-                            tc::mma_bf16(d, ad_l, bd, idesc, 1u);
-                        }
-#pragma unroll
-                        for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
-                            const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                            const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
-                            tc::mma_bf16(d, ad_h, bd, idesc2, 1u);
-                            tc::mma_bf16(d, ad_l, bd, idesc, 1u);
-                        }
-                    } else {
-                    // taps u' = 0..15 of each source row: one K = 16 MMA per row (K groups 0, 1)
+                    const uint32_t d = tmem + (uint32_t)(tb * C::TSTRIDE);
+                    // taps u' = 0..15 of each source row: one K = 16 MMA per row and product
 #pragma unroll
                     for (int g = 0; g < G; g++) {
-                        const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]), LBO, SBO_A);
-                        const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]), LBO, SBO_A);
-                        const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]), LBO, SBO_B);
-                        const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[bs][g][1]), LBO, SBO_B);
-                        tc::mma_bf16(d, ad_h, bd_h, idesc, g ? 1u : 0u);
-                        tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
-                        tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
+#pragma unroll
+                        for (int pr = 0; pr < P; pr++) {
+                            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;   // hi*hi, hi*lo, lo*hi
+                            const uint64_t ad = tc::smem_desc(tc::smem_u32(S.a[s][pa][g]), LBO, SBO_A);
+                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][pb]), LBO, SBO_B);
+                            tc::mma_bf16(d, ad, bd, idesc, (g | pr) ? 1u : 0u);
+                        }
                     }
                     // taps 16..23 of two source rows in one K = 16 MMA: K group 0 is group 2
                     // of row g, K group 1 group 2 of row g + 1 (the K-group stride is the
-                    // distance between the two rows' operands)
+                    // distance between the two rows' operands of the same part)
 #pragma unroll
                     for (int g = 0; g < (KS > 16 ? G : 0); g += 2) {
-                        const uint64_t ad_h = tc::smem_desc(tc::smem_u32(S.ahi[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                        const uint64_t ad_l = tc::smem_desc(tc::smem_u32(S.alo[s][g]) + 2 * 128, A_BYTES, SBO_A);
-                        const uint64_t bd_h = tc::smem_desc(tc::smem_u32(S.b[bs][g][0]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
-                        const uint64_t bd_l = tc::smem_desc(tc::smem_u32(S.b[bs][g][1]) + 2 * 128, 2 * C::B_BYTES, SBO_B);
-                        tc::mma_bf16(d, ad_h, bd_h, idesc, 1u);
-                        tc::mma_bf16(d, ad_h, bd_l, idesc, 1u);
-                        tc::mma_bf16(d, ad_l, bd_h, idesc, 1u);
-                    }
+#pragma unroll
+                        for (int pr = 0; pr < P; pr++) {
+                            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+                            const uint64_t ad = tc::smem_desc(tc::smem_u32(S.a[s][pa][g]) + 2 * 128, A_BYTES, SBO_A);
+                            const uint64_t bd = tc::smem_desc(tc::smem_u32(S.b[bs][g][pb]) + 2 * 128,
+                                                              NP * C::B_BYTES, SBO_B);
+                            tc::mma_bf16(d, ad, bd, idesc, 1u);
+                        }
                     }
                     tc::commit(&S.empty[s]);
                     tc::commit(&S.tfull[tb]);
@@ -392,17 +392,18 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
             }
         }
         __syncwarp();
-    } else if (warp < 4) {
-        // ---------------- epilogue: output column x0 + tid of each strip
-        const int m = tid;
+    } else {
+        // ---------------- epilogue: warp w owns output columns x0 + 32 w .. + 31 (TMEM lanes
+        // 32 w ..), one per thread; it stages their observed values and flag bytes itself.
+        const int m = tid, w = warp;
         const float ysc = a.H > 1 ? 2.0f / (float)(a.H - 1) : 0.0f;   // yt = 2 (y + oy) / (H - 1) - 1
         const float yof = a.H > 1 ? -1.0f : 0.0f;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tl = tmem + ((uint32_t)(w * 32) << 16);
         // p_k = xt^i yt^j: the xt^i factor is fixed for a column, so each T column
         // enters the ring already multiplied by it and the ring keeps one sum per
         // power of yt (NJ = degree + 1) instead of one per term
         constexpr int NJ = NK == 1 ? 1 : (NK == 3 ? 2 : 3);
-        constexpr int RL = C::NJB;
+        constexpr int RLP = C::RLP, UNR = C::UNR;
         bool run = true;
         int gb = 0;
         for (int item = blockIdx.x; item < nitems && run; item += gridDim.x) {
@@ -426,118 +427,127 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
             }
             const bool xin = x >= R && x <= a.w - 1 - R;
             const float xp[3] = {1.0f, VAR ? 1.0f : xt, VAR ? 1.0f : xt * xt};
-            float acc[RL][NJ];
+            float acc[RLP][NJ];
 #pragma unroll
-            for (int i = 0; i < RL; i++)
+            for (int i = 0; i < RLP; i++)
 #pragma unroll
                 for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
-            // science values and flag words of the output rows of block blk (rows
-            // blk G - 2R + i) into slots row & (NQ - 1), one cp.async group per block
-            // (the pitch is a multiple of 16, so the flag byte sits at byte x & 3 of its word)
+            // observed values and flag bytes of this warp's columns in the output rows of
+            // block blk (rows blk G - 2R + i) into slots row & (NQ - 1), one cp.async group per
+            // block: lane l copies 16 bytes of values of row l / 8, lanes 0-7 16 flag bytes of
+            // row l / 2 (columns past w are zero-filled)
             auto fetch = [&](int blk) {
-#pragma unroll
-                for (int i = 0; i < G; i++) {
-                    const int eta = blk * G - 2 * R + i;
-                    const bool in = eta >= 0 && eta < nout && x < a.w;
-                    const long p = in ? (long)(y0 + eta) * a.pitch + x : 0;
-                    const int slot = eta & (NQ - 1);
-                    tc::cp_async4(&S.qI[slot][m], obs + p, in ? 4 : 0);
-                    tc::cp_async4(&S.qF[slot][m], a.flags + (p & ~3L), in ? 4 : 0);
+                {
+                    const int i = lane >> 3, c = lane & 7;
+                    const int eta = blk * G - 2 * R + i, X = x0 + 32 * w + 4 * c;
+                    const bool in = eta >= 0 && eta < nout && X < a.w;
+                    const int nb = in ? 4 * min(4, a.w - X) : 0;
+                    tc::cp_async16(&S.qI[w][eta & (NQ - 1)][4 * c], nb ? obs + (long)(y0 + eta) * a.pitch + X : obs, nb);
+                }
+                if (lane < 8) {
+                    const int i = lane >> 1, c = lane & 1;
+                    const int eta = blk * G - 2 * R + i, X = x0 + 32 * w + 16 * c;
+                    const bool in = eta >= 0 && eta < nout && X < a.w;
+                    const int nb = in ? min(16, a.w - X) : 0;
+                    tc::cp_async16(&S.qF[w][eta & (NQ - 1)][16 * c], nb ? a.flags + (long)(y0 + eta) * a.pitch + X : a.flags, nb);
                 }
                 tc::cp_async_commit();
             };
-            const int fsh = 8 * (x & 3);
-            fetch(0);
-            fetch(1);
-            // ring index i holds output row blk G - 2R + i; block blk adds its column (i, k)
-            // at index i, after which indices 0 .. G-1 are complete and the ring shifts by G
+#pragma unroll
+            for (int b = 0; b < LA; b++) fetch(b);
+            // ring: output row blk G - 2R + j of block blk sits in slot (U G + j) mod RLP, U = blk
+            // mod UNR; a block completes the rows in slots U G .. U G + G - 1, which are then
+            // written out and cleared for the rows RLP further down (ROT), or written out
+            // before the ring shifts by G (U = 0)
 #pragma unroll 1
-            for (int blk = 0; blk < nblk; blk++, gb++) {
-                fetch(blk + 2);
-                const int tb = gb % NTB;
-                // lane 0 waits (fewer pollers on the barrier), the warp follows
-                bool ok = true;
-                if (lane == 0) ok = wait_or_abort(S, &S.tfull[tb], (gb / NTB) & 1, status);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) { run = false; break; }
-                tc::fence_after();
-                if constexpr (VAR) {
-                    // column j of the term is the sum of columns j and N + j
-                    constexpr int NCV = C::N / 16;
+            for (int blk0 = 0; blk0 < nblk && run; blk0 += UNR) {
 #pragma unroll
-                    for (int c = 0; c < NCV; c++) {
-                        uint32_t r0[16], r1[16];
-                        tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + c * 16), r0);
-                        tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + C::N + c * 16), r1);
-                        tc::tmem_wait_ld(r0, r1);
+                for (int U = 0; U < UNR; U++) {
+                    const int blk = blk0 + U;
+                    if (blk >= nblk) break;
+                    fetch(blk + LA);
+                    const int tb = gb % NTB;
+                    // lane 0 waits (fewer pollers on the barrier), the warp follows
+                    bool ok = true;
+                    if (lane == 0) ok = wait_or_abort(S, &S.tfull[tb], (gb / NTB) & 1, status);
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) { run = false; break; }
+                    tc::fence_after();
+                    constexpr int NCH = (C::NCOL + 15) / 16;   // 16-column chunks
+                    constexpr int LG = C::ROT ? 3 : 2;          // chunks per TMEM wait (registers)
 #pragma unroll
-                        for (int j = 0; j < 16; j++)
-                            if (c * 16 + j < C::NCOL)
-                                acc[c * 16 + j][0] += __uint_as_float(r0[j]) + __uint_as_float(r1[j]);
-                    }
-                }
-                constexpr int NCH = VAR ? 0 : (C::NCOL + 15) / 16;   // 16-column chunks
+                    for (int c3 = 0; c3 < NCH; c3 += LG) {
+                        uint32_t r[3][16];
 #pragma unroll
-                for (int c3 = 0; c3 < NCH; c3 += 3) {
-                    uint32_t r[3][16];
+                        for (int q = 0; q < 3; q++) {
+                            if (q < LG && c3 + q < NCH) {
+                                tc::tmem_ld16_nowait(tl + (uint32_t)(tb * C::TSTRIDE + (c3 + q) * 16), r[q]);
+                            } else {
 #pragma unroll
-                    for (int q = 0; q < 3; q++) {
-                        if (c3 + q < NCH) {
-                            tc::tmem_ld16_nowait(tl + (uint32_t)(tb * TS + (c3 + q) * 16), r[q]);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 16; j++) r[q][j] = 0u;
-                        }
-                    }
-                    tc::tmem_wait_ld(r[0], r[1], r[2]);
-#pragma unroll
-                    for (int q = 0; q < 3; q++)
-#pragma unroll
-                        for (int j = 0; j < 16; j++) {
-                            const int n = (c3 + q) * 16 + j;
-                            if (n < C::NCOL) {
-                                const int jj = n / NK, k = n - jj * NK;
-                                // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
-                                const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
-                                const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
-                                acc[jj][tj] = fmaf(xp[ti], __uint_as_float(r[q][j]), acc[jj][tj]);
+                                for (int j = 0; j < 16; j++) r[q][j] = 0u;
                             }
                         }
-                }
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&S.tempty[tb]);
-                tc::cp_async_wait<2>();          // this block's science rows have landed
+                        tc::tmem_wait_ld(r[0], r[1], r[2]);
 #pragma unroll
-                for (int i = 0; i < G; i++) {
-                    const int eta = blk * G - 2 * R + i;
-                    if (eta >= 0 && eta < nout && x < a.w) {
-                        const int slot = eta & (NQ - 1);
-                        const float I = S.qI[slot][m];
-                        const uint32_t fl = (S.qF[slot][m] >> fsh) & 0xffu;
-                        const int y = y0 + eta;
-                        const float yt = fmaf((float)(y + a.oy), ysc, yof);
-                        // model = (acc0 + B0) + (acc1 + B1) yt + (acc2 + B2) yt^2
-                        float c2 = B2, c1 = B1;
-                        if constexpr (NJ > 2) c2 += acc[i][2];
-                        if constexpr (NJ > 1) c1 += acc[i][1];
-                        const float model = fmaf(fmaf(c2, yt, c1), yt, acc[i][0] + B0);
-                        const bool inner = xin && y >= R && y <= a.h - 1 - R && fl == 0;
-                        if (VAR) outp[(long)y * a.pitch + x] = inner ? I + acc[i][0] : 0.0f;
-                        else outp[(long)y * a.pitch + x] = inner ? I - model : 0.0f;
+                        for (int q = 0; q < LG; q++)
+#pragma unroll
+                            for (int j = 0; j < 16; j++) {
+                                const int n = (c3 + q) * 16 + j;
+                                if (n < C::NCOL) {
+                                    const int jj = n / NK, k = n - jj * NK;
+                                    // term k of 1, y, y^2, x, x y, x^2 (or 1, y, x) as (i, j)
+                                    const int ti = NK == 6 ? (k < 3 ? 0 : (k < 5 ? 1 : 2)) : (NK == 3 ? (k == 2) : 0);
+                                    const int tj = NK == 6 ? (k < 3 ? k : (k == 4 ? 1 : 0)) : (NK == 3 ? (k == 1) : 0);
+                                    float& dst = acc[(U * G + jj) % RLP][tj];
+                                    dst = VAR ? dst + __uint_as_float(r[q][j]) : fmaf(xp[ti], __uint_as_float(r[q][j]), dst);
+                                }
+                            }
                     }
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&S.tempty[tb]);
+                    tc::cp_async_wait<LA>();         // this block's rows have landed (own copies)
+                    __syncwarp();                    // ... and the other lanes' copies are visible
+#pragma unroll
+                    for (int i = 0; i < G; i++) {
+                        const int eta = blk * G - 2 * R + i;
+                        if (eta >= 0 && eta < nout && x < a.w) {
+                            const int slot = eta & (NQ - 1);
+                            const float I = S.qI[w][slot][lane];
+                            const uint32_t fl = S.qF[w][slot][lane];
+                            const int y = y0 + eta;
+                            const float yt = fmaf((float)(y + a.oy), ysc, yof);
+                            // model = (acc0 + B0) + (acc1 + B1) yt + (acc2 + B2) yt^2
+                            float c2 = B2, c1 = B1;
+                            if constexpr (NJ > 2) c2 += acc[(U * G + i) % RLP][NJ > 2 ? 2 : 0];
+                            if constexpr (NJ > 1) c1 += acc[(U * G + i) % RLP][NJ > 1 ? 1 : 0];
+                            const float a0 = acc[(U * G + i) % RLP][0];
+                            const float model = fmaf(fmaf(c2, yt, c1), yt, a0 + B0);
+                            const bool inner = xin && y >= R && y <= a.h - 1 - R && fl == 0;
+                            if (VAR) outp[(long)y * a.pitch + x] = inner ? I + a0 : 0.0f;
+                            else outp[(long)y * a.pitch + x] = inner ? I - model : 0.0f;
+                        }
+                        if constexpr (C::ROT) {
+#pragma unroll
+                            for (int j = 0; j < NJ; j++) acc[(U * G + i) % RLP][j] = 0.0f;
+                        }
+                    }
+                    if constexpr (!C::ROT) {
+#pragma unroll
+                        for (int i = 0; i + G < RLP; i++)
+#pragma unroll
+                            for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + G][j];
+#pragma unroll
+                        for (int i = RLP - G; i < RLP; i++)
+#pragma unroll
+                            for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
+                    }
+                    gb++;
                 }
-#pragma unroll
-                for (int i = 0; i + G < RL; i++)
-#pragma unroll
-                    for (int j = 0; j < NJ; j++) acc[i][j] = acc[i + G][j];
-#pragma unroll
-                for (int i = RL - G; i < RL; i++)
-#pragma unroll
-                    for (int j = 0; j < NJ; j++) acc[i][j] = 0.0f;
             }
             tc::cp_async_wait<0>();              // the zero-filled fetches past the strip land before
-        }                                        // the next strip's fetches reuse their slots
+            __syncwarp();                        // the next strip's fetches reuse their slots
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -547,20 +557,20 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
 
 template <int KS, int NK, bool VAR>
 int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
-    // the difference image: more than half the shared memory, so one CTA per SM, which
-    // holds all 512 TMEM columns; the variance: two CTAs per SM with 256 columns each
+    // the difference image: more than half the shared memory, so one CTA per SM; the
+    // variance: two CTAs per SM
     size_t smem = sizeof(TcShared<KS, NK, VAR>) + 1024;
     if (!VAR && smem < 116 * 1024) smem = 116 * 1024;
     if (VAR && smem > 113 * 1024) return ARGUS_ERR_UNSUPPORTED;
-    if (cudaFuncSetAttribute(subtract_tc_kernel<KS, NK, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return ARGUS_ERR_CUDA;
+    cudaError_t e = cudaFuncSetAttribute(subtract_tc_kernel<KS, NK, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return argus_cuda_fail(e);
     const int nitems = ((a.w + TCX - 1) / TCX) * ((a.h + TCY - 1) / TCY);
-    // persistent: one CTA per SM walks the strips (the set-up once per SM)
+    // persistent: the CTAs walk the strips (the set-up once per CTA)
     int grid = nitems, dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return ARGUS_ERR_CUDA;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return argus_cuda_fail(e);
     if (grid > (VAR ? 2 : 1) * sms) grid = (VAR ? 2 : 1) * sms;
     subtract_tc_kernel<KS, NK, VAR><<<grid, TC_THREADS, smem, st>>>(a, status); argus_count_launch(1);
     return argus_launch_status();
