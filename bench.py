@@ -64,7 +64,7 @@ def traffic_bytes(rec):
     return int(rec["bytes_per_px"] * W * H)
 
 
-def workload_config(precision="fp32"):
+def workload_config(precision="tf32"):
     return {"workload": f"full-frame plain DIA, {W}x{H} uint16 IMX455 frame + float32 reference",
             "frame": [W, H], "stars": N_STARS, "psf_sigma": "1.3-2.2 px (science), 1.2 px (reference)",
             "kernel": KSIZE, "spatial_degree": SDEG, "bg_degree": BGDEG, "basis": "3 Gaussians x degrees (6,4,2)",
@@ -241,6 +241,13 @@ def run_gpu(args):
     for p, s in zip(pipes[1:], streams[1:]):   # warm the other pipelines too
         p.run(d_raw, calib, d_R, d_Vr, s)
     torch.cuda.synchronize(device)
+    # each in-flight pipeline's frame as one CUDA graph on a side stream of its own
+    gstreams = [torch.cuda.Stream(device) for _ in range(nfl)]
+    graphs, per_frame = [], 0
+    for p, s in zip(pipes, gstreams):
+        g, per_frame = p.capture(d_raw, calib, d_R, d_Vr, s)
+        graphs.append(g)
+    torch.cuda.synchronize(device)
 
     # timed region: K steps, frame i on pipeline and stream i mod nfl
     t0 = torch.cuda.Event(enable_timing=True)
@@ -249,23 +256,17 @@ def run_gpu(args):
         if args.clocks else None
     barrier(dist, device)
     torch.cuda.synchronize(device)
-    n0 = B.argus_launch_count()
     t0.record(stream)
-    for s in streams[1:]:
+    for s in gstreams:
         s.wait_event(t0)
     for i in range(args.steps):
-        p, s = pipes[i % nfl], streams[i % nfl]
-        p.calibrate(d_raw, calib, s)
-        p.select_stamps(d_R, s)
-        p.fit(d_R, s)
-        p.subtract_variance(d_Vr, s)
-        p.subtract_difference(d_R, d_Vr, s)
-        p.detect(s)
-    for s in streams[1:]:
+        with torch.cuda.stream(gstreams[i % nfl]):
+            graphs[i % nfl].replay()
+    for s in gstreams:
         stream.wait_stream(s)
     t1.record(stream)
     torch.cuda.synchronize(device)
-    launches = B.argus_launch_count() - n0
+    launches = per_frame * args.steps   # graph replays: the frame's launches, counted at capture
     barrier(dist, device)
     clk = clocks.stop() if clocks else None
     elapsed = t0.elapsed_time(t1) / 1e3
@@ -305,22 +306,32 @@ def run_gpu(args):
     out_host = [torch.empty(pipe.sources.numel(), dtype=torch.uint8).pin_memory() for _ in range(nfl)]
     nf_hosts = [torch.empty(4, dtype=torch.int32).pin_memory() for _ in range(nfl)]
     ke = max(3, args.steps // 4)
+    # one graph per in-flight pipeline: pinned raw frame in, the frame, sources and count out
+    egraphs = []
+    for j, (p, s) in enumerate(zip(pipes, gstreams)):
+        def pre(j=j):
+            d_raws[j].copy_(raw_host, non_blocking=True)
+
+        def post(j=j, p=p):
+            nf_hosts[j].copy_(p.n_found, non_blocking=True)
+            out_host[j].copy_(p.sources, non_blocking=True)
+        with torch.cuda.stream(s):
+            pre()
+            p.run(d_raws[j], calib, d_R, d_Vr, s)
+            post()
+        torch.cuda.synchronize(device)
+        egraphs.append(p.capture(d_raws[j], calib, d_R, d_Vr, s, pre=pre, post=post)[0])
     barrier(dist, device)
     torch.cuda.synchronize(device)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for s in streams[1:]:
+    for s in gstreams:
         s.wait_event(e0)
     for i in range(ke):
-        j = i % nfl
-        p, s = pipes[j], streams[j]
-        with torch.cuda.stream(s):
-            d_raws[j].copy_(raw_host, non_blocking=True)
-            p.run(d_raws[j], calib, d_R, d_Vr, s)
-            nf_hosts[j].copy_(p.n_found, non_blocking=True)
-            out_host[j].copy_(p.sources, non_blocking=True)
-    for s in streams[1:]:
+        with torch.cuda.stream(gstreams[i % nfl]):
+            egraphs[i % nfl].replay()
+    for s in gstreams:
         stream.wait_stream(s)
     e1.record(stream)
     nf_host = nf_hosts[(ke - 1) % nfl]
@@ -368,7 +379,8 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**workload_config(args.precision), "frames_in_flight": nfl},
+        "config": {**workload_config(args.precision), "frames_in_flight": nfl,
+                   "launch": "each frame one CUDA graph replay (captured once per in-flight pipeline)"},
         # the dominant kernel of the step (the larger of the two subtraction kernels)
         "roofline": dict(kernels["subtract_tc"] if tc_ms >= var_ms else kernels["variance"]),
         "kernels": kernels,
@@ -954,7 +966,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16_split"])
+    # TF32 normal equations on the tensor cores by default: they meet the 1e-3 kernel-pixel bar
+    # on the full frame; --precision fp32 / bf16 / bf16_split select the others
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16", "bf16_split"])
     ap.add_argument("--band-rows", type=int, default=48)
     ap.add_argument("--frames-in-flight", type=int, default=2,
                     help="frames processed concurrently, each on its own pipeline and stream")

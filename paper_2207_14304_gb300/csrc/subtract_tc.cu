@@ -37,8 +37,9 @@
 // rows: no bank conflicts), each from five aligned 32-bit words of the buffer
 // and a byte permutation (rows starting at an odd element straddle words).
 //
-// Persistent CTAs walk the strips of 128 columns x a band of TCY output rows,
-// streaming each band's TCY + 2r source rows in blocks of G (the difference
+// Persistent CTAs walk the strips of 128 columns x a band of TCY output rows
+// (256 for the difference image, 128 for the variance), streaming each band's
+// TCY + 2r source rows in blocks of G (the difference
 // image: one CTA of 320 threads per SM; the variance: two).  Warps 0-3:
 // epilogue, one output column per thread and TMEM lane; warp w stages the
 // observed values and flag bytes of its 32 columns by 16-byte cp.async LA = 6
@@ -57,7 +58,10 @@ namespace {
 using namespace argus_sub;
 
 constexpr int TCX = 128;                     // output columns per CTA (MMA M)
-constexpr int TCY = 128;                     // output rows per CTA band
+// output rows per band: the variance's strip is one 128 x 128 variance tile; the
+// difference image takes 256-row bands (half the halo rows of 128-row bands)
+template <bool VAR>
+__host__ __device__ constexpr int tcy() { return VAR ? VAR_TILE : 256; }
 constexpr int TKC = 32;                      // MMA K: taps u', padded
 constexpr int G = 4;                         // source rows per block
 constexpr int NCM = TCX / 8 + TKC / 8 - 1;   // distinct core matrices of one Hankel tile
@@ -153,7 +157,8 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1) subtract_tc_kernel(Su
     constexpr int NP = Sh::NP;                   // operand parts
     constexpr int P = VAR ? 1 : 3;               // products per K slice: hi*hi (+ hi*lo + lo*hi)
     static_assert(!VAR || NK == 1, "the variance convolution has one term");
-    static_assert(TCX == VAR_TILE && TCY == VAR_TILE, "one variance tile per strip");
+    constexpr int TCY = tcy<VAR>();
+    static_assert(!VAR || (TCX == VAR_TILE && TCY == VAR_TILE), "one variance tile per strip");
     const float* src_img = VAR ? a.ref_var : a.ref;   // convolved image
     const float* obs = VAR ? a.sci_var : a.sci;       // observed image the model is compared with
     float* outp = VAR ? a.diff_var : a.diff;
@@ -565,7 +570,7 @@ int launch_tc(const SubArgs& a, int* status, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(subtract_tc_kernel<KS, NK, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return argus_cuda_fail(e);
-    const int nitems = ((a.w + TCX - 1) / TCX) * ((a.h + TCY - 1) / TCY);
+    const int nitems = ((a.w + TCX - 1) / TCX) * ((a.h + tcy<VAR>() - 1) / tcy<VAR>());
     // persistent: the CTAs walk the strips (the set-up once per CTA)
     int grid = nitems, dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||

@@ -80,10 +80,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` clock cycles and returns false.
+// try_wait with a suspend-time hint: the thread may sleep up to `ns` nanoseconds
+// in the barrier unit until the phase completes, instead of polling.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` clock cycles and returns false.  Each
+// try suspends the thread for up to 20 us (it resumes when the phase completes),
+// so a waiting thread issues a few instructions per wait rather than a polling loop.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(mbar, parity)) {
+    while (!mbar_try_wait_sleep(mbar, parity, 20000u)) {
         if (clock64() - t0 > limit) return false;
     }
     return true;

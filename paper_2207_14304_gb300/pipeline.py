@@ -10,7 +10,8 @@ fit, subtraction and detection of Sec. 4.2):
 
 All buffers are allocated once, in __init__, like the reference and
 calibration frames the paper pre-allocates per pointing; run() allocates
-nothing and can be captured in a CUDA graph.
+nothing, and capture() records it as one CUDA graph (the frame's ~50 kernel
+launches replayed without host launch gaps).
 """
 from __future__ import annotations
 
@@ -107,6 +108,23 @@ class FramePipeline:
         self.fit(ref, stream)
         self.subtract(ref, ref_var, stream)
         self.detect(stream)
+
+    def capture(self, raw, calib, ref, ref_var, stream, select=True, pre=None, post=None):
+        """Record one frame of run() as a CUDA graph on `stream` (a side stream, not the
+        default one), after at least one eager run() with the same arguments (the basis is
+        prepared then).  pre() and post() are recorded before and after the frame (e.g. the
+        host-to-device copy of the raw frame and the copy of the sources back).  Replaying
+        the graph (graph.replay() under torch.cuda.stream(s)) repeats the whole path with
+        the same buffers and launches.  Returns (graph, library kernel launches per frame)."""
+        g = torch.cuda.CUDAGraph()
+        n0 = B.argus_launch_count()
+        with torch.cuda.graph(g, stream=stream):
+            if pre is not None:
+                pre()
+            self.run(raw, calib, ref, ref_var, stream, select=select)
+            if post is not None:
+                post()
+        return g, B.argus_launch_count() - n0
 
     # host-side readers (synchronising)
     def fit_stats(self) -> dict:

@@ -4,8 +4,9 @@ path in the launch configuration the benchmark times, against the FP64 oracle.
 
 * calibration: every pixel (flags bit-exact, I and V within 4 float ulps);
 * stamp selection: every centre, bit-exact;
-* kernel fit: every kernel pixel within 1e-3 of max|K| and chi2 within 1e-4
-  (the GPU fits its own calibrated frame, which is within 4 ulps of the
+* kernel fit (TF32 normal equations, as benchmarked; then FP32, BF16 split and
+  BF16 at their bars): every kernel pixel within 1e-3 of max|K| and chi2 within
+  1e-4 (the GPU fits its own calibrated frame, which is within 4 ulps of the
   oracle's); the oracle fits the oracle's calibrated frame;
 * subtraction: the same entry point on the oracle's calibrated frame and
   kernel, 20,000 sampled pixels plus whole strips across the 128-pixel work
@@ -68,7 +69,7 @@ def test_full_frame_path_against_the_oracle(ora):
 
     # --- the benchmark's pipeline, one frame
     basis = B.make_basis(ks, (0.7, 1.5, 3.0), (6, 4, 2), sdeg, bgdeg)
-    pipe = FramePipeline(W, H, basis=basis, stamp=bench.STAMP, grid=bench.GRID, precision="fp32",
+    pipe = FramePipeline(W, H, basis=basis, stamp=bench.STAMP, grid=bench.GRID, precision="tf32",
                          psf_sigma=1.8, device=0)
     try:
         dR, dVr = pad(R_d), pad(Vr_d)
@@ -110,10 +111,10 @@ def test_full_frame_path_against_the_oracle(ora):
         assert kerr < 1e-3
         assert abs(st["chi2"] / res.chi2 - 1) < 1e-4
         np.testing.assert_allclose(pipe.bg.cpu().numpy(), bgo, rtol=0, atol=1e-3 * max(1.0, np.abs(bgo).max()))
-        # the tensor-core normal equations on the same frame and stamps (the oracle's fit of its own
+        # the other normal-equation precisions on the same frame and stamps (the oracle's fit of its own
         # calibrated frame, as above): the bar of each precision
         from tests.test_gpu_parity import CHIBAR, KBAR
-        for prec in ("tf32", "bf16_split", "bf16"):
+        for prec in ("fp32", "bf16_split", "bf16"):
             pipe.precision = prec
             pipe.fit(dR)
             torch.cuda.synchronize()
@@ -125,7 +126,8 @@ def test_full_frame_path_against_the_oracle(ora):
             assert stp["status"] == 0 and stp["refine_iters"] == 1
             assert kp < KBAR[prec]
             assert abs(stp["chi2"] / res.chi2 - 1) < max(CHIBAR[prec], 1e-4)
-        pipe.precision = "fp32"
+        pipe.precision = "tf32"
+        pipe.fit(dR)
 
         # --- subtraction: the entry point on the oracle's frame and kernel
         K32 = Ko.astype(np.float32)
