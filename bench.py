@@ -970,7 +970,7 @@ def main(argv=None):
     # on the full frame; --precision fp32 / bf16 / bf16_split select the others
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16", "bf16_split"])
     ap.add_argument("--band-rows", type=int, default=48)
-    ap.add_argument("--frames-in-flight", type=int, default=2,
+    ap.add_argument("--frames-in-flight", type=int, default=3,
                     help="frames processed concurrently, each on its own pipeline and stream")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")

@@ -1295,6 +1295,39 @@ __global__ void __launch_bounds__(256) refine_update_kernel(double* a, const dou
     }
 }
 
+// chi^2 of the refined solution c + delta from the first residual pass, without a
+// second pass over the design rows: with r = C^T W (I - C c),
+//   chi^2(c + delta) = chi^2(c) - 2 delta.r + delta^T M delta
+// (M the Gram the solves used; delta is small, so its rounding enters only at
+// second order).  chi_n[0..1] = (chi^2, n) of c; out[0..1] the same for c + delta
+// (unchanged when no step was applied).  One CTA, FP64 sums in a fixed order.
+__global__ void __launch_bounds__(256) chi2_update_kernel(const double* M, int ld, int Nc, const double* r,
+                                                          const double* delta, const double* chi_n,
+                                                          const double* flag, double* out) {
+    __shared__ double red[256];
+    if (flag[0] != 0.0) return;
+    const bool applied = flag[3] > 0.0;
+    double acc = 0.0;
+    if (applied) {
+        for (int i = threadIdx.x; i < Nc; i += blockDim.x) {
+            const double* Mi = M + (long)i * ld;
+            double q = 0.0;
+            for (int j = 0; j < Nc; j++) q = fma(Mi[j], delta[j], q);
+            acc += delta[i] * (q - 2.0 * r[i]);
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = chi_n[0] + red[0];
+        out[1] = chi_n[1];
+    }
+}
+
 // Map the solution c of the orthonormalised basis back to Alard-Lupton
 // coefficients (a_{n,k} = sum_m S[n][m] c_{m,k}, FP64) and write the stats.
 __global__ void finalize_kernel(BasisDev b, const double* c, const double* S, const double* flag,
@@ -1815,6 +1848,7 @@ void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, d
 // C^T W (I - C c) from the FP32 design and FP64 sums; its relative size is
 // reported as max_step.
 constexpr int REFINE_MAX = 1;
+static_assert(REFINE_MAX == 1, "chi2_update_kernel takes r and delta of the first iterate");
 
 extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* sci_var, const float* ref,
                                 const uint8_t* flags, argus_shape shape, const int* centers,
@@ -1959,8 +1993,8 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         argus_tri_solve(ctx, NP, n, rv, 1, dl, st);
         refine_update_kernel<<<1, 256, 0, st>>>(c, dl, n, flag); argus_count_launch(1);
     }
-    resid_kernel<<<nparts, RT, rsmem, st>>>(g, ctx->rowmeta, c, flag, 0, ctx->resid_part); argus_count_launch(1);
-    resid_reduce_kernel<<<rr_blocks, 256, 0, st>>>(ctx->resid_part, nparts, NP, 0, rv, chif, flag, 0); argus_count_launch(1);
+    // chi^2 of the refined solution from the first residual pass (rv = r of c, dl = delta)
+    chi2_update_kernel<<<1, 256, 0, st>>>(ctx->M, NP, n, rv, dl, chi0, flag, chif); argus_count_launch(1);
     finalize_kernel<<<1, 256, 0, st>>>(d, c, ctx->basis_S, flag, chi0, chif, max_stamps, n_stamps, centers, stamp,
                                        shape.w, shape.h, precision, coeffs, stats); argus_count_launch(1);
     return argus_launch_status();
