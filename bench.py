@@ -245,7 +245,10 @@ def run_gpu(args):
     gstreams = [torch.cuda.Stream(device) for _ in range(nfl)]
     graphs, per_frame = [], 0
     for p, s in zip(pipes, gstreams):
-        g, per_frame = p.capture(d_raw, calib, d_R, d_Vr, s)
+        with torch.cuda.stream(s):
+            (p.run_fused if args.fused else p.run)(d_raw, calib, d_R, d_Vr, s)
+        torch.cuda.synchronize(device)
+        g, per_frame = p.capture(d_raw, calib, d_R, d_Vr, s, fused=args.fused)
         graphs.append(g)
     torch.cuda.synchronize(device)
 
@@ -317,10 +320,10 @@ def run_gpu(args):
             out_host[j].copy_(p.sources, non_blocking=True)
         with torch.cuda.stream(s):
             pre()
-            p.run(d_raws[j], calib, d_R, d_Vr, s)
+            (p.run_fused if args.fused else p.run)(d_raws[j], calib, d_R, d_Vr, s)
             post()
         torch.cuda.synchronize(device)
-        egraphs.append(p.capture(d_raws[j], calib, d_R, d_Vr, s, pre=pre, post=post)[0])
+        egraphs.append(p.capture(d_raws[j], calib, d_R, d_Vr, s, pre=pre, post=post, fused=args.fused)[0])
     barrier(dist, device)
     torch.cuda.synchronize(device)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -380,7 +383,9 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": round(tmax / args.steps * 1e3, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {**workload_config(args.precision), "frames_in_flight": nfl,
-                   "launch": "each frame one CUDA graph replay (captured once per in-flight pipeline)"},
+                   "launch": ("each frame one argus_dia_frame call" if args.fused
+                              else "each frame the separate calls argus_calibrate .. argus_detect")
+                             + ", captured once per in-flight pipeline as a CUDA graph and replayed"},
         # the dominant kernel of the step (the larger of the two subtraction kernels)
         "roofline": dict(kernels["subtract_tc"] if tc_ms >= var_ms else kernels["variance"]),
         "kernels": kernels,
@@ -972,6 +977,8 @@ def main(argv=None):
     ap.add_argument("--band-rows", type=int, default=48)
     ap.add_argument("--frames-in-flight", type=int, default=3,
                     help="frames processed concurrently, each on its own pipeline and stream")
+    ap.add_argument("--no-fused", dest="fused", action="store_false",
+                    help="capture the separate calls (argus_calibrate .. argus_detect) instead of argus_dia_frame")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-clocks", dest="clocks", action="store_false")

@@ -240,6 +240,35 @@ int argus_detect(argus_ctx *ctx, const float *diff, const float *diff_var, const
                  argus_shape shape, float nsigma, float psf_sigma, uint8_t *mask,
                  argus_source *out, int cap, int *n_found, argus_stream stream);
 
+/* The whole per-frame reduction of one raw frame in one call (paper Sec. 4:
+ * calibration, then the subtraction and detection of transient candidates of
+ * Sec. 4.2; the frame stays on the GPU from the raw copy to the source list,
+ * with reference and calibration frames resident per pointing, Sec. 3.2):
+ *   argus_calibrate -> argus_select_stamps -> argus_fit_kernel ->
+ *   argus_expand_kernel -> difference variance -> difference image -> detection,
+ * with the same arguments and results as those calls made in turn, frame
+ * coordinates equal to image coordinates (frame_w = w, ox = oy = 0) and
+ * max_stamps = grid_x * grid_y.  One stream, no host round trip between the
+ * steps; the call allocates nothing and can be captured in a CUDA graph.
+ *   raw, calib: as argus_calibrate; ref, ref_var: the reference and its
+ *     variance (float [h][pitch]);
+ *   grid_x, grid_y, stamp, max_peak, iso, iso_frac: stamp selection (khalf =
+ *     basis->ksize / 2); basis, precision: the fit; nsigma, psf_sigma: detection;
+ *   outputs (device, caller-owned, all [h][pitch] unless stated): img, var,
+ *     flags (calibrated frame); centers int [grid_x*grid_y][2], n_stamps int;
+ *     coeffs double [Nc], stats (argus_fit_stats); K float [Ks][ksize][ksize],
+ *     bg double [Kb]; diff, diff_var; mask uint8; out argus_source [cap],
+ *     n_found int.
+ * Returns the first error of the calls it makes (argument errors synchronously;
+ * device-detected ones through argus_sync_status); nothing after a failing step
+ * is enqueued. */
+int argus_dia_frame(argus_ctx *ctx, const uint16_t *raw, argus_shape shape, const argus_calib *calib,
+                    const float *ref, const float *ref_var, int grid_x, int grid_y, int stamp, float max_peak,
+                    int iso, float iso_frac, const argus_basis *basis, int precision, float nsigma,
+                    float psf_sigma, float *img, float *var, uint8_t *flags, int *centers, int *n_stamps,
+                    double *coeffs, argus_fit_stats *stats, float *K, double *bg, float *diff, float *diff_var,
+                    uint8_t *mask, argus_source *out, int cap, int *n_found, argus_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Batched segments (paper Sec. 5: subtraction parallelised over image
  * segments; Sec. 4.1.1: HEALPix segments).  Many square cutouts of uneven size

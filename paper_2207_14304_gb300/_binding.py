@@ -115,6 +115,8 @@ SIGNATURES = {
     "argus_expand_kernel": ([P, C.POINTER(argus_basis), P, P, P, P], I),
     "argus_subtract": ([P, P, P, P, P, P, SH, I, I, I, I, I, I, P, I, P, P, P, P], I),
     "argus_detect": ([P, P, P, P, SH, F, F, P, P, I, P, P], I),
+    "argus_dia_frame": ([P, P, SH, C.POINTER(argus_calib), P, P, I, I, I, F, I, F, C.POINTER(argus_basis), I, F, F,
+                         P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, P], I),
     "argus_select_stamps_noalloc": ([P, P, SH, I, I, I, I, F, I, F, P, P, P], I),
     "argus_segments_plan": ([P, C.POINTER(argus_segment), I, I, I, C.POINTER(argus_basis),
                              C.POINTER(argus_seg_config), C.POINTER(P)], I),
@@ -418,6 +420,18 @@ def argus_detect(ctx, diff, diff_var, flags, shape, nsigma, psf_sigma, mask, out
     _check(load().argus_detect(ctx, _ptr(diff), _ptr(diff_var), _ptr(flags), shape, float(nsigma),
                                float(psf_sigma), _ptr(mask), _ptr(out), int(cap), _ptr(n_found),
                                _stream(stream)), "argus_detect")
+
+
+def argus_dia_frame(ctx, raw, shape, calib, ref, ref_var, grid_x, grid_y, stamp, max_peak, iso, iso_frac, basis,
+                    precision, nsigma, psf_sigma, img, var, flags, centers, n_stamps, coeffs, stats, K, bg, diff,
+                    diff_var, mask, out, cap, n_found, stream=None):
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    _check(load().argus_dia_frame(ctx, _ptr(raw), shape, C.byref(calib), _ptr(ref), _ptr(ref_var), int(grid_x),
+                                  int(grid_y), int(stamp), float(max_peak), int(iso), float(iso_frac),
+                                  C.byref(basis), prec, float(nsigma), float(psf_sigma), _ptr(img), _ptr(var),
+                                  _ptr(flags), _ptr(centers), _ptr(n_stamps), _ptr(coeffs), _ptr(stats), _ptr(K),
+                                  _ptr(bg), _ptr(diff), _ptr(diff_var), _ptr(mask), _ptr(out), int(cap),
+                                  _ptr(n_found), _stream(stream)), "argus_dia_frame")
 
 
 def argus_minipix(ctx, img, shape, cell, targets, n_targets, sources, n_sources, sources_cap, keep, out,

@@ -100,6 +100,14 @@ class FramePipeline:
         B.argus_detect(self.ctx, self.diff, self.diff_var, self.flags, self.shape, self.nsigma,
                        self.psf_sigma, self.mask, self.sources, self.src_cap, self.n_found, stream)
 
+    def run_fused(self, raw, calib, ref, ref_var, stream=None):
+        """The same frame through argus_dia_frame: one library call for the whole path."""
+        B.argus_dia_frame(self.ctx, raw, self.shape, calib, ref, ref_var, self.grid[0], self.grid[1], self.stamp,
+                          self.max_peak, self.iso, self.iso_frac, self.basis, self.precision, self.nsigma,
+                          self.psf_sigma, self.img, self.var, self.flags, self.centers, self.n_stamps, self.coeffs,
+                          self.stats, self.K, self.bg, self.diff, self.diff_var, self.mask, self.sources,
+                          self.src_cap, self.n_found, stream)
+
     def run(self, raw, calib, ref, ref_var, stream=None, select=True):
         """One frame through the whole path; all outputs stay on the device."""
         self.calibrate(raw, calib, stream)
@@ -109,19 +117,23 @@ class FramePipeline:
         self.subtract(ref, ref_var, stream)
         self.detect(stream)
 
-    def capture(self, raw, calib, ref, ref_var, stream, select=True, pre=None, post=None):
+    def capture(self, raw, calib, ref, ref_var, stream, select=True, pre=None, post=None, fused=False):
         """Record one frame of run() as a CUDA graph on `stream` (a side stream, not the
         default one), after at least one eager run() with the same arguments (the basis is
         prepared then).  pre() and post() are recorded before and after the frame (e.g. the
         host-to-device copy of the raw frame and the copy of the sources back).  Replaying
         the graph (graph.replay() under torch.cuda.stream(s)) repeats the whole path with
-        the same buffers and launches.  Returns (graph, library kernel launches per frame)."""
+        the same buffers and launches; fused=True records run_fused (argus_dia_frame) instead.
+        Returns (graph, library kernel launches per frame)."""
         g = torch.cuda.CUDAGraph()
         n0 = B.argus_launch_count()
         with torch.cuda.graph(g, stream=stream):
             if pre is not None:
                 pre()
-            self.run(raw, calib, ref, ref_var, stream, select=select)
+            if fused:
+                self.run_fused(raw, calib, ref, ref_var, stream)
+            else:
+                self.run(raw, calib, ref, ref_var, stream, select=select)
             if post is not None:
                 post()
         return g, B.argus_launch_count() - n0

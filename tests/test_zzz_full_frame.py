@@ -171,5 +171,24 @@ def test_full_frame_path_against_the_oracle(ora):
         assert nf <= pipe.src_cap and nf > 0
         n_p, n_n = check_detection_properties(D, VD, g_fl, mask, src, nf, pipe.nsigma)
         print(f"[full frame] sources {nf} (+{n_p} / -{n_n})")
+        del D, VD, mask
+
+        # --- the one-call path the benchmark captures (argus_dia_frame): bit for bit the separate
+        # calls' outputs
+        fused = FramePipeline(W, H, basis=basis, stamp=bench.STAMP, grid=bench.GRID, precision="tf32",
+                              psf_sigma=1.8, device=0)
+        try:
+            pipe.precision = "tf32"
+            pipe.run(pad(torch.from_numpy(raw).to(device)), calib, dR, dVr)
+            fused.run_fused(pad(torch.from_numpy(raw).to(device)), calib, dR, dVr)
+            torch.cuda.synchronize()
+            assert fused.status() == 0
+            for name in ("coeffs", "diff", "diff_var", "mask"):
+                assert torch.equal(getattr(pipe, name), getattr(fused, name)), name
+            s1, n1 = pipe.sources_host()
+            s2, n2 = fused.sources_host()
+            assert n1 == n2 and s1.tobytes() == s2.tobytes()
+        finally:
+            fused.close()
     finally:
         pipe.close()
