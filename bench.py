@@ -46,10 +46,10 @@ BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
 # launch, scaled by pixels to the frame (the kernel streams its bands once, so traffic
 # grows in proportion).  It holds only for the kernel sources it was taken on (None
 # until a capture of these sources is recorded here).
-SUBTRACT_TRAFFIC = {"bytes_per_px": 11.5154, "sources_sha1": "bf8c44811104a0a5ce56f7206e58459da9e30684",
+SUBTRACT_TRAFFIC = {"bytes_per_px": 11.4330, "sources_sha1": "742991b03a7e077a2df7c354b361e8e70989f863",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh")}
 # the same for the difference-variance kernel (V_I, V_ref and flags in, V_D out)
-VARIANCE_TRAFFIC = {"bytes_per_px": 11.6997, "sources_sha1": "e2edd1ccf124b72064e8c94007fe20a68077f31d",
+VARIANCE_TRAFFIC = {"bytes_per_px": 11.4742, "sources_sha1": "22be4cba892a1156e31bc5d354f56b8d3e1e3b01",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh", "subtract.cu")}
 
 

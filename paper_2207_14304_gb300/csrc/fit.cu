@@ -1300,30 +1300,32 @@ __global__ void __launch_bounds__(256) refine_update_kernel(double* a, const dou
 //   chi^2(c + delta) = chi^2(c) - 2 delta.r + delta^T M delta
 // (M the Gram the solves used; delta is small, so its rounding enters only at
 // second order).  chi_n[0..1] = (chi^2, n) of c; out[0..1] the same for c + delta
-// (unchanged when no step was applied).  One CTA, FP64 sums in a fixed order.
-__global__ void __launch_bounds__(256) chi2_update_kernel(const double* M, int ld, int Nc, const double* r,
-                                                          const double* delta, const double* chi_n,
-                                                          const double* flag, double* out) {
-    __shared__ double red[256];
+// (unchanged when no step was applied).  One CTA of 32 warps, a warp per row of M,
+// FP64 sums in a fixed order.
+__global__ void __launch_bounds__(1024) chi2_update_kernel(const double* M, int ld, int Nc, const double* r,
+                                                           const double* delta, const double* chi_n,
+                                                           const double* flag, double* out) {
+    __shared__ double red[32];
     if (flag[0] != 0.0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool applied = flag[3] > 0.0;
-    double acc = 0.0;
+    double acc = 0.0;   // lane 0 of each warp: its rows' delta_i (M delta - 2 r)_i
     if (applied) {
-        for (int i = threadIdx.x; i < Nc; i += blockDim.x) {
+        for (int i = warp; i < Nc; i += 32) {   // one warp per row, lanes along the row
             const double* Mi = M + (long)i * ld;
             double q = 0.0;
-            for (int j = 0; j < Nc; j++) q = fma(Mi[j], delta[j], q);
+            for (int j = lane; j < Nc; j += 32) q = fma(Mi[j], delta[j], q);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
             acc += delta[i] * (q - 2.0 * r[i]);
         }
     }
-    red[threadIdx.x] = acc;
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        out[0] = chi_n[0] + red[0];
+        double t = 0.0;
+        for (int w = 0; w < 32; w++) t += red[w];
+        out[0] = chi_n[0] + t;
         out[1] = chi_n[1];
     }
 }
@@ -1994,7 +1996,7 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
         refine_update_kernel<<<1, 256, 0, st>>>(c, dl, n, flag); argus_count_launch(1);
     }
     // chi^2 of the refined solution from the first residual pass (rv = r of c, dl = delta)
-    chi2_update_kernel<<<1, 256, 0, st>>>(ctx->M, NP, n, rv, dl, chi0, flag, chif); argus_count_launch(1);
+    chi2_update_kernel<<<1, 1024, 0, st>>>(ctx->M, NP, n, rv, dl, chi0, flag, chif); argus_count_launch(1);
     finalize_kernel<<<1, 256, 0, st>>>(d, c, ctx->basis_S, flag, chi0, chif, max_stamps, n_stamps, centers, stamp,
                                        shape.w, shape.h, precision, coeffs, stats); argus_count_launch(1);
     return argus_launch_status();
