@@ -130,8 +130,11 @@ __global__ void cnn_out_kernel(const float* h5, const WT* w, float* y, int n) {
     }
 }
 
-// loss = mean (y - t)^2 (accumulated in FP64), dy = 2 (y - t) / n_total
-__global__ void cnn_mse_kernel(const float* y, const float* t, long n, float* dy, double* loss) {
+// loss = mean (y - t)^2 (accumulated in FP64), dy = 2 (y - t) / n_total; each block
+// writes its partial sum to part[blockIdx.x] (reduced in a fixed order afterwards)
+__global__ void __launch_bounds__(256) cnn_mse_kernel(const float* y, const float* t, long n, float* dy,
+                                                      double* part) {
+    __shared__ double red[8];
     double s = 0.0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const float d = y[i] - t[i];
@@ -140,13 +143,37 @@ __global__ void cnn_mse_kernel(const float* y, const float* t, long n, float* dy
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (double)n);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) v += red[w8];
+        part[blockIdx.x] = v / (double)n;
+    }
+}
+
+__global__ void cnn_sum_d_kernel(const double* part, int nb, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double v = 0.0;
+        for (int b = 0; b < nb; b++) v += part[b];
+        *out = v;
+    }
+}
+
+// dst[e] = sum over b < nb of part[b * width + e], in the order of b (the per-CTA
+// partial gradients reduced without atomics, so training is bit-reproducible)
+__global__ void cnn_reduce_kernel(const float* part, int nb, long width, float* dst) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < width; e += (long)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        for (int b = 0; b < nb; b++) v += part[(long)b * width + e];
+        dst[e] = v;
+    }
 }
 
 // dh5 = W6 dy; grad W6 += sum dy h5; grad b6 += sum dy
 template <typename WT>
 __global__ void __launch_bounds__(256) cnn_out_bwd_kernel(const float* h5, const float* dy, const WT* w, float* dh5,
-                                                          float* grad, int n) {
+                                                          float* part, int n) {
     __shared__ float red[8][C + 1];
     float gw[C + 1];
 #pragma unroll
@@ -170,10 +197,10 @@ __global__ void __launch_bounds__(256) cnn_out_bwd_kernel(const float* h5, const
         if (lane == 0) red[wid][c] = v;
     }
     __syncthreads();
-    if (threadIdx.x <= C) {
+    if (threadIdx.x <= C) {   // this block's (W6, b6) partial: part[blockIdx.x][C + 1]
         float v = 0.0f;
         for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) v += red[w8][threadIdx.x];
-        atomicAdd(grad + (threadIdx.x < C ? OFF_W6 + threadIdx.x : OFF_B6), v);
+        part[(long)blockIdx.x * (C + 1) + threadIdx.x] = v;
     }
 }
 
@@ -241,8 +268,12 @@ __global__ void __launch_bounds__(256) cnn_conv7_dgrad_kernel(const float* dh_ou
 // weight gradient of a conv7 layer for one kernel row ky (blockIdx.y):
 // dW[ky][kx][i][o] = sum_{img,y,x} in[y+ky-3][x+kx-3][i] dz[y][x][o], db[o] = sum dz[o].
 // 448 threads: (kx, 4 input channels, 4 output channels) each; images in chunks per CTA.
+// Each CTA (chunk bx of images, kernel row ky) writes its sums to its own partial slot
+// part[bx][ky * KS * C * C .. + KS * C * C) (and the bias partial at [bx][49 C C ..] for
+// ky = 0); the slots are reduced in a fixed order afterwards.
+constexpr long WPART = 49L * 1024 + 32;   // one layer's weights and biases
 __global__ void __launch_bounds__(448) cnn_conv7_wgrad_kernel(const float* hin, const float* dh_out,
-                                                              const float* h_out, float* gW, float* gb, int n,
+                                                              const float* h_out, float* part, int n,
                                                               int per_cta) {
     extern __shared__ __align__(16) float sm[];
     float* pad = sm;                                 // input, zero padded
@@ -285,19 +316,20 @@ __global__ void __launch_bounds__(448) cnn_conv7_wgrad_kernel(const float* hin, 
         }
     }
     if (kx < KS) {
+        float* gW = part + (long)blockIdx.x * WPART;
 #pragma unroll
         for (int a = 0; a < 4; a++)
 #pragma unroll
             for (int c = 0; c < 4; c++)
-                atomicAdd(gW + ((long)(ky * KS + kx) * C + i4 * 4 + a) * C + o4 * 4 + c, acc[a][c]);
+                gW[((long)(ky * KS + kx) * C + i4 * 4 + a) * C + o4 * 4 + c] = acc[a][c];
         if (ky == 0 && kx == 0 && i4 == 0)
 #pragma unroll
-            for (int c = 0; c < 4; c++) atomicAdd(gb + o4 * 4 + c, accb[c]);
+            for (int c = 0; c < 4; c++) gW[49L * 1024 + o4 * 4 + c] = accb[c];
     }
 }
 
 // layer 1 (linear): grad W1[o][j] += sum x[q][j] dh1[q][o], grad b1[o] += sum dh1[q][o]
-__global__ void __launch_bounds__(256) cnn_in_bwd_kernel(const float* x, const float* dh1, float* grad, int n) {
+__global__ void __launch_bounds__(256) cnn_in_bwd_kernel(const float* x, const float* dh1, float* part, int n) {
     __shared__ float red[8][3 * C];
     float g[3 * C];
 #pragma unroll
@@ -322,11 +354,10 @@ __global__ void __launch_bounds__(256) cnn_in_bwd_kernel(const float* x, const f
         if (lane == 0) red[wid][k] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 3 * C) {
+    if (threadIdx.x < 3 * C) {   // this block's (W1, b1) partial: part[blockIdx.x][3 C]
         float v = 0.0f;
         for (int w8 = 0; w8 < (int)(blockDim.x >> 5); w8++) v += red[w8][threadIdx.x];
-        const int k = threadIdx.x;
-        atomicAdd(grad + (k < 2 * C ? OFF_W1 + k : OFF_B1 + (k - 2 * C)), v);
+        part[(long)blockIdx.x * 3 * C + threadIdx.x] = v;
     }
 }
 
@@ -697,6 +728,8 @@ struct argus_cnn {
     float* dy;              // [max_batch][441]
     float* y;               // [max_batch][441]
     double* loss;           // [1]
+    float* part;            // per-CTA partial gradients: [num_sms][WPART] (a layer at a time)
+    double* lpart;          // per-block partial losses [num_sms * 2]
     int step;
 };
 
@@ -724,7 +757,9 @@ extern "C" int argus_cnn_create(argus_cnn** out, int device, int max_batch, unsi
               cudaMalloc(&n->dh1, sizeof(float) * L) == cudaSuccess &&
               cudaMalloc(&n->dy, sizeof(float) * (size_t)max_batch * NPX) == cudaSuccess &&
               cudaMalloc(&n->y, sizeof(float) * (size_t)max_batch * NPX) == cudaSuccess &&
-              cudaMalloc(&n->loss, sizeof(double)) == cudaSuccess;
+              cudaMalloc(&n->loss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&n->part, sizeof(float) * (size_t)n->num_sms * (size_t)WPART) == cudaSuccess &&
+              cudaMalloc(&n->lpart, sizeof(double) * (size_t)n->num_sms * 2) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         argus_cnn_destroy(n);
@@ -752,7 +787,8 @@ extern "C" int argus_cnn_create(argus_cnn** out, int device, int max_batch, unsi
 extern "C" int argus_cnn_destroy(argus_cnn* n) {
     if (!n) return ARGUS_ERR_ARG;
     cudaSetDevice(n->device);
-    void* ps[] = {n->master, n->wbf, n->m, n->v, n->grad, n->acts, n->dh0, n->dh1, n->dy, n->y, n->loss};
+    void* ps[] = {n->master, n->wbf, n->m, n->v, n->grad, n->acts, n->dh0, n->dh1, n->dy, n->y, n->loss, n->part,
+                  n->lpart};
     for (void* p : ps)
         if (p) cudaFree(p);
     free(n);
@@ -803,24 +839,29 @@ extern "C" int argus_cnn_forward(argus_cnn* nn, const float* x, int n, float* y,
 template <typename WT>
 static void backward_impl(argus_cnn* nn, const WT* w, const float* x, const float* dy, int n, cudaStream_t st) {
     const size_t L = (size_t)nn->max_batch * NPX * C;
-    const int g = nn->num_sms * 4;
-    cudaMemsetAsync(nn->grad, 0, sizeof(float) * NPARAM, st);
+    // every gradient is a fixed-order sum of per-CTA partials (no float atomics): the
+    // partial buffer holds num_sms slots of one layer, reused layer by layer in stream order
+    const int gs = nn->num_sms;   // grid of the element-wise gradient kernels (<= num_sms slots)
+    const int rg = nn->num_sms * 4;
     float* dh = nn->dh0;
     float* dn = nn->dh1;
-    cnn_out_bwd_kernel<WT><<<g, 256, 0, st>>>(nn->acts + 4 * L, dy, w, dh, nn->grad, n); argus_count_launch(1);
+    cnn_out_bwd_kernel<WT><<<gs, 256, 0, st>>>(nn->acts + 4 * L, dy, w, dh, nn->part, n); argus_count_launch(1);
+    cnn_reduce_kernel<<<1, 64, 0, st>>>(nn->part, gs, C + 1, nn->grad + OFF_W6); argus_count_launch(1);
     for (int l = 3; l >= 0; l--) {
         const float* hin = nn->acts + l * L;
         const float* hout = nn->acts + (l + 1) * L;
         int per = (n + nn->num_sms - 1) / nn->num_sms;
         if (per < 1) per = 1;
-        cnn_conv7_wgrad_kernel<<<dim3((n + per - 1) / per, KS), 448, wgrad_smem(), st>>>(
-            hin, dh, hout, nn->grad + off_w(l), nn->grad + off_b(l), n, per); argus_count_launch(1);
+        const int nbx = (n + per - 1) / per;
+        cnn_conv7_wgrad_kernel<<<dim3(nbx, KS), 448, wgrad_smem(), st>>>(hin, dh, hout, nn->part, n, per); argus_count_launch(1);
+        cnn_reduce_kernel<<<rg, 256, 0, st>>>(nn->part, nbx, WPART, nn->grad + off_w(l)); argus_count_launch(1);
         cnn_conv7_dgrad_kernel<WT><<<min(n, nn->num_sms * 2), 256, fwd_smem(), st>>>(dh, hout, w + off_w(l), dn, n); argus_count_launch(1);
         float* t = dh;
         dh = dn;
         dn = t;
     }
-    cnn_in_bwd_kernel<<<g, 256, 0, st>>>(x, dh, nn->grad, n); argus_count_launch(1);
+    cnn_in_bwd_kernel<<<gs, 256, 0, st>>>(x, dh, nn->part, n); argus_count_launch(1);
+    cnn_reduce_kernel<<<1, 128, 0, st>>>(nn->part, gs, 3 * C, nn->grad + OFF_W1); argus_count_launch(1);
 }
 
 extern "C" int argus_cnn_backward(argus_cnn* nn, const float* x, const float* dy, int n, float* grad_out,
@@ -844,8 +885,8 @@ extern "C" int argus_cnn_train_step(argus_cnn* nn, const float* x, const float* 
     int rc = argus_cnn_forward(nn, x, n, nn->y, stream);
     if (rc) return rc;
     double* loss = loss_out ? loss_out : nn->loss;
-    if (cudaMemsetAsync(loss, 0, sizeof(double), st) != cudaSuccess) return ARGUS_ERR_CUDA;
-    cnn_mse_kernel<<<nn->num_sms * 2, 256, 0, st>>>(nn->y, target, (long)n * NPX, nn->dy, loss); argus_count_launch(1);
+    cnn_mse_kernel<<<nn->num_sms * 2, 256, 0, st>>>(nn->y, target, (long)n * NPX, nn->dy, nn->lpart); argus_count_launch(1);
+    cnn_sum_d_kernel<<<1, 32, 0, st>>>(nn->lpart, nn->num_sms * 2, loss); argus_count_launch(1);
     rc = argus_cnn_backward(nn, x, nn->dy, n, NULL, stream);
     if (rc) return rc;
     nn->step++;

@@ -237,3 +237,18 @@ def segment_origins(sides, w: int, h: int, seed: int):
     x0 = torch.floor(u[:, 0] * (w - s + 1)).to(torch.int64).tolist()
     y0 = torch.floor(u[:, 1] * (h - s + 1)).to(torch.int64).tolist()
     return list(zip(x0, y0))
+
+
+def transient_catalog(n: int, w: int, h: int, seed: int, sigma: float, noise: float, snr=(5.0, 20.0),
+                      border=30.0):
+    """Point-like transients to inject into a science frame: uniform positions at least
+    `border` px from the edges, fluxes giving a peak-pixel S/N log-uniform in `snr` for a
+    Gaussian PSF of width sigma over per-pixel noise `noise` (peak = F / (2 pi sigma^2)).
+    Returns (Catalog, peak S/N float64 [n])."""
+    g = _gen(seed * 104729 + 3)
+    u = torch.rand(n, 3, generator=g, dtype=torch.float64)
+    x = border + u[:, 0] * (w - 1 - 2 * border)
+    y = border + u[:, 1] * (h - 1 - 2 * border)
+    s = torch.exp(math.log(snr[0]) + u[:, 2] * (math.log(snr[1]) - math.log(snr[0])))
+    flux = s * noise * 2.0 * math.pi * sigma * sigma
+    return Catalog(x, y, flux), s
