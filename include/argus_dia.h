@@ -363,10 +363,22 @@ int argus_cnn_destroy(argus_cnn *net);
 /* Device pointers to the FP32 master parameters and Adam moments (each
  * [count] floats) and the Adam step, for checkpoints and tests. */
 int argus_cnn_params(argus_cnn *net, float **master, float **adam_m, float **adam_v, long *count, int *step);
-/* Select ARGUS_PREC_BF16 / ARGUS_PREC_FP32 weights, set the Adam step, and
- * refresh the BF16 copy from the master weights (after a checkpoint load). */
+/* Select the arithmetic, set the Adam step, and refresh the BF16 copy from the
+ * master weights (after a checkpoint load):
+ *   ARGUS_PREC_FP32        FP32 weights, FP32 CUDA-core kernels;
+ *   ARGUS_PREC_BF16        BF16 weights, FP32 activations, FP32 CUDA-core kernels;
+ *   ARGUS_PREC_BF16_SPLIT  BF16 weights; the forward on the tensor cores
+ *                          (tcgen05 implicit GEMMs, FP32 accumulation) with each
+ *                          activation split into BF16 hi + lo parts (within
+ *                          2^-17 relative of the FP32 value); the backward as
+ *                          ARGUS_PREC_BF16.
+ * The tensor-core forward's bounded device waits latch ARGUS_ERR_TIMEOUT, read
+ * by argus_cnn_status. */
 int argus_cnn_set_state(argus_cnn *net, int precision, int step, argus_stream stream);
 int argus_cnn_forward(argus_cnn *net, const float *x, int n, float *y, argus_stream stream);
+/* Synchronises the stream, returns the first error latched by the object's
+ * kernels since the last call (ARGUS_OK if none) and clears it. */
+int argus_cnn_status(argus_cnn *net, argus_stream stream);
 /* dL/dparams for a given dL/dy after argus_cnn_forward on the same x (the
  * activations are kept); grad_out (device, [count] floats) may be NULL. */
 int argus_cnn_backward(argus_cnn *net, const float *x, const float *dy, int n, float *grad_out,

@@ -130,6 +130,7 @@ SIGNATURES = {
     "argus_cnn_params": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(C.c_long), C.POINTER(I)], I),
     "argus_cnn_set_state": ([P, I, I, P], I),
     "argus_cnn_forward": ([P, P, I, P, P], I),
+    "argus_cnn_status": ([P, P], I),
     "argus_cnn_backward": ([P, P, P, I, P, P], I),
     "argus_cnn_train_step": ([P, P, P, I, F, P, P], I),
     "argus_cnn_adam": ([P, P, F, P], I),
@@ -349,6 +350,10 @@ def argus_cnn_set_state(net, precision, step, stream=None):
 
 def argus_cnn_forward(net, x, n, y, stream=None):
     _check(load().argus_cnn_forward(net, _ptr(x), int(n), _ptr(y), _stream(stream)), "argus_cnn_forward")
+
+
+def argus_cnn_status(net, stream=None) -> int:
+    return load().argus_cnn_status(net, _stream(stream))
 
 
 def argus_cnn_backward(net, x, dy, n, grad_out=None, stream=None):

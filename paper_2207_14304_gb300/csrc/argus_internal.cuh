@@ -81,5 +81,11 @@ int argus_cholesky_solve_prepare(argus_ctx* ctx, const double* M, int ld, int n,
 void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, double* x, cudaStream_t st);
 int argus_basis_count(const argus_basis* b);
 int argus_nterms(int deg);
+// the learned kernel's forward on the tensor cores (cnn_tc.cu): wbf the BF16
+// parameter vector, wpack argus_cnn_tc_pack_bytes() of scratch for the packed
+// weights, acts (optional) the FP32 activations h1..h5 at acts + l * lstride
+int argus_cnn_forward_tc(const float* x, const void* wbf, void* wpack, int n, float* y, float* acts, long lstride,
+                         int num_sms, int* status, cudaStream_t st);
+size_t argus_cnn_tc_pack_bytes();
 
 static inline int argus_round_up(int a, int m) { return (a + m - 1) / m * m; }

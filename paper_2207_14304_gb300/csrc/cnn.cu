@@ -12,7 +12,8 @@
 // accumulation; activations are FP32, channels last with a padded channel
 // stride of 33 in shared memory (conflict-free across pixels).  Training runs
 // entirely in these kernels: forward, MSE, data and weight gradients, Adam on
-// FP32 master weights with a BF16 working copy.
+// FP32 master weights with a BF16 working copy.  With ARGUS_PREC_BF16_SPLIT
+// the forward runs instead on the tensor cores (cnn_tc.cu).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
@@ -730,6 +731,8 @@ struct argus_cnn {
     double* loss;           // [1]
     float* part;            // per-CTA partial gradients: [num_sms][WPART] (a layer at a time)
     double* lpart;          // per-block partial losses [num_sms * 2]
+    void* wpack;            // the 7x7 weights in the tensor-core operand layout
+    int* d_status;          // latched device status word
     int step;
 };
 
@@ -759,12 +762,15 @@ extern "C" int argus_cnn_create(argus_cnn** out, int device, int max_batch, unsi
               cudaMalloc(&n->y, sizeof(float) * (size_t)max_batch * NPX) == cudaSuccess &&
               cudaMalloc(&n->loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&n->part, sizeof(float) * (size_t)n->num_sms * (size_t)WPART) == cudaSuccess &&
-              cudaMalloc(&n->lpart, sizeof(double) * (size_t)n->num_sms * 2) == cudaSuccess;
+              cudaMalloc(&n->lpart, sizeof(double) * (size_t)n->num_sms * 2) == cudaSuccess &&
+              cudaMalloc(&n->wpack, argus_cnn_tc_pack_bytes()) == cudaSuccess &&
+              cudaMalloc(&n->d_status, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         argus_cnn_destroy(n);
         return ARGUS_ERR_NOMEM;
     }
+    cudaMemset(n->d_status, 0, sizeof(int));
     cudaMemset(n->m, 0, sizeof(float) * NPARAM);
     cudaMemset(n->v, 0, sizeof(float) * NPARAM);
     cnn_init_kernel<<<n->num_sms * 4, 256>>>(n->master, NPARAM, seed); argus_count_launch(1);
@@ -788,7 +794,7 @@ extern "C" int argus_cnn_destroy(argus_cnn* n) {
     if (!n) return ARGUS_ERR_ARG;
     cudaSetDevice(n->device);
     void* ps[] = {n->master, n->wbf, n->m, n->v, n->grad, n->acts, n->dh0, n->dh1, n->dy, n->y, n->loss, n->part,
-                  n->lpart};
+                  n->lpart, n->wpack, n->d_status};
     for (void* p : ps)
         if (p) cudaFree(p);
     free(n);
@@ -807,7 +813,9 @@ extern "C" int argus_cnn_params(argus_cnn* n, float** master, float** adam_m, fl
 }
 
 extern "C" int argus_cnn_set_state(argus_cnn* n, int precision, int step, argus_stream stream) {
-    if (!n || (precision != ARGUS_PREC_FP32 && precision != ARGUS_PREC_BF16) || step < 0) return ARGUS_ERR_ARG;
+    if (!n || (precision != ARGUS_PREC_FP32 && precision != ARGUS_PREC_BF16 && precision != ARGUS_PREC_BF16_SPLIT) ||
+        step < 0)
+        return ARGUS_ERR_ARG;
     if (cudaSetDevice(n->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     n->precision = precision;
     n->step = step;
@@ -831,9 +839,24 @@ extern "C" int argus_cnn_forward(argus_cnn* nn, const float* x, int n, float* y,
     if (!nn || !x || !y || n < 1 || n > nn->max_batch) return ARGUS_ERR_ARG;
     if (cudaSetDevice(nn->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    if (nn->precision == ARGUS_PREC_BF16_SPLIT)
+        return argus_cnn_forward_tc(x, nn->wbf, nn->wpack, n, y, nn->acts, (long)nn->max_batch * NPX * C, nn->num_sms,
+                                    nn->d_status, st);
     if (nn->precision == ARGUS_PREC_BF16) forward_impl<__nv_bfloat16>(nn, nn->wbf, x, n, y, st);
     else forward_impl<float>(nn, nn->master, x, n, y, st);
     return argus_launch_status();
+}
+
+extern "C" int argus_cnn_status(argus_cnn* nn, argus_stream stream) {
+    if (!nn) return ARGUS_ERR_ARG;
+    if (cudaSetDevice(nn->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, nn->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(nn->d_status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return argus_cuda_fail(e);
+    return h;
 }
 
 template <typename WT>
@@ -869,7 +892,7 @@ extern "C" int argus_cnn_backward(argus_cnn* nn, const float* x, const float* dy
     if (!nn || !x || !dy || n < 1 || n > nn->max_batch) return ARGUS_ERR_ARG;
     if (cudaSetDevice(nn->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    if (nn->precision == ARGUS_PREC_BF16) backward_impl<__nv_bfloat16>(nn, nn->wbf, x, dy, n, st);
+    if (nn->precision != ARGUS_PREC_FP32) backward_impl<__nv_bfloat16>(nn, nn->wbf, x, dy, n, st);
     else backward_impl<float>(nn, nn->master, x, dy, n, st);
     if (grad_out && cudaMemcpyAsync(grad_out, nn->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, st) !=
                         cudaSuccess)

@@ -39,7 +39,11 @@ class _DevArray:
 
 
 class KernelNet:
-    def __init__(self, device=0, max_batch=1024, seed=1, precision="bf16"):
+    """precision: "bf16_split" (BF16 weights, the forward on the tensor cores with
+    activations as BF16 hi + lo parts), "bf16" (BF16 weights, CUDA-core kernels) or
+    "fp32"; the backward runs on the CUDA cores in every mode."""
+
+    def __init__(self, device=0, max_batch=1024, seed=1, precision="bf16_split"):
         self.device = torch.device("cuda", device)
         self.max_batch = int(max_batch)
         self.net = B.argus_cnn_create(device, max_batch, seed)
