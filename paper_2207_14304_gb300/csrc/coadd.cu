@@ -6,11 +6,11 @@
 // One thread per output pixel of a 32 x 8 tile.  Per frame, the raw window
 // the tile needs is loaded once, coalesced, and calibrated into shared memory.
 // The frame loop is unrolled to the compile-time stack bound NMAX so every
-// per-frame value lives in a register at a static index: invalid or absent
-// frames hold +inf and sort to the end.  A bitonic
-// network sorts the samples; because rejection |v - c| > kappa*s keeps a
-// value-closed set, the survivors stay one contiguous range [lo, hi) of the
-// sorted array, and every statistic is a predicated pass over static indices.
+// per-frame sample lives in a register at a static index: invalid or absent
+// frames hold +inf and sort to the end.  A bitonic network sorts the samples;
+// because rejection |v - c| > kappa*s keeps a value-closed set, the survivors
+// stay one contiguous range [lo, hi) of the sorted array, so each clipping
+// pass touches only that range of the sorted column in shared memory.
 // Traffic: 2 bytes per frame plus 9 bytes of calibration per pixel in, 9 out.
 #include "argus_internal.cuh"
 
@@ -30,18 +30,6 @@ struct CoaddArgs {
     float gain, rn2, kappa;
 };
 
-__device__ __forceinline__ bool calib_px(const CoaddArgs& a, int f, int x, int y, float& v, float& vr) {
-    if (x < 0 || y < 0 || x >= a.w || y >= a.h) return false;
-    const long p = (long)y * a.pitch + x;
-    const int raw = a.raw[(long)f * a.frame_stride + p];
-    const float fl = a.flat ? __ldg(a.flat + p) : 1.0f;
-    if ((a.bpm && __ldg(a.bpm + p)) || !(fl > 0.0f) || !(fl <= 3.402823466e38f) || raw >= a.sat) return false;
-    const float ng = (float)(raw - a.bias) * a.gain;
-    v = (ng - (a.dark ? __ldg(a.dark + p) : 0.0f)) / fl;
-    vr = (fmaxf(ng, 0.0f) + a.rn2) / (fl * fl);
-    return true;
-}
-
 template <int N>
 __device__ __forceinline__ void bitonic_sort(float (&s)[N]) {
 #pragma unroll
@@ -60,155 +48,242 @@ __device__ __forceinline__ void bitonic_sort(float (&s)[N]) {
             }
 }
 
-template <int N>
-__device__ __forceinline__ float pick(const float (&s)[N], int idx) {
-    float r = 0.0f;
-#pragma unroll
-    for (int i = 0; i < N; i++) r = (i == idx) ? s[i] : r;
-    return r;
-}
-
-template <int N>
-__device__ __forceinline__ float median_range(const float (&s)[N], int lo, int hi) {
-    const int n = hi - lo;
-    const float a = pick(s, lo + (n - 1) / 2), b = pick(s, lo + n / 2);
-    return (n & 1) ? b : 0.5f * (a + b);
-}
-
-// One CTA per 32 x 8 output tile.  Phase 1 loads, for every frame, the
-// (33 x 9) window of raw pixels the tile's samples need -- placed at the
-// frame's integer offset -- with coalesced reads (all frames' loads in flight
-// together) and calibrates each pixel once into shared memory: value, or NaN
-// where the pixel is unusable, and variance.  Phase 2: each thread
-// interpolates its samples from four shared values per frame, sorts them in
-// registers and clips; the survivors' variances are recomputed from shared
-// memory in the last pass instead of being held in registers.
+// One CTA per 32 x 8 output tile.  Per tile:
+//
+// Phase 0: the calibration constants (the reciprocal of the flat, or NaN where
+// the pixel is unusable -- outside the frame, flagged bad, flat not positive
+// and finite -- and the dark) of the union of the frames' windows into shared
+// memory, once: frames share their pixels' calibration, and their windows
+// differ only by the integer parts of the shifts.  When that union exceeds
+// UCAP pixels (shifts spread by more than 4 px) each frame's window reads its
+// constants from global memory instead.
+//
+// Phase 1: every frame's (33 x 9) window of raw pixels -- at the frame's
+// integer offset -- calibrated into shared memory as (value, variance) pairs:
+// value NaN where unusable.  The nf x 297 window pixels are spread evenly over
+// the threads; per pixel one raw load and table lookups.  The flat enters
+// through its correctly rounded reciprocal (within 1 ulp of the quotient).
+//
+// Phase 2: each thread interpolates its samples from four shared pairs per
+// frame (the value by nested lerps, the variance by the squared weights) and
+// sums the variances of the valid samples as it goes; it sorts the values in
+// registers with a bitonic network and writes the sorted column to shared
+// memory.  The survivors of a clipping pass stay one contiguous range [lo, hi)
+// of the sorted samples, so each pass reads only that range: the median from
+// two slots, the mean and the spread in two loops over the range, and the
+// rejected samples by scanning inward from both ends (the rejected set is a
+// prefix below the median and a suffix above it, because the rounded distance
+// to the median is monotone in the sample).  The variance of the mean is the
+// valid samples' sum minus the rejected samples' variances, summed with
+// error-free transformations.
 constexpr int CTX = 32, CTY = 8, CWX = CTX + 1, CWY = CTY + 1, CWN = CWX * CWY;
+constexpr int CT = CTX * CTY;                  // threads (one per output pixel of the tile)
+constexpr int UCAP = 512;                      // union window capacity (pixels): shift spreads up to 4 px
+constexpr float FMAXF = 3.402823466e38f;
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fffffff); }
 
-// Bilinear sample of one frame from its calibrated window (nested lerps with
-// explicit fused multiply-adds, so that the two evaluations of a sample in the
-// kernel round identically).  Non-finite when a needed pixel is unusable.
-__device__ __forceinline__ float sample(const float* wv, int o, float fx, float fy) {
+// Median of the sorted range [lo, hi) of one thread's column of samples
+// (slot i at col[i * CT]); the mean of the two middle values for even counts.
+__device__ __forceinline__ float median_col(const float* col, int lo, int hi) {
+    const int n = hi - lo;
+    const float a = col[(lo + (n - 1) / 2) * CT], b = col[(lo + n / 2) * CT];
+    return (n & 1) ? b : 0.5f * (a + b);
+}
+
+// Calibration constants of frame pixel (gx, gy): (1 / flat, dark), with NaN
+// in place of 1 / flat when the pixel is unusable.
+__device__ __forceinline__ float2 calib_const(const CoaddArgs& a, int gx, int gy) {
+    float2 c = make_float2(qnan(), 0.0f);
+    if (gx >= 0 && gy >= 0 && gx < a.w && gy < a.h) {
+        const long p = (long)gy * a.pitch + gx;
+        const float fl = a.flat ? __ldg(a.flat + p) : 1.0f;
+        const bool bad = a.bpm && __ldg(a.bpm + p);
+        if (!bad && fl > 0.0f && fl <= FMAXF) c.x = __frcp_rn(fl);
+        c.y = a.dark ? __ldg(a.dark + p) : 0.0f;
+    }
+    return c;
+}
+
+// Calibrated (value, variance) of one raw pixel given its constants.
+__device__ __forceinline__ float2 calib_pair(const CoaddArgs& a, int raw, float2 c) {
+    float2 r = make_float2(qnan(), 0.0f);
+    if (c.x == c.x && raw < a.sat) {
+        const float ng = (float)(raw - a.bias) * a.gain;
+        const float cv = (ng - c.y) * c.x;
+        if (fabsf(cv) <= FMAXF) {   // non-finite: unusable
+            r.x = cv;
+            r.y = (fmaxf(ng, 0.0f) + a.rn2) * (c.x * c.x);
+        }
+    }
+    return r;
+}
+
+// s + e = a + b exactly (Knuth's two-sum; no reassociation: the library is not
+// built with fast-math).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Bilinear sample of one frame from its calibrated window: the value by nested
+// lerps with explicit fused multiply-adds (non-finite when a needed pixel is
+// unusable), the variance as the sum of squared weights (q) times the four
+// pixels' variances.
+__device__ __forceinline__ float sample(const float2* w, int o, float fx, float fy, float4 q, float& var) {
     const bool n1 = fx > 0.0f, n2 = fy > 0.0f;
-    const float v00 = wv[o];
-    const float v10 = n1 ? wv[o + 1] : v00;
-    const float v01 = n2 ? wv[o + CWX] : v00;
-    const float v11 = (n1 && n2) ? wv[o + CWX + 1] : (n1 ? v10 : v01);
-    const float top = __fmaf_rn(fx, __fsub_rn(v10, v00), v00);
-    const float bot = __fmaf_rn(fx, __fsub_rn(v11, v01), v01);
+    const float2 p00 = w[o];
+    const float2 p10 = n1 ? w[o + 1] : p00;
+    const float2 p01 = n2 ? w[o + CWX] : p00;
+    const float2 p11 = (n1 && n2) ? w[o + CWX + 1] : (n1 ? p10 : p01);
+    var = q.x * p00.y + (n1 ? q.y * p10.y : 0.0f) + (n2 ? q.z * p01.y : 0.0f) + (n1 && n2 ? q.w * p11.y : 0.0f);
+    const float top = __fmaf_rn(fx, __fsub_rn(p10.x, p00.x), p00.x);
+    const float bot = __fmaf_rn(fx, __fsub_rn(p11.x, p01.x), p01.x);
     return __fmaf_rn(fy, __fsub_rn(bot, top), top);
 }
 
-__device__ __forceinline__ float sample_var(const float* wr, int o, float fx, float fy) {
-    const bool n1 = fx > 0.0f, n2 = fy > 0.0f;
-    const float w0 = (1.0f - fx) * (1.0f - fy), w1 = fx * (1.0f - fy);
-    const float w2 = (1.0f - fx) * fy, w3 = fx * fy;
-    return w0 * w0 * wr[o] + (n1 ? w1 * w1 * wr[o + 1] : 0.0f) + (n2 ? w2 * w2 * wr[o + CWX] : 0.0f) +
-           (n1 && n2 ? w3 * w3 * wr[o + CWX + 1] : 0.0f);
-}
-
 template <int NMAX>
-__global__ void __launch_bounds__(CTX * CTY) coadd_kernel(CoaddArgs a) {
+__global__ void __launch_bounds__(CT, NMAX <= 32 ? 2 : 1) coadd_kernel(CoaddArgs a) {
     extern __shared__ float4 coadd_smem[];
-    float* wv = reinterpret_cast<float*>(coadd_smem);   // [nf][CWY][CWX] values
-    float* wr = wv + a.nf * CWN;                         // [nf][CWY][CWX] variances
-    __shared__ int s_ix[NMAX], s_iy[NMAX];
-    __shared__ float s_fx[NMAX], s_fy[NMAX];
-    for (int f = threadIdx.x; f < NMAX; f += blockDim.x) {
+    float2* wvr = reinterpret_cast<float2*>(coadd_smem);         // [nf][CWN] (value, variance)
+    float* ss = reinterpret_cast<float*>(wvr + a.nf * CWN);      // [NMAX][CT] sorted samples, a column per thread
+    float2* ucal = reinterpret_cast<float2*>(ss + NMAX * CT);    // [UCAP] union calibration window
+    __shared__ int2 s_j[CWN];              // window pixel j: (union offset jy * UW + jx, raw offset jy * pitch + jx)
+    __shared__ short2 s_jxy[CWN];          // (jx, jy)
+    __shared__ int s_ix[NMAX], s_iy[NMAX], s_fofs[NMAX];
+    __shared__ long long s_rb[NMAX];       // per tile: raw element offset of frame f's window origin
+    __shared__ float2 s_fxy[NMAX];
+    __shared__ float4 s_q[NMAX];
+    __shared__ int s_umin[2], s_uwh[2];
+    const int tid = threadIdx.x;
+    if (tid == 0) { s_umin[0] = s_umin[1] = 1 << 30; s_uwh[0] = s_uwh[1] = -(1 << 30); }
+    __syncthreads();
+    for (int f = tid; f < NMAX; f += blockDim.x) {
+        float fxf = 0.0f, fyf = 0.0f;
+        int ix = 0, iy = 0;
         if (f < a.nf) {
             const double dx = a.shifts[2 * f], dy = a.shifts[2 * f + 1];
             const double fx = floor(dx), fy = floor(dy);
-            s_ix[f] = (int)fx;
-            s_iy[f] = (int)fy;
-            s_fx[f] = (float)(dx - fx);
-            s_fy[f] = (float)(dy - fy);
-        } else {
-            s_ix[f] = 0; s_iy[f] = 0; s_fx[f] = 0.0f; s_fy[f] = 0.0f;
+            ix = (int)fx;
+            iy = (int)fy;
+            fxf = (float)(dx - fx);
+            fyf = (float)(dy - fy);
+            atomicMin(&s_umin[0], ix); atomicMin(&s_umin[1], iy);
+            atomicMax(&s_uwh[0], ix); atomicMax(&s_uwh[1], iy);
         }
+        s_ix[f] = ix;
+        s_iy[f] = iy;
+        s_fxy[f] = make_float2(fxf, fyf);
+        const float w0 = (1.0f - fxf) * (1.0f - fyf), w1 = fxf * (1.0f - fyf);
+        const float w2 = (1.0f - fxf) * fyf, w3 = fxf * fyf;
+        s_q[f] = make_float4(w0 * w0, w1 * w1, w2 * w2, w3 * w3);
     }
+    __syncthreads();
+    const int ixmin = s_umin[0], iymin = s_umin[1];
+    const int UW = CWX + (s_uwh[0] - ixmin), UH = CWY + (s_uwh[1] - iymin);
+    const bool uni = UW * UH <= UCAP;      // the same for every CTA
+    for (int j = tid; j < CWN; j += blockDim.x) {
+        const int jy = j / CWX, jx = j - jy * CWX;
+        s_j[j] = make_int2(jy * UW + jx, (int)(jy * a.pitch) + jx);
+        s_jxy[j] = make_short2((short)jx, (short)jy);
+    }
+    for (int f = tid; f < a.nf; f += blockDim.x) s_fofs[f] = (s_iy[f] - iymin) * UW + (s_ix[f] - ixmin);
     const int ntx = (a.w + CTX - 1) / CTX, nty = (a.h + CTY - 1) / CTY;
-    const int lx = threadIdx.x % CTX, ly = threadIdx.x / CTX;
+    const int lx = tid % CTX, ly = tid / CTX;
     const int o = ly * CWX + lx;
     const int tot = a.nf * CWN;
-    constexpr int U = 4;
+    float* col = ss + tid;
     for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
         const int tx0 = (tile % ntx) * CTX, ty0 = (tile / ntx) * CTY;
         const int x = tx0 + lx, y = ty0 + ly;
-        __syncthreads();   // shifts staged; previous tile's windows consumed
-        for (int e0 = threadIdx.x; e0 < tot; e0 += U * CTX * CTY) {
-            int raw[U];
-            long p[U];
-            bool in[U];
+        __syncthreads();   // tables staged; previous tile's windows consumed
+        for (int f = tid; f < a.nf; f += blockDim.x)
+            s_rb[f] = (long long)f * a.frame_stride + (long long)(ty0 + s_iy[f]) * a.pitch + (tx0 + s_ix[f]);
+        if (uni)
+            for (int e = tid; e < UW * UH; e += blockDim.x) {
+                const int uy = e / UW, ux = e - uy * UW;
+                ucal[e] = calib_const(a, tx0 + ixmin + ux, ty0 + iymin + uy);
+            }
+        __syncthreads();
+        // window pixel e = f * CWN + j, e = tid + k * CT: j advances by CT < CWN, wrapping at most once
+        int f = 0, j = tid;
+        constexpr int U = 4;
+        for (int e0 = tid; e0 < tot; e0 += U * CT) {
+            int fu[U], ju[U], raw[U];
+            float2 cu[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const int e = e0 + u * CTX * CTY;
-                const int f = e / CWN, j = e - f * CWN;
-                const int jy = j / CWX, jx = j - jy * CWX;
-                const int gx = tx0 + s_ix[f < a.nf ? f : 0] + jx, gy = ty0 + s_iy[f < a.nf ? f : 0] + jy;
-                in[u] = e < tot && gx >= 0 && gy >= 0 && gx < a.w && gy < a.h;
-                p[u] = in[u] ? (long)gy * a.pitch + gx : 0;
-                raw[u] = in[u] ? (int)__ldg(a.raw + (long)f * a.frame_stride + p[u]) : 0;
+                fu[u] = f;
+                ju[u] = j;
+                j += CT;
+                if (j >= CWN) { j -= CWN; f++; }
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                const int e = e0 + u * CTX * CTY;
-                if (e >= tot) break;
-                float cv = qnan(), cr = 0.0f;
-                if (in[u]) {
-                    const float fl = a.flat ? __ldg(a.flat + p[u]) : 1.0f;
-                    const bool bad = (a.bpm && __ldg(a.bpm + p[u])) || !(fl > 0.0f) || !(fl <= 3.402823466e38f) ||
-                                     raw[u] >= a.sat;
-                    if (!bad) {
-                        const float ng = (float)(raw[u] - a.bias) * a.gain;
-                        cv = (ng - (a.dark ? __ldg(a.dark + p[u]) : 0.0f)) / fl;
-                        cr = (fmaxf(ng, 0.0f) + a.rn2) / (fl * fl);
-                        if (!(fabsf(cv) <= 3.402823466e38f)) cv = qnan();   // non-finite: unusable
-                    }
+                const bool live = e0 + u * CT < tot;
+                const int fc = live ? fu[u] : 0;
+                if (uni) {
+                    cu[u] = ucal[s_fofs[fc] + s_j[ju[u]].x];
+                } else {
+                    const short2 jj = s_jxy[ju[u]];
+                    cu[u] = calib_const(a, tx0 + s_ix[fc] + jj.x, ty0 + s_iy[fc] + jj.y);
                 }
-                wv[e] = cv;
-                wr[e] = cr;
+                raw[u] = (live && cu[u].x == cu[u].x) ? (int)__ldg(a.raw + s_rb[fc] + s_j[ju[u]].y) : 0;
             }
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (e0 + u * CT < tot) wvr[fu[u] * CWN + ju[u]] = calib_pair(a, raw[u], cu[u]);
         }
         __syncthreads();
         if (x >= a.w || y >= a.h) continue;
-        float s[NMAX];
+        float u[NMAX], s[NMAX];
         int n = 0;
+        float svh = 0.0f, svl = 0.0f;   // compensated sum of the valid samples' variances
 #pragma unroll
-        for (int f = 0; f < NMAX; f++) {
+        for (int fi = 0; fi < NMAX; fi++) {
             float sv = __int_as_float(0x7f800000);   // +inf: absent or invalid
-            if (f < a.nf) {
-                const float v = sample(wv + f * CWN, o, s_fx[f], s_fy[f]);
-                const bool ok = fabsf(v) <= 3.402823466e38f;
+            u[fi] = sv;
+            if (fi < a.nf) {
+                const float2 fxy = s_fxy[fi];
+                float vr;
+                const float v = sample(wvr + fi * CWN, o, fxy.x, fxy.y, s_q[fi], vr);
+                const bool ok = fabsf(v) <= FMAXF;
+                u[fi] = v;
                 sv = ok ? v : sv;
                 n += ok ? 1 : 0;
+                float e;
+                two_sum(svh, ok ? vr : 0.0f, svh, e);
+                svl += e;
             }
-            s[f] = sv;
+            s[fi] = sv;
         }
         bitonic_sort(s);
+#pragma unroll
+        for (int i = 0; i < NMAX; i++) col[i * CT] = s[i];
         int lo = 0, hi = n;
         for (int it = 0; it < a.max_iter && hi > lo; it++) {
             const int cnt = hi - lo;
-            const float c = median_range(s, lo, hi);
+            const float c = median_col(col, lo, hi);
             float sum = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NMAX; i++) sum += (i >= lo && i < hi) ? s[i] : 0.0f;
+            for (int i = lo; i < hi; i++) sum += col[i * CT];
             const float m = sum / (float)cnt;
             float s2 = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NMAX; i++) {
-                const float d = s[i] - m;
-                s2 += (i >= lo && i < hi) ? d * d : 0.0f;
+            for (int i = lo; i < hi; i++) {
+                const float d = col[i * CT] - m;
+                s2 += d * d;
             }
             const float ks = a.kappa * sqrtf(s2 / (float)cnt);
             int nlo = 0, nhi = 0;
-#pragma unroll
-            for (int i = 0; i < NMAX; i++) {
-                const bool in = i >= lo && i < hi;
-                const bool rej = in && (fabsf(s[i] - c) > ks);
-                nlo += (rej && s[i] < c) ? 1 : 0;
-                nhi += (rej && s[i] >= c) ? 1 : 0;
+            while (lo + nlo < hi) {
+                const float v = col[(lo + nlo) * CT];
+                if (!(v < c && fabsf(v - c) > ks)) break;
+                nlo++;
+            }
+            while (hi - 1 - nhi >= lo + nlo) {
+                const float v = col[(hi - 1 - nhi) * CT];
+                if (!(v >= c && fabsf(v - c) > ks)) break;
+                nhi++;
             }
             if (nlo + nhi == 0 || nlo + nhi == cnt) break;
             lo += nlo;
@@ -222,16 +297,24 @@ __global__ void __launch_bounds__(CTX * CTY) coadd_kernel(CoaddArgs a) {
             continue;
         }
         const int cnt = hi - lo;
-        const float c = median_range(s, lo, hi);
-        const float vlo = pick(s, lo), vhi = pick(s, hi - 1);
-        float sd = 0.0f, svar = 0.0f;
+        const float c = median_col(col, lo, hi);
+        const float vlo = col[lo * CT], vhi = col[(hi - 1) * CT];
+        float sd = 0.0f;
+        for (int i = lo; i < hi; i++) sd += col[i * CT] - c;
+        if (cnt < n) {   // the rejected samples' variances out (compensated: a rejected cosmic
+                         // ray's variance can exceed the survivors' sum many times)
 #pragma unroll
-        for (int i = 0; i < NMAX; i++) sd += (i >= lo && i < hi) ? s[i] - c : 0.0f;
-        for (int f = 0; f < a.nf; f++) {
-            const float fx = s_fx[f], fy = s_fy[f];
-            const float v = sample(wv + f * CWN, o, fx, fy);
-            if (v >= vlo && v <= vhi) svar += sample_var(wr + f * CWN, o, fx, fy);
+            for (int fi = 0; fi < NMAX; fi++)
+                if (fi < a.nf && fabsf(u[fi]) <= FMAXF && (u[fi] < vlo || u[fi] > vhi)) {
+                    const float2 fxy = s_fxy[fi];
+                    float vr;
+                    sample(wvr + fi * CWN, o, fxy.x, fxy.y, s_q[fi], vr);
+                    float e;
+                    two_sum(svh, -vr, svh, e);
+                    svl += e;
+                }
         }
+        const float svar = svh + svl;
         a.coadd[p] = c + sd / (float)cnt;
         a.var[p] = svar / ((float)cnt * (float)cnt);
         a.n_used[p] = (uint8_t)cnt;
@@ -240,18 +323,19 @@ __global__ void __launch_bounds__(CTX * CTY) coadd_kernel(CoaddArgs a) {
 
 template <int NMAX>
 int launch(const CoaddArgs& a, int sms, cudaStream_t st) {
-    const size_t smem = (size_t)a.nf * CWN * 2 * sizeof(float);
+    const size_t smem = ((size_t)a.nf * CWN * 2 + (size_t)NMAX * CT + (size_t)UCAP * 2) * sizeof(float);
     if (cudaFuncSetAttribute(coadd_kernel<NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(coadd_kernel<NMAX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
         return ARGUS_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coadd_kernel<NMAX>, CTX * CTY, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coadd_kernel<NMAX>, CT, smem) != cudaSuccess ||
         per_sm < 1)
         return ARGUS_ERR_CUDA;
     const long tiles = (long)((a.w + CTX - 1) / CTX) * ((a.h + CTY - 1) / CTY);
     long blocks = tiles;
     if (blocks > (long)sms * per_sm) blocks = (long)sms * per_sm;
-    coadd_kernel<NMAX><<<(unsigned)blocks, CTX * CTY, smem, st>>>(a); argus_count_launch(1);
+    coadd_kernel<NMAX><<<(unsigned)blocks, CT, smem, st>>>(a); argus_count_launch(1);
     return argus_launch_status();
 }
 

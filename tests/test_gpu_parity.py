@@ -490,11 +490,14 @@ def test_expand_parity(ora):
 
 
 # --------------------------------------------------------------------------- coadd
-@pytest.mark.parametrize("nf,w,h", [(7, 100, 70), (30, 133, 41), (2, 40, 40), (1, 17, 9)])
-def test_coadd_parity(ora, nf, w, h):
+# amp: shift amplitude in px (0.5: sub-pixel shifts, whose integer parts differ by at most 1;
+# 6: a dithered stack, whose frames' windows spread beyond the kernel's shared calibration window)
+@pytest.mark.parametrize("nf,w,h,amp", [(7, 100, 70, 0.5), (30, 133, 41, 0.5), (2, 40, 40, 0.5), (1, 17, 9, 0.5),
+                                        (40, 70, 33, 0.5), (64, 45, 20, 0.5), (12, 90, 60, 6.0)])
+def test_coadd_parity(ora, nf, w, h, amp):
     cal = synth.make_calib(w, h, seed=nf, bad_frac=0.003)
     cat = synth.star_catalog(w * h // 200, w, h, seed=nf + 1)
-    sh = synth.uniform_shifts(nf, seed=nf).numpy()
+    sh = synth.uniform_shifts(nf, seed=nf, amp=amp).numpy()
     frames = []
     for f in range(nf):
         e = synth.render(cat, w, h, 1.5, sky=300.0, shift=(-float(sh[f, 0]), -float(sh[f, 1])))
