@@ -8,8 +8,11 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include <cstdio>
+
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 
 #include "argus_internal.cuh"
 
@@ -59,6 +62,39 @@ int argus_launch_status() {
 }
 
 extern "C" const char* argus_last_cuda_error(void) { return g_last_cuda_error; }
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link
+// against libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+static std::once_flag g_encode_once;
+
+int argus_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, int esize, const void* base, long w, long h, long pitch,
+                  int bx, int by) {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    if (!g_encode_tiled) {
+        snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "cuTensorMapEncodeTiled not available from the driver");
+        return ARGUS_ERR_CUDA;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * (cuuint64_t)esize};
+    const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode_tiled(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "cuTensorMapEncodeTiled: CUresult %d", (int)r);
+        return ARGUS_ERR_CUDA;
+    }
+    return ARGUS_OK;
+}
 
 template <typename T>
 static bool dalloc(T** p, size_t n) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the sm_103a translation units of libargusdia.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +74,12 @@ int argus_check_ptr16(const void* p);
 int argus_launch_status();   // ARGUS_OK or ARGUS_ERR_CUDA after a launch
 int argus_cuda_fail(cudaError_t e);   // records e for argus_last_cuda_error, returns ARGUS_ERR_CUDA
 void argus_count_launch(int n);   // host-side tally of kernel launches
+// Tensor map of a pitched 2-D image of w x h elements of esize bytes (row pitch
+// in elements) for tiled TMA copies of bx x by boxes, zero fill outside the
+// image; ARGUS_ERR_CUDA when the driver rejects it (the reason goes to
+// argus_last_cuda_error).  Host only, no device work (legal during stream capture).
+int argus_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, int esize, const void* base, long w, long h, long pitch,
+                  int bx, int by);
 extern "C" unsigned long long argus_launch_count(void);
 
 // Inter-unit launchers

@@ -2,9 +2,11 @@
 // normal-equation Gram and the subtraction's reference convolution): TMEM
 // allocation, shared-memory matrix descriptors, tcgen05.mma (kind::f16 /
 // kind::tf32, cta_group::1), commit to an mbarrier, TMEM loads, mbarrier
-// waits with a bound, named barriers, cp.async and bulk copies.  Only compiled
+// waits with a bound, named barriers, cp.async, bulk copies and tiled tensor
+// copies (TMA).  Only compiled
 // for sm_103a.
 #pragma once
+#include <cuda.h>   // CUtensorMap
 #include <stdint.h>
 
 namespace tc {
@@ -211,6 +213,22 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t 
             smem_u32(sdst)),
         "l"(gsrc), "r"(bytes), "r"(smem_u32(mbar))
         : "memory");
+}
+
+// Tiled 2-D tensor copy (TMA) of one box of `map` at element coordinates
+// (x, y) into this CTA's shared memory (dense box order, 128-byte aligned),
+// completing on `mbar`.  x times the element size must be a multiple of 16
+// bytes; x and y may lie outside the tensor (those elements read as zero).
+__device__ __forceinline__ void tma_load_2d(void* sdst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(sdst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Prefetch a tensor map (a kernel parameter) into the descriptor cache.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 // 4-byte asynchronous global -> shared copy; bytes past `src_bytes` (0..4)
