@@ -1129,26 +1129,41 @@ __global__ void __launch_bounds__(1024) tri_solve_kernel(const double* L, int ld
 
 // Residual pass over all design rows with coefficients a (FP64 in, FP32 model).
 // A CTA takes 256 rows at a time (one per thread): each thread forms its
-// row's model and residual e and stages X_m and g_k = w e p_k in shared
-// memory; then r_j = sum_rows c_j w e is a set of 256-term dot products from
-// shared memory, summed in FP32 per tile and in FP64 across tiles.  Also
-// chi2 = sum w e^2 and the count of weighted rows.  Per-CTA partials
-// [NP + 4] are reduced in a fixed order.
+// row's model and residual e, stages its X_m in shared memory (row stride odd:
+// no bank conflicts either way) and g_k = w e p_k, gb_k = w e pb_k beside them.
+// Then the outputs r_(m,k) = sum_rows X_m g_k are owned by basis function:
+// groups of nb threads split the 256 rows into contiguous chunks, thread
+// (q, m) sums X_m g_k for every k over chunk q (the g_k are one broadcast
+// read per row), and thread (q, 0) also the gb_k.  Sums are FP32 per
+// chunk (at most 52 rows), FP64 across chunks, tiles and (in a fixed order)
+// groups.  Also chi2 = sum w e^2 and the count of weighted rows.  Per-CTA
+// partials [NP + 4] are reduced in a fixed order.
 constexpr int RT = 256;
+constexpr int RG = 16;   // staged g_k (0..5) and gb_k (8..13) per row
+
+__host__ __device__ inline int resid_xst(int nb) { return nb | 1; }
 
 __global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const float* rw, const double* a, const double* flag,
                                                    int want_r, double* part) {
-    extern __shared__ __align__(16) float rsm[];   // Xs[nb][RT], Gk[Ks + Kb][RT]
+    extern __shared__ __align__(16) float rsm[];   // Gs[RT][RG], Xs[RT][xst]; after the rows: red (FP64)
     __shared__ float af[1024];
     __shared__ double wchi[RT / 32], wn[RT / 32];
     if (flag[0] != 0.0 || (want_r && flag[1] != 0.0)) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float* Xs = rsm;
-    float* Gk = rsm + g.nb * RT;
+    const int nb = g.nb, Ks = g.Ks, Kb = g.Kb, xst = resid_xst(nb);
+    float* Gs = rsm;
+    float* Xs = rsm + RT * RG;
     for (int j = tid; j < g.Nc; j += RT) af[j] = (float)a[j];
     const long nrows = (long)min(*g.n_stamps, g.max_stamps) * g.ss;
-    const int nx = 1 + (g.nb - 1) * g.Ks;
-    double racc[2] = {0.0, 0.0};      // outputs j = tid and j = tid + RT
+    const int nx = 1 + (nb - 1) * Ks;
+    // output ownership: thread (q, m), q < ng groups of nb threads, rows [q ch, q ch + ch) of a tile
+    const int ng = RT / nb, ch = (RT + ng - 1) / ng;
+    const int q = tid / nb, m = tid - q * nb;
+    const bool owner = q < ng;
+    const int t0 = owner ? q * ch : 0, t1 = owner ? min(RT, t0 + ch) : 0;
+    double racc[6], rbg[6];   // Ks, Kb <= 6
+#pragma unroll
+    for (int k = 0; k < 6; k++) racc[k] = rbg[k] = 0.0;
     double chi = 0.0, cnt = 0.0;
     __syncthreads();
     for (long base = (long)blockIdx.x * RT; base < nrows; base += (long)gridDim.x * RT) {
@@ -1159,55 +1174,71 @@ __global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const float* rw, 
         if (rho < nrows) {
             const float4* src = reinterpret_cast<const float4*>(rw + rho * RMETA);
 #pragma unroll
-            for (int q = 0; q < 4; q++) *reinterpret_cast<float4*>(o + 4 * q) = __ldg(src + q);
+            for (int u = 0; u < 4; u++) *reinterpret_cast<float4*>(o + 4 * u) = __ldg(src + u);
         } else {
 #pragma unroll
-            for (int q = 0; q < RMETA; q++) o[q] = 0.0f;
+            for (int u = 0; u < RMETA; u++) o[u] = 0.0f;
         }
         const bool use = o[0] > 0.0f;
         const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
         float model = 0.0f;   // sqrt(w) times the model
-        for (int n = 0; n < g.nb; n++) {
-            const float xv = use ? __ldg(g.X + ((long)s * g.nb + n) * g.ss + pix) : 0.0f;
-            Xs[n * RT + tid] = xv;
+        for (int n = 0; n < nb; n++) {
+            const float xv = use ? __ldg(g.X + ((long)s * nb + n) * g.ss + pix) : 0.0f;
+            Xs[tid * xst + n] = xv;
             float qn;
             if (n == 0) {
                 qn = af[0] * o[0];
             } else {
                 qn = 0.0f;
-                for (int k = 0; k < g.Ks; k++) qn = fmaf(o[k], af[1 + (n - 1) * g.Ks + k], qn);
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    if (k < Ks) qn = fmaf(o[k], af[1 + (n - 1) * Ks + k], qn);
             }
             model = fmaf(xv, qn, model);
         }
-        for (int k = 0; k < g.Kb; k++) model = fmaf(o[6 + k], af[nx + k], model);
+#pragma unroll
+        for (int k = 0; k < 6; k++)
+            if (k < Kb) model = fmaf(o[6 + k], af[nx + k], model);
         const float ew = use ? o[12] - model : 0.0f;   // sqrt(w) (I - model)
         chi += (double)ew * (double)ew;
         cnt += use ? 1.0 : 0.0;
-        for (int k = 0; k < g.Ks; k++) Gk[k * RT + tid] = ew * o[k];
-        for (int k = 0; k < g.Kb; k++) Gk[(g.Ks + k) * RT + tid] = ew * o[6 + k];
-        __syncthreads();
-        if (want_r) {
+        {
+            float gr[RG];
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int j = tid + h * RT;
-                if (j >= g.Nc) continue;
-                const float* xa;
-                const float* gb;
-                if (j < nx) {
-                    const int n = j == 0 ? 0 : 1 + (j - 1) / g.Ks, k = j == 0 ? 0 : (j - 1) % g.Ks;
-                    xa = Xs + n * RT;
-                    gb = Gk + k * RT;
-                } else {
-                    xa = nullptr;
-                    gb = Gk + (g.Ks + (j - nx)) * RT;
+            for (int k = 0; k < 6; k++) {
+                gr[k] = k < Ks ? ew * o[k] : 0.0f;
+                gr[8 + k] = k < Kb ? ew * o[6 + k] : 0.0f;
+            }
+            gr[6] = gr[7] = gr[14] = gr[15] = 0.0f;
+            float4* gd = reinterpret_cast<float4*>(Gs + tid * RG);
+#pragma unroll
+            for (int u = 0; u < 4; u++) gd[u] = make_float4(gr[4 * u], gr[4 * u + 1], gr[4 * u + 2], gr[4 * u + 3]);
+        }
+        __syncthreads();
+        if (want_r && owner) {
+            float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float abg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const bool bgt = m == 0;
+            for (int t = t0; t < t1; t++) {
+                const float xv = Xs[t * xst + m];
+                const float4 g0 = *reinterpret_cast<const float4*>(Gs + t * RG);
+                const float4 g1 = *reinterpret_cast<const float4*>(Gs + t * RG + 4);
+                acc[0] = fmaf(xv, g0.x, acc[0]);
+                acc[1] = fmaf(xv, g0.y, acc[1]);
+                acc[2] = fmaf(xv, g0.z, acc[2]);
+                acc[3] = fmaf(xv, g0.w, acc[3]);
+                acc[4] = fmaf(xv, g1.x, acc[4]);
+                acc[5] = fmaf(xv, g1.y, acc[5]);
+                if (bgt) {
+                    const float4 b0 = *reinterpret_cast<const float4*>(Gs + t * RG + 8);
+                    const float4 b1 = *reinterpret_cast<const float4*>(Gs + t * RG + 12);
+                    abg[0] += b0.x; abg[1] += b0.y; abg[2] += b0.z; abg[3] += b0.w; abg[4] += b1.x; abg[5] += b1.y;
                 }
-                float acc = 0.0f;
-                if (xa) {
-                    for (int t = 0; t < RT; t++) acc = fmaf(xa[t], gb[t], acc);
-                } else {
-                    for (int t = 0; t < RT; t++) acc += gb[t];
-                }
-                racc[h] += (double)acc;
+            }
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                racc[k] += (double)acc[k];
+                rbg[k] += (double)abg[k];
             }
         }
         __syncthreads();
@@ -1218,12 +1249,27 @@ __global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const float* rw, 
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     }
     if (lane == 0) { wchi[warp] = chi; wn[warp] = cnt; }
+    // the groups' sums, added in group order: red[q][m][k] (k < 6), then redbg[q][k]
+    double* red = reinterpret_cast<double*>(rsm);
+    double* redbg = red + ng * nb * 8;
+    if (want_r && owner) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) red[(q * nb + m) * 8 + k] = racc[k];
+        if (m == 0)
+#pragma unroll
+            for (int k = 0; k < 6; k++) redbg[q * 8 + k] = rbg[k];
+    }
     __syncthreads();
     double* out = part + (long)blockIdx.x * (g.NP + 4);
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int j = tid + h * RT;
-        if (j < g.Nc) out[j] = want_r ? racc[h] : 0.0;
+    for (int j = tid; j < g.Nc; j += RT) {
+        int mm, kk;
+        if (j == 0) { mm = 0; kk = 0; }
+        else if (j < nx) { mm = 1 + (j - 1) / Ks; kk = (j - 1) % Ks; }
+        else { mm = -1; kk = j - nx; }
+        double v = 0.0;
+        if (want_r)
+            for (int qq = 0; qq < ng; qq++) v += mm >= 0 ? red[(qq * nb + mm) * 8 + kk] : redbg[qq * 8 + kk];
+        out[j] = v;
     }
     if (tid == 0) {
         double c = 0.0, n = 0.0;
@@ -1986,7 +2032,10 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     argus_tri_solve(ctx, NP, n, ctx->M + n, NP, c, st);
     int nparts = ctx->num_sms * 2;
     if (nparts > ctx->resid_parts) nparts = ctx->resid_parts;
-    const size_t rsmem = sizeof(float) * (size_t)(d.nb + d.Ks + d.Kb) * RT;
+    // rows staged as Gs [RT][RG] and Xs [RT][xst] floats; the group sums reuse the
+    // space as [RT / nb][nb][8] + [RT / nb][8] doubles (at most 2 * 256 * 8 doubles)
+    size_t rsmem = sizeof(float) * (size_t)(RG + resid_xst(d.nb)) * RT;
+    if (rsmem < sizeof(double) * RT * 16) rsmem = sizeof(double) * RT * 16;
     cudaFuncSetAttribute(resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
     const int rr_blocks = (n + 2 + 7) / 8;
     for (int it = 0; it < REFINE_MAX; it++) {

@@ -47,7 +47,7 @@
 // function of i + j, so the descriptor's row-group stride equals its K-group
 // stride (both 128 bytes) and 16-byte row t of the stored operand is
 // R(x0 - r + t + b), b = 0..7.  A producer warp rounds its source row to BF16
-// once (lane c: values 8c .. 8c + 7) into a small row buffer; lane l then
+// once (lane l: value pairs l, l + 32, ...) into a small row buffer; lane l then
 // writes operand rows t = l, l + 32, ... (consecutive lanes, consecutive 16-byte
 // rows: no bank conflicts), each from five aligned 32-bit words of the buffer
 // and a byte permutation (rows starting at an odd element straddle words).
@@ -347,11 +347,11 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1)
     if (warp >= 4 && warp < MMA_WARP) {
         // ---------------- producers: warp 4 + pw writes the A operands of source rows
         // pw RPW .. pw RPW + RPW - 1 of every block, with no barrier between producer
-        // warps.  Lane 0 copies those rows' windows (PWIN values from frame column XS, a
-        // multiple of 4, RPW rows: one box) LA blocks ahead into the warp's slot ring;
-        // lane c <= NCM rounds R(x0 - R + 8c .. 8c + 7), and the lanes write the operand
-        // rows; after the writes and a proxy fence lane 0 arrives on the stage's filled
-        // barrier (one arrival per producer warp).
+        // warps.  The warp stages those rows' windows (PWIN values from frame column XS, a
+        // multiple of 4; variance: lane 0, one box of RPW rows) LA blocks ahead into its
+        // slot ring; the lanes round each row to BF16 once and write its operand rows;
+        // after the writes and a proxy fence lane 0 arrives on the stage's filled barrier
+        // (one arrival per producer warp).
         const int pw = warp - 4;
         bool run = true;
         int gb = 0, li = 0, gs = 0;   // gs: this warp's blocks over the items
@@ -424,22 +424,18 @@ __global__ void __launch_bounds__(TC_THREADS, VAR ? 2 : 1)
                     // rows past the band's source rows are zero (the difference image's copies
                     // zero-fill them already)
                     const bool rin = !VAR || blk * G + g < nsrc;
-                    // round the row once: lane c <= NCM, values 8c .. 8c + 7 (hi, and lo)
-                    if (lane <= NCM) {
-                        const float* src = S.wsrc[pw][sl] + rq * PWIN + SOFF + 8 * lane;
-                        float v[8];
+                    // round the row once: lane l takes value pairs l, l + 32, ... (values 2p, 2p + 1:
+                    // consecutive lanes read and write consecutive words, no bank conflicts)
+                    {
+                        const float* src = S.wsrc[pw][sl] + rq * PWIN + SOFF;
 #pragma unroll
-                        for (int k = 0; k < 8; k++) v[k] = rin ? src[k] : 0.0f;
-                        uint32_t h[4], l[4];
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            h[k] = bf16x2_rn(v[2 * k], v[2 * k + 1]);
-                            l[k] = NP == 2 ? bf16x2_rn(v[2 * k] - __uint_as_float(h[k] << 16),
-                                                       v[2 * k + 1] - __uint_as_float(h[k] & 0xffff0000u))
-                                           : 0u;
+                        for (int p = lane; p < 4 * (NCM + 1); p += 32) {
+                            const float v0 = rin ? src[2 * p] : 0.0f, v1 = rin ? src[2 * p + 1] : 0.0f;
+                            const uint32_t h = bf16x2_rn(v0, v1);
+                            rb[0][p] = h;
+                            if constexpr (NP == 2)
+                                rb[NP - 1][p] = bf16x2_rn(v0 - __uint_as_float(h << 16), v1 - __uint_as_float(h & 0xffff0000u));
                         }
-                        *reinterpret_cast<uint4*>(&rb[0][4 * lane]) = make_uint4(h[0], h[1], h[2], h[3]);
-                        if constexpr (NP == 2) *reinterpret_cast<uint4*>(&rb[NP - 1][4 * lane]) = make_uint4(l[0], l[1], l[2], l[3]);
                     }
                     __syncwarp();
                     // operand row t = lane + 32 rho holds elements t .. t + 7 of the rounded row
