@@ -567,7 +567,7 @@ def bench_segments(device, stream, cameras, log=None):
     basis = B.make_basis(15, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)
     key = f"segments_{cameras}x{per}_ks15"
     cfg = tuned_config(key)
-    batch = SegmentBatch(sides, basis=basis, width=2048, cfg=cfg or B.argus_seg_config(8, 1, 4, 0),
+    batch = SegmentBatch(sides, basis=basis, width=2048, cfg=cfg or B.argus_seg_config(64, 1, 8, 0),
                          device=device.index)
     try:
         t0 = time.time()
@@ -584,7 +584,8 @@ def bench_segments(device, stream, cameras, log=None):
     px = sum(s * s for s in sides)
     return {"workload": f"{cameras} cameras x {per} segments, 64-512 px log-uniform, 15x15 kernel per segment",
             "segments": len(sides), "pixels": px, "ms": round(ms, 3), "value": round(px / 1e6 / (ms / 1e3), 1),
-            "unit": "Mpix/s", "config": {"fit_ctas_per_sm": cfg.fit_ctas_per_sm, "sub_ctas_per_sm": cfg.sub_ctas_per_sm},
+            "unit": "Mpix/s", "config": {"fit_band": cfg.fit_band, "fit_ctas_per_sm": cfg.fit_ctas_per_sm,
+                                         "sub_ctas_per_sm": cfg.sub_ctas_per_sm},
             "work_units": {"fit": fit_items, "subtract": sub_items}, "sources": nsrc, "status": st,
             "generation_s": round(gen_s, 1)}
 

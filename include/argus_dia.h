@@ -291,7 +291,8 @@ typedef struct {
 
 /* Launch shape of the batched kernels (picked by the autotuner). */
 typedef struct {
-    int fit_band;          /* reserved for the fit work-unit height (the kernel uses 8-row bands) */
+    int fit_band;          /* interior rows per fit work unit (8..128; even) of the tensor-core fit
+                              (kernel sides <= 15); the CUDA-core fit (side 21) uses 8-row bands */
     int fit_ctas_per_sm;   /* persistent fit CTAs per SM (1..4) */
     int sub_ctas_per_sm;   /* persistent subtraction CTAs per SM (1..16) */
     int reserved;

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "basis.cuh"
+#include "segments_fit.cuh"
 #include "subtract_tile.cuh"
 
 struct argus_seg_plan {
@@ -38,8 +39,14 @@ struct argus_seg_plan {
     int NPC;               // Gram columns: nb + 2 (basis, background, target)
     argus_seg_config cfg;
     int4* d_seg;           // (row0, side, col0, -)
-    int2* d_fit_items;     // (segment, band y0)
+    int2* d_fit_items;     // (segment, band y0): CUDA-core fit
     int n_fit_items;
+    int fit_tc;            // the fit runs on the tensor cores (kernel sides <= 15)
+    int4* d_fit_tc_items;  // (segment, x0, y0, -): tensor-core fit, 128 columns x band rows
+    int n_fit_tc_items;
+    int* d_fit_tc_start;   // [fit_tc_ctas + 1] item range of each CTA, equal row pairs
+    float* d_rscale;       // [n] per-segment scale of R for the FP16 operands
+    int fit_tc_ctas;
     int2* d_sub_items;     // (segment, tile index)
     int n_sub_items;
     int* d_counters;       // [4]
@@ -469,11 +476,41 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     // work items, largest segments first
     std::sort(order.begin(), order.end(), [&](int a, int b) { return table[a].side > table[b].side; });
     std::vector<int2> fit_items, sub_items;
+    std::vector<int4> fit_tc_items;
+    const int NPC0 = bd.nb + 2;
+    const bool fit_tc = argus_seg_fit_tc_smem(bd.ks, NPC0) != 0 && argus_seg_fit_tc_smem(bd.ks, NPC0) <= 227 * 1024 &&
+                        bd.nb <= 56;
+    const int band = c.fit_band & ~1;   // the tensor-core fit's rows per item (pairs of rows)
+    std::vector<int> fit_tc_start;
     for (int i : order) {
         const int side = table[i].side;
-        for (int y0 = bd.r; y0 < side - bd.r; y0 += FIT_ROWS) fit_items.push_back(make_int2(i, y0));
+        if (fit_tc) {
+            for (int y0 = bd.r; y0 < side - bd.r; y0 += band)
+                for (int x0 = bd.r; x0 < side - bd.r; x0 += 128) fit_tc_items.push_back(make_int4(i, x0, y0, 0));
+        } else {
+            for (int y0 = bd.r; y0 < side - bd.r; y0 += FIT_ROWS) fit_items.push_back(make_int2(i, y0));
+        }
         const int nt = (side + 31) / 32;
         for (int t = 0; t < nt * nt; t++) sub_items.push_back(make_int2(i, t));
+    }
+    // the tensor-core fit's CTA ranges: row pairs (its unit of work) split evenly over one CTA per SM
+    int fit_tc_ctas = 0;
+    if (fit_tc) {
+        std::vector<long> cum(fit_tc_items.size() + 1, 0);
+        for (size_t k = 0; k < fit_tc_items.size(); k++) {
+            const int4 it = fit_tc_items[k];
+            const int rows = std::min(band, table[it.x].side - bd.r - it.z);
+            cum[k + 1] = cum[k] + (rows + 1) / 2;
+        }
+        fit_tc_ctas = std::max(1, std::min(ctx->num_sms, (int)fit_tc_items.size()));
+        fit_tc_start.assign(fit_tc_ctas + 1, 0);
+        size_t k = 0;
+        for (int b = 1; b < fit_tc_ctas; b++) {
+            const long target = cum.back() * b / fit_tc_ctas;
+            while (k < fit_tc_items.size() && cum[k] < target) k++;
+            fit_tc_start[b] = (int)k;
+        }
+        fit_tc_start[fit_tc_ctas] = (int)fit_tc_items.size();
     }
     // shared memory of the fit kernel: transposed basis taps, design chunk, reference window
     const int NPC = bd.nb + 2;
@@ -481,7 +518,7 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     const size_t fit_smem = sizeof(float) * ((size_t)ng * bd.ks * bd.ks * FG + (size_t)FIT_CH * (NPC + 1) +
                                              (size_t)(FIT_ROWS + bd.ks - 1) * (512 + bd.ks - 1));
     const int nbk = (NPC + 3) / 4;
-    if (fit_smem > 220 * 1024 || ng > 8 || nbk * (nbk + 1) / 2 > 256) return ARGUS_ERR_UNSUPPORTED;
+    if (!fit_tc && (fit_smem > 220 * 1024 || ng > 8 || nbk * (nbk + 1) / 2 > 256)) return ARGUS_ERR_UNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     argus_seg_plan* p = (argus_seg_plan*)calloc(1, sizeof(argus_seg_plan));
     if (!p) return ARGUS_ERR_NOMEM;
@@ -489,8 +526,14 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     p->basis = *basis; p->bd = bd; p->NPC = NPC; p->cfg = c;
     p->n_fit_items = (int)fit_items.size();
     p->n_sub_items = (int)sub_items.size();
+    p->fit_tc = fit_tc ? 1 : 0;
+    p->n_fit_tc_items = (int)fit_tc_items.size();
+    p->fit_tc_ctas = fit_tc_ctas;
     bool ok = cudaMalloc(&p->d_seg, sizeof(int4) * n) == cudaSuccess &&
-              cudaMalloc(&p->d_fit_items, sizeof(int2) * fit_items.size()) == cudaSuccess &&
+              cudaMalloc(&p->d_fit_items, sizeof(int2) * (fit_items.size() + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_fit_tc_items, sizeof(int4) * (fit_tc_items.size() + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_fit_tc_start, sizeof(int) * (fit_tc_start.size() + 1)) == cudaSuccess &&
+              cudaMalloc(&p->d_rscale, sizeof(float) * n) == cudaSuccess &&
               cudaMalloc(&p->d_sub_items, sizeof(int2) * sub_items.size()) == cudaSuccess &&
               cudaMalloc(&p->d_counters, sizeof(int) * 4) == cudaSuccess &&
               cudaMalloc(&p->d_gram, sizeof(double) * (size_t)n * NPC * NPC) == cudaSuccess &&
@@ -498,8 +541,14 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
               cudaMalloc(&p->d_bg, sizeof(double) * (size_t)n) == cudaSuccess;
     if (ok)
         ok = cudaMemcpy(p->d_seg, seg.data(), sizeof(int4) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(p->d_fit_items, fit_items.data(), sizeof(int2) * fit_items.size(),
-                        cudaMemcpyHostToDevice) == cudaSuccess &&
+             (fit_items.empty() || cudaMemcpy(p->d_fit_items, fit_items.data(), sizeof(int2) * fit_items.size(),
+                                              cudaMemcpyHostToDevice) == cudaSuccess) &&
+             (fit_tc_items.empty() || cudaMemcpy(p->d_fit_tc_items, fit_tc_items.data(),
+                                                 sizeof(int4) * fit_tc_items.size(),
+                                                 cudaMemcpyHostToDevice) == cudaSuccess) &&
+             (fit_tc_start.empty() || cudaMemcpy(p->d_fit_tc_start, fit_tc_start.data(),
+                                                 sizeof(int) * fit_tc_start.size(),
+                                                 cudaMemcpyHostToDevice) == cudaSuccess) &&
              cudaMemcpy(p->d_sub_items, sub_items.data(), sizeof(int2) * sub_items.size(),
                         cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
@@ -526,7 +575,7 @@ extern "C" int argus_segments_destroy(argus_seg_plan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    void* ps[] = {p->d_seg, p->d_fit_items, p->d_sub_items, p->d_counters, p->d_gram, p->d_K, p->d_bg};
+    void* ps[] = {p->d_seg, p->d_fit_items, p->d_fit_tc_items, p->d_fit_tc_start, p->d_rscale, p->d_sub_items, p->d_counters, p->d_gram, p->d_K, p->d_bg};
     for (void* q : ps)
         if (q) cudaFree(q);
     free(p);
@@ -547,14 +596,24 @@ static int segments_enqueue(argus_seg_plan* p, const float* sci, const float* sc
     if ((size_t)p->n * sizeof(int) > (size_t)ctx->resid_parts * (ctx->np_cols + 4) * sizeof(double))
         return ARGUS_ERR_CAPACITY;
     if (cudaMemsetAsync(npix, 0, sizeof(int) * p->n, st) != cudaSuccess) return ARGUS_ERR_CUDA;
+    if (p->fit_tc) {
+        SegFitTcArgs ta;
+        ta.sci = sci; ta.var = sci_var; ta.ref = ref; ta.flags = flags; ta.pitch = p->pitch; ta.seg = p->d_seg;
+        ta.items = p->d_fit_tc_items; ta.n_items = p->n_fit_tc_items; ta.cta_start = p->d_fit_tc_start;
+        ta.n_ctas = p->fit_tc_ctas; ta.bimg = ctx->basis_imgf; ta.nb = bd.nb;
+        ta.NPC = NPC; ta.band = p->cfg.fit_band & ~1; ta.gram = p->d_gram; ta.n_pix = npix; ta.status = ctx->d_status;
+        ta.rscale = p->d_rscale; ta.n_segments = p->n;
+        const int trc = argus_seg_fit_tc(ta, bd.ks, st);
+        if (trc) return trc;
+    }
     SegFitArgs fa;
     fa.sci = sci; fa.var = sci_var; fa.ref = ref; fa.flags = flags; fa.pitch = p->pitch; fa.seg = p->d_seg;
     fa.items = p->d_fit_items; fa.n_items = p->n_fit_items; fa.counter = p->d_counters;
     fa.bimg = ctx->basis_imgf; fa.nb = bd.nb; fa.ks = bd.ks; fa.r = bd.r; fa.NPC = NPC;
     fa.ngroups = (bd.nb + FG - 1) / FG; fa.gram = p->d_gram; fa.n_pix = npix;
     const int fgrid = ctx->num_sms * p->cfg.fit_ctas_per_sm;
-    int frc;
-    switch (bd.ks) {
+    int frc = ARGUS_OK;
+    if (!p->fit_tc) switch (bd.ks) {
         case 7: frc = launch_seg_fit<7>(fa, fgrid, st); break;
         case 9: frc = launch_seg_fit<9>(fa, fgrid, st); break;
         case 11: frc = launch_seg_fit<11>(fa, fgrid, st); break;
@@ -644,7 +703,7 @@ extern "C" int argus_segments_run(argus_seg_plan* p, const float* sci, const flo
 
 extern "C" int argus_segments_items(const argus_seg_plan* p, int* n_fit_items, int* n_sub_items) {
     if (!p) return ARGUS_ERR_ARG;
-    if (n_fit_items) *n_fit_items = p->n_fit_items;
+    if (n_fit_items) *n_fit_items = p->fit_tc ? p->n_fit_tc_items : p->n_fit_items;
     if (n_sub_items) *n_sub_items = p->n_sub_items;
     return ARGUS_OK;
 }

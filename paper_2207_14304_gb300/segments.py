@@ -126,12 +126,15 @@ C_SIZE_STATS = 16
 
 
 def candidate_configs():
-    """Launch shapes the autotuner tries: persistent CTAs per SM of the fit and of the
-    subtraction kernels (the fit's work unit is a fixed 8-row band)."""
+    """Launch shapes the autotuner tries: rows per fit work unit (the tensor-core fit of
+    kernel sides <= 15; one CTA per SM), persistent CTAs per SM of the CUDA-core fit
+    (side 21, 8-row units) and of the subtraction kernels."""
     out = []
-    for fcta in (1, 2):
-        for scta in (2, 4, 6, 8):
-            out.append((8, fcta, scta))
+    for band in (32, 64, 128):
+        for scta in (4, 8):
+            out.append((band, 1, scta))
+    for scta in (4, 8):
+        out.append((8, 2, scta))
     return out
 
 
