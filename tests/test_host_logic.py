@@ -52,8 +52,13 @@ def test_tuned_config_table(tmp_path):
     assert tuned_config("other", table_path=path) is None
     open(path, "w").write("{not json")
     assert tuned_config("k", table_path=path) is None
+    # candidates: distinct launch shapes the plan accepts (fit bands even, 8..128; fit CTAs 1..4;
+    # subtraction CTAs 1..16), among them the CUDA-core fit's 8-row units and larger
+    # tensor-core fit bands
     cands = candidate_configs()
-    assert len(cands) == len(set(cands)) and all(c[0] == 8 for c in cands)
+    assert len(cands) == len(set(cands))
+    assert all(c[0] % 2 == 0 and 8 <= c[0] <= 128 and 1 <= c[1] <= 4 and 1 <= c[2] <= 16 for c in cands)
+    assert any(c[0] == 8 for c in cands) and any(c[0] > 8 for c in cands)
 
 
 def _free_port():
