@@ -1,7 +1,7 @@
 // K7: variance-weighted threshold detection on the difference image (paper
 // Sec. 4.2 transient candidates; Table 2 "Source detection").
 //
-//  1. mask pass (HBM-bound, 4 pixels per thread, 128-bit loads of D and V_D):
+//  1. mask pass (HBM-bound, 16 pixels per thread, 128-bit loads of D, V_D and flags):
 //     S = D / sqrt(V_D) in IEEE float, mask bits, and a compact list of the
 //     above-threshold pixels (warp-aggregated append); label[p] = p.
 //  2. union-find over the list only (8-connectivity, equal sign): lock-free
@@ -50,33 +50,49 @@ __device__ __forceinline__ uint8_t mask_of(float d, float v, uint8_t f, float ns
 }
 
 __global__ void __launch_bounds__(256) mask_kernel(DetArgs a) {
-    const long vpr = a.pitch >> 2;
+    // 16 pixels per thread and step: four 128-bit loads of D and of V_D, one of the flags,
+    // one 128-bit store of the mask (rows start on 16-pixel boundaries: pitch % 16 == 0)
+    const long vpr = a.pitch >> 4;
     const long nv = vpr * a.h;
     const int lane = threadIdx.x & 31;
     for (long v0 = blockIdx.x * (long)blockDim.x; v0 < nv; v0 += (long)gridDim.x * blockDim.x) {
         const long v = v0 + threadIdx.x;
         int nset = 0;
         long p0 = 0;
-        uint8_t m[4] = {0, 0, 0, 0};
+        uint8_t m[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) m[i] = 0;
         if (v < nv) {
             const long y = v / vpr;
-            const int x0 = (int)(v - y * vpr) << 2;
+            const int x0 = (int)(v - y * vpr) << 4;
             p0 = y * a.pitch + x0;
             if (x0 < a.w) {
-                const float4 d4 = *reinterpret_cast<const float4*>(a.D + p0);
-                const float4 v4 = *reinterpret_cast<const float4*>(a.V + p0);
-                const uchar4 f4 = *reinterpret_cast<const uchar4*>(a.flags + p0);
-                float s;
-                m[0] = mask_of(d4.x, v4.x, f4.x, a.nsig, s);
-                m[1] = mask_of(d4.y, v4.y, f4.y, a.nsig, s);
-                m[2] = mask_of(d4.z, v4.z, f4.z, a.nsig, s);
-                m[3] = mask_of(d4.w, v4.w, f4.w, a.nsig, s);
-                if (x0 + 4 <= a.w) {
-                    *reinterpret_cast<uchar4*>(a.mask + p0) = make_uchar4(m[0], m[1], m[2], m[3]);
-                } else {
-                    for (int i = 0; x0 + i < a.w; i++) a.mask[p0 + i] = m[i];
+                const uint4 f16 = *reinterpret_cast<const uint4*>(a.flags + p0);
+                const uint32_t fw[4] = {f16.x, f16.y, f16.z, f16.w};
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const float4 d4 = *reinterpret_cast<const float4*>(a.D + p0 + 4 * k);
+                    const float4 v4 = *reinterpret_cast<const float4*>(a.V + p0 + 4 * k);
+                    float s;
+                    m[4 * k + 0] = mask_of(d4.x, v4.x, (uint8_t)(fw[k] & 0xffu), a.nsig, s);
+                    m[4 * k + 1] = mask_of(d4.y, v4.y, (uint8_t)((fw[k] >> 8) & 0xffu), a.nsig, s);
+                    m[4 * k + 2] = mask_of(d4.z, v4.z, (uint8_t)((fw[k] >> 16) & 0xffu), a.nsig, s);
+                    m[4 * k + 3] = mask_of(d4.w, v4.w, (uint8_t)(fw[k] >> 24), a.nsig, s);
                 }
-                for (int i = 0; i < 4; i++) {
+                if (x0 + 16 <= a.w) {
+                    uint32_t mw[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        mw[k] = (uint32_t)m[4 * k] | ((uint32_t)m[4 * k + 1] << 8) | ((uint32_t)m[4 * k + 2] << 16) |
+                                ((uint32_t)m[4 * k + 3] << 24);
+                    *reinterpret_cast<uint4*>(a.mask + p0) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        if (x0 + i < a.w) a.mask[p0 + i] = m[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
                     if (x0 + i >= a.w) m[i] = 0;
                     nset += (m[i] & 3) ? 1 : 0;
                 }
@@ -95,7 +111,8 @@ __global__ void __launch_bounds__(256) mask_kernel(DetArgs a) {
         base = __shfl_sync(0xffffffffu, base, 31);
         if (nset) {
             int pos = base + incl - nset;
-            for (int i = 0; i < 4; i++) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
                 if (m[i] & 3) {
                     if (pos < a.cap) {
                         a.list[pos] = (int)(p0 + i);
@@ -372,7 +389,7 @@ extern "C" int argus_detect(argus_ctx* ctx, const float* diff, const float* diff
     if (cudaMemsetAsync(ctx->det_count, 0, 2 * sizeof(int), s) != cudaSuccess) return ARGUS_ERR_CUDA;
     if (cudaMemsetAsync(ctx->row_count, 0, sizeof(int) * (2 * (size_t)shape.h + 2), s) != cudaSuccess)
         return ARGUS_ERR_CUDA;
-    const long nv = (shape.pitch / 4) * (long)shape.h;
+    const long nv = (shape.pitch / 16) * (long)shape.h;
     long blocks = (nv + 255) / 256;
     if (blocks > (long)ctx->num_sms * 8) blocks = (long)ctx->num_sms * 8;
     mask_kernel<<<(unsigned)blocks, 256, 0, s>>>(a); argus_count_launch(1);
