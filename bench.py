@@ -47,10 +47,10 @@ BYTES_PER_PX = 2 + 4 + 4 + 1 + 4 + 4 + 4 + 4 + 1
 # launch, scaled by pixels to the frame (the kernel streams its bands once, so traffic
 # grows in proportion).  It holds only for the kernel sources it was taken on (None
 # until a capture of these sources is recorded here).
-SUBTRACT_TRAFFIC = {"bytes_per_px": 11.4330, "sources_sha1": "742991b03a7e077a2df7c354b361e8e70989f863",
+SUBTRACT_TRAFFIC = {"bytes_per_px": 11.4422, "sources_sha1": "b88d70334bc10c960f3a5630a72c35fb9f6525bc",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh")}
 # the same for the difference-variance kernel (V_I, V_ref and flags in, V_D out)
-VARIANCE_TRAFFIC = {"bytes_per_px": 11.4742, "sources_sha1": "22be4cba892a1156e31bc5d354f56b8d3e1e3b01",
+VARIANCE_TRAFFIC = {"bytes_per_px": 11.4747, "sources_sha1": "9332ad8c9b092988cc87fafc1738f66d06951598",
                     "sources": ("subtract_tc.cu", "subtract_tile.cuh", "tc_ptx.cuh", "subtract.cu")}
 
 
