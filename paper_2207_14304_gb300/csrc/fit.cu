@@ -1182,6 +1182,8 @@ __global__ void __launch_bounds__(RT) resid_kernel(GramArgs g, const float* rw, 
         const bool use = o[0] > 0.0f;
         const int s = (int)(rho / g.ss), pix = (int)(rho - (long)s * g.ss);
         float model = 0.0f;   // sqrt(w) times the model
+        // the row's nb design values are independent loads: unrolled so that several are in flight
+#pragma unroll 8
         for (int n = 0; n < nb; n++) {
             const float xv = use ? __ldg(g.X + ((long)s * nb + n) * g.ss + pix) : 0.0f;
             Xs[tid * xst + n] = xv;
@@ -1559,7 +1561,9 @@ __host__ __device__ inline SelGeom sel_geom(int iso) {
     g.ox = (4 - ((iso + 1) & 3)) & 3;                     // r column 0 is frame x0 - iso - 1 - ox
     g.rw = (SEL_TX + 2 * iso + 2 + g.ox + 3) & ~3;
     g.rh = SEL_TY + 2 * iso + 2;
-    g.mw = SEL_TX + 2 * g.qr;
+    // mv rows are padded so that 4-column groups aligned with r start on 16-byte boundaries
+    // (mv element (jy, jx) at jy * mw + jx + moff, moff = (4 - qr % 4) % 4)
+    g.mw = (SEL_TX + 2 * g.qr + (4 - g.qr % 4) % 4 + 3) & ~3;
     g.mh = SEL_TY + 2 * g.qr;
     return g;
 }
@@ -1609,18 +1613,21 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) select_tile_kernel(const float
                                                                     float max_peak, int iso, float iso_frac,
                                                                     unsigned long long* cell_key) {
     constexpr int MW = SEL_TX + 2 * QR, MH = SEL_TY + 2 * QR;
+    constexpr int MOFF = (4 - QR % 4) % 4;                       // r column of mv column 0 is cx = -QR mod 4
+    constexpr int MWP = (MW + MOFF + 3) & ~3;                    // padded mv row
     extern __shared__ float4 sel_smem[];
     const SelGeom g = sel_geom(iso);
     float* r = reinterpret_cast<float*>(sel_smem);              // [rh][rw]
-    float* mv = r + g.rw * (g.rh + SEL_RPAD);                    // [MH][MW]
-    unsigned short* cand = reinterpret_cast<unsigned short*>(mv + MW * MH);
+    float* mvr = r + g.rw * (g.rh + SEL_RPAD);                   // [MH][MWP]
+    float* mv = mvr + MOFF;                                      // mv[jy * MWP + jx]
+    unsigned short* cand = reinterpret_cast<unsigned short*>(mvr + MWP * MH);
     unsigned short* surv = cand + SEL_LIST;
-    __shared__ int n_cand, n_surv;
+    __shared__ int n_cand, n_surv, n_fin;
     const int ntx = (w + SEL_TX - 1) / SEL_TX;
     const int x0 = (int)(blockIdx.x % ntx) * SEL_TX, y0 = (int)(blockIdx.x / ntx) * SEL_TY;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = SEL_THREADS / 32;
     const int XS = x0 - iso - 1 - g.ox, YS = y0 - iso - 1;      // frame position of r[0][0]
-    if (tid == 0) { n_cand = 0; n_surv = 0; }
+    if (tid == 0) { n_cand = 0; n_surv = 0; n_fin = 0; }
     // 1. stage R in 16-byte chunks; XS is a multiple of 4, so a chunk is inside or
     //    outside the frame but for the one that holds column w (partly zero-filled)
     {
@@ -1640,85 +1647,109 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) select_tile_kernel(const float
         tc::cp_async_wait<0>();
     }
     __syncthreads();
-    // 2. masked strict local maxima over the tile + QR, four rows per item, and the
-    //    candidate list
+    // 2. masked strict local maxima over the tile + QR, four rows x four columns per item
+    //    (each row of the item is one aligned 16-byte load of r and its two neighbours),
+    //    and the candidate list
     const float NEG = __int_as_float(0xff800000), INF = __int_as_float(0x7f800000);
     {
-        const int cx = iso + 1 + g.ox - QR, cy = iso + 1 - QR;     // r position of mv[0][0]
-        constexpr int NSTRIP = (MH + 3) / 4, N = MW * NSTRIP;
-        constexpr int SS = SEL_THREADS / MW, SX = SEL_THREADS - SS * MW;
-        int js = tid / MW, jx = tid - js * MW;
+        const int cx = iso + 1 + g.ox - QR, cy = iso + 1 - QR;     // r position of mv[0][0]; cx % 4 == MOFF
+        constexpr int NSTRIP = (MH + 3) / 4, NCG = MWP / 4, N = NCG * NSTRIP;
         for (int e = tid; e < N; e += SEL_THREADS) {
-            const int jy0 = 4 * js;
-            const float* q = r + (cy + jy0 - 1) * g.rw + (cx + jx);
-            float h3[6], lft[6], rgt[6], ctr[6];
+            const int js = e / NCG, jg = e - js * NCG;
+            const int jy0 = 4 * js, jx0 = 4 * jg - MOFF;          // columns jx0 .. jx0 + 3 (cx + jx0: 16-byte aligned)
+            const float* q = r + (cy + jy0 - 1) * g.rw + (cx + jx0);
+            // v[t][k]: r at row jy0 - 1 + t, column jx0 - 1 + k
+            float v[6][6], h3[6][4];
 #pragma unroll
             for (int t = 0; t < 6; t++) {
                 const float* qt = q + t * g.rw;
-                lft[t] = qt[-1];
-                ctr[t] = qt[0];
-                rgt[t] = qt[1];
-                h3[t] = fmax_nan(fmax_nan(lft[t], ctr[t]), rgt[t]);
+                const float4 c4 = *reinterpret_cast<const float4*>(qt);
+                v[t][0] = cx + jx0 > 0 ? qt[-1] : NEG;   // r column -1 only feeds a column jx < 0 (discarded)
+                v[t][1] = c4.x; v[t][2] = c4.y; v[t][3] = c4.z; v[t][4] = c4.w;
+                v[t][5] = qt[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) h3[t][c] = fmax_nan(fmax_nan(v[t][c], v[t][c + 1]), v[t][c + 2]);
             }
-            const int X = x0 - QR + jx, x = jx - QR;
-            const bool xin = X >= 1 && X <= w - 2;
-            const bool xc = x >= 0 && x < SEL_TX && X - m >= 0 && X + m <= w - 1;
-            // candidates of this strip: at most two (vertical neighbours are never both maxima)
-            int nc = 0, e0 = 0, e1 = 0;
+            int nc = 0, ev0 = 0, ev1 = 0, ev2 = 0, ev3 = 0;
 #pragma unroll
             for (int t = 1; t <= 4; t++) {
                 const int jy = jy0 + t - 1, y = jy - QR;
                 const int Y = y0 + y;
-                const float c = ctr[t];
-                const float nb = fmax_nan(fmax_nan(h3[t - 1], h3[t + 1]), fmax_nan(lft[t], rgt[t]));
-                const bool l = jy < MH && xin && Y >= 1 && Y <= h - 2 && c > nb && c < INF;
-                if (jy < MH) mv[jy * MW + jx] = l ? c : NEG;
-                if (l && xc && y >= 0 && y < SEL_TY && Y - m >= 0 && Y + m <= h - 1 && c < max_peak) {
-                    const int ev = y * SEL_TX + x;
-                    if (nc == 0) e0 = ev; else e1 = ev;
-                    nc++;
+                float o[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const int jx = jx0 + c, x = jx - QR, X = x0 - QR + jx;
+                    const bool xin = X >= 1 && X <= w - 2;
+                    const bool xc = x >= 0 && x < SEL_TX && X - m >= 0 && X + m <= w - 1;
+                    const float cv = v[t][c + 1];
+                    const float nb = fmax_nan(fmax_nan(h3[t - 1][c], h3[t + 1][c]), fmax_nan(v[t][c], v[t][c + 2]));
+                    const bool l = jy < MH && jx >= 0 && jx < MW && xin && Y >= 1 && Y <= h - 2 && cv > nb && cv < INF;
+                    o[c] = l ? cv : NEG;
+                    // at most one strict maximum per 2 x 2 block: at most four per item
+                    if (l && xc && y >= 0 && y < SEL_TY && Y - m >= 0 && Y + m <= h - 1 && cv < max_peak) {
+                        const int ev = y * SEL_TX + x;
+                        ev3 = nc == 3 ? ev : ev3;
+                        ev2 = nc == 2 ? ev : ev2;
+                        ev1 = nc == 1 ? ev : ev1;
+                        ev0 = nc == 0 ? ev : ev0;
+                        nc++;
+                    }
                 }
+                if (jy < MH) *reinterpret_cast<float4*>(mv + jy * MWP + jx0) = make_float4(o[0], o[1], o[2], o[3]);
             }
-            // warp-aggregated append: nc = b0 + 2 b1 per lane
-            const unsigned act = __activemask();
-            const unsigned b0 = __ballot_sync(act, nc & 1), b1 = __ballot_sync(act, nc & 2);
-            if (b0 | b1) {
-                const int leader = __ffs(act) - 1;
-                const unsigned lt = (1u << lane) - 1u;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&n_cand, __popc(b0) + 2 * __popc(b1));
-                base = __shfl_sync(act, base, leader) + __popc(b0 & lt) + 2 * __popc(b1 & lt);
-                if (nc > 0) cand[base] = (unsigned short)e0;
-                if (nc > 1) cand[base + 1] = (unsigned short)e1;
+            if (nc) {
+                const int base = atomicAdd(&n_cand, nc);
+                cand[base] = (unsigned short)ev0;
+                if (nc > 1) cand[base + 1] = (unsigned short)ev1;
+                if (nc > 2) cand[base + 2] = (unsigned short)ev2;
+                if (nc > 3) cand[base + 3] = (unsigned short)ev3;
             }
-            jx += SX;
-            js += SS;
-            if (jx >= MW) { jx -= MW; js++; }
         }
     }
     __syncthreads();
-    // 3. the other maxima within QR
+    // 3. the other maxima within QR: radius 1 holds none (the neighbours of a strict
+    //    maximum are below it, so none of them is one); radius 2 for every candidate,
+    //    radius 3 only for the survivors of radius 2 (most noise peaks meet another
+    //    maximum at radius 2), listed in between so that warps stay full
     for (int i = tid; i < n_cand; i += SEL_THREADS) {
         const int e = cand[i];
         const int y = e / SEL_TX, x = e - y * SEL_TX;
-        const float* q = mv + y * MW + x;                          // window corner (y - QR, x - QR)
-        const float c = q[QR * MW + QR];
+        const float* q = mv + y * MWP + x;                         // window corner (y - QR, x - QR)
+        const float c = q[QR * MWP + QR];
         float other = NEG;
+        if (QR >= 2) {
 #pragma unroll
-        for (int dy = 0; dy <= 2 * QR; dy++)
+            for (int dy = QR - 2; dy <= QR + 2; dy++)
 #pragma unroll
-            for (int dx = 0; dx <= 2 * QR; dx++)
-                if (dy != QR || dx != QR) other = fmaxf(other, q[dy * MW + dx]);
+                for (int dx = QR - 2; dx <= QR + 2; dx++)
+                    if (dy == QR - 2 || dy == QR + 2 || dx == QR - 2 || dx == QR + 2) other = fmaxf(other, q[dy * MWP + dx]);
+        }
         if (!(other > iso_frac * c)) surv[atomicAdd(&n_surv, 1)] = (unsigned short)e;
+    }
+    __syncthreads();
+    for (int i = tid; i < n_surv; i += SEL_THREADS) {
+        const int e = surv[i];
+        const int y = e / SEL_TX, x = e - y * SEL_TX;
+        const float* q = mv + y * MWP + x;
+        const float c = q[QR * MWP + QR];
+        float other = NEG;
+        if (QR >= 3) {
+#pragma unroll
+            for (int dy = 0; dy <= 2 * QR; dy++)
+#pragma unroll
+                for (int dx = 0; dx <= 2 * QR; dx++)
+                    if (dy == 0 || dy == 2 * QR || dx == 0 || dx == 2 * QR) other = fmaxf(other, q[dy * MWP + dx]);
+        }
+        if (!(other > iso_frac * c)) cand[atomicAdd(&n_fin, 1)] = (unsigned short)e;
     }
     __syncthreads();
     // 4. one warp per survivor: rest of the isolation window, flag window, cell key
     const int side = 2 * iso + 1, fside = 2 * m + 1;
-    for (int i = wid; i < n_surv; i += nw) {
-        const int e = surv[i];
+    for (int i = wid; i < n_fin; i += nw) {
+        const int e = cand[i];
         const int y = e / SEL_TX, x = e - y * SEL_TX;
         const int X = x0 + x, Y = y0 + y;
-        const float c = mv[(y + QR) * MW + x + QR];
+        const float c = mv[(y + QR) * MWP + x + QR];
         const float thr = iso_frac * c;
         bool bad = false;
         if (iso > QR) {
