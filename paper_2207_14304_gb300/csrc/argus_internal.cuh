@@ -94,5 +94,9 @@ int argus_nterms(int deg);
 int argus_cnn_forward_tc(const float* x, const void* wbf, void* wpack, int n, float* y, float* acts, long lstride,
                          int num_sms, int* status, cudaStream_t st);
 size_t argus_cnn_tc_pack_bytes();
+// the data gradient of 7x7 layer `layer` on the tensor cores (cnn_tc.cu): dh_in =
+// conv^T(dh_out (h_out > 0)); wpack receives the layer's packed transposed kernel
+int argus_cnn_dgrad_tc(const float* dh_out, const float* h_out, const void* wbf, void* wpack, int layer, int n,
+                       float* dh_in, int num_sms, int* status, cudaStream_t st);
 
 static inline int argus_round_up(int a, int m) { return (a + m - 1) / m * m; }

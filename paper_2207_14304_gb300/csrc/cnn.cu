@@ -13,7 +13,8 @@
 // stride of 33 in shared memory (conflict-free across pixels).  Training runs
 // entirely in these kernels: forward, MSE, data and weight gradients, Adam on
 // FP32 master weights with a BF16 working copy.  With ARGUS_PREC_BF16_SPLIT
-// the forward runs instead on the tensor cores (cnn_tc.cu).
+// the forward and the data gradients of the 7x7 layers run instead on the
+// tensor cores (cnn_tc.cu); the weight gradients stay on the CUDA cores.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <stdlib.h>
@@ -859,8 +860,11 @@ extern "C" int argus_cnn_status(argus_cnn* nn, argus_stream stream) {
     return h;
 }
 
+// tc_dgrad: the data gradients of the 7x7 layers on the tensor cores (ARGUS_PREC_BF16_SPLIT:
+// BF16 weights against BF16 hi + lo gradients, FP32-level); otherwise the CUDA-core kernel
 template <typename WT>
-static void backward_impl(argus_cnn* nn, const WT* w, const float* x, const float* dy, int n, cudaStream_t st) {
+static int backward_impl(argus_cnn* nn, const WT* w, const float* x, const float* dy, int n, bool tc_dgrad,
+                         cudaStream_t st) {
     const size_t L = (size_t)nn->max_batch * NPX * C;
     // every gradient is a fixed-order sum of per-CTA partials (no float atomics): the
     // partial buffer holds num_sms slots of one layer, reused layer by layer in stream order
@@ -878,13 +882,19 @@ static void backward_impl(argus_cnn* nn, const WT* w, const float* x, const floa
         const int nbx = (n + per - 1) / per;
         cnn_conv7_wgrad_kernel<<<dim3(nbx, KS), 448, wgrad_smem(), st>>>(hin, dh, hout, nn->part, n, per); argus_count_launch(1);
         cnn_reduce_kernel<<<rg, 256, 0, st>>>(nn->part, nbx, WPART, nn->grad + off_w(l)); argus_count_launch(1);
-        cnn_conv7_dgrad_kernel<WT><<<min(n, nn->num_sms * 2), 256, fwd_smem(), st>>>(dh, hout, w + off_w(l), dn, n); argus_count_launch(1);
+        if (tc_dgrad) {
+            const int rc = argus_cnn_dgrad_tc(dh, hout, nn->wbf, nn->wpack, l, n, dn, nn->num_sms, nn->d_status, st);
+            if (rc) return rc;
+        } else {
+            cnn_conv7_dgrad_kernel<WT><<<min(n, nn->num_sms * 2), 256, fwd_smem(), st>>>(dh, hout, w + off_w(l), dn, n); argus_count_launch(1);
+        }
         float* t = dh;
         dh = dn;
         dn = t;
     }
     cnn_in_bwd_kernel<<<gs, 256, 0, st>>>(x, dh, nn->part, n); argus_count_launch(1);
     cnn_reduce_kernel<<<1, 128, 0, st>>>(nn->part, gs, 3 * C, nn->grad + OFF_W1); argus_count_launch(1);
+    return ARGUS_OK;
 }
 
 extern "C" int argus_cnn_backward(argus_cnn* nn, const float* x, const float* dy, int n, float* grad_out,
@@ -892,8 +902,10 @@ extern "C" int argus_cnn_backward(argus_cnn* nn, const float* x, const float* dy
     if (!nn || !x || !dy || n < 1 || n > nn->max_batch) return ARGUS_ERR_ARG;
     if (cudaSetDevice(nn->device) != cudaSuccess) return ARGUS_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    if (nn->precision != ARGUS_PREC_FP32) backward_impl<__nv_bfloat16>(nn, nn->wbf, x, dy, n, st);
-    else backward_impl<float>(nn, nn->master, x, dy, n, st);
+    const int rc = nn->precision != ARGUS_PREC_FP32
+                       ? backward_impl<__nv_bfloat16>(nn, nn->wbf, x, dy, n, nn->precision == ARGUS_PREC_BF16_SPLIT, st)
+                       : backward_impl<float>(nn, nn->master, x, dy, n, false, st);
+    if (rc) return rc;
     if (grad_out && cudaMemcpyAsync(grad_out, nn->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, st) !=
                         cudaSuccess)
         return ARGUS_ERR_CUDA;

@@ -35,6 +35,10 @@
 // activations for the backward pass, and after the last one the 1x1 output.
 // Two CTAs per SM overlap one another's epilogues and weight waits.  Every
 // wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
+//
+// The data gradient of each 7x7 layer is the same implicit GEMM with the
+// layer's kernel transposed and flipped (cnn_dgrad_tc_kernel): the gradient
+// planes dz (BF16 hi + lo) against W'[ky][kx][o][i] = W[6 - ky][6 - kx][i][o].
 #include <cuda_bf16.h>
 
 #include "argus_internal.cuh"
@@ -307,7 +311,190 @@ __global__ void __launch_bounds__(NTHR, 2) cnn_fwd_tc_kernel(const float* __rest
     if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// Packs the BF16 weights of 7x7 layer l for its data gradient: the transposed, flipped
+// kernel W'[ky][kx][o][i] = W[6 - ky][6 - kx][i][o] in the B-operand layout
+// [tap][o / 8][i][o % 8] (N = the layer's input channels, K = its output channels).
+__global__ void cnn_pack_dgrad_tc_kernel(const __nv_bfloat16* w, __nv_bfloat16* wp, int l) {
+    const long tot = (long)NTAP * C * C;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e & 7), i = (int)((e >> 3) & 31), oc = (int)((e >> 8) & 3), tap = (int)(e >> 10);
+        const int ky = tap / KS, kx = tap - KS * ky;
+        const int ft = (KS - 1 - ky) * KS + (KS - 1 - kx);
+        wp[e] = w[off_w(l) + ((long)ft * C + i) * C + oc * 8 + j];
+    }
+}
+
+// Data gradient of one 7x7 layer on the tensor cores: dz = dh_out (h_out > 0) and
+//   dh_in[y][x][i] = sum_{ky,kx,o} W[ky][kx][i][o] dz[y - ky + 3][x - kx + 3][o]
+//                  = sum_{ky,kx,o} W'[ky][kx][o][i] dz[y + ky - 3][x + kx - 3][o],
+// the forward's implicit GEMM with the packed W' (cnn_pack_dgrad_tc_kernel) and dz in
+// the operand planes (BF16 hi + lo).  dh_out, h_out, dh_in: [n][441][32] FP32.  Roles as
+// in the forward: warp 0 issues the MMAs of the 49 taps per image, warp 1 streams the
+// weights, warps 2-5 write dz into the planes and read the accumulators into dh_in.
+__global__ void __launch_bounds__(NTHR, 2) cnn_dgrad_tc_kernel(const float* __restrict__ dh_out,
+                                                               const float* __restrict__ h_out,
+                                                               const uint8_t* __restrict__ wpack,
+                                                               float* __restrict__ dh_in, int n, int* status) {
+    extern __shared__ __align__(1024) uint8_t cnn_tc_smem[];
+    CnnTcShared& sh = *reinterpret_cast<CnnTcShared*>(cnn_tc_smem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // both operand sets zeroed once: the padding stays zero, interiors are rewritten per image
+    for (int e = tid; e < 2 * SETB / 16; e += NTHR) reinterpret_cast<uint4*>(sh.act[0])[e] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int s = 0; s < NSLOT; s++) {
+            tc::mbar_init(&sh.wfull[s], 1);
+            tc::mbar_init(&sh.wempty[s], 1);
+        }
+        tc::mbar_init(&sh.ready, NEPI);
+        tc::mbar_init(&sh.accfull, 1);
+        tc::mbar_init(&sh.drain, 1);
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&sh.tmem, TMEM_COLS);
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = sh.tmem;
+
+    if (warp == 0) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::instr_desc(1, 128, C);
+            const uint32_t abase = tc::smem_u32(sh.act[0]), bbase = tc::smem_u32(sh.wb[0]);
+            int cnt = 0, rk = 0;
+            bool run = true, any = false;
+            for (int img = blockIdx.x; img < n && run; img += gridDim.x) {
+                if (!wait_or_abort(sh, &sh.ready, rk & 1, status)) { run = false; break; }
+                rk++;
+                tc::fence_after();
+                for (int tap = 0; tap < NTAP; tap++, cnt++) {
+                    const int s = cnt % NSLOT;
+                    if (!wait_or_abort(sh, &sh.wfull[s], (cnt / NSLOT) & 1, status)) { run = false; break; }
+                    tc::fence_after();
+                    const int ky = tap / KS, kx = tap - KS * ky;
+                    const uint32_t bs = bbase + (uint32_t)(s * TAPB);
+#pragma unroll
+                    for (int t = 0; t < MT; t++) {
+                        const uint32_t arow = abase + (uint32_t)((tile_q0(t) + ky * WP + kx) * 16);
+#pragma unroll
+                        for (int kc = 0; kc < 2; kc++) {
+                            const uint64_t bd = tc::smem_desc(bs + (uint32_t)(kc * 2 * 512), 512, 128);
+#pragma unroll
+                            for (int hl = 0; hl < 2; hl++) {
+                                const uint64_t ad = tc::smem_desc(arow + (uint32_t)(hl * SETB + 2 * kc * PLANE), PLANE, 128);
+                                tc::mma_bf16(tmem + (uint32_t)(t * C), ad, bd, idesc, (tap | kc | hl) ? 1u : 0u);
+                            }
+                        }
+                    }
+                    tc::commit(&sh.wempty[s]);
+                    any = true;
+                }
+                if (run) tc::commit(&sh.accfull);
+            }
+            if (any) {
+                tc::commit(&sh.drain);
+                if (!tc::mbar_wait_bounded(&sh.drain, 0, WAIT_LIMIT)) {
+                    sh.abort = 1;
+                    argus_latch(status, ARGUS_ERR_TIMEOUT);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- weight producer: one bulk copy per tap, in the MMA order
+        if (lane == 0) {
+            int cnt = 0;
+            bool run = true;
+            for (int img = blockIdx.x; img < n && run; img += gridDim.x)
+                for (int tap = 0; tap < NTAP; tap++, cnt++) {
+                    const int s = cnt % NSLOT;
+                    if (cnt >= NSLOT && !wait_or_abort(sh, &sh.wempty[s], (cnt / NSLOT - 1) & 1, status)) {
+                        run = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(&sh.wfull[s], TAPB);
+                    tc::bulk_g2s(sh.wb[s], wpack + (long)tap * TAPB, TAPB, &sh.wfull[s]);
+                }
+            for (int j = cnt > NSLOT ? cnt - NSLOT : 0; j < cnt; j++)
+                if (!tc::mbar_wait_bounded(&sh.wfull[j % NSLOT], (j / NSLOT) & 1, WAIT_LIMIT)) {
+                    sh.abort = 1;
+                    argus_latch(status, ARGUS_ERR_TIMEOUT);
+                    break;
+                }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- dz into the planes, accumulators into dh_in
+        const int et = tid - 64;
+        const int lq = warp & 3;
+        const int r = lq * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
+        int ak = 0;
+        for (int img = blockIdx.x; img < n; img += gridDim.x) {
+            const float* go = dh_out + (long)img * NPX * C;
+            const float* ho = h_out + (long)img * NPX * C;
+            for (int p = et; p < NPX; p += NEPI) {
+                float g[C];
+#pragma unroll
+                for (int k = 0; k < C / 4; k++) {
+                    const float4 gv = reinterpret_cast<const float4*>(go + (long)p * C)[k];
+                    const float4 hv = reinterpret_cast<const float4*>(ho + (long)p * C)[k];
+                    g[4 * k] = hv.x > 0.0f ? gv.x : 0.0f;
+                    g[4 * k + 1] = hv.y > 0.0f ? gv.y : 0.0f;
+                    g[4 * k + 2] = hv.z > 0.0f ? gv.z : 0.0f;
+                    g[4 * k + 3] = hv.w > 0.0f ? gv.w : 0.0f;
+                }
+                const int py = p / S, px = p - py * S;
+                store_planes(sh, (py + 3) * WP + px + 3, g);
+            }
+            tc::fence_proxy_async();   // plane writes visible to the tensor cores
+            tc::fence_before();
+            tc::mbar_arrive(&sh.ready);
+            bool ok = true;
+            if (lane == 0) ok = wait_or_abort(sh, &sh.accfull, ak & 1, status);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            ak++;
+            if (!ok) break;
+            tc::fence_after();
+            float* dst = dh_in + (long)img * NPX * C;
+#pragma unroll 1
+            for (int t = 0; t < MT; t++) {
+                uint32_t v[32];
+                tc::tmem_ld32_nowait(tl + (uint32_t)(t * C), v);
+                tc::tmem_wait_ld32(v);
+                const int q = tile_q0(t) + r;
+                const int qy = q / WP, qx = q - qy * WP;
+                if ((t == MT - 1 && q < 128 * (MT - 1)) || qx >= S) continue;   // not owned, or padding
+                float h[C];
+#pragma unroll
+                for (int o = 0; o < C; o++) h[o] = __uint_as_float(v[o]);
+                store_acts(dst + (long)(qy * S + qx) * C, h);
+            }
+            tc::fence_before();   // the accumulators are read before the next image's MMAs
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
 }  // namespace
+
+int argus_cnn_dgrad_tc(const float* dh_out, const float* h_out, const void* wbf, void* wpack, int layer, int n,
+                       float* dh_in, int num_sms, int* status, cudaStream_t st) {
+    cnn_pack_dgrad_tc_kernel<<<num_sms, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(wbf),
+                                                       static_cast<__nv_bfloat16*>(wpack), layer); argus_count_launch(1);
+    const int smem = (int)sizeof(CnnTcShared);
+    cudaError_t e = cudaFuncSetAttribute(cnn_dgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cnn_dgrad_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return argus_cuda_fail(e);
+    const int grid = n < 2 * num_sms ? n : 2 * num_sms;
+    cnn_dgrad_tc_kernel<<<grid, NTHR, smem, st>>>(dh_out, h_out, static_cast<const uint8_t*>(wpack), dh_in, n, status); argus_count_launch(1);
+    return argus_launch_status();
+}
 
 int argus_cnn_forward_tc(const float* x, const void* wbf, void* wpack, int n, float* y, float* acts, long lstride,
                          int num_sms, int* status, cudaStream_t st) {

@@ -109,9 +109,10 @@ def test_cnn_forward_backward_parity(ora, bignet, prec, batch, sample, weights):
     bias gradient by a few per cent), so the BF16 gradient must instead equal, bit for bit,
     the FP32 mode's at the same rounded weights, which meets the element-wise bar here.
     bf16_split (the forward on the tensor cores, activations as BF16 hi + lo): the forward
-    element by element against the oracle at the BF16-rounded weights; its gradient (the
-    BF16 backward kernels on the tensor-core forward's activations) element by element with
-    tie-free weights."""
+    element by element against the oracle at the BF16-rounded weights; its gradient (the 7x7
+    layers' data gradients also on the tensor cores, with BF16 hi + lo gradient planes; the
+    weight gradients on the CUDA cores, on the tensor-core forward's activations) element by
+    element with tie-free weights."""
     net = bignet
     w32 = _tie_free_weights(11) if weights == "tie_free" else _test_weights(11)
     net.tensors()[0].copy_(torch.from_numpy(w32).cuda())          # the test's weights into the network
