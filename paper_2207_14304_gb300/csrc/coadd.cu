@@ -262,18 +262,22 @@ __global__ void __launch_bounds__(CT, NMAX <= 32 ? 2 : 1) coadd_kernel(CoaddArgs
 #pragma unroll
         for (int i = 0; i < NMAX; i++) col[i * CT] = s[i];
         int lo = 0, hi = n;
+        float last_s1 = 0.0f;   // sum of v - median over [lo, hi) when the last pass kept every sample
+        bool have_s1 = false;
         for (int it = 0; it < a.max_iter && hi > lo; it++) {
             const int cnt = hi - lo;
             const float c = median_col(col, lo, hi);
-            float sum = 0.0f;
-            for (int i = lo; i < hi; i++) sum += col[i * CT];
-            const float m = sum / (float)cnt;
-            float s2 = 0.0f;
+            // mean and spread in one pass over the range, about the median (the sums of
+            // v - c and (v - c)^2; the median lies inside the samples, so the difference
+            // of the second sum and the squared first one does not cancel)
+            float s1 = 0.0f, s2 = 0.0f;
             for (int i = lo; i < hi; i++) {
-                const float d = col[i * CT] - m;
-                s2 += d * d;
+                const float d = col[i * CT] - c;
+                s1 += d;
+                s2 = fmaf(d, d, s2);
             }
-            const float ks = a.kappa * sqrtf(s2 / (float)cnt);
+            const float d1 = s1 / (float)cnt;
+            const float ks = a.kappa * sqrtf(fmaxf(s2 / (float)cnt - d1 * d1, 0.0f));
             int nlo = 0, nhi = 0;
             while (lo + nlo < hi) {
                 const float v = col[(lo + nlo) * CT];
@@ -285,7 +289,12 @@ __global__ void __launch_bounds__(CT, NMAX <= 32 ? 2 : 1) coadd_kernel(CoaddArgs
                 if (!(v >= c && fabsf(v - c) > ks)) break;
                 nhi++;
             }
-            if (nlo + nhi == 0 || nlo + nhi == cnt) break;
+            if (nlo + nhi == 0) {
+                last_s1 = s1;
+                have_s1 = true;
+                break;
+            }
+            if (nlo + nhi == cnt) break;
             lo += nlo;
             hi -= nhi;
         }
@@ -299,20 +308,27 @@ __global__ void __launch_bounds__(CT, NMAX <= 32 ? 2 : 1) coadd_kernel(CoaddArgs
         const int cnt = hi - lo;
         const float c = median_col(col, lo, hi);
         const float vlo = col[lo * CT], vhi = col[(hi - 1) * CT];
-        float sd = 0.0f;
-        for (int i = lo; i < hi; i++) sd += col[i * CT] - c;
+        float sd = last_s1;   // the converged pass's sum over the same range about the same median
+        if (!have_s1)
+            for (int i = lo; i < hi; i++) sd += col[i * CT] - c;
         if (cnt < n) {   // the rejected samples' variances out (compensated: a rejected cosmic
-                         // ray's variance can exceed the survivors' sum many times)
+                         // ray's variance can exceed the survivors' sum many times); the
+                         // rejected frames as a bit mask first, then one sample per set bit,
+                         // so a warp runs as many samples as its lane with the most rejections
+            unsigned long long rej = 0ull;
 #pragma unroll
             for (int fi = 0; fi < NMAX; fi++)
-                if (fi < a.nf && fabsf(u[fi]) <= FMAXF && (u[fi] < vlo || u[fi] > vhi)) {
-                    const float2 fxy = s_fxy[fi];
-                    float vr;
-                    sample(wvr + fi * CWN, o, fxy.x, fxy.y, s_q[fi], vr);
-                    float e;
-                    two_sum(svh, -vr, svh, e);
-                    svl += e;
-                }
+                if (fi < a.nf && fabsf(u[fi]) <= FMAXF && (u[fi] < vlo || u[fi] > vhi)) rej |= 1ull << fi;
+            while (rej) {
+                const int fi = __ffsll((long long)rej) - 1;
+                rej &= rej - 1ull;
+                const float2 fxy = s_fxy[fi];
+                float vr;
+                sample(wvr + fi * CWN, o, fxy.x, fxy.y, s_q[fi], vr);
+                float e;
+                two_sum(svh, -vr, svh, e);
+                svl += e;
+            }
         }
         const float svar = svh + svl;
         a.coadd[p] = c + sd / (float)cnt;
