@@ -479,7 +479,7 @@ extern "C" int argus_segments_plan(argus_ctx* ctx, const argus_segment* table, i
     std::vector<int4> fit_tc_items;
     const int NPC0 = bd.nb + 2;
     const bool fit_tc = argus_seg_fit_tc_smem(bd.ks, NPC0) != 0 && argus_seg_fit_tc_smem(bd.ks, NPC0) <= 227 * 1024 &&
-                        bd.nb <= 56;
+                        bd.nb + 2 <= 52;   // the Gram's 2 x 4 blocks fit one 192-thread set
     const int band = c.fit_band & ~1;   // the tensor-core fit's rows per item (pairs of rows)
     std::vector<int> fit_tc_start;
     for (int i : order) {

@@ -30,20 +30,23 @@
 // exactly.
 //
 // The normal matrix stays on the CUDA cores in the fold the precision needs:
-// each thread owns a 4 x 4 block of the upper triangle of the (nb + 2)^2
-// Gram, sums FP32 products over 8 pixels and folds every such partial into a
-// double-float accumulator (error-free two-sum; sums over 16 and 32 pixels
-// measured 1.8x and 2.1x the kernel error); when the CTA's next item
-// belongs to another segment the blocks go to the segment's FP64 normal matrix
-// by atomics.
+// FP32 sums over 8 pixels, each folded into a double-float accumulator
+// (error-free two-sum; sums over 16 and 32 pixels measured 1.8x and 2.1x the
+// kernel error).  The design rows of a pair are stored pixel-pair interleaved
+// and the arithmetic is on packed FP32 pairs (fma/add/sub.rn.f32x2): the two
+// lanes of a register hold an even and an odd pixel, so each lane still sums
+// 8 pixels per fold while one instruction does two of the operations.  Each
+// thread owns a 2 x 4 block of the upper triangle of the (nb + 2)^2 Gram; when
+// the CTA's next item belongs to another segment the blocks go to the
+// segment's FP64 normal matrix by atomics.
 //
 // Roles (16 warps): warps 0-3 read the accumulators (thread = pixel, the TMEM
 // lane), weight them and write the design rows of the pair (256 pixels) to
 // shared memory; warps 4-6 stage the source rows (16-byte cp.async, zero past
 // the segment) and write the A operands; warp 7 issues the MMAs; warps 8-15
-// and, once the rows are written, warps 0-3 sum the Gram, three 128-thread sets
-// of 4 x 4 blocks over a third of the pair's pixels each.  Two TMEM
-// accumulators let the MMAs of one pair run while the previous one is read.
+// and, once the rows are written, warps 0-3 sum the Gram: two sets of 192
+// threads (the 182 blocks of a 51-column Gram), one per row of the pair.  Two
+// TMEM accumulators let the MMAs of one pair run while the previous one is read.
 // Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_fp16.h>
 
@@ -103,6 +106,25 @@ __device__ __forceinline__ uint32_t f16x2_rn(float v0, float v1) {
 __device__ __forceinline__ float f16_lo(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h & 0xffffu))); }
 __device__ __forceinline__ float f16_hi(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h >> 16))); }
 
+// Packed FP32 pairs (two lanes of one 64-bit register), round to nearest.
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float f2_x(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_y(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
 // The power of two 2^k with m 2^k in [2^13, 2^14] (1 for m = 0 or not finite).
 __host__ __device__ inline float ft_pow2_scale(float m) {
     if (!(m > 0.0f) || !(m < 3.0e38f)) return 1.0f;
@@ -156,46 +178,53 @@ __device__ __forceinline__ FtItem ft_item(const SegFitTcArgs& a, int item) {
     return t;
 }
 
-// One thread's share of the Gram of a pair's 256 design rows (Z [256][zs]): the 4 x 4
-// block bidx of the upper triangle of the NPC x NPC matrix, over the 8-pixel fold groups
-// g = set, set + 3, ... of the rows (three 128-thread sets share every pair); FP32 sums
-// over a group, each folded into (hi, lo) by an error-free two-sum.
+// One thread's share of the Gram of a pair's 256 design rows, stored pixel-pair
+// interleaved (Z [128 pixel pairs][zs][2]): the 2 x 4 block bidx (rows 2 bi, 2 bi + 1,
+// columns 4 bj .. 4 bj + 3) of the upper triangle of the NPC x NPC matrix, over the
+// pixel pairs of one half of the pair (two sets of 192 threads).  Arithmetic on packed
+// FP32 pairs: the two lanes of every accumulator sum the even and the odd pixel of the
+// pixel pairs, 8 pixels each per fold group (8 pixel pairs), each group folded into
+// (hi, lo) by an error-free two-sum.
 struct GramShare {
-    int bi, bj, set;
+    int bi, bj, half;
     bool active;
-    float hi[16], lo[16];
-    __device__ __forceinline__ void init(int bidx, int set_, int NPC) {
-        const int nbk = (NPC + 3) / 4;
-        active = bidx < nbk * (nbk + 1) / 2;
-        set = set_;
-        bi = 0;
+    uint64_t hi[8], lo[8];
+    __device__ __forceinline__ void init(int bidx, int half_, int NPC) {
+        const int nbi = (NPC + 1) / 2, nbj = (NPC + 3) / 4;
+        half = half_;
+        active = false;
+        bi = bj = 0;
         int rem = bidx;
-        while (bi < nbk && rem >= nbk - bi) { rem -= nbk - bi; bi++; }
-        bj = bi + rem;
+        for (int c = 0; c < nbj; c++) {   // column block c holds row blocks 0 .. min(nbi - 1, (4c + 3) / 2)
+            const int nr = min(nbi - 1, (4 * c + 3) / 2) + 1;
+            if (rem < nr) { bi = rem; bj = c; active = true; break; }
+            rem -= nr;
+        }
 #pragma unroll
-        for (int q = 0; q < 16; q++) hi[q] = lo[q] = 0.0f;
+        for (int q = 0; q < 8; q++) hi[q] = lo[q] = 0ull;
     }
     __device__ __forceinline__ void add(const float* Z, int zs) {
         if (!active) return;
-        for (int g = set; g < 32; g += 3) {
-            float acc[16];
+        for (int g = 0; g < 8; g++) {
+            uint64_t acc[8];
 #pragma unroll
-            for (int q = 0; q < 16; q++) acc[q] = 0.0f;
+            for (int q = 0; q < 8; q++) acc[q] = 0ull;
 #pragma unroll
-            for (int px = 8 * g; px < 8 * g + 8; px++) {
-                const float* zp = Z + px * zs;
-                const float4 zi = *reinterpret_cast<const float4*>(zp + 4 * bi);
-                const float4 zj = *reinterpret_cast<const float4*>(zp + 4 * bj);
-                const float ai[4] = {zi.x, zi.y, zi.z, zi.w}, aj[4] = {zj.x, zj.y, zj.z, zj.w};
+            for (int k = 0; k < 8; k++) {
+                const float* zp = Z + (size_t)(half * 64 + g * 8 + k) * zs * 2;
+                const ulonglong2 i01 = *reinterpret_cast<const ulonglong2*>(zp + 4 * bi);
+                const ulonglong2 j01 = *reinterpret_cast<const ulonglong2*>(zp + 8 * bj);
+                const ulonglong2 j23 = *reinterpret_cast<const ulonglong2*>(zp + 8 * bj + 4);
+                const uint64_t ai[2] = {i01.x, i01.y}, aj[4] = {j01.x, j01.y, j23.x, j23.y};
 #pragma unroll
-                for (int u = 0; u < 4; u++)
+                for (int u = 0; u < 2; u++)
 #pragma unroll
-                    for (int v = 0; v < 4; v++) acc[u * 4 + v] = fmaf(ai[u], aj[v], acc[u * 4 + v]);
+                    for (int v = 0; v < 4; v++) acc[u * 4 + v] = f2_fma(ai[u], aj[v], acc[u * 4 + v]);
             }
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-                const float sum = hi[q] + acc[q], bp = sum - hi[q];
-                lo[q] += (hi[q] - (sum - bp)) + (acc[q] - bp);
+            for (int q = 0; q < 8; q++) {
+                const uint64_t sum = f2_add(hi[q], acc[q]), bp = f2_sub(sum, hi[q]);
+                lo[q] = f2_add(lo[q], f2_add(f2_sub(hi[q], f2_sub(sum, bp)), f2_sub(acc[q], bp)));
                 hi[q] = sum;
             }
         }
@@ -204,14 +233,16 @@ struct GramShare {
     __device__ __forceinline__ void flush(double* G, int NPC) {
         if (!active) return;
 #pragma unroll
-        for (int u = 0; u < 4; u++)
+        for (int u = 0; u < 2; u++)
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const int i = bi * 4 + u, j = bj * 4 + v;
-                if (i < NPC && j < NPC && i <= j) atomicAdd(G + i * NPC + j, (double)hi[u * 4 + v] + (double)lo[u * 4 + v]);
+                const int i = bi * 2 + u, j = bj * 4 + v, q = u * 4 + v;
+                if (i < NPC && j < NPC && i <= j)
+                    atomicAdd(G + i * NPC + j, ((double)f2_x(hi[q]) + (double)f2_x(lo[q])) +
+                                                   ((double)f2_y(hi[q]) + (double)f2_y(lo[q])));
             }
 #pragma unroll
-        for (int q = 0; q < 16; q++) hi[q] = lo[q] = 0.0f;
+        for (int q = 0; q < 8; q++) hi[q] = lo[q] = 0ull;
     }
 };
 
@@ -227,7 +258,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
     uint8_t* aring = sm + L.a;                      // [FT_NA][2 parts][FT_A_BYTES]
     float* win = reinterpret_cast<float*>(sm + L.win);          // [FT_NPROD][FT_NWIN][FT_WIN]
     uint32_t* rowb = reinterpret_cast<uint32_t*>(sm + L.rowb);  // [FT_NPROD][2][(FT_NCM + 1) * 4]
-    float* Z = reinterpret_cast<float*>(sm + L.z);               // [256][zs]
+    float* Z = reinterpret_cast<float*>(sm + L.z);               // [128 pixel pairs][zs][2]
     FtBar& S = *reinterpret_cast<FtBar*>(sm + L.bar);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int* status = a.status;
@@ -427,8 +458,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
         // ---------------- accumulator readers: thread = pixel column x0 + tid of the strip
         const int m = tid;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        GramShare gs;
-        gs.init(tid, 2, NPC);
+        GramShare gs;   // Gram threads 0 .. 127 of 384: set 0 (with Gram warps 8 and 9)
+        gs.init(tid, 0, NPC);
         int tp = 0;
         bool run = true;
         for (int item = ilo; item < ihi && run; item++) {
@@ -473,27 +504,36 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
                 if (ok && lane == 0 && tp >= 1) ok = ft_wait(S, &S.zempty, (uint32_t)(tp - 1) & 1u, status);
                 if (!__shfl_sync(0xffffffffu, ok, 0)) { run = false; break; }
                 tc::fence_after();
+                // design rows, two pixels interleaved: value f of pixel px at
+                // Z[((px / 2) zs + f) 2 + px % 2]; lanes m, m + 1 (pixels 2k, 2k + 1) swap
+                // half of their values so that each writes whole 16-byte groups
+                const bool odd = m & 1;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    float* zr = Z + (h * 128 + m) * zs;
+                    float* zp = Z + (size_t)((h * 128 + m) >> 1) * zs * 2;
                     for (int c = 0; c < nb; c += 16) {
                         float v[16];
                         tc::tmem_ld16(tl + (uint32_t)(acc * 128 + h * 64 + c), v);
 #pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            if (c + j + 4 <= nb) {
-                                *reinterpret_cast<float4*>(zr + c + j) =
-                                    make_float4(v[j] * wx[h], v[j + 1] * wx[h], v[j + 2] * wx[h], v[j + 3] * wx[h]);
-                            } else {
-#pragma unroll
-                                for (int u = 0; u < 4; u++)
-                                    if (c + j + u < nb) zr[c + j + u] = v[j + u] * wx[h];
-                            }
+                        for (int g = 0; g < 4; g++) {
+                            const float x0 = v[4 * g] * wx[h], x1 = v[4 * g + 1] * wx[h];
+                            const float x2 = v[4 * g + 2] * wx[h], x3 = v[4 * g + 3] * wx[h];
+                            const float r0 = __shfl_xor_sync(0xffffffffu, odd ? x0 : x2, 1);
+                            const float r1 = __shfl_xor_sync(0xffffffffu, odd ? x1 : x3, 1);
+                            const int f = c + 4 * g + (odd ? 2 : 0);
+                            if (c + 4 * g + 3 < zs)
+                                *reinterpret_cast<float4*>(zp + 2 * f) =
+                                    odd ? make_float4(r0, x2, r1, x3) : make_float4(x0, r0, x1, r1);
                         }
                     }
-                    zr[nb] = sqw[h];
-                    zr[nb + 1] = sqw[h] * Iv[h];
-                    for (int c = nb + 2; c < zs; c++) zr[c] = 0.0f;
+                }
+                __syncwarp();   // the swapped groups are written before the last columns
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    float* zp = Z + (size_t)((h * 128 + m) >> 1) * zs * 2 + (odd ? 1 : 0);
+                    zp[2 * nb] = sqw[h];
+                    zp[2 * (nb + 1)] = sqw[h] * Iv[h];
+                    for (int c = nb + 2; c < zs; c++) zp[2 * c] = 0.0f;
                 }
                 tc::fence_before();
                 __syncwarp();
@@ -515,10 +555,11 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
             if (item + 1 == ihi || a.items[item + 1].x != t.s) gs.flush(a.gram + (long)t.s * NPC * NPC, NPC);
         }
     } else if (warp >= FT_GRAM_WARP) {
-        // ---------------- Gram warps: sets 0 and 1 of the pair's Gram (the readers are set 2)
-        const int gt = tid - FT_GRAM_WARP * 32;
+        // ---------------- Gram warps: Gram threads 128 .. 383 (the readers are 0 .. 127); set
+        // s = gt / 192 takes the pixel pairs of half s of the pair's rows
+        const int gt = 128 + tid - FT_GRAM_WARP * 32;
         GramShare gs;
-        gs.init(gt & 127, gt >> 7, NPC);
+        gs.init(gt % 192, gt / 192, NPC);
         int tp = 0;
         bool run = true;
         for (int item = ilo; item < ihi && run; item++) {
@@ -580,6 +621,7 @@ size_t argus_seg_fit_tc_smem(int ks, int NPC) {
 
 int argus_seg_fit_tc(const SegFitTcArgs& a, int ks, cudaStream_t st) {
     if (a.band < 2 || (a.band & 1) || a.nb > 64 || a.n_ctas < 1) return ARGUS_ERR_ARG;
+    if (a.NPC > 52) return ARGUS_ERR_UNSUPPORTED;   // more 2 x 4 Gram blocks than a 192-thread set
     switch (ks) {
         case 7: return launch_fit_tc<7>(a, st);
         case 9: return launch_fit_tc<9>(a, st);
