@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
             const uint32_t bz_hi = tc::smem_u32(bz), bz_lo = bz_hi + NSLOT * FT_BZ_SLOT;
             const uint32_t a0 = tc::smem_u32(aring);
             int g0 = 0, tp = 0, issued = -1;
+            int seen = -1;   // source rows up to this one are known to be written (a row stays
+                             // written until its last pair's MMAs release it)
             bool run = true;
             for (int item = ilo; item < ihi && run; item++) {
                 const FtItem t = ft_item<KS>(a, item);
@@ -428,8 +430,11 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
                     const uint32_t d = tmem + (uint32_t)(acc * 128);
                     for (int i = 0; i < 2 * R + 2; i++) {
                         const int g = g0 + 2 * p + i, sl = g % FT_NA;
-                        if (!ft_wait(S, &S.afull[sl], (uint32_t)(g / FT_NA) & 1u, status)) { run = false; break; }
-                        tc::fence_after();
+                        if (g > seen) {
+                            if (!ft_wait(S, &S.afull[sl], (uint32_t)(g / FT_NA) & 1u, status)) { run = false; break; }
+                            seen = g;
+                            tc::fence_after();
+                        }
                         const uint32_t boff = (uint32_t)(2 * R - i + 1) * (64 / 8) * FT_SBO_B;   // slot iv0 + 1
                         const uint32_t ahi = a0 + (uint32_t)sl * 2 * FT_A_BYTES, alo = ahi + FT_A_BYTES;
                         const uint64_t dah = tc::smem_desc(ahi, FT_LBO, FT_SBO_A), dal = tc::smem_desc(alo, FT_LBO, FT_SBO_A);
@@ -511,19 +516,33 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     float* zp = Z + (size_t)((h * 128 + m) >> 1) * zs * 2;
-                    for (int c = 0; c < nb; c += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tl + (uint32_t)(acc * 128 + h * 64 + c), v);
+                    // two 16-column chunks per TMEM wait
+                    for (int c2 = 0; c2 < nb; c2 += 32) {
+                        uint32_t rv[2][16];
+                        tc::tmem_ld16_nowait(tl + (uint32_t)(acc * 128 + h * 64 + c2), rv[0]);
+                        if (c2 + 16 < nb) {
+                            tc::tmem_ld16_nowait(tl + (uint32_t)(acc * 128 + h * 64 + c2 + 16), rv[1]);
+                        } else {
 #pragma unroll
-                        for (int g = 0; g < 4; g++) {
-                            const float x0 = v[4 * g] * wx[h], x1 = v[4 * g + 1] * wx[h];
-                            const float x2 = v[4 * g + 2] * wx[h], x3 = v[4 * g + 3] * wx[h];
-                            const float r0 = __shfl_xor_sync(0xffffffffu, odd ? x0 : x2, 1);
-                            const float r1 = __shfl_xor_sync(0xffffffffu, odd ? x1 : x3, 1);
-                            const int f = c + 4 * g + (odd ? 2 : 0);
-                            if (c + 4 * g + 3 < zs)
-                                *reinterpret_cast<float4*>(zp + 2 * f) =
-                                    odd ? make_float4(r0, x2, r1, x3) : make_float4(x0, r0, x1, r1);
+                            for (int j = 0; j < 16; j++) rv[1][j] = 0u;
+                        }
+                        tc::tmem_wait_ld(rv[0], rv[1]);
+#pragma unroll
+                        for (int hc = 0; hc < 2; hc++) {
+                            const int c = c2 + 16 * hc;
+#pragma unroll
+                            for (int g = 0; g < 4; g++) {
+                                const float x0 = __uint_as_float(rv[hc][4 * g]) * wx[h];
+                                const float x1 = __uint_as_float(rv[hc][4 * g + 1]) * wx[h];
+                                const float x2 = __uint_as_float(rv[hc][4 * g + 2]) * wx[h];
+                                const float x3 = __uint_as_float(rv[hc][4 * g + 3]) * wx[h];
+                                const float r0 = __shfl_xor_sync(0xffffffffu, odd ? x0 : x2, 1);
+                                const float r1 = __shfl_xor_sync(0xffffffffu, odd ? x1 : x3, 1);
+                                const int f = c + 4 * g + (odd ? 2 : 0);
+                                if (c < nb && c + 4 * g + 3 < zs)
+                                    *reinterpret_cast<float4*>(zp + 2 * f) =
+                                        odd ? make_float4(r0, x2, r1, x3) : make_float4(x0, r0, x1, r1);
+                            }
                         }
                     }
                 }
