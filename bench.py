@@ -1022,7 +1022,7 @@ def main(argv=None):
     # on the full frame; --precision fp32 / bf16 / bf16_split select the others
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "bf16", "bf16_split"])
     ap.add_argument("--band-rows", type=int, default=48)
-    ap.add_argument("--frames-in-flight", type=int, default=3,
+    ap.add_argument("--frames-in-flight", type=int, default=4,
                     help="frames processed concurrently, each on its own pipeline and stream")
     ap.add_argument("--no-fused", dest="fused", action="store_false",
                     help="capture the separate calls (argus_calibrate .. argus_detect) instead of argus_dia_frame")

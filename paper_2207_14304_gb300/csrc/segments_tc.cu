@@ -125,12 +125,14 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
 __device__ __forceinline__ float f2_x(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float f2_y(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
-// The power of two 2^k with m 2^k in [2^13, 2^14] (1 for m = 0 or not finite).
+// The power of two 2^k with m 2^k in [2^13, 2^14) (1 for m = 0 or not finite), with k at
+// most 64: a largest |value| below 2^-50 is scaled by 2^64 only, so that the scales and
+// their products stay finite (such values then sit below 2^13 and lose FP16 precision).
 __host__ __device__ inline float ft_pow2_scale(float m) {
-    if (!(m > 0.0f) || !(m < 3.0e38f)) return 1.0f;
+    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
     int e;
     frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
-    return ldexpf(1.0f, 14 - e);
+    return ldexpf(1.0f, 14 - e < 64 ? 14 - e : 64);
 }
 
 __device__ __forceinline__ bool ft_wait(FtBar& S, uint64_t* bar, uint32_t parity, int* status) {

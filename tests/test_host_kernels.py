@@ -29,7 +29,7 @@ def drivers(tmp_path_factory):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     d = tmp_path_factory.mktemp("host_drivers")
-    for name in ("host_fft", "host_zogy", "host_coadd", "host_background", "host_healpix"):
+    for name in ("host_fft", "host_zogy", "host_coadd", "host_background", "host_healpix", "host_segscale"):
         subprocess.check_call([nvcc, "-O2", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
                                "-I", CSRC, "-I", INCLUDE, "-I", DRV, "-o", str(d / name),
                                os.path.join(DRV, name + ".cu")])
@@ -248,3 +248,29 @@ def test_healpix_resampling_matches_the_oracle(drivers, nside_seg, k, delta0, us
         np.testing.assert_array_equal(cov[i], oc)
         assert np.abs(out[i] - o).max() <= tol
     assert cov[:-1].any() and cov[-1].any() and not cov[-1].all()     # the edge segment is partly covered
+
+
+def test_segment_fit_fp16_range_scale(drivers):
+    """The batched segment fit scales each segment's reference (and the basis) by the power of
+    two that puts its largest |value| in [2^13, 2^14), so that the FP16 hi part can never
+    overflow (FP16's largest finite value is 65504) and the lo part keeps 11 more bits; zero,
+    infinite or NaN maxima leave the data unscaled; maxima below 2^-50 are scaled by 2^64 at
+    most, so that scales and their products stay finite."""
+    rng = np.random.default_rng(3)
+    m = np.concatenate([10.0 ** rng.uniform(-14, 37, 2000), 2.0 ** np.arange(-40, 120, 1.0),
+                        [1.0, 8192.0, 16383.99, 16384.0, 65504.0, 3.0e38, 1e-20, 1e-38, 1e-44,
+                         0.0, -0.0, np.inf, np.nan]]).astype(np.float32)
+    m.tofile(drivers / "scale_in.bin")
+    subprocess.check_call([str(drivers / "host_segscale"), str(drivers / "scale_in.bin"),
+                           str(drivers / "scale_out.bin")])
+    s = np.fromfile(drivers / "scale_out.bin", dtype=np.float32)
+    assert s.shape == m.shape and np.all(np.isfinite(s)) and np.all(s > 0)
+    frac, _ = np.frexp(s.astype(np.float64))
+    assert np.all(frac == 0.5)                               # powers of two: scaling is exact
+    ok = np.isfinite(m) & (m > 0)
+    big = ok & (m >= 2.0 ** -50)
+    ms = m[big].astype(np.float64) * s[big]
+    assert np.all((ms >= 2.0 ** 13) & (ms < 2.0 ** 14)), (m[big][~((ms >= 2 ** 13) & (ms < 2 ** 14))])
+    assert np.all(s[ok & (m < 2.0 ** -50)] == 2.0 ** 64)
+    assert np.all(s[~ok] == 1.0)
+    assert np.all(m[big].astype(np.float64) * s[big] * (1 + 2.0 ** -11) < 65504.0)
