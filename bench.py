@@ -349,6 +349,24 @@ def run_gpu(args):
     step_s = tmax / args.steps
     hbm_frac = BYTES_PER_PX * W * H / step_s / 1e9 / hbm
     kernels = kernel_rooflines(tc_ms, var_ms, ktiming, peaks)
+    # the step against the compute roof: algorithmic FLOPs of its dense contractions (the
+    # difference image 2 x 6 x 441, the variance 2 x 441 per pixel; the fit's stamp
+    # convolutions and normal equations per frame) over the step time, against the
+    # sustained cuBLAS BF16 rate (the step is a long run)
+    nst = GRID[0] * GRID[1]
+    nunk = 1 + (49 - 1) * 6 + 6
+    fit_flop = 2.0 * nst * STAMP * STAMP * 49 * KSIZE * KSIZE + 2.0 * nst * STAMP * STAMP * (nunk + 1) * (nunk + 2) / 2
+    step_flop_px = 2 * 6 * KSIZE * KSIZE + 2 * KSIZE * KSIZE + fit_flop / (W * H)
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    step_tflops = step_flop_px * W * H / step_s / 1e12
+    compute_roofline = {"flop_per_px": round(step_flop_px, 1), "achieved": round(step_tflops, 2),
+                        "peak": bf16_peak, "unit": "TFLOP/s", "frac": round(step_tflops / bf16_peak, 4),
+                        "algorithmic": "difference image 2x6x441 + variance 2x441 FLOP/px, with the fit's stamp "
+                                       "convolutions (400 x 441 px x 49 x 441 taps) and normal equations "
+                                       "(400 x 441 rows, 296 columns, upper triangle) per frame",
+                        "peak_source": ("measured, MEASURED_PEAKS.json bf16_tflops_sustained"
+                                        if "bf16_tflops_sustained" in peaks
+                                        else "fallback, 1.7 PFLOP/s sustained from an earlier GB300 measurement")}
 
     var = {}
     if args.variants and ws == 1:
@@ -392,6 +410,7 @@ def run_gpu(args):
         "kernels": kernels,
         "hbm_roofline_frac": round(hbm_frac, 4),
         "hbm_bytes_per_px": BYTES_PER_PX,
+        "compute_roofline": compute_roofline,
         "stage_ms": stage, "subtract_ms": round(tc_ms + var_ms, 4),
         "subtract_detect_mpix_s": round(W * H / 1e6 / ((stage["subtract"] + stage["detect"]) / 1e3), 1),
         "e2e": {"value": round(e2e_value, 2), "unit": "Mpix/s", "h2d_bytes_per_step": int(raw_host.numel() * 2),
