@@ -129,13 +129,18 @@ TRAIN_CHUNK = 32768   # pairs per batched-segment run (one run's per-segment scr
 
 
 def training_set(n, seed=5, device=0, sky=300.0, flux=(1e4, 1e6), sig_ref=1.0, sig_range=(1.0, 3.0),
-                 jump_p=0.1, ctx=None):
+                 jump_p=0.1, ctx=None, crowd=None):
     """Seeded stamp pairs and plain-method targets, generated in chunks of at most
-    TRAIN_CHUNK pairs (chunk c uses seed + 1000 c); see `_training_chunk`."""
+    TRAIN_CHUNK pairs (chunk c uses seed + 1000 c); see `_training_chunk`.
+
+    crowd: None (one star per window) or (mean count, flux_min, flux_max, index):
+    each window also holds Poisson(mean count) field stars at uniform positions
+    (over the window and a 5-px border) with dN/dF ~ F**index fluxes, rendered in
+    both images."""
     xs, ts, sigs = [], [], []
     for c, s0 in enumerate(range(0, n, TRAIN_CHUNK)):
         x, t, sg = _training_chunk(min(TRAIN_CHUNK, n - s0), seed + 1000 * c, device, sky, flux, sig_ref,
-                                   sig_range, jump_p, ctx)
+                                   sig_range, jump_p, ctx, crowd)
         xs.append(x)
         ts.append(t)
         sigs.append(sg)
@@ -144,10 +149,53 @@ def training_set(n, seed=5, device=0, sky=300.0, flux=(1e4, 1e6), sig_ref=1.0, s
     return torch.cat(xs), torch.cat(ts), np.concatenate(sigs)
 
 
-def _training_chunk(n, seed, device, sky, flux, sig_ref, sig_range, jump_p, ctx):
+def field_stars(n, seed, mean, flux_min, flux_max, index, border=5.0, device="cpu"):
+    """Field stars for n windows of WIN x WIN pixels: Poisson(mean) per window,
+    positions uniform over the window plus `border` pixels, power-law fluxes.
+    Returns (window index [m] int64, x [m], y [m], flux [m]) as float64 tensors."""
+    g = torch.Generator().manual_seed(seed)
+    cnt = torch.poisson(torch.full((n,), float(mean), dtype=torch.float64), generator=g).to(torch.int64)
+    m = int(cnt.sum())
+    widx = torch.repeat_interleave(torch.arange(n, dtype=torch.int64), cnt)
+    pos = torch.rand(m, 2, generator=g, dtype=torch.float64) * (WIN + 2 * border) - border
+    f = synth.power_law_fluxes(m, seed + 1, flux_min, flux_max, index)
+    dev = torch.device(device)
+    return widx.to(dev), pos[:, 0].to(dev), pos[:, 1].to(dev), f.to(dev)
+
+
+def render_field(n, stars, sigma, device="cpu"):
+    """Expected electrons of field stars in n windows (FP32 [n, WIN, WIN]):
+    pixel-integrated Gaussians of width sigma (a float or a per-window array).
+    Stars are added in passes of at most one star per window (the k-th star of
+    every window in pass k), so the sums do not depend on scheduling."""
+    widx, x, y, f = stars
+    dev = torch.device(device)
+    img = torch.zeros((n, WIN, WIN), dtype=torch.float32, device=dev)
+    if widx.numel() == 0:
+        return img
+    sig = torch.as_tensor(sigma, dtype=torch.float64, device=dev)
+    if sig.dim() == 0:
+        sig = sig.expand(n)
+    order = torch.argsort(widx, stable=True)
+    widx, x, y, f = widx[order], x[order], y[order], f[order]
+    rank = torch.arange(widx.numel(), device=widx.device) - torch.searchsorted(widx, widx)
+    ax = torch.arange(WIN, dtype=torch.float64, device=dev)
+    phi = lambda z: 0.5 * (1 + torch.erf(z / math.sqrt(2)))
+    for k in range(int(rank.max()) + 1):
+        sel = rank == k
+        w, cx, cy, fl = widx[sel], x[sel][:, None], y[sel][:, None], f[sel]
+        sw = sig[w][:, None]
+        fx = phi((ax + 0.5 - cx) / sw) - phi((ax - 0.5 - cx) / sw)
+        fy = phi((ax + 0.5 - cy) / sw) - phi((ax - 0.5 - cy) / sw)
+        img[w] += (fl[:, None, None] * fy[:, :, None] * fx[:, None, :]).to(torch.float32)
+    return img
+
+
+def _training_chunk(n, seed, device, sky, flux, sig_ref, sig_range, jump_p, ctx, crowd=None):
     """Seeded stamp pairs and plain-method targets.
 
-    Each pair is a 41x41 window with one star near its centre; the science PSF
+    Each pair is a 41x41 window with one star near its centre (plus, with crowd,
+    the field stars of `field_stars`); the science PSF
     width follows a sequence with seeing jumps (redrawn from U(1, 3) px with
     probability jump_p per stamp), the reference is at 1 px with the noise of a
     30-frame average.  The target is the 21x21 least-squares kernel fitted over
@@ -180,6 +228,11 @@ def _training_chunk(n, seed, device, sky, flux, sig_ref, sig_range, jump_p, ctx)
 
     Rexp = render(np.full(n, sig_ref)) + sky
     Iexp = render(sig) + sky
+    if crowd is not None:
+        stars = field_stars(n, seed + 13, *crowd, device=dev)
+        Rexp += render_field(n, stars, sig_ref, device=dev)
+        Iexp += render_field(n, stars, sig, device=dev)
+        del stars
     R, Vr = synth.reference_image(Rexp, 30, 1.7, seed + 11)
     I, V = synth.calibrated_image(Iexp, 1.7, seed + 12)
     basis = B.make_basis(STAMP, (0.7, 1.5, 3.0), (6, 4, 2), 0, 0)

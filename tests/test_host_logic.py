@@ -161,3 +161,31 @@ def test_kernel_rooflines_pick_the_binding_roof():
     assert abs(v["frac"] - v["achieved"] / 6777.0) < 1e-4
     ridge = 1719.5e12 / 6777e9
     assert 2 * 6 * 441 / 13 > ridge > 2 * 441 / bench.VAR_BYTES_PER_PX
+
+
+def test_training_field_stars_match_the_frame_renderer():
+    # crowded training windows: the field stars of a window rendered by the
+    # training set's separable renderer equal the frame renderer's image of the
+    # same catalogue (same pixel-integrated Gaussian, footprint 5 sigma there)
+    import torch
+    from paper_2207_14304_gb300 import learned
+    n = 5
+    stars = learned.field_stars(n, seed=3, mean=6.0, flux_min=3.0, flux_max=3e4, index=-1.5)
+    widx, x, y, f = stars
+    assert widx.numel() > 0 and bool((widx[1:] >= widx[:-1]).all())
+    assert float(x.min()) >= -5.0 and float(x.max()) < learned.WIN + 5.0
+    assert float(f.min()) >= 3.0 and float(f.max()) <= 3e4
+    sig = np.array([1.0, 1.5, 2.0, 2.5, 3.0])
+    img = learned.render_field(n, stars, sig)
+    for w in range(n):
+        sel = widx == w
+        cat = synth.Catalog(x[sel], y[sel], f[sel])
+        ref = synth.render(cat, learned.WIN, learned.WIN, float(sig[w]))
+        assert torch.allclose(img[w].double(), ref, rtol=1e-5, atol=1e-4 * max(1.0, float(ref.max())))
+    # the reference width is one float for every window
+    one = learned.render_field(n, stars, 1.0)
+    assert one.shape == (n, learned.WIN, learned.WIN)
+    # a star far inside a window keeps its whole flux there
+    st = (torch.tensor([2]), torch.tensor([20.3]), torch.tensor([19.6]), torch.tensor([1234.0], dtype=torch.float64))
+    im = learned.render_field(n, st, 2.0)
+    assert abs(float(im[2].double().sum()) - 1234.0) < 1e-3 and float(im[[0, 1, 3, 4]].abs().sum()) == 0.0
