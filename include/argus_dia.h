@@ -177,6 +177,25 @@ int argus_select_stamps(argus_ctx *ctx, const float *ref, const uint8_t *flags, 
                         int grid_x, int grid_y, int stamp, int khalf, float max_peak, int iso,
                         float iso_frac, int *centers, int *n_stamps, argus_stream stream);
 
+/* Basis convolution on the stamps (the design values of the kernel fit below;
+ * paper Sec. 4.2 direct image subtraction with the Alard-Lupton basis):
+ *   X[(s * nb + m) * stamp^2 + j * stamp + i] =
+ *       sum_{iv, iu} images[m][iv * ksize + iu] ref(x0 + i + r - iu + r, y0 + j + r - iv + r)
+ * with (x0, y0) = centers[s] - stamp/2 - r, r = ksize/2, i.e. X_m = ref (x) image_m
+ * at stamp pixel (i, j); for s < min(*n_stamps, max_stamps); zero for stamps
+ * whose window [x - stamp/2 - r, x + stamp/2 + r]^2 leaves the frame.  ref:
+ * float [h][pitch]; centers: int [max_stamps][2] (x, y); n_stamps: device int;
+ * images: float [nb][ksize^2] (device, 16-byte aligned), nb <= 64; X: float
+ * [max_stamps][nb][stamp^2] (device, 16-byte aligned).  argus_fit_kernel runs the
+ * same convolution on its orthonormalised basis.  21 x 21 stamps with 21 x 21
+ * images run on the tensor cores (FP16 hi/lo operands with a power-of-two
+ * scale per stamp and one for the images, three products, FP32 accumulation:
+ * the FP32 product sums to ~1e-6 relative), the other shapes in FP32 on the
+ * CUDA cores.  A stalled tensor-core pipeline latches ARGUS_ERR_TIMEOUT. */
+int argus_stamp_basis(argus_ctx *ctx, const float *ref, argus_shape shape, const int *centers,
+                      const int *n_stamps, int max_stamps, int stamp, const float *images, int nb,
+                      int ksize, float *X, argus_stream stream);
+
 /* PSF-matching kernel fit (Alard-Lupton least squares; the subtraction of
  * paper Sec. 4.2).  For every pixel of every stamp (side `stamp`, centres
  * centers[s], s < *n_stamps, at most max_stamps):

@@ -195,6 +195,20 @@ def select_stamps(R, flags, gx, gy, stamp, khalf, max_peak, iso=10, iso_frac=0.1
     return cen[:n].copy()
 
 
+def stamp_conv(R, centers, stamp, images):
+    """The basis convolution of ora_stamp_basis with given images [nb][ks*ks]
+    (FP64 sums): X [n_stamps][stamp^2][nb], zero for stamps whose window
+    leaves the frame."""
+    R = _c(R, np.float32); cen = _c(centers, np.int32)
+    img = _c(images, np.float64)
+    nb, kk = img.shape
+    ks = int(round(kk ** 0.5))
+    h, w = R.shape
+    X = np.empty((cen.shape[0], stamp * stamp, nb))
+    lib().ora_stamp_basis(w, h, _p(R), _p(cen), cen.shape[0], stamp, _p(img), nb, ks, _p(X))
+    return X
+
+
 def stamp_basis(R, centers, stamp, b: Basis):
     R = _c(R, np.float32); cen = _c(centers, np.int32)
     h, w = R.shape

@@ -111,6 +111,7 @@ SIGNATURES = {
     "argus_calibrate": ([P, P, SH, C.POINTER(argus_calib), P, P, P, P], I),
     "argus_coadd": ([P, P, I, SH, P, C.POINTER(argus_calib), F, I, P, P, P, P], I),
     "argus_select_stamps": ([P, P, P, SH, I, I, I, I, F, I, F, P, P, P], I),
+    "argus_stamp_basis": ([P, P, SH, P, P, I, I, P, I, I, P, P], I),
     "argus_fit_kernel": ([P, P, P, P, P, SH, P, P, I, I, C.POINTER(argus_basis), I, P, P, P], I),
     "argus_expand_kernel": ([P, C.POINTER(argus_basis), P, P, P, P], I),
     "argus_subtract": ([P, P, P, P, P, P, SH, I, I, I, I, I, I, P, I, P, P, P, P], I),
@@ -396,6 +397,12 @@ def argus_fit_scale_background(ctx, sci, sci_var, ref, flags, shape, centers, n_
                                              _ptr(centers), _ptr(n_stamps), int(max_stamps), int(stamp), _ptr(K),
                                              int(ksize), int(spatial_degree), int(bg_degree), _ptr(bg), _ptr(stats),
                                              _stream(stream)), "argus_fit_scale_background")
+
+
+def argus_stamp_basis(ctx, ref, shape, centers, n_stamps, max_stamps, stamp, images, nb, ksize, X, stream=None):
+    _check(load().argus_stamp_basis(ctx, _ptr(ref), shape, _ptr(centers), _ptr(n_stamps), int(max_stamps),
+                                    int(stamp), _ptr(images), int(nb), int(ksize), _ptr(X), _stream(stream)),
+           "argus_stamp_basis")
 
 
 def argus_fit_kernel(ctx, sci, sci_var, ref, flags, shape, centers, n_stamps, max_stamps, stamp,

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libargusdia.so")
 
-SOURCES = ["api.cu", "calibrate.cu", "coadd.cu", "subtract.cu", "subtract_tc.cu", "detect.cu", "fit.cu", "segments.cu", "segments_tc.cu",
+SOURCES = ["api.cu", "calibrate.cu", "coadd.cu", "subtract.cu", "subtract_tc.cu", "detect.cu", "fit.cu", "stamp_conv_tc.cu", "segments.cu", "segments_tc.cu",
            "cnn.cu", "cnn_tc.cu", "sparse.cu", "background.cu", "proper.cu", "healpix.cu", "frame.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -107,7 +107,8 @@ extern "C" int argus_destroy(argus_ctx* c) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    void* ps[] = {c->d_status, c->basis_img, c->basis_imgf, c->basis_h, c->basis_ab, c->basis_S, c->X, c->rowmeta, c->design,
+    void* ps[] = {c->d_status, c->basis_img, c->basis_imgf, c->basis_h, c->basis_ab, c->basis_S, c->X, c->stamp_b,
+                  c->rowmeta, c->design,
                   c->gram_part, c->M, c->L, c->Dinv, c->vec, c->resid_part, c->cell_key, c->label,
                   c->det_list, c->det_count, c->comp_key, c->comp_npix, c->comp_order,
                   c->row_count};
@@ -146,6 +147,7 @@ extern "C" int argus_create(argus_ctx** out, int device, size_t max_pixels, int 
               dalloc(&c->basis_ab, (size_t)ARGUS_MAX_NB * 2) &&
               dalloc(&c->basis_S, (size_t)ARGUS_MAX_NB * ARGUS_MAX_NB) &&
               dalloc(&c->X, (size_t)max_stamps * ARGUS_MAX_STAMP * ARGUS_MAX_STAMP * ARGUS_MAX_NB) &&
+              dalloc(&c->stamp_b, argus_stamp_conv_tc_bytes()) &&
               dalloc(&c->rowmeta, (size_t)max_stamps * ARGUS_MAX_STAMP * ARGUS_MAX_STAMP * 16) &&
               dalloc(&c->design, ((size_t)max_stamps * ARGUS_MAX_STAMP * ARGUS_MAX_STAMP + 32) * np) &&
               dalloc(&c->gram_part, (size_t)c->gram_parts * np * np) &&

@@ -35,6 +35,7 @@ struct argus_ctx {
 
     // fit scratch
     float* X;            // [max_stamps * 31*31][64] basis-convolved stamp pixels
+    uint8_t* stamp_b;    // argus_stamp_conv_tc_bytes(): packed FP16 basis operands of the tensor-core stamp convolution
     float* rowmeta;      // [max_stamps * 31*31][16] per-row design weights of the fit
     float* design;       // [max_stamps * 31*31 rounded up to 32][np_cols] weighted design matrix (FP32)
     int gram_parts;      // number of partial Gram slots
@@ -98,5 +99,14 @@ size_t argus_cnn_tc_pack_bytes();
 // conv^T(dh_out (h_out > 0)); wpack receives the layer's packed transposed kernel
 int argus_cnn_dgrad_tc(const float* dh_out, const float* h_out, const void* wbf, void* wpack, int layer, int n,
                        float* dh_in, int num_sms, int* status, cudaStream_t st);
+
+// the basis convolution of 21 x 21 stamps with up to 64 images of 21 x 21 taps on
+// the tensor cores (stamp_conv_tc.cu): X[(s nb + m) 441 + pix] = (ref (x) img_m) on
+// stamp s < min(*n_stamps, max_stamps), zero where the stamp's window leaves the
+// frame; bpack receives argus_stamp_conv_tc_bytes() of packed basis operands
+int argus_stamp_conv_tc(const float* ref, long pitch, int w, int h, const int* centers, const int* n_stamps,
+                        int max_stamps, const float* img, int nb, uint8_t* bpack, float* X, int num_sms, int* status,
+                        cudaStream_t st);
+size_t argus_stamp_conv_tc_bytes();
 
 static inline int argus_round_up(int a, int m) { return (a + m - 1) / m * m; }

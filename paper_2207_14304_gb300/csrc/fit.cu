@@ -1923,6 +1923,57 @@ void argus_tri_solve(argus_ctx* ctx, int ld, int n, const double* rhs, int rs, d
     tri_solve_kernel<<<1, 1024, sm, st>>>(ctx->L, ld, n, ctx->Dinv, rhs, rs, x, flag); argus_count_launch(1);
 }
 
+// a4: X[(s nb + m) ss + pix] = (ref (x) img_m) at every pixel of every stamp s <
+// *n_stamps (zero for stamps whose window leaves the frame).  21 x 21 stamps
+// and kernels with at most 64 images run on the tensor cores
+// (stamp_conv_tc.cu), 21 x 21 stamps with 11 x 11 kernels in the register-
+// blocked CUDA-core kernel, everything else in the general one.
+static int stamp_basis_conv(argus_ctx* ctx, const float* ref, const argus_shape& shape, const int* centers,
+                     const int* n_stamps, int max_stamps, int stamp, const float* img, int nb, int ks, float* X,
+                     cudaStream_t st) {
+    if (stamp == SC_ST && ks == 21 && nb <= 64)
+        return argus_stamp_conv_tc(ref, shape.pitch, shape.w, shape.h, centers, n_stamps, max_stamps, img, nb,
+                                   ctx->stamp_b, X, ctx->num_sms, ctx->d_status, st);
+    BasisDev d;
+    memset(&d, 0, sizeof(d));
+    d.ks = ks;
+    d.r = (ks - 1) / 2;
+    d.nb = nb;
+    const int WW = stamp + 2 * d.r, kk = ks * ks;
+    if (stamp == SC_ST && ks == 11 && nb <= 52) {
+        // 13 warps x 4 functions cover up to 52 basis functions
+        const size_t fsm = sizeof(float) * ((size_t)SC_NS * WW * WW + (size_t)nb * kk);
+        const int nblk = (max_stamps + SC_NS - 1) / SC_NS;
+        cudaFuncSetAttribute(stamp_conv_fast_kernel<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+        stamp_conv_fast_kernel<11><<<nblk, 416, fsm, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers,
+                                                           n_stamps, img, X); argus_count_launch(1);
+        return argus_launch_status();
+    }
+    int group = (int)((200 * 1024 / sizeof(float) - (size_t)WW * WW) / kk);
+    if (group > nb) group = nb;
+    if (group < 4 && group < nb) return ARGUS_ERR_UNSUPPORTED;
+    const size_t conv_smem = sizeof(float) * ((size_t)WW * WW + (size_t)group * kk);
+    cudaFuncSetAttribute(stamp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
+    stamp_conv_kernel<<<max_stamps, 256, conv_smem, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers, n_stamps,
+                                                          stamp, img, group, X); argus_count_launch(1);
+    return argus_launch_status();
+}
+
+extern "C" int argus_stamp_basis(argus_ctx* ctx, const float* ref, argus_shape shape, const int* centers,
+                                 const int* n_stamps, int max_stamps, int stamp, const float* images, int nb,
+                                 int ksize, float* X, argus_stream stream) {
+    if (!ctx || !ref || !centers || !n_stamps || !images || !X) return ARGUS_ERR_ARG;
+    if (max_stamps < 1 || max_stamps > ctx->max_stamps || stamp < 1 || stamp > ARGUS_MAX_STAMP || !(stamp & 1))
+        return ARGUS_ERR_ARG;
+    if (nb < 1 || nb > ARGUS_MAX_NB || ksize < 3 || ksize > ARGUS_MAX_KS || !(ksize & 1)) return ARGUS_ERR_ARG;
+    int rc = argus_check_shape(shape, ctx->max_pixels);
+    if (rc) return rc;
+    if (argus_check_ptr16(X) || argus_check_ptr16(images)) return ARGUS_ERR_ALIGN;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ARGUS_ERR_CUDA;
+    return stamp_basis_conv(ctx, ref, shape, centers, n_stamps, max_stamps, stamp, images, nb, ksize, X,
+                            (cudaStream_t)stream);
+}
+
 // Steps of iterative refinement after the first solve: one, with the residual
 // C^T W (I - C c) from the FP32 design and FP64 sums; its relative size is
 // reported as max_step.
@@ -1950,31 +2001,10 @@ extern "C" int argus_fit_kernel(argus_ctx* ctx, const float* sci, const float* s
     rc = argus_basis_prepare(ctx, basis, st);
     if (rc) return rc;
 
-    const int ss = stamp * stamp, WW = stamp + 2 * d.r, kk = d.ks * d.ks;
-    if (stamp == SC_ST && (d.ks == 21 || d.ks == 11) && d.nb <= 52) {
-        // 13 warps x 4 functions cover up to 52 basis functions
-        const size_t fsm = sizeof(float) * ((size_t)SC_NS * WW * WW + (size_t)d.nb * kk);
-        const int nblk = (max_stamps + SC_NS - 1) / SC_NS;
-        if (d.ks == 21) {
-            cudaFuncSetAttribute(stamp_conv_fast_kernel<21>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            stamp_conv_fast_kernel<21><<<nblk, 416, fsm, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers,
-                                                               n_stamps, ctx->basis_imgf, ctx->X); argus_count_launch(1);
-        } else {
-            cudaFuncSetAttribute(stamp_conv_fast_kernel<11>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            stamp_conv_fast_kernel<11><<<nblk, 416, fsm, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers,
-                                                               n_stamps, ctx->basis_imgf, ctx->X); argus_count_launch(1);
-        }
-        if ((rc = argus_launch_status())) return rc;
-    } else {
-    int group = (int)((200 * 1024 / sizeof(float) - (size_t)WW * WW) / kk);
-    if (group > d.nb) group = d.nb;
-    if (group < 4) return ARGUS_ERR_UNSUPPORTED;
-    const size_t conv_smem = sizeof(float) * ((size_t)WW * WW + (size_t)group * kk);
-    cudaFuncSetAttribute(stamp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem);
-    stamp_conv_kernel<<<max_stamps, 256, conv_smem, st>>>(d, ref, shape.pitch, shape.w, shape.h, centers, n_stamps,
-                                                          stamp, ctx->basis_imgf, group, ctx->X); argus_count_launch(1);
-    if ((rc = argus_launch_status())) return rc;
-    }
+    const int ss = stamp * stamp;
+    rc = stamp_basis_conv(ctx, ref, shape, centers, n_stamps, max_stamps, stamp, ctx->basis_imgf, d.nb, d.ks, ctx->X,
+                          st);
+    if (rc) return rc;
 
     GramArgs g;
     g.X = ctx->X; g.sci = sci; g.var = sci_var; g.flags = flags; g.centers = centers; g.n_stamps = n_stamps;
