@@ -29,12 +29,13 @@
 // out lo lo only, so each product is the FP32 product to ~2^-21, and the
 // accumulators are scaled back exactly.
 //
-// Roles (320 threads, one CTA per SM, persistent over stamps): warps 0-3 read
+// Roles (448 threads, one CTA per SM, persistent over stamps): warps 0-3 read
 // the accumulators (thread = TMEM lane = output row of a tile) and write X;
-// warps 4-7 load each stamp's window, find its scale and write the plane (the
+// warps 4-11 load each stamp's window, find its scale and write the plane (the
 // window of the next stamp is loaded while the MMAs of the current one run);
-// warp 8 allocates TMEM and one lane issues the MMAs; warp 9 lane 0 streams the
-// packed basis (12 KB per pair of plane rows, bulk copies into a ring of two).
+// warp 12 allocates TMEM and one lane issues the MMAs; warp 13 lane 0 streams
+// the packed basis (12 KB per pair of plane rows, bulk copies into a ring of
+// four: a pair's 63 MMAs take about as long as one copy's latency).
 // Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_fp16.h>
 
@@ -56,8 +57,11 @@ constexpr int SCT_NPAIR = 11;                // pairs of plane rows (row 21 of t
 constexpr uint32_t SCT_KSTEP_B = 2048;       // B of one K step and part: 64 functions x 16 taps
 constexpr uint32_t SCT_BSLOT = 3 * 2 * SCT_KSTEP_B;   // B of a pair: 3 K steps x 2 parts
 constexpr int SCT_WINF = 1784;               // staged window floats (reads reach W[1759 + 16 + 7])
-constexpr int SCT_THREADS = 320;
-constexpr int SCT_MMA_WARP = 8, SCT_LOAD_WARP = 9;
+constexpr int SCT_NPW = 8;                   // producer warps
+constexpr int SCT_NPT = SCT_NPW * 32;        // producer threads
+constexpr int SCT_NBS = 4;                   // basis ring slots
+constexpr int SCT_MMA_WARP = 4 + SCT_NPW, SCT_LOAD_WARP = SCT_MMA_WARP + 1;
+constexpr int SCT_THREADS = (SCT_LOAD_WARP + 1) * 32;
 constexpr uint32_t SCT_TMEM_COLS = 512;      // 7 tiles x 64 columns used
 constexpr long long SCT_WAIT = 2000000000LL;   // ~1 s of SM clock
 static_assert(SCT_MT * 128 >= SCT_NQ, "the tiles cover every output row");
@@ -67,15 +71,17 @@ static_assert(SCT_MT * 64 <= (int)SCT_TMEM_COLS, "accumulators fit the allocatio
 
 struct SctcShared {
     alignas(128) uint8_t plane[2][SCT_PART];        // [hi | lo][chunk][pixel][8 values]
-    alignas(128) uint8_t bring[2][SCT_BSLOT];       // [slot][K step][hi | lo][2 KB]
+    alignas(128) uint8_t bring[SCT_NBS][SCT_BSLOT];   // [slot][K step][hi | lo][2 KB]
     alignas(16) float win[SCT_WINF];                // the stamp's window, FP32, flattened
-    uint64_t pfull, pempty, tfull, tempty, bfull[2], bempty[2], sfull[4];
+    uint64_t pfull, pempty, tfull, tempty, bfull[SCT_NBS], bempty[SCT_NBS], sfull[4];
     float sinv[4];                                  // 1 / (window scale) per stamp slot
-    float wmax[4];
+    float wmax[SCT_NPW];
     uint32_t tmem;
     int pok;
     int abort;
 };
+
+static_assert(sizeof(SctcShared) + 128 <= 227 * 1024, "one CTA's shared memory");
 
 // The power of two 2^k with m 2^k in [2^13, 2^14) (1 for m = 0 or not finite),
 // k at most 64.
@@ -183,11 +189,11 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
     const int nk = (int)blockIdx.x < ns ? (ns - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     for (int e = tid; e < SCT_WINF; e += SCT_THREADS) S.win[e] = 0.0f;
     if (tid == 0) {
-        tc::mbar_init(&S.pfull, 4);     // the producer warps' lane 0
+        tc::mbar_init(&S.pfull, SCT_NPW);   // the producer warps' lane 0
         tc::mbar_init(&S.pempty, 1);    // an MMA commit
         tc::mbar_init(&S.tfull, 1);     // an MMA commit
         tc::mbar_init(&S.tempty, 4);    // the four accumulator-reading warps
-        for (int i = 0; i < 2; i++) {
+        for (int i = 0; i < SCT_NBS; i++) {
             tc::mbar_init(&S.bfull[i], 1);    // the loader's expect_tx arrival (+ the copy's bytes)
             tc::mbar_init(&S.bempty[i], 1);   // an MMA commit
         }
@@ -203,17 +209,17 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
     tc::fence_after();
     const uint32_t tmem = S.tmem;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < 4 + SCT_NPW) {
         // ---------------- producers: window, scale, plane
-        const int ptid = tid - 128, pw = warp - 4;
+        const int ptid = tid - 128, pw = warp - 4;   // 0 .. SCT_NPT - 1, 0 .. SCT_NPW - 1
         for (int k = 0; k < nk; k++) {
             const int s = (int)blockIdx.x + k * (int)gridDim.x;
-            tc::named_sync(1, 128);   // every producer is done reading the previous window
+            tc::named_sync(1, SCT_NPT);   // every producer is done reading the previous window
             const int xs = __ldg(a.centers + 2 * s), ys = __ldg(a.centers + 2 * s + 1);
             const int x0 = xs - SCT_ST / 2 - (SCT_KS - 1) / 2, y0 = ys - SCT_ST / 2 - (SCT_KS - 1) / 2;
             const bool valid = x0 >= 0 && y0 >= 0 && x0 + SCT_W - 1 <= a.w - 1 && y0 + SCT_W - 1 <= a.h - 1;
             float mx = 0.0f;
-            for (int e = ptid; e < SCT_WN; e += 128) {
+            for (int e = ptid; e < SCT_WN; e += SCT_NPT) {
                 const int wy = e / SCT_W, wx = e - wy * SCT_W;
                 const float v = valid ? __ldg(a.ref + (long)(y0 + wy) * a.pitch + (x0 + wx)) : 0.0f;
                 S.win[e] = v;
@@ -222,8 +228,11 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0) S.wmax[pw] = mx;
-            tc::named_sync(1, 128);
-            const float sc = sct_pow2_scale(fmaxf(fmaxf(S.wmax[0], S.wmax[1]), fmaxf(S.wmax[2], S.wmax[3])));
+            tc::named_sync(1, SCT_NPT);
+            float wm = S.wmax[0];
+#pragma unroll
+            for (int i = 1; i < SCT_NPW; i++) wm = fmaxf(wm, S.wmax[i]);
+            const float sc = sct_pow2_scale(wm);
             if (ptid == 0) {
                 // the epilogue of stamp k - 4 read this slot before the MMAs of stamp k - 2
                 // began, and those finished before the plane of stamp k - 1 was written
@@ -232,13 +241,13 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
                 // the MMAs of the previous stamp are done with the plane
                 S.pok = k == 0 || sct_wait(S, &S.pempty, (uint32_t)(k - 1) & 1u, status);
             }
-            tc::named_sync(1, 128);
+            tc::named_sync(1, SCT_NPT);
             if (!S.pok) break;
             if (k > 0)
                 while (!tc::mbar_try_wait(&S.pempty, (uint32_t)(k - 1) & 1u)) {
                 }
             // plane pixel P, chunk c: W[P + 8c .. P + 8c + 7] scaled, as FP16 hi and lo
-            for (int e = ptid; e < 3 * SCT_NPP; e += 128) {
+            for (int e = ptid; e < 3 * SCT_NPP; e += SCT_NPT) {
                 const int c = e / SCT_NPP, P = e - c * SCT_NPP;
                 const float* src = S.win + P + 8 * c;
                 uint32_t hi[4], lo[4];
@@ -271,9 +280,9 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
                 tc::fence_after();
                 for (int p = 0; p < SCT_NPAIR; p++) {
                     const int g = k * SCT_NPAIR + p;
-                    if (!sct_wait(S, &S.bfull[g & 1], (uint32_t)(g >> 1) & 1u, status)) { run = false; break; }
+                    if (!sct_wait(S, &S.bfull[g % SCT_NBS], (uint32_t)(g / SCT_NBS) & 1u, status)) { run = false; break; }
                     tc::fence_after();
-                    const uint32_t bs = b0 + (uint32_t)(g & 1) * SCT_BSLOT;
+                    const uint32_t bs = b0 + (uint32_t)(g % SCT_NBS) * SCT_BSLOT;
                     for (int t = 0; t < SCT_MT; t++) {
                         const uint32_t d = tmem + (uint32_t)(t * 64);
                         const uint32_t q0 = 128u * (uint32_t)t;
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
                             pending = true;
                         }
                     }
-                    tc::commit(&S.bempty[g & 1]);
+                    tc::commit(&S.bempty[g % SCT_NBS]);
                 }
                 if (!run) break;
                 tc::commit(&S.pempty);
@@ -323,13 +332,14 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
             const int G = nk * SCT_NPAIR;
             int g = 0;
             for (; g < G; g++) {
-                if (g >= 2 && !sct_wait(S, &S.bempty[g & 1], (uint32_t)((g >> 1) - 1) & 1u, status)) break;
-                tc::mbar_arrive_expect_tx(&S.bfull[g & 1], SCT_BSLOT);
-                tc::bulk_g2s(S.bring[g & 1], a.bpack + (size_t)(g % SCT_NPAIR) * SCT_BSLOT, SCT_BSLOT, &S.bfull[g & 1]);
+                const int sl = g % SCT_NBS;
+                if (g >= SCT_NBS && !sct_wait(S, &S.bempty[sl], (uint32_t)(g / SCT_NBS - 1) & 1u, status)) break;
+                tc::mbar_arrive_expect_tx(&S.bfull[sl], SCT_BSLOT);
+                tc::bulk_g2s(S.bring[sl], a.bpack + (size_t)(g % SCT_NPAIR) * SCT_BSLOT, SCT_BSLOT, &S.bfull[sl]);
             }
             // copies in flight land before the CTA exits
-            for (int q = g - 2 < 0 ? 0 : g - 2; q < g; q++)
-                if (!tc::mbar_wait_bounded(&S.bfull[q & 1], (uint32_t)(q >> 1) & 1u, SCT_WAIT)) {
+            for (int q = g - SCT_NBS < 0 ? 0 : g - SCT_NBS; q < g; q++)
+                if (!tc::mbar_wait_bounded(&S.bfull[q % SCT_NBS], (uint32_t)(q / SCT_NBS) & 1u, SCT_WAIT)) {
                     S.abort = 1;
                     argus_latch(status, ARGUS_ERR_TIMEOUT);
                 }
