@@ -271,6 +271,13 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
             const uint32_t idesc = tc::instr_desc(0, 128, 64);   // FP16 operands, FP32 accumulate
             const uint32_t phi = tc::smem_u32(S.plane[0]), plo = tc::smem_u32(S.plane[1]);
             const uint32_t b0 = tc::smem_u32(S.bring[0]);
+            // descriptors at the operands' origins; an operand at a byte offset o is the
+            // origin's descriptor plus o / 16 (the start-address field, which the offsets
+            // keep below 2^14)
+            const uint64_t a01h = tc::smem_desc(phi, SCT_CH, 128), a01l = tc::smem_desc(plo, SCT_CH, 128);
+            const uint64_t a2h = tc::smem_desc(phi + 2 * SCT_CH, SCT_W * 16, 128);
+            const uint64_t a2l = tc::smem_desc(plo + 2 * SCT_CH, SCT_W * 16, 128);
+            const uint64_t bh0 = tc::smem_desc(b0, 1024, 128), bl0 = tc::smem_desc(b0 + SCT_KSTEP_B, 1024, 128);
             int ncommit = 0;        // tfull commits
             bool pending = false;   // MMAs issued since the last tfull commit
             bool run = true;
@@ -282,30 +289,27 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
                     const int g = k * SCT_NPAIR + p;
                     if (!sct_wait(S, &S.bfull[g % SCT_NBS], (uint32_t)(g / SCT_NBS) & 1u, status)) { run = false; break; }
                     tc::fence_after();
-                    const uint32_t bs = b0 + (uint32_t)(g % SCT_NBS) * SCT_BSLOT;
+                    const uint64_t bso = (uint64_t)((g % SCT_NBS) * (SCT_BSLOT / 16));
+                    const uint64_t row = (uint64_t)(SCT_W * 2 * p);          // plane pixel of row 2p (16-byte units)
+                    const bool last = p == SCT_NPAIR - 1;                    // plane row 21 is zero
+#pragma unroll
                     for (int t = 0; t < SCT_MT; t++) {
                         const uint32_t d = tmem + (uint32_t)(t * 64);
-                        const uint32_t q0 = 128u * (uint32_t)t;
-#pragma unroll
-                        for (int ks = 0; ks < 3; ks++) {
-                            if (p == SCT_NPAIR - 1 && ks == 1) continue;   // plane row 21 is zero
-                            uint32_t aoff, lbo;
-                            if (ks < 2) {
-                                aoff = (q0 + (uint32_t)(SCT_W * (2 * p + ks))) * 16;
-                                lbo = SCT_CH;
-                            } else {
-                                aoff = 2 * SCT_CH + (q0 + (uint32_t)(SCT_W * 2 * p)) * 16;
-                                lbo = SCT_W * 16;
-                            }
-                            const uint64_t adh = tc::smem_desc(phi + aoff, lbo, 128), adl = tc::smem_desc(plo + aoff, lbo, 128);
-                            const uint32_t bk = bs + (uint32_t)ks * 2 * SCT_KSTEP_B;
-                            const uint64_t bdh = tc::smem_desc(bk, 1024, 128), bdl = tc::smem_desc(bk + SCT_KSTEP_B, 1024, 128);
-                            tc::mma_bf16(d, adh, bdh, idesc, (p == 0 && ks == 0) ? 0u : 1u);
-                            tc::mma_bf16(d, adh, bdl, idesc, 1u);
-                            tc::mma_bf16(d, adl, bdh, idesc, 1u);
-                            pending = true;
+                        const uint64_t q0 = 128u * (uint64_t)t + row;
+                        // taps 0..15 of row 2p, of row 2p + 1, then taps 16..23 of both
+                        tc::mma_bf16(d, a01h + q0, bh0 + bso, idesc, p == 0 ? 0u : 1u);
+                        tc::mma_bf16(d, a01h + q0, bl0 + bso, idesc, 1u);
+                        tc::mma_bf16(d, a01l + q0, bh0 + bso, idesc, 1u);
+                        if (!last) {
+                            tc::mma_bf16(d, a01h + q0 + SCT_W, bh0 + bso + 256, idesc, 1u);
+                            tc::mma_bf16(d, a01h + q0 + SCT_W, bl0 + bso + 256, idesc, 1u);
+                            tc::mma_bf16(d, a01l + q0 + SCT_W, bh0 + bso + 256, idesc, 1u);
                         }
+                        tc::mma_bf16(d, a2h + q0, bh0 + bso + 512, idesc, 1u);
+                        tc::mma_bf16(d, a2h + q0, bl0 + bso + 512, idesc, 1u);
+                        tc::mma_bf16(d, a2l + q0, bh0 + bso + 512, idesc, 1u);
                     }
+                    pending = true;
                     tc::commit(&S.bempty[g % SCT_NBS]);
                 }
                 if (!run) break;
