@@ -17,7 +17,9 @@
 // Design rows are stamp pixels; the columns are [X_0, p_k X_m (m >= 1),
 // p_k (background)] scaled by sqrt(w), plus the target sqrt(w) I as one extra
 // column, so the Gram of the augmented design holds M = C^T W C, b = C^T W I
-// and I^T W I at once.  X_m = R (x) B'_m by direct 2-D convolution.
+// and I^T W I at once.  X_m = R (x) B'_m by direct 2-D convolution: on the
+// tensor cores for 21 x 21 stamps and kernels (stamp_conv_tc.cu), on the CUDA
+// cores otherwise (below).
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -314,7 +316,8 @@ __device__ __forceinline__ void col_code(const GramArgs& g, int j, int& n, int& 
 }
 
 
-// K3, register-blocked form for 21x21 stamps: three stamps side by side per
+// K3, register-blocked form for 21x21 stamps (used for 11 x 11 kernels; 21 x 21
+// kernels run on the tensor cores): three stamps side by side per
 // CTA (63 columns over two lane-halves), warp g owns basis functions
 // 4g .. 4g+3 (warp-uniform basis loads are broadcasts), a thread owns one
 // column and all 21 rows of its four functions (84 accumulators).  Per tap
