@@ -363,6 +363,32 @@ def test_fit_gaussian_kernel_moments(ora):
 
 
 # --------------------------------------------------------------------------- subtract / variance
+def test_stamp_basis_matches_library_convolution(ora):
+    """The basis convolution on stamps (the fit's design values, Sec. 4.2): at every pixel of a
+    stamp X_m = (R (x) B_m)(x, y), the 'same'-size 2-D convolution of scipy; a unit tap at
+    (du, dv) = (iu - r, iv - r) picks R(x - du, y - dv); stamps whose window leaves the frame are
+    zero (the rule of the fit)."""
+    w, h, stamp, ks = 90, 70, 9, 7
+    r, hs = ks // 2, stamp // 2
+    rng = np.random.default_rng(11)
+    R = rng.uniform(-50, 500, size=(h, w)).astype(np.float32)
+    B = rng.normal(size=(5, ks, ks))
+    B[3] = 0.0; B[3, r + 2, r - 1] = 1.0                      # unit tap at (du, dv) = (-1, 2)
+    cen = np.array([[30, 25], [hs + r, hs + r], [w - 1 - hs - r, h - 1 - hs - r], [hs + r - 1, 40],
+                    [50, h - hs - r]], np.int32)               # the last two leave the frame by one
+    X = ora.stamp_conv(R, cen, stamp, B.reshape(5, ks * ks))
+    assert X.shape == (5, stamp * stamp, 5)
+    full = np.stack([_conv(R.astype(np.float64), B[m]) for m in range(5)], -1)   # [h][w][m]
+    for s, (xs, ys) in enumerate(cen):
+        if s >= 3:
+            assert (X[s] == 0.0).all()
+            continue
+        want = full[ys - hs:ys + hs + 1, xs - hs:xs + hs + 1].reshape(stamp * stamp, 5)
+        np.testing.assert_allclose(X[s], want, rtol=1e-12, atol=1e-9)
+        shifted = R[ys - hs - 2:ys + hs - 1, xs - hs + 1:xs + hs + 2].reshape(-1)
+        np.testing.assert_array_equal(X[s][:, 3], shifted)
+
+
 def test_subtract_exact_model_gives_zero(ora):
     w = h = 80
     b = ora.Basis(ksize=11)
