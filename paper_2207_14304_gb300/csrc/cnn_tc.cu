@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include "argus_internal.cuh"
+#include "split16.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -93,13 +94,6 @@ __device__ __forceinline__ bool wait_or_abort(CnnTcShared& sh, uint64_t* bar, ui
         return false;
     }
     return true;
-}
-
-// Two floats rounded to BF16 and packed, v0 in the low half.
-__device__ __forceinline__ uint32_t bf16x2_rn(float v0, float v1) {
-    uint32_t d;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
-    return d;
 }
 
 // The 32 channels of plane pixel P as BF16 hi and lo parts into both operand sets.

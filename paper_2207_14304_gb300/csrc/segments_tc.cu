@@ -51,6 +51,7 @@
 #include <cuda_fp16.h>
 
 #include "segments_fit.cuh"
+#include "split16.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -97,15 +98,6 @@ __host__ __device__ inline FtLayout ft_layout(int ks, int zs) {
     return L;
 }
 
-// Two floats rounded to FP16 and packed, v0 in the low half; and the FP16 value back.
-__device__ __forceinline__ uint32_t f16x2_rn(float v0, float v1) {
-    uint32_t d;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
-    return d;
-}
-__device__ __forceinline__ float f16_lo(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h & 0xffffu))); }
-__device__ __forceinline__ float f16_hi(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h >> 16))); }
-
 // Packed FP32 pairs (two lanes of one 64-bit register), round to nearest.
 __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
     uint64_t d;
@@ -124,16 +116,6 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
 }
 __device__ __forceinline__ float f2_x(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float f2_y(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
-
-// The power of two 2^k with m 2^k in [2^13, 2^14) (1 for m = 0 or not finite), with k at
-// most 64: a largest |value| below 2^-50 is scaled by 2^64 only, so that the scales and
-// their products stay finite (such values then sit below 2^13 and lose FP16 precision).
-__host__ __device__ inline float ft_pow2_scale(float m) {
-    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
-    int e;
-    frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
-    return ldexpf(1.0f, 14 - e < 64 ? 14 - e : 64);
-}
 
 __device__ __forceinline__ bool ft_wait(FtBar& S, uint64_t* bar, uint32_t parity, int* status) {
     if (tc::mbar_try_wait(bar, parity)) return true;
@@ -280,7 +262,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) seg_fit_tc_kernel(SegFitTcArgs 
         __syncthreads();
         if (tid == 0) {
             for (int w = 1; w < FT_WARPS; w++) mx = fmaxf(mx, wmax[w]);
-            S.bscale = ft_pow2_scale(wmax[0] > mx ? wmax[0] : mx);
+            S.bscale = f16_range_scale(wmax[0] > mx ? wmax[0] : mx);
         }
         __syncthreads();
     }
@@ -617,7 +599,7 @@ __global__ void __launch_bounds__(256) seg_rscale_kernel(const float* ref, long 
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < 8; w++) mx = fmaxf(mx, wmax[w]);
-        rscale[blockIdx.x] = ft_pow2_scale(fmaxf(mx, wmax[0]));
+        rscale[blockIdx.x] = f16_range_scale(fmaxf(mx, wmax[0]));
     }
 }
 

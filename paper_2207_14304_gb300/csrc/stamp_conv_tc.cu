@@ -40,6 +40,7 @@
 #include <cuda_fp16.h>
 
 #include "argus_internal.cuh"
+#include "split16.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -82,23 +83,6 @@ struct SctcShared {
 };
 
 static_assert(sizeof(SctcShared) + 128 <= 227 * 1024, "one CTA's shared memory");
-
-// The power of two 2^k with m 2^k in [2^13, 2^14) (1 for m = 0 or not finite),
-// k at most 64.
-__device__ __forceinline__ float sct_pow2_scale(float m) {
-    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
-    int e;
-    frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
-    return ldexpf(1.0f, 14 - e < 64 ? 14 - e : 64);
-}
-
-__device__ __forceinline__ uint32_t f16x2_rn(float v0, float v1) {
-    uint32_t d;
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(v1), "f"(v0));
-    return d;
-}
-__device__ __forceinline__ float f16_lo(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h & 0xffffu))); }
-__device__ __forceinline__ float f16_hi(uint32_t h) { return __half2float(__ushort_as_half((unsigned short)(h >> 16))); }
 
 __device__ __forceinline__ bool sct_wait(SctcShared& S, uint64_t* bar, uint32_t parity, int* status) {
     if (tc::mbar_try_wait(bar, parity)) return true;
@@ -146,7 +130,7 @@ __global__ void __launch_bounds__(1024) stamp_pack_b_kernel(const float* img, in
     if (tid == 0) {
         float m = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, wmax[w]);
-        s_scale = sct_pow2_scale(m);
+        s_scale = f16_range_scale(m);
         *reinterpret_cast<float*>(bpack + SCT_NPAIR * SCT_BSLOT) = 1.0f / s_scale;
     }
     __syncthreads();
@@ -232,7 +216,7 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
             float wm = S.wmax[0];
 #pragma unroll
             for (int i = 1; i < SCT_NPW; i++) wm = fmaxf(wm, S.wmax[i]);
-            const float sc = sct_pow2_scale(wm);
+            const float sc = f16_range_scale(wm);
             if (ptid == 0) {
                 // the epilogue of stamp k - 4 read this slot before the MMAs of stamp k - 2
                 // began, and those finished before the plane of stamp k - 1 was written

@@ -1,4 +1,4 @@
-// CPU driver of the segment fit's FP16 range scale (segments_tc.cu): ft_pow2_scale, the
+// CPU driver of the segment fit's FP16 range scale (segments_tc.cu): f16_range_scale, the
 // kernels' own host-callable code, for every value of a file.
 // usage: host_segscale in out   (in: f32 [n], out: f32 [n] scales)
 #include <cstdio>
@@ -20,7 +20,7 @@ int main(int argc, char** argv) {
     while (fread(&x, 4, 1, f) == 1) v.push_back(x);
     fclose(f);
     std::vector<float> out(v.size());
-    for (size_t i = 0; i < v.size(); i++) out[i] = ft_pow2_scale(v[i]);
+    for (size_t i = 0; i < v.size(); i++) out[i] = f16_range_scale(v[i]);
     FILE* g = fopen(argv[2], "wb");
     if (!g || fwrite(out.data(), 4, out.size(), g) != out.size()) return 1;
     fclose(g);
