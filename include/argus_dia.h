@@ -180,13 +180,15 @@ int argus_select_stamps(argus_ctx *ctx, const float *ref, const uint8_t *flags, 
 /* Basis convolution on the stamps (the design values of the kernel fit below;
  * paper Sec. 4.2 direct image subtraction with the Alard-Lupton basis):
  *   X[(s * nb + m) * stamp^2 + j * stamp + i] =
- *       sum_{iv, iu} images[m][iv * ksize + iu] ref(x0 + i + r - iu + r, y0 + j + r - iv + r)
- * with (x0, y0) = centers[s] - stamp/2 - r, r = ksize/2, i.e. X_m = ref (x) image_m
- * at stamp pixel (i, j); for s < min(*n_stamps, max_stamps); zero for stamps
- * whose window [x - stamp/2 - r, x + stamp/2 + r]^2 leaves the frame.  ref:
- * float [h][pitch]; centers: int [max_stamps][2] (x, y); n_stamps: device int;
- * images: float [nb][ksize^2] (device, 16-byte aligned), nb <= 64; X: float
- * [max_stamps][nb][stamp^2] (device, 16-byte aligned).  argus_fit_kernel runs the
+ *       sum_{iv, iu} images[m][iv * ksize + iu] ref(x + r - iu, y + r - iv),
+ *   (x, y) = centers[s] - (stamp/2, stamp/2) + (i, j),  r = ksize/2,
+ * i.e. X_m = ref (x) image_m at stamp pixel (i, j); for s < min(*n_stamps, max_stamps),
+ * X of the other stamps untouched; zero for stamps whose window, centers[s] +- (stamp/2 + r)
+ * in x and y, leaves the frame.  ref: float [h][pitch]; centers: int [max_stamps][2] (x, y);
+ * n_stamps: device int; images: float [nb][ksize^2] (device, 16-byte aligned), nb <= 64; X:
+ * float [max_stamps][nb][stamp^2] (device, 16-byte aligned); all caller-owned.  Odd stamp <= 31,
+ * odd ksize <= 31 and max_stamps <= the context's, else ARGUS_ERR_ARG; unaligned images or X:
+ * ARGUS_ERR_ALIGN.  argus_fit_kernel runs the
  * same convolution on its orthonormalised basis.  21 x 21 stamps with 21 x 21
  * images run on the tensor cores (FP16 hi/lo operands with a power-of-two
  * scale per stamp and one for the images, three products, FP32 accumulation:
