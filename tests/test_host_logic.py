@@ -189,3 +189,21 @@ def test_training_field_stars_match_the_frame_renderer():
     st = (torch.tensor([2]), torch.tensor([20.3]), torch.tensor([19.6]), torch.tensor([1234.0], dtype=torch.float64))
     im = learned.render_field(n, st, 2.0)
     assert abs(float(im[2].double().sum()) - 1234.0) < 1e-3 and float(im[[0, 1, 3, 4]].abs().sum()) == 0.0
+
+
+def test_training_field_stars_are_seeded_and_order_independent():
+    # the same seed gives the same field; the rendered windows do not depend on the order
+    # in which the stars are listed (one star per window per pass)
+    import torch
+    from paper_2207_14304_gb300 import learned
+    a = learned.field_stars(7, seed=9, mean=5.0, flux_min=3.0, flux_max=3e4, index=-1.5)
+    b = learned.field_stars(7, seed=9, mean=5.0, flux_min=3.0, flux_max=3e4, index=-1.5)
+    c = learned.field_stars(7, seed=10, mean=5.0, flux_min=3.0, flux_max=3e4, index=-1.5)
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
+    assert not (a[0].numel() == c[0].numel() and all(torch.equal(x, y) for x, y in zip(a, c)))
+    img = learned.render_field(7, a, 1.5)
+    assert torch.equal(img, learned.render_field(7, b, 1.5))
+    perm = torch.randperm(a[0].numel(), generator=torch.Generator().manual_seed(1))
+    shuffled = tuple(t[perm] for t in a)
+    torch.testing.assert_close(learned.render_field(7, shuffled, 1.5), img, rtol=1e-6, atol=1e-4)
+    assert learned.render_field(3, tuple(t[:0] for t in a), 1.0).abs().sum() == 0
