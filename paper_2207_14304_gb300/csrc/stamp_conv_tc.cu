@@ -29,13 +29,13 @@
 // out lo lo only, so each product is the FP32 product to ~2^-21, and the
 // accumulators are scaled back exactly.
 //
-// Roles (448 threads, one CTA per SM, persistent over stamps): warps 0-3 read
+// Roles (480 threads, one CTA per SM, persistent over stamps): warps 0-3 read
 // the accumulators (thread = TMEM lane = output row of a tile) and write X;
 // warps 4-11 load each stamp's window, find its scale and write the plane (the
 // window of the next stamp is loaded while the MMAs of the current one run);
-// warp 12 allocates TMEM and one lane issues the MMAs; warp 13 lane 0 streams
-// the packed basis (12 KB per pair of plane rows, bulk copies into a ring of
-// four: a pair's 63 MMAs take about as long as one copy's latency).
+// warp 12 allocates TMEM; one lane each of warps 12 and 14 issues the MMAs of
+// tiles 0-3 and 4-6; warp 13 lane 0 streams the packed basis (12 KB per pair of
+// plane rows, bulk copies into a ring of four).
 // Every wait is bounded; a timeout latches ARGUS_ERR_TIMEOUT and all roles stop.
 #include <cuda_fp16.h>
 
@@ -61,8 +61,9 @@ constexpr int SCT_WINF = 1784;               // staged window floats (reads reac
 constexpr int SCT_NPW = 8;                   // producer warps
 constexpr int SCT_NPT = SCT_NPW * 32;        // producer threads
 constexpr int SCT_NBS = 4;                   // basis ring slots
-constexpr int SCT_MMA_WARP = 4 + SCT_NPW, SCT_LOAD_WARP = SCT_MMA_WARP + 1;
-constexpr int SCT_THREADS = (SCT_LOAD_WARP + 1) * 32;
+constexpr int SCT_MMA_WARP = 4 + SCT_NPW, SCT_LOAD_WARP = SCT_MMA_WARP + 1, SCT_MMA_WARP2 = SCT_LOAD_WARP + 1;
+constexpr int SCT_THREADS = (SCT_MMA_WARP2 + 1) * 32;
+constexpr int SCT_T1 = 4;                    // tiles 0..3 on the first MMA issuer, 4..6 on the second
 constexpr uint32_t SCT_TMEM_COLS = 512;      // 7 tiles x 64 columns used
 constexpr long long SCT_WAIT = 2000000000LL;   // ~1 s of SM clock
 static_assert(SCT_MT * 128 >= SCT_NQ, "the tiles cover every output row");
@@ -174,12 +175,12 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
     for (int e = tid; e < SCT_WINF; e += SCT_THREADS) S.win[e] = 0.0f;
     if (tid == 0) {
         tc::mbar_init(&S.pfull, SCT_NPW);   // the producer warps' lane 0
-        tc::mbar_init(&S.pempty, 1);    // an MMA commit
-        tc::mbar_init(&S.tfull, 1);     // an MMA commit
+        tc::mbar_init(&S.pempty, 2);    // both MMA issuers' commits
+        tc::mbar_init(&S.tfull, 2);     // both MMA issuers' commits
         tc::mbar_init(&S.tempty, 4);    // the four accumulator-reading warps
         for (int i = 0; i < SCT_NBS; i++) {
             tc::mbar_init(&S.bfull[i], 1);    // the loader's expect_tx arrival (+ the copy's bytes)
-            tc::mbar_init(&S.bempty[i], 1);   // an MMA commit
+            tc::mbar_init(&S.bempty[i], 2);   // both MMA issuers' commits
         }
         for (int i = 0; i < 4; i++) tc::mbar_init(&S.sfull[i], 1);
         S.abort = 0;
@@ -249,8 +250,11 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&S.pfull);
         }
-    } else if (warp == SCT_MMA_WARP) {
-        // ---------------- MMA issuer
+    } else if (warp == SCT_MMA_WARP || warp == SCT_MMA_WARP2) {
+        // ---------------- MMA issuers: one lane of each issues the MMAs of its tiles
+        // (a thread that issues an MMA waits for it to be accepted; two issuers keep the
+        // narrow MMAs of the two tile sets in flight together)
+        const int t0 = warp == SCT_MMA_WARP ? 0 : SCT_T1, t1 = warp == SCT_MMA_WARP ? SCT_T1 : SCT_MT;
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc(0, 128, 64);   // FP16 operands, FP32 accumulate
             const uint32_t phi = tc::smem_u32(S.plane[0]), plo = tc::smem_u32(S.plane[1]);
@@ -276,8 +280,7 @@ __global__ void __launch_bounds__(SCT_THREADS, 1) stamp_conv_tc_kernel(SctcArgs 
                     const uint64_t bso = (uint64_t)((g % SCT_NBS) * (SCT_BSLOT / 16));
                     const uint64_t row = (uint64_t)(SCT_W * 2 * p);          // plane pixel of row 2p (16-byte units)
                     const bool last = p == SCT_NPAIR - 1;                    // plane row 21 is zero
-#pragma unroll
-                    for (int t = 0; t < SCT_MT; t++) {
+                    for (int t = t0; t < t1; t++) {
                         const uint32_t d = tmem + (uint32_t)(t * 64);
                         const uint64_t q0 = 128u * (uint64_t)t + row;
                         // taps 0..15 of row 2p, of row 2p + 1, then taps 16..23 of both
