@@ -207,3 +207,23 @@ def test_training_field_stars_are_seeded_and_order_independent():
     shuffled = tuple(t[perm] for t in a)
     torch.testing.assert_close(learned.render_field(7, shuffled, 1.5), img, rtol=1e-6, atol=1e-4)
     assert learned.render_field(3, tuple(t[:0] for t in a), 1.0).abs().sum() == 0
+
+
+def test_reference_arm_line_on_a_small_frame():
+    # the oracle arm end to end on the host cores (a 512 x 512 frame): one JSON line with the
+    # contract's keys, its own cpu_baseline and an e2e object without host-device copies
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--frame", "512", "512"], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT, check=True).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["n_gpus"] == 1 and line["steps"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["frame"] == [512, 512]
